@@ -1,0 +1,153 @@
+"""FP64 CPU oracle for noise-subspace DOA estimation (PHD, MUSIC, EV, MN).
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package. It shares no code with the CUDA
+library in ``paper_2007_14135_gb300``; the two are written independently from the paper
+(Eray & Temizel, arXiv 2007.14135).
+
+The arithmetic lives in ``doa_oracle.c`` (plain C99, FP64, no FMA contraction). This module
+compiles it with gcc on first use and exposes NumPy-friendly wrappers:
+
+  covariance  -- Sec. 3.1 Eq. 3, Table 2 Step-1
+  eigh        -- Table 2 Step-2 (cyclic Jacobi, eigenvalues descending)
+  weighting   -- Table 3 Steps 3-4, explicit M x M matrix C
+  scan        -- Table 2 Step-5 with the steering vector of Eq. 2 (half-wavelength ULA)
+  peaks       -- Table 2 Step-6
+  solve       -- Steps 1-6 for one snapshot matrix and one algorithm
+
+The MLP oracle used for the learned proposal lives in ``oracle/mlp.py`` (NumPy, FP64).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+PHD, MUSIC, EV, MN = 0, 1, 2, 3
+ALG_NAMES = {PHD: "PHD", MUSIC: "MUSIC", EV: "EV", MN: "MN"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "doa_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile doa_oracle.c into liboracle.so with gcc (plain -O2, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            d, i, p = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+            lib.oracle_covariance.argtypes = [p, i, i, i, p]
+            lib.oracle_covariance.restype = None
+            lib.oracle_eigh.argtypes = [p, i, d, i, p, p]
+            lib.oracle_eigh.restype = i
+            lib.oracle_weighting.argtypes = [p, p, i, i, i, p]
+            lib.oracle_weighting.restype = i
+            lib.oracle_scan.argtypes = [p, i, d, d, i, p, p]
+            lib.oracle_scan.restype = None
+            lib.oracle_peaks.argtypes = [p, i, i, p, p]
+            lib.oracle_peaks.restype = i
+            lib.oracle_solve.argtypes = [p, i, i, i, i, i, d, d, i, p, p, p, p, p]
+            lib.oracle_solve.restype = i
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _as_c64_rows(X: np.ndarray) -> np.ndarray:
+    X = np.ascontiguousarray(X, dtype=np.complex64)
+    assert X.ndim == 2
+    return X
+
+
+def covariance(X: np.ndarray) -> np.ndarray:
+    """R = X X^H / N (Eq. 3) for complex64 X of shape (M, N); returns complex128 (M, M)."""
+    X = _as_c64_rows(X)
+    M, N = X.shape
+    R = np.empty((M, M), dtype=np.complex128)
+    _load().oracle_covariance(_ptr(X), M, N, N, _ptr(R))
+    return R
+
+
+def eigh(R: np.ndarray, tol: float = 1e-15, max_sweeps: int = 100):
+    """Cyclic Jacobi eigendecomposition. Returns (evals desc, V with eigenvectors as columns, sweeps).
+
+    sweeps < 0 means the sweep cap was reached (-4).
+    """
+    R = np.ascontiguousarray(R, dtype=np.complex128)
+    M = R.shape[0]
+    ev = np.empty(M, dtype=np.float64)
+    Vt = np.empty((M, M), dtype=np.complex128)  # row i = eigenvector i (column-major V)
+    sweeps = _load().oracle_eigh(_ptr(R), M, tol, max_sweeps, _ptr(ev), _ptr(Vt))
+    return ev, Vt.T.copy(), sweeps
+
+
+def weighting(evals: np.ndarray, V: np.ndarray, D: int, alg: int):
+    """Explicit weighting matrix C of Table 3. Returns (C, status); status 5 = rank failure."""
+    evals = np.ascontiguousarray(evals, dtype=np.float64)
+    M = evals.shape[0]
+    Vt = np.ascontiguousarray(np.asarray(V, dtype=np.complex128).T)
+    C = np.empty((M, M), dtype=np.complex128)
+    st = _load().oracle_weighting(_ptr(evals), _ptr(Vt), M, D, alg, _ptr(C))
+    return C, st
+
+
+def grid_angles(lo: float, step: float, L: int) -> np.ndarray:
+    """theta_k = lo + k*step (rounded product, then rounded sum), in degrees."""
+    k = np.arange(L, dtype=np.float64)
+    return lo + k * step
+
+
+def scan(C: np.ndarray, lo: float, step: float, L: int):
+    """P_k = 1 / (a_k^H C a_k) over the grid. Returns (P float64[L], max relative imaginary part)."""
+    C = np.ascontiguousarray(C, dtype=np.complex128)
+    M = C.shape[0]
+    P = np.empty(L, dtype=np.float64)
+    rel = ctypes.c_double(0.0)
+    _load().oracle_scan(_ptr(C), M, float(lo), float(step), int(L), _ptr(P), ctypes.byref(rel))
+    return P, rel.value
+
+
+def peaks(P: np.ndarray, D: int):
+    """Step-6 peak finding and selection. Returns (idx int32[count], val float64[count])."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    idx = np.empty(max(D, 1), dtype=np.int32)
+    val = np.empty(max(D, 1), dtype=np.float64)
+    n = _load().oracle_peaks(_ptr(P), P.shape[0], D, _ptr(idx), _ptr(val))
+    return idx[:n].copy(), val[:n].copy()
+
+
+def solve(X: np.ndarray, D: int, alg: int, lo: float, step: float, L: int):
+    """Steps 1-6 for one snapshot matrix. Returns dict(P, evals, C, idx, val, status)."""
+    X = _as_c64_rows(X)
+    M, N = X.shape
+    P = np.empty(L, dtype=np.float64)
+    ev = np.empty(M, dtype=np.float64)
+    C = np.empty((M, M), dtype=np.complex128)
+    idx = np.empty(max(D, 1), dtype=np.int32)
+    val = np.empty(max(D, 1), dtype=np.float64)
+    r = _load().oracle_solve(_ptr(X), M, N, N, D, alg, float(lo), float(step), int(L),
+                             _ptr(P), _ptr(ev), _ptr(C), _ptr(idx), _ptr(val))
+    status = -r if r < 0 else 0
+    n = r if r >= 0 else 0
+    return dict(P=P, evals=ev, C=C, idx=idx[:n].copy(), val=val[:n].copy(), status=status)

@@ -1,0 +1,359 @@
+/*
+ * FP64 CPU oracle for noise-subspace narrowband DOA estimation (PHD, MUSIC, EV, MN).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the plain, slow, obviously-correct statement of what
+ * the GPU path computes. Only the test suite, the smoke check and the benchmark's CPU-baseline
+ * leg may load it. It shares no code, header, table or constant with the CUDA library; the two
+ * are written independently from the paper (Eray & Temizel, "Performance Analysis of Noise
+ * Subspace-based Narrowband DOA Estimation Algorithms on CPU and GPU").
+ *
+ * Every step follows the paper in its own order and notation:
+ *   Step-1  sample covariance                      Sec. 3.1, Eq. 3; Table 2 Step-1
+ *   Step-2  Hermitian eigendecomposition of R      Table 2 Step-2 (SVD of a Hermitian PSD matrix
+ *           = its eigendecomposition; singular values = eigenvalues, sorted descending)
+ *   Step-3  noise subspace selection               Table 3 (Step-3 rows)
+ *   Step-4  weighting matrix C (explicit M x M)    Table 3 (Step-4 rows)
+ *   Step-5  pseudospectrum P = 1 / (a^H C a)       Table 2 Step-5, steering vector Eq. 2
+ *   Step-6  peak finding and selection of D peaks  Table 2 Step-6
+ *
+ * Readings where the paper is silent (each one is listed in the design notes):
+ *   - steering vector: Eq. 2 for a uniform linear array on the x axis with half-wavelength
+ *     spacing, phi = 90 deg: a_m(theta) = exp(+j * pi * m * sin(theta)), m = 0..M-1,
+ *     theta in degrees measured from broadside;
+ *   - grid: theta_k = lo + k * step (one rounded multiply, one rounded add, no FMA);
+ *   - PHD takes the last column after the descending sort (the minimum eigenvalue);
+ *   - a peak is the left end i of a maximal plateau [i..j] with P[i-1] < P[i] and
+ *     P[j+1] < P[j]; the end points 0 and L-1 are never peaks; the D largest are kept
+ *     (ties to the lower index) and returned in ascending index order;
+ *   - invP <= 0 gives P = +inf (exact-covariance self-tests only).
+ *
+ * Numbers are FP64 throughout; complex values use C99 `double complex`.
+ * Compile with -ffp-contract=off so that every product and sum is rounded as written.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_PI 3.14159265358979323846
+
+enum { ORACLE_PHD = 0, ORACLE_MUSIC = 1, ORACLE_EV = 2, ORACLE_MN = 3 };
+enum { ORACLE_OK = 0, ORACLE_EINVAL = 1, ORACLE_ENOCONV = 4, ORACLE_ERANK = 5 };
+
+/* ---------------------------------------------------------------------------------------------
+ * Step-1, Eq. 3:  R = (1/N) * sum_{k=1..N} X(t_k) X(t_k)^H.
+ * X: M x N complex64, row-major, interleaved (re, im), row stride ldx complex elements.
+ * R: M x M complex128, row-major, interleaved. Each float is promoted exactly to double.
+ * ------------------------------------------------------------------------------------------- */
+void oracle_covariance(const float *X, int M, int N, int ldx, double *R) {
+  for (int a = 0; a < M; ++a) {
+    for (int b = 0; b < M; ++b) {
+      double complex acc = 0.0;
+      for (int t = 0; t < N; ++t) {
+        const float *xa = X + 2 * ((size_t)a * ldx + t);
+        const float *xb = X + 2 * ((size_t)b * ldx + t);
+        double complex va = (double)xa[0] + I * (double)xa[1];
+        double complex vb = (double)xb[0] + I * (double)xb[1];
+        acc += va * conj(vb);
+      }
+      acc /= (double)N;
+      R[2 * (a * M + b)] = creal(acc);
+      R[2 * (a * M + b) + 1] = cimag(acc);
+    }
+  }
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Step-2: eigendecomposition of the Hermitian matrix R by the cyclic Jacobi method
+ * (Jacobi 1846; Golub & Van Loan, Matrix Computations, Sec. 8.5, extended to complex
+ * Hermitian matrices by a phase factor). Pairs are visited row by row, (0,1), (0,2), ...,
+ * (M-2, M-1). A pair is rotated when |a_pq| > tol * sqrt(|a_pp a_qq|) (and a_pq != 0);
+ * the iteration stops after the first sweep that rotates nothing.
+ *
+ * For the pair (p, q) with a_pq = |a_pq| e^{j phi}, the unitary rotation
+ *     J = [[ c,            s e^{j phi} ],
+ *          [ -s e^{-j phi}, c          ]]      (acting on coordinates p, q)
+ * with tau = (a_qq - a_pp) / (2 |a_pq|), t = sgn(tau) / (|tau| + sqrt(1 + tau^2)),
+ * c = 1 / sqrt(1 + t^2), s = t c, makes (J^H A J)_pq = 0.  A <- J^H A J, V <- V J.
+ *
+ * Output: evals[M] descending (stable: equal values keep their original order),
+ * V: M x M complex128, column-major (column i = eigenvector of evals[i]), interleaved.
+ * Returns the number of sweeps (>= 1), or -ORACLE_ENOCONV when max_sweeps is reached.
+ * ------------------------------------------------------------------------------------------- */
+int oracle_eigh(const double *R, int M, double tol, int max_sweeps, double *evals, double *V) {
+  double complex *A = (double complex *)malloc(sizeof(double complex) * M * M);
+  double complex *W = (double complex *)malloc(sizeof(double complex) * M * M);
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < M; ++j) {
+      A[i * M + j] = R[2 * (i * M + j)] + I * R[2 * (i * M + j) + 1];
+      W[i * M + j] = (i == j) ? 1.0 : 0.0; /* W is row-major here: W[i*M + j] = V(i, j) */
+    }
+  int sweeps = 0, converged = 0;
+  while (sweeps < max_sweeps) {
+    ++sweeps;
+    int rotations = 0;
+    for (int p = 0; p < M - 1; ++p) {
+      for (int q = p + 1; q < M; ++q) {
+        double complex apq = A[p * M + q];
+        double mag = cabs(apq);
+        double app = creal(A[p * M + p]), aqq = creal(A[q * M + q]);
+        if (mag == 0.0 || mag <= tol * sqrt(fabs(app * aqq))) continue;
+        ++rotations;
+        double complex ph = apq / mag; /* e^{j phi} */
+        double tau = (aqq - app) / (2.0 * mag);
+        double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        double c = 1.0 / sqrt(1.0 + t * t);
+        double s = t * c;
+        /* A <- A J : columns p and q */
+        for (int r = 0; r < M; ++r) {
+          double complex xp = A[r * M + p], xq = A[r * M + q];
+          A[r * M + p] = c * xp - s * conj(ph) * xq;
+          A[r * M + q] = s * ph * xp + c * xq;
+        }
+        /* A <- J^H A : rows p and q */
+        for (int k = 0; k < M; ++k) {
+          double complex xp = A[p * M + k], xq = A[q * M + k];
+          A[p * M + k] = c * xp - s * ph * xq;
+          A[q * M + k] = s * conj(ph) * xp + c * xq;
+        }
+        /* the rotation annihilates a_pq; the diagonal of a Hermitian matrix is real */
+        A[p * M + q] = 0.0;
+        A[q * M + p] = 0.0;
+        A[p * M + p] = creal(A[p * M + p]);
+        A[q * M + q] = creal(A[q * M + q]);
+        /* V <- V J */
+        for (int r = 0; r < M; ++r) {
+          double complex xp = W[r * M + p], xq = W[r * M + q];
+          W[r * M + p] = c * xp - s * conj(ph) * xq;
+          W[r * M + q] = s * ph * xp + c * xq;
+        }
+      }
+    }
+    if (rotations == 0) {
+      converged = 1;
+      break;
+    }
+  }
+  /* stable descending sort of the eigenvalues (insertion sort on an index permutation) */
+  int *order = (int *)malloc(sizeof(int) * M);
+  for (int i = 0; i < M; ++i) order[i] = i;
+  for (int i = 1; i < M; ++i) {
+    int cur = order[i];
+    double v = creal(A[cur * M + cur]);
+    int j = i - 1;
+    while (j >= 0 && creal(A[order[j] * M + order[j]]) < v) {
+      order[j + 1] = order[j];
+      --j;
+    }
+    order[j + 1] = cur;
+  }
+  for (int i = 0; i < M; ++i) {
+    int src = order[i];
+    evals[i] = creal(A[src * M + src]);
+    for (int r = 0; r < M; ++r) {
+      V[2 * (i * M + r)] = creal(W[r * M + src]);
+      V[2 * (i * M + r) + 1] = cimag(W[r * M + src]);
+    }
+  }
+  free(order);
+  free(W);
+  free(A);
+  return converged ? sweeps : -ORACLE_ENOCONV;
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Steps 3 and 4 (Table 3): noise subspace selection and the explicit weighting matrix C.
+ * evals[M] descending, V column-major (as returned by oracle_eigh); D = number of sources.
+ *   PHD   : e_min = column of the minimum eigenvalue;      C = e_min e_min^H
+ *   MUSIC : E_n = columns D..M-1 (0-based);                C = E_n E_n^H
+ *   EV    : E_{n,w} = E_n with column i scaled by 1/lambda_i;  C = E_{n,w} E_n^H
+ *   MN    : P_n = E_n E_n^H, u = [1, 0, ..., 0]^T, lambda = (u^H P_n u)^{-1},
+ *           valph = P_n lambda u;                          C = valph valph^H
+ * C: M x M complex128 row-major interleaved. Returns ORACLE_OK, ORACLE_EINVAL or ORACLE_ERANK
+ * (EV with a non-positive noise eigenvalue; MN with u^H P_n u == 0).
+ * ------------------------------------------------------------------------------------------- */
+int oracle_weighting(const double *evals, const double *V, int M, int D, int alg, double *C) {
+  if (M < 1 || D < 0 || D >= M) return ORACLE_EINVAL;
+  double complex *Vc = (double complex *)malloc(sizeof(double complex) * M * M);
+  double complex *Cm = (double complex *)calloc((size_t)M * M, sizeof(double complex));
+  for (int col = 0; col < M; ++col)
+    for (int r = 0; r < M; ++r) Vc[col * M + r] = V[2 * (col * M + r)] + I * V[2 * (col * M + r) + 1];
+#define VCOL(col, r) Vc[(col) * M + (r)]
+  int status = ORACLE_OK;
+  if (alg == ORACLE_PHD) {
+    /* minIdx <- min(d.diag): the eigenvalues are sorted descending, so the minimum is last */
+    int minIdx = M - 1;
+    for (int i = 0; i < M; ++i)
+      for (int k = 0; k < M; ++k) Cm[i * M + k] = VCOL(minIdx, i) * conj(VCOL(minIdx, k));
+  } else if (alg == ORACLE_MUSIC) {
+    for (int i = 0; i < M; ++i)
+      for (int k = 0; k < M; ++k) {
+        double complex acc = 0.0;
+        for (int col = D; col < M; ++col) acc += VCOL(col, i) * conj(VCOL(col, k));
+        Cm[i * M + k] = acc;
+      }
+  } else if (alg == ORACLE_EV) {
+    for (int col = D; col < M; ++col)
+      if (!(evals[col] > 0.0)) status = ORACLE_ERANK;
+    if (status == ORACLE_OK)
+      for (int i = 0; i < M; ++i)
+        for (int k = 0; k < M; ++k) {
+          double complex acc = 0.0;
+          for (int col = D; col < M; ++col) acc += (VCOL(col, i) * (1.0 / evals[col])) * conj(VCOL(col, k));
+          Cm[i * M + k] = acc;
+        }
+  } else if (alg == ORACLE_MN) {
+    double complex *Pn = (double complex *)calloc((size_t)M * M, sizeof(double complex));
+    for (int i = 0; i < M; ++i)
+      for (int k = 0; k < M; ++k) {
+        double complex acc = 0.0;
+        for (int col = D; col < M; ++col) acc += VCOL(col, i) * conj(VCOL(col, k));
+        Pn[i * M + k] = acc;
+      }
+    double uPu = creal(Pn[0]); /* u^H P_n u with u = e_1 */
+    if (!(uPu > 0.0)) {
+      status = ORACLE_ERANK;
+    } else {
+      double lambda = 1.0 / uPu;
+      double complex *valph = (double complex *)malloc(sizeof(double complex) * M);
+      for (int i = 0; i < M; ++i) valph[i] = Pn[i * M + 0] * lambda; /* P_n * lambda * u */
+      for (int i = 0; i < M; ++i)
+        for (int k = 0; k < M; ++k) Cm[i * M + k] = valph[i] * conj(valph[k]);
+      free(valph);
+    }
+    free(Pn);
+  } else {
+    status = ORACLE_EINVAL;
+  }
+#undef VCOL
+  for (int i = 0; i < M * M; ++i) {
+    C[2 * i] = creal(Cm[i]);
+    C[2 * i + 1] = cimag(Cm[i]);
+  }
+  free(Cm);
+  free(Vc);
+  return status;
+}
+
+/* Eq. 2 for the half-wavelength uniform linear array: a_m = exp(j pi m sin(theta)). */
+static void oracle_steering(int M, double theta_deg, double complex *a) {
+  double s = sin(theta_deg * (ORACLE_PI / 180.0));
+  for (int m = 0; m < M; ++m) {
+    double phase = ORACLE_PI * (double)m * s;
+    a[m] = cos(phase) + I * sin(phase);
+  }
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Step-5 (Table 2): for every grid angle theta_k = lo + k*step, k = 0..L-1,
+ *   invP_k = a_k^H C a_k,  P_k = 1 / invP_k.
+ * C: M x M complex128 row-major interleaved. P: L doubles. The imaginary part of invP is
+ * returned through max_rel_imag (max over k of |Im invP| / |Re invP|), which is zero up to
+ * rounding for a Hermitian C. invP <= 0 gives P = +inf.
+ * ------------------------------------------------------------------------------------------- */
+void oracle_scan(const double *C, int M, double lo, double step, int L, double *P, double *max_rel_imag) {
+  double complex *Cm = (double complex *)malloc(sizeof(double complex) * M * M);
+  double complex *a = (double complex *)malloc(sizeof(double complex) * M);
+  for (int i = 0; i < M * M; ++i) Cm[i] = C[2 * i] + I * C[2 * i + 1];
+  double worst = 0.0;
+  for (int k = 0; k < L; ++k) {
+    double kstep = (double)k * step;
+    double theta = lo + kstep;
+    oracle_steering(M, theta, a);
+    double complex invP = 0.0;
+    for (int i = 0; i < M; ++i) {
+      double complex row = 0.0;
+      for (int j = 0; j < M; ++j) row += Cm[i * M + j] * a[j];
+      invP += conj(a[i]) * row;
+    }
+    double re = creal(invP);
+    if (re != 0.0) {
+      double r = fabs(cimag(invP)) / fabs(re);
+      if (r > worst) worst = r;
+    }
+    P[k] = (re > 0.0) ? 1.0 / re : INFINITY;
+  }
+  if (max_rel_imag) *max_rel_imag = worst;
+  free(a);
+  free(Cm);
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Step-6 (Table 2): findPeaks then PeakSelection(peakVals, inds, D).
+ * A peak is the left end i of a maximal run [i..j] of equal values with 1 <= i, j <= L-2,
+ * P[i-1] < P[i] and P[j+1] < P[j]. The D largest values are selected (equal values: lower
+ * index first) and written to idx/val in ascending index order. Returns the count (<= D).
+ * ------------------------------------------------------------------------------------------- */
+int oracle_peaks(const double *P, int L, int D, int *idx, double *val) {
+  int cap = 0, n = 0;
+  int *cand = NULL;
+  for (int i = 1; i <= L - 2; ++i) {
+    if (!(P[i - 1] < P[i])) continue;
+    int j = i;
+    while (j + 1 <= L - 1 && P[j + 1] == P[i]) ++j;
+    if (j + 1 <= L - 1 && P[j + 1] < P[j]) {
+      if (n == cap) {
+        cap = cap ? 2 * cap : 64;
+        cand = (int *)realloc(cand, sizeof(int) * cap);
+      }
+      cand[n++] = i;
+    }
+  }
+  /* order candidates by (value descending, index ascending): insertion sort, stable on index */
+  for (int a = 1; a < n; ++a) {
+    int cur = cand[a];
+    int b = a - 1;
+    while (b >= 0 && (P[cand[b]] < P[cur])) {
+      cand[b + 1] = cand[b];
+      --b;
+    }
+    cand[b + 1] = cur;
+  }
+  int count = n < D ? n : D;
+  /* ascending index order for the selected ones */
+  for (int a = 1; a < count; ++a) {
+    int cur = cand[a];
+    int b = a - 1;
+    while (b >= 0 && cand[b] > cur) {
+      cand[b + 1] = cand[b];
+      --b;
+    }
+    cand[b + 1] = cur;
+  }
+  for (int a = 0; a < count; ++a) {
+    idx[a] = cand[a];
+    val[a] = P[cand[a]];
+  }
+  free(cand);
+  return count;
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Whole method for one snapshot matrix and one algorithm (Table 2, Steps 1-6).
+ * Outputs: P[L], evals[M], C[M*M*2], idx/val[D]; returns count of peaks (>= 0) or -status.
+ * ------------------------------------------------------------------------------------------- */
+int oracle_solve(const float *X, int M, int N, int ldx, int D, int alg, double lo, double step, int L,
+                 double *P, double *evals, double *C, int *idx, double *val) {
+  if (M < 2 || N < 1 || L < 3 || D < 0 || D >= M) return -ORACLE_EINVAL;
+  double *R = (double *)malloc(sizeof(double) * 2 * M * M);
+  double *V = (double *)malloc(sizeof(double) * 2 * M * M);
+  oracle_covariance(X, M, N, ldx, R);
+  int sweeps = oracle_eigh(R, M, 1e-15, 100, evals, V);
+  int status = 0;
+  if (sweeps < 0) {
+    status = -sweeps;
+  } else {
+    int st = oracle_weighting(evals, V, M, D, alg, C);
+    if (st != ORACLE_OK) status = st;
+  }
+  int count = 0;
+  if (status == 0) {
+    double rel_imag = 0.0;
+    oracle_scan(C, M, lo, step, L, P, &rel_imag);
+    count = oracle_peaks(P, L, D, idx, val);
+  }
+  free(V);
+  free(R);
+  return status ? -status : count;
+}

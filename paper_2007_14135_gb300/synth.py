@@ -1,0 +1,196 @@
+"""Seeded synthetic array snapshots (the signal model of Sec. 3.1, Eq. 1 and Table 1).
+
+This module only generates inputs; it holds none of the estimation method's arithmetic
+(no covariance, decomposition, spectrum or peak code). Both the CUDA path and the FP64
+oracle consume exactly the complex64 bytes produced here.
+
+Model (Eq. 1): X(t) = A(theta) S(t) + W(t) for a half-wavelength uniform linear array of M
+omnidirectional elements on the x axis (Eq. 2 with x_m = m lambda/2, y = z = 0, phi = 90 deg),
+so the array response of source i is exp(+j pi m sin(theta_i)), m = 0..M-1.
+Sources are unit-power circular complex Gaussian, s ~ CN(0, 1) = (g1 + j g2)/sqrt(2), mutually
+independent (uncorrelated narrowband sources); noise is white CN(0, sigma^2) per element with
+sigma^2 = 10^(-SNR/10), one SNR per instance shared by all sources.
+
+Random numbers come from NumPy's Philox4x32-10 counter-based generator (Salmon et al.,
+SC'11) keyed by the instance seed, so every instance is reproducible on any machine.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+GRID_LO = -90.0
+GRID_HI = 90.0
+
+
+def grid_size(step: float, lo: float = GRID_LO, hi: float = GRID_HI) -> int:
+    """Number of points of the grid lo:step:hi (inclusive)."""
+    return int(round((hi - lo) / step)) + 1
+
+
+@dataclasses.dataclass
+class Instance:
+    """One snapshot matrix with its ground truth and its scan grid."""
+    X: np.ndarray            # complex64 (M, N), row-major: row m = time series of element m
+    M: int
+    d: int
+    N: int
+    angles: np.ndarray       # true DOAs in degrees, ascending
+    snr_db: float
+    lo: float                # scan grid theta_k = lo + k*step, k = 0..L-1
+    step: float
+    L: int
+    seed: int
+    alg: int = 1             # algorithm for single-algorithm workloads (0 PHD, 1 MUSIC, 2 EV, 3 MN)
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=int(seed)))
+
+
+def _source_response(M: int, angles_deg: Sequence[float]) -> np.ndarray:
+    """Array response of the sources, (M, d) complex128: exp(j pi m sin(theta_i))."""
+    m = np.arange(M, dtype=np.float64)[:, None]
+    s = np.sin(np.deg2rad(np.asarray(angles_deg, dtype=np.float64)))[None, :]
+    return np.exp(1j * np.pi * m * s)
+
+
+def draw_angles(rng: np.random.Generator, d: int, lo: float, hi: float, min_sep: float,
+                max_tries: int = 10000) -> np.ndarray:
+    """d angles uniform in [lo, hi] with pairwise separation >= min_sep (rejection sampling)."""
+    for _ in range(max_tries):
+        a = np.sort(rng.uniform(lo, hi, size=d))
+        if d < 2 or np.min(np.diff(a)) >= min_sep:
+            return a
+    raise RuntimeError("could not draw separated angles")
+
+
+def snapshots(rng: np.random.Generator, M: int, N: int, angles_deg: Sequence[float],
+              snr_db: float) -> np.ndarray:
+    """X = A S + W as complex64 (M, N)."""
+    d = len(angles_deg)
+    sigma = math.sqrt(10.0 ** (-snr_db / 10.0))
+    inv_sqrt2 = 1.0 / math.sqrt(2.0)
+    if d > 0:
+        g = rng.standard_normal((2, d, N), dtype=np.float32)
+        S = (g[0].astype(np.float64) + 1j * g[1].astype(np.float64)) * inv_sqrt2
+        X = _source_response(M, angles_deg) @ S
+    else:
+        X = np.zeros((M, N), dtype=np.complex128)
+    w = rng.standard_normal((2, M, N), dtype=np.float32)
+    X += (w[0].astype(np.float64) + 1j * w[1].astype(np.float64)) * (sigma * inv_sqrt2)
+    return X.astype(np.complex64)
+
+
+# ---------------------------------------------------------------------------------------------
+# Workload recipes. Each one is a seeded function of the instance number.
+# ---------------------------------------------------------------------------------------------
+
+def single_c1(seed: int = 20071413) -> Instance:
+    """M=8 ULA, two unit-power sources at -20 and 35 deg, SNR 10 dB, N=1024, 0.1 deg grid."""
+    M, N, snr, step = 8, 1024, 10.0, 0.1
+    ang = np.array([-20.0, 35.0])
+    X = snapshots(_rng(seed), M, N, ang, snr)
+    return Instance(X, M, 2, N, ang, snr, GRID_LO, step, grid_size(step), seed)
+
+
+def paper_density(i: int, base_seed: int = 20071414, N: int = 4096) -> Instance:
+    """M=16, d=4 in U[-60,60] with 5 deg separation, SNR U[0,20] dB, N=4096, 0.01 deg grid."""
+    seed = base_seed + i
+    rng = _rng(seed)
+    M, d, step = 16, 4, 0.01
+    ang = draw_angles(rng, d, -60.0, 60.0, 5.0)
+    snr = float(rng.uniform(0.0, 20.0))
+    X = snapshots(rng, M, N, ang, snr)
+    return Instance(X, M, d, N, ang, snr, GRID_LO, step, grid_size(step), seed)
+
+
+def paper_density_batch(count: int, base_seed: int = 20071414, N: int = 4096):
+    """`count` independent replicas of paper_density as one contiguous complex64 (count, M, N)."""
+    M = 16
+    X = np.empty((count, M, N), dtype=np.complex64)
+    meta = []
+    for i in range(count):
+        inst = paper_density(i, base_seed, N)
+        X[i] = inst.X
+        inst.X = None
+        meta.append(inst)
+    return X, meta
+
+
+@dataclasses.dataclass
+class ProblemSpec:
+    """Shape and truth of one problem of the uneven batch (X generated on demand)."""
+    index: int
+    M: int
+    d: int
+    N: int
+    step: float
+    L: int
+    alg: int
+    angles: np.ndarray
+    snr_db: float
+    seed: int
+
+
+def uneven_specs(count: int = 4096, seed: int = 20071415) -> List[ProblemSpec]:
+    """Uneven batch: M in {8,12,16,32}, d in U{1..M/2}, N in U{256..8192}, step in
+    {0.1, 0.01, 0.001} deg, algorithm uniform over PHD/MUSIC/EV/MN, angles U[-60,60] with
+    5 deg separation, SNR U[0,20] dB."""
+    rng = _rng(seed)
+    specs = []
+    for i in range(count):
+        M = int(rng.choice([8, 12, 16, 32]))
+        d = int(rng.integers(1, M // 2 + 1))
+        N = int(rng.integers(256, 8193))
+        step = float(rng.choice([0.1, 0.01, 0.001]))
+        alg = int(rng.integers(0, 4))
+        ang = draw_angles(rng, d, -60.0, 60.0, 5.0)
+        snr = float(rng.uniform(0.0, 20.0))
+        specs.append(ProblemSpec(i, M, d, N, step, grid_size(step), alg, ang, snr,
+                                 seed * 100003 + i))
+    return specs
+
+
+def uneven_instance(spec: ProblemSpec) -> Instance:
+    X = snapshots(_rng(spec.seed), spec.M, spec.N, spec.angles, spec.snr_db)
+    return Instance(X, spec.M, spec.d, spec.N, spec.angles, spec.snr_db, GRID_LO, spec.step,
+                    spec.L, spec.seed, spec.alg)
+
+
+def large_array(i: int, base_seed: int = 20071416) -> Instance:
+    """M=64, d=8 in U[-60,60] with 1 deg separation, SNR U[0,15] dB, N=16384, 0.0005 deg grid."""
+    seed = base_seed + i
+    rng = _rng(seed)
+    M, d, N, step = 64, 8, 16384, 0.0005
+    ang = draw_angles(rng, d, -60.0, 60.0, 1.0)
+    snr = float(rng.uniform(0.0, 15.0))
+    X = snapshots(rng, M, N, ang, snr)
+    return Instance(X, M, d, N, ang, snr, GRID_LO, step, grid_size(step), seed)
+
+
+def proposal_instance(i: int, base_seed: int = 20071418, N: int = 2048) -> Instance:
+    """M=16, d in U{1..6}, SNR U[-5,20] dB, angles U[-80,80] with 3 deg separation, N=2048,
+    0.001 deg fine grid."""
+    seed = base_seed * 1000003 + i
+    rng = _rng(seed)
+    M = 16
+    d = int(rng.integers(1, 7))
+    ang = draw_angles(rng, d, -80.0, 80.0, 3.0)
+    snr = float(rng.uniform(-5.0, 20.0))
+    X = snapshots(rng, M, N, ang, snr)
+    step = 0.001
+    return Instance(X, M, d, N, ang, snr, GRID_LO, step, grid_size(step), seed)
+
+
+def custom(M: int, d: int, N: int, angles: Optional[Sequence[float]], snr_db: float, step: float,
+           seed: int) -> Instance:
+    """Arbitrary instance for tests (angles None -> drawn U[-60,60] with 5 deg separation)."""
+    rng = _rng(seed)
+    ang = (np.sort(np.asarray(angles, dtype=np.float64)) if angles is not None
+           else draw_angles(rng, d, -60.0, 60.0, 5.0))
+    X = snapshots(rng, M, N, ang, snr_db)
+    return Instance(X, M, d, N, ang, snr_db, GRID_LO, step, grid_size(step), seed)
