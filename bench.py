@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Throughput of the noise-subspace DOA hot path (PHD, MUSIC, EV, MN) on GB300.
+
+Workload (one step): a batch of independent ULA problems shaped like the paper-density
+configuration -- M=16 elements, d=4 sources in U[-60,60] deg with 5 deg separation, SNR U[0,20]
+dB, N=4096 complex64 snapshots, scan -90:0.01:90 deg (L=18001) -- each solved with all four
+algorithms: covariance, FP64 Jacobi eig + noise subspace, fused FP32 scan, peak picking, all in
+the library's CUDA kernels through one doa_solve_batch call. Inputs are seeded synthetic data
+(Eq. 1) resident in HBM; per-GPU batch fixed (weak scaling), no collective on the data path.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on a bounded sample
+of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "scan points/s and DOA solves/s vs plain GPU form at equal peak-index accuracy"
+M, D, N_SNAP, STEP, LO = 16, 4, 4096, 0.01, -90.0
+ALGS = (0, 1, 2, 3)
+SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3   # derived FFMA peak, 80.5 TFLOP/s
+FP64_PEAK_TFLOPS = 1.25                                          # nominal FP64 rate of the part
+
+
+def grid_L():
+    return int(round(180.0 / STEP)) + 1
+
+
+def workload_name(batch):
+    return (f"paper-density batch: {batch} ULA problems M={M}, d={D}, N={N_SNAP} complex64 snapshots, "
+            f"grid -90:{STEP}:90 deg (L={grid_L()}), PHD+MUSIC+EV+MN on each")
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# --------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------- oracle leg
+def _oracle_task(args):
+    X, alg = args
+    import oracle
+    r = oracle.solve(X, D, alg, LO, STEP, grid_L())
+    return alg, r["idx"], r["P"].astype(np.float32), r["status"]
+
+
+def oracle_sample(Xs, workers):
+    """Times the FP64 oracle on the given instances x all four algorithms (spawned workers)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    tasks = [(X, a) for X in Xs for a in ALGS]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(workers) as pool:
+        warm = pool.map(_oracle_task, tasks[:workers])      # imports + library load, untimed
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_task, tasks)
+    dt = time.perf_counter() - t0
+    del warm
+    return res, dt
+
+
+# --------------------------------------------------------------------------------- GPU leg
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2007_14135_gb300 import synth
+    # inputs first (spawned generator processes, before any CUDA call)
+    Xh, meta = synth.paper_density_batch_parallel(args.batch, base_seed=20071414 + rank * args.batch)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2007_14135_gb300 import build
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_2007_14135_gb300", "libdoa.so")):
+        build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2007_14135_gb300 import doa
+
+    B, L = args.batch, grid_L()
+    nalg = len(ALGS)
+    dev = torch.device("cuda", local)
+    X = torch.from_numpy(Xh).to(dev)
+    P = torch.empty((B, nalg, L), dtype=torch.float32, device=dev)
+    idx = torch.empty((B, nalg, D), dtype=torch.int32, device=dev)
+    val = torch.empty((B, nalg, D), dtype=torch.float32, device=dev)
+    cnt = torch.empty((B, nalg), dtype=torch.int32, device=dev)
+    status = torch.empty(B, dtype=torch.int32, device=dev)
+    g = doa.grid(LO, STEP, L)
+    probs = [doa.make_problem(X[i], D, 0xF, g, P[i], idx[i], val[i], cnt[i]) for i in range(B)]
+    plan = doa.BatchPlan(probs, device=str(dev))
+    ws = doa.workspace(plan, device=str(dev))
+    stream = torch.cuda.current_stream(dev)
+
+    hdr = plan.host[:128].view(np.int32)
+    # launches per solve: phase tables, covariance (+ chunk reduce), eig per M bucket, scan per M bucket, peaks
+    nreduce = int(hdr[5])
+    eig_b = sum(int(c) > 0 for c in hdr[6:10])
+    scan_b = sum(int(c) > 0 for c in hdr[10:14])
+    launches_per_step = 1 + 1 + (nreduce > 0) + eig_b + scan_b + 1
+
+    def step(events=None):
+        doa.doa_solve_batch(plan, ws, status, stage_events=events, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    st = status.cpu().numpy()
+    if np.any(st != 0):
+        raise RuntimeError(f"device status errors: {np.unique(st, return_counts=True)}")
+
+    nst = doa.BATCH_STAGES + 1
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nst)] for _ in range(args.steps)]
+    t_begin = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_begin.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = t_begin.elapsed_time(t_end) / args.steps
+    stage_ms = [statistics.fmean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
+                for i in range(doa.BATCH_STAGES)]
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- end to end through the C ABI from pinned host buffers: H2D of X, solve, D2H of the peaks
+    Xpin = torch.from_numpy(Xh).pin_memory()
+    out_idx = torch.empty(idx.shape, dtype=idx.dtype).pin_memory()
+    out_val = torch.empty(val.shape, dtype=val.dtype).pin_memory()
+    out_cnt = torch.empty(cnt.shape, dtype=cnt.dtype).pin_memory()
+    out_st = torch.empty(status.shape, dtype=status.dtype).pin_memory()
+    h2d = Xpin.numel() * Xpin.element_size()
+    d2h = sum(t.numel() * t.element_size() for t in (out_idx, out_val, out_cnt, out_st))
+
+    def e2e_step():
+        X.copy_(Xpin, non_blocking=True)
+        step()
+        out_idx.copy_(idx, non_blocking=True)
+        out_val.copy_(val, non_blocking=True)
+        out_cnt.copy_(cnt, non_blocking=True)
+        out_st.copy_(status, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    points = B * nalg * L * world
+    solves = B * nalg * world
+    value = points / (ms / 1e3)
+
+    # ---- roofline of the dominant stage
+    peaks_json = load_peaks()
+    hbm_peak = peaks_json.get("hbm_gbs", 6800.0)
+    K = {0: 1, 1: M - D, 2: M - D, 3: 1}
+    scan_flops = B * L * sum(K[a] * (8 * M + 4) for a in ALGS)
+    cov_bytes = B * (8 * M * N_SNAP + 16 * M * M)
+    stage_info = {}
+    names = doa.STAGE_NAMES
+    for i, name in enumerate(names):
+        stage_info[name] = {"ms": round(stage_ms[i], 4)}
+    stage_info["scan"].update(bound="alu", achieved=scan_flops / (stage_ms[3] / 1e3) / 1e12, unit="TFLOP/s",
+                              peak=FP32_PEAK_TFLOPS)
+    stage_info["covariance"].update(bound="hbm", achieved=cov_bytes / (stage_ms[1] / 1e3) / 1e9, unit="GB/s",
+                                    peak=hbm_peak)
+    dom = max(range(doa.BATCH_STAGES), key=lambda i: stage_ms[i])
+    dname = names[dom]
+    if dname == "scan":
+        roof = {"bound": "alu", "achieved": round(stage_info["scan"]["achieved"], 3), "peak": round(FP32_PEAK_TFLOPS, 2),
+                "unit": "TFLOP/s", "frac": round(stage_info["scan"]["achieved"] / FP32_PEAK_TFLOPS, 4),
+                "traffic": None, "kernel": "scan_batch_kernel<16,2>",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+    elif dname == "covariance":
+        a = stage_info["covariance"]["achieved"]
+        roof = {"bound": "hbm", "achieved": round(a, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(a / hbm_peak, 4), "traffic": None, "kernel": "covariance_batch_kernel",
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "kernel": dname, "peak_source": "nominal FP64"}
+    for v in stage_info.values():
+        if "achieved" in v:
+            v["achieved"] = round(v["achieved"], 3)
+            v["frac"] = round(v["achieved"] / v["peak"], 4)
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Eq. 1 ULA snapshots, Philox)",
+        "config": {"workload": workload_name(B), "batch_per_gpu": B, "M": M, "d": D, "N": N_SNAP, "L": L,
+                   "algorithms": ["PHD", "MUSIC", "EV", "MN"], "eig": "FP64 Jacobi", "scan": "FP32 FFMA",
+                   "l2": f"inputs {Xh.nbytes / 1e9:.2f} GB per step > 129 MB L2 (no flush needed)",
+                   "parallelism": f"replicas x{world}"},
+        "solves_per_s": solves / (ms / 1e3),
+        "gpu_launches": launches_per_step * args.steps,
+        "stages": stage_info,
+        "roofline": roof,
+        "e2e": {"value": points / (e2e_ms / 1e3), "unit": "points/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "clocks": clk,
+    }
+
+    # ---- CPU baseline (oracle) on a bounded sample, rank 0, N = 1; also a parity spot check
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        S = args.cpu_sample
+        workers = min(os.cpu_count() or 1, 16)
+        res, dt = oracle_sample([Xh[i] for i in range(S)], workers)
+        pts = S * nalg * L
+        result["cpu_baseline"] = {"value": pts / dt, "unit": "points/s", "cores": workers, "kind": "oracle",
+                                  "sample": f"first {S} problems of the batch x 4 algorithms ({pts} points)",
+                                  "seconds": round(dt, 3)}
+        Pg = P[:S].cpu().numpy()
+        ig = idx[:S].cpu().numpy()
+        cg = cnt[:S].cpu().numpy()
+        worst_db, agree = 0.0, 0
+        for t, (alg, io, Po, sto) in enumerate(res):
+            i, a = divmod(t, nalg)
+            worst_db = max(worst_db, float(np.max(np.abs(10 * np.log10(Pg[i, a].astype(np.float64) /
+                                                                       Po.astype(np.float64))))))
+            agree += list(ig[i, a, :cg[i, a]]) == list(io)
+        result["parity"] = {"sampled_solves": len(res), "peak_index_agreement": agree, "max_db_err": worst_db}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on host cores, on a bounded sample of the same workload per step."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2007_14135_gb300 import synth
+    S = args.cpu_sample
+    Xh, _ = synth.paper_density_batch(S)
+    workers = min(os.cpu_count() or 1, 16)
+    L = grid_L()
+    times = []
+    for k in range(args.warmup + args.steps):
+        _, dt = oracle_sample([Xh[i] for i in range(S)], workers)
+        if k >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * statistics.fmean(times)
+    pts = S * len(ALGS) * L
+    value = pts / (ms / 1e3)
+    result = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Eq. 1 ULA snapshots, Philox)",
+        "config": {"workload": workload_name(S) + " (oracle sample per step)", "batch_per_gpu": S},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": workers, "kind": "oracle",
+                         "sample": f"{S} problems x 4 algorithms per step"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(result), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--batch", type=int, default=4096, help="problems per GPU per step")
+    ap.add_argument("--cpu-sample", type=int, default=48, help="problems timed on the oracle")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gpu":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * doa.h -- C ABI of libdoa.so: noise-subspace narrowband DOA estimation (PHD, MUSIC, EV, MN)
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the one of Eray & Temizel, "Performance Analysis of Noise Subspace-based
+ * Narrowband DOA Estimation Algorithms on CPU and GPU" (arXiv 2007.14135):
+ *   Step-1  R = X X^H / N                                   (Sec. 3.1, Eq. 3; Table 2)
+ *   Step-2  eigendecomposition of the Hermitian R           (Table 2; SVD == EVD for PSD R)
+ *   Step-3/4 noise subspace and weighting                   (Table 3)
+ *   Step-5  P(theta) = 1 / (a(theta)^H C a(theta))          (Table 2; steering vector Eq. 2)
+ *   Step-6  peak finding and selection of D peaks           (Table 2)
+ *
+ * Conventions shared by every entry point:
+ *   - All data pointers are DEVICE pointers unless stated otherwise; the caller owns every
+ *     buffer. No entry point allocates device or pinned memory, and none synchronises the
+ *     stream: each call only enqueues work on `stream` (a cudaStream_t passed as void*; NULL =
+ *     legacy default stream).
+ *   - Complex numbers are interleaved (re, im): complex64 = 2 floats, complex128 = 2 doubles.
+ *   - The array is a half-wavelength uniform linear array (Eq. 2 with x_m = m*lambda/2,
+ *     y = z = 0, phi = 90 deg): a_m(theta) = exp(+j*pi*m*sin(theta)), m = 0..M-1, theta in
+ *     degrees from broadside. Element 0 is the reference element of MN.
+ *   - The scan grid is theta_k = lo_deg + k*step_deg, k = 0..L-1, evaluated in FP64.
+ *   - Argument errors are reported synchronously by the return value and enqueue nothing.
+ *     Launch failures return DOA_ECUDA. Numerical problems found on the device (no
+ *     convergence, rank loss, non-finite data) are written to the caller's `info`/`status`
+ *     words; kernels never trap.
+ *   - Sizes: 2 <= M <= 64, 0 <= d < M, N >= 1, 3 <= L <= 2^30.
+ */
+#ifndef DOA_H
+#define DOA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DOA_OK = 0,
+  DOA_EINVAL = 1,      /* bad argument (size, null or misaligned pointer, unknown enum)     */
+  DOA_ENOMEM = 2,      /* caller-provided workspace too small                                */
+  DOA_ECUDA = 3,       /* a CUDA launch or runtime call failed                               */
+  DOA_ENOCONV = 4,     /* Jacobi sweep cap reached                                           */
+  DOA_ERANK = 5,       /* EV with a non-positive noise eigenvalue, MN with e1^H P_n e1 == 0 */
+  DOA_ENONFINITE = 6,  /* NaN or Inf in the covariance                                       */
+  DOA_ETIMEOUT = 7     /* reserved: a bounded device wait ran out                            */
+} doa_status;
+
+typedef enum { DOA_PHD = 0, DOA_MUSIC = 1, DOA_EV = 2, DOA_MN = 3 } doa_alg;
+
+/* Arithmetic of the covariance and scan contractions. */
+typedef enum {
+  DOA_FP32 = 0,    /* FP32 operands, FP32 FMA on CUDA cores                                   */
+  DOA_BF16 = 1,    /* one BF16 tensor-core product, FP32 accumulation                        */
+  DOA_BF16X3 = 2,  /* BF16 hi+lo split operands, three tensor-core products, FP32 accumulation */
+  DOA_FP16X3 = 3   /* FP16 hi+lo split operands, three tensor-core products, FP32 accumulation */
+} doa_prec;
+
+/* Scan grid theta_k = lo_deg + k*step_deg (degrees, FP64), k = 0..L-1. */
+typedef struct {
+  double lo_deg;
+  double step_deg;
+  int32_t L;
+  int32_t reserved;
+} doa_grid;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *doa_status_str(int status);
+
+/*
+ * Step-1 (Eq. 3): R = (1/N) * sum_t X(t_t) X(t_t)^H.
+ *   X    : M x N complex64, row-major: row m is the time series of element m; row stride
+ *          ldx >= N complex elements. 8-byte aligned.
+ *   R    : M x M complex64 row-major (nullable).
+ *   R64  : M x M complex128 row-major (nullable). At least one of R, R64 is non-NULL.
+ *   prec : DOA_FP32: products and partial sums in FP32 within ranges of snapshots, ranges
+ *          combined in FP64 (a cluster of up to 8 CTAs, reduced through distributed shared
+ *          memory). Other values are rejected (DOA_EINVAL).
+ * Errors: DOA_EINVAL for M outside [2, 64], N < 1, ldx < N, NULL X, both outputs NULL.
+ */
+doa_status doa_covariance(const float *X, int M, int N, int ldx, float *R, double *R64, int prec,
+                          void *stream);
+
+/*
+ * Steps 2-4: Hermitian eigendecomposition of R by FP64 cyclic Jacobi (one warp per matrix,
+ * parallel round-robin ordering), eigenvalues sorted descending (equal values keep their
+ * index order), then the noise-subspace factor B of the weighting matrix, C = B B^H (Table 3):
+ *   PHD   : B = e_min (last eigenvector),                K = 1
+ *   MUSIC : B = E_n = eigenvectors d..M-1,               K = M - d
+ *   EV    : B = E_n diag(lambda_i^{-1/2}),               K = M - d
+ *   MN    : B = valph = P_n e1 / (e1^H P_n e1),          K = 1
+ *   R64   : M x M complex128 row-major (Hermitian; only the upper triangle is read).
+ *   evals : M doubles, descending (nullable).
+ *   B     : M x K complex128, column-major with leading dimension M (capacity M*M).
+ *   K_out : one int32 receiving K (nullable).
+ *   info  : one int32: > 0 number of sweeps; < 0 minus a doa_status (ENOCONV, ERANK,
+ *           ENONFINITE). Never NULL.
+ */
+doa_status doa_noise_subspace(const double *R64, int M, int d, int alg, double *evals, double *B,
+                              int *K_out, int *info, void *stream);
+
+/*
+ * Step-5: P_k = 1 / ||B^H a(theta_k)||^2 for k = 0..L-1 (equal to 1/(a^H C a) with C = B B^H).
+ *   B    : M x K complex128 column-major, leading dimension M (as written by
+ *          doa_noise_subspace). 1 <= K <= M.
+ *   grid : scan grid; L >= 3.
+ *   prec : DOA_FP32 (CUDA-core FFMA; phases exact to 2^-31 of a half turn).
+ *   P    : L floats, 4-byte aligned. The call first writes the grid's phase table into P and
+ *          then overwrites it with the spectrum, so P needs no companion buffer.
+ */
+doa_status doa_scan(const double *B, int M, int K, doa_grid grid, int prec, float *P, void *stream);
+
+/*
+ * Step-6: peaks of P (left end of each strict local-maximum plateau, end points excluded),
+ * the d largest (equal values: lower index first), written in ascending index order.
+ *   idx, val : d entries each (entries past *count are left untouched); count: one int32.
+ */
+doa_status doa_peaks(const float *P, int L, int d, int *idx, float *val, int *count, void *stream);
+
+/* ----------------------------------------------------------------------------------------- */
+/* Batched solve (not in the paper): many independent problems with uneven M, d, N, L and    */
+/* algorithms in one plan, executed as a fixed sequence of kernels on one stream that a       */
+/* caller may capture into a CUDA graph.                                                      */
+/* ----------------------------------------------------------------------------------------- */
+
+/* One problem of a batch. All pointers are device pointers owned by the caller. */
+typedef struct {
+  const float *X;        /* M x N complex64 row-major, row stride ldx                        */
+  float *P;              /* nalg x L spectra (nalg = popcount(alg_mask), in bit order)       */
+  int32_t *peak_idx;     /* nalg x d peak indices (ascending per algorithm)                  */
+  float *peak_val;       /* nalg x d peak values                                             */
+  int32_t *peak_count;   /* nalg counts                                                      */
+  double *evals;         /* M eigenvalues, descending (nullable)                             */
+  doa_grid grid;
+  int32_t M, N, ldx, d;
+  uint32_t alg_mask;     /* bit a set => algorithm a (DOA_PHD=bit 0 ... DOA_MN=bit 3)        */
+  int32_t prec;          /* doa_prec of the covariance and scan                              */
+} doa_problem;
+
+/*
+ * Host-only planning. doa_batch_plan_bytes returns the plan size for these problems (0 if one
+ * is invalid). doa_batch_plan packs the problems into `plan` (caller host memory of at least
+ * that size) and returns the device workspace size in *ws_bytes.
+ * The caller copies the same plan bytes to device memory (16-byte aligned) before
+ * doa_solve_batch. Errors: DOA_EINVAL for an invalid problem (its index in *bad_index if
+ * bad_index is not NULL), DOA_ENOMEM if plan_bytes is too small.
+ */
+size_t doa_batch_plan_bytes(const doa_problem *probs, int nprob);
+doa_status doa_batch_plan(const doa_problem *probs, int nprob, void *plan, size_t plan_bytes,
+                          size_t *ws_bytes, int *bad_index);
+
+/* Stages of doa_solve_batch, in launch order (for per-stage timing). */
+#define DOA_BATCH_STAGES 5 /* 0 phase tables, 1 covariance, 2 eig + noise subspace, 3 scan, 4 peaks */
+
+/*
+ * Executes a plan: covariance, eigendecomposition + noise subspace, scan and peaks for every
+ * problem and algorithm. Only prec == DOA_FP32 problems are accepted by this version.
+ *   plan_host, plan_dev : the same plan bytes on the host and in device memory (16-byte aligned).
+ *   ws      : device memory of at least the planned size, 256-byte aligned. Its contents need
+ *             no initialisation and are overwritten.
+ *   status  : one int32 per problem: 0, or a doa_status found on the device.
+ *   stage_events : NULL, or DOA_BATCH_STAGES + 1 cudaEvent_t handles; event i is recorded on
+ *             `stream` before stage i and the last one after the final stage (the per-stage time
+ *             breakdown of the method, cf. the paper's Fig. 2).
+ * The call reads only plan_host on the host and enqueues a fixed sequence of kernels, so a
+ * stream capture of it replays as a CUDA graph.
+ */
+doa_status doa_solve_batch(const void *plan_host, const void *plan_dev, void *ws, size_t ws_bytes,
+                           int *status, void *const *stage_events, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DOA_H */

@@ -1,0 +1,288 @@
+// C ABI of libdoa.so (declarations and contracts in include/doa.h): argument checks, batch
+// planning on the host, and the launch sequences. No entry point allocates memory or
+// synchronises; every launch goes to the caller's stream.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "doa_internal.cuh"
+
+using namespace doa;
+
+namespace {
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+inline doa_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DOA_OK : DOA_ECUDA; }
+
+inline int factor_width(int alg, int M, int d) { return (alg == DOA_PHD || alg == DOA_MN) ? 1 : M - d; }
+
+bool grid_ok(const doa_grid &g) {
+  return g.L >= 3 && g.L <= (1 << 30) && std::isfinite(g.lo_deg) && std::isfinite(g.step_deg) &&
+         g.step_deg != 0.0;
+}
+
+bool problem_ok(const doa_problem &p) {
+  if (p.M < 2 || p.M > kMaxM || p.d < 0 || p.d >= p.M || p.N < 1 || p.ldx < p.N) return false;
+  if (!p.X || !aligned(p.X, 8) || !p.P || !aligned(p.P, 4)) return false;
+  if (p.alg_mask == 0u || p.alg_mask > 15u) return false;
+  if (p.d > 0 && (!p.peak_idx || !p.peak_val)) return false;
+  if (!p.peak_count) return false;
+  if (p.prec != DOA_FP32) return false;
+  return grid_ok(p.grid);
+}
+
+struct PlanSizes {
+  int nprob = 0, njobs = 0, ngrids = 0, ncov = 0, nreduce = 0;
+  int eig[kNumBuckets] = {0, 0, 0, 0};
+  int scan[kNumBuckets] = {0, 0, 0, 0};
+};
+
+bool same_grid(const doa_grid &a, const doa_grid &b) {
+  return a.L == b.L && std::memcmp(&a.lo_deg, &b.lo_deg, sizeof(double)) == 0 &&
+         std::memcmp(&a.step_deg, &b.step_deg, sizeof(double)) == 0;
+}
+
+// Counts the plan's arrays; returns false on an invalid problem.
+bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<doa_grid> &grids,
+                std::vector<int> &grid_of, int *bad_index) {
+  sz.nprob = nprob;
+  grid_of.resize(nprob);
+  for (int i = 0; i < nprob; ++i) {
+    const doa_problem &p = probs[i];
+    if (!problem_ok(p)) {
+      if (bad_index) *bad_index = i;
+      return false;
+    }
+    int chunks = (p.N + kCovChunk - 1) / kCovChunk;
+    sz.ncov += chunks;
+    sz.nreduce += chunks > 1;
+    sz.eig[m_bucket(p.M)] += 1;
+    int nalg = __builtin_popcount(p.alg_mask);
+    sz.njobs += nalg;
+    sz.scan[m_bucket(p.M)] += nalg;
+    int g = -1;
+    for (size_t k = 0; k < grids.size(); ++k)
+      if (same_grid(grids[k], p.grid)) {
+        g = (int)k;
+        break;
+      }
+    if (g < 0) {
+      g = (int)grids.size();
+      grids.push_back(p.grid);
+    }
+    grid_of[i] = g;
+  }
+  sz.ngrids = (int)grids.size();
+  return true;
+}
+
+struct PlanOffsets {
+  int64_t prob, job, grid, cov, reduce, eig[kNumBuckets], scan[kNumBuckets], total;
+};
+
+PlanOffsets plan_offsets(const PlanSizes &sz) {
+  PlanOffsets o;
+  int64_t at = round_up(sizeof(PlanHeader), 16);
+  o.prob = at;
+  at = round_up(at + (int64_t)sz.nprob * sizeof(PlanProblem), 16);
+  o.job = at;
+  at = round_up(at + (int64_t)sz.njobs * sizeof(PlanJob), 16);
+  o.grid = at;
+  at = round_up(at + (int64_t)sz.ngrids * sizeof(PlanGrid), 16);
+  o.cov = at;
+  at = round_up(at + (int64_t)sz.ncov * sizeof(PlanCovItem), 16);
+  o.reduce = at;
+  at = round_up(at + (int64_t)sz.nreduce * 4, 16);
+  for (int b = 0; b < kNumBuckets; ++b) {
+    o.eig[b] = at;
+    at = round_up(at + (int64_t)sz.eig[b] * 4, 16);
+  }
+  for (int b = 0; b < kNumBuckets; ++b) {
+    o.scan[b] = at;
+    at = round_up(at + (int64_t)sz.scan[b] * 4, 16);
+  }
+  o.total = at;
+  return o;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *doa_status_str(int status) {
+  switch (status) {
+    case DOA_OK: return "ok";
+    case DOA_EINVAL: return "invalid argument";
+    case DOA_ENOMEM: return "workspace or plan buffer too small";
+    case DOA_ECUDA: return "CUDA launch or runtime error";
+    case DOA_ENOCONV: return "Jacobi sweep cap reached";
+    case DOA_ERANK: return "noise subspace rank failure";
+    case DOA_ENONFINITE: return "non-finite covariance";
+    case DOA_ETIMEOUT: return "bounded device wait ran out";
+    default: return "unknown status";
+  }
+}
+
+doa_status doa_covariance(const float *X, int M, int N, int ldx, float *R, double *R64, int prec, void *stream) {
+  if (!X || M < 2 || M > kMaxM || N < 1 || ldx < N || (!R && !R64) || prec != DOA_FP32) return DOA_EINVAL;
+  if (!aligned(X, 8) || (R && !aligned(R, 8)) || (R64 && !aligned(R64, 16))) return DOA_EINVAL;
+  return cuda_status(launch_covariance_single(reinterpret_cast<const float2 *>(X), M, N, ldx,
+                                              reinterpret_cast<float2 *>(R), reinterpret_cast<double2 *>(R64),
+                                              as_stream(stream)));
+}
+
+doa_status doa_noise_subspace(const double *R64, int M, int d, int alg, double *evals, double *B, int *K_out,
+                              int *info, void *stream) {
+  if (!R64 || !B || !info || M < 2 || M > kMaxM || d < 0 || d >= M || alg < DOA_PHD || alg > DOA_MN)
+    return DOA_EINVAL;
+  if (!aligned(R64, 16) || !aligned(B, 16) || (evals && !aligned(evals, 8))) return DOA_EINVAL;
+  return cuda_status(launch_eig_single(reinterpret_cast<const double2 *>(R64), M, d, alg, evals,
+                                       reinterpret_cast<double2 *>(B), K_out, info, as_stream(stream)));
+}
+
+doa_status doa_scan(const double *B, int M, int K, doa_grid grid, int prec, float *P, void *stream) {
+  if (!B || !P || M < 2 || M > kMaxM || K < 1 || K > M || !grid_ok(grid) || prec != DOA_FP32) return DOA_EINVAL;
+  if (!aligned(B, 16) || !aligned(P, 4)) return DOA_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  uint32_t *S = reinterpret_cast<uint32_t *>(P);  // phase table first, spectrum over it
+  cudaError_t e = launch_grid_table_single(grid.lo_deg, grid.step_deg, grid.L, S, s);
+  if (e != cudaSuccess) return DOA_ECUDA;
+  return cuda_status(launch_scan_single(reinterpret_cast<const double2 *>(B), M, K, grid.L, S, P, s));
+}
+
+doa_status doa_peaks(const float *P, int L, int d, int *idx, float *val, int *count, void *stream) {
+  if (!P || !count || L < 3 || d < 0 || d >= kMaxM || (d > 0 && (!idx || !val))) return DOA_EINVAL;
+  return cuda_status(launch_peaks_single(P, L, d, idx, val, count, as_stream(stream)));
+}
+
+size_t doa_batch_plan_bytes(const doa_problem *probs, int nprob) {
+  if (!probs || nprob < 1) return 0;
+  PlanSizes sz;
+  std::vector<doa_grid> grids;
+  std::vector<int> grid_of;
+  if (!count_plan(probs, nprob, sz, grids, grid_of, nullptr)) return 0;
+  return (size_t)plan_offsets(sz).total;
+}
+
+doa_status doa_batch_plan(const doa_problem *probs, int nprob, void *plan, size_t plan_bytes, size_t *ws_bytes,
+                          int *bad_index) {
+  if (bad_index) *bad_index = -1;
+  if (!probs || nprob < 1 || !ws_bytes) return DOA_EINVAL;
+  PlanSizes sz;
+  std::vector<doa_grid> grids;
+  std::vector<int> grid_of;
+  if (!count_plan(probs, nprob, sz, grids, grid_of, bad_index)) return DOA_EINVAL;
+  const PlanOffsets o = plan_offsets(sz);
+  if (!plan || plan_bytes < (size_t)o.total) return DOA_ENOMEM;
+  uint8_t *base = static_cast<uint8_t *>(plan);
+  std::memset(base, 0, (size_t)o.total);
+  PlanHeader &h = *reinterpret_cast<PlanHeader *>(base);
+  PlanProblem *pp = reinterpret_cast<PlanProblem *>(base + o.prob);
+  PlanJob *jobs = reinterpret_cast<PlanJob *>(base + o.job);
+  PlanGrid *pg = reinterpret_cast<PlanGrid *>(base + o.grid);
+  PlanCovItem *cov = reinterpret_cast<PlanCovItem *>(base + o.cov);
+  int32_t *reduce = reinterpret_cast<int32_t *>(base + o.reduce);
+  int32_t *eig[kNumBuckets], *scan[kNumBuckets];
+  for (int b = 0; b < kNumBuckets; ++b) {
+    eig[b] = reinterpret_cast<int32_t *>(base + o.eig[b]);
+    scan[b] = reinterpret_cast<int32_t *>(base + o.scan[b]);
+  }
+  h.magic = kPlanMagic;
+  h.nprob = sz.nprob;
+  h.njobs = sz.njobs;
+  h.ngrids = sz.ngrids;
+  h.ncov = sz.ncov;
+  h.nreduce = sz.nreduce;
+  h.off_prob = o.prob;
+  h.off_job = o.job;
+  h.off_grid = o.grid;
+  h.off_cov = o.cov;
+  h.off_reduce = o.reduce;
+  for (int b = 0; b < kNumBuckets; ++b) {
+    h.off_eig[b] = o.eig[b];
+    h.off_scan[b] = o.scan[b];
+  }
+  // workspace: per-grid phase tables, then per-problem R and partials, then per-job factors
+  int64_t ws = 0;
+  for (int g = 0; g < sz.ngrids; ++g) {
+    pg[g].lo = grids[g].lo_deg;
+    pg[g].step = grids[g].step_deg;
+    pg[g].L = grids[g].L;
+    pg[g].S_off = ws;
+    ws = round_up(ws + (int64_t)grids[g].L * 4, 256);
+    h.grid_points += grids[g].L;
+  }
+  int icov = 0, ired = 0, ijob = 0;
+  int ie[kNumBuckets] = {0, 0, 0, 0}, is[kNumBuckets] = {0, 0, 0, 0};
+  int64_t tiles[kNumBuckets] = {0, 0, 0, 0};
+  for (int i = 0; i < nprob; ++i) {
+    const doa_problem &p = probs[i];
+    PlanProblem &q = pp[i];
+    q.p = p;
+    const int M = p.M, b = m_bucket(M);
+    const int64_t mm = (int64_t)M * M * 16;
+    q.r64_off = ws;
+    ws = round_up(ws + mm, 256);
+    q.nchunks = (p.N + kCovChunk - 1) / kCovChunk;
+    q.part_off = ws;
+    if (q.nchunks > 1) {
+      ws = round_up(ws + mm * q.nchunks, 256);
+      reduce[ired++] = i;
+    }
+    for (int c = 0; c < q.nchunks; ++c) cov[icov++] = PlanCovItem{i, c};
+    eig[b][ie[b]++] = i;
+    q.grid_id = grid_of[i];
+    q.first_job = ijob;
+    int slot = 0;
+    const int tp = scan_tile_points(b);
+    for (int a = 0; a < 4; ++a) {
+      if (!((p.alg_mask >> a) & 1u)) continue;
+      PlanJob &j = jobs[ijob];
+      j.prob = i;
+      j.alg = a;
+      j.slot = slot++;
+      j.K = factor_width(a, M, p.d);
+      j.B_off = ws;
+      ws = round_up(ws + mm, 256);
+      j.tile_start = tiles[b];
+      tiles[b] += (p.grid.L + tp - 1) / tp;
+      scan[b][is[b]++] = ijob;
+      ++ijob;
+    }
+    q.njobs = slot;
+  }
+  for (int b = 0; b < kNumBuckets; ++b) {
+    h.eig_count[b] = sz.eig[b];
+    h.scan_jobs[b] = sz.scan[b];
+    h.scan_tiles[b] = tiles[b];
+  }
+  h.ws_bytes = ws;
+  *ws_bytes = (size_t)ws;
+  return DOA_OK;
+}
+
+doa_status doa_solve_batch(const void *plan_host, const void *plan_dev, void *ws, size_t ws_bytes, int *status,
+                           void *const *stage_events, void *stream) {
+  if (!plan_host || !plan_dev || !ws || !status) return DOA_EINVAL;
+  const PlanHeader &h = *static_cast<const PlanHeader *>(plan_host);
+  if (h.magic != kPlanMagic || h.nprob < 1) return DOA_EINVAL;
+  if (!aligned(plan_dev, 16) || !aligned(ws, 256) || !aligned(status, 4)) return DOA_EINVAL;
+  if (ws_bytes < (size_t)h.ws_bytes) return DOA_ENOMEM;
+  cudaStream_t s = as_stream(stream);
+  const uint8_t *pd = static_cast<const uint8_t *>(plan_dev);
+  uint8_t *w = static_cast<uint8_t *>(ws);
+  auto mark = [&](int i) -> bool {
+    return !stage_events || cudaEventRecord(static_cast<cudaEvent_t>(stage_events[i]), s) == cudaSuccess;
+  };
+  if (!mark(0) || launch_grid_tables(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
+  if (!mark(1) || launch_covariance_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
+  if (!mark(2) || launch_eig_batch(pd, h, w, status, s) != cudaSuccess) return DOA_ECUDA;
+  if (!mark(3) || launch_scan_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
+  if (!mark(4) || launch_peaks_batch(pd, h, s) != cudaSuccess) return DOA_ECUDA;
+  if (!mark(5)) return DOA_ECUDA;
+  return DOA_OK;
+}
+
+}  // extern "C"

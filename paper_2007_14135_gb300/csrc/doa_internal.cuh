@@ -1,0 +1,156 @@
+// Internal declarations shared by the CUDA translation units of libdoa.so.
+// Device helpers here are header-only (inline) so that every kernel file compiles on its own.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "doa.h"
+
+namespace doa {
+
+constexpr int kMaxM = 64;
+constexpr int kCovChunk = 1024;    // snapshots per covariance work item
+constexpr int kMaxSweeps = 60;     // Jacobi sweep cap (ENOCONV beyond)
+constexpr double kJacobiTol = 1e-15;
+
+// ------------------------------------------------------------------------------------------
+// Complex helpers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// ------------------------------------------------------------------------------------------
+// Grid phase table. theta_k = lo + k*step in FP64 (rounded multiply, rounded add), and the
+// phase increment of the half-wavelength ULA, s_k = sin(theta_k), stored as a 32-bit fixed
+// point fraction of a half turn: S_k = round(s_k * 2^31) mod 2^32. Then for element m the
+// phase m*pi*s_k equals pi * (m*S_k mod 2^32) * 2^-31 exactly in integer arithmetic
+// (the wrap of 2^32 is a whole number of turns), so the phase error is that of one rounding
+// of s_k (<= 2^-32 half turns), independent of m.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t grid_phase_step(double lo, double step, int k) {
+  double theta = __dadd_rn(lo, __dmul_rn((double)k, step));
+  double s = sin(theta * 0.017453292519943295);  // pi/180
+  long long q = __double2ll_rn(s * 2147483648.0);
+  return (uint32_t)q;
+}
+
+// exp(j*pi*phi*2^-31) for a 32-bit phase phi (a fraction of a full turn: 2^32 = 2 pi).
+// The top two bits (rounded) select the quadrant; the signed remainder f in [-1/2, 1/2) of a
+// quarter turn is evaluated with the Taylor series of sin and cos about 0 in the variable
+// x = (pi/2) f, |x| <= pi/4, through x^9 and x^10 (Lagrange remainders below 2e-9 and 2e-10).
+// Coefficients are (pi/2)^n / n! folded so that the polynomials take f directly.
+__device__ __forceinline__ float2 phasor_q32(uint32_t phi) {
+  uint32_t quad = (phi + 0x20000000u) >> 30;             // nearest quarter turn, 0..3
+  int32_t rem = (int32_t)(phi - (quad << 30));            // [-2^29, 2^29)
+  float f = (float)rem * 9.31322574615478515625e-10f;     // * 2^-30 -> [-0.5, 0.5)
+  float f2 = f * f;
+  // sin((pi/2) f) = f*(s1 + f2*(s3 + f2*(s5 + f2*(s7 + f2*s9))))
+  const float s1 = 1.5707963267948966f, s3 = -0.6459640975062462f, s5 = 0.07969262624616704f,
+              s7 = -0.004681754135318687f, s9 = 0.00016044118478735982f;
+  // cos((pi/2) f) = 1 + f2*(c2 + f2*(c4 + f2*(c6 + f2*(c8 + f2*c10))))
+  const float c2 = -1.2337005501361697f, c4 = 0.25366950790104797f, c6 = -0.020863480763352958f,
+              c8 = 0.0009192602748394263f, c10 = -2.5202042373060603e-05f;
+  float sp = fmaf(f2, s9, s7);
+  sp = fmaf(f2, sp, s5);
+  sp = fmaf(f2, sp, s3);
+  sp = fmaf(f2, sp, s1);
+  float sn = f * sp;
+  float cp = fmaf(f2, c10, c8);
+  cp = fmaf(f2, cp, c6);
+  cp = fmaf(f2, cp, c4);
+  cp = fmaf(f2, cp, c2);
+  float cs = fmaf(f2, cp, 1.0f);
+  // rotate by quad quarter turns: (c, s) -> quad 1: (-s, c), 2: (-c, -s), 3: (s, -c)
+  float re = (quad & 1u) ? sn : cs;
+  float im = (quad & 1u) ? cs : sn;
+  if ((quad + 1u) & 2u) re = -re;   // quad 1 or 2
+  if (quad & 2u) im = -im;          // quad 2 or 3
+  return make_float2(re, im);
+}
+
+// ------------------------------------------------------------------------------------------
+// Batch plan. The same bytes live on the host (for launch sizes) and on the device.
+// ------------------------------------------------------------------------------------------
+constexpr uint32_t kPlanMagic = 0x444f4131u;  // "DOA1"
+constexpr int kNumBuckets = 4;                // M <= 8, <= 16, <= 32, <= 64
+
+struct PlanProblem {
+  doa_problem p;          // the caller's descriptor
+  int64_t r64_off;        // byte offset of R (M x M complex128) in the workspace
+  int64_t part_off;       // byte offset of the covariance partials (nchunks x M x M complex128)
+  int32_t nchunks;        // covariance work items of this problem
+  int32_t first_job;      // first (problem, algorithm) job
+  int32_t njobs;
+  int32_t grid_id;        // index of the problem's phase table
+};
+
+struct PlanJob {
+  int64_t B_off;          // byte offset of B (M x M capacity, complex128, column-major)
+  int64_t tile_start;     // first scan tile of this job within its bucket's tile range
+  int32_t prob;
+  int32_t alg;
+  int32_t slot;           // position of the algorithm among the problem's algorithms
+  int32_t K;
+};
+
+struct PlanGrid {
+  double lo, step;
+  int32_t L;
+  int32_t pad;
+  int64_t S_off;          // byte offset of the phase table (L x uint32) in the workspace
+};
+
+struct PlanCovItem {
+  int32_t prob;
+  int32_t chunk;
+};
+
+struct PlanHeader {
+  uint32_t magic;
+  int32_t nprob, njobs, ngrids, ncov;
+  int32_t nreduce;                       // problems with more than one covariance chunk
+  int32_t eig_count[kNumBuckets];        // problems per M bucket
+  int32_t scan_jobs[kNumBuckets];        // jobs per M bucket
+  int64_t scan_tiles[kNumBuckets];       // scan tiles per M bucket
+  int64_t grid_points;                   // sum of L over distinct grids
+  int64_t ws_bytes;
+  // byte offsets of the arrays inside the plan
+  int64_t off_prob, off_job, off_grid, off_cov, off_reduce, off_eig[kNumBuckets],
+      off_scan[kNumBuckets], off_grid_pts;
+};
+
+// Scan tiles: kScanThreads threads, each evaluating scan_pt(bucket) consecutive grid points.
+constexpr int kScanThreads = 128;
+__host__ __device__ constexpr int scan_pt(int bucket) { return bucket == 0 ? 4 : (bucket == 1 ? 2 : 1); }
+__host__ __device__ constexpr int scan_tile_points(int bucket) { return kScanThreads * scan_pt(bucket); }
+
+__host__ __device__ inline int m_bucket(int M) { return M <= 8 ? 0 : (M <= 16 ? 1 : (M <= 32 ? 2 : 3)); }
+
+// ------------------------------------------------------------------------------------------
+// Host launchers (one translation unit each). They return cudaError_t of the launch.
+// ------------------------------------------------------------------------------------------
+cudaError_t launch_grid_table_single(double lo, double step, int L, uint32_t *S, cudaStream_t s);
+cudaError_t launch_grid_tables(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
+
+cudaError_t launch_covariance_single(const float2 *X, int M, int N, int ldx, float2 *R, double2 *R64,
+                                     cudaStream_t s);
+cudaError_t launch_covariance_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws,
+                                    cudaStream_t s);
+
+cudaError_t launch_eig_single(const double2 *R64, int M, int d, int alg, double *evals, double2 *B,
+                              int *K_out, int *info, cudaStream_t s);
+cudaError_t launch_eig_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, int *status,
+                             cudaStream_t s);
+
+cudaError_t launch_scan_single(const double2 *B, int M, int K, int L, const uint32_t *S, float *P,
+                               cudaStream_t s);
+cudaError_t launch_scan_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
+
+cudaError_t launch_peaks_single(const float *P, int L, int d, int *idx, float *val, int *count,
+                                cudaStream_t s);
+cudaError_t launch_peaks_batch(const uint8_t *plan_dev, const PlanHeader &h, cudaStream_t s);
+
+}  // namespace doa

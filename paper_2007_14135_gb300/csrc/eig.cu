@@ -1,0 +1,315 @@
+// Steps 2-4 (Table 2 Step-2, Table 3): Hermitian eigendecomposition of R by FP64 cyclic Jacobi,
+// one warp per matrix, followed by the noise-subspace factor B of each algorithm's weighting
+// matrix C = B B^H.
+//
+// Jacobi (Golub & Van Loan, Sec. 8.5, with a phase factor for complex Hermitian matrices):
+// for a pair (p, q) with a_pq = |a_pq| e^{j phi}, tau = (a_qq - a_pp) / (2 |a_pq|),
+// t = sgn(tau) / (|tau| + hypot(1, tau)), c = 1/sqrt(1 + t^2), s = t c, sigma = s e^{j phi};
+// J = [[c, sigma], [-conj(sigma), c]] on coordinates (p, q) zeroes (J^H A J)_pq.
+// The warp applies n/2 disjoint rotations at once (round-robin "circle" ordering over
+// n = M rounded up to even; pairs that touch the padding index are skipped): first the row
+// update A <- J^H A for all rotated pairs, then the column updates A <- A J and V <- V J.
+// A pair is rotated when |a_pq| > tol sqrt(|a_pp a_qq|); the matrix has converged after the
+// first sweep that rotates nothing. A and V live in shared memory with a padded row stride
+// (NP + 1 complex128) so that column accesses by consecutive lanes hit distinct banks.
+#include "doa_internal.cuh"
+
+namespace doa {
+namespace {
+
+struct Rot {
+  double c, sr, si;  // cosine and sigma = s e^{j phi}
+};
+
+template <int NP>
+struct EigSmem {
+  double2 A[NP][NP + 1];
+  double2 V[NP][NP + 1];
+  Rot rot[NP / 2];
+  int2 pq[NP / 2];
+  double lam[NP];
+  int order[NP];
+};
+
+template <int NP>
+constexpr int eig_warps() { return NP <= 8 ? 8 : (NP <= 16 ? 4 : (NP <= 32 ? 2 : 1)); }
+
+__device__ __forceinline__ int rr_player(int pos, int r, int n) {
+  return pos == 0 ? 0 : ((pos - 1 + r) % (n - 1)) + 1;
+}
+
+// Loads R (upper triangle) into A, runs Jacobi. Returns sweeps (> 0) or -status.
+template <int NP>
+__device__ int jacobi_warp(const double2 *__restrict__ R, int M, EigSmem<NP> &s) {
+  const int lane = threadIdx.x & 31;
+  bool finite = true;
+  for (int e = lane; e < M * M; e += 32) {
+    int i = e / M, j = e % M;
+    double2 v;
+    if (i <= j) {
+      v = R[i * M + j];
+    } else {
+      v = R[j * M + i];
+      v.y = -v.y;
+    }
+    if (i == j) v.y = 0.0;
+    finite = finite && isfinite(v.x) && isfinite(v.y);
+    s.A[i][j] = v;
+    s.V[i][j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  finite = __all_sync(0xffffffffu, finite);
+  __syncwarp();
+  if (!finite) return -DOA_ENONFINITE;
+
+  const int n = (M + 1) & ~1;
+  const int npairs = n / 2;
+  for (int sweep = 1; sweep <= kMaxSweeps; ++sweep) {
+    bool any = false;
+    for (int r = 0; r < n - 1; ++r) {
+      bool act = false;
+      if (lane < npairs) {
+        int a = rr_player(lane, r, n), b = rr_player(n - 1 - lane, r, n);
+        int p = min(a, b), q = max(a, b);
+        if (q < M) {
+          double app = s.A[p][p].x, aqq = s.A[q][q].x;
+          double2 apq = s.A[p][q];
+          double mag = hypot(apq.x, apq.y);
+          if (mag > 0.0 && mag > kJacobiTol * sqrt(fabs(app * aqq))) {
+            act = true;
+            double tau = (aqq - app) / (2.0 * mag);
+            double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
+            double c = 1.0 / sqrt(1.0 + t * t);
+            double sn = t * c;
+            s.rot[lane] = Rot{c, sn * (apq.x / mag), sn * (apq.y / mag)};
+            s.pq[lane] = make_int2(p, q);
+          }
+        }
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, act);
+      if (mask == 0u) continue;
+      any = true;
+      __syncwarp();
+      // rows: A <- J^H A. new row p = c x_p - sigma x_q; new row q = conj(sigma) x_p + c x_q
+      for (int it = lane; it < npairs * M; it += 32) {
+        int i = it / M, k = it % M;
+        if (!((mask >> i) & 1u)) continue;
+        const Rot ro = s.rot[i];
+        int2 pq = s.pq[i];
+        double2 xp = s.A[pq.x][k], xq = s.A[pq.y][k];
+        s.A[pq.x][k] = make_double2(ro.c * xp.x - (ro.sr * xq.x - ro.si * xq.y),
+                                    ro.c * xp.y - (ro.sr * xq.y + ro.si * xq.x));
+        s.A[pq.y][k] = make_double2(ro.c * xq.x + (ro.sr * xp.x + ro.si * xp.y),
+                                    ro.c * xq.y + (ro.sr * xp.y - ro.si * xp.x));
+      }
+      __syncwarp();
+      // columns: A <- A J, V <- V J. new col p = c x_p - conj(sigma) x_q; new col q = sigma x_p + c x_q
+      for (int it = lane; it < npairs * M; it += 32) {
+        int i = it / M, k = it % M;
+        if (!((mask >> i) & 1u)) continue;
+        const Rot ro = s.rot[i];
+        int2 pq = s.pq[i];
+        double2 xp = s.A[k][pq.x], xq = s.A[k][pq.y];
+        s.A[k][pq.x] = make_double2(ro.c * xp.x - (ro.sr * xq.x + ro.si * xq.y),
+                                    ro.c * xp.y - (ro.sr * xq.y - ro.si * xq.x));
+        s.A[k][pq.y] = make_double2(ro.c * xq.x + (ro.sr * xp.x - ro.si * xp.y),
+                                    ro.c * xq.y + (ro.sr * xp.y + ro.si * xp.x));
+        double2 vp = s.V[k][pq.x], vq = s.V[k][pq.y];
+        s.V[k][pq.x] = make_double2(ro.c * vp.x - (ro.sr * vq.x + ro.si * vq.y),
+                                    ro.c * vp.y - (ro.sr * vq.y - ro.si * vq.x));
+        s.V[k][pq.y] = make_double2(ro.c * vq.x + (ro.sr * vp.x - ro.si * vp.y),
+                                    ro.c * vq.y + (ro.sr * vp.y + ro.si * vp.x));
+      }
+      __syncwarp();
+      if (lane < npairs && ((mask >> lane) & 1u)) {
+        int2 pq = s.pq[lane];
+        s.A[pq.x][pq.y] = make_double2(0.0, 0.0);
+        s.A[pq.y][pq.x] = make_double2(0.0, 0.0);
+        s.A[pq.x][pq.x].y = 0.0;
+        s.A[pq.y][pq.y].y = 0.0;
+      }
+      __syncwarp();
+    }
+    if (!any) return sweep;
+  }
+  return -DOA_ENOCONV;
+}
+
+// Stable descending order of the eigenvalues (equal values keep index order).
+template <int NP>
+__device__ void sort_desc(int M, EigSmem<NP> &s) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < M; i += 32) s.lam[i] = s.A[i][i].x;
+  __syncwarp();
+  for (int i = lane; i < M; i += 32) {
+    double li = s.lam[i];
+    int rank = 0;
+    for (int j = 0; j < M; ++j) {
+      double lj = s.lam[j];
+      rank += (lj > li) || (lj == li && j < i);
+    }
+    s.order[rank] = i;
+  }
+  __syncwarp();
+}
+
+// Writes B (column-major, ld M) of algorithm alg; returns 0 or a doa_status.
+template <int NP>
+__device__ int build_factor(int M, int d, int alg, EigSmem<NP> &s, double2 *__restrict__ B) {
+  const int lane = threadIdx.x & 31;
+  const int Kn = M - d;  // noise subspace dimension
+  if (alg == DOA_PHD) {
+    int col = s.order[M - 1];
+    for (int r = lane; r < M; r += 32) B[r] = s.V[r][col];
+    return 0;
+  }
+  if (alg == DOA_MUSIC || alg == DOA_EV) {
+    bool bad = false;
+    for (int e = lane; e < M * Kn; e += 32) {
+      int c = e / M, r = e % M;
+      int col = s.order[d + c];
+      double2 v = s.V[r][col];
+      if (alg == DOA_EV) {
+        double l = s.lam[col];
+        if (!(l > 0.0)) {
+          bad = true;
+          v = make_double2(0.0, 0.0);
+        } else {
+          double w = 1.0 / sqrt(l);
+          v.x *= w;
+          v.y *= w;
+        }
+      }
+      B[c * M + r] = v;
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    return bad ? DOA_ERANK : 0;
+  }
+  // MN: valph = P_n e1 / (e1^H P_n e1); (P_n e1)_r = sum_c V[r][c] conj(V[0][c]) over noise c
+  double nrm = 0.0;
+  for (int c = 0; c < Kn; ++c) {
+    double2 g = s.V[0][s.order[d + c]];
+    nrm += g.x * g.x + g.y * g.y;
+  }
+  if (!(nrm > 0.0)) {
+    for (int r = lane; r < M; r += 32) B[r] = make_double2(0.0, 0.0);
+    return DOA_ERANK;
+  }
+  const double inv = 1.0 / nrm;
+  for (int r = lane; r < M; r += 32) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int c = 0; c < Kn; ++c) {
+      int col = s.order[d + c];
+      double2 v = s.V[r][col], g = s.V[0][col];
+      // v * conj(g)
+      acc.x += v.x * g.x + v.y * g.y;
+      acc.y += v.y * g.x - v.x * g.y;
+    }
+    B[r] = make_double2(acc.x * inv, acc.y * inv);
+  }
+  return 0;
+}
+
+template <int NP>
+__global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_single_kernel(const double2 *R64, int M, int d, int alg,
+                                                                          double *evals, double2 *B, int *K_out,
+                                                                          int *info) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  EigSmem<NP> &s = *reinterpret_cast<EigSmem<NP> *>(smem);
+  const int lane = threadIdx.x & 31;
+  int res = jacobi_warp<NP>(R64, M, s);
+  int st = 0;
+  if (res > 0) {
+    sort_desc<NP>(M, s);
+    if (evals)
+      for (int i = lane; i < M; i += 32) evals[i] = s.lam[s.order[i]];
+    st = build_factor<NP>(M, d, alg, s, B);
+  } else {
+    st = -res;
+  }
+  if (lane == 0) {
+    *info = st ? -st : res;
+    if (K_out) *K_out = (alg == DOA_PHD || alg == DOA_MN) ? 1 : M - d;
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_batch_kernel(const uint8_t *plan, uint8_t *ws, int bucket,
+                                                                         int *status) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  EigSmem<NP> &s = reinterpret_cast<EigSmem<NP> *>(smem)[warp];
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
+  const int idx = blockIdx.x * eig_warps<NP>() + warp;
+  if (idx >= h->eig_count[bucket]) return;
+  const int prob = reinterpret_cast<const int32_t *>(plan + h->off_eig[bucket])[idx];
+  const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[prob];
+  const PlanJob *jobs = reinterpret_cast<const PlanJob *>(plan + h->off_job);
+  const int M = pp.p.M, d = pp.p.d;
+  int res = jacobi_warp<NP>(reinterpret_cast<const double2 *>(ws + pp.r64_off), M, s);
+  int st = 0;
+  if (res > 0) {
+    sort_desc<NP>(M, s);
+    if (pp.p.evals)
+      for (int i = lane; i < M; i += 32) pp.p.evals[i] = s.lam[s.order[i]];
+    for (int j = 0; j < pp.njobs; ++j) {
+      const PlanJob &jb = jobs[pp.first_job + j];
+      int e = build_factor<NP>(M, d, jb.alg, s, reinterpret_cast<double2 *>(ws + jb.B_off));
+      if (e && !st) st = e;
+    }
+  } else {
+    st = -res;
+    // a failed decomposition leaves zero factors, so the scan writes the 1/FLT_MIN sentinel
+    for (int j = 0; j < pp.njobs; ++j) {
+      const PlanJob &jb = jobs[pp.first_job + j];
+      double2 *B = reinterpret_cast<double2 *>(ws + jb.B_off);
+      for (int e = lane; e < M * jb.K; e += 32) B[e] = make_double2(0.0, 0.0);
+    }
+  }
+  if (lane == 0) status[prob] = st;
+}
+
+template <int NP>
+cudaError_t run_single(const double2 *R64, int M, int d, int alg, double *evals, double2 *B, int *K_out,
+                       int *info, cudaStream_t st) {
+  const int smem = (int)sizeof(EigSmem<NP>);
+  cudaError_t e = cudaFuncSetAttribute(eig_single_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  eig_single_kernel<NP><<<1, 32, smem, st>>>(R64, M, d, alg, evals, B, K_out, info);
+  return cudaGetLastError();
+}
+
+template <int NP>
+cudaError_t run_batch(const uint8_t *plan, const PlanHeader &h, uint8_t *ws, int *status, int bucket,
+                      cudaStream_t st) {
+  const int count = h.eig_count[bucket];
+  if (count == 0) return cudaSuccess;
+  constexpr int W = eig_warps<NP>();
+  const int smem = (int)sizeof(EigSmem<NP>) * W;
+  cudaError_t e = cudaFuncSetAttribute(eig_batch_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  eig_batch_kernel<NP><<<(count + W - 1) / W, 32 * W, smem, st>>>(plan, ws, bucket, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_eig_single(const double2 *R64, int M, int d, int alg, double *evals, double2 *B, int *K_out,
+                              int *info, cudaStream_t s) {
+  switch (m_bucket(M)) {
+    case 0: return run_single<8>(R64, M, d, alg, evals, B, K_out, info, s);
+    case 1: return run_single<16>(R64, M, d, alg, evals, B, K_out, info, s);
+    case 2: return run_single<32>(R64, M, d, alg, evals, B, K_out, info, s);
+    default: return run_single<64>(R64, M, d, alg, evals, B, K_out, info, s);
+  }
+}
+
+cudaError_t launch_eig_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, int *status,
+                             cudaStream_t s) {
+  cudaError_t e;
+  if ((e = run_batch<8>(plan_dev, h, ws, status, 0, s)) != cudaSuccess) return e;
+  if ((e = run_batch<16>(plan_dev, h, ws, status, 1, s)) != cudaSuccess) return e;
+  if ((e = run_batch<32>(plan_dev, h, ws, status, 2, s)) != cudaSuccess) return e;
+  return run_batch<64>(plan_dev, h, ws, status, 3, s);
+}
+
+}  // namespace doa

@@ -1,0 +1,204 @@
+// Step-5 (Table 2; steering vector Eq. 2): pseudospectrum P_k = 1 / ||B^H a(theta_k)||^2, which
+// equals 1 / (a^H C a) for the weighting matrix C = B B^H of Table 3 and is never negative.
+//
+// Fused, on CUDA cores in FP32: every thread evaluates PT consecutive grid points. For each it
+// generates the M steering phasors in registers from the grid's 32-bit phase step S_k
+// (phase of element m = m*S_k mod 2^32, exact integer arithmetic; phasor_q32 turns a phase into
+// cos + j sin), contracts them with the noise factor B (held in shared memory as FP32, read as
+// warp-wide broadcasts) one column at a time, accumulates |y_k|^2, and stores 1/den with
+// vectorised stores. The whole block of PT x M phasors is reused across the K columns of B.
+#include <float.h>
+
+#include "doa_internal.cuh"
+
+namespace doa {
+namespace {
+
+__global__ void grid_table_single_kernel(double lo, double step, int L, uint32_t *S) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < L) S[k] = grid_phase_step(lo, step, k);
+}
+
+__global__ void grid_table_batch_kernel(const uint8_t *plan, uint8_t *ws) {
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
+  const PlanGrid g = reinterpret_cast<const PlanGrid *>(plan + h->off_grid)[blockIdx.y];
+  uint32_t *S = reinterpret_cast<uint32_t *>(ws + g.S_off);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.L; k += gridDim.x * blockDim.x)
+    S[k] = grid_phase_step(g.lo, g.step, k);
+}
+
+// B (M x K complex128, column-major, ld M) -> Bs[k][m] (FP32, rows m >= M zero-padded to MP).
+template <int MP>
+__device__ __forceinline__ void load_factor(const double2 *__restrict__ B, int M, int K, float2 *Bs) {
+  for (int e = threadIdx.x; e < K * MP; e += blockDim.x) {
+    int k = e / MP, m = e % MP;
+    float2 v = make_float2(0.f, 0.f);
+    if (m < M) {
+      double2 b = B[(size_t)k * M + m];
+      v = make_float2((float)b.x, (float)b.y);
+    }
+    Bs[e] = v;
+  }
+}
+
+// Evaluates the PT points k0 .. k0+PT-1 (those < L) of one spectrum. S may alias P: each
+// thread reads its own phase steps before it writes its own outputs.
+template <int MP, int PT>
+__device__ __forceinline__ void scan_points(const float2 *Bs, int K, const uint32_t *S, float *P, int L, int k0) {
+  float2 a[PT][MP];
+#pragma unroll
+  for (int j = 0; j < PT; ++j) {
+    uint32_t step = (k0 + j < L) ? S[k0 + j] : 0u;
+    uint32_t phi = 0u;
+#pragma unroll
+    for (int m = 0; m < MP; ++m) {
+      a[j][m] = phasor_q32(phi);
+      phi += step;
+    }
+  }
+  float den[PT];
+#pragma unroll
+  for (int j = 0; j < PT; ++j) den[j] = 0.f;
+  for (int k = 0; k < K; ++k) {
+    float yr[PT], yi[PT];
+#pragma unroll
+    for (int j = 0; j < PT; ++j) yr[j] = yi[j] = 0.f;
+#pragma unroll
+    for (int m = 0; m < MP; ++m) {
+      const float2 b = Bs[k * MP + m];
+#pragma unroll
+      for (int j = 0; j < PT; ++j) {
+        // conj(b) * a = (br ar + bi ai) + j (br ai - bi ar)
+        yr[j] = fmaf(b.x, a[j][m].x, fmaf(b.y, a[j][m].y, yr[j]));
+        yi[j] = fmaf(b.x, a[j][m].y, fmaf(-b.y, a[j][m].x, yi[j]));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < PT; ++j) den[j] = fmaf(yr[j], yr[j], fmaf(yi[j], yi[j], den[j]));
+  }
+  float out[PT];
+#pragma unroll
+  for (int j = 0; j < PT; ++j) out[j] = 1.0f / fmaxf(den[j], FLT_MIN);
+  // vectorised store when the whole group is in range and aligned
+  if (PT == 4 && k0 + 3 < L && ((reinterpret_cast<uintptr_t>(P + k0) & 15u) == 0)) {
+    *reinterpret_cast<float4 *>(P + k0) = make_float4(out[0], out[1], out[2 % PT], out[3 % PT]);
+  } else if (PT == 2 && k0 + 1 < L && ((reinterpret_cast<uintptr_t>(P + k0) & 7u) == 0)) {
+    *reinterpret_cast<float2 *>(P + k0) = make_float2(out[0], out[1 % PT]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < PT; ++j)
+      if (k0 + j < L) P[k0 + j] = out[j];
+  }
+}
+
+template <int MP, int PT>
+__global__ void __launch_bounds__(kScanThreads) scan_single_kernel(const double2 *B, int M, int K, int L,
+                                                                   const uint32_t *S, float *P) {
+  __shared__ __align__(16) float2 Bs[MP * MP];
+  load_factor<MP>(B, M, K, Bs);
+  __syncthreads();
+  const int k0 = (blockIdx.x * kScanThreads + threadIdx.x) * PT;
+  scan_points<MP, PT>(Bs, K, S, P, L, k0);
+}
+
+// Persistent batched scan over the tiles of the jobs of one M bucket. Tiles are striped over
+// the CTAs; the job of a tile is found by binary search on the jobs' first tiles.
+template <int MP, int PT>
+__global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t *plan, uint8_t *ws, int bucket) {
+  __shared__ __align__(16) float2 Bs[MP * MP];
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
+  const int njobs = h->scan_jobs[bucket];
+  const int64_t ntiles = h->scan_tiles[bucket];
+  const int32_t *list = reinterpret_cast<const int32_t *>(plan + h->off_scan[bucket]);
+  const PlanJob *jobs = reinterpret_cast<const PlanJob *>(plan + h->off_job);
+  const PlanProblem *probs = reinterpret_cast<const PlanProblem *>(plan + h->off_prob);
+  const PlanGrid *grids = reinterpret_cast<const PlanGrid *>(plan + h->off_grid);
+  constexpr int TP = kScanThreads * PT;
+  int cur = -1;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {  // last job with tile_start <= t
+      int mid = (lo + hi + 1) >> 1;
+      if (jobs[list[mid]].tile_start <= t) lo = mid; else hi = mid - 1;
+    }
+    const PlanJob &jb = jobs[list[lo]];
+    const PlanProblem &pp = probs[jb.prob];
+    if (lo != cur) {
+      __syncthreads();
+      load_factor<MP>(reinterpret_cast<const double2 *>(ws + jb.B_off), pp.p.M, jb.K, Bs);
+      __syncthreads();
+      cur = lo;
+    }
+    const PlanGrid &g = grids[pp.grid_id];
+    const uint32_t *S = reinterpret_cast<const uint32_t *>(ws + g.S_off);
+    float *P = pp.p.P + (size_t)jb.slot * g.L;
+    const int k0 = (int)(t - jb.tile_start) * TP + threadIdx.x * PT;
+    scan_points<MP, PT>(Bs, jb.K, S, P, g.L, k0);
+  }
+}
+
+int g_num_sms = 0;
+
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+template <int MP, int PT>
+cudaError_t run_batch(const uint8_t *plan, const PlanHeader &h, uint8_t *ws, int bucket, cudaStream_t s) {
+  const int64_t tiles = h.scan_tiles[bucket];
+  if (tiles == 0) return cudaSuccess;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_batch_kernel<MP, PT>, kScanThreads, 0);
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)num_sms() * per_sm;
+  if (grid > tiles) grid = tiles;
+  scan_batch_kernel<MP, PT><<<(unsigned)grid, kScanThreads, 0, s>>>(plan, ws, bucket);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_grid_table_single(double lo, double step, int L, uint32_t *S, cudaStream_t s) {
+  grid_table_single_kernel<<<(L + 255) / 256, 256, 0, s>>>(lo, step, L, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grid_tables(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s) {
+  if (h.ngrids == 0) return cudaSuccess;
+  int64_t per = (h.grid_points + h.ngrids - 1) / h.ngrids;
+  int bx = (int)((per + 255) / 256);
+  if (bx > 4096) bx = 4096;
+  if (bx < 1) bx = 1;
+  grid_table_batch_kernel<<<dim3(bx, h.ngrids), 256, 0, s>>>(plan_dev, ws);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_single(const double2 *B, int M, int K, int L, const uint32_t *S, float *P,
+                               cudaStream_t s) {
+  const int b = m_bucket(M);
+  const int tp = scan_tile_points(b);
+  const unsigned grid = (unsigned)((L + tp - 1) / tp);
+  switch (b) {
+    case 0: scan_single_kernel<8, 4><<<grid, kScanThreads, 0, s>>>(B, M, K, L, S, P); break;
+    case 1: scan_single_kernel<16, 2><<<grid, kScanThreads, 0, s>>>(B, M, K, L, S, P); break;
+    case 2: scan_single_kernel<32, 1><<<grid, kScanThreads, 0, s>>>(B, M, K, L, S, P); break;
+    default: scan_single_kernel<64, 1><<<grid, kScanThreads, 0, s>>>(B, M, K, L, S, P); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = run_batch<8, 4>(plan_dev, h, ws, 0, s)) != cudaSuccess) return e;
+  if ((e = run_batch<16, 2>(plan_dev, h, ws, 1, s)) != cudaSuccess) return e;
+  if ((e = run_batch<32, 1>(plan_dev, h, ws, 2, s)) != cudaSuccess) return e;
+  return run_batch<64, 1>(plan_dev, h, ws, 3, s);
+}
+
+}  // namespace doa

@@ -1,0 +1,187 @@
+"""Thin Python binding of libdoa.so (C ABI declared in include/doa.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA kernels.
+PyTorch supplies device memory and streams. The library must have been built
+(``paper_2007_14135_gb300.build.build()``); importing this module without it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdoa.so")
+
+PHD, MUSIC, EV, MN = 0, 1, 2, 3
+FP32, BF16, BF16X3, FP16X3 = 0, 1, 2, 3
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ERANK, ENONFINITE, ETIMEOUT = range(8)
+BATCH_STAGES = 5
+STAGE_NAMES = ("phase_tables", "covariance", "eig_noise_subspace", "scan", "peaks")
+
+# every symbol include/doa.h declares
+EXPORTS = ("doa_status_str", "doa_covariance", "doa_noise_subspace", "doa_scan", "doa_peaks",
+           "doa_batch_plan_bytes", "doa_batch_plan", "doa_solve_batch")
+
+
+class DoaError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {status_str(status)} ({status})")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("lo_deg", ctypes.c_double), ("step_deg", ctypes.c_double),
+                ("L", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("P", ctypes.c_void_p), ("peak_idx", ctypes.c_void_p),
+                ("peak_val", ctypes.c_void_p), ("peak_count", ctypes.c_void_p),
+                ("evals", ctypes.c_void_p), ("grid", Grid), ("M", ctypes.c_int32),
+                ("N", ctypes.c_int32), ("ldx", ctypes.c_int32), ("d", ctypes.c_int32),
+                ("alg_mask", ctypes.c_uint32), ("prec", ctypes.c_int32)]
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise RuntimeError(f"libdoa.so is missing at {path}: run paper_2007_14135_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    lib.doa_status_str.argtypes = [i]
+    lib.doa_status_str.restype = ctypes.c_char_p
+    lib.doa_covariance.argtypes = [vp, i, i, i, vp, vp, i, vp]
+    lib.doa_noise_subspace.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp]
+    lib.doa_scan.argtypes = [vp, i, i, Grid, i, vp, vp]
+    lib.doa_peaks.argtypes = [vp, i, i, vp, vp, vp, vp]
+    lib.doa_batch_plan_bytes.argtypes = [ctypes.POINTER(Problem), i]
+    lib.doa_batch_plan_bytes.restype = sz
+    lib.doa_batch_plan.argtypes = [ctypes.POINTER(Problem), i, vp, sz, ctypes.POINTER(sz),
+                                   ctypes.POINTER(ctypes.c_int)]
+    lib.doa_solve_batch.argtypes = [vp, vp, vp, sz, vp, vp, vp]
+    for name in ("doa_covariance", "doa_noise_subspace", "doa_scan", "doa_peaks",
+                 "doa_batch_plan", "doa_solve_batch"):
+        getattr(lib, name).restype = i
+    return lib
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def status_str(status: int) -> str:
+    return lib().doa_status_str(int(status)).decode()
+
+
+def _check(status: int, where: str) -> None:
+    if status != OK:
+        raise DoaError(status, where)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev(t: Optional[torch.Tensor]) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    return t.data_ptr()
+
+
+def grid(lo: float, step: float, L: int) -> Grid:
+    return Grid(float(lo), float(step), int(L), 0)
+
+
+# ------------------------------------------------------------------------------------ stages
+def doa_covariance(X: torch.Tensor, R: Optional[torch.Tensor] = None, R64: Optional[torch.Tensor] = None,
+                   prec: int = FP32, stream=None) -> None:
+    """R = X X^H / N. X: complex64 (M, N) with unit column stride (row stride = ldx)."""
+    assert X.dtype == torch.complex64 and X.dim() == 2 and X.stride(1) == 1
+    M, N = X.shape
+    _check(lib().doa_covariance(_dev(X), M, N, X.stride(0), _dev(R), _dev(R64), prec, _stream(stream)),
+           "doa_covariance")
+
+
+def doa_noise_subspace(R64: torch.Tensor, d: int, alg: int, B: torch.Tensor, info: torch.Tensor,
+                       evals: Optional[torch.Tensor] = None, K_out: Optional[torch.Tensor] = None,
+                       stream=None) -> None:
+    """Jacobi eig of R64 (complex128 (M, M)) and the factor B (complex128, M*M capacity)."""
+    M = R64.shape[0]
+    assert R64.dtype == torch.complex128 and B.dtype == torch.complex128 and B.numel() >= M * M
+    _check(lib().doa_noise_subspace(_dev(R64), M, d, alg, _dev(evals), _dev(B), _dev(K_out), _dev(info),
+                                    _stream(stream)), "doa_noise_subspace")
+
+
+def doa_scan(B: torch.Tensor, M: int, K: int, g: Grid, P: torch.Tensor, prec: int = FP32, stream=None) -> None:
+    """P_k = 1/||B^H a(theta_k)||^2 for the grid. B: complex128, column-major (ld M)."""
+    assert B.dtype == torch.complex128 and P.dtype == torch.float32 and P.numel() >= g.L
+    _check(lib().doa_scan(_dev(B), M, K, g, prec, _dev(P), _stream(stream)), "doa_scan")
+
+
+def doa_peaks(P: torch.Tensor, d: int, idx: torch.Tensor, val: torch.Tensor, count: torch.Tensor,
+              L: Optional[int] = None, stream=None) -> None:
+    L = P.numel() if L is None else L
+    _check(lib().doa_peaks(_dev(P), L, d, _dev(idx), _dev(val), _dev(count), _stream(stream)), "doa_peaks")
+
+
+# ------------------------------------------------------------------------------------ batch
+def make_problem(X: torch.Tensor, d: int, alg_mask: int, g: Grid, P: torch.Tensor, peak_idx: torch.Tensor,
+                 peak_val: torch.Tensor, peak_count: torch.Tensor, evals: Optional[torch.Tensor] = None,
+                 prec: int = FP32) -> Problem:
+    """Descriptor of one problem; the tensors must outlive every solve that uses it."""
+    assert X.dtype == torch.complex64 and X.dim() == 2 and X.stride(1) == 1
+    M, N = X.shape
+    return Problem(_dev(X), _dev(P), _dev(peak_idx), _dev(peak_val), _dev(peak_count), _dev(evals), g,
+                   M, N, X.stride(0), d, alg_mask, prec)
+
+
+class BatchPlan:
+    """Host plan bytes, their device copy, and the workspace size (doa_batch_plan)."""
+
+    def __init__(self, problems: Sequence[Problem], device: str = "cuda"):
+        arr = (Problem * len(problems))(*problems)
+        n = lib().doa_batch_plan_bytes(arr, len(problems))
+        if n == 0:
+            bad = ctypes.c_int(-1)
+            ws = ctypes.c_size_t(0)
+            st = lib().doa_batch_plan(arr, len(problems), None, 0, ctypes.byref(ws), ctypes.byref(bad))
+            raise DoaError(st if st else EINVAL, f"doa_batch_plan (problem {bad.value})")
+        self.host = np.zeros(n, dtype=np.uint8)
+        ws = ctypes.c_size_t(0)
+        bad = ctypes.c_int(-1)
+        _check(lib().doa_batch_plan(arr, len(problems), self.host.ctypes.data, n, ctypes.byref(ws),
+                                    ctypes.byref(bad)), f"doa_batch_plan (problem {bad.value})")
+        self.ws_bytes = int(ws.value)
+        self.nprob = len(problems)
+        self.dev = torch.from_numpy(self.host).to(device)
+        self.problems = arr
+
+
+def doa_solve_batch(plan: BatchPlan, ws: torch.Tensor, status: torch.Tensor, stage_events=None,
+                    stream=None) -> None:
+    """Runs the plan. stage_events: None or DOA_BATCH_STAGES + 1 torch.cuda.Event (enable_timing)."""
+    assert ws.numel() * ws.element_size() >= plan.ws_bytes and status.numel() >= plan.nprob
+    ev = None
+    if stage_events is not None:
+        assert len(stage_events) == BATCH_STAGES + 1
+        ev = (ctypes.c_void_p * len(stage_events))(*[e.cuda_event for e in stage_events])
+    _check(lib().doa_solve_batch(plan.host.ctypes.data, _dev(plan.dev), _dev(ws), plan.ws_bytes, _dev(status),
+                                 ev, _stream(stream)), "doa_solve_batch")
+
+
+def workspace(plan: BatchPlan, device: str = "cuda") -> torch.Tensor:
+    """A device buffer of the plan's workspace size (256-byte aligned by the caching allocator)."""
+    return torch.empty(max(plan.ws_bytes, 256), dtype=torch.uint8, device=device)

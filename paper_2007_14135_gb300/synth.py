@@ -194,3 +194,50 @@ def custom(M: int, d: int, N: int, angles: Optional[Sequence[float]], snr_db: fl
            else draw_angles(rng, d, -60.0, 60.0, 5.0))
     X = snapshots(rng, M, N, ang, snr_db)
     return Instance(X, M, d, N, ang, snr_db, GRID_LO, step, grid_size(step), seed)
+
+
+def _fill_paper_density(args):
+    shm_name, shape, start, stop, base_seed, N = args
+    from multiprocessing import shared_memory
+    shm = shared_memory.SharedMemory(name=shm_name)
+    try:
+        X = np.ndarray(shape, dtype=np.complex64, buffer=shm.buf)
+        meta = []
+        for i in range(start, stop):
+            inst = paper_density(i, base_seed, N)
+            X[i] = inst.X
+            meta.append((inst.angles, inst.snr_db, inst.seed))
+        return meta
+    finally:
+        shm.close()
+
+
+def paper_density_batch_parallel(count: int, base_seed: int = 20071414, N: int = 4096,
+                                 workers: Optional[int] = None):
+    """Same bytes as paper_density_batch, generated by `workers` spawned processes into shared
+    memory. Returns (X complex64 (count, 16, N), list of Instance without X)."""
+    import multiprocessing as mp
+    import os
+    from multiprocessing import shared_memory
+    workers = workers or min(16, os.cpu_count() or 1)
+    M = 16
+    shape = (count, M, N)
+    nbytes = int(np.prod(shape)) * 8
+    if workers <= 1 or count < 64:
+        return paper_density_batch(count, base_seed, N)
+    shm = shared_memory.SharedMemory(create=True, size=nbytes)
+    try:
+        per = (count + workers - 1) // workers
+        tasks = [(shm.name, shape, s, min(count, s + per), base_seed, N) for s in range(0, count, per)]
+        with mp.get_context("spawn").Pool(len(tasks)) as pool:
+            metas = pool.map(_fill_paper_density, tasks)
+        X = np.ndarray(shape, dtype=np.complex64, buffer=shm.buf).copy()
+    finally:
+        shm.close()
+        shm.unlink()
+    step = 0.01
+    meta = []
+    for part in metas:
+        for ang, snr, seed in part:
+            meta.append(Instance(None, M, 4, N, ang, snr, GRID_LO, step, grid_size(step), seed))
+    return X, meta

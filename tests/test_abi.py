@@ -1,0 +1,112 @@
+"""The C ABI library builds, loads and exports every symbol include/doa.h declares; host-side
+planning and argument checks behave as documented. No GPU needed (no kernel is launched)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libdoa():
+    from paper_2007_14135_gb300 import build
+    build.build()
+    from paper_2007_14135_gb300 import doa
+    return doa
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "doa.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(doa_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(libdoa):
+    declared = _declared_functions()
+    assert len(declared) >= 8
+    lib = ctypes.CDLL(libdoa.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(libdoa.EXPORTS) == declared
+
+
+def test_status_strings(libdoa):
+    for s in range(8):
+        assert libdoa.status_str(s)
+    assert libdoa.status_str(99) == "unknown status"
+
+
+def test_argument_errors_return_einval(libdoa):
+    L = libdoa.lib()
+    fake = ctypes.c_void_p(0x10000)  # never dereferenced: every call below fails its checks first
+    g = libdoa.grid(-90.0, 0.1, 1801)
+    assert L.doa_covariance(None, 8, 100, 100, fake, fake, 0, None) == libdoa.EINVAL
+    assert L.doa_covariance(fake, 1, 100, 100, fake, fake, 0, None) == libdoa.EINVAL
+    assert L.doa_covariance(fake, 65, 100, 100, fake, fake, 0, None) == libdoa.EINVAL
+    assert L.doa_covariance(fake, 8, 100, 99, fake, fake, 0, None) == libdoa.EINVAL
+    assert L.doa_covariance(fake, 8, 100, 100, None, None, 0, None) == libdoa.EINVAL
+    assert L.doa_covariance(ctypes.c_void_p(0x10004), 8, 100, 100, fake, fake, 0, None) == libdoa.EINVAL
+    assert L.doa_noise_subspace(fake, 8, 8, 1, None, fake, None, fake, None) == libdoa.EINVAL
+    assert L.doa_noise_subspace(fake, 8, 2, 4, None, fake, None, fake, None) == libdoa.EINVAL
+    assert L.doa_noise_subspace(fake, 8, 2, 1, None, fake, None, None, None) == libdoa.EINVAL
+    assert L.doa_scan(fake, 8, 0, g, 0, fake, None) == libdoa.EINVAL
+    assert L.doa_scan(fake, 8, 9, g, 0, fake, None) == libdoa.EINVAL
+    assert L.doa_scan(fake, 8, 6, libdoa.grid(-90.0, 0.1, 2), 0, fake, None) == libdoa.EINVAL
+    assert L.doa_scan(fake, 8, 6, libdoa.grid(-90.0, 0.0, 100), 0, fake, None) == libdoa.EINVAL
+    assert L.doa_scan(fake, 8, 6, g, 7, fake, None) == libdoa.EINVAL
+    assert L.doa_peaks(fake, 2, 1, fake, fake, fake, None) == libdoa.EINVAL
+    assert L.doa_peaks(fake, 10, 1, None, fake, fake, None) == libdoa.EINVAL
+
+
+def _prob(libdoa, M=16, N=4096, d=4, mask=0xF, L=18001, step=0.01, **kw):
+    p = libdoa.Problem(0x100000, 0x200000, 0x300000, 0x400000, 0x500000, 0, libdoa.grid(-90.0, step, L),
+                       M, N, N, d, mask, 0)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def test_batch_plan_layout(libdoa):
+    import numpy as np
+    probs = [_prob(libdoa), _prob(libdoa, M=8, N=1000, d=2, mask=0b0010, L=1801, step=0.1),
+             _prob(libdoa, M=33, N=3000, d=5, mask=0b1001, L=1801, step=0.1)]
+    arr = (libdoa.Problem * 3)(*probs)
+    n = libdoa.lib().doa_batch_plan_bytes(arr, 3)
+    assert n > 0
+    buf = np.zeros(n, np.uint8)
+    ws = ctypes.c_size_t(0)
+    bad = ctypes.c_int(7)
+    assert libdoa.lib().doa_batch_plan(arr, 3, buf.ctypes.data, n, ctypes.byref(ws), ctypes.byref(bad)) == 0
+    assert bad.value == -1
+    hdr = buf[:64].view(np.int32)
+    assert hdr[0] == 0x444F4131            # magic
+    assert list(hdr[1:6]) == [3, 4 + 1 + 2, 2, 4 + 1 + 3, 2]   # nprob, njobs, ngrids, ncov, nreduce
+    # workspace: tables, 3 R + partials, 7 factors (M*M complex128 each), 256-byte rounded
+    need = 18001 * 4 + 1801 * 4 + (16 * 16 * 16) * (1 + 4 + 4) + (8 * 8 * 16) * (1 + 1) + (33 * 33 * 16) * (1 + 3 + 2)
+    assert ws.value >= need and ws.value < need + 256 * 40
+    # too small a buffer
+    assert libdoa.lib().doa_batch_plan(arr, 3, buf.ctypes.data, n - 1, ctypes.byref(ws), None) == libdoa.ENOMEM
+
+
+@pytest.mark.parametrize("field,value", [("M", 1), ("M", 65), ("d", 16), ("d", -1), ("N", 0), ("ldx", 100),
+                                         ("alg_mask", 0), ("alg_mask", 16), ("prec", 9), ("X", None)])
+def test_batch_plan_rejects(libdoa, field, value):
+    import numpy as np
+    probs = [_prob(libdoa), _prob(libdoa, **{field: value})]
+    arr = (libdoa.Problem * 2)(*probs)
+    assert libdoa.lib().doa_batch_plan_bytes(arr, 2) == 0
+    buf = np.zeros(1 << 16, np.uint8)
+    ws = ctypes.c_size_t(0)
+    bad = ctypes.c_int(-5)
+    st = libdoa.lib().doa_batch_plan(arr, 2, buf.ctypes.data, buf.size, ctypes.byref(ws), ctypes.byref(bad))
+    assert st == libdoa.EINVAL and bad.value == 1
+
+
+def test_solve_batch_rejects_bad_plan(libdoa):
+    import numpy as np
+    junk = np.zeros(256, np.uint8)
+    fake = ctypes.c_void_p(0x10000)
+    assert libdoa.lib().doa_solve_batch(junk.ctypes.data, fake, fake, 1 << 20, fake, None, None) == libdoa.EINVAL

@@ -1,0 +1,285 @@
+"""GPU parity: every stage of the CUDA path, called through the C ABI, against the FP64 oracle on
+the same seeded complex64 inputs."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2007_14135_gb300 import synth
+from tests.gpu_common import (DB_TOL, EV, MN, MUSIC, PHD, compare_peaks, db_error, factor_from_decomposition,
+                              percent_error, require_gpu)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    return require_gpu()
+
+
+# ------------------------------------------------------------------------------ Step-1
+@pytest.mark.parametrize("M,N,pad", [(2, 3, 0), (3, 7, 1), (8, 1024, 0), (12, 1000, 3), (16, 4096, 0),
+                                     (16, 4097, 5), (32, 3000, 0), (64, 5000, 2), (64, 16384, 0)])
+def test_covariance(env, M, N, pad):
+    torch, doa = env
+    inst = synth.custom(M, min(3, M - 1), N, None, 10.0, 0.1, seed=1000 + M * 7 + N)
+    Xh = np.zeros((M, N + pad), np.complex64)
+    Xh[:, :N] = inst.X
+    X = torch.from_numpy(Xh).cuda()[:, :N]
+    R64 = torch.empty((M, M), dtype=torch.complex128, device="cuda")
+    R32 = torch.empty((M, M), dtype=torch.complex64, device="cuda")
+    doa.doa_covariance(X, R=R32, R64=R64)
+    torch.cuda.synchronize()
+    Ro = oracle.covariance(inst.X)
+    scale = np.max(np.abs(Ro))
+    err = np.max(np.abs(R64.cpu().numpy() - Ro)) / scale
+    assert err < 2e-6, err
+    assert np.max(np.abs(R32.cpu().numpy() - Ro)) / scale < 3e-6
+    Rg = R64.cpu().numpy()
+    assert np.array_equal(Rg, Rg.conj().T)
+
+
+# ------------------------------------------------------------------------------ Steps 2-4
+@pytest.mark.parametrize("M,d", [(2, 1), (3, 1), (5, 2), (8, 2), (8, 0), (8, 7), (12, 5), (16, 4), (31, 9),
+                                 (32, 16), (64, 8)])
+def test_noise_subspace(env, M, d):
+    torch, doa = env
+    inst = synth.custom(M, d, max(4 * M, 256), None, 12.0, 0.1, seed=2000 + M * 13 + d)
+    Ro = oracle.covariance(inst.X)
+    ev_o, V_o, _ = oracle.eigh(Ro)
+    R = torch.from_numpy(Ro).cuda()
+    for alg in (PHD, MUSIC, EV, MN):
+        B = torch.zeros(M * M, dtype=torch.complex128, device="cuda")
+        ev = torch.empty(M, dtype=torch.float64, device="cuda")
+        info = torch.zeros(1, dtype=torch.int32, device="cuda")
+        K = torch.zeros(1, dtype=torch.int32, device="cuda")
+        doa.doa_noise_subspace(R, d, alg, B, info, evals=ev, K_out=K)
+        torch.cuda.synchronize()
+        assert info.item() > 0, info.item()
+        Kx = 1 if alg in (PHD, MN) else M - d
+        assert K.item() == Kx
+        np.testing.assert_allclose(ev.cpu().numpy(), ev_o, rtol=0, atol=1e-12 * ev_o[0])
+        Bg = B.cpu().numpy()[:M * Kx].reshape(Kx, M).T
+        Cg = Bg @ Bg.conj().T
+        Co, st = oracle.weighting(ev_o, V_o, d, alg)
+        assert st == 0
+        assert np.max(np.abs(Cg - Co)) < 1e-10 * np.max(np.abs(Co)), (alg, np.max(np.abs(Cg - Co)))
+
+
+def test_noise_subspace_exact_covariance(env):
+    """R = A A^H + sigma^2 I: noise eigenvalues sigma^2 and E_n^H a(theta_i) = 0 on the GPU too."""
+    torch, doa = env
+    M, ang, s2 = 8, [-20.0, 35.0], 0.1
+    m = np.arange(M)[:, None]
+    A = np.exp(1j * np.pi * m * np.sin(np.radians(ang))[None, :])
+    R = torch.from_numpy(A @ A.conj().T + s2 * np.eye(M)).cuda()
+    B = torch.zeros(M * M, dtype=torch.complex128, device="cuda")
+    ev = torch.empty(M, dtype=torch.float64, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    doa.doa_noise_subspace(R, 2, MUSIC, B, info, evals=ev)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(ev.cpu().numpy()[2:], s2, rtol=1e-12)
+    En = B.cpu().numpy()[:M * 6].reshape(6, M).T
+    assert np.linalg.norm(En.conj().T @ A) < 1e-12
+    assert np.max(np.abs(En.conj().T @ En - np.eye(6))) < 1e-13
+
+
+def test_noise_subspace_status(env):
+    torch, doa = env
+    M = 6
+    R = torch.zeros((M, M), dtype=torch.complex128, device="cuda")
+    B = torch.zeros(M * M, dtype=torch.complex128, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    doa.doa_noise_subspace(R, 2, EV, B, info)          # all eigenvalues 0
+    assert info.item() == -doa.ERANK
+    doa.doa_noise_subspace(R, 2, MN, B, info)          # V = I: e_1 outside the noise subspace
+    assert info.item() == -doa.ERANK
+    doa.doa_noise_subspace(R, 2, MUSIC, B, info)
+    assert info.item() > 0
+    R[1, 2] = float("nan")
+    doa.doa_noise_subspace(R, 2, MUSIC, B, info)
+    assert info.item() == -doa.ENONFINITE
+
+
+# ------------------------------------------------------------------------------ Step-5
+@pytest.mark.parametrize("M,d,step,L", [(8, 2, 0.1, 1801), (16, 4, 0.01, 18001), (12, 3, 0.07, 2573),
+                                        (32, 5, 0.05, 3601), (64, 8, 0.01, 18001), (5, 1, 45.0, 5),
+                                        (2, 1, 90.0, 3), (16, 0, 1.0, 181)])
+def test_scan(env, M, d, step, L):
+    torch, doa = env
+    inst = synth.custom(M, d, 2048, None, 15.0, step, seed=3000 + M + d)
+    Ro = oracle.covariance(inst.X)
+    ev_o, V_o, _ = oracle.eigh(Ro)
+    lo = -90.0
+    for alg in (PHD, MUSIC, EV, MN):
+        Co, _ = oracle.weighting(ev_o, V_o, d, alg)
+        Bf = factor_from_decomposition(ev_o, V_o, d, alg)
+        assert np.max(np.abs(Bf @ Bf.conj().T - Co)) < 1e-12 * np.max(np.abs(Co))
+        K = Bf.shape[1]
+        Po, _ = oracle.scan(Co, lo, step, L)
+        B = torch.from_numpy(np.ascontiguousarray(Bf.T).reshape(-1)).cuda()
+        P = torch.empty(L + 1, dtype=torch.float32, device="cuda")[1:]   # 4-byte aligned, not 8
+        doa.doa_scan(B, M, K, doa.grid(lo, step, L), P)
+        torch.cuda.synchronize()
+        Pg = P.cpu().numpy()
+        assert db_error(Pg, Po) < DB_TOL, (alg, db_error(Pg, Po))
+        assert percent_error(Pg, Po) < 0.05
+        assert Pg[0] == Pg[-1] or abs(step * (L - 1) - 180.0) > 1e-9
+
+
+# ------------------------------------------------------------------------------ Step-6
+def test_peaks_golden(env):
+    import json, os
+    torch, doa = env
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "peaks_cases.json")))
+    for c in g["cases"]:
+        P = torch.tensor(c["P"], dtype=torch.float32, device="cuda")
+        d = c["d"]
+        idx = torch.full((max(d, 1),), -7, dtype=torch.int32, device="cuda")
+        val = torch.zeros(max(d, 1), dtype=torch.float32, device="cuda")
+        cnt = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        doa.doa_peaks(P, d, idx, val, cnt)
+        n = cnt.item()
+        assert idx.cpu().numpy()[:n].tolist() == c["idx"], c["name"]
+
+
+@pytest.mark.parametrize("L,d,levels", [(3, 1, 3), (50, 3, 4), (1000, 5, 6), (18001, 4, 1000), (180001, 8, 50),
+                                        (360001, 8, 1 << 20)])
+def test_peaks_random(env, L, d, levels):
+    """Random (often tied) spectra: the GPU picker and the oracle's see the same float32 values."""
+    torch, doa = env
+    rng = np.random.default_rng(L + d)
+    for trial in range(3):
+        Ph = (rng.integers(0, levels, L) / levels).astype(np.float32)
+        P = torch.from_numpy(Ph).cuda()
+        idx = torch.zeros(d, dtype=torch.int32, device="cuda")
+        val = torch.zeros(d, dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        doa.doa_peaks(P, d, idx, val, cnt)
+        n = cnt.item()
+        io, vo = oracle.peaks(Ph.astype(np.float64), d)
+        assert idx.cpu().numpy()[:n].tolist() == io.tolist()
+        assert np.array_equal(val.cpu().numpy()[:n].astype(np.float64), vo)
+
+
+# ------------------------------------------------------------------------------ Steps 1-6
+def _single_pipeline(torch, doa, inst, alg):
+    M, d, L = inst.M, inst.d, inst.L
+    X = torch.from_numpy(inst.X).cuda()
+    R = torch.empty((M, M), dtype=torch.complex128, device="cuda")
+    B = torch.zeros(M * M, dtype=torch.complex128, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    K = torch.zeros(1, dtype=torch.int32, device="cuda")
+    P = torch.empty(L, dtype=torch.float32, device="cuda")
+    idx = torch.zeros(max(d, 1), dtype=torch.int32, device="cuda")
+    val = torch.zeros(max(d, 1), dtype=torch.float32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    doa.doa_covariance(X, R64=R)
+    doa.doa_noise_subspace(R, d, alg, B, info, K_out=K)
+    Kx = 1 if alg in (PHD, MN) else M - d
+    doa.doa_scan(B, M, Kx, doa.grid(inst.lo, inst.step, L), P)
+    doa.doa_peaks(P, d, idx, val, cnt)
+    torch.cuda.synchronize()
+    assert info.item() > 0 and K.item() == Kx
+    return P.cpu().numpy(), idx.cpu().numpy()[:cnt.item()]
+
+
+def test_single_calls_c1(env):
+    torch, doa = env
+    inst = synth.single_c1()
+    for alg in (PHD, MUSIC, EV, MN):
+        ref = oracle.solve(inst.X, inst.d, alg, inst.lo, inst.step, inst.L)
+        P, idx = _single_pipeline(torch, doa, inst, alg)
+        assert db_error(P, ref["P"]) < DB_TOL
+        assert idx.tolist() == ref["idx"].tolist()
+
+
+def _batch_solve(torch, doa, insts, masks):
+    tensors, probs = [], []
+    for inst, mask in zip(insts, masks):
+        nalg = bin(mask).count("1")
+        X = torch.from_numpy(inst.X).cuda()
+        P = torch.empty(nalg * inst.L, dtype=torch.float32, device="cuda")
+        idx = torch.full((nalg * max(inst.d, 1),), -1, dtype=torch.int32, device="cuda")
+        val = torch.zeros(nalg * max(inst.d, 1), dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(nalg, dtype=torch.int32, device="cuda")
+        ev = torch.empty(inst.M, dtype=torch.float64, device="cuda")
+        tensors.append((X, P, idx, val, cnt, ev))
+        probs.append(doa.make_problem(X, inst.d, mask, doa.grid(inst.lo, inst.step, inst.L), P, idx, val, cnt, ev))
+    plan = doa.BatchPlan(probs)
+    ws = doa.workspace(plan)
+    status = torch.full((len(insts),), -1, dtype=torch.int32, device="cuda")
+    doa.doa_solve_batch(plan, ws, status)
+    torch.cuda.synchronize()
+    return tensors, status.cpu().numpy()
+
+
+def _check_batch(torch, doa, insts, masks):
+    tensors, status = _batch_solve(torch, doa, insts, masks)
+    assert np.all(status == 0), status
+    worst = 0.0
+    for inst, mask, t in zip(insts, masks, tensors):
+        _, P, idx, _, cnt, ev = t
+        P = P.cpu().numpy().reshape(-1, inst.L)
+        idx = idx.cpu().numpy().reshape(-1, max(inst.d, 1))
+        cnt = cnt.cpu().numpy()
+        slot = 0
+        for alg in range(4):
+            if not (mask >> alg) & 1:
+                continue
+            ref = oracle.solve(inst.X, inst.d, alg, inst.lo, inst.step, inst.L)
+            err = db_error(P[slot], ref["P"])
+            worst = max(worst, err)
+            assert err < DB_TOL, (inst.seed, alg, err)
+            ok, ties = compare_peaks(idx[slot][:cnt[slot]], ref["idx"], ref["P"], 1e-4)
+            assert ok, (inst.seed, alg, idx[slot][:cnt[slot]], ref["idx"], ties)
+            slot += 1
+        np.testing.assert_allclose(ev.cpu().numpy(), ref["evals"], rtol=0, atol=1e-5 * ref["evals"][0])
+    return worst
+
+
+def test_batch_c1_all_algorithms(env):
+    torch, doa = env
+    _check_batch(torch, doa, [synth.single_c1()], [0xF])
+
+
+def test_batch_paper_density_sample(env):
+    torch, doa = env
+    insts = [synth.paper_density(i) for i in range(8)]
+    _check_batch(torch, doa, insts, [0xF] * len(insts))
+
+
+def test_batch_uneven_sample(env):
+    """Problems drawn from the uneven recipe (every M bucket, every algorithm), fine grids thinned."""
+    torch, doa = env
+    specs = synth.uneven_specs(4096)
+    picked, seen = [], set()
+    for s in specs:
+        key = (s.M, s.alg)
+        if key in seen or s.step < 0.01:
+            continue
+        seen.add(key)
+        picked.append(s)
+    insts = [synth.uneven_instance(s) for s in picked]
+    _check_batch(torch, doa, insts, [1 << s.alg for s in picked])
+
+
+def test_batch_edge_shapes(env):
+    torch, doa = env
+    insts = [synth.custom(2, 1, 5, [10.0], 20.0, 45.0, seed=1),           # L = 5
+             synth.custom(3, 0, 64, [], 0.0, 60.0, seed=2),               # d = 0, L = 4
+             synth.custom(9, 8, 700, None, 25.0, 0.25, seed=3),           # d = M - 1
+             synth.custom(64, 8, 2500, None, 10.0, 0.05, seed=4),
+             synth.custom(17, 3, 1, None, 10.0, 0.5, seed=5)]             # N = 1
+    insts[0].angles = np.array([10.0])
+    masks = [0xF, 0b0010, 0xF, 0b0110, 0b0010]
+    tensors, status = _batch_solve(torch, doa, insts, masks)
+    assert np.all(status == 0)
+    for inst, mask, t in zip(insts, masks, tensors):
+        P = t[1].cpu().numpy().reshape(-1, inst.L)
+        slot = 0
+        for alg in range(4):
+            if (mask >> alg) & 1:
+                ref = oracle.solve(inst.X, inst.d, alg, inst.lo, inst.step, inst.L)
+                if inst.N >= inst.M:   # rank-deficient R (N = 1) has an ill-posed noise basis
+                    assert db_error(P[slot], ref["P"]) < DB_TOL
+                slot += 1
