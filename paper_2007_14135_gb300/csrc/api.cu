@@ -149,7 +149,7 @@ doa_status doa_scan(const double *B, int M, int K, doa_grid grid, int prec, floa
   uint32_t *S = reinterpret_cast<uint32_t *>(P);  // phase table first, spectrum over it
   cudaError_t e = launch_grid_table_single(grid.lo_deg, grid.step_deg, grid.L, S, s);
   if (e != cudaSuccess) return DOA_ECUDA;
-  return cuda_status(launch_scan_single(reinterpret_cast<const double2 *>(B), M, K, grid.L, S, P, s));
+  return cuda_status(launch_scan_single(reinterpret_cast<const double2 *>(B), M, K, grid.L, grid.lo_deg, grid.step_deg, S, P, s));
 }
 
 doa_status doa_peaks(const float *P, int L, int d, int *idx, float *val, int *count, void *stream) {

@@ -1,16 +1,23 @@
-// Step-1 (Sec. 3.1, Eq. 3): R = X X^H / N on CUDA cores (FP32 products, FP64 across chunks).
+// Step-1 (Sec. 3.1, Eq. 3): R = X X^H / N on CUDA cores.
 //
 // A CTA handles one range of snapshots of one problem. It stages tiles of kTS snapshots of all
 // M rows in shared memory (loads coalesced along time); each thread owns a 4 x 4 block of the
-// upper triangle of R and a strided subset of each tile's snapshots and accumulates
-// x_a conj(x_b) with FP32 FMAs. The per-thread sums are then added across snapshot groups in
-// FP32 (a few dozen terms each) and the CTA's partial leaves as FP64.
+// upper triangle of R and a strided subset of each tile's snapshots.
+//
+// Two accumulation modes (template kComp):
+//  - plain: x_a conj(x_b) accumulated with FP32 FMAs (relative error ~1e-7 of |R|);
+//  - compensated: every real product is split exactly into p + e (p = fl(a*b), e = fma(a, b, -p))
+//    and added to a double-float accumulator (hi, lo) with TwoSum (Knuth), so the only error is
+//    the final rounding of hi + lo (about 2^-44 relative). The Pisarenko (PHD) spectrum needs it:
+//    its minimum eigenvector moves by |dR| / (lambda_{M-2} - lambda_{M-1}), and the noise
+//    eigenvalue gaps are tiny, so an FP32-accurate R shifts that spectrum by up to ~1 dB.
+// The per-thread sums are added across snapshot groups in double-float and leave as FP64.
 //
 // Batched form: one CTA per work item (problem, chunk of kCovChunk snapshots); multi-chunk
 // problems add their chunk partials in chunk order in FP64 (covariance_reduce_batch), so the
-// result is deterministic.
-// Single-problem form: a thread-block cluster of up to 8 CTAs splits the snapshots; CTA rank 0
-// adds the other CTAs' partials through distributed shared memory in rank order.
+// result is deterministic. Problems that request PHD use the compensated mode.
+// Single-problem form: a thread-block cluster of up to 8 CTAs splits the snapshots (always
+// compensated); CTA rank 0 adds the other CTAs' partials through distributed shared memory.
 #include <cooperative_groups.h>
 
 #include "doa_internal.cuh"
@@ -23,7 +30,8 @@ namespace {
 constexpr int kCovThreads = 256;
 constexpr int kTS = 64;   // snapshots per shared-memory tile
 constexpr int kRB = 4;    // register block edge
-constexpr int kSmemBytes = 32768;  // max(tile = 64 x 64 float2, group partials = 256 x 32 floats)
+// max(tile = 64 x 64 float2, staged group sums = 256 threads x 16 slots x float4)
+constexpr int kSmemBytes = 65536;
 constexpr int kMaxCluster = 8;
 
 struct CovLayout {
@@ -43,9 +51,41 @@ struct CovLayout {
   __device__ int nout() const { return nb * kRB * kRB; }
 };
 
-// Accumulates the snapshots [t0, t1) and leaves the CTA's FP32 sums (nb x 16 complex) at the
-// start of `smem`, which it returns.
-__device__ float2 *cov_accumulate(const float2 *__restrict__ X, int ldx, int t0, int t1, const CovLayout &lay,
+// s + e = a + b exactly (Knuth's TwoSum; no assumption on the magnitudes).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (h, l) += (h2, l2) in double-float arithmetic, renormalised.
+__device__ __forceinline__ void df_add(float &h, float &l, float h2, float l2) {
+  float s, e;
+  two_sum(h, h2, s, e);
+  e = __fadd_rn(e, __fadd_rn(l, l2));
+  h = __fadd_rn(s, e);
+  l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+// hi + lo += a * b, exactly up to the rounding of lo.
+template <bool kComp>
+__device__ __forceinline__ void mac(float &hi, float &lo, float a, float b) {
+  if (kComp) {
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    float s, t;
+    two_sum(hi, p, s, t);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, t));
+  } else {
+    hi = fmaf(a, b, hi);
+  }
+}
+
+// Accumulates the snapshots [t0, t1) and leaves the CTA's sums (nb x 16 slots of float4
+// (re_hi, re_lo, im_hi, im_lo)) at the start of `smem`, which it returns.
+template <bool kComp>
+__device__ float4 *cov_accumulate(const float2 *__restrict__ X, int ldx, int t0, int t1, const CovLayout &lay,
                                   uint8_t *smem) {
   float2 *tile = reinterpret_cast<float2 *>(smem);
   const int tid = threadIdx.x;
@@ -55,11 +95,11 @@ __device__ float2 *cov_accumulate(const float2 *__restrict__ X, int ldx, int t0,
   int bi, bj;
   lay.block_of(blk, bi, bj);
 
-  float acc[kRB][kRB][2];
+  float rh[kRB][kRB], rl[kRB][kRB], ih[kRB][kRB], il[kRB][kRB];
 #pragma unroll
   for (int i = 0; i < kRB; ++i)
 #pragma unroll
-    for (int j = 0; j < kRB; ++j) acc[i][j][0] = acc[i][j][1] = 0.f;
+    for (int j = 0; j < kRB; ++j) rh[i][j] = rl[i][j] = ih[i][j] = il[i][j] = 0.f;
 
   const int MP = lay.MB * kRB;
   for (int ts = t0; ts < t1; ts += kTS) {
@@ -85,37 +125,44 @@ __device__ float2 *cov_accumulate(const float2 *__restrict__ X, int ldx, int t0,
 #pragma unroll
           for (int j = 0; j < kRB; ++j) {
             // x_a * conj(x_b) = (ar br + ai bi) + j (ai br - ar bi)
-            acc[i][j][0] = fmaf(xa[i].x, xb[j].x, fmaf(xa[i].y, xb[j].y, acc[i][j][0]));
-            acc[i][j][1] = fmaf(xa[i].y, xb[j].x, fmaf(-xa[i].x, xb[j].y, acc[i][j][1]));
+            mac<kComp>(rh[i][j], rl[i][j], xa[i].x, xb[j].x);
+            mac<kComp>(rh[i][j], rl[i][j], xa[i].y, xb[j].y);
+            mac<kComp>(ih[i][j], il[i][j], xa[i].y, xb[j].x);
+            mac<kComp>(ih[i][j], il[i][j], -xa[i].x, xb[j].y);
           }
       }
     }
   }
-  // add across snapshot groups: stage the per-thread sums (tile memory is reused)
+  // add across snapshot groups (tile memory is reused for the staged sums)
   __syncthreads();
-  float2 *stage = reinterpret_cast<float2 *>(smem);  // groups x nb x 16
+  float4 *stage = reinterpret_cast<float4 *>(smem);  // groups x nb x 16
   const int nout = lay.nout();
   if (active) {
 #pragma unroll
     for (int i = 0; i < kRB; ++i)
 #pragma unroll
       for (int j = 0; j < kRB; ++j)
-        stage[(size_t)grp * nout + blk * kRB * kRB + i * kRB + j] = make_float2(acc[i][j][0], acc[i][j][1]);
+        stage[(size_t)grp * nout + blk * kRB * kRB + i * kRB + j] =
+            make_float4(rh[i][j], rl[i][j], ih[i][j], il[i][j]);
   }
   __syncthreads();
   // the owner of slot e is the only reader of stage[g * nout + e] for every g, so it may
-  // overwrite stage[e] (= out[e]) in place
+  // overwrite stage[e] in place
   for (int e = tid; e < nout; e += kCovThreads) {
-    float2 s = make_float2(0.f, 0.f);
-    for (int g = 0; g < lay.groups; ++g) {
-      float2 v = stage[(size_t)g * nout + e];
-      s.x += v.x;
-      s.y += v.y;
+    float4 s = stage[e];
+    for (int g = 1; g < lay.groups; ++g) {
+      float4 v = stage[(size_t)g * nout + e];
+      df_add(s.x, s.y, v.x, v.y);
+      df_add(s.z, s.w, v.z, v.w);
     }
     stage[e] = s;
   }
   __syncthreads();
   return stage;
+}
+
+__device__ __forceinline__ double2 slot_value(const float4 &v) {
+  return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
 }
 
 // Maps output slot e (block-major) to (row, col); returns false outside the upper triangle.
@@ -145,14 +192,14 @@ __device__ __forceinline__ void store_r(int M, int row, int col, double2 v, doub
 
 __global__ void __launch_bounds__(kCovThreads) covariance_cluster_kernel(const float2 *X, int M, int N, int ldx,
                                                                          int per_cta, float2 *R, double2 *R64) {
-  __shared__ __align__(16) uint8_t smem[kSmemBytes];
+  extern __shared__ __align__(16) uint8_t smem[];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int nranks = (int)cluster.num_blocks();
   CovLayout lay(M);
   const int t0 = rank * per_cta;
   const int t1 = min(N, t0 + per_cta);
-  float2 *part = cov_accumulate(X, ldx, t0, max(t0, t1), lay, smem);
+  float4 *part = cov_accumulate<true>(X, ldx, t0, max(t0, t1), lay, smem);
   cluster.sync();
   if (rank == 0) {
     const double inv_n = 1.0 / (double)N;
@@ -161,10 +208,10 @@ __global__ void __launch_bounds__(kCovThreads) covariance_cluster_kernel(const f
       if (!slot_rc(lay, e, row, col)) continue;
       double2 s = make_double2(0.0, 0.0);
       for (int r = 0; r < nranks; ++r) {
-        const float2 *rp = cluster.map_shared_rank(part, r);
-        float2 v = rp[e];
-        s.x += (double)v.x;
-        s.y += (double)v.y;
+        const float4 *rp = cluster.map_shared_rank(part, r);
+        double2 v = slot_value(rp[e]);
+        s.x += v.x;
+        s.y += v.y;
       }
       store_r(M, row, col, s, inv_n, R, R64);
     }
@@ -174,7 +221,7 @@ __global__ void __launch_bounds__(kCovThreads) covariance_cluster_kernel(const f
 
 // Batch: one CTA per work item (problem, chunk).
 __global__ void __launch_bounds__(kCovThreads) covariance_batch_kernel(const uint8_t *plan, uint8_t *ws) {
-  __shared__ __align__(16) uint8_t smem[kSmemBytes];
+  extern __shared__ __align__(16) uint8_t smem[];
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
   const PlanCovItem it = reinterpret_cast<const PlanCovItem *>(plan + h->off_cov)[blockIdx.x];
   const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[it.prob];
@@ -182,14 +229,16 @@ __global__ void __launch_bounds__(kCovThreads) covariance_batch_kernel(const uin
   CovLayout lay(M);
   const int t0 = it.chunk * kCovChunk;
   const int t1 = min(N, t0 + kCovChunk);
-  const float2 *part = cov_accumulate(reinterpret_cast<const float2 *>(pp.p.X), pp.p.ldx, t0, t1, lay, smem);
+  const float2 *X = reinterpret_cast<const float2 *>(pp.p.X);
+  const float4 *part = (pp.p.alg_mask & (1u << DOA_PHD)) ? cov_accumulate<true>(X, pp.p.ldx, t0, t1, lay, smem)
+                                                          : cov_accumulate<false>(X, pp.p.ldx, t0, t1, lay, smem);
   double2 *R64 = reinterpret_cast<double2 *>(ws + pp.r64_off);
   double2 *partial = reinterpret_cast<double2 *>(ws + pp.part_off) + (size_t)it.chunk * M * M;
   const double inv_n = 1.0 / (double)N;
   for (int e = threadIdx.x; e < lay.nout(); e += kCovThreads) {
     int row, col;
     if (!slot_rc(lay, e, row, col)) continue;
-    double2 v = make_double2((double)part[e].x, (double)part[e].y);
+    double2 v = slot_value(part[e]);
     if (pp.nchunks == 1)
       store_r(M, row, col, v, inv_n, nullptr, R64);
     else
@@ -223,27 +272,41 @@ __global__ void covariance_reduce_batch(const uint8_t *plan, uint8_t *ws) {
 
 cudaError_t launch_covariance_single(const float2 *X, int M, int N, int ldx, float2 *R, double2 *R64,
                                      cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(covariance_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   int chunks = (N + kCovChunk - 1) / kCovChunk;
   int nc = chunks < kMaxCluster ? chunks : kMaxCluster;
   int per = (N + nc - 1) / nc;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nc);
   cfg.blockDim = dim3(kCovThreads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = kSmemBytes;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = nc;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
+  cudaLaunchAttribute attr_[1];
+  attr_[0].id = cudaLaunchAttributeClusterDimension;
+  attr_[0].val.clusterDim.x = nc;
+  attr_[0].val.clusterDim.y = 1;
+  attr_[0].val.clusterDim.z = 1;
+  cfg.attrs = attr_;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, covariance_cluster_kernel, X, M, N, ldx, per, R, R64);
 }
 
 cudaError_t launch_covariance_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws,
                                     cudaStream_t s) {
-  if (h.ncov > 0) covariance_batch_kernel<<<h.ncov, kCovThreads, 0, s>>>(plan_dev, ws);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(covariance_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (h.ncov > 0) covariance_batch_kernel<<<h.ncov, kCovThreads, kSmemBytes, s>>>(plan_dev, ws);
   if (h.nreduce > 0) covariance_reduce_batch<<<h.nreduce, 256, 0, s>>>(plan_dev, ws);
   return cudaGetLastError();
 }

@@ -177,6 +177,9 @@ def doa_solve_batch(plan: BatchPlan, ws: torch.Tensor, status: torch.Tensor, sta
     ev = None
     if stage_events is not None:
         assert len(stage_events) == BATCH_STAGES + 1
+        for e in stage_events:      # torch creates the CUDA event on its first record
+            if not e.cuda_event:
+                e.record(torch.cuda.current_stream() if stream is None else stream)
         ev = (ctypes.c_void_p * len(stage_events))(*[e.cuda_event for e in stage_events])
     _check(lib().doa_solve_batch(plan.host.ctypes.data, _dev(plan.dev), _dev(ws), plan.ws_bytes, _dev(status),
                                  ev, _stream(stream)), "doa_solve_batch")

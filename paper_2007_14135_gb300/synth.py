@@ -58,14 +58,17 @@ def _source_response(M: int, angles_deg: Sequence[float]) -> np.ndarray:
     return np.exp(1j * np.pi * m * s)
 
 
-def draw_angles(rng: np.random.Generator, d: int, lo: float, hi: float, min_sep: float,
-                max_tries: int = 10000) -> np.ndarray:
-    """d angles uniform in [lo, hi] with pairwise separation >= min_sep (rejection sampling)."""
-    for _ in range(max_tries):
-        a = np.sort(rng.uniform(lo, hi, size=d))
-        if d < 2 or np.min(np.diff(a)) >= min_sep:
-            return a
-    raise RuntimeError("could not draw separated angles")
+def draw_angles(rng: np.random.Generator, d: int, lo: float, hi: float, min_sep: float) -> np.ndarray:
+    """d angles uniform over {theta in [lo, hi]^d : sorted gaps >= min_sep}: sorted uniforms on
+    [lo, hi - (d-1) min_sep] shifted by i*min_sep (a bijection onto the separated set that keeps
+    the distribution uniform)."""
+    if d == 0:
+        return np.zeros(0)
+    span = hi - lo - (d - 1) * min_sep
+    if span < 0:
+        raise ValueError("cannot place d separated angles in the range")
+    u = np.sort(rng.uniform(0.0, span, size=d))
+    return lo + u + min_sep * np.arange(d)
 
 
 def snapshots(rng: np.random.Generator, M: int, N: int, angles_deg: Sequence[float],

@@ -43,7 +43,8 @@ def test_covariance(env, M, N, pad):
                                  (32, 16), (64, 8)])
 def test_noise_subspace(env, M, d):
     torch, doa = env
-    inst = synth.custom(M, d, max(4 * M, 256), None, 12.0, 0.1, seed=2000 + M * 13 + d)
+    ang = None if d <= 8 else np.linspace(-70.0, 70.0, d) + 0.37   # many sources: spread evenly
+    inst = synth.custom(M, d, max(4 * M, 256), ang, 12.0, 0.1, seed=2000 + M * 13 + d)
     Ro = oracle.covariance(inst.X)
     ev_o, V_o, _ = oracle.eigh(Ro)
     R = torch.from_numpy(Ro).cuda()
