@@ -83,6 +83,28 @@ doa_status doa_covariance(const float *X, int M, int N, int ldx, float *R, doubl
                           void *stream);
 
 /*
+ * Covariance for callers that cannot allocate: same computation and result as doa_covariance
+ * (compensated FP32 accumulation, FP64 output; chunk sums combined in chunk order), but with no
+ * allocation and no caller workspace. The paper has no counterpart.
+ *   Who needs it: code that must not call cudaMalloc once running -- a fixed-memory real-time
+ *   processing loop (cudaMalloc can synchronise the device and take driver locks), a host
+ *   framework that forbids allocation after start-up, or a caller without its own allocator.
+ *   Scratch: a library-owned device array of DOA_NOALLOC_SCRATCH_BYTES (4 MiB), resident on
+ *   every GPU that loads the library until the process exits. A call needs
+ *   ceil(N / 1024) * M * M * 16 bytes of it (M = 64: N <= 65536); larger problems return
+ *   DOA_ENOMEM and enqueue nothing. Nothing in it needs to start at zero.
+ *   Sharing: all calls on a device use the same array, so calls that overlap on one GPU (other
+ *   streams or host threads) race on it; the caller must serialise them.
+ *   First call per device: looks up the array's device address (cudaGetSymbolAddress, with that
+ *   device current) and sets the kernel's shared-memory limit. Make that first call before any
+ *   stream capture.
+ *   Arguments and other errors: as doa_covariance (no prec argument: always DOA_FP32).
+ */
+#define DOA_NOALLOC_SCRATCH_BYTES (4u << 20)
+doa_status doa_covariance_noalloc(const float *X, int M, int N, int ldx, float *R, double *R64,
+                                  void *stream);
+
+/*
  * Steps 2-4: Hermitian eigendecomposition of R by FP64 cyclic Jacobi (one warp per matrix,
  * parallel round-robin ordering), eigenvalues sorted descending (equal values keep their
  * index order), then the noise-subspace factor B of the weighting matrix, C = B B^H (Table 3):

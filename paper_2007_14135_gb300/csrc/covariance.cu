@@ -312,3 +312,113 @@ cudaError_t launch_covariance_batch(const uint8_t *plan_dev, const PlanHeader &h
 }
 
 }  // namespace doa
+
+// ------------------------------------------------------------------------------------------
+// Covariance that allocates nothing and needs no caller workspace.
+//
+// Some callers cannot allocate device memory when they call in: a fixed-memory real-time loop
+// (cudaMalloc may synchronise the device and take driver locks), a host framework that forbids
+// allocation after start-up, or code without an allocator of its own. This entry point keeps
+// the per-chunk partial sums of the batched covariance in a library-owned, file-scope device
+// array instead of a caller workspace. The paper has no counterpart.
+//
+// Limits and sharing: the array holds kNoallocScratchBytes (DOA_NOALLOC_SCRATCH_BYTES); a
+// problem needs ceil(N / 1024) * M * M * 16 bytes of it and larger ones are rejected with
+// DOA_ENOMEM. Every GPU that loads the library keeps the array until the process exits. All
+// calls on a device share it, so calls that overlap on that GPU (other streams, other host
+// threads) race on its contents; serialise them. Nothing in it has to start at zero: every
+// chunk writes every entry it later reads. The first call on each device looks up the array's
+// device address (cudaGetSymbolAddress, with that device current) and sets the kernel's shared
+// memory limit; make that first call before any stream capture.
+// ------------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace doa {
+namespace {
+
+constexpr size_t kNoallocScratchBytes = DOA_NOALLOC_SCRATCH_BYTES;
+constexpr int kNoallocMaxDevices = 64;
+
+static __device__ __align__(256) double2 g_noalloc_scratch[kNoallocScratchBytes / sizeof(double2)];
+
+std::mutex g_noalloc_mutex;
+double2 *g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+__global__ void __launch_bounds__(kCovThreads) covariance_noalloc_kernel(const float2 *X, int M, int N, int ldx,
+                                                                         double2 *partials, float2 *R, double2 *R64) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  CovLayout lay(M);
+  const int t0 = blockIdx.x * kCovChunk;
+  const int t1 = min(N, t0 + kCovChunk);
+  const float4 *part = cov_accumulate<true>(X, ldx, t0, t1, lay, smem);
+  const double inv_n = 1.0 / (double)N;
+  double2 *mine = partials + (size_t)blockIdx.x * M * M;
+  for (int e = threadIdx.x; e < lay.nout(); e += kCovThreads) {
+    int row, col;
+    if (!slot_rc(lay, e, row, col)) continue;
+    double2 v = slot_value(part[e]);
+    if (gridDim.x == 1)
+      store_r(M, row, col, v, inv_n, R, R64);
+    else
+      mine[row * M + col] = v;
+  }
+}
+
+__global__ void covariance_noalloc_reduce(const double2 *partials, int nchunks, int M, int N, float2 *R,
+                                          double2 *R64) {
+  const double inv_n = 1.0 / (double)N;
+  for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+    int row = e / M, col = e % M;
+    if (row > col) continue;
+    double2 s = make_double2(0.0, 0.0);
+    for (int c = 0; c < nchunks; ++c) {
+      double2 v = partials[(size_t)c * M * M + row * M + col];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    store_r(M, row, col, s, inv_n, R, R64);
+  }
+}
+
+// Device address of the scratch array for the current device (looked up once per device).
+cudaError_t noalloc_scratch(double2 **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    double2 *p = nullptr;
+    e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(covariance_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace doa
+
+extern "C" doa_status doa_covariance_noalloc(const float *X, int M, int N, int ldx, float *R, double *R64,
+                                             void *stream) {
+  using namespace doa;
+  if (!X || M < 2 || M > kMaxM || N < 1 || ldx < N || (!R && !R64)) return DOA_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(X) & 7u) || (reinterpret_cast<uintptr_t>(R) & 7u) ||
+      (reinterpret_cast<uintptr_t>(R64) & 15u))
+    return DOA_EINVAL;
+  const int nchunks = (N + kCovChunk - 1) / kCovChunk;
+  if ((size_t)nchunks * M * M * sizeof(double2) > kNoallocScratchBytes) return DOA_ENOMEM;
+  double2 *scratch = nullptr;
+  if (noalloc_scratch(&scratch) != cudaSuccess) return DOA_ECUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  covariance_noalloc_kernel<<<nchunks, kCovThreads, kSmemBytes, s>>>(
+      reinterpret_cast<const float2 *>(X), M, N, ldx, scratch, reinterpret_cast<float2 *>(R),
+      reinterpret_cast<double2 *>(R64));
+  if (nchunks > 1)
+    covariance_noalloc_reduce<<<1, 256, 0, s>>>(scratch, nchunks, M, N, reinterpret_cast<float2 *>(R),
+                                                reinterpret_cast<double2 *>(R64));
+  return cudaGetLastError() == cudaSuccess ? DOA_OK : DOA_ECUDA;
+}

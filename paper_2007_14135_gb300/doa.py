@@ -19,12 +19,13 @@ LIB_PATH = os.path.join(_HERE, "libdoa.so")
 PHD, MUSIC, EV, MN = 0, 1, 2, 3
 FP32, BF16, BF16X3, FP16X3 = 0, 1, 2, 3
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ERANK, ENONFINITE, ETIMEOUT = range(8)
+NOALLOC_SCRATCH_BYTES = 4 << 20
 BATCH_STAGES = 5
 STAGE_NAMES = ("phase_tables", "covariance", "eig_noise_subspace", "scan", "peaks")
 
 # every symbol include/doa.h declares
-EXPORTS = ("doa_status_str", "doa_covariance", "doa_noise_subspace", "doa_scan", "doa_peaks",
-           "doa_batch_plan_bytes", "doa_batch_plan", "doa_solve_batch")
+EXPORTS = ("doa_status_str", "doa_covariance", "doa_covariance_noalloc", "doa_noise_subspace", "doa_scan",
+           "doa_peaks", "doa_batch_plan_bytes", "doa_batch_plan", "doa_solve_batch")
 
 
 class DoaError(RuntimeError):
@@ -54,6 +55,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.doa_status_str.argtypes = [i]
     lib.doa_status_str.restype = ctypes.c_char_p
     lib.doa_covariance.argtypes = [vp, i, i, i, vp, vp, i, vp]
+    lib.doa_covariance_noalloc.argtypes = [vp, i, i, i, vp, vp, vp]
     lib.doa_noise_subspace.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp]
     lib.doa_scan.argtypes = [vp, i, i, Grid, i, vp, vp]
     lib.doa_peaks.argtypes = [vp, i, i, vp, vp, vp, vp]
@@ -62,7 +64,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.doa_batch_plan.argtypes = [ctypes.POINTER(Problem), i, vp, sz, ctypes.POINTER(sz),
                                    ctypes.POINTER(ctypes.c_int)]
     lib.doa_solve_batch.argtypes = [vp, vp, vp, sz, vp, vp, vp]
-    for name in ("doa_covariance", "doa_noise_subspace", "doa_scan", "doa_peaks",
+    for name in ("doa_covariance", "doa_covariance_noalloc", "doa_noise_subspace", "doa_scan", "doa_peaks",
                  "doa_batch_plan", "doa_solve_batch"):
         getattr(lib, name).restype = i
     return lib
@@ -113,6 +115,17 @@ def doa_covariance(X: torch.Tensor, R: Optional[torch.Tensor] = None, R64: Optio
     M, N = X.shape
     _check(lib().doa_covariance(_dev(X), M, N, X.stride(0), _dev(R), _dev(R64), prec, _stream(stream)),
            "doa_covariance")
+
+
+def doa_covariance_noalloc(X: torch.Tensor, R: Optional[torch.Tensor] = None, R64: Optional[torch.Tensor] = None,
+                           stream=None) -> None:
+    """Same as doa_covariance, but the library allocates nothing and takes no workspace: the
+    chunk sums live in a fixed library-owned device array (DOA_NOALLOC_SCRATCH_BYTES), for
+    callers that cannot allocate while running. Calls that overlap on one GPU race on it."""
+    assert X.dtype == torch.complex64 and X.dim() == 2 and X.stride(1) == 1
+    M, N = X.shape
+    _check(lib().doa_covariance_noalloc(_dev(X), M, N, X.stride(0), _dev(R), _dev(R64), _stream(stream)),
+           "doa_covariance_noalloc")
 
 
 def doa_noise_subspace(R64: torch.Tensor, d: int, alg: int, B: torch.Tensor, info: torch.Tensor,
