@@ -166,10 +166,15 @@ size_t doa_batch_plan_bytes(const doa_problem *probs, int nprob) {
   return (size_t)plan_offsets(sz).total;
 }
 
-doa_status doa_batch_plan(const doa_problem *probs, int nprob, void *plan, size_t plan_bytes, size_t *ws_bytes,
-                          int *bad_index) {
+doa_status doa_batch_plan(const doa_problem *probs, int nprob, const int32_t *scan_pt, void *plan, size_t plan_bytes,
+                          size_t *ws_bytes, int *bad_index) {
   if (bad_index) *bad_index = -1;
   if (!probs || nprob < 1 || !ws_bytes) return DOA_EINVAL;
+  int pt[kNumBuckets];
+  for (int b = 0; b < kNumBuckets; ++b) {
+    pt[b] = (scan_pt && scan_pt[b] != 0) ? scan_pt[b] : scan_pt_default(b);
+    if (!scan_pt_allowed(b, pt[b])) return DOA_EINVAL;
+  }
   PlanSizes sz;
   std::vector<doa_grid> grids;
   std::vector<int> grid_of;
@@ -190,6 +195,7 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, void *plan, size_
     scan[b] = reinterpret_cast<int32_t *>(base + o.scan[b]);
   }
   h.magic = kPlanMagic;
+  for (int b = 0; b < kNumBuckets; ++b) h.scan_pt[b] = pt[b];
   h.nprob = sz.nprob;
   h.njobs = sz.njobs;
   h.ngrids = sz.ngrids;
@@ -236,7 +242,7 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, void *plan, size_
     q.grid_id = grid_of[i];
     q.first_job = ijob;
     int slot = 0;
-    const int tp = scan_tile_points(b);
+    const int tp = kScanThreads * pt[b];
     for (int a = 0; a < 4; ++a) {
       if (!((p.alg_mask >> a) & 1u)) continue;
       PlanJob &j = jobs[ijob];

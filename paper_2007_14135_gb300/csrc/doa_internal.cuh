@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "doa.h"
@@ -115,6 +116,7 @@ struct PlanHeader {
   int32_t eig_count[kNumBuckets];        // problems per M bucket
   int32_t scan_jobs[kNumBuckets];        // jobs per M bucket
   int64_t scan_tiles[kNumBuckets];       // scan tiles per M bucket
+  int32_t scan_pt[kNumBuckets];          // grid points per scan thread, per M bucket
   int64_t grid_points;                   // sum of L over distinct grids
   int64_t ws_bytes;
   // byte offsets of the arrays inside the plan
@@ -122,10 +124,18 @@ struct PlanHeader {
       off_scan[kNumBuckets], off_grid_pts;
 };
 
-// Scan tiles: kScanThreads threads, each evaluating scan_pt(bucket) consecutive grid points.
+// The Python binding reads these header fields by position (int32 index 22 = scan_pt).
+static_assert(offsetof(PlanHeader, scan_pt) == 88, "PlanHeader layout changed");
+static_assert(offsetof(PlanHeader, scan_tiles) == 56, "PlanHeader layout changed");
+
+// Scan tiles: kScanThreads threads, each evaluating PT consecutive grid points (tile shape
+// 128 x PT). PT is chosen per M bucket (the autotuner's knob); the register budget limits it
+// to {1,2,4} for M <= 16, {1,2} for M <= 32 and 1 for M <= 64.
 constexpr int kScanThreads = 128;
-__host__ __device__ constexpr int scan_pt(int bucket) { return bucket == 0 ? 4 : (bucket == 1 ? 2 : 1); }
-__host__ __device__ constexpr int scan_tile_points(int bucket) { return kScanThreads * scan_pt(bucket); }
+__host__ __device__ constexpr int scan_pt_default(int bucket) { return bucket == 0 ? 4 : (bucket == 1 ? 2 : 1); }
+__host__ __device__ inline bool scan_pt_allowed(int bucket, int pt) {
+  return pt == 1 || (pt == 2 && bucket <= 2) || (pt == 4 && bucket <= 1);
+}
 
 __host__ __device__ inline int m_bucket(int M) { return M <= 8 ? 0 : (M <= 16 ? 1 : (M <= 32 ? 2 : 3)); }
 

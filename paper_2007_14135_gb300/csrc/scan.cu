@@ -313,7 +313,7 @@ cudaError_t launch_grid_tables(const uint8_t *plan_dev, const PlanHeader &h, uin
 cudaError_t launch_scan_single(const double2 *B, int M, int K, int L, double lo, double step, const uint32_t *S,
                                float *P, cudaStream_t s) {
   const int b = m_bucket(M);
-  const int tp = scan_tile_points(b);
+  const int tp = kScanThreads * scan_pt_default(b);
   const unsigned grid = (unsigned)((L + tp - 1) / tp);
   switch (b) {
     case 0: scan_single_kernel<8, 4><<<grid, kScanThreads, 0, s>>>(B, M, K, L, lo, step, S, P); break;
@@ -326,9 +326,23 @@ cudaError_t launch_scan_single(const double2 *B, int M, int K, int L, double lo,
 
 cudaError_t launch_scan_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s) {
   cudaError_t e;
-  if ((e = run_batch<8, 4>(plan_dev, h, ws, 0, s)) != cudaSuccess) return e;
-  if ((e = run_batch<16, 2>(plan_dev, h, ws, 1, s)) != cudaSuccess) return e;
-  if ((e = run_batch<32, 1>(plan_dev, h, ws, 2, s)) != cudaSuccess) return e;
+  switch (h.scan_pt[0]) {
+    case 1: e = run_batch<8, 1>(plan_dev, h, ws, 0, s); break;
+    case 2: e = run_batch<8, 2>(plan_dev, h, ws, 0, s); break;
+    default: e = run_batch<8, 4>(plan_dev, h, ws, 0, s); break;
+  }
+  if (e != cudaSuccess) return e;
+  switch (h.scan_pt[1]) {
+    case 1: e = run_batch<16, 1>(plan_dev, h, ws, 1, s); break;
+    case 4: e = run_batch<16, 4>(plan_dev, h, ws, 1, s); break;
+    default: e = run_batch<16, 2>(plan_dev, h, ws, 1, s); break;
+  }
+  if (e != cudaSuccess) return e;
+  if (h.scan_pt[2] == 2)
+    e = run_batch<32, 2>(plan_dev, h, ws, 2, s);
+  else
+    e = run_batch<32, 1>(plan_dev, h, ws, 2, s);
+  if (e != cudaSuccess) return e;
   return run_batch<64, 1>(plan_dev, h, ws, 3, s);
 }
 

@@ -61,7 +61,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.doa_peaks.argtypes = [vp, i, i, vp, vp, vp, vp]
     lib.doa_batch_plan_bytes.argtypes = [ctypes.POINTER(Problem), i]
     lib.doa_batch_plan_bytes.restype = sz
-    lib.doa_batch_plan.argtypes = [ctypes.POINTER(Problem), i, vp, sz, ctypes.POINTER(sz),
+    lib.doa_batch_plan.argtypes = [ctypes.POINTER(Problem), i, vp, vp, sz, ctypes.POINTER(sz),
                                    ctypes.POINTER(ctypes.c_int)]
     lib.doa_solve_batch.argtypes = [vp, vp, vp, sz, vp, vp, vp]
     for name in ("doa_covariance", "doa_covariance_noalloc", "doa_noise_subspace", "doa_scan", "doa_peaks",
@@ -162,25 +162,42 @@ def make_problem(X: torch.Tensor, d: int, alg_mask: int, g: Grid, P: torch.Tenso
 
 
 class BatchPlan:
-    """Host plan bytes, their device copy, and the workspace size (doa_batch_plan)."""
+    """Host plan bytes, their device copy, and the workspace size (doa_batch_plan).
 
-    def __init__(self, problems: Sequence[Problem], device: str = "cuda"):
+    scan_pt: None or 4 ints (grid points per scan thread for M <= 8, 16, 32, 64; 0 = default)."""
+
+    def __init__(self, problems: Sequence[Problem], device: str = "cuda", scan_pt: Optional[Sequence[int]] = None):
         arr = (Problem * len(problems))(*problems)
+        pt = None if scan_pt is None else (ctypes.c_int32 * 4)(*[int(v) for v in scan_pt])
+        pt_ptr = None if pt is None else ctypes.cast(pt, ctypes.c_void_p)
         n = lib().doa_batch_plan_bytes(arr, len(problems))
-        if n == 0:
-            bad = ctypes.c_int(-1)
-            ws = ctypes.c_size_t(0)
-            st = lib().doa_batch_plan(arr, len(problems), None, 0, ctypes.byref(ws), ctypes.byref(bad))
-            raise DoaError(st if st else EINVAL, f"doa_batch_plan (problem {bad.value})")
-        self.host = np.zeros(n, dtype=np.uint8)
         ws = ctypes.c_size_t(0)
         bad = ctypes.c_int(-1)
-        _check(lib().doa_batch_plan(arr, len(problems), self.host.ctypes.data, n, ctypes.byref(ws),
+        if n == 0:
+            st = lib().doa_batch_plan(arr, len(problems), pt_ptr, None, 0, ctypes.byref(ws), ctypes.byref(bad))
+            raise DoaError(st if st else EINVAL, f"doa_batch_plan (problem {bad.value})")
+        self.host = np.zeros(n, dtype=np.uint8)
+        _check(lib().doa_batch_plan(arr, len(problems), pt_ptr, self.host.ctypes.data, n, ctypes.byref(ws),
                                     ctypes.byref(bad)), f"doa_batch_plan (problem {bad.value})")
         self.ws_bytes = int(ws.value)
         self.nprob = len(problems)
+        self.scan_pt = [int(v) for v in self.host[:256].view(np.int32)[self.header_index("scan_pt"):][:4]]
         self.dev = torch.from_numpy(self.host).to(device)
         self.problems = arr
+
+    @staticmethod
+    def header_index(field: str) -> int:
+        """int32 index of a PlanHeader field (layout of csrc/doa_internal.cuh)."""
+        order = {"magic": 0, "nprob": 1, "njobs": 2, "ngrids": 3, "ncov": 4, "nreduce": 5, "eig_count": 6,
+                 "scan_jobs": 10, "scan_tiles": 14, "scan_pt": 22}
+        return order[field]
+
+    def launches(self) -> int:
+        """Kernels one doa_solve_batch of this plan launches."""
+        h = self.host[:256].view(np.int32)
+        eig_b = sum(int(c) > 0 for c in h[6:10])
+        scan_b = sum(int(c) > 0 for c in h[10:14])
+        return 1 + 1 + int(h[5] > 0) + eig_b + scan_b + 1
 
 
 def doa_solve_batch(plan: BatchPlan, ws: torch.Tensor, status: torch.Tensor, stage_events=None,

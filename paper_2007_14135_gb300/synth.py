@@ -244,3 +244,52 @@ def paper_density_batch_parallel(count: int, base_seed: int = 20071414, N: int =
         for ang, snr, seed in part:
             meta.append(Instance(None, M, 4, N, ang, snr, GRID_LO, step, grid_size(step), seed))
     return X, meta
+
+
+def _fill_uneven(args):
+    shm_name, total, specs, offsets = args
+    from multiprocessing import shared_memory
+    shm = shared_memory.SharedMemory(name=shm_name)
+    try:
+        buf = np.ndarray((total,), dtype=np.complex64, buffer=shm.buf)
+        for spec, off in zip(specs, offsets):
+            X = snapshots(_rng(spec.seed), spec.M, spec.N, spec.angles, spec.snr_db)
+            buf[off:off + spec.M * spec.N] = X.reshape(-1)
+        return len(specs)
+    finally:
+        shm.close()
+
+
+def uneven_batch_parallel(specs: Sequence[ProblemSpec], workers: Optional[int] = None):
+    """Snapshots of every spec in one flat complex64 buffer (problem i at offsets[i], shape
+    (M_i, N_i) row-major), generated by spawned workers. Same bytes as uneven_instance(spec).X."""
+    import multiprocessing as mp
+    import os
+    from multiprocessing import shared_memory
+    sizes = np.array([s.M * s.N for s in specs], dtype=np.int64)
+    offsets = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    # keep every problem 8-complex (64-byte) aligned
+    offsets = np.zeros(len(specs), dtype=np.int64)
+    at = 0
+    for i, sz in enumerate(sizes):
+        offsets[i] = at
+        at += int((sz + 7) // 8 * 8)
+    total = max(at, 8)
+    workers = workers or min(16, os.cpu_count() or 1)
+    if workers <= 1 or len(specs) < 64:
+        buf = np.zeros(total, dtype=np.complex64)
+        for spec, off in zip(specs, offsets):
+            buf[off:off + spec.M * spec.N] = uneven_instance(spec).X.reshape(-1)
+        return buf, offsets
+    shm = shared_memory.SharedMemory(create=True, size=total * 8)
+    try:
+        order = np.argsort(-sizes)          # deal large problems round-robin for balance
+        parts = [order[w::workers] for w in range(workers)]
+        tasks = [(shm.name, total, [specs[i] for i in part], [int(offsets[i]) for i in part]) for part in parts]
+        with mp.get_context("spawn").Pool(workers) as pool:
+            pool.map(_fill_uneven, tasks)
+        buf = np.ndarray((total,), dtype=np.complex64, buffer=shm.buf).copy()
+    finally:
+        shm.close()
+        shm.unlink()
+    return buf, offsets

@@ -79,7 +79,7 @@ def test_batch_plan_layout(libdoa):
     buf = np.zeros(n, np.uint8)
     ws = ctypes.c_size_t(0)
     bad = ctypes.c_int(7)
-    assert libdoa.lib().doa_batch_plan(arr, 3, buf.ctypes.data, n, ctypes.byref(ws), ctypes.byref(bad)) == 0
+    assert libdoa.lib().doa_batch_plan(arr, 3, None, buf.ctypes.data, n, ctypes.byref(ws), ctypes.byref(bad)) == 0
     assert bad.value == -1
     hdr = buf[:64].view(np.int32)
     assert hdr[0] == 0x444F4131            # magic
@@ -88,7 +88,7 @@ def test_batch_plan_layout(libdoa):
     need = 18001 * 4 + 1801 * 4 + (16 * 16 * 16) * (1 + 4 + 4) + (8 * 8 * 16) * (1 + 1) + (33 * 33 * 16) * (1 + 3 + 2)
     assert ws.value >= need and ws.value < need + 256 * 40
     # too small a buffer
-    assert libdoa.lib().doa_batch_plan(arr, 3, buf.ctypes.data, n - 1, ctypes.byref(ws), None) == libdoa.ENOMEM
+    assert libdoa.lib().doa_batch_plan(arr, 3, None, buf.ctypes.data, n - 1, ctypes.byref(ws), None) == libdoa.ENOMEM
 
 
 @pytest.mark.parametrize("field,value", [("M", 1), ("M", 65), ("d", 16), ("d", -1), ("N", 0), ("ldx", 100),
@@ -101,7 +101,7 @@ def test_batch_plan_rejects(libdoa, field, value):
     buf = np.zeros(1 << 16, np.uint8)
     ws = ctypes.c_size_t(0)
     bad = ctypes.c_int(-5)
-    st = libdoa.lib().doa_batch_plan(arr, 2, buf.ctypes.data, buf.size, ctypes.byref(ws), ctypes.byref(bad))
+    st = libdoa.lib().doa_batch_plan(arr, 2, None, buf.ctypes.data, buf.size, ctypes.byref(ws), ctypes.byref(bad))
     assert st == libdoa.EINVAL and bad.value == 1
 
 
@@ -110,3 +110,24 @@ def test_solve_batch_rejects_bad_plan(libdoa):
     junk = np.zeros(256, np.uint8)
     fake = ctypes.c_void_p(0x10000)
     assert libdoa.lib().doa_solve_batch(junk.ctypes.data, fake, fake, 1 << 20, fake, None, None) == libdoa.EINVAL
+
+
+def test_batch_plan_scan_pt(libdoa):
+    import numpy as np
+    probs = [_prob(libdoa, M=8, N=1000, d=2, mask=0b0010, L=1801, step=0.1), _prob(libdoa, M=33, N=3000, d=5)]
+    arr = (libdoa.Problem * 2)(*probs)
+    n = libdoa.lib().doa_batch_plan_bytes(arr, 2)
+    ws = ctypes.c_size_t(0)
+    for pts, ok in [((1, 1, 1, 1), True), ((4, 4, 2, 1), True), ((2, 0, 0, 0), True), ((8, 0, 0, 0), False),
+                    ((0, 0, 4, 0), False), ((0, 0, 0, 2), False)]:
+        buf = np.zeros(n, np.uint8)
+        arrp = (ctypes.c_int32 * 4)(*pts)
+        st = libdoa.lib().doa_batch_plan(arr, 2, ctypes.cast(arrp, ctypes.c_void_p), buf.ctypes.data, n,
+                                         ctypes.byref(ws), None)
+        assert (st == 0) == ok, pts
+        if ok:
+            got = buf[:128].view(np.int32)[22:26]
+            want = [p if p else d for p, d in zip(pts, (4, 2, 1, 1))]
+            assert list(got) == want
+            tiles = buf[:128].view(np.int64)[7:11]      # scan_tiles per bucket
+            assert tiles[0] == -(-1801 // (128 * want[0])) and tiles[3] == 4 * -(-18001 // 128)

@@ -1,0 +1,102 @@
+"""Batched solve: tile shapes, CUDA-graph replay and the autotuner (GPU, through the C ABI)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2007_14135_gb300 import synth
+from tests.gpu_common import DB_TOL, compare_peaks, db_error, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    return require_gpu()
+
+
+def _uneven(torch, doa, n=48, thin=True):
+    specs = [s for s in synth.uneven_specs(4096) if not thin or s.step >= 0.01][:n]
+    insts = [synth.uneven_instance(s) for s in specs]
+    tensors, probs = [], []
+    for inst in insts:
+        X = torch.from_numpy(inst.X).cuda()
+        P = torch.empty(inst.L, dtype=torch.float32, device="cuda")
+        idx = torch.full((inst.d,), -1, dtype=torch.int32, device="cuda")
+        val = torch.zeros(inst.d, dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        tensors.append((X, P, idx, val, cnt))
+        probs.append(doa.make_problem(X, inst.d, 1 << inst.alg, doa.grid(inst.lo, inst.step, inst.L), P, idx, val, cnt))
+    return insts, tensors, probs
+
+
+def test_tile_shapes_give_identical_spectra(env):
+    """The points-per-thread knob changes the tiling only: every point is bit-identical."""
+    torch, doa = env
+    insts, tensors, probs = _uneven(torch, doa, n=40)
+    outs = []
+    for pts in [(1, 1, 1, 1), (4, 2, 1, 1), (2, 4, 2, 1)]:
+        plan = doa.BatchPlan(probs, scan_pt=pts)
+        ws = doa.workspace(plan)
+        status = torch.full((plan.nprob,), -1, dtype=torch.int32, device="cuda")
+        doa.doa_solve_batch(plan, ws, status)
+        torch.cuda.synchronize()
+        assert np.all(status.cpu().numpy() == 0)
+        outs.append([t[1].cpu().numpy().copy() for t in tensors])
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+    for a, b in zip(outs[0], outs[2]):
+        assert np.array_equal(a, b)
+
+
+def test_graph_replay_matches_direct_call_and_oracle(env):
+    torch, doa = env
+    insts, tensors, probs = _uneven(torch, doa, n=32)
+    plan = doa.BatchPlan(probs)
+    ws = doa.workspace(plan)
+    status = torch.full((plan.nprob,), -1, dtype=torch.int32, device="cuda")
+    doa.doa_solve_batch(plan, ws, status)
+    torch.cuda.synchronize()
+    direct = [t[1].cpu().numpy().copy() for t in tensors]
+    for t in tensors:
+        t[1].fill_(float("nan"))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        doa.doa_solve_batch(plan, ws, status, stream=s)     # warm-up off the capture
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        doa.doa_solve_batch(plan, ws, status)
+    for t in tensors:
+        t[1].fill_(float("nan"))
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for a, t in zip(direct, tensors):
+        assert np.array_equal(a, t[1].cpu().numpy())
+    for inst, t in zip(insts[:12], tensors[:12]):
+        ref = oracle.solve(inst.X, inst.d, inst.alg, inst.lo, inst.step, inst.L)
+        assert db_error(t[1].cpu().numpy(), ref["P"]) < DB_TOL
+        n = t[4].item()
+        ok, ties = compare_peaks(t[2].cpu().numpy()[:n], ref["idx"], ref["P"], 1e-4)
+        assert ok, ties
+
+
+def test_autotuner_picks_allowed_tiles_and_persists(env, tmp_path):
+    torch, doa = env
+    from paper_2007_14135_gb300 import autotune
+    insts, tensors, probs = _uneven(torch, doa, n=24)
+    path = str(tmp_path / "tune.json")
+    log = []
+    pts = autotune.tune(probs, path=path, log=log, reps=1)
+    assert len(pts) == 4
+    for b, p in enumerate(pts):
+        assert p in autotune.CANDIDATES[b]
+    table = json.load(open(path))
+    assert len(table) == len(log) >= 1
+    for entry in log:
+        assert set(entry["ms"]) == set(autotune.CANDIDATES[entry["bucket"]])
+    assert autotune.tune(probs, path=path) == pts          # second call: from the table, no timing
