@@ -1,16 +1,20 @@
 // Steps 2-4 (Table 2 Step-2, Table 3): Hermitian eigendecomposition of R by FP64 cyclic Jacobi,
-// one warp per matrix, followed by the noise-subspace factor B of each algorithm's weighting
-// matrix C = B B^H.
+// followed by the noise-subspace factor B of each algorithm's weighting matrix C = B B^H.
 //
 // Jacobi (Golub & Van Loan, Sec. 8.5, with a phase factor for complex Hermitian matrices):
 // for a pair (p, q) with a_pq = |a_pq| e^{j phi}, tau = (a_qq - a_pp) / (2 |a_pq|),
-// t = sgn(tau) / (|tau| + hypot(1, tau)), c = 1/sqrt(1 + t^2), s = t c, sigma = s e^{j phi};
+// t = sgn(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c, sigma = s e^{j phi};
 // J = [[c, sigma], [-conj(sigma), c]] on coordinates (p, q) zeroes (J^H A J)_pq.
-// The warp applies n/2 disjoint rotations at once (round-robin "circle" ordering over
-// n = M rounded up to even; pairs that touch the padding index are skipped): first the row
-// update A <- J^H A for all rotated pairs, then the column updates A <- A J and V <- V J.
-// A pair is rotated when |a_pq| > tol sqrt(|a_pp a_qq|); the matrix has converged after the
-// first sweep that rotates nothing. A and V live in shared memory with a padded row stride
+// Each rotation's parameters use reciprocal square roots and one reciprocal (no divisions,
+// hypot or sqrt), so c^2 + |sigma|^2 = 1 holds to FP64 rounding.
+//
+// Parallel ordering: n/2 disjoint rotations per round (round-robin "circle" ordering over
+// n = M rounded up to even; pairs that touch the padding index are skipped): the row update
+// A <- J^H A for all rotated pairs, then the column updates A <- A J and V <- V J. A pair is
+// rotated when |a_pq|^2 > tol^2 |a_pp a_qq|; a matrix has converged after a sweep that rotates
+// nothing. A warp holds 32 / (NP/2) matrices so that every lane owns one pair's rotation
+// (8 matrices of M <= 8, 4 of M <= 16, 2 of M <= 32, 1 of M <= 64); the element updates of each
+// matrix are spread over all 32 lanes. A and V live in shared memory with a padded row stride
 // (NP + 1 complex128) so that column accesses by consecutive lanes hit distinct banks.
 #include "doa_internal.cuh"
 
@@ -32,96 +36,145 @@ struct EigSmem {
 };
 
 template <int NP>
-constexpr int eig_warps() { return NP <= 8 ? 8 : (NP <= 16 ? 4 : (NP <= 32 ? 2 : 1)); }
+__host__ __device__ constexpr int mats_per_warp() { return 64 / NP; }
+template <int NP>
+__host__ __device__ constexpr int eig_warps() { return NP <= 8 ? 4 : (NP <= 16 ? 2 : 1); }
 
 __device__ __forceinline__ int rr_player(int pos, int r, int n) {
   return pos == 0 ? 0 : ((pos - 1 + r) % (n - 1)) + 1;
 }
 
-// Loads R (upper triangle) into A, runs Jacobi. Returns sweeps (> 0) or -status.
+// Rotation of pair (p, q) of A; returns false if the pair is below threshold.
 template <int NP>
-__device__ int jacobi_warp(const double2 *__restrict__ R, int M, EigSmem<NP> &s) {
-  const int lane = threadIdx.x & 31;
-  bool finite = true;
-  for (int e = lane; e < M * M; e += 32) {
-    int i = e / M, j = e % M;
-    double2 v;
-    if (i <= j) {
-      v = R[i * M + j];
-    } else {
-      v = R[j * M + i];
-      v.y = -v.y;
-    }
-    if (i == j) v.y = 0.0;
-    finite = finite && isfinite(v.x) && isfinite(v.y);
-    s.A[i][j] = v;
-    s.V[i][j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+__device__ __forceinline__ bool rotation(EigSmem<NP> &s, int p, int q, Rot &ro) {
+  const double app = s.A[p][p].x, aqq = s.A[q][q].x;
+  const double2 apq = s.A[p][q];
+  const double n2 = apq.x * apq.x + apq.y * apq.y;
+  if (!(n2 > 0.0) || !(n2 > kJacobiTol * kJacobiTol * fabs(app * aqq))) return false;
+  const double r = rsqrt(n2);                         // 1 / |a_pq|
+  const double tau = (aqq - app) * (0.5 * r);
+  double t;
+  if (fabs(tau) > 1e18) {
+    t = 0.5 * __drcp_rn(tau);                         // t = 1/(2 tau) to within tau^-2
+  } else {
+    const double u = fma(tau, tau, 1.0);
+    const double h = u * rsqrt(u);                    // sqrt(1 + tau^2)
+    t = copysign(__drcp_rn(fabs(tau) + h), tau);
   }
-  finite = __all_sync(0xffffffffu, finite);
-  __syncwarp();
-  if (!finite) return -DOA_ENONFINITE;
+  const double c = rsqrt(fma(t, t, 1.0));
+  const double sn = t * c * r;
+  ro = Rot{c, sn * apq.x, sn * apq.y};
+  return true;
+}
 
-  const int n = (M + 1) & ~1;
-  const int npairs = n / 2;
-  for (int sweep = 1; sweep <= kMaxSweeps; ++sweep) {
-    bool any = false;
-    for (int r = 0; r < n - 1; ++r) {
+// Runs Jacobi on the G matrices of a warp (matrix j has size Ms[j] <= NP, 0 = unused), all
+// loaded from Rs[j] (upper triangle). res[j] receives sweeps (> 0) or -status.
+template <int NP, int G>
+__device__ void jacobi_group(EigSmem<NP> *mats, const int *Ms, const double2 *const *Rs, int *res) {
+  constexpr int HP = NP / 2;
+  const int lane = threadIdx.x & 31;
+  unsigned live = 0u;  // matrices still iterating
+  for (int j = 0; j < G; ++j) {
+    const int M = Ms[j];
+    res[j] = 0;
+    if (M <= 0) continue;
+    EigSmem<NP> &s = mats[j];
+    const double2 *R = Rs[j];
+    bool finite = true;
+    for (int e = lane; e < M * M; e += 32) {
+      int i = e / M, k = e % M;
+      double2 v;
+      if (i <= k) {
+        v = R[i * M + k];
+      } else {
+        v = R[k * M + i];
+        v.y = -v.y;
+      }
+      if (i == k) v.y = 0.0;
+      finite = finite && isfinite(v.x) && isfinite(v.y);
+      s.A[i][k] = v;
+      s.V[i][k] = make_double2(i == k ? 1.0 : 0.0, 0.0);
+    }
+    if (__all_sync(0xffffffffu, finite))
+      live |= 1u << j;
+    else
+      res[j] = -DOA_ENONFINITE;
+  }
+  __syncwarp();
+  int maxn = 0;
+  for (int j = 0; j < G; ++j)
+    if ((live >> j) & 1u) maxn = max(maxn, (Ms[j] + 1) & ~1);
+  // lane -> (matrix, pair) for the rotation parameters
+  const int lj = lane / HP, li = lane % HP;
+  for (int sweep = 1; sweep <= kMaxSweeps && live; ++sweep) {
+    unsigned rotated = 0u;
+    for (int r = 0; r < maxn - 1; ++r) {
       bool act = false;
-      if (lane < npairs) {
-        int a = rr_player(lane, r, n), b = rr_player(n - 1 - lane, r, n);
-        int p = min(a, b), q = max(a, b);
-        if (q < M) {
-          double app = s.A[p][p].x, aqq = s.A[q][q].x;
-          double2 apq = s.A[p][q];
-          double mag = hypot(apq.x, apq.y);
-          if (mag > 0.0 && mag > kJacobiTol * sqrt(fabs(app * aqq))) {
-            act = true;
-            double tau = (aqq - app) / (2.0 * mag);
-            double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
-            double c = 1.0 / sqrt(1.0 + t * t);
-            double sn = t * c;
-            s.rot[lane] = Rot{c, sn * (apq.x / mag), sn * (apq.y / mag)};
-            s.pq[lane] = make_int2(p, q);
+      if (lj < G && ((live >> lj) & 1u)) {
+        const int M = Ms[lj], n = (M + 1) & ~1;
+        if (r < n - 1 && li < n / 2) {
+          const int a = rr_player(li, r, n), b = rr_player(n - 1 - li, r, n);
+          const int p = min(a, b), q = max(a, b);
+          if (q < M) {
+            Rot ro;
+            if (rotation<NP>(mats[lj], p, q, ro)) {
+              act = true;
+              mats[lj].rot[li] = ro;
+              mats[lj].pq[li] = make_int2(p, q);
+            }
           }
         }
       }
       const unsigned mask = __ballot_sync(0xffffffffu, act);
       if (mask == 0u) continue;
-      any = true;
       __syncwarp();
       // rows: A <- J^H A. new row p = c x_p - sigma x_q; new row q = conj(sigma) x_p + c x_q
-      for (int it = lane; it < npairs * M; it += 32) {
-        int i = it / M, k = it % M;
-        if (!((mask >> i) & 1u)) continue;
-        const Rot ro = s.rot[i];
-        int2 pq = s.pq[i];
-        double2 xp = s.A[pq.x][k], xq = s.A[pq.y][k];
-        s.A[pq.x][k] = make_double2(ro.c * xp.x - (ro.sr * xq.x - ro.si * xq.y),
-                                    ro.c * xp.y - (ro.sr * xq.y + ro.si * xq.x));
-        s.A[pq.y][k] = make_double2(ro.c * xq.x + (ro.sr * xp.x + ro.si * xp.y),
-                                    ro.c * xq.y + (ro.sr * xp.y - ro.si * xp.x));
+      for (int j = 0; j < G; ++j) {
+        const unsigned seg = (mask >> (j * HP)) & ((HP == 32) ? 0xffffffffu : ((1u << HP) - 1u));
+        if (!seg) continue;
+        rotated |= 1u << j;
+        EigSmem<NP> &s = mats[j];
+        const int M = Ms[j];
+        for (int it = lane; it < HP * M; it += 32) {
+          const int i = it / M, k = it % M;
+          if (!((seg >> i) & 1u)) continue;
+          const Rot ro = s.rot[i];
+          const int2 pq = s.pq[i];
+          const double2 xp = s.A[pq.x][k], xq = s.A[pq.y][k];
+          s.A[pq.x][k] = make_double2(ro.c * xp.x - (ro.sr * xq.x - ro.si * xq.y),
+                                      ro.c * xp.y - (ro.sr * xq.y + ro.si * xq.x));
+          s.A[pq.y][k] = make_double2(ro.c * xq.x + (ro.sr * xp.x + ro.si * xp.y),
+                                      ro.c * xq.y + (ro.sr * xp.y - ro.si * xp.x));
+        }
       }
       __syncwarp();
       // columns: A <- A J, V <- V J. new col p = c x_p - conj(sigma) x_q; new col q = sigma x_p + c x_q
-      for (int it = lane; it < npairs * M; it += 32) {
-        int i = it / M, k = it % M;
-        if (!((mask >> i) & 1u)) continue;
-        const Rot ro = s.rot[i];
-        int2 pq = s.pq[i];
-        double2 xp = s.A[k][pq.x], xq = s.A[k][pq.y];
-        s.A[k][pq.x] = make_double2(ro.c * xp.x - (ro.sr * xq.x + ro.si * xq.y),
-                                    ro.c * xp.y - (ro.sr * xq.y - ro.si * xq.x));
-        s.A[k][pq.y] = make_double2(ro.c * xq.x + (ro.sr * xp.x - ro.si * xp.y),
-                                    ro.c * xq.y + (ro.sr * xp.y + ro.si * xp.x));
-        double2 vp = s.V[k][pq.x], vq = s.V[k][pq.y];
-        s.V[k][pq.x] = make_double2(ro.c * vp.x - (ro.sr * vq.x + ro.si * vq.y),
-                                    ro.c * vp.y - (ro.sr * vq.y - ro.si * vq.x));
-        s.V[k][pq.y] = make_double2(ro.c * vq.x + (ro.sr * vp.x - ro.si * vp.y),
-                                    ro.c * vq.y + (ro.sr * vp.y + ro.si * vp.x));
+      for (int j = 0; j < G; ++j) {
+        const unsigned seg = (mask >> (j * HP)) & ((HP == 32) ? 0xffffffffu : ((1u << HP) - 1u));
+        if (!seg) continue;
+        EigSmem<NP> &s = mats[j];
+        const int M = Ms[j];
+        for (int it = lane; it < HP * M; it += 32) {
+          const int i = it / M, k = it % M;
+          if (!((seg >> i) & 1u)) continue;
+          const Rot ro = s.rot[i];
+          const int2 pq = s.pq[i];
+          const double2 xp = s.A[k][pq.x], xq = s.A[k][pq.y];
+          s.A[k][pq.x] = make_double2(ro.c * xp.x - (ro.sr * xq.x + ro.si * xq.y),
+                                      ro.c * xp.y - (ro.sr * xq.y - ro.si * xq.x));
+          s.A[k][pq.y] = make_double2(ro.c * xq.x + (ro.sr * xp.x - ro.si * xp.y),
+                                      ro.c * xq.y + (ro.sr * xp.y + ro.si * xp.x));
+          const double2 vp = s.V[k][pq.x], vq = s.V[k][pq.y];
+          s.V[k][pq.x] = make_double2(ro.c * vp.x - (ro.sr * vq.x + ro.si * vq.y),
+                                      ro.c * vp.y - (ro.sr * vq.y - ro.si * vq.x));
+          s.V[k][pq.y] = make_double2(ro.c * vq.x + (ro.sr * vp.x - ro.si * vp.y),
+                                      ro.c * vq.y + (ro.sr * vp.y + ro.si * vp.x));
+        }
       }
       __syncwarp();
-      if (lane < npairs && ((mask >> lane) & 1u)) {
-        int2 pq = s.pq[lane];
+      if (act) {
+        EigSmem<NP> &s = mats[lj];
+        const int2 pq = s.pq[li];
         s.A[pq.x][pq.y] = make_double2(0.0, 0.0);
         s.A[pq.y][pq.x] = make_double2(0.0, 0.0);
         s.A[pq.x][pq.x].y = 0.0;
@@ -129,9 +182,15 @@ __device__ int jacobi_warp(const double2 *__restrict__ R, int M, EigSmem<NP> &s)
       }
       __syncwarp();
     }
-    if (!any) return sweep;
+    // matrices without a rotation in this sweep have converged
+    for (int j = 0; j < G; ++j)
+      if (((live >> j) & 1u) && !((rotated >> j) & 1u)) {
+        res[j] = sweep;
+        live &= ~(1u << j);
+      }
   }
-  return -DOA_ENOCONV;
+  for (int j = 0; j < G; ++j)
+    if ((live >> j) & 1u) res[j] = -DOA_ENOCONV;
 }
 
 // Stable descending order of the eigenvalues (equal values keep index order).
@@ -210,24 +269,32 @@ __device__ int build_factor(int M, int d, int alg, EigSmem<NP> &s, double2 *__re
 }
 
 template <int NP>
-__global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_single_kernel(const double2 *R64, int M, int d, int alg,
-                                                                          double *evals, double2 *B, int *K_out,
-                                                                          int *info) {
+__global__ void __launch_bounds__(32) eig_single_kernel(const double2 *R64, int M, int d, int alg, double *evals,
+                                                       double2 *B, int *K_out, int *info) {
   extern __shared__ __align__(16) uint8_t smem[];
-  EigSmem<NP> &s = *reinterpret_cast<EigSmem<NP> *>(smem);
+  constexpr int G = mats_per_warp<NP>();
+  EigSmem<NP> *mats = reinterpret_cast<EigSmem<NP> *>(smem);
   const int lane = threadIdx.x & 31;
-  int res = jacobi_warp<NP>(R64, M, s);
+  int Ms[G];
+  const double2 *Rs[G];
+  int res[G];
+  for (int j = 0; j < G; ++j) {
+    Ms[j] = j == 0 ? M : 0;
+    Rs[j] = R64;
+  }
+  jacobi_group<NP, G>(mats, Ms, Rs, res);
+  EigSmem<NP> &s = mats[0];
   int st = 0;
-  if (res > 0) {
+  if (res[0] > 0) {
     sort_desc<NP>(M, s);
     if (evals)
       for (int i = lane; i < M; i += 32) evals[i] = s.lam[s.order[i]];
     st = build_factor<NP>(M, d, alg, s, B);
   } else {
-    st = -res;
+    st = -res[0];
   }
   if (lane == 0) {
-    *info = st ? -st : res;
+    *info = st ? -st : res[0];
     if (K_out) *K_out = (alg == DOA_PHD || alg == DOA_MN) ? 1 : M - d;
   }
 }
@@ -236,42 +303,57 @@ template <int NP>
 __global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_batch_kernel(const uint8_t *plan, uint8_t *ws, int bucket,
                                                                          int *status) {
   extern __shared__ __align__(16) uint8_t smem[];
+  constexpr int G = mats_per_warp<NP>();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  EigSmem<NP> &s = reinterpret_cast<EigSmem<NP> *>(smem)[warp];
+  EigSmem<NP> *mats = reinterpret_cast<EigSmem<NP> *>(smem) + warp * G;
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
-  const int idx = blockIdx.x * eig_warps<NP>() + warp;
-  if (idx >= h->eig_count[bucket]) return;
-  const int prob = reinterpret_cast<const int32_t *>(plan + h->off_eig[bucket])[idx];
-  const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[prob];
+  const int base = (blockIdx.x * eig_warps<NP>() + warp) * G;
+  const int count = h->eig_count[bucket];
+  if (base >= count) return;
+  const int32_t *list = reinterpret_cast<const int32_t *>(plan + h->off_eig[bucket]);
+  const PlanProblem *probs = reinterpret_cast<const PlanProblem *>(plan + h->off_prob);
   const PlanJob *jobs = reinterpret_cast<const PlanJob *>(plan + h->off_job);
-  const int M = pp.p.M, d = pp.p.d;
-  int res = jacobi_warp<NP>(reinterpret_cast<const double2 *>(ws + pp.r64_off), M, s);
-  int st = 0;
-  if (res > 0) {
-    sort_desc<NP>(M, s);
-    if (pp.p.evals)
-      for (int i = lane; i < M; i += 32) pp.p.evals[i] = s.lam[s.order[i]];
-    for (int j = 0; j < pp.njobs; ++j) {
-      const PlanJob &jb = jobs[pp.first_job + j];
-      int e = build_factor<NP>(M, d, jb.alg, s, reinterpret_cast<double2 *>(ws + jb.B_off));
-      if (e && !st) st = e;
-    }
-  } else {
-    st = -res;
-    // a failed decomposition leaves zero factors, so the scan writes the 1/FLT_MIN sentinel
-    for (int j = 0; j < pp.njobs; ++j) {
-      const PlanJob &jb = jobs[pp.first_job + j];
-      double2 *B = reinterpret_cast<double2 *>(ws + jb.B_off);
-      for (int e = lane; e < M * jb.K; e += 32) B[e] = make_double2(0.0, 0.0);
-    }
+  int Ms[G], prob[G], res[G];
+  const double2 *Rs[G];
+  for (int j = 0; j < G; ++j) {
+    prob[j] = base + j < count ? list[base + j] : -1;
+    Ms[j] = prob[j] >= 0 ? probs[prob[j]].p.M : 0;
+    Rs[j] = prob[j] >= 0 ? reinterpret_cast<const double2 *>(ws + probs[prob[j]].r64_off) : nullptr;
   }
-  if (lane == 0) status[prob] = st;
+  jacobi_group<NP, G>(mats, Ms, Rs, res);
+  for (int j = 0; j < G; ++j) {
+    if (prob[j] < 0) continue;
+    const PlanProblem &pp = probs[prob[j]];
+    EigSmem<NP> &s = mats[j];
+    const int M = pp.p.M, d = pp.p.d;
+    int st = 0;
+    if (res[j] > 0) {
+      sort_desc<NP>(M, s);
+      if (pp.p.evals)
+        for (int i = lane; i < M; i += 32) pp.p.evals[i] = s.lam[s.order[i]];
+      for (int k = 0; k < pp.njobs; ++k) {
+        const PlanJob &jb = jobs[pp.first_job + k];
+        int e = build_factor<NP>(M, d, jb.alg, s, reinterpret_cast<double2 *>(ws + jb.B_off));
+        if (e && !st) st = e;
+      }
+    } else {
+      st = -res[j];
+      // a failed decomposition leaves zero factors, so the scan writes the 1/FLT_MIN sentinel
+      for (int k = 0; k < pp.njobs; ++k) {
+        const PlanJob &jb = jobs[pp.first_job + k];
+        double2 *B = reinterpret_cast<double2 *>(ws + jb.B_off);
+        for (int e = lane; e < M * jb.K; e += 32) B[e] = make_double2(0.0, 0.0);
+      }
+    }
+    if (lane == 0) status[prob[j]] = st;
+    __syncwarp();
+  }
 }
 
 template <int NP>
 cudaError_t run_single(const double2 *R64, int M, int d, int alg, double *evals, double2 *B, int *K_out,
                        int *info, cudaStream_t st) {
-  const int smem = (int)sizeof(EigSmem<NP>);
+  const int smem = (int)sizeof(EigSmem<NP>) * mats_per_warp<NP>();
   cudaError_t e = cudaFuncSetAttribute(eig_single_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   eig_single_kernel<NP><<<1, 32, smem, st>>>(R64, M, d, alg, evals, B, K_out, info);
@@ -284,10 +366,11 @@ cudaError_t run_batch(const uint8_t *plan, const PlanHeader &h, uint8_t *ws, int
   const int count = h.eig_count[bucket];
   if (count == 0) return cudaSuccess;
   constexpr int W = eig_warps<NP>();
-  const int smem = (int)sizeof(EigSmem<NP>) * W;
+  constexpr int per_cta = W * mats_per_warp<NP>();
+  const int smem = (int)sizeof(EigSmem<NP>) * per_cta;
   cudaError_t e = cudaFuncSetAttribute(eig_batch_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  eig_batch_kernel<NP><<<(count + W - 1) / W, 32 * W, smem, st>>>(plan, ws, bucket, status);
+  eig_batch_kernel<NP><<<(count + per_cta - 1) / per_cta, 32 * W, smem, st>>>(plan, ws, bucket, status);
   return cudaGetLastError();
 }
 
