@@ -143,13 +143,17 @@ doa_status doa_noise_subspace(const double *R64, int M, int d, int alg, double *
 }
 
 doa_status doa_scan(const double *B, int M, int K, doa_grid grid, int prec, float *P, void *stream) {
-  if (!B || !P || M < 2 || M > kMaxM || K < 1 || K > M || !grid_ok(grid) || prec != DOA_FP32) return DOA_EINVAL;
+  if (!B || !P || M < 2 || M > kMaxM || K < 1 || K > M || !grid_ok(grid) || prec < DOA_FP32 || prec > DOA_FP16X3)
+    return DOA_EINVAL;
   if (!aligned(B, 16) || !aligned(P, 4)) return DOA_EINVAL;
   cudaStream_t s = as_stream(stream);
   uint32_t *S = reinterpret_cast<uint32_t *>(P);  // phase table first, spectrum over it
   cudaError_t e = launch_grid_table_single(grid.lo_deg, grid.step_deg, grid.L, S, s);
   if (e != cudaSuccess) return DOA_ECUDA;
-  return cuda_status(launch_scan_single(reinterpret_cast<const double2 *>(B), M, K, grid.L, grid.lo_deg, grid.step_deg, S, P, s));
+  const double2 *B2 = reinterpret_cast<const double2 *>(B);
+  if (prec == DOA_FP32)
+    return cuda_status(launch_scan_single(B2, M, K, grid.L, grid.lo_deg, grid.step_deg, S, P, s));
+  return cuda_status(launch_scan_tc_single(B2, M, K, grid.L, grid.lo_deg, grid.step_deg, prec, S, P, s));
 }
 
 doa_status doa_peaks(const float *P, int L, int d, int *idx, float *val, int *count, void *stream) {

@@ -158,6 +158,8 @@ cudaError_t launch_eig_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8
 cudaError_t launch_scan_single(const double2 *B, int M, int K, int L, double lo, double step, const uint32_t *S,
                                float *P, cudaStream_t s);
 cudaError_t launch_scan_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
+cudaError_t launch_scan_tc_single(const double2 *B, int M, int K, int L, double lo, double step, int prec,
+                                  const uint32_t *S, float *P, cudaStream_t s);
 
 cudaError_t launch_peaks_single(const float *P, int L, int d, int *idx, float *val, int *count,
                                 cudaStream_t s);

@@ -284,3 +284,67 @@ def test_batch_edge_shapes(env):
                 if inst.N >= inst.M:   # rank-deficient R (N = 1) has an ill-posed noise basis
                     assert db_error(P[slot], ref["P"]) < DB_TOL
                 slot += 1
+
+
+# ------------------------------------------------------------------------------ Step-5, tensor cores
+@pytest.mark.parametrize("M,d,step,L", [(16, 4, 0.01, 18001), (64, 8, 0.01, 18001), (37, 5, 0.05, 3601),
+                                        (48, 47, 0.1, 1801), (64, 0, 0.5, 361)])
+def test_scan_tensor_core_split(env, M, d, step, L):
+    """BF16x3 / FP16x3 tcgen05 scan with near-null re-evaluation: within 0.01 dB of the oracle."""
+    torch, doa = env
+    inst = synth.custom(M, d, 4 * M + 500, None if d <= 8 else np.linspace(-70, 70, d) + 0.31, 12.0, step,
+                        seed=4000 + M + d)
+    Ro = oracle.covariance(inst.X)
+    ev_o, V_o, _ = oracle.eigh(Ro)
+    for alg in (PHD, MUSIC, EV, MN):
+        Co, _ = oracle.weighting(ev_o, V_o, d, alg)
+        Bf = factor_from_decomposition(ev_o, V_o, d, alg)
+        K = Bf.shape[1]
+        Po, _ = oracle.scan(Co, -90.0, step, L)
+        B = torch.from_numpy(np.ascontiguousarray(Bf.T).reshape(-1)).cuda()
+        for prec in (doa.BF16X3, doa.FP16X3):
+            P = torch.empty(L, dtype=torch.float32, device="cuda")
+            doa.doa_scan(B, M, K, doa.grid(-90.0, step, L), P, prec=prec)
+            torch.cuda.synchronize()
+            err = db_error(P.cpu().numpy(), Po)
+            assert err < DB_TOL, (alg, prec, err)
+        P = torch.empty(L, dtype=torch.float32, device="cuda")
+        doa.doa_scan(B, M, K, doa.grid(-90.0, step, L), P, prec=doa.BF16)      # one BF16 product
+        torch.cuda.synchronize()
+        assert np.all(np.isfinite(P.cpu().numpy()))
+
+
+def test_scan_tensor_core_large_array_sampled(env):
+    """Full large-array grid (M=64, d=8, 360001 points at 0.0005 deg): tensor-core split scan vs the
+    oracle at sampled grid points, including every picked peak and its neighbours."""
+    torch, doa = env
+    inst = synth.large_array(0)
+    Ro = oracle.covariance(inst.X)
+    ev_o, V_o, _ = oracle.eigh(Ro)
+    rng = np.random.default_rng(1)
+    for alg in (MUSIC, EV):
+        Co, _ = oracle.weighting(ev_o, V_o, inst.d, alg)
+        Bf = factor_from_decomposition(ev_o, V_o, inst.d, alg)
+        B = torch.from_numpy(np.ascontiguousarray(Bf.T).reshape(-1)).cuda()
+        g = doa.grid(inst.lo, inst.step, inst.L)
+        for prec in (doa.FP32, doa.BF16X3, doa.FP16X3):
+            P = torch.empty(inst.L, dtype=torch.float32, device="cuda")
+            doa.doa_scan(B, inst.M, Bf.shape[1], g, P, prec=prec)
+            idx = torch.zeros(inst.d, dtype=torch.int32, device="cuda")
+            val = torch.zeros(inst.d, dtype=torch.float32, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+            doa.doa_peaks(P, inst.d, idx, val, cnt)
+            torch.cuda.synchronize()
+            Pg = P.cpu().numpy()
+            pk = idx.cpu().numpy()[:cnt.item()]
+            ks = set(rng.integers(0, inst.L, 1500).tolist())
+            for k in pk:
+                ks.update(range(max(0, k - 3), min(inst.L, k + 4)))
+            ks = sorted(ks)
+            Po = np.array([oracle.scan(Co, inst.lo + k * inst.step, inst.step, 1)[0][0] for k in ks])
+            err = float(np.max(np.abs(10 * np.log10(Pg[ks].astype(np.float64) / Po))))
+            assert err < DB_TOL, (alg, prec, err)
+            # the picked peaks are local maxima of the oracle's spectrum too
+            for k in pk:
+                a = [oracle.scan(Co, inst.lo + j * inst.step, inst.step, 1)[0][0] for j in (k - 1, k, k + 1)]
+                assert a[1] >= a[0] and a[1] >= a[2]
