@@ -74,9 +74,13 @@ const char *doa_status_str(int status);
  *          ldx >= N complex elements. 8-byte aligned.
  *   R    : M x M complex64 row-major (nullable).
  *   R64  : M x M complex128 row-major (nullable). At least one of R, R64 is non-NULL.
- *   prec : DOA_FP32: products and partial sums in FP32 within ranges of snapshots, ranges
- *          combined in FP64 (a cluster of up to 8 CTAs, reduced through distributed shared
- *          memory). Other values are rejected (DOA_EINVAL).
+ *   prec : DOA_FP32: exact FP32 products (FMA) accumulated in double-float within ranges of
+ *          snapshots, ranges combined in FP64 (a cluster of up to 8 CTAs, reduced through
+ *          distributed shared memory); about 2^-44 relative error.
+ *          DOA_BF16 / DOA_BF16X3 / DOA_FP16X3: one real tcgen05 GEMM [Y; Z] Y^T fed by TMA
+ *          (Y = X as reals, Z = pairs (re, im) -> (im, -re)) with BF16 or split hi+lo operands
+ *          and FP32 accumulation (about 2^-8, 2^-16, 2^-22 relative per product); these need a
+ *          16-byte aligned X and an even ldx.
  * Errors: DOA_EINVAL for M outside [2, 64], N < 1, ldx < N, NULL X, both outputs NULL.
  */
 doa_status doa_covariance(const float *X, int M, int N, int ldx, float *R, double *R64, int prec,
@@ -127,7 +131,12 @@ doa_status doa_noise_subspace(const double *R64, int M, int d, int alg, double *
  *   B    : M x K complex128 column-major, leading dimension M (as written by
  *          doa_noise_subspace). 1 <= K <= M.
  *   grid : scan grid; L >= 3.
- *   prec : DOA_FP32 (CUDA-core FFMA; phases exact to 2^-31 of a half turn).
+ *   prec : DOA_FP32: CUDA-core FFMA; phases exact to 2^-31 of a half turn; points whose
+ *          denominator is small are re-evaluated in FP64 (warp per point).
+ *          DOA_BF16 / DOA_BF16X3 / DOA_FP16X3: tcgen05 GEMM of the generated steering block
+ *          against the real embedding of B (one BF16 product, or split hi+lo operands with three
+ *          products); for the split forms the points below the split's error threshold are
+ *          re-evaluated in FP32 and then FP64, so they meet the FP32 tolerance.
  *   P    : L floats, 4-byte aligned. The call first writes the grid's phase table into P and
  *          then overwrites it with the spectrum, so P needs no companion buffer.
  */

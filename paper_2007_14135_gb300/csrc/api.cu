@@ -126,11 +126,17 @@ const char *doa_status_str(int status) {
 }
 
 doa_status doa_covariance(const float *X, int M, int N, int ldx, float *R, double *R64, int prec, void *stream) {
-  if (!X || M < 2 || M > kMaxM || N < 1 || ldx < N || (!R && !R64) || prec != DOA_FP32) return DOA_EINVAL;
+  if (!X || M < 2 || M > kMaxM || N < 1 || ldx < N || (!R && !R64) || prec < DOA_FP32 || prec > DOA_FP16X3)
+    return DOA_EINVAL;
   if (!aligned(X, 8) || (R && !aligned(R, 8)) || (R64 && !aligned(R64, 16))) return DOA_EINVAL;
-  return cuda_status(launch_covariance_single(reinterpret_cast<const float2 *>(X), M, N, ldx,
-                                              reinterpret_cast<float2 *>(R), reinterpret_cast<double2 *>(R64),
-                                              as_stream(stream)));
+  const float2 *X2 = reinterpret_cast<const float2 *>(X);
+  if (prec == DOA_FP32)
+    return cuda_status(launch_covariance_single(X2, M, N, ldx, reinterpret_cast<float2 *>(R),
+                                                reinterpret_cast<double2 *>(R64), as_stream(stream)));
+  // tensor-core forms read X with TMA: 16-byte aligned base and row pitch
+  if (!aligned(X, 16) || (ldx & 1)) return DOA_EINVAL;
+  return cuda_status(launch_covariance_tc_single(X2, M, N, ldx, prec, reinterpret_cast<float2 *>(R),
+                                                 reinterpret_cast<double2 *>(R64), as_stream(stream)));
 }
 
 doa_status doa_noise_subspace(const double *R64, int M, int d, int alg, double *evals, double *B, int *K_out,

@@ -149,6 +149,8 @@ cudaError_t launch_covariance_single(const float2 *X, int M, int N, int ldx, flo
                                      cudaStream_t s);
 cudaError_t launch_covariance_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws,
                                     cudaStream_t s);
+cudaError_t launch_covariance_tc_single(const float2 *X, int M, int N, int ldx, int prec, float2 *R, double2 *R64,
+                                        cudaStream_t s);
 
 cudaError_t launch_eig_single(const double2 *R64, int M, int d, int alg, double *evals, double2 *B,
                               int *K_out, int *info, cudaStream_t s);

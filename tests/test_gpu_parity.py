@@ -348,3 +348,42 @@ def test_scan_tensor_core_large_array_sampled(env):
             for k in pk:
                 a = [oracle.scan(Co, inst.lo + j * inst.step, inst.step, 1)[0][0] for j in (k - 1, k, k + 1)]
                 assert a[1] >= a[0] and a[1] >= a[2]
+
+
+# ------------------------------------------------------------------------------ Step-1, tensor cores
+def tc_cov_tol(prec, N):
+    """Relative error bound (max |R_gpu - R_oracle| / max |R|) of the tcgen05 covariance: the
+    operand representation (BF16 2^-8; split BF16 ~2^-16; split FP16 ~2^-21, each doubled for the
+    two factors) plus FP32 accumulation over 2N products (4 sqrt(2N) 2^-24)."""
+    rep = {1: 2 * 2.0 ** -8, 2: 4 * 2.0 ** -16, 3: 4 * 2.0 ** -21}[prec]
+    return rep + 4 * np.sqrt(2 * N) * 2.0 ** -24
+
+
+@pytest.mark.parametrize("M,N", [(8, 1024), (16, 4096), (37, 1000), (64, 16384), (64, 33), (5, 20000)])
+def test_covariance_tensor_core(env, M, N):
+    torch, doa = env
+    inst = synth.custom(M, min(4, M - 1), N, None, 10.0, 0.1, seed=5000 + M * 11 + N)
+    ld = N + (N & 1)                      # TMA needs an even row pitch (16-byte rows)
+    Xh = np.zeros((M, ld), np.complex64)
+    Xh[:, :N] = inst.X
+    X = torch.from_numpy(Xh).cuda()[:, :N]
+    Ro = oracle.covariance(inst.X)
+    scale = np.max(np.abs(Ro))
+    for prec in (doa.BF16, doa.BF16X3, doa.FP16X3):
+        tol = tc_cov_tol(prec, N)
+        R64 = torch.full((M, M), float("nan"), dtype=torch.complex128, device="cuda")
+        doa.doa_covariance(X, R64=R64, prec=prec)
+        torch.cuda.synchronize()
+        Rg = R64.cpu().numpy()
+        err = np.max(np.abs(Rg - Ro)) / scale
+        assert err < tol, (prec, err)
+        assert np.array_equal(Rg, Rg.conj().T)
+
+
+def test_covariance_tensor_core_rejects_unaligned(env):
+    torch, doa = env
+    X = torch.zeros((8, 101), dtype=torch.complex64, device="cuda")
+    R = torch.empty((8, 8), dtype=torch.complex128, device="cuda")
+    with pytest.raises(doa.DoaError):
+        doa.doa_covariance(X[:, :100], R64=R, prec=doa.FP16X3)     # row pitch 101 is odd
+    doa.doa_covariance(X[:, :100], R64=R, prec=doa.FP32)           # the FP32 path takes any pitch
