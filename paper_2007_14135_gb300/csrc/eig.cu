@@ -13,8 +13,8 @@
 // A <- J^H A for all rotated pairs, then the column updates A <- A J and V <- V J. A pair is
 // rotated when |a_pq|^2 > tol^2 |a_pp a_qq|; a matrix has converged after a sweep that rotates
 // nothing. A warp holds 32 / (NP/2) matrices so that every lane owns one pair's rotation
-// (8 matrices of M <= 8, 4 of M <= 16, 2 of M <= 32, 1 of M <= 64); the element updates of each
-// matrix are spread over all 32 lanes. A and V live in shared memory with a padded row stride
+// (8 matrices of M <= 8, 4 of M <= 16, 2 of M <= 32); a matrix of M <= 64 gets a whole CTA.
+// The element updates of each matrix are spread over all threads of its group. A and V live in shared memory with a padded row stride
 // (NP + 1 complex128) so that column accesses by consecutive lanes hit distinct banks.
 #include "doa_internal.cuh"
 
@@ -33,12 +33,30 @@ struct EigSmem {
   int2 pq[NP / 2];
   double lam[NP];
   int order[NP];
+  unsigned mask;   // rotation mask broadcast when a group spans several warps
 };
 
+// A group of T threads works on G matrices: one warp on 8, 4 or 2 matrices of M <= 8, 16, 32
+// (every lane owns one pair), or a whole 8-warp CTA on one matrix of M <= 64 (the 32 pairs
+// are owned by warp 0's lanes; the element updates are spread over all 256 threads).
 template <int NP>
-__host__ __device__ constexpr int mats_per_warp() { return 64 / NP; }
+__host__ __device__ constexpr int grp_threads() { return NP <= 32 ? 32 : 256; }
 template <int NP>
-__host__ __device__ constexpr int eig_warps() { return NP <= 8 ? 4 : (NP <= 16 ? 2 : 1); }
+__host__ __device__ constexpr int mats_per_warp() { return NP <= 32 ? 64 / NP : 1; }
+template <int NP>
+__host__ __device__ constexpr int eig_warps() { return NP <= 8 ? 4 : (NP <= 16 ? 2 : (NP <= 32 ? 1 : 8)); }
+template <int NP>
+__host__ __device__ constexpr int groups_per_cta() { return NP <= 32 ? eig_warps<NP>() : 1; }
+
+template <int T>
+struct Grp {
+  __device__ static int id() { return (int)(threadIdx.x % T); }
+  __device__ static void sync() {
+    if (T == 32) __syncwarp(); else __syncthreads();
+  }
+  __device__ static bool all(bool p) { return T == 32 ? __all_sync(0xffffffffu, p) : __syncthreads_and(p) != 0; }
+  __device__ static bool any(bool p) { return T == 32 ? __any_sync(0xffffffffu, p) : __syncthreads_or(p) != 0; }
+};
 
 __device__ __forceinline__ int rr_player(int pos, int r, int n) {
   return pos == 0 ? 0 : ((pos - 1 + r) % (n - 1)) + 1;
@@ -72,7 +90,9 @@ __device__ __forceinline__ bool rotation(EigSmem<NP> &s, int p, int q, Rot &ro) 
 template <int NP, int G>
 __device__ void jacobi_group(EigSmem<NP> *mats, const int *Ms, const double2 *const *Rs, int *res) {
   constexpr int HP = NP / 2;
-  const int lane = threadIdx.x & 31;
+  constexpr int T = grp_threads<NP>();
+  using g = Grp<T>;
+  const int lane = g::id();
   unsigned live = 0u;  // matrices still iterating
   for (int j = 0; j < G; ++j) {
     const int M = Ms[j];
@@ -81,7 +101,7 @@ __device__ void jacobi_group(EigSmem<NP> *mats, const int *Ms, const double2 *co
     EigSmem<NP> &s = mats[j];
     const double2 *R = Rs[j];
     bool finite = true;
-    for (int e = lane; e < M * M; e += 32) {
+    for (int e = lane; e < M * M; e += T) {
       int i = e / M, k = e % M;
       double2 v;
       if (i <= k) {
@@ -95,17 +115,17 @@ __device__ void jacobi_group(EigSmem<NP> *mats, const int *Ms, const double2 *co
       s.A[i][k] = v;
       s.V[i][k] = make_double2(i == k ? 1.0 : 0.0, 0.0);
     }
-    if (__all_sync(0xffffffffu, finite))
+    if (g::all(finite))
       live |= 1u << j;
     else
       res[j] = -DOA_ENONFINITE;
   }
-  __syncwarp();
+  g::sync();
   int maxn = 0;
   for (int j = 0; j < G; ++j)
     if ((live >> j) & 1u) maxn = max(maxn, (Ms[j] + 1) & ~1);
   // lane -> (matrix, pair) for the rotation parameters
-  const int lj = lane / HP, li = lane % HP;
+  const int lj = lane < 32 ? lane / HP : G, li = lane % HP;
   for (int sweep = 1; sweep <= kMaxSweeps && live; ++sweep) {
     unsigned rotated = 0u;
     for (int r = 0; r < maxn - 1; ++r) {
@@ -125,9 +145,18 @@ __device__ void jacobi_group(EigSmem<NP> *mats, const int *Ms, const double2 *co
           }
         }
       }
-      const unsigned mask = __ballot_sync(0xffffffffu, act);
+      unsigned mask;
+      if (T == 32) {
+        mask = __ballot_sync(0xffffffffu, act);
+      } else {
+        const unsigned m0 = __ballot_sync(0xffffffffu, act);
+        if (threadIdx.x == 0) mats[0].mask = m0;    // only warp 0 owns pairs
+        __syncthreads();
+        mask = mats[0].mask;
+        __syncthreads();
+      }
       if (mask == 0u) continue;
-      __syncwarp();
+      g::sync();
       // rows: A <- J^H A. new row p = c x_p - sigma x_q; new row q = conj(sigma) x_p + c x_q
       for (int j = 0; j < G; ++j) {
         const unsigned seg = (mask >> (j * HP)) & ((HP == 32) ? 0xffffffffu : ((1u << HP) - 1u));
@@ -135,7 +164,7 @@ __device__ void jacobi_group(EigSmem<NP> *mats, const int *Ms, const double2 *co
         rotated |= 1u << j;
         EigSmem<NP> &s = mats[j];
         const int M = Ms[j];
-        for (int it = lane; it < HP * M; it += 32) {
+        for (int it = lane; it < HP * M; it += T) {
           const int i = it / M, k = it % M;
           if (!((seg >> i) & 1u)) continue;
           const Rot ro = s.rot[i];
@@ -147,14 +176,14 @@ __device__ void jacobi_group(EigSmem<NP> *mats, const int *Ms, const double2 *co
                                       ro.c * xq.y + (ro.sr * xp.y - ro.si * xp.x));
         }
       }
-      __syncwarp();
+      g::sync();
       // columns: A <- A J, V <- V J. new col p = c x_p - conj(sigma) x_q; new col q = sigma x_p + c x_q
       for (int j = 0; j < G; ++j) {
         const unsigned seg = (mask >> (j * HP)) & ((HP == 32) ? 0xffffffffu : ((1u << HP) - 1u));
         if (!seg) continue;
         EigSmem<NP> &s = mats[j];
         const int M = Ms[j];
-        for (int it = lane; it < HP * M; it += 32) {
+        for (int it = lane; it < HP * M; it += T) {
           const int i = it / M, k = it % M;
           if (!((seg >> i) & 1u)) continue;
           const Rot ro = s.rot[i];
@@ -171,7 +200,7 @@ __device__ void jacobi_group(EigSmem<NP> *mats, const int *Ms, const double2 *co
                                       ro.c * vq.y + (ro.sr * vp.y + ro.si * vp.x));
         }
       }
-      __syncwarp();
+      g::sync();
       if (act) {
         EigSmem<NP> &s = mats[lj];
         const int2 pq = s.pq[li];
@@ -180,7 +209,7 @@ __device__ void jacobi_group(EigSmem<NP> *mats, const int *Ms, const double2 *co
         s.A[pq.x][pq.x].y = 0.0;
         s.A[pq.y][pq.y].y = 0.0;
       }
-      __syncwarp();
+      g::sync();
     }
     // matrices without a rotation in this sweep have converged
     for (int j = 0; j < G; ++j)
@@ -196,10 +225,12 @@ __device__ void jacobi_group(EigSmem<NP> *mats, const int *Ms, const double2 *co
 // Stable descending order of the eigenvalues (equal values keep index order).
 template <int NP>
 __device__ void sort_desc(int M, EigSmem<NP> &s) {
-  const int lane = threadIdx.x & 31;
-  for (int i = lane; i < M; i += 32) s.lam[i] = s.A[i][i].x;
-  __syncwarp();
-  for (int i = lane; i < M; i += 32) {
+  constexpr int T = grp_threads<NP>();
+  using g = Grp<T>;
+  const int lane = g::id();
+  for (int i = lane; i < M; i += T) s.lam[i] = s.A[i][i].x;
+  g::sync();
+  for (int i = lane; i < M; i += T) {
     double li = s.lam[i];
     int rank = 0;
     for (int j = 0; j < M; ++j) {
@@ -208,22 +239,24 @@ __device__ void sort_desc(int M, EigSmem<NP> &s) {
     }
     s.order[rank] = i;
   }
-  __syncwarp();
+  g::sync();
 }
 
 // Writes B (column-major, ld M) of algorithm alg; returns 0 or a doa_status.
 template <int NP>
 __device__ int build_factor(int M, int d, int alg, EigSmem<NP> &s, double2 *__restrict__ B) {
-  const int lane = threadIdx.x & 31;
+  constexpr int T = grp_threads<NP>();
+  using g = Grp<T>;
+  const int lane = g::id();
   const int Kn = M - d;  // noise subspace dimension
   if (alg == DOA_PHD) {
     int col = s.order[M - 1];
-    for (int r = lane; r < M; r += 32) B[r] = s.V[r][col];
+    for (int r = lane; r < M; r += T) B[r] = s.V[r][col];
     return 0;
   }
   if (alg == DOA_MUSIC || alg == DOA_EV) {
     bool bad = false;
-    for (int e = lane; e < M * Kn; e += 32) {
+    for (int e = lane; e < M * Kn; e += T) {
       int c = e / M, r = e % M;
       int col = s.order[d + c];
       double2 v = s.V[r][col];
@@ -240,7 +273,7 @@ __device__ int build_factor(int M, int d, int alg, EigSmem<NP> &s, double2 *__re
       }
       B[c * M + r] = v;
     }
-    bad = __any_sync(0xffffffffu, bad);
+    bad = g::any(bad);
     return bad ? DOA_ERANK : 0;
   }
   // MN: valph = P_n e1 / (e1^H P_n e1); (P_n e1)_r = sum_c V[r][c] conj(V[0][c]) over noise c
@@ -250,11 +283,11 @@ __device__ int build_factor(int M, int d, int alg, EigSmem<NP> &s, double2 *__re
     nrm += g.x * g.x + g.y * g.y;
   }
   if (!(nrm > 0.0)) {
-    for (int r = lane; r < M; r += 32) B[r] = make_double2(0.0, 0.0);
+    for (int r = lane; r < M; r += T) B[r] = make_double2(0.0, 0.0);
     return DOA_ERANK;
   }
   const double inv = 1.0 / nrm;
-  for (int r = lane; r < M; r += 32) {
+  for (int r = lane; r < M; r += T) {
     double2 acc = make_double2(0.0, 0.0);
     for (int c = 0; c < Kn; ++c) {
       int col = s.order[d + c];
@@ -269,12 +302,13 @@ __device__ int build_factor(int M, int d, int alg, EigSmem<NP> &s, double2 *__re
 }
 
 template <int NP>
-__global__ void __launch_bounds__(32) eig_single_kernel(const double2 *R64, int M, int d, int alg, double *evals,
+__global__ void __launch_bounds__(grp_threads<NP>()) eig_single_kernel(const double2 *R64, int M, int d, int alg, double *evals,
                                                        double2 *B, int *K_out, int *info) {
   extern __shared__ __align__(16) uint8_t smem[];
   constexpr int G = mats_per_warp<NP>();
   EigSmem<NP> *mats = reinterpret_cast<EigSmem<NP> *>(smem);
-  const int lane = threadIdx.x & 31;
+  constexpr int T = grp_threads<NP>();
+  const int lane = Grp<T>::id();
   int Ms[G];
   const double2 *Rs[G];
   int res[G];
@@ -288,7 +322,7 @@ __global__ void __launch_bounds__(32) eig_single_kernel(const double2 *R64, int 
   if (res[0] > 0) {
     sort_desc<NP>(M, s);
     if (evals)
-      for (int i = lane; i < M; i += 32) evals[i] = s.lam[s.order[i]];
+      for (int i = lane; i < M; i += T) evals[i] = s.lam[s.order[i]];
     st = build_factor<NP>(M, d, alg, s, B);
   } else {
     st = -res[0];
@@ -304,10 +338,11 @@ __global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_batch_kernel(const u
                                                                          int *status) {
   extern __shared__ __align__(16) uint8_t smem[];
   constexpr int G = mats_per_warp<NP>();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  EigSmem<NP> *mats = reinterpret_cast<EigSmem<NP> *>(smem) + warp * G;
+  constexpr int T = grp_threads<NP>();
+  const int grp = threadIdx.x / T, lane = Grp<T>::id();
+  EigSmem<NP> *mats = reinterpret_cast<EigSmem<NP> *>(smem) + grp * G;
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
-  const int base = (blockIdx.x * eig_warps<NP>() + warp) * G;
+  const int base = (blockIdx.x * groups_per_cta<NP>() + grp) * G;
   const int count = h->eig_count[bucket];
   if (base >= count) return;
   const int32_t *list = reinterpret_cast<const int32_t *>(plan + h->off_eig[bucket]);
@@ -330,7 +365,7 @@ __global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_batch_kernel(const u
     if (res[j] > 0) {
       sort_desc<NP>(M, s);
       if (pp.p.evals)
-        for (int i = lane; i < M; i += 32) pp.p.evals[i] = s.lam[s.order[i]];
+        for (int i = lane; i < M; i += T) pp.p.evals[i] = s.lam[s.order[i]];
       for (int k = 0; k < pp.njobs; ++k) {
         const PlanJob &jb = jobs[pp.first_job + k];
         int e = build_factor<NP>(M, d, jb.alg, s, reinterpret_cast<double2 *>(ws + jb.B_off));
@@ -342,11 +377,11 @@ __global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_batch_kernel(const u
       for (int k = 0; k < pp.njobs; ++k) {
         const PlanJob &jb = jobs[pp.first_job + k];
         double2 *B = reinterpret_cast<double2 *>(ws + jb.B_off);
-        for (int e = lane; e < M * jb.K; e += 32) B[e] = make_double2(0.0, 0.0);
+        for (int e = lane; e < M * jb.K; e += T) B[e] = make_double2(0.0, 0.0);
       }
     }
     if (lane == 0) status[prob[j]] = st;
-    __syncwarp();
+    Grp<T>::sync();
   }
 }
 
@@ -356,7 +391,7 @@ cudaError_t run_single(const double2 *R64, int M, int d, int alg, double *evals,
   const int smem = (int)sizeof(EigSmem<NP>) * mats_per_warp<NP>();
   cudaError_t e = cudaFuncSetAttribute(eig_single_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  eig_single_kernel<NP><<<1, 32, smem, st>>>(R64, M, d, alg, evals, B, K_out, info);
+  eig_single_kernel<NP><<<1, grp_threads<NP>(), smem, st>>>(R64, M, d, alg, evals, B, K_out, info);
   return cudaGetLastError();
 }
 
@@ -366,7 +401,7 @@ cudaError_t run_batch(const uint8_t *plan, const PlanHeader &h, uint8_t *ws, int
   const int count = h.eig_count[bucket];
   if (count == 0) return cudaSuccess;
   constexpr int W = eig_warps<NP>();
-  constexpr int per_cta = W * mats_per_warp<NP>();
+  constexpr int per_cta = groups_per_cta<NP>() * mats_per_warp<NP>();
   const int smem = (int)sizeof(EigSmem<NP>) * per_cta;
   cudaError_t e = cudaFuncSetAttribute(eig_batch_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
