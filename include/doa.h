@@ -204,6 +204,51 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const int32_t *sc
 doa_status doa_solve_batch(const void *plan_host, const void *plan_dev, void *ws, size_t ws_bytes,
                            int *status, void *const *stage_events, void *stream);
 
+/* ----------------------------------------------------------------------------------------- */
+/* Learned angle proposal (not in the paper): a multilayer perceptron that maps the             */
+/* trace-normalised upper triangle of R (136 complex = 272 reals, doa_problem.features) to a     */
+/* 181-bin (1 degree, -90..90) occupancy map, so the fine scan runs only in windows around the   */
+/* proposed angles. Layers 272 -> 256 -> 256 -> 256 -> 181, ReLU hidden, sigmoid output,        */
+/* binary cross-entropy on logits, Adam. FP32 master weights; the products run as BF16 tcgen05  */
+/* GEMMs (TMA-fed) with FP32 accumulation.                                                       */
+/* ----------------------------------------------------------------------------------------- */
+#define DOA_MLP_IN 272
+#define DOA_MLP_HIDDEN 256
+#define DOA_MLP_OUT 181
+
+/* Device buffers of the network, layer l = 0..3 with (in, out) = (272,256), (256,256),
+ * (256,256), (256,181). W[l] is out x in row-major FP32, b[l] out FP32; mW/vW/mb/vb are the Adam
+ * moments and gW/gb the gradients (same shapes; only needed for training). Wh[l] is the BF16
+ * copy of W[l] (row pitch in), WhT[l] its transpose (in x out, row pitch out rounded up to 8). */
+typedef struct {
+  float *W[4], *b[4];
+  float *mW[4], *vW[4], *mb[4], *vb[4];
+  float *gW[4], *gb[4];
+  void *Wh[4], *WhT[4];
+} doa_mlp;
+
+/* Workspace of a forward/backward pass on `batch` rows (a multiple of 8); 0 if invalid. */
+size_t doa_mlp_workspace_bytes(int batch);
+
+/* Writes the BF16 copies Wh/WhT from the FP32 masters W (after initialisation). */
+doa_status doa_mlp_refresh(const doa_mlp *net, void *stream);
+
+/* features: batch x 272 FP32. probs (nullable): batch x 181 sigmoid outputs; logits (nullable):
+ * batch x 181. ws: doa_mlp_workspace_bytes(batch) bytes, 256-byte aligned. */
+doa_status doa_mlp_forward(const doa_mlp *net, const float *features, int batch, float *probs,
+                           float *logits, void *ws, size_t ws_bytes, void *stream);
+
+/* Forward + backward on one minibatch: fills gW/gb with the gradient of the mean (over rows)
+ * summed binary cross-entropy against labels (batch x 181, in [0, 1]); loss (nullable device
+ * float) receives that mean. */
+doa_status doa_mlp_backward(const doa_mlp *net, const float *features, const float *labels,
+                            int batch, float *loss, void *ws, size_t ws_bytes, void *stream);
+
+/* One Adam step (Kingma & Ba) on every parameter with bias corrections for step t >= 1, then
+ * refreshes the BF16 copies. */
+doa_status doa_mlp_adam(const doa_mlp *net, float lr, float beta1, float beta2, float eps, int t,
+                        void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,8 @@ STAGE_NAMES = ("phase_tables", "covariance", "eig_noise_subspace", "scan", "peak
 
 # every symbol include/doa.h declares
 EXPORTS = ("doa_status_str", "doa_covariance", "doa_covariance_noalloc", "doa_noise_subspace", "doa_scan",
-           "doa_peaks", "doa_batch_plan_bytes", "doa_batch_plan", "doa_solve_batch")
+           "doa_peaks", "doa_batch_plan_bytes", "doa_batch_plan", "doa_solve_batch", "doa_mlp_workspace_bytes",
+           "doa_mlp_refresh", "doa_mlp_forward", "doa_mlp_backward", "doa_mlp_adam")
 
 
 class DoaError(RuntimeError):
@@ -218,3 +219,111 @@ def doa_solve_batch(plan: BatchPlan, ws: torch.Tensor, status: torch.Tensor, sta
 def workspace(plan: BatchPlan, device: str = "cuda") -> torch.Tensor:
     """A device buffer of the plan's workspace size (256-byte aligned by the caching allocator)."""
     return torch.empty(max(plan.ws_bytes, 256), dtype=torch.uint8, device=device)
+
+
+# ------------------------------------------------------------------------------------ network
+MLP_DIMS = (272, 256, 256, 256, 181)
+
+
+class MlpStruct(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p * 4) for name in
+                ("W", "b", "mW", "vW", "mb", "vb", "gW", "gb", "Wh", "WhT")]
+
+
+def _bind_mlp(lib_):
+    vp, i, sz, f = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_float
+    lib_.doa_mlp_workspace_bytes.argtypes = [i]
+    lib_.doa_mlp_workspace_bytes.restype = sz
+    lib_.doa_mlp_refresh.argtypes = [ctypes.POINTER(MlpStruct), vp]
+    lib_.doa_mlp_forward.argtypes = [ctypes.POINTER(MlpStruct), vp, i, vp, vp, vp, sz, vp]
+    lib_.doa_mlp_backward.argtypes = [ctypes.POINTER(MlpStruct), vp, vp, i, vp, vp, sz, vp]
+    lib_.doa_mlp_adam.argtypes = [ctypes.POINTER(MlpStruct), f, f, f, f, i, vp]
+    for n in ("doa_mlp_refresh", "doa_mlp_forward", "doa_mlp_backward", "doa_mlp_adam"):
+        getattr(lib_, n).restype = i
+
+
+class Mlp:
+    """Device buffers of the proposal network (doa_mlp) and thin wrappers of its entry points.
+
+    Initial weights: He-uniform (bound sqrt(6 / fan_in)) from a seeded NumPy Philox generator,
+    biases zero, Adam moments zero."""
+
+    def __init__(self, seed: int = 0, device: str = "cuda", train: bool = True):
+        _bind_mlp(lib())
+        self.device = device
+        rng = np.random.Generator(np.random.Philox(key=int(seed)))
+        self.t = 0
+        fields = ("W", "b", "mW", "vW", "mb", "vb", "gW", "gb", "Wh", "WhT")
+        self.buf = {k: [] for k in fields}
+        for l in range(4):
+            fin, fout = MLP_DIMS[l], MLP_DIMS[l + 1]
+            bound = np.sqrt(6.0 / fin)
+            W = rng.uniform(-bound, bound, size=(fout, fin)).astype(np.float32)
+            self.buf["W"].append(torch.from_numpy(W).to(device))
+            self.buf["b"].append(torch.zeros(fout, dtype=torch.float32, device=device))
+            for k, shape in (("mW", (fout, fin)), ("vW", (fout, fin)), ("gW", (fout, fin)),
+                             ("mb", (fout,)), ("vb", (fout,)), ("gb", (fout,))):
+                self.buf[k].append(torch.zeros(shape, dtype=torch.float32, device=device) if train else None)
+            self.buf["Wh"].append(torch.zeros((fout, fin), dtype=torch.bfloat16, device=device))
+            self.buf["WhT"].append(torch.zeros((fin, (fout + 7) // 8 * 8), dtype=torch.bfloat16, device=device))
+        self.struct = MlpStruct()
+        for k in fields:
+            arr = getattr(self.struct, k)
+            for l in range(4):
+                t = self.buf[k][l]
+                arr[l] = t.data_ptr() if t is not None else None
+        self.refresh()
+
+    def refresh(self, stream=None):
+        _check(lib().doa_mlp_refresh(ctypes.byref(self.struct), _stream(stream)), "doa_mlp_refresh")
+
+    def workspace(self, batch: int) -> torch.Tensor:
+        n = lib().doa_mlp_workspace_bytes(batch)
+        if n == 0:
+            raise DoaError(EINVAL, "doa_mlp_workspace_bytes (batch must be a positive multiple of 8)")
+        return torch.empty(n, dtype=torch.uint8, device=self.device)
+
+    def forward(self, features: torch.Tensor, ws: torch.Tensor, probs=None, logits=None, stream=None):
+        B = features.shape[0]
+        _check(lib().doa_mlp_forward(ctypes.byref(self.struct), _dev(features), B, _dev(probs), _dev(logits),
+                                     _dev(ws), ws.numel(), _stream(stream)), "doa_mlp_forward")
+
+    def backward(self, features: torch.Tensor, labels: torch.Tensor, ws: torch.Tensor, loss=None, stream=None):
+        B = features.shape[0]
+        _check(lib().doa_mlp_backward(ctypes.byref(self.struct), _dev(features), _dev(labels), B, _dev(loss),
+                                      _dev(ws), ws.numel(), _stream(stream)), "doa_mlp_backward")
+
+    def adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream=None):
+        self.t += 1
+        _check(lib().doa_mlp_adam(ctypes.byref(self.struct), lr, beta1, beta2, eps, self.t, _stream(stream)),
+               "doa_mlp_adam")
+
+    def params_numpy(self):
+        return [(self.buf["W"][l].cpu().numpy().astype(np.float64), self.buf["b"][l].cpu().numpy().astype(np.float64))
+                for l in range(4)]
+
+    def save(self, path: str) -> None:
+        """Checkpoint: magic, Adam step, then every FP32 buffer (W, b, moments) in layer order."""
+        with open(path, "wb") as f:
+            f.write(np.array([0x4D4C5031, self.t], dtype=np.int64).tobytes())
+            for k in ("W", "b", "mW", "vW", "mb", "vb"):
+                for l in range(4):
+                    t = self.buf[k][l]
+                    f.write((t if t is not None else torch.zeros(1)).detach().cpu().numpy().astype(np.float32).tobytes())
+
+    def load(self, path: str) -> None:
+        raw = open(path, "rb").read()
+        head = np.frombuffer(raw[:16], dtype=np.int64)
+        if head[0] != 0x4D4C5031:
+            raise ValueError("not a network checkpoint")
+        self.t = int(head[1])
+        at = 16
+        for k in ("W", "b", "mW", "vW", "mb", "vb"):
+            for l in range(4):
+                t = self.buf[k][l]
+                n = t.numel() if t is not None else 1
+                arr = np.frombuffer(raw[at:at + 4 * n], dtype=np.float32)
+                at += 4 * n
+                if t is not None:
+                    t.copy_(torch.from_numpy(arr.copy()).view_as(t))
+        self.refresh()
