@@ -167,6 +167,10 @@ typedef struct {
   int32_t M, N, ldx, d;
   uint32_t alg_mask;     /* bit a set => algorithm a (DOA_PHD=bit 0 ... DOA_MN=bit 3)        */
   int32_t prec;          /* doa_prec of the covariance and scan                              */
+  float *features;       /* nullable: M(M+1) floats, the upper triangle (row by row, i <= j)  */
+                         /* of R / tr(R) as (re, im) pairs (the proposal network's input)     */
+  double *B_out;         /* nullable: copy of the factor B of the first algorithm in          */
+                         /* alg_mask (M x K complex128, column-major, ld M)                   */
 } doa_problem;
 
 /*
@@ -248,6 +252,49 @@ doa_status doa_mlp_backward(const doa_mlp *net, const float *features, const flo
  * refreshes the BF16 copies. */
 doa_status doa_mlp_adam(const doa_mlp *net, float lr, float beta1, float beta2, float eps, int t,
                         void *stream);
+
+/*
+ * Seeded ULA snapshots generated on the GPU (training data of the proposal network; the signal
+ * model of Sec. 3.1, Eq. 1): X_b = A(theta_b) S_b + W_b with unit-power CN(0,1) sources and white
+ * CN(0, sigma_b^2) noise, sigma_b^2 = 10^(-snr_db[b]/10). Random numbers: Philox4x32-10 (Salmon et
+ * al., SC'11) with key = seed and counter = (snapshot, instance, instance >> 32, draw), instance =
+ * first_instance + b; normals by Box-Muller. The per-instance source count d[b] <= 16, angles
+ * (degrees, row b holds d[b] of dmax entries) and SNR are device inputs.
+ *   X: batch x M x N complex64 (row-major per instance). batch <= 65535, M <= 64.
+ */
+doa_status doa_synth_ula(int batch, int M, int N, const int32_t *d, const float *angles_deg, int dmax,
+                         const float *snr_db, uint64_t seed, uint64_t first_instance, float *X,
+                         void *stream);
+
+/*
+ * Proposal decoding: for each row b of probs (batch x 181 sigmoid outputs of 1-degree bins centred
+ * at -90, -89, ..., 90 deg), the min(d[b] + extra, dmax) highest bins (ties: lower bin) with the
+ * two neighbours of every pick suppressed; pick w becomes a window of `width` points of the fine
+ * grid starting at win_first[b*dmax + w] (the grid index of the bin centre minus width/2, clamped
+ * into the grid); unused entries are -1. dmax <= 8.
+ */
+doa_status doa_proposal_windows(const float *probs, const int32_t *d, int batch, int dmax, int extra,
+                                doa_grid fine, int width, int32_t *win_first, void *stream);
+
+/*
+ * Windowed fine scan (FP32 path with FP64 near-null refinement, M <= 16) and merged peaks.
+ *   B: batch x (M*M) complex128 factors (row b: M x K[b], column-major, ld M), e.g. from
+ *      doa_problem.B_out. rows: NULL (rows 0..nrows-1) or nrows row indices.
+ *   full = 0: row b scans its windows [win_first[b*dmax+w], +width) of `fine`; full = 1: row b
+ *      scans the whole grid (the fallback and the plain full-grid method).
+ *   S: L uint32 scratch (phase table); Pwin: nrows x (full ? 1 : dmax) x (full ? L : width) floats
+ *      scratch (the window spectra, readable afterwards).
+ *   Peaks: interior local maxima of each window (the plateau rule of doa_peaks inside the window),
+ *      duplicates from overlapping windows merged, the d[b] largest (ties: lower index) written to
+ *      idx/val[b*dmax ..] as fine-grid indices in ascending order, count[b]. fallback[b]
+ *      (nullable) = 1 when fewer than d[b] peaks were found, or a window's maximum lies on its
+ *      first or last point with a value above the weakest selected peak (the spectrum rises
+ *      beyond the window above the d-th peak); the caller then rescans row b with full = 1.
+ */
+doa_status doa_scan_windows(const double *B, int M, const int32_t *K, const int32_t *d, const int32_t *rows,
+                            int nrows, int dmax, doa_grid fine, const int32_t *win_first, int width, int full,
+                            uint32_t *S, float *Pwin, int32_t *idx, float *val, int32_t *count,
+                            int32_t *fallback, void *stream);
 
 #ifdef __cplusplus
 }

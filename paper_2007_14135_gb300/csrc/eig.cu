@@ -362,6 +362,20 @@ __global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_batch_kernel(const u
     EigSmem<NP> &s = mats[j];
     const int M = pp.p.M, d = pp.p.d;
     int st = 0;
+    if (pp.p.features) {
+      // proposal-network input: upper triangle of R / tr(R), (re, im) pairs row by row
+      const double2 *R = reinterpret_cast<const double2 *>(ws + pp.r64_off);
+      double tr = 0.0;
+      for (int i = 0; i < M; ++i) tr += R[i * M + i].x;
+      const double inv = tr > 0.0 ? 1.0 / tr : 0.0;
+      for (int e = lane; e < M * (M + 1) / 2; e += T) {
+        int i = 0, rem = e;
+        while (rem >= M - i) { rem -= M - i; ++i; }
+        const double2 v = R[i * M + i + rem];
+        pp.p.features[2 * e] = (float)(v.x * inv);
+        pp.p.features[2 * e + 1] = (float)(v.y * inv);
+      }
+    }
     if (res[j] > 0) {
       sort_desc<NP>(M, s);
       if (pp.p.evals)
@@ -370,6 +384,7 @@ __global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_batch_kernel(const u
         const PlanJob &jb = jobs[pp.first_job + k];
         int e = build_factor<NP>(M, d, jb.alg, s, reinterpret_cast<double2 *>(ws + jb.B_off));
         if (e && !st) st = e;
+        if (k == 0 && pp.p.B_out) build_factor<NP>(M, d, jb.alg, s, reinterpret_cast<double2 *>(pp.p.B_out));
       }
     } else {
       st = -res[j];

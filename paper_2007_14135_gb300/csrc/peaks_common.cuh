@@ -1,0 +1,129 @@
+// Block-wide peak search and top-d selection shared by doa_peaks and the windowed scan.
+// A peak is the left end i of a maximal run [i..j] of equal values with 1 <= i, j <= L-2,
+// P[i-1] < P[i] and P[j+1] < P[j] (Table 2 Step-6). Each thread owns a contiguous chunk and keeps
+// its best kCache peaks in registers; d rounds of a block arg-max pick the winners, a thread
+// rescanning its chunk only when its cache runs dry.
+#pragma once
+
+#include <climits>
+
+#include "doa_internal.cuh"
+
+namespace doa {
+namespace pk {
+
+constexpr int kPeakThreads = 256;
+constexpr int kCache = 4;
+
+struct Cand {
+  float v;
+  int i;  // INT_MAX = none
+};
+
+inline __device__ bool better(const Cand &a, const Cand &b) {
+  if (a.i == INT_MAX) return false;
+  if (b.i == INT_MAX) return true;
+  return a.v > b.v || (a.v == b.v && a.i < b.i);
+}
+
+inline __device__ bool is_peak(const float *__restrict__ P, int L, int i, float v) {
+  if (!(P[i - 1] < v)) return false;
+  int j = i;
+  while (j + 1 <= L - 1 && P[j + 1] == v) ++j;
+  return j + 1 <= L - 1 && P[j + 1] < v;
+}
+
+// Fills cache with the best peaks of [c0, c1) that are worse than thr (thr.i == INT_MAX: any).
+// Returns whether more such peaks exist beyond the cache.
+inline __device__ bool fill(const float *__restrict__ P, int L, int c0, int c1, const Cand &thr, Cand (&cache)[kCache],
+                     int &n) {
+  n = 0;
+  bool more = false;
+  for (int i = c0; i < c1; ++i) {
+    float v = P[i];
+    if (!is_peak(P, L, i, v)) continue;
+    Cand c{v, i};
+    if (thr.i != INT_MAX && !better(thr, c)) continue;
+    if (n < kCache) {
+      int k = n++;
+      while (k > 0 && better(c, cache[k - 1])) {
+        cache[k] = cache[k - 1];
+        --k;
+      }
+      cache[k] = c;
+    } else if (better(c, cache[kCache - 1])) {
+      more = true;
+      int k = kCache - 1;
+      while (k > 0 && better(c, cache[k - 1])) {
+        cache[k] = cache[k - 1];
+        --k;
+      }
+      cache[k] = c;
+    } else {
+      more = true;
+    }
+  }
+  return more;
+}
+
+inline __device__ Cand block_best(Cand c, Cand *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    Cand o;
+    o.v = __shfl_down_sync(0xffffffffu, c.v, off);
+    o.i = __shfl_down_sync(0xffffffffu, c.i, off);
+    if (better(o, c)) c = o;
+  }
+  if (lane == 0) red[warp] = c;
+  __syncthreads();
+  if (warp == 0) {
+    c = lane < (kPeakThreads / 32) ? red[lane] : Cand{0.f, INT_MAX};
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      Cand o;
+      o.v = __shfl_down_sync(0xffffffffu, c.v, off);
+      o.i = __shfl_down_sync(0xffffffffu, c.i, off);
+      if (better(o, c)) c = o;
+    }
+    if (lane == 0) red[kPeakThreads / 32] = c;
+  }
+  __syncthreads();
+  Cand w = red[kPeakThreads / 32];
+  __syncthreads();
+  return w;
+}
+
+// Selects the d best peaks of P[0..L) (value descending, index ascending) into sel[0..n),
+// n returned (identical in every thread). All threads of the block must call it.
+__device__ __forceinline__ int select_top(const float *__restrict__ P, int L, int d, Cand *sel) {
+  __shared__ Cand red[kPeakThreads / 32 + 1];
+  const int interior = L - 2;
+  const int chunk = (interior + kPeakThreads - 1) / kPeakThreads;
+  const int c0 = 1 + threadIdx.x * chunk;
+  const int c1 = min(L - 1, c0 + chunk);
+  Cand cache[kCache];
+  int n = 0, head = 0;
+  const Cand none{0.f, INT_MAX};
+  bool more = fill(P, L, c0, c1, none, cache, n);
+  int nsel = 0;
+  for (int r = 0; r < d; ++r) {
+    Cand mine = head < n ? cache[head] : none;
+    Cand w = block_best(mine, red);
+    if (w.i == INT_MAX) break;
+    if (threadIdx.x == 0) sel[nsel] = w;
+    ++nsel;
+    if (mine.i == w.i) {
+      ++head;
+      if (head == n && more) {
+        more = fill(P, L, c0, c1, w, cache, n);
+        head = 0;
+      }
+    }
+  }
+  __syncthreads();
+  return nsel;
+}
+
+}  // namespace pk
+}  // namespace doa

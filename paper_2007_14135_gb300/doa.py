@@ -26,7 +26,8 @@ STAGE_NAMES = ("phase_tables", "covariance", "eig_noise_subspace", "scan", "peak
 # every symbol include/doa.h declares
 EXPORTS = ("doa_status_str", "doa_covariance", "doa_covariance_noalloc", "doa_noise_subspace", "doa_scan",
            "doa_peaks", "doa_batch_plan_bytes", "doa_batch_plan", "doa_solve_batch", "doa_mlp_workspace_bytes",
-           "doa_mlp_refresh", "doa_mlp_forward", "doa_mlp_backward", "doa_mlp_adam")
+           "doa_mlp_refresh", "doa_mlp_forward", "doa_mlp_backward", "doa_mlp_adam", "doa_synth_ula",
+           "doa_proposal_windows", "doa_scan_windows")
 
 
 class DoaError(RuntimeError):
@@ -45,7 +46,8 @@ class Problem(ctypes.Structure):
                 ("peak_val", ctypes.c_void_p), ("peak_count", ctypes.c_void_p),
                 ("evals", ctypes.c_void_p), ("grid", Grid), ("M", ctypes.c_int32),
                 ("N", ctypes.c_int32), ("ldx", ctypes.c_int32), ("d", ctypes.c_int32),
-                ("alg_mask", ctypes.c_uint32), ("prec", ctypes.c_int32)]
+                ("alg_mask", ctypes.c_uint32), ("prec", ctypes.c_int32), ("features", ctypes.c_void_p),
+                ("B_out", ctypes.c_void_p)]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -154,12 +156,13 @@ def doa_peaks(P: torch.Tensor, d: int, idx: torch.Tensor, val: torch.Tensor, cou
 # ------------------------------------------------------------------------------------ batch
 def make_problem(X: torch.Tensor, d: int, alg_mask: int, g: Grid, P: torch.Tensor, peak_idx: torch.Tensor,
                  peak_val: torch.Tensor, peak_count: torch.Tensor, evals: Optional[torch.Tensor] = None,
-                 prec: int = FP32) -> Problem:
+                 prec: int = FP32, features: Optional[torch.Tensor] = None,
+                 B_out: Optional[torch.Tensor] = None) -> Problem:
     """Descriptor of one problem; the tensors must outlive every solve that uses it."""
     assert X.dtype == torch.complex64 and X.dim() == 2 and X.stride(1) == 1
     M, N = X.shape
     return Problem(_dev(X), _dev(P), _dev(peak_idx), _dev(peak_val), _dev(peak_count), _dev(evals), g,
-                   M, N, X.stride(0), d, alg_mask, prec)
+                   M, N, X.stride(0), d, alg_mask, prec, _dev(features), _dev(B_out))
 
 
 class BatchPlan:
@@ -327,3 +330,43 @@ class Mlp:
                 if t is not None:
                     t.copy_(torch.from_numpy(arr.copy()).view_as(t))
         self.refresh()
+
+
+# ------------------------------------------------------------------------------------ proposal pipeline
+def _bind_proposal(lib_):
+    vp, i, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64
+    lib_.doa_synth_ula.argtypes = [i, i, i, vp, vp, i, vp, u64, u64, vp, vp]
+    lib_.doa_proposal_windows.argtypes = [vp, vp, i, i, i, Grid, i, vp, vp]
+    lib_.doa_scan_windows.argtypes = [vp, i, vp, vp, vp, i, i, Grid, vp, i, i, vp, vp, vp, vp, vp, vp, vp]
+    for n in ("doa_synth_ula", "doa_proposal_windows", "doa_scan_windows"):
+        getattr(lib_, n).restype = i
+
+
+def doa_synth_ula(d: torch.Tensor, angles: torch.Tensor, snr_db: torch.Tensor, M: int, N: int, seed: int,
+                  first_instance: int, X: torch.Tensor, stream=None) -> None:
+    """X[b] = A S + W for every row b (see include/doa.h). d int32 (B), angles float32 (B, dmax)."""
+    _bind_proposal(lib())
+    B, dmax = angles.shape
+    _check(lib().doa_synth_ula(B, M, N, _dev(d), _dev(angles), dmax, _dev(snr_db), seed, first_instance, _dev(X),
+                               _stream(stream)), "doa_synth_ula")
+
+
+def doa_proposal_windows(probs: torch.Tensor, d: torch.Tensor, fine: Grid, width: int, win_first: torch.Tensor,
+                         extra: int = 0, stream=None) -> None:
+    _bind_proposal(lib())
+    B, dmax = win_first.shape
+    _check(lib().doa_proposal_windows(_dev(probs), _dev(d), B, dmax, extra, fine, width, _dev(win_first),
+                                      _stream(stream)), "doa_proposal_windows")
+
+
+def doa_scan_windows(B: torch.Tensor, M: int, K: torch.Tensor, d: torch.Tensor, fine: Grid, S: torch.Tensor,
+                     Pwin: torch.Tensor, idx: torch.Tensor, val: torch.Tensor, count: torch.Tensor,
+                     win_first: Optional[torch.Tensor] = None, width: int = 0, full: bool = False,
+                     rows: Optional[torch.Tensor] = None, nrows: Optional[int] = None,
+                     fallback: Optional[torch.Tensor] = None, stream=None) -> None:
+    _bind_proposal(lib())
+    dmax = idx.shape[1]
+    n = nrows if nrows is not None else (rows.numel() if rows is not None else idx.shape[0])
+    _check(lib().doa_scan_windows(_dev(B), M, _dev(K), _dev(d), _dev(rows), n, dmax, fine, _dev(win_first), width,
+                                  1 if full else 0, _dev(S), _dev(Pwin), _dev(idx), _dev(val), _dev(count),
+                                  _dev(fallback), _stream(stream)), "doa_scan_windows")

@@ -293,3 +293,20 @@ def uneven_batch_parallel(specs: Sequence[ProblemSpec], workers: Optional[int] =
         shm.close()
         shm.unlink()
     return buf, offsets
+
+
+def proposal_params(count: int, seed: int, dmax: int = 6):
+    """Per-instance parameters of the learned-proposal workload, vectorised: d in U{1..6},
+    angles U[-80, 80] with 3 deg separation (spacing transform), SNR U[-5, 20] dB.
+    Returns (d int32 (count,), angles float32 (count, dmax) zero-padded, snr float32 (count,))."""
+    rng = _rng(seed)
+    d = rng.integers(1, dmax + 1, size=count).astype(np.int32)
+    lo, hi, sep = -80.0, 80.0, 3.0
+    u = rng.uniform(0.0, 1.0, size=(count, dmax))
+    span = (hi - lo) - (d - 1) * sep                          # per-row room for the sorted uniforms
+    mask = np.arange(dmax)[None, :] < d[:, None]
+    u = np.where(mask, u * span[:, None], np.inf)
+    u = np.sort(u, axis=1)
+    ang = np.where(mask, lo + u + sep * np.arange(dmax)[None, :], 0.0).astype(np.float32)
+    snr = rng.uniform(-5.0, 20.0, size=count).astype(np.float32)
+    return d, ang, snr
