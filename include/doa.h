@@ -260,7 +260,7 @@ doa_status doa_mlp_adam(const doa_mlp *net, float lr, float beta1, float beta2, 
  * al., SC'11) with key = seed and counter = (snapshot, instance, instance >> 32, draw), instance =
  * first_instance + b; normals by Box-Muller. The per-instance source count d[b] <= 16, angles
  * (degrees, row b holds d[b] of dmax entries) and SNR are device inputs.
- *   X: batch x M x N complex64 (row-major per instance). batch <= 65535, M <= 64.
+ *   X: batch x M x N complex64 (row-major per instance). M <= 64.
  */
 doa_status doa_synth_ula(int batch, int M, int N, const int32_t *d, const float *angles_deg, int dmax,
                          const float *snr_db, uint64_t seed, uint64_t first_instance, float *X,

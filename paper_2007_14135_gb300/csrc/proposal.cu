@@ -308,12 +308,15 @@ using namespace doa;
 extern "C" doa_status doa_synth_ula(int batch, int M, int N, const int32_t *d, const float *angles_deg, int dmax,
                                     const float *snr_db, uint64_t seed, uint64_t first_instance, float *X,
                                     void *stream) {
-  if (batch < 1 || batch > 65535 || M < 2 || M > kMaxM || N < 1 || dmax < 1 || dmax > kSynthMaxD || !d ||
-      !angles_deg || !snr_db || !X)
+  if (batch < 1 || M < 2 || M > kMaxM || N < 1 || dmax < 1 || dmax > kSynthMaxD || !d || !angles_deg || !snr_db || !X)
     return DOA_EINVAL;
-  dim3 grid((N + 255) / 256, batch);
-  synth_kernel<<<grid, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-      M, N, d, angles_deg, dmax, snr_db, seed, first_instance, reinterpret_cast<float2 *>(X));
+  for (int b0 = 0; b0 < batch; b0 += 65535) {   // grid.y holds at most 65535 instances per launch
+    const int nb = batch - b0 < 65535 ? batch - b0 : 65535;
+    dim3 grid((N + 255) / 256, nb);
+    synth_kernel<<<grid, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        M, N, d + b0, angles_deg + (size_t)b0 * dmax, dmax, snr_db + b0, seed, first_instance + (uint64_t)b0,
+        reinterpret_cast<float2 *>(X) + (size_t)b0 * M * N);
+  }
   return cudaGetLastError() == cudaSuccess ? DOA_OK : DOA_ECUDA;
 }
 

@@ -185,3 +185,38 @@ def full_grid(sol: Solved, rows_chunk: int = 8192, device: str = "cuda"):
         del P
     torch.cuda.synchronize()
     return idx.cpu().numpy(), cnt.cpu().numpy(), time.perf_counter() - t0
+
+
+class TestSet:
+    """A resident batch of proposal-workload instances with a reusable plan: solve() runs the
+    covariance, Jacobi, features and MUSIC factor for every instance (3-point dummy grid: the
+    spectrum is produced later, by the windows or by the full-grid scan)."""
+
+    def __init__(self, count: int, seed: int = TEST_SEED, device: str = "cuda"):
+        self.d_np, self.ang, self.snr = synth.proposal_params(count, seed)
+        n = count
+        self.n = n
+        self.device = device
+        self.d = torch.from_numpy(self.d_np).to(device)
+        self.X = torch.empty((n, M, N_SNAP), dtype=torch.complex64, device=device)
+        doa.doa_synth_ula(self.d, torch.from_numpy(self.ang).to(device), torch.from_numpy(self.snr).to(device), M,
+                          N_SNAP, seed, 0, self.X)
+        g = doa.grid(-90.0, 90.0, 3)
+        self.P = torch.empty((n, 3), dtype=torch.float32, device=device)
+        self.idx = torch.empty((n, DMAX), dtype=torch.int32, device=device)
+        self.val = torch.empty((n, DMAX), dtype=torch.float32, device=device)
+        self.cnt = torch.empty(n, dtype=torch.int32, device=device)
+        self.features = torch.empty((n, M * (M + 1)), dtype=torch.float32, device=device)
+        self.B = torch.zeros((n, M * M), dtype=torch.complex128, device=device)
+        probs = [doa.make_problem(self.X[i], int(self.d_np[i]), 1 << doa.MUSIC, g, self.P[i], self.idx[i], self.val[i],
+                                  self.cnt[i:i + 1], features=self.features[i], B_out=self.B[i]) for i in range(n)]
+        self.plan = doa.BatchPlan(probs, device=device)
+        self.ws = doa.workspace(self.plan, device=device)
+        self.status = torch.empty(n, dtype=torch.int32, device=device)
+        self.K = torch.from_numpy((M - self.d_np).astype(np.int32)).to(device)
+
+    def solve(self):
+        doa.doa_solve_batch(self.plan, self.ws, self.status)
+
+    def solved(self) -> Solved:
+        return Solved(self.features, self.B, self.K, self.d, self.idx, self.cnt)
