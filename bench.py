@@ -241,8 +241,11 @@ def run_gpu(args):
     # ---- roofline of the dominant stage
     peaks_json = load_peaks()
     hbm_peak = peaks_json.get("hbm_gbs", 6800.0)
-    K = {0: 1, 1: M - D, 2: M - D, 3: 1}
-    scan_flops = B * L * sum(K[a] * (8 * M + 4) for a in ALGS)
+    # one shared contraction per problem: E_n (M - D columns) read by PHD / MUSIC / EV, plus the
+    # MN column; per point 8M + 4 flops per column (complex MACs and |y|^2) and 3 per E_n column
+    # for the MUSIC sum and the EV weighted sum (steering generation not counted)
+    Kf = (M - D) + 1
+    scan_flops = B * L * (Kf * (8 * M + 4) + 3 * (M - D))
     cov_bytes = B * (8 * M * N_SNAP + 16 * M * M)
     stage_info = {}
     names = doa.STAGE_NAMES

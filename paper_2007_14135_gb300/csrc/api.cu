@@ -16,7 +16,24 @@ inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline doa_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DOA_OK : DOA_ECUDA; }
 
-inline int factor_width(int alg, int M, int d) { return (alg == DOA_PHD || alg == DOA_MN) ? 1 : M - d; }
+// Columns of a problem's scan factor F (see PlanProblem): E_n when MUSIC or EV is requested (PHD
+// then reads its last column), else v_min for PHD; plus valph for MN.
+void factor_layout(const doa_problem &p, PlanProblem &q) {
+  const unsigned m = p.alg_mask;
+  const bool en = (m >> DOA_MUSIC) & 1u || (m >> DOA_EV) & 1u;
+  int k = 0;
+  q.Kn = 0;
+  q.kphd = q.kmn = -1;
+  if (en) {
+    q.Kn = p.M - p.d;
+    k = q.Kn;
+    if ((m >> DOA_PHD) & 1u) q.kphd = q.Kn - 1;
+  } else if ((m >> DOA_PHD) & 1u) {
+    q.kphd = k++;
+  }
+  if ((m >> DOA_MN) & 1u) q.kmn = k++;
+  q.Kf = k;
+}
 
 bool grid_ok(const doa_grid &g) {
   return g.L >= 3 && g.L <= (1 << 30) && std::isfinite(g.lo_deg) && std::isfinite(g.step_deg) &&
@@ -59,9 +76,8 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
     sz.ncov += chunks;
     sz.nreduce += chunks > 1;
     sz.eig[m_bucket(p.M)] += 1;
-    int nalg = __builtin_popcount(p.alg_mask);
-    sz.njobs += nalg;
-    sz.scan[m_bucket(p.M)] += nalg;
+    sz.njobs += __builtin_popcount(p.alg_mask);
+    sz.scan[m_bucket(p.M)] += 1;
     int g = -1;
     for (size_t k = 0; k < grids.size(); ++k)
       if (same_grid(grids[k], p.grid)) {
@@ -220,7 +236,7 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const int32_t *sc
     h.off_eig[b] = o.eig[b];
     h.off_scan[b] = o.scan[b];
   }
-  // workspace: per-grid phase tables, then per-problem R and partials, then per-job factors
+  // workspace: per-grid phase and sine tables, then per problem R, partials and scan factor
   int64_t ws = 0;
   for (int g = 0; g < sz.ngrids; ++g) {
     pg[g].lo = grids[g].lo_deg;
@@ -228,6 +244,8 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const int32_t *sc
     pg[g].L = grids[g].L;
     pg[g].S_off = ws;
     ws = round_up(ws + (int64_t)grids[g].L * 4, 256);
+    pg[g].sin_off = ws;
+    ws = round_up(ws + (int64_t)grids[g].L * 8, 256);
     h.grid_points += grids[g].L;
   }
   int icov = 0, ired = 0, ijob = 0;
@@ -252,22 +270,22 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const int32_t *sc
     q.grid_id = grid_of[i];
     q.first_job = ijob;
     int slot = 0;
-    const int tp = kScanThreads * pt[b];
     for (int a = 0; a < 4; ++a) {
+      q.slot[a] = -1;
       if (!((p.alg_mask >> a) & 1u)) continue;
-      PlanJob &j = jobs[ijob];
+      PlanJob &j = jobs[ijob++];
       j.prob = i;
       j.alg = a;
-      j.slot = slot++;
-      j.K = factor_width(a, M, p.d);
-      j.B_off = ws;
-      ws = round_up(ws + mm, 256);
-      j.tile_start = tiles[b];
-      tiles[b] += (p.grid.L + tp - 1) / tp;
-      scan[b][is[b]++] = ijob;
-      ++ijob;
+      j.slot = q.slot[a] = slot++;
     }
     q.njobs = slot;
+    factor_layout(p, q);
+    q.fac_off = ws;
+    ws = round_up(ws + factor_bytes(M), 256);
+    const int tp = kScanThreads * pt[b];
+    q.tile_start = tiles[b];
+    tiles[b] += (p.grid.L + tp - 1) / tp;
+    scan[b][is[b]++] = i;
   }
   for (int b = 0; b < kNumBuckets; ++b) {
     h.eig_count[b] = sz.eig[b];

@@ -31,11 +31,13 @@ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -
 // (the wrap of 2^32 is a whole number of turns), so the phase error is that of one rounding
 // of s_k (<= 2^-32 half turns), independent of m.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t grid_phase_step(double lo, double step, int k) {
-  double theta = __dadd_rn(lo, __dmul_rn((double)k, step));
-  double s = sin(theta * 0.017453292519943295);  // pi/180
+__device__ __forceinline__ uint32_t phase_step_of_sin(double s) {
   long long q = __double2ll_rn(s * 2147483648.0);
   return (uint32_t)q;
+}
+__device__ __forceinline__ uint32_t grid_phase_step(double lo, double step, int k) {
+  double theta = __dadd_rn(lo, __dmul_rn((double)k, step));
+  return phase_step_of_sin(sin(theta * 0.017453292519943295));  // pi/180
 }
 
 // exp(j*pi*phi*2^-31) for a 32-bit phase phi (a fraction of a full turn: 2^32 = 2 pi).
@@ -82,19 +84,26 @@ struct PlanProblem {
   doa_problem p;          // the caller's descriptor
   int64_t r64_off;        // byte offset of R (M x M complex128) in the workspace
   int64_t part_off;       // byte offset of the covariance partials (nchunks x M x M complex128)
+  int64_t fac_off;        // byte offset of the scan factor F (M x (M+1) complex128 capacity,
+                          // column-major) followed by the EV weights (M doubles)
+  int64_t tile_start;     // first scan tile of this problem within its bucket's tile range
   int32_t nchunks;        // covariance work items of this problem
   int32_t first_job;      // first (problem, algorithm) job
   int32_t njobs;
   int32_t grid_id;        // index of the problem's phase table
+  int32_t Kf, Kn;         // factor columns; columns read by MUSIC / EV (E_n), 0 if neither
+  int32_t kphd, kmn;      // columns read by PHD (v_min) and MN (valph), -1 if absent
+  int32_t slot[4];        // output row of each algorithm (doa_alg order), -1 if not requested
 };
 
-struct PlanJob {
-  int64_t B_off;          // byte offset of B (M x M capacity, complex128, column-major)
-  int64_t tile_start;     // first scan tile of this job within its bucket's tile range
+// Bytes of a problem's scan factor area: F (M x (M+1) complex128) + EV weights (M doubles).
+__host__ __device__ inline int64_t factor_bytes(int M) { return (int64_t)M * (M + 1) * 16 + (int64_t)M * 8; }
+
+struct PlanJob {          // one (problem, algorithm) pair: a spectrum and its peaks
   int32_t prob;
   int32_t alg;
   int32_t slot;           // position of the algorithm among the problem's algorithms
-  int32_t K;
+  int32_t pad;
 };
 
 struct PlanGrid {
@@ -102,6 +111,7 @@ struct PlanGrid {
   int32_t L;
   int32_t pad;
   int64_t S_off;          // byte offset of the phase table (L x uint32) in the workspace
+  int64_t sin_off;        // byte offset of sin(theta_k) (L x double) in the workspace
 };
 
 struct PlanCovItem {
@@ -114,7 +124,7 @@ struct PlanHeader {
   int32_t nprob, njobs, ngrids, ncov;
   int32_t nreduce;                       // problems with more than one covariance chunk
   int32_t eig_count[kNumBuckets];        // problems per M bucket
-  int32_t scan_jobs[kNumBuckets];        // jobs per M bucket
+  int32_t scan_jobs[kNumBuckets];        // scan jobs (problems) per M bucket
   int64_t scan_tiles[kNumBuckets];       // scan tiles per M bucket
   int32_t scan_pt[kNumBuckets];          // grid points per scan thread, per M bucket
   int64_t grid_points;                   // sum of L over distinct grids

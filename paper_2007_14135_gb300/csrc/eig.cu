@@ -1,5 +1,7 @@
 // Steps 2-4 (Table 2 Step-2, Table 3): Hermitian eigendecomposition of R by FP64 cyclic Jacobi,
-// followed by the noise-subspace factor B of each algorithm's weighting matrix C = B B^H.
+// followed by the noise-subspace factor B of each algorithm's weighting matrix C = B B^H (one
+// call), or, in the batch, one scan factor per problem from which every requested algorithm's
+// spectrum is read (E_n with EV weights 1/lambda, v_min, valph).
 //
 // Jacobi (Golub & Van Loan, Sec. 8.5, with a phase factor for complex Hermitian matrices):
 // for a pair (p, q) with a_pq = |a_pq| e^{j phi}, tau = (a_qq - a_pp) / (2 |a_pq|),
@@ -301,6 +303,37 @@ __device__ int build_factor(int M, int d, int alg, EigSmem<NP> &s, double2 *__re
   return 0;
 }
 
+// Writes a batch problem's scan factor F (columns as laid out by the plan: E_n, or v_min; then
+// valph) and the EV weights w_c = 1 / lambda_{d+c}; returns 0 or a doa_status.
+template <int NP>
+__device__ int build_scan_factor(const PlanProblem &pp, EigSmem<NP> &s, double2 *__restrict__ F,
+                                 double *__restrict__ w) {
+  constexpr int T = grp_threads<NP>();
+  using g = Grp<T>;
+  const int lane = g::id();
+  const int M = pp.p.M, d = pp.p.d;
+  int st = 0;
+  if (pp.Kn > 0) {
+    build_factor<NP>(M, d, DOA_MUSIC, s, F);
+    if (pp.slot[DOA_EV] >= 0) {
+      bool bad = false;
+      for (int c = lane; c < pp.Kn; c += T) {
+        const double l = s.lam[s.order[d + c]];
+        bad = bad || !(l > 0.0);
+        w[c] = l > 0.0 ? 1.0 / l : 0.0;
+      }
+      if (g::any(bad)) st = DOA_ERANK;
+    }
+  } else if (pp.kphd >= 0) {
+    build_factor<NP>(M, d, DOA_PHD, s, F + (size_t)pp.kphd * M);
+  }
+  if (pp.kmn >= 0) {
+    const int e = build_factor<NP>(M, d, DOA_MN, s, F + (size_t)pp.kmn * M);
+    if (e && !st) st = e;
+  }
+  return st;
+}
+
 template <int NP>
 __global__ void __launch_bounds__(grp_threads<NP>()) eig_single_kernel(const double2 *R64, int M, int d, int alg, double *evals,
                                                        double2 *B, int *K_out, int *info) {
@@ -376,24 +409,19 @@ __global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_batch_kernel(const u
         pp.p.features[2 * e + 1] = (float)(v.y * inv);
       }
     }
+    double2 *F = reinterpret_cast<double2 *>(ws + pp.fac_off);
+    double *w = reinterpret_cast<double *>(F + (size_t)M * (M + 1));
     if (res[j] > 0) {
       sort_desc<NP>(M, s);
       if (pp.p.evals)
         for (int i = lane; i < M; i += T) pp.p.evals[i] = s.lam[s.order[i]];
-      for (int k = 0; k < pp.njobs; ++k) {
-        const PlanJob &jb = jobs[pp.first_job + k];
-        int e = build_factor<NP>(M, d, jb.alg, s, reinterpret_cast<double2 *>(ws + jb.B_off));
-        if (e && !st) st = e;
-        if (k == 0 && pp.p.B_out) build_factor<NP>(M, d, jb.alg, s, reinterpret_cast<double2 *>(pp.p.B_out));
-      }
+      st = build_scan_factor<NP>(pp, s, F, w);
+      if (pp.p.B_out) build_factor<NP>(M, d, jobs[pp.first_job].alg, s, reinterpret_cast<double2 *>(pp.p.B_out));
     } else {
       st = -res[j];
-      // a failed decomposition leaves zero factors, so the scan writes the 1/FLT_MIN sentinel
-      for (int k = 0; k < pp.njobs; ++k) {
-        const PlanJob &jb = jobs[pp.first_job + k];
-        double2 *B = reinterpret_cast<double2 *>(ws + jb.B_off);
-        for (int e = lane; e < M * jb.K; e += T) B[e] = make_double2(0.0, 0.0);
-      }
+      // a failed decomposition leaves a zero factor, so the scan writes the 1/FLT_MIN sentinel
+      for (int e = lane; e < M * pp.Kf; e += T) F[e] = make_double2(0.0, 0.0);
+      for (int e = lane; e < pp.Kn; e += T) w[e] = 0.0;
     }
     if (lane == 0) status[prob[j]] = st;
     Grp<T>::sync();

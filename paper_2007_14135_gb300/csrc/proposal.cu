@@ -164,17 +164,22 @@ __global__ void __launch_bounds__(kScanThreads) scan_windows_kernel(const double
   const int first = full ? 0 : win_first[(size_t)r * dmax + w];
   if (first < 0) return;
   const int len = full ? L : min(width, L - first);
-  const double2 *Br = B + (size_t)r * M * M;
-  const int Kr = K[r];
-  load_factor<MP>(Br, M, Kr, Bs);
+  ScanJob j{};
+  j.F = B + (size_t)r * M * M;
+  j.P[kRoMusic] = Pwin + ((size_t)slot * nw + w) * (size_t)(full ? L : width);
+  j.lo = lo;
+  j.step = step;
+  j.M = M;
+  j.Kf = j.Kn = K[r];
+  j.kphd = j.kmn = -1;
+  j.kofs = first;
+  load_job<MP>(j, Bs, sh);
   __syncthreads();
-  set_threshold<MP>(Bs, Kr, sh);
+  set_threshold<MP>(Bs, j, sh);
   __syncthreads();
-  float *P = Pwin + ((size_t)slot * nw + w) * (size_t)(full ? L : width);
-  const RefineCtx rc{Br, M, Kr, lo, step, first};
   const int k0 = (tile * kScanThreads + threadIdx.x) * PT;
-  scan_points<MP, PT>(Bs, Kr, S + first, P, len, k0, rc, sh);
-  drain_refinements(rc, P, sh);
+  scan_points<MP, PT>(Bs, j, S + first, len, k0, sh);
+  drain_refinements(j, sh);
 }
 
 // Peaks of one row's windows, merged: the d best peaks of each window (the plateau rule of

@@ -4,16 +4,22 @@
 // Fused, on CUDA cores in FP32: every thread evaluates PT consecutive grid points. For each it
 // generates the M steering phasors in registers from the grid's 32-bit phase step S_k
 // (phase of element m = m*S_k mod 2^32, exact integer arithmetic; phasor_q32 turns a phase into
-// cos + j sin), contracts them with the noise factor B (held in shared memory as FP32, read as
-// warp-wide broadcasts) one column at a time, accumulates |y_k|^2, and stores 1/den with
-// vectorised stores. The whole block of PT x M phasors is reused across the K columns of B.
+// cos + j sin), contracts them with the factor (held in shared memory as FP32, read as
+// warp-wide broadcasts) one column at a time, and forms the readouts of scan_common.cuh. The
+// whole block of PT x M phasors is reused across the columns.
+//
+// Batched: one scan job per problem. A problem that asks for MUSIC or EV contracts its noise
+// eigenvectors E_n once and reads MUSIC, EV and PHD (v_min is the last column of E_n) from the
+// same column outputs, plus one extra column for MN (valph); PHD / MN alone contract one column
+// each. All four of Table 3's spectra of one problem therefore share one steering generation.
 //
 // Near-null refinement: where the FP32 denominator is small its relative error grows (the
-// contraction cancels), so every point with den < kRefineC * E, E = sum_k (sum_m |b_mk|)^2, is
-// re-evaluated in FP64 from the grid angle (theta_k, sin theta_k and the phasors in FP64) and the
-// FP64 factor. Flagged points of a tile are queued in shared memory and each is then handled by a
-// whole warp (lanes own phasors, then columns of B), so the FP64 work runs without divergence.
-// With per-term FP32 errors below ~4 eps the FP32 result elsewhere stays within ~5e-4 relative.
+// contraction cancels), so every point with den_r < kRefineC * E_r for some readout r is
+// re-evaluated in FP64 from the grid angle (sin theta_k in FP64 from a per-grid table in the
+// batch, else recomputed) and the FP64 factor, for all readouts of the job. Flagged points of a
+// tile are queued in shared memory and each is then handled by a whole warp (lanes own phasors,
+// then elements of columns), so the FP64 work runs without divergence. With per-term FP32
+// errors below ~4 eps the FP32 result elsewhere stays within ~5e-4 relative.
 #include <float.h>
 
 #include "doa_internal.cuh"
@@ -33,8 +39,13 @@ __global__ void grid_table_batch_kernel(const uint8_t *plan, uint8_t *ws) {
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
   const PlanGrid g = reinterpret_cast<const PlanGrid *>(plan + h->off_grid)[blockIdx.y];
   uint32_t *S = reinterpret_cast<uint32_t *>(ws + g.S_off);
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.L; k += gridDim.x * blockDim.x)
-    S[k] = grid_phase_step(g.lo, g.step, k);
+  double *sn = reinterpret_cast<double *>(ws + g.sin_off);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.L; k += gridDim.x * blockDim.x) {
+    const double theta = __dadd_rn(g.lo, __dmul_rn((double)k, g.step));
+    const double s = sin(theta * 0.017453292519943295);
+    sn[k] = s;
+    S[k] = phase_step_of_sin(s);
+  }
 }
 
 template <int MP, int PT>
@@ -42,55 +53,72 @@ __global__ void __launch_bounds__(kScanThreads) scan_single_kernel(const double2
                                                                    double step, const uint32_t *S, float *P) {
   __shared__ __align__(16) float2 Bs[MP * MP];
   __shared__ ScanShared sh;
-  load_factor<MP>(B, M, K, Bs);
+  ScanJob j{};
+  j.F = B;
+  j.P[kRoMusic] = P;
+  j.lo = lo;
+  j.step = step;
+  j.M = M;
+  j.Kf = K;
+  j.Kn = K;
+  j.kphd = j.kmn = -1;
+  load_job<MP>(j, Bs, sh);
   __syncthreads();
-  set_threshold<MP>(Bs, K, sh);
+  set_threshold<MP>(Bs, j, sh);
   __syncthreads();
-  const RefineCtx rc{B, M, K, lo, step, 0};
   const int k0 = (blockIdx.x * kScanThreads + threadIdx.x) * PT;
-  scan_points<MP, PT>(Bs, K, S, P, L, k0, rc, sh);
-  drain_refinements(rc, P, sh);
+  scan_points<MP, PT>(Bs, j, S, L, k0, sh);
+  drain_refinements(j, sh);
 }
 
-// Persistent batched scan over the tiles of the jobs of one M bucket. Tiles are striped over
-// the CTAs; the job of a tile is found by binary search on the jobs' first tiles.
+// Persistent batched scan over the tiles of the problems of one M bucket. Tiles are striped over
+// the CTAs; the problem of a tile is found by binary search on the problems' first tiles.
 template <int MP, int PT>
 __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t *plan, uint8_t *ws, int bucket) {
-  __shared__ __align__(16) float2 Bs[MP * MP];
+  __shared__ __align__(16) float2 Bs[(MP + 1) * MP];
   __shared__ ScanShared sh;
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
-  const int njobs = h->scan_jobs[bucket];
+  const int nunits = h->scan_jobs[bucket];
   const int64_t ntiles = h->scan_tiles[bucket];
   const int32_t *list = reinterpret_cast<const int32_t *>(plan + h->off_scan[bucket]);
-  const PlanJob *jobs = reinterpret_cast<const PlanJob *>(plan + h->off_job);
   const PlanProblem *probs = reinterpret_cast<const PlanProblem *>(plan + h->off_prob);
   const PlanGrid *grids = reinterpret_cast<const PlanGrid *>(plan + h->off_grid);
   constexpr int TP = kScanThreads * PT;
   int cur = -1;
+  ScanJob j{};
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    int lo = 0, hi = njobs - 1;
-    while (lo < hi) {  // last job with tile_start <= t
+    int lo = 0, hi = nunits - 1;
+    while (lo < hi) {  // last problem with tile_start <= t
       int mid = (lo + hi + 1) >> 1;
-      if (jobs[list[mid]].tile_start <= t) lo = mid; else hi = mid - 1;
+      if (probs[list[mid]].tile_start <= t) lo = mid; else hi = mid - 1;
     }
-    const PlanJob &jb = jobs[list[lo]];
-    const PlanProblem &pp = probs[jb.prob];
-    const double2 *B64 = reinterpret_cast<const double2 *>(ws + jb.B_off);
+    const PlanProblem &pp = probs[list[lo]];
+    const PlanGrid &g = grids[pp.grid_id];
     if (lo != cur) {
+      j.F = reinterpret_cast<const double2 *>(ws + pp.fac_off);
+      j.w = pp.Kn > 0 && pp.slot[DOA_EV] >= 0 ? reinterpret_cast<const double *>(ws + pp.fac_off) + 2 * pp.p.M * (pp.p.M + 1)
+                                              : nullptr;
+      j.sin64 = reinterpret_cast<const double *>(ws + g.sin_off);
+      for (int r = 0; r < 4; ++r) j.P[r] = pp.slot[r] >= 0 ? pp.p.P + (size_t)pp.slot[r] * g.L : nullptr;
+      j.lo = g.lo;
+      j.step = g.step;
+      j.M = pp.p.M;
+      j.Kf = pp.Kf;
+      j.Kn = pp.Kn;
+      j.kphd = pp.kphd;
+      j.kmn = pp.kmn;
+      j.kofs = 0;
       __syncthreads();
-      load_factor<MP>(B64, pp.p.M, jb.K, Bs);
+      load_job<MP>(j, Bs, sh);
       __syncthreads();
-      set_threshold<MP>(Bs, jb.K, sh);
+      set_threshold<MP>(Bs, j, sh);
       __syncthreads();
       cur = lo;
     }
-    const PlanGrid &g = grids[pp.grid_id];
     const uint32_t *S = reinterpret_cast<const uint32_t *>(ws + g.S_off);
-    float *P = pp.p.P + (size_t)jb.slot * g.L;
-    const RefineCtx rc{B64, pp.p.M, jb.K, g.lo, g.step, 0};
-    const int k0 = (int)(t - jb.tile_start) * TP + threadIdx.x * PT;
-    scan_points<MP, PT>(Bs, jb.K, S, P, g.L, k0, rc, sh);
-    drain_refinements(rc, P, sh);
+    const int k0 = (int)(t - pp.tile_start) * TP + threadIdx.x * PT;
+    scan_points<MP, PT>(Bs, j, S, g.L, k0, sh);
+    drain_refinements(j, sh);
   }
 }
 

@@ -1,4 +1,14 @@
 // Device pieces of the CUDA-core FP32 scan shared by the full-grid, batched and windowed scans.
+//
+// One scan job contracts the steering vectors with the Kf columns f_k of a factor F and turns the
+// column outputs y_k = f_k^H a into up to four pseudospectra ("readouts", Table 3):
+//   MUSIC  den = sum_{k<Kn} |y_k|^2                 (F[:, :Kn] = E_n)
+//   EV     den = sum_{k<Kn} w_k |y_k|^2, w_k = 1/lambda_k   (E_n Lambda_n^-1 E_n^H)
+//   PHD    den = |y_kphd|^2                         (column kphd = v_min)
+//   MN     den = |y_kmn|^2                          (column kmn = valph = P_n e1 / (e1^H P_n e1))
+// so a problem that asks for several algorithms generates its steering vectors once and
+// contracts the noise eigenvectors once. A single-factor scan (doa_scan) is the MUSIC readout
+// with F = B, Kn = K.
 #pragma once
 
 #include <float.h>
@@ -8,182 +18,307 @@
 namespace doa {
 namespace scanc {
 
-// B (M x K complex128, column-major, ld M) -> Bs[k][m] (FP32, rows m >= M zero-padded to MP).
+constexpr float kRefineC = 3.7e-6f;   // (4 * 4 eps32 / 5e-4)^2
+constexpr int kFlagCap = 256;          // queued refinements per tile (overflow: refined in place)
+constexpr int kScanWarps = kScanThreads / 32;
+constexpr int kMaxCols = kMaxM + 1;    // E_n (up to M columns when d = 0) plus valph
+
+// Readout slots, in doa_alg order.
+constexpr int kRoPhd = 0, kRoMusic = 1, kRoEv = 2, kRoMn = 3;
+
+struct ScanJob {
+  const double2 *F;      // FP64 factor, column-major, ld M, Kf columns
+  const double *w;       // FP64 EV weights (Kn entries); null when EV is absent
+  const double *sin64;   // FP64 sin(theta) per local point, or null (computed from lo, step)
+  float *P[4];           // output row of each readout (local point index); null = absent
+  double lo, step;
+  int M, Kf, Kn, kphd, kmn;
+  int kofs;              // grid index of local point 0 (windowed scans)
+};
+
+struct ScanShared {
+  double2 ph[kScanWarps][kMaxM];      // per-warp FP64 phasors for refinement
+  double2 yb[kScanWarps][kMaxCols];   // per-warp FP64 column outputs for refinement
+  float w32[kMaxM];                   // FP32 EV weights
+  int flags[kFlagCap];
+  int nflag;
+  float thr[4];                       // per-readout refinement thresholds (-1: readout absent)
+};
+
+// F (M x Kf complex128, column-major, ld M) -> Bs[k][m] (FP32, rows m >= M zero-padded to MP);
+// EV weights -> sh.w32.
 template <int MP>
-__device__ __forceinline__ void load_factor(const double2 *__restrict__ B, int M, int K, float2 *Bs) {
-  for (int e = threadIdx.x; e < K * MP; e += blockDim.x) {
+__device__ __forceinline__ void load_job(const ScanJob &j, float2 *Bs, ScanShared &sh) {
+  for (int e = threadIdx.x; e < j.Kf * MP; e += blockDim.x) {
     int k = e / MP, m = e % MP;
     float2 v = make_float2(0.f, 0.f);
-    if (m < M) {
-      double2 b = B[(size_t)k * M + m];
+    if (m < j.M) {
+      double2 b = j.F[(size_t)k * j.M + m];
       v = make_float2((float)b.x, (float)b.y);
     }
     Bs[e] = v;
   }
+  for (int k = threadIdx.x; k < j.Kn; k += blockDim.x) sh.w32[k] = j.w ? (float)j.w[k] : 1.f;
 }
 
-constexpr float kRefineC = 3.7e-6f;   // (4 * 4 eps32 / 5e-4)^2
-constexpr int kFlagCap = 256;          // queued refinements per tile (overflow: refined in place)
-constexpr int kScanWarps = kScanThreads / 32;
-
-struct RefineCtx {
-  const double2 *B;   // FP64 factor, column-major, ld M
-  int M, K;
-  double lo, step;
-  int kofs;           // grid index of local point 0 (windowed scans)
-};
-
-struct ScanShared {
-  double2 ph[kScanWarps][kMaxM];   // per-warp FP64 phasors for refinement
-  int flags[kFlagCap];
-  int nflag;
-  float thr;
-};
-
-// E = sum_k (sum_m |b_mk|)^2 over the FP32 factor in shared memory; thr = kRefineC * E.
+// Threshold of readout r = kRefineC * E_r with s_k = sum_m |f_mk| (FP32 factor):
+// E_MUSIC = sum_{k<Kn} s_k^2, E_EV = sum_{k<Kn} w_k s_k^2, E_PHD = s_kphd^2, E_MN = s_kmn^2.
+// (A bound of ~4 eps per term on y_k gives den a relative error below ~5e-4 above it.)
 template <int MP>
-__device__ __forceinline__ void set_threshold(const float2 *Bs, int K, ScanShared &sh) {
+__device__ __forceinline__ void set_threshold(const float2 *Bs, const ScanJob &j, ScanShared &sh) {
   if (threadIdx.x < 32) {
-    float e = 0.f;
-    for (int k = threadIdx.x; k < K; k += 32) {
+    const int lane = threadIdx.x;
+    float em = 0.f, ee = 0.f;
+    for (int k = lane; k < j.Kf; k += 32) {
       float n1 = 0.f;
       for (int m = 0; m < MP; ++m) {
         float2 b = Bs[k * MP + m];
         n1 += sqrtf(b.x * b.x + b.y * b.y);
       }
-      e += n1 * n1;
+      const float e = n1 * n1;
+      if (k < j.Kn) {
+        em += e;
+        ee += sh.w32[k] * e;
+      }
+      if (k == j.kphd) sh.thr[kRoPhd] = kRefineC * e;
+      if (k == j.kmn) sh.thr[kRoMn] = kRefineC * e;
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
-    if (threadIdx.x == 0) {
-      sh.thr = kRefineC * e;
+    for (int off = 16; off > 0; off >>= 1) {
+      em += __shfl_xor_sync(0xffffffffu, em, off);
+      ee += __shfl_xor_sync(0xffffffffu, ee, off);
+    }
+    if (lane == 0) {
+      sh.thr[kRoMusic] = kRefineC * em;
+      sh.thr[kRoEv] = kRefineC * ee;
       sh.nflag = 0;
     }
   }
 }
 
-// FP64 re-evaluation of grid point k by one whole warp: lanes compute phasors m = lane, lane+32,
-// then each lane contracts whole columns k = lane, lane+32 of B; den is a warp sum.
-inline __device__ void refine_point_warp(const RefineCtx &c, int k, float *P, double2 *ph) {
+__device__ __forceinline__ double sin_of_point(const ScanJob &j, int k) {
+  if (j.sin64) return j.sin64[k];
+  const double theta = __dadd_rn(j.lo, __dmul_rn((double)(k + j.kofs), j.step));
+  return sin(theta * 0.017453292519943295);
+}
+
+__device__ __forceinline__ float recip_out(double den) { return 1.0f / (float)fmax(den, (double)FLT_MIN); }
+
+// FP64 re-evaluation of local point k by one whole warp. Lanes first compute the phasors
+// (m = lane, lane + 32), then contract: for M <= 32 the lanes form 32 / MQ groups of MQ >= M
+// lanes, each group one column per pass (lane = element), reduced by shuffles; for M > 32 every
+// lane takes two elements of one column per pass. Lane 0 forms the readouts.
+inline __device__ void refine_point_warp(const ScanJob &j, int k, double2 *ph, double2 *yb) {
   const int lane = threadIdx.x & 31;
-  const double theta = __dadd_rn(c.lo, __dmul_rn((double)(k + c.kofs), c.step));
-  const double s = sin(theta * 0.017453292519943295);
-  for (int m = lane; m < c.M; m += 32) {
+  const double s = sin_of_point(j, k);
+  for (int m = lane; m < j.M; m += 32) {
     double sn, cs;
     sincospi((double)m * s, &sn, &cs);
     ph[m] = make_double2(cs, sn);
   }
   __syncwarp();
-  double den = 0.0;
-  for (int col = lane; col < c.K; col += 32) {
-    double yr = 0.0, yi = 0.0;
-    const double2 *b = c.B + (size_t)col * c.M;
-    for (int m = 0; m < c.M; ++m) {
-      double2 bb = b[m], a = ph[m];
-      yr = fma(bb.x, a.x, fma(bb.y, a.y, yr));
-      yi = fma(bb.x, a.y, fma(-bb.y, a.x, yi));
+  const int M = j.M;
+  if (M <= 32) {
+    const int MQ = M <= 8 ? 8 : (M <= 16 ? 16 : 32);
+    const int m = lane & (MQ - 1), grp = lane / MQ, ngrp = 32 / MQ;
+    const double2 a = m < M ? ph[m] : make_double2(0.0, 0.0);
+    for (int c0 = 0; c0 < j.Kf; c0 += ngrp) {
+      const int col = c0 + grp;
+      double yr = 0.0, yi = 0.0;
+      if (col < j.Kf && m < M) {
+        const double2 b = j.F[(size_t)col * M + m];   // conj(b) * a
+        yr = fma(b.x, a.x, b.y * a.y);
+        yi = fma(b.x, a.y, -b.y * a.x);
+      }
+      for (int off = MQ >> 1; off > 0; off >>= 1) {
+        yr += __shfl_xor_sync(0xffffffffu, yr, off);
+        yi += __shfl_xor_sync(0xffffffffu, yi, off);
+      }
+      if (m == 0 && col < j.Kf) yb[col] = make_double2(yr, yi);
     }
-    den = fma(yr, yr, fma(yi, yi, den));
+  } else {
+    const double2 a0 = ph[lane];
+    const double2 a1 = lane + 32 < M ? ph[lane + 32] : make_double2(0.0, 0.0);
+    for (int col = 0; col < j.Kf; ++col) {
+      const double2 b0 = j.F[(size_t)col * M + lane];
+      const double2 b1 = lane + 32 < M ? j.F[(size_t)col * M + lane + 32] : make_double2(0.0, 0.0);
+      double yr = fma(b0.x, a0.x, b0.y * a0.y), yi = fma(b0.x, a0.y, -b0.y * a0.x);
+      yr = fma(b1.x, a1.x, fma(b1.y, a1.y, yr));
+      yi = fma(b1.x, a1.y, fma(-b1.y, a1.x, yi));
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        yr += __shfl_xor_sync(0xffffffffu, yr, off);
+        yi += __shfl_xor_sync(0xffffffffu, yi, off);
+      }
+      if (lane == 0) yb[col] = make_double2(yr, yi);
+    }
+  }
+  __syncwarp();
+  // MUSIC / EV sums over the lanes' columns
+  double dm = 0.0, de = 0.0;
+  for (int c = lane; c < j.Kn; c += 32) {
+    const double2 y = yb[c];
+    const double n = fma(y.x, y.x, y.y * y.y);
+    dm += n;
+    if (j.w) de = fma(j.w[c], n, de);
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) den += __shfl_xor_sync(0xffffffffu, den, off);
-  if (lane == 0) P[k] = (float)(1.0 / fmax(den, (double)FLT_MIN));
+  for (int off = 16; off > 0; off >>= 1) {
+    dm += __shfl_xor_sync(0xffffffffu, dm, off);
+    de += __shfl_xor_sync(0xffffffffu, de, off);
+  }
+  if (lane == 0) {
+    if (j.P[kRoMusic]) j.P[kRoMusic][k] = recip_out(dm);
+    if (j.P[kRoEv]) j.P[kRoEv][k] = recip_out(de);
+    if (j.P[kRoPhd]) {
+      const double2 y = yb[j.kphd];
+      j.P[kRoPhd][k] = recip_out(fma(y.x, y.x, y.y * y.y));
+    }
+    if (j.P[kRoMn]) {
+      const double2 y = yb[j.kmn];
+      j.P[kRoMn][k] = recip_out(fma(y.x, y.x, y.y * y.y));
+    }
+  }
   __syncwarp();
 }
 
 // Same computation by a single thread (only when a tile's queue overflows).
-inline __device__ void refine_point_thread(const RefineCtx &c, int k, float *P) {
-  const double theta = __dadd_rn(c.lo, __dmul_rn((double)(k + c.kofs), c.step));
-  const double s = sin(theta * 0.017453292519943295);
-  double den = 0.0;
-  for (int col = 0; col < c.K; ++col) {
+inline __device__ void refine_point_thread(const ScanJob &j, int k) {
+  const double s = sin_of_point(j, k);
+  double dm = 0.0, de = 0.0, dp = 0.0, dn = 0.0;
+  for (int col = 0; col < j.Kf; ++col) {
     double yr = 0.0, yi = 0.0;
-    for (int m = 0; m < c.M; ++m) {
+    for (int m = 0; m < j.M; ++m) {
       double sn, cs;
       sincospi((double)m * s, &sn, &cs);
-      double2 bb = c.B[(size_t)col * c.M + m];
-      yr = fma(bb.x, cs, fma(bb.y, sn, yr));
-      yi = fma(bb.x, sn, fma(-bb.y, cs, yi));
+      const double2 b = j.F[(size_t)col * j.M + m];
+      yr = fma(b.x, cs, fma(b.y, sn, yr));
+      yi = fma(b.x, sn, fma(-b.y, cs, yi));
     }
-    den = fma(yr, yr, fma(yi, yi, den));
+    const double n = fma(yr, yr, yi * yi);
+    if (col < j.Kn) {
+      dm += n;
+      if (j.w) de = fma(j.w[col], n, de);
+    }
+    if (col == j.kphd) dp = n;
+    if (col == j.kmn) dn = n;
   }
-  P[k] = (float)(1.0 / fmax(den, (double)FLT_MIN));
+  if (j.P[kRoMusic]) j.P[kRoMusic][k] = recip_out(dm);
+  if (j.P[kRoEv]) j.P[kRoEv][k] = recip_out(de);
+  if (j.P[kRoPhd]) j.P[kRoPhd][k] = recip_out(dp);
+  if (j.P[kRoMn]) j.P[kRoMn][k] = recip_out(dn);
 }
 
 // Drains the tile's refinement queue (all threads of the CTA call this).
-__device__ __forceinline__ void drain_refinements(const RefineCtx &c, float *P, ScanShared &sh) {
+__device__ __forceinline__ void drain_refinements(const ScanJob &j, ScanShared &sh) {
   __syncthreads();
   const int n = min(sh.nflag, kFlagCap);
   const int warp = threadIdx.x >> 5;
-  for (int i = warp; i < n; i += kScanWarps) refine_point_warp(c, sh.flags[i], P, sh.ph[warp]);
+  for (int i = warp; i < n; i += kScanWarps) refine_point_warp(j, sh.flags[i], sh.ph[warp], sh.yb[warp]);
   __syncthreads();
   if (threadIdx.x == 0) sh.nflag = 0;
   __syncthreads();
 }
 
-// Evaluates the PT points k0 .. k0+PT-1 (those < L) of one spectrum. S may alias P: each
-// thread reads its own phase steps before it writes its own outputs. Points below the
-// refinement threshold are queued for drain_refinements.
-template <int MP, int PT>
-__device__ __forceinline__ void scan_points(const float2 *Bs, int K, const uint32_t *S, float *P, int L, int k0,
-                                            const RefineCtx &rc, ScanShared &sh) {
-  float2 a[PT][MP];
-#pragma unroll
-  for (int j = 0; j < PT; ++j) {
-    uint32_t step = (k0 + j < L) ? S[k0 + j] : 0u;
-    uint32_t phi = 0u;
-#pragma unroll
-    for (int m = 0; m < MP; ++m) {
-      a[j][m] = phasor_q32(phi);
-      phi += step;
-    }
-  }
-  float den[PT];
-#pragma unroll
-  for (int j = 0; j < PT; ++j) den[j] = 0.f;
-  for (int k = 0; k < K; ++k) {
-    float yr[PT], yi[PT];
-#pragma unroll
-    for (int j = 0; j < PT; ++j) yr[j] = yi[j] = 0.f;
-#pragma unroll
-    for (int m = 0; m < MP; ++m) {
-      const float2 b = Bs[k * MP + m];
-#pragma unroll
-      for (int j = 0; j < PT; ++j) {
-        // conj(b) * a = (br ar + bi ai) + j (br ai - bi ar)
-        yr[j] = fmaf(b.x, a[j][m].x, fmaf(b.y, a[j][m].y, yr[j]));
-        yi[j] = fmaf(b.x, a[j][m].y, fmaf(-b.y, a[j][m].x, yi[j]));
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < PT; ++j) den[j] = fmaf(yr[j], yr[j], fmaf(yi[j], yi[j], den[j]));
-  }
-  float out[PT];
-  int pos[PT];
-  const float thr = sh.thr;
-#pragma unroll
-  for (int j = 0; j < PT; ++j) {
-    out[j] = 1.0f / fmaxf(den[j], FLT_MIN);
-    pos[j] = -1;
-    if (k0 + j < L && den[j] < thr) {
-      pos[j] = atomicAdd(&sh.nflag, 1);
-      if (pos[j] < kFlagCap) sh.flags[pos[j]] = k0 + j;
-    }
-  }
-  // vectorised store when the whole group is in range and aligned
+template <int PT>
+__device__ __forceinline__ void store_row(float *P, int L, int k0, const float (&out)[PT]) {
   if (PT == 4 && k0 + 3 < L && ((reinterpret_cast<uintptr_t>(P + k0) & 15u) == 0)) {
-    *reinterpret_cast<float4 *>(P + k0) = make_float4(out[0], out[1], out[2 % PT], out[3 % PT]);
+    *reinterpret_cast<float4 *>(P + k0) = make_float4(out[0], out[1 % PT], out[2 % PT], out[3 % PT]);
   } else if (PT == 2 && k0 + 1 < L && ((reinterpret_cast<uintptr_t>(P + k0) & 7u) == 0)) {
     *reinterpret_cast<float2 *>(P + k0) = make_float2(out[0], out[1 % PT]);
   } else {
 #pragma unroll
-    for (int j = 0; j < PT; ++j)
-      if (k0 + j < L) P[k0 + j] = out[j];
+    for (int q = 0; q < PT; ++q)
+      if (k0 + q < L) P[k0 + q] = out[q];
+  }
+}
+
+// Evaluates the local points k0 .. k0+PT-1 (those < L) of one job. S may alias a P row of a
+// single-readout job: each thread reads its own phase steps before it writes its own outputs.
+// Points where any readout falls below its refinement threshold are queued for drain_refinements.
+template <int MP, int PT>
+__device__ __forceinline__ void scan_points(const float2 *Bs, const ScanJob &j, const uint32_t *S, int L, int k0,
+                                            ScanShared &sh) {
+  float2 a[PT][MP];
+#pragma unroll
+  for (int q = 0; q < PT; ++q) {
+    uint32_t step = (k0 + q < L) ? S[k0 + q] : 0u;
+    uint32_t phi = 0u;
+#pragma unroll
+    for (int m = 0; m < MP; ++m) {
+      a[q][m] = phasor_q32(phi);
+      phi += step;
+    }
+  }
+  float dm[PT], de[PT], dp[PT], dn[PT];
+#pragma unroll
+  for (int q = 0; q < PT; ++q) dm[q] = de[q] = dp[q] = dn[q] = 0.f;
+  const int Kf = j.Kf, Kn = j.Kn, kphd = j.kphd, kmn = j.kmn;
+  for (int k = 0; k < Kf; ++k) {
+    float yr[PT], yi[PT];
+#pragma unroll
+    for (int q = 0; q < PT; ++q) yr[q] = yi[q] = 0.f;
+#pragma unroll
+    for (int m = 0; m < MP; ++m) {
+      const float2 b = Bs[k * MP + m];
+#pragma unroll
+      for (int q = 0; q < PT; ++q) {
+        // conj(b) * a = (br ar + bi ai) + j (br ai - bi ar)
+        yr[q] = fmaf(b.x, a[q][m].x, fmaf(b.y, a[q][m].y, yr[q]));
+        yi[q] = fmaf(b.x, a[q][m].y, fmaf(-b.y, a[q][m].x, yi[q]));
+      }
+    }
+    float n[PT];
+#pragma unroll
+    for (int q = 0; q < PT; ++q) n[q] = fmaf(yr[q], yr[q], yi[q] * yi[q]);
+    if (k < Kn) {
+      const float w = sh.w32[k];
+#pragma unroll
+      for (int q = 0; q < PT; ++q) {
+        dm[q] += n[q];
+        de[q] = fmaf(w, n[q], de[q]);
+      }
+    }
+    if (k == kphd) {
+#pragma unroll
+      for (int q = 0; q < PT; ++q) dp[q] = n[q];
+    }
+    if (k == kmn) {
+#pragma unroll
+      for (int q = 0; q < PT; ++q) dn[q] = n[q];
+    }
+  }
+  bool flag[PT];
+#pragma unroll
+  for (int q = 0; q < PT; ++q) flag[q] = false;
+  float out[PT];
+#define DOA_READOUT(R, DEN)                                                   \
+  if (j.P[R]) {                                                               \
+    const float thr = sh.thr[R];                                              \
+    _Pragma("unroll") for (int q = 0; q < PT; ++q) {                          \
+      out[q] = 1.0f / fmaxf(DEN[q], FLT_MIN);                                 \
+      flag[q] = flag[q] || DEN[q] < thr;                                      \
+    }                                                                         \
+    store_row<PT>(j.P[R], L, k0, out);                                        \
+  }
+  DOA_READOUT(kRoPhd, dp)
+  DOA_READOUT(kRoMusic, dm)
+  DOA_READOUT(kRoEv, de)
+  DOA_READOUT(kRoMn, dn)
+#undef DOA_READOUT
+  int pos[PT];
+#pragma unroll
+  for (int q = 0; q < PT; ++q) {
+    pos[q] = -1;
+    if (k0 + q < L && flag[q]) {
+      pos[q] = atomicAdd(&sh.nflag, 1);
+      if (pos[q] < kFlagCap) sh.flags[pos[q]] = k0 + q;
+    }
   }
   // queue overflow (more than kFlagCap small denominators in one tile): refine in place
 #pragma unroll
-  for (int j = 0; j < PT; ++j)
-    if (pos[j] >= kFlagCap) refine_point_thread(rc, k0 + j, P);
+  for (int q = 0; q < PT; ++q)
+    if (pos[q] >= kFlagCap) refine_point_thread(j, k0 + q);
 }
 
 }  // namespace scanc

@@ -84,9 +84,14 @@ def test_batch_plan_layout(libdoa):
     hdr = buf[:64].view(np.int32)
     assert hdr[0] == 0x444F4131            # magic
     assert list(hdr[1:6]) == [3, 4 + 1 + 2, 2, 4 + 1 + 3, 2]   # nprob, njobs, ngrids, ncov, nreduce
-    # workspace: tables, 3 R + partials, 7 factors (M*M complex128 each), 256-byte rounded
-    need = 18001 * 4 + 1801 * 4 + (16 * 16 * 16) * (1 + 4 + 4) + (8 * 8 * 16) * (1 + 1) + (33 * 33 * 16) * (1 + 3 + 2)
-    assert ws.value >= need and ws.value < need + 256 * 40
+    # workspace: phase (uint32) and sine (double) tables per grid, then per problem R, the
+    # covariance partials and one scan factor (M x (M+1) complex128 + M EV weights), each
+    # allocation rounded up to 256 bytes
+    def factor(M):
+        return M * (M + 1) * 16 + M * 8
+    need = (18001 + 1801) * 12 + (16 * 16 * 16) * (1 + 4) + factor(16) + (8 * 8 * 16) + factor(8) \
+        + (33 * 33 * 16) * (1 + 3) + factor(33)
+    assert ws.value >= need and ws.value < need + 256 * 12
     # too small a buffer
     assert libdoa.lib().doa_batch_plan(arr, 3, None, buf.ctypes.data, n - 1, ctypes.byref(ws), None) == libdoa.ENOMEM
 
@@ -130,4 +135,5 @@ def test_batch_plan_scan_pt(libdoa):
             want = [p if p else d for p, d in zip(pts, (4, 2, 1, 1))]
             assert list(got) == want
             tiles = buf[:128].view(np.int64)[7:11]      # scan_tiles per bucket
-            assert tiles[0] == -(-1801 // (128 * want[0])) and tiles[3] == 4 * -(-18001 // 128)
+            # one scan job per problem: its four algorithms share the tiles of one grid pass
+            assert tiles[0] == -(-1801 // (128 * want[0])) and tiles[3] == -(-18001 // 128)

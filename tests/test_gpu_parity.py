@@ -264,6 +264,22 @@ def test_batch_uneven_sample(env):
     _check_batch(torch, doa, insts, [1 << s.alg for s in picked])
 
 
+def test_batch_every_algorithm_subset(env):
+    """All 15 non-empty algorithm sets, over every M bucket: the shared-contraction scan reads
+    each requested spectrum from one factor (E_n with PHD / EV / MUSIC readouts, valph for MN,
+    or v_min / valph alone) and every one matches the oracle's Table 3 spectrum."""
+    torch, doa = env
+    Ms = [8, 12, 16, 33, 6]
+    insts, masks = [], []
+    for mask in range(1, 16):
+        M = Ms[mask % len(Ms)]
+        insts.append(synth.custom(M, 1 + mask % 3, 1500 + 37 * mask, None, 5.0 + mask, 0.1, seed=900 + mask))
+        masks.append(mask)
+    insts.append(synth.custom(5, 0, 64, [], 0.0, 0.5, seed=931))     # d = 0: E_n = all of V, valph = e1
+    masks.append(0xF)
+    _check_batch(torch, doa, insts, masks)
+
+
 def test_batch_edge_shapes(env):
     torch, doa = env
     insts = [synth.custom(2, 1, 5, [10.0], 20.0, 45.0, seed=1),           # L = 5
