@@ -353,8 +353,9 @@ def run_uneven(args):
         probs.append(doa.make_problem(X, s.d, 1 << s.alg, doa.grid(LO, s.step, s.L), P[int(p_off[i]):int(p_off[i] + s.L)],
                                       idx[i], val[i], cnt[i:i + 1]))
     tune_log = []
-    scan_pt = autotune.tune(probs, device=str(dev), log=tune_log) if not args.no_tune else list(autotune.DEFAULT)
-    plan = doa.BatchPlan(probs, device=str(dev), scan_pt=scan_pt)
+    scan_pt, eig_mats = (autotune.tune(probs, device=str(dev), log=tune_log) if not args.no_tune
+                         else (list(autotune.DEFAULT), [0, 0, 0, 0]))
+    plan = doa.BatchPlan(probs, device=str(dev), scan_pt=scan_pt, eig_mats=eig_mats)
     ws = doa.workspace(plan, device=str(dev))
     status = torch.empty(len(specs), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -430,7 +431,7 @@ def run_uneven(args):
         "config": {"workload": f"uneven batch: {len(specs)} problems, M in {{8,12,16,32}}, d in U{{1..M/2}}, "
                                f"N in U{{256..8192}}, step in {{0.1,0.01,0.001}} deg, one algorithm each",
                    "batch_per_gpu": len(specs), "points_per_gpu": int(Ls.sum()), "graph": True,
-                   "scan_pt": scan_pt, "l2": f"inputs {buf.nbytes / 1e9:.2f} GB > 129 MB L2 (no flush needed)",
+                   "scan_pt": scan_pt, "eig_mats": plan.eig_mats, "l2": f"inputs {buf.nbytes / 1e9:.2f} GB > 129 MB L2 (no flush needed)",
                    "parallelism": f"replicas x{world}"},
         "solves_per_s": len(specs) * world / (ms / 1e3),
         "gpu_launches": plan.launches() * args.steps,

@@ -173,20 +173,29 @@ typedef struct {
                          /* alg_mask (M x K complex128, column-major, ld M)                   */
 } doa_problem;
 
+/* Launch-shape knobs of a plan, per M bucket (M <= 8, <= 16, <= 32, <= 64); 0 = default. */
+typedef struct {
+  int32_t scan_pt[4];    /* grid points per scan thread (tile = 128 threads x scan_pt points).  */
+                         /* Allowed {1, 2, 4}, {1, 2, 4}, {1, 2}, {1} (the register budget of   */
+                         /* the in-register phasors); default (4, 2, 1, 1).                     */
+  int32_t eig_mats[4];   /* matrices per Jacobi warp. Allowed {1, 2, 4, 8}, {1, 2, 4}, {1, 2},   */
+                         /* {1} (a lane per rotation pair); default: 1 unless the bucket holds   */
+                         /* enough problems to keep ~24 packed warps per SM busy.               */
+} doa_tuning;
+
 /*
  * Host-only planning. doa_batch_plan_bytes returns the plan size for these problems (0 if one
  * is invalid). doa_batch_plan packs the problems into `plan` (caller host memory of at least
  * that size) and returns the device workspace size in *ws_bytes.
- * scan_pt: NULL, or 4 entries (M <= 8, <= 16, <= 32, <= 64) giving the grid points each scan
- * thread evaluates (tile = 128 threads x scan_pt points); 0 keeps the default (4, 2, 1, 1).
- * Allowed: {1, 2, 4} for the first two buckets, {1, 2} for the third, 1 for the last
- * (the register budget of the in-register phasors). This is the autotuner's knob.
+ * tuning: NULL (defaults) or the launch shapes above; these are the autotuner's knobs and do
+ * not change any result bit.
  * The caller copies the same plan bytes to device memory (16-byte aligned) before
  * doa_solve_batch. Errors: DOA_EINVAL for an invalid problem (its index in *bad_index if
- * bad_index is not NULL), DOA_ENOMEM if plan_bytes is too small.
+ * bad_index is not NULL) or a tuning value outside the allowed sets, DOA_ENOMEM if plan_bytes
+ * is too small.
  */
 size_t doa_batch_plan_bytes(const doa_problem *probs, int nprob);
-doa_status doa_batch_plan(const doa_problem *probs, int nprob, const int32_t *scan_pt, void *plan,
+doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning *tuning, void *plan,
                           size_t plan_bytes, size_t *ws_bytes, int *bad_index);
 
 /* Stages of doa_solve_batch, in launch order (for per-stage timing). */

@@ -1,12 +1,16 @@
-"""Scan tile autotuner for doa_solve_batch.
+"""Launch-shape autotuner for doa_solve_batch.
 
-The batched scan evaluates tiles of 128 threads x PT consecutive grid points, with the PT x M
-steering phasors of a thread held in registers. PT trades register pressure (occupancy)
-against reuse of each B element loaded from shared memory, and the best value depends on the
-M bucket (8, 16, 32, 64) and on how long the spectra are. The tuner times the scan stage of
-the caller's own batch for every allowed PT of every occupied bucket (per-stage events of
-doa_solve_batch), keeps the fastest, and persists the table as JSON keyed by GPU name, M bucket
-and grid-size class (decade of the mean L), so later runs reuse it without timing.
+Two knobs per M bucket (8, 16, 32, 64), neither of which changes a result bit:
+  * scan_pt — the batched scan evaluates tiles of 128 threads x PT consecutive grid points, with
+    the PT x M steering phasors of a thread held in registers; PT trades register pressure
+    (occupancy) against reuse of each factor element loaded from shared memory;
+  * eig_mats — matrices per Jacobi warp; packing several small matrices into one warp gives every
+    lane a rotation pair, but leaves fewer warps to hide the FP64 latency of the rotations.
+The best values depend on the bucket and on the batch (how many problems, how long the
+spectra). The tuner times the scan and eig stages of the caller's own batch for every allowed
+value of every occupied bucket (per-stage events of doa_solve_batch), keeps the fastest, and
+persists the table as JSON keyed by GPU name, M bucket and size class (decade of the bucket's
+problem count and of its mean points per problem), so later runs reuse it without timing.
 """
 from __future__ import annotations
 
@@ -14,13 +18,14 @@ import json
 import math
 import os
 import statistics
-from typing import Dict, List, Optional, Sequence
+from typing import Dict, List, Optional, Sequence, Tuple
 
 import torch
 
 from . import doa
 
 CANDIDATES = ((1, 2, 4), (1, 2, 4), (1, 2), (1,))
+EIG_CANDIDATES = ((1, 2, 4, 8), (1, 2, 4), (1, 2), (1,))
 DEFAULT = (4, 2, 1, 1)
 
 
@@ -38,7 +43,8 @@ def _keys(problems: Sequence[doa.Problem], device) -> Dict[int, str]:
     Ls: Dict[int, List[int]] = {}
     for p in problems:
         Ls.setdefault(_bucket(p.M), []).append(int(p.grid.L) * bin(int(p.alg_mask)).count("1"))
-    return {b: f"{name}|M{b}|L1e{int(round(math.log10(max(1.0, sum(v) / len(v)))))}" for b, v in Ls.items()}
+    return {b: f"{name}|M{b}|n1e{int(round(math.log10(len(v))))}|L1e{int(round(math.log10(max(1.0, sum(v) / len(v)))))}"
+            for b, v in Ls.items()}
 
 
 def _load(path: str) -> dict:
@@ -49,50 +55,62 @@ def _load(path: str) -> dict:
         return {}
 
 
-def _scan_ms(plan: doa.BatchPlan, ws: torch.Tensor, status: torch.Tensor, reps: int) -> float:
+def _stage_ms(plan: doa.BatchPlan, ws: torch.Tensor, status: torch.Tensor, reps: int, stage: int) -> float:
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(doa.BATCH_STAGES + 1)]
     doa.doa_solve_batch(plan, ws, status, stage_events=ev)      # warm-up
     times = []
     for _ in range(reps):
         doa.doa_solve_batch(plan, ws, status, stage_events=ev)
         torch.cuda.synchronize()
-        times.append(ev[3].elapsed_time(ev[4]))
+        times.append(ev[stage].elapsed_time(ev[stage + 1]))
     return statistics.median(times)
 
 
+EIG_STAGE, SCAN_STAGE = 2, 3
+
+
 def tune(problems: Sequence[doa.Problem], device: str = "cuda", reps: int = 3, use_cache: bool = True,
-         persist: bool = True, path: Optional[str] = None, log: Optional[list] = None) -> List[int]:
-    """Returns scan_pt (4 ints) for doa.BatchPlan. Buckets without problems keep the default."""
+         persist: bool = True, path: Optional[str] = None, log: Optional[list] = None) -> Tuple[List[int], List[int]]:
+    """Returns (scan_pt, eig_mats), 4 ints each, for doa.BatchPlan. Empty buckets keep 0 (default)."""
     path = path or cache_path()
     keys = _keys(problems, device)
     table = _load(path) if use_cache else {}
-    choice = list(DEFAULT)
+    pt, em = list(DEFAULT), [0, 0, 0, 0]
     todo = []
     for b, key in keys.items():
-        if key in table:
-            choice[b] = int(table[key]["pt"])
+        if key in table and "eig_mats" in table[key]:
+            pt[b] = int(table[key]["pt"])
+            em[b] = int(table[key]["eig_mats"])
         else:
             todo.append(b)
     if todo:
-        base = doa.BatchPlan(problems, device=device, scan_pt=choice)
+        base = doa.BatchPlan(problems, device=device, scan_pt=pt, eig_mats=em)
+        em = [v if v else d for v, d in zip(em, base.eig_mats)]
         ws = doa.workspace(base, device=device)
         status = torch.empty(base.nprob, dtype=torch.int32, device=device)
         for b in todo:
-            results = {}
-            for pt in CANDIDATES[b]:
-                trial = list(choice)
-                trial[b] = pt
-                plan = doa.BatchPlan(problems, device=device, scan_pt=trial)
-                results[pt] = _scan_ms(plan, ws, status, reps)
-            best = min(results, key=results.get)
-            choice[b] = best
-            table[keys[b]] = {"pt": best, "scan_ms": {str(k): round(v, 4) for k, v in results.items()}}
+            res_pt, res_em = {}, {}
+            for v in CANDIDATES[b]:
+                trial = list(pt)
+                trial[b] = v
+                res_pt[v] = _stage_ms(doa.BatchPlan(problems, device=device, scan_pt=trial, eig_mats=em), ws, status,
+                                      reps, SCAN_STAGE)
+            pt[b] = min(res_pt, key=res_pt.get)
+            for v in EIG_CANDIDATES[b]:
+                trial = list(em)
+                trial[b] = v
+                res_em[v] = _stage_ms(doa.BatchPlan(problems, device=device, scan_pt=pt, eig_mats=trial), ws, status,
+                                      reps, EIG_STAGE)
+            em[b] = min(res_em, key=res_em.get)
+            table[keys[b]] = {"pt": pt[b], "scan_ms": {str(k): round(v, 4) for k, v in res_pt.items()},
+                              "eig_mats": em[b], "eig_ms": {str(k): round(v, 4) for k, v in res_em.items()}}
             if log is not None:
-                log.append({"bucket": b, "key": keys[b], "ms": results, "best": best})
+                log.append({"bucket": b, "key": keys[b], "scan_ms": res_pt, "pt": pt[b], "eig_ms": res_em,
+                            "eig_mats": em[b]})
         if persist:
             os.makedirs(os.path.dirname(path), exist_ok=True)
             tmp = path + f".{os.getpid()}.tmp"
             with open(tmp, "w") as f:
                 json.dump(table, f, indent=1, sort_keys=True)
             os.replace(tmp, path)
-    return choice
+    return pt, [em[b] if b in keys else 0 for b in range(4)]

@@ -192,14 +192,15 @@ size_t doa_batch_plan_bytes(const doa_problem *probs, int nprob) {
   return (size_t)plan_offsets(sz).total;
 }
 
-doa_status doa_batch_plan(const doa_problem *probs, int nprob, const int32_t *scan_pt, void *plan, size_t plan_bytes,
-                          size_t *ws_bytes, int *bad_index) {
+doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning *tuning, void *plan,
+                          size_t plan_bytes, size_t *ws_bytes, int *bad_index) {
   if (bad_index) *bad_index = -1;
   if (!probs || nprob < 1 || !ws_bytes) return DOA_EINVAL;
   int pt[kNumBuckets];
   for (int b = 0; b < kNumBuckets; ++b) {
-    pt[b] = (scan_pt && scan_pt[b] != 0) ? scan_pt[b] : scan_pt_default(b);
+    pt[b] = (tuning && tuning->scan_pt[b] != 0) ? tuning->scan_pt[b] : scan_pt_default(b);
     if (!scan_pt_allowed(b, pt[b])) return DOA_EINVAL;
+    if (tuning && tuning->eig_mats[b] != 0 && !eig_mats_allowed(b, tuning->eig_mats[b])) return DOA_EINVAL;
   }
   PlanSizes sz;
   std::vector<doa_grid> grids;
@@ -236,7 +237,7 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const int32_t *sc
     h.off_eig[b] = o.eig[b];
     h.off_scan[b] = o.scan[b];
   }
-  // workspace: per-grid phase and sine tables, then per problem R, partials and scan factor
+  // workspace: per-grid 32- and 64-bit phase tables, then per problem R, partials and scan factor
   int64_t ws = 0;
   for (int g = 0; g < sz.ngrids; ++g) {
     pg[g].lo = grids[g].lo_deg;
@@ -244,7 +245,7 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const int32_t *sc
     pg[g].L = grids[g].L;
     pg[g].S_off = ws;
     ws = round_up(ws + (int64_t)grids[g].L * 4, 256);
-    pg[g].sin_off = ws;
+    pg[g].S64_off = ws;
     ws = round_up(ws + (int64_t)grids[g].L * 8, 256);
     h.grid_points += grids[g].L;
   }
@@ -288,6 +289,7 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const int32_t *sc
     scan[b][is[b]++] = i;
   }
   for (int b = 0; b < kNumBuckets; ++b) {
+    h.eig_mats[b] = (tuning && tuning->eig_mats[b] != 0) ? tuning->eig_mats[b] : eig_mats_default(b, sz.eig[b]);
     h.eig_count[b] = sz.eig[b];
     h.scan_jobs[b] = sz.scan[b];
     h.scan_tiles[b] = tiles[b];

@@ -40,6 +40,12 @@ __device__ __forceinline__ uint32_t grid_phase_step(double lo, double step, int 
   return phase_step_of_sin(sin(theta * 0.017453292519943295));  // pi/180
 }
 
+// 64-bit form of the same phase step, S64 = round(2^63 sin theta) mod 2^64 (computed as twice
+// round(2^62 s) so that s = +-1 stays in range; both map to 2^63, a half turn, as they must).
+__device__ __forceinline__ uint64_t phase_step64_of_sin(double s) {
+  return (uint64_t)__double2ll_rn(s * 4611686018427387904.0) << 1;   // 2^62
+}
+
 // exp(j*pi*phi*2^-31) for a 32-bit phase phi (a fraction of a full turn: 2^32 = 2 pi).
 // The top two bits (rounded) select the quadrant; the signed remainder f in [-1/2, 1/2) of a
 // quarter turn is evaluated with the Taylor series of sin and cos about 0 in the variable
@@ -72,6 +78,51 @@ __device__ __forceinline__ float2 phasor_q32(uint32_t phi) {
   if ((quad + 1u) & 2u) re = -re;   // quad 1 or 2
   if (quad & 2u) im = -im;          // quad 2 or 3
   return make_float2(re, im);
+}
+
+// FP64 counterpart for refinement: exp(j 2 pi phi 2^-64) for a 64-bit phase phi (fraction of a
+// full turn). Quadrant from the top two bits (rounded), remainder f in [-1/2, 1/2) of a quarter
+// turn, then the Taylor series of sin and cos of x = (pi/2) f (|x| <= pi/4) through x^17 and
+// x^16: the first omitted terms are below 1e-19 and 3e-18. The coefficients (pi/2)^n / n! are
+// formed at compile time from pi/2.
+__host__ __device__ constexpr double half_pi_taylor(int n) {
+  double c = 1.0;
+  for (int k = 1; k <= n; ++k) c *= 1.5707963267948966 / k;
+  return c;
+}
+__device__ __forceinline__ double2 phasor_q64(uint64_t phi) {
+  const uint64_t quad = (phi + (1ull << 61)) >> 62;
+  const int64_t rem = (int64_t)(phi - (quad << 62));                 // [-2^61, 2^61)
+  const double f = (double)rem * 2.168404344971009e-19;              // * 2^-62
+  const double f2 = f * f;
+  constexpr double s1 = half_pi_taylor(1), s3 = -half_pi_taylor(3), s5 = half_pi_taylor(5),
+                   s7 = -half_pi_taylor(7), s9 = half_pi_taylor(9), s11 = -half_pi_taylor(11),
+                   s13 = half_pi_taylor(13), s15 = -half_pi_taylor(15), s17 = half_pi_taylor(17);
+  constexpr double c2 = -half_pi_taylor(2), c4 = half_pi_taylor(4), c6 = -half_pi_taylor(6),
+                   c8 = half_pi_taylor(8), c10 = -half_pi_taylor(10), c12 = half_pi_taylor(12),
+                   c14 = -half_pi_taylor(14), c16 = half_pi_taylor(16);
+  double sp = fma(f2, s17, s15);
+  sp = fma(f2, sp, s13);
+  sp = fma(f2, sp, s11);
+  sp = fma(f2, sp, s9);
+  sp = fma(f2, sp, s7);
+  sp = fma(f2, sp, s5);
+  sp = fma(f2, sp, s3);
+  sp = fma(f2, sp, s1);
+  const double sn = f * sp;
+  double cp = fma(f2, c16, c14);
+  cp = fma(f2, cp, c12);
+  cp = fma(f2, cp, c10);
+  cp = fma(f2, cp, c8);
+  cp = fma(f2, cp, c6);
+  cp = fma(f2, cp, c4);
+  cp = fma(f2, cp, c2);
+  const double cs = fma(f2, cp, 1.0);
+  double re = (quad & 1u) ? sn : cs;
+  double im = (quad & 1u) ? cs : sn;
+  if ((quad + 1u) & 2u) re = -re;   // quad 1 or 2
+  if (quad & 2u) im = -im;          // quad 2 or 3
+  return make_double2(re, im);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -111,7 +162,7 @@ struct PlanGrid {
   int32_t L;
   int32_t pad;
   int64_t S_off;          // byte offset of the phase table (L x uint32) in the workspace
-  int64_t sin_off;        // byte offset of sin(theta_k) (L x double) in the workspace
+  int64_t S64_off;        // byte offset of the 64-bit phase table (L x uint64) in the workspace
 };
 
 struct PlanCovItem {
@@ -132,11 +183,13 @@ struct PlanHeader {
   // byte offsets of the arrays inside the plan
   int64_t off_prob, off_job, off_grid, off_cov, off_reduce, off_eig[kNumBuckets],
       off_scan[kNumBuckets], off_grid_pts;
+  int32_t eig_mats[kNumBuckets];         // matrices per Jacobi warp, per M bucket
 };
 
-// The Python binding reads these header fields by position (int32 index 22 = scan_pt).
+// The Python binding reads these header fields by position (int32 index 22 = scan_pt, 58 = eig_mats).
 static_assert(offsetof(PlanHeader, scan_pt) == 88, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, scan_tiles) == 56, "PlanHeader layout changed");
+static_assert(offsetof(PlanHeader, eig_mats) == 232, "PlanHeader layout changed");
 
 // Scan tiles: kScanThreads threads, each evaluating PT consecutive grid points (tile shape
 // 128 x PT). PT is chosen per M bucket (the autotuner's knob); the register budget limits it
@@ -145,6 +198,19 @@ constexpr int kScanThreads = 128;
 __host__ __device__ constexpr int scan_pt_default(int bucket) { return bucket == 0 ? 4 : (bucket == 1 ? 2 : 1); }
 __host__ __device__ inline bool scan_pt_allowed(int bucket, int pt) {
   return pt == 1 || (pt == 2 && bucket <= 2) || (pt == 4 && bucket <= 1);
+}
+
+// Jacobi packing: a warp holds G matrices of one bucket with G x (NP / 2) <= 32 rotation pairs
+// (one lane each); the M <= 64 bucket runs one matrix per 256-thread CTA.
+__host__ __device__ constexpr int eig_mats_max(int bucket) { return bucket == 0 ? 8 : (bucket == 1 ? 4 : (bucket == 2 ? 2 : 1)); }
+__host__ __device__ inline bool eig_mats_allowed(int bucket, int g) {
+  return g >= 1 && g <= eig_mats_max(bucket) && (g & (g - 1)) == 0;
+}
+// Default: the largest packing that still leaves ~24 warps per SM (152 SMs) of work, else 1.
+__host__ __device__ inline int eig_mats_default(int bucket, int count) {
+  int g = eig_mats_max(bucket);
+  while (g > 1 && (count + g - 1) / g < 152 * 24) g >>= 1;
+  return g;
 }
 
 __host__ __device__ inline int m_bucket(int M) { return M <= 8 ? 0 : (M <= 16 ? 1 : (M <= 32 ? 2 : 3)); }

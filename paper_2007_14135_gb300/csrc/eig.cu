@@ -366,11 +366,10 @@ __global__ void __launch_bounds__(grp_threads<NP>()) eig_single_kernel(const dou
   }
 }
 
-template <int NP>
+template <int NP, int G>
 __global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_batch_kernel(const uint8_t *plan, uint8_t *ws, int bucket,
                                                                          int *status) {
   extern __shared__ __align__(16) uint8_t smem[];
-  constexpr int G = mats_per_warp<NP>();
   constexpr int T = grp_threads<NP>();
   const int grp = threadIdx.x / T, lane = Grp<T>::id();
   EigSmem<NP> *mats = reinterpret_cast<EigSmem<NP> *>(smem) + grp * G;
@@ -438,18 +437,28 @@ cudaError_t run_single(const double2 *R64, int M, int d, int alg, double *evals,
   return cudaGetLastError();
 }
 
+template <int NP, int G>
+cudaError_t run_batch_g(const uint8_t *plan, int count, uint8_t *ws, int *status, int bucket, cudaStream_t st) {
+  constexpr int W = eig_warps<NP>();
+  constexpr int per_cta = groups_per_cta<NP>() * G;
+  const int smem = (int)sizeof(EigSmem<NP>) * per_cta;
+  cudaError_t e = cudaFuncSetAttribute(eig_batch_kernel<NP, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  eig_batch_kernel<NP, G><<<(count + per_cta - 1) / per_cta, 32 * W, smem, st>>>(plan, ws, bucket, status);
+  return cudaGetLastError();
+}
+
+// Matrices per warp from the plan (G in {1, 2, 4, 8} up to the bucket's maximum).
 template <int NP>
 cudaError_t run_batch(const uint8_t *plan, const PlanHeader &h, uint8_t *ws, int *status, int bucket,
                       cudaStream_t st) {
   const int count = h.eig_count[bucket];
   if (count == 0) return cudaSuccess;
-  constexpr int W = eig_warps<NP>();
-  constexpr int per_cta = groups_per_cta<NP>() * mats_per_warp<NP>();
-  const int smem = (int)sizeof(EigSmem<NP>) * per_cta;
-  cudaError_t e = cudaFuncSetAttribute(eig_batch_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  eig_batch_kernel<NP><<<(count + per_cta - 1) / per_cta, 32 * W, smem, st>>>(plan, ws, bucket, status);
-  return cudaGetLastError();
+  const int g = h.eig_mats[bucket];
+  if (g >= 8 && mats_per_warp<NP>() >= 8) return run_batch_g<NP, (mats_per_warp<NP>() >= 8 ? 8 : 1)>(plan, count, ws, status, bucket, st);
+  if (g >= 4 && mats_per_warp<NP>() >= 4) return run_batch_g<NP, (mats_per_warp<NP>() >= 4 ? 4 : 1)>(plan, count, ws, status, bucket, st);
+  if (g >= 2 && mats_per_warp<NP>() >= 2) return run_batch_g<NP, (mats_per_warp<NP>() >= 2 ? 2 : 1)>(plan, count, ws, status, bucket, st);
+  return run_batch_g<NP, 1>(plan, count, ws, status, bucket, st);
 }
 
 }  // namespace

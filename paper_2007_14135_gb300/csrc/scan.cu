@@ -15,8 +15,9 @@
 //
 // Near-null refinement: where the FP32 denominator is small its relative error grows (the
 // contraction cancels), so every point with den_r < kRefineC * E_r for some readout r is
-// re-evaluated in FP64 from the grid angle (sin theta_k in FP64 from a per-grid table in the
-// batch, else recomputed) and the FP64 factor, for all readouts of the job. Flagged points of a
+// re-evaluated with FP64 steering and contraction (exact 64-bit phases m * S64_k from a per-grid
+// table in the batch, else from sin theta_k recomputed in FP64) and the FP64 factor, for all
+// readouts of the job. Flagged points of a
 // tile are queued in shared memory and each is then handled by a whole warp (lanes own phasors,
 // then elements of columns), so the FP64 work runs without divergence. With per-term FP32
 // errors below ~4 eps the FP32 result elsewhere stays within ~5e-4 relative.
@@ -39,12 +40,12 @@ __global__ void grid_table_batch_kernel(const uint8_t *plan, uint8_t *ws) {
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
   const PlanGrid g = reinterpret_cast<const PlanGrid *>(plan + h->off_grid)[blockIdx.y];
   uint32_t *S = reinterpret_cast<uint32_t *>(ws + g.S_off);
-  double *sn = reinterpret_cast<double *>(ws + g.sin_off);
+  uint64_t *S64 = reinterpret_cast<uint64_t *>(ws + g.S64_off);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.L; k += gridDim.x * blockDim.x) {
     const double theta = __dadd_rn(g.lo, __dmul_rn((double)k, g.step));
     const double s = sin(theta * 0.017453292519943295);
-    sn[k] = s;
     S[k] = phase_step_of_sin(s);
+    S64[k] = phase_step64_of_sin(s);
   }
 }
 
@@ -71,8 +72,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_single_kernel(const double2
   drain_refinements(j, sh);
 }
 
-// Persistent batched scan over the tiles of the problems of one M bucket. Tiles are striped over
-// the CTAs; the problem of a tile is found by binary search on the problems' first tiles.
+// Persistent batched scan over the tiles of the problems of one M bucket. Every CTA takes a
+// contiguous range of tiles (equal counts), so it changes problem only at the few problem
+// boundaries inside its range; the first problem comes from a binary search on the problems'
+// first tiles, the following ones by stepping through the bucket's list.
 template <int MP, int PT>
 __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t *plan, uint8_t *ws, int bucket) {
   __shared__ __align__(16) float2 Bs[(MP + 1) * MP];
@@ -84,40 +87,46 @@ __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t 
   const PlanProblem *probs = reinterpret_cast<const PlanProblem *>(plan + h->off_prob);
   const PlanGrid *grids = reinterpret_cast<const PlanGrid *>(plan + h->off_grid);
   constexpr int TP = kScanThreads * PT;
+  const int64_t t_begin = ntiles * blockIdx.x / gridDim.x, t_end = ntiles * (blockIdx.x + 1) / gridDim.x;
+  if (t_begin >= t_end) return;
+  int u = 0, hi = nunits - 1;
+  while (u < hi) {  // last problem with tile_start <= t_begin
+    int mid = (u + hi + 1) >> 1;
+    if (probs[list[mid]].tile_start <= t_begin) u = mid; else hi = mid - 1;
+  }
   int cur = -1;
   ScanJob j{};
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    int lo = 0, hi = nunits - 1;
-    while (lo < hi) {  // last problem with tile_start <= t
-      int mid = (lo + hi + 1) >> 1;
-      if (probs[list[mid]].tile_start <= t) lo = mid; else hi = mid - 1;
-    }
-    const PlanProblem &pp = probs[list[lo]];
-    const PlanGrid &g = grids[pp.grid_id];
-    if (lo != cur) {
-      j.F = reinterpret_cast<const double2 *>(ws + pp.fac_off);
-      j.w = pp.Kn > 0 && pp.slot[DOA_EV] >= 0 ? reinterpret_cast<const double *>(ws + pp.fac_off) + 2 * pp.p.M * (pp.p.M + 1)
-                                              : nullptr;
-      j.sin64 = reinterpret_cast<const double *>(ws + g.sin_off);
-      for (int r = 0; r < 4; ++r) j.P[r] = pp.slot[r] >= 0 ? pp.p.P + (size_t)pp.slot[r] * g.L : nullptr;
-      j.lo = g.lo;
-      j.step = g.step;
-      j.M = pp.p.M;
-      j.Kf = pp.Kf;
-      j.Kn = pp.Kn;
-      j.kphd = pp.kphd;
-      j.kmn = pp.kmn;
+  const PlanProblem *pp = nullptr;
+  const PlanGrid *g = nullptr;
+  for (int64_t t = t_begin; t < t_end; ++t) {
+    while (u + 1 < nunits && probs[list[u + 1]].tile_start <= t) ++u;
+    if (u != cur) {
+      pp = &probs[list[u]];
+      g = &grids[pp->grid_id];
+      j.F = reinterpret_cast<const double2 *>(ws + pp->fac_off);
+      j.w = pp->Kn > 0 && pp->slot[DOA_EV] >= 0
+                ? reinterpret_cast<const double *>(ws + pp->fac_off) + 2 * pp->p.M * (pp->p.M + 1)
+                : nullptr;
+      j.S64 = reinterpret_cast<const uint64_t *>(ws + g->S64_off);
+      for (int r = 0; r < 4; ++r) j.P[r] = pp->slot[r] >= 0 ? pp->p.P + (size_t)pp->slot[r] * g->L : nullptr;
+      j.lo = g->lo;
+      j.step = g->step;
+      j.M = pp->p.M;
+      j.Kf = pp->Kf;
+      j.Kn = pp->Kn;
+      j.kphd = pp->kphd;
+      j.kmn = pp->kmn;
       j.kofs = 0;
       __syncthreads();
       load_job<MP>(j, Bs, sh);
       __syncthreads();
       set_threshold<MP>(Bs, j, sh);
       __syncthreads();
-      cur = lo;
+      cur = u;
     }
-    const uint32_t *S = reinterpret_cast<const uint32_t *>(ws + g.S_off);
-    const int k0 = (int)(t - pp.tile_start) * TP + threadIdx.x * PT;
-    scan_points<MP, PT>(Bs, j, S, g.L, k0, sh);
+    const uint32_t *S = reinterpret_cast<const uint32_t *>(ws + g->S_off);
+    const int k0 = (int)(t - pp->tile_start) * TP + threadIdx.x * PT;
+    scan_points<MP, PT>(Bs, j, S, g->L, k0, sh);
     drain_refinements(j, sh);
   }
 }

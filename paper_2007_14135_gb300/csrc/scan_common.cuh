@@ -29,7 +29,7 @@ constexpr int kRoPhd = 0, kRoMusic = 1, kRoEv = 2, kRoMn = 3;
 struct ScanJob {
   const double2 *F;      // FP64 factor, column-major, ld M, Kf columns
   const double *w;       // FP64 EV weights (Kn entries); null when EV is absent
-  const double *sin64;   // FP64 sin(theta) per local point, or null (computed from lo, step)
+  const uint64_t *S64;   // 64-bit phase steps per local point, or null (computed from lo, step)
   float *P[4];           // output row of each readout (local point index); null = absent
   double lo, step;
   int M, Kf, Kn, kphd, kmn;
@@ -38,7 +38,7 @@ struct ScanJob {
 
 struct ScanShared {
   double2 ph[kScanWarps][kMaxM];      // per-warp FP64 phasors for refinement
-  double2 yb[kScanWarps][kMaxCols];   // per-warp FP64 column outputs for refinement
+  float2 yb[kScanWarps][kMaxCols];    // per-warp column outputs of refinement (rounded once)
   float w32[kMaxM];                   // FP32 EV weights
   int flags[kFlagCap];
   int nflag;
@@ -96,71 +96,55 @@ __device__ __forceinline__ void set_threshold(const float2 *Bs, const ScanJob &j
   }
 }
 
-__device__ __forceinline__ double sin_of_point(const ScanJob &j, int k) {
-  if (j.sin64) return j.sin64[k];
+__device__ __forceinline__ uint64_t phase64_of_point(const ScanJob &j, int k) {
+  if (j.S64) return j.S64[k];
   const double theta = __dadd_rn(j.lo, __dmul_rn((double)(k + j.kofs), j.step));
-  return sin(theta * 0.017453292519943295);
+  return phase_step64_of_sin(sin(theta * 0.017453292519943295));
 }
 
-__device__ __forceinline__ float recip_out(double den) { return 1.0f / (float)fmax(den, (double)FLT_MIN); }
+__device__ __forceinline__ float recip_out(float den) { return 1.0f / fmaxf(den, FLT_MIN); }
 
-// FP64 re-evaluation of local point k by one whole warp. Lanes first compute the phasors
-// (m = lane, lane + 32), then contract: for M <= 32 the lanes form 32 / MQ groups of MQ >= M
-// lanes, each group one column per pass (lane = element), reduced by shuffles; for M > 32 every
-// lane takes two elements of one column per pass. Lane 0 forms the readouts.
-inline __device__ void refine_point_warp(const ScanJob &j, int k, double2 *ph, double2 *yb) {
+// Re-evaluation of local point k by one whole warp with the steering vector and the contraction
+// in FP64: phasors from the exact 64-bit phase m * S64 (lane m), then y_c = f_c^H a with LPC
+// lanes per column (LPC = the largest power of two with Kf * LPC <= 32, so one pass covers the
+// columns when it can), each lane summing a contiguous run of elements and the LPC partial sums
+// combined by shuffles. The cancellation that makes the FP32 result inaccurate happens inside
+// y_c; the readouts sum |y_c|^2 >= 0 and are formed from y_c rounded once to FP32.
+inline __device__ void refine_point_warp(const ScanJob &j, int k, const float *w32, double2 *ph, float2 *yb) {
   const int lane = threadIdx.x & 31;
-  const double s = sin_of_point(j, k);
-  for (int m = lane; m < j.M; m += 32) {
-    double sn, cs;
-    sincospi((double)m * s, &sn, &cs);
-    ph[m] = make_double2(cs, sn);
+  const uint64_t step = phase64_of_point(j, k);
+  const int M = j.M, Kf = j.Kf;
+  for (int m = lane; m < M; m += 32) ph[m] = phasor_q64((uint64_t)m * step);
+  __syncwarp();
+  int lpc = 1;
+  while (lpc < 32 && Kf * lpc * 2 <= 32 && lpc < M) lpc <<= 1;
+  const int epl = (M + lpc - 1) / lpc;     // elements per lane
+  const int sub = lane % lpc, cpp = 32 / lpc;
+  for (int c0 = 0; c0 < Kf; c0 += cpp) {
+    const int col = c0 + lane / lpc;
+    double yr = 0.0, yi = 0.0;
+    if (col < Kf) {
+      const double2 *f = j.F + (size_t)col * M;
+      const int m1 = min(M, (sub + 1) * epl);
+      for (int m = sub * epl; m < m1; ++m) {
+        const double2 b = f[m], a = ph[m];     // conj(b) * a
+        yr = fma(b.x, a.x, fma(b.y, a.y, yr));
+        yi = fma(b.x, a.y, fma(-b.y, a.x, yi));
+      }
+    }
+    for (int off = lpc >> 1; off > 0; off >>= 1) {
+      yr += __shfl_xor_sync(0xffffffffu, yr, off);
+      yi += __shfl_xor_sync(0xffffffffu, yi, off);
+    }
+    if (sub == 0 && col < Kf) yb[col] = make_float2((float)yr, (float)yi);
   }
   __syncwarp();
-  const int M = j.M;
-  if (M <= 32) {
-    const int MQ = M <= 8 ? 8 : (M <= 16 ? 16 : 32);
-    const int m = lane & (MQ - 1), grp = lane / MQ, ngrp = 32 / MQ;
-    const double2 a = m < M ? ph[m] : make_double2(0.0, 0.0);
-    for (int c0 = 0; c0 < j.Kf; c0 += ngrp) {
-      const int col = c0 + grp;
-      double yr = 0.0, yi = 0.0;
-      if (col < j.Kf && m < M) {
-        const double2 b = j.F[(size_t)col * M + m];   // conj(b) * a
-        yr = fma(b.x, a.x, b.y * a.y);
-        yi = fma(b.x, a.y, -b.y * a.x);
-      }
-      for (int off = MQ >> 1; off > 0; off >>= 1) {
-        yr += __shfl_xor_sync(0xffffffffu, yr, off);
-        yi += __shfl_xor_sync(0xffffffffu, yi, off);
-      }
-      if (m == 0 && col < j.Kf) yb[col] = make_double2(yr, yi);
-    }
-  } else {
-    const double2 a0 = ph[lane];
-    const double2 a1 = lane + 32 < M ? ph[lane + 32] : make_double2(0.0, 0.0);
-    for (int col = 0; col < j.Kf; ++col) {
-      const double2 b0 = j.F[(size_t)col * M + lane];
-      const double2 b1 = lane + 32 < M ? j.F[(size_t)col * M + lane + 32] : make_double2(0.0, 0.0);
-      double yr = fma(b0.x, a0.x, b0.y * a0.y), yi = fma(b0.x, a0.y, -b0.y * a0.x);
-      yr = fma(b1.x, a1.x, fma(b1.y, a1.y, yr));
-      yi = fma(b1.x, a1.y, fma(-b1.y, a1.x, yi));
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        yr += __shfl_xor_sync(0xffffffffu, yr, off);
-        yi += __shfl_xor_sync(0xffffffffu, yi, off);
-      }
-      if (lane == 0) yb[col] = make_double2(yr, yi);
-    }
-  }
-  __syncwarp();
-  // MUSIC / EV sums over the lanes' columns
-  double dm = 0.0, de = 0.0;
+  float dm = 0.f, de = 0.f;
   for (int c = lane; c < j.Kn; c += 32) {
-    const double2 y = yb[c];
-    const double n = fma(y.x, y.x, y.y * y.y);
+    const float2 y = yb[c];
+    const float n = fmaf(y.x, y.x, y.y * y.y);
     dm += n;
-    if (j.w) de = fma(j.w[c], n, de);
+    de = fmaf(w32[c], n, de);
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -171,34 +155,34 @@ inline __device__ void refine_point_warp(const ScanJob &j, int k, double2 *ph, d
     if (j.P[kRoMusic]) j.P[kRoMusic][k] = recip_out(dm);
     if (j.P[kRoEv]) j.P[kRoEv][k] = recip_out(de);
     if (j.P[kRoPhd]) {
-      const double2 y = yb[j.kphd];
-      j.P[kRoPhd][k] = recip_out(fma(y.x, y.x, y.y * y.y));
+      const float2 y = yb[j.kphd];
+      j.P[kRoPhd][k] = recip_out(fmaf(y.x, y.x, y.y * y.y));
     }
     if (j.P[kRoMn]) {
-      const double2 y = yb[j.kmn];
-      j.P[kRoMn][k] = recip_out(fma(y.x, y.x, y.y * y.y));
+      const float2 y = yb[j.kmn];
+      j.P[kRoMn][k] = recip_out(fmaf(y.x, y.x, y.y * y.y));
     }
   }
   __syncwarp();
 }
 
 // Same computation by a single thread (only when a tile's queue overflows).
-inline __device__ void refine_point_thread(const ScanJob &j, int k) {
-  const double s = sin_of_point(j, k);
-  double dm = 0.0, de = 0.0, dp = 0.0, dn = 0.0;
+inline __device__ void refine_point_thread(const ScanJob &j, int k, const float *w32) {
+  const uint64_t step = phase64_of_point(j, k);
+  float dm = 0.f, de = 0.f, dp = 0.f, dn = 0.f;
   for (int col = 0; col < j.Kf; ++col) {
     double yr = 0.0, yi = 0.0;
     for (int m = 0; m < j.M; ++m) {
-      double sn, cs;
-      sincospi((double)m * s, &sn, &cs);
+      const double2 a = phasor_q64((uint64_t)m * step);
       const double2 b = j.F[(size_t)col * j.M + m];
-      yr = fma(b.x, cs, fma(b.y, sn, yr));
-      yi = fma(b.x, sn, fma(-b.y, cs, yi));
+      yr = fma(b.x, a.x, fma(b.y, a.y, yr));
+      yi = fma(b.x, a.y, fma(-b.y, a.x, yi));
     }
-    const double n = fma(yr, yr, yi * yi);
+    const float fr = (float)yr, fi = (float)yi;
+    const float n = fmaf(fr, fr, fi * fi);
     if (col < j.Kn) {
       dm += n;
-      if (j.w) de = fma(j.w[col], n, de);
+      de = fmaf(w32[col], n, de);
     }
     if (col == j.kphd) dp = n;
     if (col == j.kmn) dn = n;
@@ -214,7 +198,7 @@ __device__ __forceinline__ void drain_refinements(const ScanJob &j, ScanShared &
   __syncthreads();
   const int n = min(sh.nflag, kFlagCap);
   const int warp = threadIdx.x >> 5;
-  for (int i = warp; i < n; i += kScanWarps) refine_point_warp(j, sh.flags[i], sh.ph[warp], sh.yb[warp]);
+  for (int i = warp; i < n; i += kScanWarps) refine_point_warp(j, sh.flags[i], sh.w32, sh.ph[warp], sh.yb[warp]);
   __syncthreads();
   if (threadIdx.x == 0) sh.nflag = 0;
   __syncthreads();
@@ -318,7 +302,7 @@ __device__ __forceinline__ void scan_points(const float2 *Bs, const ScanJob &j, 
   // queue overflow (more than kFlagCap small denominators in one tile): refine in place
 #pragma unroll
   for (int q = 0; q < PT; ++q)
-    if (pos[q] >= kFlagCap) refine_point_thread(j, k0 + q);
+    if (pos[q] >= kFlagCap) refine_point_thread(j, k0 + q, sh.w32);
 }
 
 }  // namespace scanc

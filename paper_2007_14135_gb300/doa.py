@@ -165,27 +165,39 @@ def make_problem(X: torch.Tensor, d: int, alg_mask: int, g: Grid, P: torch.Tenso
                    M, N, X.stride(0), d, alg_mask, prec, _dev(features), _dev(B_out))
 
 
+class Tuning(ctypes.Structure):
+    """doa_tuning: per-M-bucket launch shapes (0 = default)."""
+    _fields_ = [("scan_pt", ctypes.c_int32 * 4), ("eig_mats", ctypes.c_int32 * 4)]
+
+
 class BatchPlan:
     """Host plan bytes, their device copy, and the workspace size (doa_batch_plan).
 
-    scan_pt: None or 4 ints (grid points per scan thread for M <= 8, 16, 32, 64; 0 = default)."""
+    scan_pt: None or 4 ints (grid points per scan thread for M <= 8, 16, 32, 64; 0 = default).
+    eig_mats: None or 4 ints (matrices per Jacobi warp per bucket; 0 = default)."""
 
-    def __init__(self, problems: Sequence[Problem], device: str = "cuda", scan_pt: Optional[Sequence[int]] = None):
+    def __init__(self, problems: Sequence[Problem], device: str = "cuda", scan_pt: Optional[Sequence[int]] = None,
+                 eig_mats: Optional[Sequence[int]] = None):
         arr = (Problem * len(problems))(*problems)
-        pt = None if scan_pt is None else (ctypes.c_int32 * 4)(*[int(v) for v in scan_pt])
-        pt_ptr = None if pt is None else ctypes.cast(pt, ctypes.c_void_p)
+        tun = None
+        if scan_pt is not None or eig_mats is not None:
+            tun = Tuning((ctypes.c_int32 * 4)(*[int(v) for v in (scan_pt or (0, 0, 0, 0))]),
+                         (ctypes.c_int32 * 4)(*[int(v) for v in (eig_mats or (0, 0, 0, 0))]))
+        tun_ptr = None if tun is None else ctypes.cast(ctypes.pointer(tun), ctypes.c_void_p)
         n = lib().doa_batch_plan_bytes(arr, len(problems))
         ws = ctypes.c_size_t(0)
         bad = ctypes.c_int(-1)
         if n == 0:
-            st = lib().doa_batch_plan(arr, len(problems), pt_ptr, None, 0, ctypes.byref(ws), ctypes.byref(bad))
+            st = lib().doa_batch_plan(arr, len(problems), tun_ptr, None, 0, ctypes.byref(ws), ctypes.byref(bad))
             raise DoaError(st if st else EINVAL, f"doa_batch_plan (problem {bad.value})")
         self.host = np.zeros(n, dtype=np.uint8)
-        _check(lib().doa_batch_plan(arr, len(problems), pt_ptr, self.host.ctypes.data, n, ctypes.byref(ws),
+        _check(lib().doa_batch_plan(arr, len(problems), tun_ptr, self.host.ctypes.data, n, ctypes.byref(ws),
                                     ctypes.byref(bad)), f"doa_batch_plan (problem {bad.value})")
         self.ws_bytes = int(ws.value)
         self.nprob = len(problems)
-        self.scan_pt = [int(v) for v in self.host[:256].view(np.int32)[self.header_index("scan_pt"):][:4]]
+        hdr = self.host[:256].view(np.int32)
+        self.scan_pt = [int(v) for v in hdr[self.header_index("scan_pt"):][:4]]
+        self.eig_mats = [int(v) for v in hdr[self.header_index("eig_mats"):][:4]]
         self.dev = torch.from_numpy(self.host).to(device)
         self.problems = arr
 
@@ -193,7 +205,7 @@ class BatchPlan:
     def header_index(field: str) -> int:
         """int32 index of a PlanHeader field (layout of csrc/doa_internal.cuh)."""
         order = {"magic": 0, "nprob": 1, "njobs": 2, "ngrids": 3, "ncov": 4, "nreduce": 5, "eig_count": 6,
-                 "scan_jobs": 10, "scan_tiles": 14, "scan_pt": 22}
+                 "scan_jobs": 10, "scan_tiles": 14, "scan_pt": 22, "eig_mats": 58}
         return order[field]
 
     def launches(self) -> int:

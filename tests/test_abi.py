@@ -84,7 +84,7 @@ def test_batch_plan_layout(libdoa):
     hdr = buf[:64].view(np.int32)
     assert hdr[0] == 0x444F4131            # magic
     assert list(hdr[1:6]) == [3, 4 + 1 + 2, 2, 4 + 1 + 3, 2]   # nprob, njobs, ngrids, ncov, nreduce
-    # workspace: phase (uint32) and sine (double) tables per grid, then per problem R, the
+    # workspace: 32- and 64-bit phase tables per grid, then per problem R, the
     # covariance partials and one scan factor (M x (M+1) complex128 + M EV weights), each
     # allocation rounded up to 256 bytes
     def factor(M):
@@ -126,9 +126,9 @@ def test_batch_plan_scan_pt(libdoa):
     for pts, ok in [((1, 1, 1, 1), True), ((4, 4, 2, 1), True), ((2, 0, 0, 0), True), ((8, 0, 0, 0), False),
                     ((0, 0, 4, 0), False), ((0, 0, 0, 2), False)]:
         buf = np.zeros(n, np.uint8)
-        arrp = (ctypes.c_int32 * 4)(*pts)
-        st = libdoa.lib().doa_batch_plan(arr, 2, ctypes.cast(arrp, ctypes.c_void_p), buf.ctypes.data, n,
-                                         ctypes.byref(ws), None)
+        tun = libdoa.Tuning((ctypes.c_int32 * 4)(*pts), (ctypes.c_int32 * 4)(0, 0, 0, 0))
+        st = libdoa.lib().doa_batch_plan(arr, 2, ctypes.cast(ctypes.pointer(tun), ctypes.c_void_p), buf.ctypes.data,
+                                         n, ctypes.byref(ws), None)
         assert (st == 0) == ok, pts
         if ok:
             got = buf[:128].view(np.int32)[22:26]
@@ -137,3 +137,25 @@ def test_batch_plan_scan_pt(libdoa):
             tiles = buf[:128].view(np.int64)[7:11]      # scan_tiles per bucket
             # one scan job per problem: its four algorithms share the tiles of one grid pass
             assert tiles[0] == -(-1801 // (128 * want[0])) and tiles[3] == -(-18001 // 128)
+
+
+def test_batch_plan_eig_mats(libdoa):
+    """Matrices per Jacobi warp: allowed powers of two up to the bucket's lane budget, default by
+    problem count; written to the plan header."""
+    import numpy as np
+    probs = [_prob(libdoa, M=8, N=1000, d=2, mask=0b0010, L=1801, step=0.1), _prob(libdoa, M=16, N=3000, d=5),
+             _prob(libdoa, M=20, N=300, d=2, mask=1, L=1801, step=0.1)]
+    arr = (libdoa.Problem * 3)(*probs)
+    n = libdoa.lib().doa_batch_plan_bytes(arr, 3)
+    ws = ctypes.c_size_t(0)
+    for em, ok in [((0, 0, 0, 0), True), ((8, 4, 2, 1), True), ((1, 2, 1, 0), True), ((16, 0, 0, 0), False),
+                   ((0, 8, 0, 0), False), ((0, 0, 4, 0), False), ((0, 0, 0, 2), False), ((3, 0, 0, 0), False)]:
+        buf = np.zeros(n, np.uint8)
+        tun = libdoa.Tuning((ctypes.c_int32 * 4)(0, 0, 0, 0), (ctypes.c_int32 * 4)(*em))
+        st = libdoa.lib().doa_batch_plan(arr, 3, ctypes.cast(ctypes.pointer(tun), ctypes.c_void_p), buf.ctypes.data,
+                                         n, ctypes.byref(ws), None)
+        assert (st == 0) == ok, em
+        if ok:
+            got = list(buf[:256].view(np.int32)[58:62])
+            # default with one problem per bucket: no packing
+            assert got == [v if v else 1 for v in em], (em, got)

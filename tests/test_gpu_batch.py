@@ -33,12 +33,14 @@ def _uneven(torch, doa, n=48, thin=True):
 
 
 def test_tile_shapes_give_identical_spectra(env):
-    """The points-per-thread knob changes the tiling only: every point is bit-identical."""
+    """The points-per-thread and matrices-per-warp knobs change the launch shape only: every
+    point is bit-identical."""
     torch, doa = env
     insts, tensors, probs = _uneven(torch, doa, n=40)
     outs = []
-    for pts in [(1, 1, 1, 1), (4, 2, 1, 1), (2, 4, 2, 1)]:
-        plan = doa.BatchPlan(probs, scan_pt=pts)
+    for pts, em in [((1, 1, 1, 1), (1, 1, 1, 1)), ((4, 2, 1, 1), (8, 4, 2, 1)), ((2, 4, 2, 1), (2, 2, 1, 1))]:
+        plan = doa.BatchPlan(probs, scan_pt=pts, eig_mats=em)
+        assert plan.eig_mats == list(em)
         ws = doa.workspace(plan)
         status = torch.full((plan.nprob,), -1, dtype=torch.int32, device="cuda")
         doa.doa_solve_batch(plan, ws, status)
@@ -91,12 +93,15 @@ def test_autotuner_picks_allowed_tiles_and_persists(env, tmp_path):
     insts, tensors, probs = _uneven(torch, doa, n=24)
     path = str(tmp_path / "tune.json")
     log = []
-    pts = autotune.tune(probs, path=path, log=log, reps=1)
-    assert len(pts) == 4
+    pts, em = autotune.tune(probs, path=path, log=log, reps=1)
+    assert len(pts) == 4 and len(em) == 4
     for b, p in enumerate(pts):
         assert p in autotune.CANDIDATES[b]
     table = json.load(open(path))
     assert len(table) == len(log) >= 1
     for entry in log:
-        assert set(entry["ms"]) == set(autotune.CANDIDATES[entry["bucket"]])
-    assert autotune.tune(probs, path=path) == pts          # second call: from the table, no timing
+        b = entry["bucket"]
+        assert set(entry["scan_ms"]) == set(autotune.CANDIDATES[b])
+        assert set(entry["eig_ms"]) == set(autotune.EIG_CANDIDATES[b])
+        assert em[b] in autotune.EIG_CANDIDATES[b]
+    assert autotune.tune(probs, path=path) == (pts, em)    # second call: from the table, no timing
