@@ -52,6 +52,7 @@ bool problem_ok(const doa_problem &p) {
 
 struct PlanSizes {
   int nprob = 0, njobs = 0, ngrids = 0, ncov = 0, nreduce = 0;
+  int cov_class[kCovClasses] = {0, 0, 0, 0};
   int eig[kNumBuckets] = {0, 0, 0, 0};
   int scan[kNumBuckets] = {0, 0, 0, 0};
 };
@@ -74,6 +75,7 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
     }
     int chunks = (p.N + kCovChunk - 1) / kCovChunk;
     sz.ncov += chunks;
+    sz.cov_class[cov_class(p.M)] += chunks;
     sz.nreduce += chunks > 1;
     sz.eig[m_bucket(p.M)] += 1;
     sz.njobs += __builtin_popcount(p.alg_mask);
@@ -249,7 +251,12 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     ws = round_up(ws + (int64_t)grids[g].L * 8, 256);
     h.grid_points += grids[g].L;
   }
-  int icov = 0, ired = 0, ijob = 0;
+  int icov[kCovClasses], ired = 0, ijob = 0;
+  h.cov_first[0] = 0;
+  for (int c = 0; c < kCovClasses; ++c) {
+    h.cov_first[c + 1] = h.cov_first[c] + sz.cov_class[c];
+    icov[c] = h.cov_first[c];
+  }
   int ie[kNumBuckets] = {0, 0, 0, 0}, is[kNumBuckets] = {0, 0, 0, 0};
   int64_t tiles[kNumBuckets] = {0, 0, 0, 0};
   for (int i = 0; i < nprob; ++i) {
@@ -266,7 +273,7 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
       ws = round_up(ws + mm * q.nchunks, 256);
       reduce[ired++] = i;
     }
-    for (int c = 0; c < q.nchunks; ++c) cov[icov++] = PlanCovItem{i, c};
+    for (int c = 0; c < q.nchunks; ++c) cov[icov[cov_class(M)]++] = PlanCovItem{i, c};
     eig[b][ie[b]++] = i;
     q.grid_id = grid_of[i];
     q.first_job = ijob;

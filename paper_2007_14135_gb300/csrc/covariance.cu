@@ -219,11 +219,217 @@ __global__ void __launch_bounds__(kCovThreads) covariance_cluster_kernel(const f
   cluster.sync();  // keep every CTA's partial alive until rank 0 has read it
 }
 
-// Batch: one CTA per work item (problem, chunk).
-__global__ void __launch_bounds__(kCovThreads) covariance_batch_kernel(const uint8_t *plan, uint8_t *ws) {
+// ------------------------------------------------------------------------------------------
+// Block-task form for 4 < M <= 16 (MB = ceil(M/4) in {2, 3, 4}). The upper triangle is cut into
+// tasks of equal work: every off-diagonal 4x4 block (16 complex entries, 64 real MACs per
+// snapshot) and every pair of diagonal blocks (4 real diagonal entries + 6 complex entries each,
+// 2 x 32 MACs), so no lane computes a lower-triangle entry or the zero imaginary part of the
+// diagonal. A warp owns one task (warp-uniform code path) and its lanes take snapshots
+// t = g, g + G, ... of each tile, G = the task's lanes; tiles of kTS = max(64, G) snapshots are
+// prefetched into registers while the previous tile is being consumed. Every task has 32 real
+// accumulators per lane; at the end the G lane partials of each accumulator are added in lane
+// order in double-float arithmetic (deterministic).
+// ------------------------------------------------------------------------------------------
+template <int MB>
+struct CovTasks {
+  static constexpr int kOff = MB * (MB - 1) / 2;
+  static constexpr int kDiag = (MB + 1) / 2;
+  static constexpr int kTasks = kOff + kDiag;
+  static constexpr int kWpt = kTasks >= 8 ? 1 : 8 / kTasks;        // warps per task
+  static constexpr int kThreads = 32 * kWpt * kTasks;
+  static constexpr int kG = 32 * kWpt;                              // snapshot lanes per task
+  static constexpr int kTS = kG >= 64 ? kG : 64;
+  static constexpr int kMP = 4 * MB;
+  static constexpr int kLoads = (kMP * kTS + kThreads - 1) / kThreads;
+  static constexpr int kStageBytes = kTasks * 32 * kG * 8;          // (hi, lo) per lane per accumulator
+  static constexpr int kTileBytes = kMP * kTS * 8;
+  static constexpr int kSmem = kStageBytes > kTileBytes ? kStageBytes : kTileBytes;
+};
+
+// Accumulator a (0..31) of task `task` -> (row, col, imaginary?) ; false if outside M.
+template <int MB>
+__device__ __forceinline__ bool task_slot(int task, int a, int M, int &row, int &col, bool &imag, bool &diag) {
+  using T = CovTasks<MB>;
+  if (task < T::kOff) {
+    int bi = 0, rem = task;
+    while (rem >= MB - 1 - bi) { rem -= MB - 1 - bi; ++bi; }
+    const int bj = bi + 1 + rem;
+    const int e = a >> 1;
+    row = bi * 4 + (e >> 2);
+    col = bj * 4 + (e & 3);
+    imag = a & 1;
+    diag = false;
+  } else {
+    const int b = 2 * (task - T::kOff) + (a >> 4);
+    const int s = a & 15;                 // 0..3: diagonal entries; 4..15: (re, im) of the 6 pairs
+    if (s < 4) {
+      row = col = b * 4 + s;
+      imag = false;
+      diag = true;
+    } else {
+      const int pr = (s - 4) >> 1;        // pair index of (i, j), i < j, in row-major order
+      constexpr int pi[6] = {0, 0, 0, 1, 1, 2}, pj[6] = {1, 2, 3, 2, 3, 3};
+      row = b * 4 + pi[pr];
+      col = b * 4 + pj[pr];
+      imag = (s - 4) & 1;
+      diag = false;
+    }
+    if (b >= MB) return false;
+  }
+  return row < M && col < M;
+}
+
+template <int MB, bool kComp>
+__device__ __forceinline__ void task_macs(int task, const float2 *tile, int t, float (&hi)[32], float (&lo)[32]) {
+  using T = CovTasks<MB>;
+  if (task < T::kOff) {
+    int bi = 0, rem = task;
+    while (rem >= MB - 1 - bi) { rem -= MB - 1 - bi; ++bi; }
+    const int bj = bi + 1 + rem;
+    float2 xa[4], xb[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      xa[i] = tile[(bi * 4 + i) * T::kTS + t];
+      xb[i] = tile[(bj * 4 + i) * T::kTS + t];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int a = 2 * (i * 4 + j);
+        // x_a conj(x_b) = (ar br + ai bi) + j (ai br - ar bi)
+        mac<kComp>(hi[a], lo[a], xa[i].x, xb[j].x);
+        mac<kComp>(hi[a], lo[a], xa[i].y, xb[j].y);
+        mac<kComp>(hi[a + 1], lo[a + 1], xa[i].y, xb[j].x);
+        mac<kComp>(hi[a + 1], lo[a + 1], -xa[i].x, xb[j].y);
+      }
+  } else {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int b = 2 * (task - T::kOff) + h;
+      if (b >= MB) break;
+      float2 x[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x[i] = tile[(b * 4 + i) * T::kTS + t];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        mac<kComp>(hi[16 * h + i], lo[16 * h + i], x[i].x, x[i].x);
+        mac<kComp>(hi[16 * h + i], lo[16 * h + i], x[i].y, x[i].y);
+      }
+      int a = 16 * h + 4;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = i + 1; j < 4; ++j) {
+          mac<kComp>(hi[a], lo[a], x[i].x, x[j].x);
+          mac<kComp>(hi[a], lo[a], x[i].y, x[j].y);
+          mac<kComp>(hi[a + 1], lo[a + 1], x[i].y, x[j].x);
+          mac<kComp>(hi[a + 1], lo[a + 1], -x[i].x, x[j].y);
+          a += 2;
+        }
+    }
+  }
+}
+
+template <int MB, bool kComp>
+__device__ void cov_tasks(const float2 *__restrict__ X, int M, int ldx, int t0, int t1, uint8_t *smem,
+                          int nchunks, double inv_n, double2 *R64, double2 *partial) {
+  using T = CovTasks<MB>;
+  float2 *tile = reinterpret_cast<float2 *>(smem);
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int task = warp / T::kWpt;
+  const int g = (warp % T::kWpt) * 32 + lane;
+  float hi[32], lo[32];
+#pragma unroll
+  for (int a = 0; a < 32; ++a) hi[a] = lo[a] = 0.f;
+  float2 pre[T::kLoads];
+  auto fetch = [&](int ts) {
+    const int cnt = min(T::kTS, t1 - ts);
+#pragma unroll
+    for (int q = 0; q < T::kLoads; ++q) {
+      const int e = tid + q * T::kThreads;
+      const int r = e / T::kTS, t = e % T::kTS;
+      pre[q] = (e < T::kMP * T::kTS && r < M && t < cnt) ? X[(size_t)r * ldx + ts + t] : make_float2(0.f, 0.f);
+    }
+  };
+  if (t0 < t1) fetch(t0);
+  for (int ts = t0; ts < t1; ts += T::kTS) {
+    const int cnt = min(T::kTS, t1 - ts);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < T::kLoads; ++q) {
+      const int e = tid + q * T::kThreads;
+      if (e < T::kMP * T::kTS) tile[e] = pre[q];
+    }
+    __syncthreads();
+    if (ts + T::kTS < t1) fetch(ts + T::kTS);
+    for (int t = g; t < cnt; t += T::kG) task_macs<MB, kComp>(task, tile, t, hi, lo);
+  }
+  // lane partials -> shared memory, then one thread per (task, accumulator) adds them in order
+  __syncthreads();
+  float2 *stage = reinterpret_cast<float2 *>(smem);   // [task][a][g]
+#pragma unroll
+  for (int a = 0; a < 32; ++a) stage[((size_t)task * 32 + a) * T::kG + g] = make_float2(hi[a], lo[a]);
+  __syncthreads();
+  for (int item = tid; item < T::kTasks * 32; item += T::kThreads) {
+    const int tk = item / 32, a = item % 32;
+    int row, col;
+    bool imag, diag;
+    if (!task_slot<MB>(tk, a, M, row, col, imag, diag)) continue;
+    const float2 *v = stage + (size_t)item * T::kG;
+    float sh = v[0].x, sl = v[0].y;
+    for (int q = 1; q < T::kG; ++q) df_add(sh, sl, v[q].x, v[q].y);
+    const double val = (double)sh + (double)sl;
+    if (nchunks == 1) {
+      const double x = val * inv_n;
+      double *up = reinterpret_cast<double *>(R64 + row * M + col), *dn = reinterpret_cast<double *>(R64 + col * M + row);
+      if (diag) {
+        up[0] = x;
+        up[1] = 0.0;
+      } else if (imag) {
+        up[1] = x;
+        dn[1] = -x;
+      } else {
+        up[0] = x;
+        dn[0] = x;
+      }
+    } else {
+      double *pv = reinterpret_cast<double *>(partial + row * M + col);
+      if (diag) {
+        pv[0] = val;
+        pv[1] = 0.0;
+      } else {
+        pv[imag ? 1 : 0] = val;
+      }
+    }
+  }
+}
+
+template <int MB>
+__global__ void __launch_bounds__(CovTasks<MB>::kThreads) covariance_tasks_kernel(const uint8_t *plan, uint8_t *ws,
+                                                                                  int first) {
   extern __shared__ __align__(16) uint8_t smem[];
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
-  const PlanCovItem it = reinterpret_cast<const PlanCovItem *>(plan + h->off_cov)[blockIdx.x];
+  const PlanCovItem it = reinterpret_cast<const PlanCovItem *>(plan + h->off_cov)[first + blockIdx.x];
+  const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[it.prob];
+  const int M = pp.p.M, N = pp.p.N;
+  const int t0 = it.chunk * kCovChunk, t1 = min(N, t0 + kCovChunk);
+  const float2 *X = reinterpret_cast<const float2 *>(pp.p.X);
+  double2 *R64 = reinterpret_cast<double2 *>(ws + pp.r64_off);
+  double2 *partial = reinterpret_cast<double2 *>(ws + pp.part_off) + (size_t)it.chunk * M * M;
+  const double inv_n = 1.0 / (double)N;
+  if (pp.p.alg_mask & (1u << DOA_PHD))
+    cov_tasks<MB, true>(X, M, pp.p.ldx, t0, t1, smem, pp.nchunks, inv_n, R64, partial);
+  else
+    cov_tasks<MB, false>(X, M, pp.p.ldx, t0, t1, smem, pp.nchunks, inv_n, R64, partial);
+}
+
+// Batch: one CTA per work item (problem, chunk) of the generic class.
+__global__ void __launch_bounds__(kCovThreads) covariance_batch_kernel(const uint8_t *plan, uint8_t *ws, int first) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
+  const PlanCovItem it = reinterpret_cast<const PlanCovItem *>(plan + h->off_cov)[first + blockIdx.x];
   const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[it.prob];
   const int M = pp.p.M, N = pp.p.N;
   CovLayout lay(M);
@@ -297,6 +503,22 @@ cudaError_t launch_covariance_single(const float2 *X, int M, int N, int ldx, flo
   return cudaLaunchKernelEx(&cfg, covariance_cluster_kernel, X, M, N, ldx, per, R, R64);
 }
 
+template <int MB>
+cudaError_t launch_tasks(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s) {
+  using T = CovTasks<MB>;
+  const int c = MB - 2, n = h.cov_first[c + 1] - h.cov_first[c];
+  if (n == 0) return cudaSuccess;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(covariance_tasks_kernel<MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         T::kSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  covariance_tasks_kernel<MB><<<n, T::kThreads, T::kSmem, s>>>(plan_dev, ws, h.cov_first[c]);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_covariance_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws,
                                     cudaStream_t s) {
   static bool attr = false;
@@ -306,7 +528,13 @@ cudaError_t launch_covariance_batch(const uint8_t *plan_dev, const PlanHeader &h
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  if (h.ncov > 0) covariance_batch_kernel<<<h.ncov, kCovThreads, kSmemBytes, s>>>(plan_dev, ws);
+  cudaError_t e;
+  if ((e = launch_tasks<2>(plan_dev, h, ws, s)) != cudaSuccess) return e;
+  if ((e = launch_tasks<3>(plan_dev, h, ws, s)) != cudaSuccess) return e;
+  if ((e = launch_tasks<4>(plan_dev, h, ws, s)) != cudaSuccess) return e;
+  const int ngen = h.cov_first[kCovClasses] - h.cov_first[kCovClasses - 1];
+  if (ngen > 0)
+    covariance_batch_kernel<<<ngen, kCovThreads, kSmemBytes, s>>>(plan_dev, ws, h.cov_first[kCovClasses - 1]);
   if (h.nreduce > 0) covariance_reduce_batch<<<h.nreduce, 256, 0, s>>>(plan_dev, ws);
   return cudaGetLastError();
 }

@@ -130,6 +130,14 @@ __device__ __forceinline__ double2 phasor_q64(uint64_t phi) {
 // ------------------------------------------------------------------------------------------
 constexpr uint32_t kPlanMagic = 0x444f4131u;  // "DOA1"
 constexpr int kNumBuckets = 4;                // M <= 8, <= 16, <= 32, <= 64
+// Covariance work-item classes: 4x4 register blocks per row, MB = ceil(M / 4) in {2, 3, 4} use
+// the block-task kernel (one launch per class, CTA shape fixed by MB); every other M the
+// generic kernel.
+constexpr int kCovClasses = 4;
+__host__ __device__ inline int cov_class(int M) {
+  const int mb = (M + 3) / 4;
+  return (mb >= 2 && mb <= 4) ? mb - 2 : 3;
+}
 
 struct PlanProblem {
   doa_problem p;          // the caller's descriptor
@@ -184,12 +192,15 @@ struct PlanHeader {
   int64_t off_prob, off_job, off_grid, off_cov, off_reduce, off_eig[kNumBuckets],
       off_scan[kNumBuckets], off_grid_pts;
   int32_t eig_mats[kNumBuckets];         // matrices per Jacobi warp, per M bucket
+  int32_t cov_first[kCovClasses + 1];    // covariance items sorted by class: class c owns
+                                         // items [cov_first[c], cov_first[c + 1])
 };
 
 // The Python binding reads these header fields by position (int32 index 22 = scan_pt, 58 = eig_mats).
 static_assert(offsetof(PlanHeader, scan_pt) == 88, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, scan_tiles) == 56, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, eig_mats) == 232, "PlanHeader layout changed");
+static_assert(offsetof(PlanHeader, cov_first) == 248, "PlanHeader layout changed");
 
 // Scan tiles: kScanThreads threads, each evaluating PT consecutive grid points (tile shape
 // 128 x PT). PT is chosen per M bucket (the autotuner's knob); the register budget limits it

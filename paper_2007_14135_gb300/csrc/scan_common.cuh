@@ -102,7 +102,7 @@ __device__ __forceinline__ uint64_t phase64_of_point(const ScanJob &j, int k) {
   return phase_step64_of_sin(sin(theta * 0.017453292519943295));
 }
 
-__device__ __forceinline__ float recip_out(float den) { return 1.0f / fmaxf(den, FLT_MIN); }
+__device__ __forceinline__ float recip_out(float den) { return __frcp_rn(fmaxf(den, FLT_MIN)); }
 
 // Re-evaluation of local point k by one whole warp with the steering vector and the contraction
 // in FP64: phasors from the exact 64-bit phase m * S64 (lane m), then y_c = f_c^H a with LPC
@@ -223,15 +223,25 @@ __device__ __forceinline__ void store_row(float *P, int L, int k0, const float (
 template <int MP, int PT>
 __device__ __forceinline__ void scan_points(const float2 *Bs, const ScanJob &j, const uint32_t *S, int L, int k0,
                                             ScanShared &sh) {
+  // Steering phasors a_m, m = 4i + r: a_{4i} and a_r (r = 1..3) from their exact integer phases,
+  // the rest as the product a_{4i} a_r (one FP32 complex multiply of two polynomial phasors).
+  static_assert(MP % 4 == 0, "MP is a multiple of 4");
   float2 a[PT][MP];
 #pragma unroll
   for (int q = 0; q < PT; ++q) {
-    uint32_t step = (k0 + q < L) ? S[k0 + q] : 0u;
-    uint32_t phi = 0u;
+    const uint32_t step = (k0 + q < L) ? S[k0 + q] : 0u;
+    a[q][0] = make_float2(1.f, 0.f);
 #pragma unroll
-    for (int m = 0; m < MP; ++m) {
-      a[q][m] = phasor_q32(phi);
-      phi += step;
+    for (int r = 1; r < 4; ++r) a[q][r] = phasor_q32((uint32_t)r * step);
+#pragma unroll
+    for (int i = 1; i < MP / 4; ++i) {
+      const float2 A = phasor_q32((uint32_t)(4 * i) * step);
+      a[q][4 * i] = A;
+#pragma unroll
+      for (int r = 1; r < 4; ++r) {
+        const float2 z = a[q][r];
+        a[q][4 * i + r] = make_float2(fmaf(A.x, z.x, -A.y * z.y), fmaf(A.x, z.y, A.y * z.x));
+      }
     }
   }
   float dm[PT], de[PT], dp[PT], dn[PT];
@@ -280,7 +290,7 @@ __device__ __forceinline__ void scan_points(const float2 *Bs, const ScanJob &j, 
   if (j.P[R]) {                                                               \
     const float thr = sh.thr[R];                                              \
     _Pragma("unroll") for (int q = 0; q < PT; ++q) {                          \
-      out[q] = 1.0f / fmaxf(DEN[q], FLT_MIN);                                 \
+      out[q] = __frcp_rn(fmaxf(DEN[q], FLT_MIN));                              \
       flag[q] = flag[q] || DEN[q] < thr;                                      \
     }                                                                         \
     store_row<PT>(j.P[R], L, k0, out);                                        \

@@ -264,6 +264,46 @@ def test_batch_uneven_sample(env):
     _check_batch(torch, doa, insts, [1 << s.alg for s in picked])
 
 
+@pytest.mark.parametrize("mask", [1 << PHD, 1 << MUSIC])
+def test_batch_covariance_entries(env, mask):
+    """Every covariance work-item class of the batch (M in 4..17, one and several 1024-snapshot
+    chunks, compensated for PHD and plain otherwise): the trace-normalised upper triangle the
+    batch writes as the proposal features matches the oracle's R entry by entry, and the
+    eigenvalues follow R to FP64 accuracy in the compensated mode."""
+    torch, doa = env
+    cases = [(4, 700), (5, 1500), (8, 1024), (9, 2500), (12, 333), (13, 4096), (16, 3000), (17, 1100)]
+    insts = [synth.custom(M, 1, N, None, 10.0, 1.0, seed=950 + M) for M, N in cases]
+    tensors, probs = [], []
+    for inst in insts:
+        M = inst.M
+        X = torch.from_numpy(inst.X).cuda()
+        P = torch.empty(inst.L, dtype=torch.float32, device="cuda")
+        idx = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        val = torch.zeros(1, dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        ev = torch.empty(M, dtype=torch.float64, device="cuda")
+        F = torch.empty(M * (M + 1), dtype=torch.float32, device="cuda")
+        tensors.append((X, P, idx, val, cnt, ev, F))
+        probs.append(doa.make_problem(X, 1, mask, doa.grid(inst.lo, inst.step, inst.L), P, idx, val, cnt, ev,
+                                      features=F))
+    plan = doa.BatchPlan(probs)
+    ws = doa.workspace(plan)
+    status = torch.full((len(insts),), -1, dtype=torch.int32, device="cuda")
+    doa.doa_solve_batch(plan, ws, status)
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    for inst, t in zip(insts, tensors):
+        M = inst.M
+        R = oracle.covariance(inst.X)
+        iu = np.triu_indices(M)
+        want = np.stack([R[iu].real, R[iu].imag], axis=1).reshape(-1) / np.trace(R).real
+        got = t[6].cpu().numpy()
+        np.testing.assert_allclose(got, want, rtol=0, atol=2e-6 * np.max(np.abs(want)), err_msg=f"M={M}")
+        ev_ref, _, _ = oracle.eigh(R)
+        tol = (1e-10 if mask == 1 << PHD else 1e-5) * ev_ref[0]
+        np.testing.assert_allclose(t[5].cpu().numpy(), ev_ref, rtol=0, atol=tol, err_msg=f"M={M}")
+
+
 def test_batch_every_algorithm_subset(env):
     """All 15 non-empty algorithm sets, over every M bucket: the shared-contraction scan reads
     each requested spectrum from one factor (E_n with PHD / EV / MUSIC readouts, valph for MN,
