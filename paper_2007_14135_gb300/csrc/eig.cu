@@ -224,6 +224,248 @@ __device__ void jacobi_group(EigSmem<NP> *mats, const int *Ms, const double2 *co
     if ((live >> j) & 1u) res[j] = -DOA_ENOCONV;
 }
 
+// ------------------------------------------------------------------------------------------
+// Double-float Jacobi for the batch. GB300 issues FP64 at ~1/64 of its FP32 rate, so the batch
+// runs the same cyclic Jacobi with A and V held as unevaluated sums hi + lo of two FP32 numbers
+// (about 48 significant bits) and every element update done on the FP32 pipe: each new real part
+// is a three-term dot product of double-float numbers, formed with exact FMA products and
+// TwoSum (a compensated dot product, relative error a few 2^-48 of the sum of |terms|).
+// The rotation angle only needs to be good to FP32: tau, t and (c, sigma) are computed in FP32
+// from the hi parts (the diagonal difference from hi and lo), then (c, sigma) is scaled by
+// 1/sqrt(c^2 + |sigma|^2) to double-float accuracy, so every applied rotation is unitary to
+// ~1e-15; a_pq is left at its computed residual (about 1e-7 of its old value) instead of being
+// set to zero, and the next sweep removes it. Converged when a sweep rotates no pair with
+// |a_pq| > kJacobiTolDF sqrt(|a_pp a_qq|). A and V are converted to FP64 in place at the end.
+// ------------------------------------------------------------------------------------------
+constexpr float kJacobiTolDF = 1e-12f;
+
+struct F2 {
+  float h, l;
+};
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// u1 v1 + u2 v2 + u3 v3 in double-float.
+__device__ __forceinline__ F2 dot3(F2 u1, F2 v1, F2 u2, F2 v2, F2 u3, F2 v3) {
+  const float p1 = __fmul_rn(u1.h, v1.h), p2 = __fmul_rn(u2.h, v2.h), p3 = __fmul_rn(u3.h, v3.h);
+  float low = __fmaf_rn(u1.h, v1.h, -p1);
+  low = __fadd_rn(low, __fmaf_rn(u2.h, v2.h, -p2));
+  low = __fadd_rn(low, __fmaf_rn(u3.h, v3.h, -p3));
+  low = __fadd_rn(low, __fmaf_rn(u1.h, v1.l, __fmul_rn(u1.l, v1.h)));
+  low = __fadd_rn(low, __fmaf_rn(u2.h, v2.l, __fmul_rn(u2.l, v2.h)));
+  low = __fadd_rn(low, __fmaf_rn(u3.h, v3.l, __fmul_rn(u3.l, v3.h)));
+  float s, e1, e2;
+  two_sum_f(p1, p2, s, e1);
+  two_sum_f(s, p3, s, e2);
+  low = __fadd_rn(low, __fadd_rn(e1, e2));
+  F2 r;
+  two_sum_f(s, low, r.h, r.l);
+  return r;
+}
+
+__device__ __forceinline__ F2 neg(F2 a) { return F2{-a.h, -a.l}; }
+__device__ __forceinline__ F2 re_of(float4 v) { return F2{v.x, v.y}; }
+__device__ __forceinline__ F2 im_of(float4 v) { return F2{v.z, v.w}; }
+__device__ __forceinline__ float4 cplx(F2 re, F2 im) { return make_float4(re.h, re.l, im.h, im.l); }
+__device__ __forceinline__ float4 df_of(double2 v) {
+  const float rh = (float)v.x, ih = (float)v.y;
+  return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+}
+
+struct RotDF {
+  F2 c, sr, si;   // cosine and sigma = s e^{j phi}, each hi + lo
+};
+
+template <int NP>
+struct EigSmemDF {   // the same bytes as EigSmem<NP>, viewed as double-float
+  float4 A[NP][NP + 1];
+  float4 V[NP][NP + 1];
+  RotDF rot[NP / 2];
+};
+static_assert(sizeof(RotDF) == sizeof(Rot), "rotation records share storage");
+
+template <int NP>
+__device__ __forceinline__ bool rotation_df(EigSmemDF<NP> &s, int p, int q, RotDF &ro) {
+  const float4 app = s.A[p][p], aqq = s.A[q][q], apq = s.A[p][q];
+  const float n2 = apq.x * apq.x + apq.z * apq.z;
+  if (!(n2 > 0.f) || !(n2 > kJacobiTolDF * kJacobiTolDF * fabsf(app.x * aqq.x))) return false;
+  const float r = rsqrtf(n2);                                   // 1 / |a_pq|
+  const float diff = __fadd_rn(__fsub_rn(aqq.x, app.x), __fsub_rn(aqq.y, app.y));
+  const float tau = diff * (0.5f * r);
+  float t;
+  if (fabsf(tau) > 1e4f) {
+    t = 0.5f / tau;                                             // 1/(2 tau), relative error < tau^-2 / 4
+  } else {
+    t = copysignf(1.f / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f))), tau);
+  }
+  const float c0 = rsqrtf(fmaf(t, t, 1.f));
+  const float sn = t * c0 * r;
+  const float sr0 = sn * apq.x, si0 = sn * apq.z;
+  // n = c0^2 + sr0^2 + si0^2 exactly to double-float; scale all three by 1/sqrt(n) = 1 + eps
+  const float q1 = __fmul_rn(c0, c0), q2 = __fmul_rn(sr0, sr0), q3 = __fmul_rn(si0, si0);
+  float low = __fadd_rn(__fadd_rn(__fmaf_rn(c0, c0, -q1), __fmaf_rn(sr0, sr0, -q2)), __fmaf_rn(si0, si0, -q3));
+  float sum, e1, e2;
+  two_sum_f(q1, q2, sum, e1);
+  two_sum_f(sum, q3, sum, e2);
+  const float delta = __fadd_rn(__fsub_rn(sum, 1.f), __fadd_rn(low, __fadd_rn(e1, e2)));
+  const float eps = delta * fmaf(0.375f, delta, -0.5f);        // (1 + delta)^(-1/2) - 1 to O(delta^3)
+  ro = RotDF{F2{c0, c0 * eps}, F2{sr0, sr0 * eps}, F2{si0, si0 * eps}};
+  return true;
+}
+
+// Same contract as jacobi_group, in double-float arithmetic; on return A and V hold FP64.
+template <int NP, int G>
+__device__ void jacobi_group_df(EigSmem<NP> *mats64, const int *Ms, const double2 *const *Rs, int *res) {
+  constexpr int HP = NP / 2;
+  constexpr int T = grp_threads<NP>();
+  using g = Grp<T>;
+  static_assert(sizeof(EigSmemDF<NP>) <= sizeof(EigSmem<NP>), "double-float view fits");
+  // matrix j's double-float view starts where its EigSmem record starts (the records are laid out
+  // with the EigSmem stride, so the view is formed per matrix, never by indexing a view array)
+  auto df = [&](int j) -> EigSmemDF<NP> & { return *reinterpret_cast<EigSmemDF<NP> *>(&mats64[j]); };
+  const int lane = g::id();
+  unsigned live = 0u;
+  for (int j = 0; j < G; ++j) {
+    const int M = Ms[j];
+    res[j] = 0;
+    if (M <= 0) continue;
+    EigSmemDF<NP> &s = df(j);
+    const double2 *R = Rs[j];
+    bool finite = true;
+    for (int e = lane; e < M * M; e += T) {
+      int i = e / M, k = e % M;
+      double2 v;
+      if (i <= k) {
+        v = R[i * M + k];
+      } else {
+        v = R[k * M + i];
+        v.y = -v.y;
+      }
+      if (i == k) v.y = 0.0;
+      finite = finite && isfinite(v.x) && isfinite(v.y);
+      s.A[i][k] = df_of(v);
+      s.V[i][k] = make_float4(i == k ? 1.f : 0.f, 0.f, 0.f, 0.f);
+    }
+    if (g::all(finite))
+      live |= 1u << j;
+    else
+      res[j] = -DOA_ENONFINITE;
+  }
+  g::sync();
+  int maxn = 0;
+  for (int j = 0; j < G; ++j)
+    if ((live >> j) & 1u) maxn = max(maxn, (Ms[j] + 1) & ~1);
+  const int lj = lane < 32 ? lane / HP : G, li = lane % HP;
+  for (int sweep = 1; sweep <= kMaxSweeps && live; ++sweep) {
+    unsigned rotated = 0u;
+    for (int r = 0; r < maxn - 1; ++r) {
+      bool act = false;
+      if (lj < G && ((live >> lj) & 1u)) {
+        const int M = Ms[lj], n = (M + 1) & ~1;
+        if (r < n - 1 && li < n / 2) {
+          const int a = rr_player(li, r, n), b = rr_player(n - 1 - li, r, n);
+          const int p = min(a, b), q = max(a, b);
+          if (q < M) {
+            RotDF ro;
+            if (rotation_df<NP>(df(lj), p, q, ro)) {
+              act = true;
+              df(lj).rot[li] = ro;
+              mats64[lj].pq[li] = make_int2(p, q);
+            }
+          }
+        }
+      }
+      unsigned mask;
+      if (T == 32) {
+        mask = __ballot_sync(0xffffffffu, act);
+      } else {
+        const unsigned m0 = __ballot_sync(0xffffffffu, act);
+        if (threadIdx.x == 0) mats64[0].mask = m0;
+        __syncthreads();
+        mask = mats64[0].mask;
+        __syncthreads();
+      }
+      if (mask == 0u) continue;
+      g::sync();
+      // rows: A <- J^H A. new row p = c x_p - sigma x_q; new row q = conj(sigma) x_p + c x_q
+      for (int j = 0; j < G; ++j) {
+        const unsigned seg = (mask >> (j * HP)) & ((HP == 32) ? 0xffffffffu : ((1u << HP) - 1u));
+        if (!seg) continue;
+        rotated |= 1u << j;
+        EigSmemDF<NP> &s = df(j);
+        const int M = Ms[j];
+        for (int it = lane; it < HP * M; it += T) {
+          const int i = it / M, k = it % M;
+          if (!((seg >> i) & 1u)) continue;
+          const RotDF ro = s.rot[i];
+          const int2 pq = mats64[j].pq[i];
+          const float4 xp = s.A[pq.x][k], xq = s.A[pq.y][k];
+          s.A[pq.x][k] = cplx(dot3(ro.c, re_of(xp), neg(ro.sr), re_of(xq), ro.si, im_of(xq)),
+                              dot3(ro.c, im_of(xp), neg(ro.sr), im_of(xq), neg(ro.si), re_of(xq)));
+          s.A[pq.y][k] = cplx(dot3(ro.c, re_of(xq), ro.sr, re_of(xp), ro.si, im_of(xp)),
+                              dot3(ro.c, im_of(xq), ro.sr, im_of(xp), neg(ro.si), re_of(xp)));
+        }
+      }
+      g::sync();
+      // columns: A <- A J, V <- V J. new col p = c x_p - conj(sigma) x_q; new col q = sigma x_p + c x_q
+      for (int j = 0; j < G; ++j) {
+        const unsigned seg = (mask >> (j * HP)) & ((HP == 32) ? 0xffffffffu : ((1u << HP) - 1u));
+        if (!seg) continue;
+        EigSmemDF<NP> &s = df(j);
+        const int M = Ms[j];
+        for (int it = lane; it < HP * M; it += T) {
+          const int i = it / M, k = it % M;
+          if (!((seg >> i) & 1u)) continue;
+          const RotDF ro = s.rot[i];
+          const int2 pq = mats64[j].pq[i];
+          const float4 xp = s.A[k][pq.x], xq = s.A[k][pq.y];
+          s.A[k][pq.x] = cplx(dot3(ro.c, re_of(xp), neg(ro.sr), re_of(xq), neg(ro.si), im_of(xq)),
+                              dot3(ro.c, im_of(xp), neg(ro.sr), im_of(xq), ro.si, re_of(xq)));
+          s.A[k][pq.y] = cplx(dot3(ro.c, re_of(xq), ro.sr, re_of(xp), neg(ro.si), im_of(xp)),
+                              dot3(ro.c, im_of(xq), ro.sr, im_of(xp), ro.si, re_of(xp)));
+          const float4 vp = s.V[k][pq.x], vq = s.V[k][pq.y];
+          s.V[k][pq.x] = cplx(dot3(ro.c, re_of(vp), neg(ro.sr), re_of(vq), neg(ro.si), im_of(vq)),
+                              dot3(ro.c, im_of(vp), neg(ro.sr), im_of(vq), ro.si, re_of(vq)));
+          s.V[k][pq.y] = cplx(dot3(ro.c, re_of(vq), ro.sr, re_of(vp), neg(ro.si), im_of(vp)),
+                              dot3(ro.c, im_of(vq), ro.sr, im_of(vp), ro.si, re_of(vp)));
+        }
+      }
+      g::sync();
+      if (act) {   // the diagonal of a Hermitian matrix is real
+        EigSmemDF<NP> &s = df(lj);
+        const int2 pq = mats64[lj].pq[li];
+        s.A[pq.x][pq.x].z = s.A[pq.x][pq.x].w = 0.f;
+        s.A[pq.y][pq.y].z = s.A[pq.y][pq.y].w = 0.f;
+      }
+      g::sync();
+    }
+    for (int j = 0; j < G; ++j)
+      if (((live >> j) & 1u) && !((rotated >> j) & 1u)) {
+        res[j] = sweep;
+        live &= ~(1u << j);
+      }
+  }
+  for (int j = 0; j < G; ++j)
+    if ((live >> j) & 1u) res[j] = -DOA_ENOCONV;
+  // double-float -> FP64 in place (same bytes per element; every element has one owner lane)
+  for (int j = 0; j < G; ++j) {
+    const int M = Ms[j];
+    if (M <= 0) continue;
+    EigSmemDF<NP> &s = df(j);
+    for (int e = lane; e < M * M; e += T) {
+      const int i = e / M, k = e % M;
+      const float4 a = s.A[i][k], v = s.V[i][k];
+      mats64[j].A[i][k] = make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
+      mats64[j].V[i][k] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    }
+  }
+  g::sync();
+}
+
 // Stable descending order of the eigenvalues (equal values keep index order).
 template <int NP>
 __device__ void sort_desc(int M, EigSmem<NP> &s) {
@@ -232,11 +474,12 @@ __device__ void sort_desc(int M, EigSmem<NP> &s) {
   const int lane = g::id();
   for (int i = lane; i < M; i += T) s.lam[i] = s.A[i][i].x;
   g::sync();
+  // ranks form a permutation even for non-finite values (NaN ranks below every number)
   for (int i = lane; i < M; i += T) {
-    double li = s.lam[i];
+    const double li = isnan(s.lam[i]) ? -INFINITY : s.lam[i];
     int rank = 0;
     for (int j = 0; j < M; ++j) {
-      double lj = s.lam[j];
+      const double lj = isnan(s.lam[j]) ? -INFINITY : s.lam[j];
       rank += (lj > li) || (lj == li && j < i);
     }
     s.order[rank] = i;
@@ -387,7 +630,7 @@ __global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_batch_kernel(const u
     Ms[j] = prob[j] >= 0 ? probs[prob[j]].p.M : 0;
     Rs[j] = prob[j] >= 0 ? reinterpret_cast<const double2 *>(ws + probs[prob[j]].r64_off) : nullptr;
   }
-  jacobi_group<NP, G>(mats, Ms, Rs, res);
+  jacobi_group_df<NP, G>(mats, Ms, Rs, res);
   for (int j = 0; j < G; ++j) {
     if (prob[j] < 0) continue;
     const PlanProblem &pp = probs[prob[j]];
