@@ -4,10 +4,10 @@
 // P[i-1] < P[i] and P[j+1] < P[j]. The D largest peaks are selected (equal values: lower
 // index first) and written in ascending index order.
 //
-// Each thread owns a contiguous chunk of [1, L-2] and keeps its best kCache peaks in registers.
-// Selection runs D rounds of a block-wide arg-max (warp shuffles, then one warp over the warp
-// winners); the winning thread pops its head and, if its cache runs dry while it still has
-// peaks, rescans its chunk for the next ones below its last selected peak. This realises the
+// Thread t owns the interior points 1 + t, 1 + t + 256, ... (coalesced loads) and keeps its best
+// kCache peaks in registers. Selection runs D rounds of a block-wide arg-max (warp shuffles, then
+// one warp over the warp winners); the winning thread pops its head and, if its cache runs dry
+// while it still has peaks, rescans its points for the next ones below its last selected peak. This realises the
 // shared-memory max-reduction that the paper names as future work for Step-6 (Sec. 6).
 #include <climits>
 

@@ -33,13 +33,13 @@ inline __device__ bool is_peak(const float *__restrict__ P, int L, int i, float 
   return j + 1 <= L - 1 && P[j + 1] < v;
 }
 
-// Fills cache with the best peaks of [c0, c1) that are worse than thr (thr.i == INT_MAX: any).
-// Returns whether more such peaks exist beyond the cache.
-inline __device__ bool fill(const float *__restrict__ P, int L, int c0, int c1, const Cand &thr, Cand (&cache)[kCache],
-                     int &n) {
+// Fills cache with the best peaks among i = c0, c0 + stride, ... < c1 that are worse than thr
+// (thr.i == INT_MAX: any). Returns whether more such peaks exist beyond the cache.
+inline __device__ bool fill(const float *__restrict__ P, int L, int c0, int c1, int stride, const Cand &thr,
+                            Cand (&cache)[kCache], int &n) {
   n = 0;
   bool more = false;
-  for (int i = c0; i < c1; ++i) {
+  for (int i = c0; i < c1; i += stride) {
     float v = P[i];
     if (!is_peak(P, L, i, v)) continue;
     Cand c{v, i};
@@ -98,14 +98,11 @@ inline __device__ Cand block_best(Cand c, Cand *red) {
 // n returned (identical in every thread). All threads of the block must call it.
 __device__ __forceinline__ int select_top(const float *__restrict__ P, int L, int d, Cand *sel) {
   __shared__ Cand red[kPeakThreads / 32 + 1];
-  const int interior = L - 2;
-  const int chunk = (interior + kPeakThreads - 1) / kPeakThreads;
-  const int c0 = 1 + threadIdx.x * chunk;
-  const int c1 = min(L - 1, c0 + chunk);
+  const int c0 = 1 + threadIdx.x, c1 = L - 1;
   Cand cache[kCache];
   int n = 0, head = 0;
   const Cand none{0.f, INT_MAX};
-  bool more = fill(P, L, c0, c1, none, cache, n);
+  bool more = fill(P, L, c0, c1, kPeakThreads, none, cache, n);
   int nsel = 0;
   for (int r = 0; r < d; ++r) {
     Cand mine = head < n ? cache[head] : none;
@@ -116,7 +113,7 @@ __device__ __forceinline__ int select_top(const float *__restrict__ P, int L, in
     if (mine.i == w.i) {
       ++head;
       if (head == n && more) {
-        more = fill(P, L, c0, c1, w, cache, n);
+        more = fill(P, L, c0, c1, kPeakThreads, w, cache, n);
         head = 0;
       }
     }

@@ -72,10 +72,13 @@ __global__ void __launch_bounds__(kScanThreads) scan_single_kernel(const double2
   drain_refinements(j, sh);
 }
 
-// Persistent batched scan over the tiles of the problems of one M bucket. Every CTA takes a
-// contiguous range of tiles (equal counts), so it changes problem only at the few problem
-// boundaries inside its range; the first problem comes from a binary search on the problems'
-// first tiles, the following ones by stepping through the bucket's list.
+// Persistent batched scan over the tiles of the problems of one M bucket. The tiles are dealt
+// to the CTAs in runs of kRun consecutive tiles, run r to CTA r mod gridDim: consecutive tiles
+// mostly share a problem (its factor stays in shared memory), while the runs of problems of
+// different cost (columns, M) spread evenly over the CTAs. The problem of a run's first tile
+// comes from a binary search on the problems' first tiles, the following ones by stepping.
+constexpr int kRun = 16;
+
 template <int MP, int PT>
 __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t *plan, uint8_t *ws, int bucket) {
   __shared__ __align__(16) float2 Bs[(MP + 1) * MP];
@@ -87,47 +90,48 @@ __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t 
   const PlanProblem *probs = reinterpret_cast<const PlanProblem *>(plan + h->off_prob);
   const PlanGrid *grids = reinterpret_cast<const PlanGrid *>(plan + h->off_grid);
   constexpr int TP = kScanThreads * PT;
-  const int64_t t_begin = ntiles * blockIdx.x / gridDim.x, t_end = ntiles * (blockIdx.x + 1) / gridDim.x;
-  if (t_begin >= t_end) return;
-  int u = 0, hi = nunits - 1;
-  while (u < hi) {  // last problem with tile_start <= t_begin
-    int mid = (u + hi + 1) >> 1;
-    if (probs[list[mid]].tile_start <= t_begin) u = mid; else hi = mid - 1;
-  }
   int cur = -1;
   ScanJob j{};
   const PlanProblem *pp = nullptr;
   const PlanGrid *g = nullptr;
-  for (int64_t t = t_begin; t < t_end; ++t) {
-    while (u + 1 < nunits && probs[list[u + 1]].tile_start <= t) ++u;
-    if (u != cur) {
-      pp = &probs[list[u]];
-      g = &grids[pp->grid_id];
-      j.F = reinterpret_cast<const double2 *>(ws + pp->fac_off);
-      j.w = pp->Kn > 0 && pp->slot[DOA_EV] >= 0
-                ? reinterpret_cast<const double *>(ws + pp->fac_off) + 2 * pp->p.M * (pp->p.M + 1)
-                : nullptr;
-      j.S64 = reinterpret_cast<const uint64_t *>(ws + g->S64_off);
-      for (int r = 0; r < 4; ++r) j.P[r] = pp->slot[r] >= 0 ? pp->p.P + (size_t)pp->slot[r] * g->L : nullptr;
-      j.lo = g->lo;
-      j.step = g->step;
-      j.M = pp->p.M;
-      j.Kf = pp->Kf;
-      j.Kn = pp->Kn;
-      j.kphd = pp->kphd;
-      j.kmn = pp->kmn;
-      j.kofs = 0;
-      __syncthreads();
-      load_job<MP>(j, Bs, sh);
-      __syncthreads();
-      set_threshold<MP>(Bs, j, sh);
-      __syncthreads();
-      cur = u;
+  for (int64_t run = blockIdx.x; run * kRun < ntiles; run += gridDim.x) {
+    const int64_t t_begin = run * kRun, t_end = min(ntiles, t_begin + kRun);
+    int u = 0, hi = nunits - 1;
+    while (u < hi) {  // last problem with tile_start <= t_begin
+      int mid = (u + hi + 1) >> 1;
+      if (probs[list[mid]].tile_start <= t_begin) u = mid; else hi = mid - 1;
     }
-    const uint32_t *S = reinterpret_cast<const uint32_t *>(ws + g->S_off);
-    const int k0 = (int)(t - pp->tile_start) * TP + threadIdx.x * PT;
-    scan_points<MP, PT>(Bs, j, S, g->L, k0, sh);
-    drain_refinements(j, sh);
+    for (int64_t t = t_begin; t < t_end; ++t) {
+      while (u + 1 < nunits && probs[list[u + 1]].tile_start <= t) ++u;
+      if (u != cur) {
+        pp = &probs[list[u]];
+        g = &grids[pp->grid_id];
+        j.F = reinterpret_cast<const double2 *>(ws + pp->fac_off);
+        j.w = pp->Kn > 0 && pp->slot[DOA_EV] >= 0
+                  ? reinterpret_cast<const double *>(ws + pp->fac_off) + 2 * pp->p.M * (pp->p.M + 1)
+                  : nullptr;
+        j.S64 = reinterpret_cast<const uint64_t *>(ws + g->S64_off);
+        for (int r = 0; r < 4; ++r) j.P[r] = pp->slot[r] >= 0 ? pp->p.P + (size_t)pp->slot[r] * g->L : nullptr;
+        j.lo = g->lo;
+        j.step = g->step;
+        j.M = pp->p.M;
+        j.Kf = pp->Kf;
+        j.Kn = pp->Kn;
+        j.kphd = pp->kphd;
+        j.kmn = pp->kmn;
+        j.kofs = 0;
+        __syncthreads();
+        load_job<MP>(j, Bs, sh);
+        __syncthreads();
+        set_threshold<MP>(Bs, j, sh);
+        __syncthreads();
+        cur = u;
+      }
+      const uint32_t *S = reinterpret_cast<const uint32_t *>(ws + g->S_off);
+      const int k0 = (int)(t - pp->tile_start) * TP + threadIdx.x * PT;
+      scan_points<MP, PT>(Bs, j, S, g->L, k0, sh);
+      drain_refinements(j, sh);
+    }
   }
 }
 
