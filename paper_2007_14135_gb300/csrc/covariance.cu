@@ -338,8 +338,18 @@ __device__ void cov_tasks(const float2 *__restrict__ X, int M, int ldx, int t0, 
   float2 *tile = reinterpret_cast<float2 *>(smem);
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int task = warp / T::kWpt;
-  const int g = (warp % T::kWpt) * 32 + lane;
+  // Warps of one task type share a scheduler: warp w runs on sub-partition w mod 4, so the
+  // diagonal-pair tasks go to warps 0 and 4 (MB = 2: the two task types alternate), keeping each
+  // sub-partition on one instruction stream.
+  int task, wit;
+  if (MB == 2) {
+    task = warp & 1;
+    wit = warp >> 1;
+  } else {
+    task = (warp & 3) == 0 ? T::kOff + (warp >> 2) : warp - 1 - (warp >> 2);
+    wit = 0;
+  }
+  const int g = wit * 32 + lane;
   float hi[32], lo[32];
 #pragma unroll
   for (int a = 0; a < 32; ++a) hi[a] = lo[a] = 0.f;

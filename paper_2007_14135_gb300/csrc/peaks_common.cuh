@@ -34,16 +34,16 @@ inline __device__ bool is_peak(const float *__restrict__ P, int L, int i, float 
 }
 
 // Fills cache with the best peaks among i = c0, c0 + stride, ... < c1 that are worse than thr
-// (thr.i == INT_MAX: any). Returns whether more such peaks exist beyond the cache.
+// (thr.i == INT_MAX: any). Returns whether more such peaks exist beyond the cache. Four points
+// are examined per step with all their loads (value and both neighbours) issued first; a point
+// whose right neighbour is equal goes through the full plateau walk of is_peak.
 inline __device__ bool fill(const float *__restrict__ P, int L, int c0, int c1, int stride, const Cand &thr,
                             Cand (&cache)[kCache], int &n) {
   n = 0;
   bool more = false;
-  for (int i = c0; i < c1; i += stride) {
-    float v = P[i];
-    if (!is_peak(P, L, i, v)) continue;
+  auto consider = [&](int i, float v) {
     Cand c{v, i};
-    if (thr.i != INT_MAX && !better(thr, c)) continue;
+    if (thr.i != INT_MAX && !better(thr, c)) return;
     if (n < kCache) {
       int k = n++;
       while (k > 0 && better(c, cache[k - 1])) {
@@ -62,6 +62,28 @@ inline __device__ bool fill(const float *__restrict__ P, int L, int c0, int c1, 
     } else {
       more = true;
     }
+  };
+  int i = c0;
+  for (; i + 3 * stride < c1; i += 4 * stride) {
+    float v[4], pv[4], nv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      v[u] = P[i + u * stride];
+      pv[u] = P[i + u * stride - 1];
+      nv[u] = P[i + u * stride + 1];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!(pv[u] < v[u])) continue;
+      const int k = i + u * stride;
+      bool pk = nv[u] < v[u];
+      if (!pk && nv[u] == v[u]) pk = is_peak(P, L, k, v[u]);
+      if (pk) consider(k, v[u]);
+    }
+  }
+  for (; i < c1; i += stride) {
+    const float v = P[i];
+    if (is_peak(P, L, i, v)) consider(i, v);
   }
   return more;
 }

@@ -244,35 +244,51 @@ __device__ __forceinline__ void scan_points(const float2 *Bs, const ScanJob &j, 
       }
     }
   }
-  float dm[PT], de[PT], dp[PT], dn[PT];
+  float dm[PT], de[PT], dp[PT], dn[PT], n[PT];
 #pragma unroll
-  for (int q = 0; q < PT; ++q) dm[q] = de[q] = dp[q] = dn[q] = 0.f;
-  const int Kf = j.Kf, Kn = j.Kn, kphd = j.kphd, kmn = j.kmn;
-  for (int k = 0; k < Kf; ++k) {
+  for (int q = 0; q < PT; ++q) dm[q] = de[q] = dp[q] = dn[q] = n[q] = 0.f;
+  // n = |f_k^H a|^2 for the PT points; factor rows read two elements (16 bytes) at a time
+  auto column = [&](int k) {
     float yr[PT], yi[PT];
 #pragma unroll
     for (int q = 0; q < PT; ++q) yr[q] = yi[q] = 0.f;
+    const float4 *b2 = reinterpret_cast<const float4 *>(Bs + k * MP);
 #pragma unroll
-    for (int m = 0; m < MP; ++m) {
-      const float2 b = Bs[k * MP + m];
+    for (int m2 = 0; m2 < MP / 2; ++m2) {
+      const float4 bb = b2[m2];
 #pragma unroll
-      for (int q = 0; q < PT; ++q) {
-        // conj(b) * a = (br ar + bi ai) + j (br ai - bi ar)
-        yr[q] = fmaf(b.x, a[q][m].x, fmaf(b.y, a[q][m].y, yr[q]));
-        yi[q] = fmaf(b.x, a[q][m].y, fmaf(-b.y, a[q][m].x, yi[q]));
+      for (int h = 0; h < 2; ++h) {
+        const float bx = h ? bb.z : bb.x, by = h ? bb.w : bb.y;
+        const int m = 2 * m2 + h;
+#pragma unroll
+        for (int q = 0; q < PT; ++q) {
+          // conj(b) * a = (br ar + bi ai) + j (br ai - bi ar)
+          yr[q] = fmaf(bx, a[q][m].x, fmaf(by, a[q][m].y, yr[q]));
+          yi[q] = fmaf(bx, a[q][m].y, fmaf(-by, a[q][m].x, yi[q]));
+        }
       }
     }
-    float n[PT];
 #pragma unroll
     for (int q = 0; q < PT; ++q) n[q] = fmaf(yr[q], yr[q], yi[q] * yi[q]);
-    if (k < Kn) {
-      const float w = sh.w32[k];
+  };
+  const int Kf = j.Kf, Kn = j.Kn, kphd = j.kphd, kmn = j.kmn;
+  // E_n columns: MUSIC and EV sums (PHD, when present, reads the last of them)
+  for (int k = 0; k < Kn; ++k) {
+    column(k);
+    const float w = sh.w32[k];
 #pragma unroll
-      for (int q = 0; q < PT; ++q) {
-        dm[q] += n[q];
-        de[q] = fmaf(w, n[q], de[q]);
-      }
+    for (int q = 0; q < PT; ++q) {
+      dm[q] += n[q];
+      de[q] = fmaf(w, n[q], de[q]);
     }
+  }
+  if (Kn > 0 && kphd == Kn - 1) {
+#pragma unroll
+    for (int q = 0; q < PT; ++q) dp[q] = n[q];
+  }
+  // remaining single columns: v_min without E_n, valph
+  for (int k = Kn; k < Kf; ++k) {
+    column(k);
     if (k == kphd) {
 #pragma unroll
       for (int q = 0; q < PT; ++q) dp[q] = n[q];
