@@ -224,27 +224,43 @@ __global__ void __launch_bounds__(kCovThreads) covariance_cluster_kernel(const f
 // tasks of equal work: every off-diagonal 4x4 block (16 complex entries, 64 real MACs per
 // snapshot) and every pair of diagonal blocks (4 real diagonal entries + 6 complex entries each,
 // 2 x 32 MACs), so no lane computes a lower-triangle entry or the zero imaginary part of the
-// diagonal. A warp owns one task (warp-uniform code path) and its lanes take snapshots
-// t = g, g + G, ... of each tile, G = the task's lanes; tiles of kTS = max(64, G) snapshots are
-// prefetched into registers while the previous tile is being consumed. Every task has 32 real
-// accumulators per lane; at the end the G lane partials of each accumulator are added in lane
-// order in double-float arithmetic (deterministic).
+// diagonal. A warp owns one task and its lanes take snapshots t = lane, lane + 32, ... of each
+// 64-snapshot tile; the next tile streams into a second shared-memory buffer (cp.async) while the
+// current one is consumed.
+// Every task has 32 real accumulators per lane; at the end the 32 lane partials of each
+// accumulator are added in lane order in double-float arithmetic (deterministic).
 // ------------------------------------------------------------------------------------------
 template <int MB>
 struct CovTasks {
   static constexpr int kOff = MB * (MB - 1) / 2;
   static constexpr int kDiag = (MB + 1) / 2;
-  static constexpr int kTasks = kOff + kDiag;
-  static constexpr int kWpt = kTasks >= 8 ? 1 : 8 / kTasks;        // warps per task
-  static constexpr int kThreads = 32 * kWpt * kTasks;
-  static constexpr int kG = 32 * kWpt;                              // snapshot lanes per task
-  static constexpr int kTS = kG >= 64 ? kG : 64;
+  static constexpr int kTS = 64;
   static constexpr int kMP = 4 * MB;
-  static constexpr int kLoads = (kMP * kTS + kThreads - 1) / kThreads;
-  static constexpr int kStageBytes = kTasks * 32 * kG * 8;          // (hi, lo) per lane per accumulator
-  static constexpr int kTileBytes = kMP * kTS * 8;
+};
+
+// One launch per task kind (0: off-diagonal blocks, 1: diagonal-block pairs), so that every SM
+// runs a single unrolled instruction stream: the two kinds' bodies together overflow the
+// instruction cache when their warps share an SM.
+template <int MB, int kKind>
+struct CovKind {
+  using T = CovTasks<MB>;
+  static constexpr int kTasks = kKind == 0 ? T::kOff : T::kDiag;
+  static constexpr int kFirst = kKind == 0 ? 0 : T::kOff;       // global index of the kind's first task
+  static constexpr int kThreads = 32 * kTasks;
+  static constexpr int kMinBlocks = (65536 / 112) / kThreads > 0 ? (65536 / 112) / kThreads : 1;  // <= 112 regs
+  static constexpr int kStageBytes = kTasks * 32 * 32 * 8;       // (hi, lo) per lane per accumulator
+  static constexpr int kTileBytes = 2 * T::kMP * T::kTS * 8;      // double-buffered tile
   static constexpr int kSmem = kStageBytes > kTileBytes ? kStageBytes : kTileBytes;
 };
+
+// Asynchronous 8-byte global -> shared copy; src_bytes = 0 writes zeros (rows >= M, ragged tail).
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // Accumulator a (0..31) of task `task` -> (row, col, imaginary?) ; false if outside M.
 template <int MB>
@@ -331,65 +347,57 @@ __device__ __forceinline__ void task_macs(int task, const float2 *tile, int t, f
   }
 }
 
-template <int MB, bool kComp>
+template <int MB, int kKind, bool kComp>
 __device__ void cov_tasks(const float2 *__restrict__ X, int M, int ldx, int t0, int t1, uint8_t *smem,
                           int nchunks, double inv_n, double2 *R64, double2 *partial) {
   using T = CovTasks<MB>;
-  float2 *tile = reinterpret_cast<float2 *>(smem);
+  using K = CovKind<MB, kKind>;
+  float2 *tiles = reinterpret_cast<float2 *>(smem);   // two tiles of kMP x kTS
   const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  // Warps of one task type share a scheduler: warp w runs on sub-partition w mod 4, so the
-  // diagonal-pair tasks go to warps 0 and 4 (MB = 2: the two task types alternate), keeping each
-  // sub-partition on one instruction stream.
-  int task, wit;
-  if (MB == 2) {
-    task = warp & 1;
-    wit = warp >> 1;
-  } else {
-    task = (warp & 3) == 0 ? T::kOff + (warp >> 2) : warp - 1 - (warp >> 2);
-    wit = 0;
-  }
-  const int g = wit * 32 + lane;
+  const int warp = tid >> 5, g = tid & 31;
+  const int task = K::kFirst + warp;
   float hi[32], lo[32];
 #pragma unroll
   for (int a = 0; a < 32; ++a) hi[a] = lo[a] = 0.f;
-  float2 pre[T::kLoads];
-  auto fetch = [&](int ts) {
+  auto issue = [&](int buf, int ts) {
     const int cnt = min(T::kTS, t1 - ts);
-#pragma unroll
-    for (int q = 0; q < T::kLoads; ++q) {
-      const int e = tid + q * T::kThreads;
+    float2 *dst = tiles + buf * (T::kMP * T::kTS);
+    for (int e = tid; e < T::kMP * T::kTS; e += K::kThreads) {
       const int r = e / T::kTS, t = e % T::kTS;
-      pre[q] = (e < T::kMP * T::kTS && r < M && t < cnt) ? X[(size_t)r * ldx + ts + t] : make_float2(0.f, 0.f);
+      const bool ok = r < M && t < cnt;
+      cp_async8(dst + e, ok ? X + (size_t)r * ldx + ts + t : X, ok ? 8 : 0);
     }
+    cp_async_commit();
   };
-  if (t0 < t1) fetch(t0);
-  for (int ts = t0; ts < t1; ts += T::kTS) {
+  if (t0 < t1) issue(0, t0);
+  int buf = 0;
+  for (int ts = t0; ts < t1; ts += T::kTS, buf ^= 1) {
     const int cnt = min(T::kTS, t1 - ts);
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < T::kLoads; ++q) {
-      const int e = tid + q * T::kThreads;
-      if (e < T::kMP * T::kTS) tile[e] = pre[q];
+    if (ts + T::kTS < t1) {
+      issue(buf ^ 1, ts + T::kTS);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
-    if (ts + T::kTS < t1) fetch(ts + T::kTS);
-    for (int t = g; t < cnt; t += T::kG) task_macs<MB, kComp>(task, tile, t, hi, lo);
+    const float2 *tile = tiles + buf * (T::kMP * T::kTS);
+    for (int t = g; t < cnt; t += 32) task_macs<MB, kComp>(task, tile, t, hi, lo);
+    __syncthreads();
   }
   // lane partials -> shared memory, then one thread per (task, accumulator) adds them in order
   __syncthreads();
-  float2 *stage = reinterpret_cast<float2 *>(smem);   // [task][a][g]
+  float2 *stage = reinterpret_cast<float2 *>(smem);   // [local task][a][lane]
 #pragma unroll
-  for (int a = 0; a < 32; ++a) stage[((size_t)task * 32 + a) * T::kG + g] = make_float2(hi[a], lo[a]);
+  for (int a = 0; a < 32; ++a) stage[((size_t)warp * 32 + a) * 32 + g] = make_float2(hi[a], lo[a]);
   __syncthreads();
-  for (int item = tid; item < T::kTasks * 32; item += T::kThreads) {
-    const int tk = item / 32, a = item % 32;
+  for (int item = tid; item < K::kTasks * 32; item += K::kThreads) {
+    const int tk = K::kFirst + item / 32, a = item % 32;
     int row, col;
     bool imag, diag;
     if (!task_slot<MB>(tk, a, M, row, col, imag, diag)) continue;
-    const float2 *v = stage + (size_t)item * T::kG;
+    const float2 *v = stage + (size_t)item * 32;
     float sh = v[0].x, sl = v[0].y;
-    for (int q = 1; q < T::kG; ++q) df_add(sh, sl, v[q].x, v[q].y);
+    for (int q = 1; q < 32; ++q) df_add(sh, sl, v[q].x, v[q].y);
     const double val = (double)sh + (double)sl;
     if (nchunks == 1) {
       const double x = val * inv_n;
@@ -416,9 +424,9 @@ __device__ void cov_tasks(const float2 *__restrict__ X, int M, int ldx, int t0, 
   }
 }
 
-template <int MB>
-__global__ void __launch_bounds__(CovTasks<MB>::kThreads) covariance_tasks_kernel(const uint8_t *plan, uint8_t *ws,
-                                                                                  int first) {
+template <int MB, int kKind>
+__global__ void __launch_bounds__(CovKind<MB, kKind>::kThreads, CovKind<MB, kKind>::kMinBlocks) covariance_tasks_kernel(const uint8_t *plan,
+                                                                                        uint8_t *ws, int first) {
   extern __shared__ __align__(16) uint8_t smem[];
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
   const PlanCovItem it = reinterpret_cast<const PlanCovItem *>(plan + h->off_cov)[first + blockIdx.x];
@@ -430,9 +438,9 @@ __global__ void __launch_bounds__(CovTasks<MB>::kThreads) covariance_tasks_kerne
   double2 *partial = reinterpret_cast<double2 *>(ws + pp.part_off) + (size_t)it.chunk * M * M;
   const double inv_n = 1.0 / (double)N;
   if (pp.p.alg_mask & (1u << DOA_PHD))
-    cov_tasks<MB, true>(X, M, pp.p.ldx, t0, t1, smem, pp.nchunks, inv_n, R64, partial);
+    cov_tasks<MB, kKind, true>(X, M, pp.p.ldx, t0, t1, smem, pp.nchunks, inv_n, R64, partial);
   else
-    cov_tasks<MB, false>(X, M, pp.p.ldx, t0, t1, smem, pp.nchunks, inv_n, R64, partial);
+    cov_tasks<MB, kKind, false>(X, M, pp.p.ldx, t0, t1, smem, pp.nchunks, inv_n, R64, partial);
 }
 
 // Batch: one CTA per work item (problem, chunk) of the generic class.
@@ -513,20 +521,27 @@ cudaError_t launch_covariance_single(const float2 *X, int M, int N, int ldx, flo
   return cudaLaunchKernelEx(&cfg, covariance_cluster_kernel, X, M, N, ldx, per, R, R64);
 }
 
-template <int MB>
-cudaError_t launch_tasks(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s) {
-  using T = CovTasks<MB>;
-  const int c = MB - 2, n = h.cov_first[c + 1] - h.cov_first[c];
-  if (n == 0) return cudaSuccess;
+template <int MB, int kKind>
+cudaError_t launch_tasks_kind(const uint8_t *plan_dev, int first, int n, uint8_t *ws, cudaStream_t s) {
+  using K = CovKind<MB, kKind>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(covariance_tasks_kernel<MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         T::kSmem);
+    cudaError_t e = cudaFuncSetAttribute(covariance_tasks_kernel<MB, kKind>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, K::kSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  covariance_tasks_kernel<MB><<<n, T::kThreads, T::kSmem, s>>>(plan_dev, ws, h.cov_first[c]);
+  covariance_tasks_kernel<MB, kKind><<<n, K::kThreads, K::kSmem, s>>>(plan_dev, ws, first);
   return cudaGetLastError();
+}
+
+template <int MB>
+cudaError_t launch_tasks(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s) {
+  const int c = MB - 2, n = h.cov_first[c + 1] - h.cov_first[c];
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = launch_tasks_kind<MB, 0>(plan_dev, h.cov_first[c], n, ws, s);
+  if (e != cudaSuccess) return e;
+  return launch_tasks_kind<MB, 1>(plan_dev, h.cov_first[c], n, ws, s);
 }
 
 cudaError_t launch_covariance_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws,
