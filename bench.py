@@ -44,6 +44,14 @@ def workload_name(batch):
             f"grid -90:{STEP}:90 deg (L={grid_L()}), PHD+MUSIC+EV+MN on each")
 
 
+# DRAM bytes (read + write) per launch of the dominant kernels on the 4096-problem paper-density
+# step: ncu captures of the 1024-problem case (profiles/paper_density_batch_kernels_ncu.md) scaled
+# by 4 (every problem is an independent, equal unit). Reset an entry to None when its kernel changes.
+TRAFFIC_BYTES = {
+    "scan_batch_kernel<16,2>": 4 * (4.137728e6 + 235.058176e6),
+}
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -102,27 +110,50 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------------- oracle leg
+_SHM = {}
+
+
 def _oracle_task(args):
-    X, alg = args
+    """One (problem, algorithm) oracle solve; the snapshots come from a shared-memory block."""
+    from multiprocessing import shared_memory
+    name, shape, i, alg, want_P = args
+    if name not in _SHM:
+        _SHM.clear()
+        shm = shared_memory.SharedMemory(name=name)
+        _SHM[name] = (shm, np.ndarray(shape, dtype=np.complex64, buffer=shm.buf))
+    X = _SHM[name][1][i]
     import oracle
     r = oracle.solve(X, D, alg, LO, STEP, grid_L())
-    return alg, r["idx"], r["P"].astype(np.float32), r["status"]
+    return i, alg, r["idx"], (r["P"].astype(np.float32) if want_P else None), r["status"]
 
 
-def oracle_sample(Xs, workers):
-    """Times the FP64 oracle on the given instances x all four algorithms (spawned workers)."""
+def oracle_sample(Xh, S, workers, full=0):
+    """Times the FP64 oracle on problems 0..S-1 of Xh x all four algorithms in spawned workers
+    (snapshots shared, not copied per task). The first `full` problems also return spectra."""
     import multiprocessing as mp
+    from multiprocessing import shared_memory
     import oracle
     oracle.build()
-    tasks = [(X, a) for X in Xs for a in ALGS]
-    t0 = time.perf_counter()
-    with mp.get_context("spawn").Pool(workers) as pool:
-        warm = pool.map(_oracle_task, tasks[:workers])      # imports + library load, untimed
-        t0 = time.perf_counter()
-        res = pool.map(_oracle_task, tasks)
-    dt = time.perf_counter() - t0
-    del warm
+    X = np.ascontiguousarray(Xh[:S])
+    shm = shared_memory.SharedMemory(create=True, size=X.nbytes)
+    try:
+        np.ndarray(X.shape, dtype=np.complex64, buffer=shm.buf)[:] = X
+        tasks = [(shm.name, X.shape, i, a, i < full) for i in range(S) for a in ALGS]
+        with mp.get_context("spawn").Pool(workers) as pool:
+            pool.map(_oracle_task, tasks[:workers], chunksize=1)     # imports + attach, untimed
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_task, tasks, chunksize=4)
+            dt = time.perf_counter() - t0
+    finally:
+        shm.close()
+        shm.unlink()
     return res, dt
+
+
+def eq4_percent(P_meas, P_truth):
+    """Eq. 4: 100/N sum |y_meas - y_truth| / |y_truth| over the N spectrum points."""
+    P_meas, P_truth = np.asarray(P_meas, np.float64), np.asarray(P_truth, np.float64)
+    return float(100.0 * np.mean(np.abs(P_meas - P_truth) / np.abs(P_truth)))
 
 
 # --------------------------------------------------------------------------------- GPU leg
@@ -260,7 +291,7 @@ def run_gpu(args):
     if dname == "scan":
         roof = {"bound": "alu", "achieved": round(stage_info["scan"]["achieved"], 3), "peak": round(FP32_PEAK_TFLOPS, 2),
                 "unit": "TFLOP/s", "frac": round(stage_info["scan"]["achieved"] / FP32_PEAK_TFLOPS, 4),
-                "traffic": None, "kernel": "scan_batch_kernel<16,2>",
+                "traffic": TRAFFIC_BYTES.get("scan_batch_kernel<16,2>"), "kernel": "scan_batch_kernel<16,2>",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
     elif dname == "covariance":
         a = stage_info["covariance"]["achieved"]
@@ -294,23 +325,30 @@ def run_gpu(args):
 
     # ---- CPU baseline (oracle) on a bounded sample, rank 0, N = 1; also a parity spot check
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        S = args.cpu_sample
+        S = min(args.cpu_sample, B)
+        full = min(args.parity_full, S)
         workers = min(os.cpu_count() or 1, 16)
-        res, dt = oracle_sample([Xh[i] for i in range(S)], workers)
+        res, dt = oracle_sample(Xh, S, workers, full=full)
         pts = S * nalg * L
         result["cpu_baseline"] = {"value": pts / dt, "unit": "points/s", "cores": workers, "kind": "oracle",
                                   "sample": f"first {S} problems of the batch x 4 algorithms ({pts} points)",
                                   "seconds": round(dt, 3)}
-        Pg = P[:S].cpu().numpy()
+        Pg = P[:full].cpu().numpy()
         ig = idx[:S].cpu().numpy()
         cg = cnt[:S].cpu().numpy()
         worst_db, agree = 0.0, 0
-        for t, (alg, io, Po, sto) in enumerate(res):
-            i, a = divmod(t, nalg)
-            worst_db = max(worst_db, float(np.max(np.abs(10 * np.log10(Pg[i, a].astype(np.float64) /
-                                                                       Po.astype(np.float64))))))
+        eq4 = {a: [] for a in ALGS}
+        for i, a, io, Po, sto in res:
             agree += list(ig[i, a, :cg[i, a]]) == list(io)
-        result["parity"] = {"sampled_solves": len(res), "peak_index_agreement": agree, "max_db_err": worst_db}
+            if Po is not None:
+                Pi = Pg[i, a].astype(np.float64)
+                worst_db = max(worst_db, float(np.max(np.abs(10 * np.log10(Pi / Po.astype(np.float64))))))
+                eq4[a].append(eq4_percent(Pi, Po))
+        names = {0: "PHD", 1: "MUSIC", 2: "EV", 3: "MN"}
+        result["parity"] = {"sampled_solves": len(res), "peak_index_agreement": agree,
+                            "spectra_compared": full * nalg, "max_db_err": worst_db,
+                            "eq4_percent_max": {names[a]: max(v) for a, v in eq4.items() if v},
+                            "eq4_percent_mean": {names[a]: statistics.fmean(v) for a, v in eq4.items() if v}}
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -663,13 +701,13 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2007_14135_gb300 import synth
-    S = args.cpu_sample
+    S = args.reference_sample
     Xh, _ = synth.paper_density_batch(S)
     workers = min(os.cpu_count() or 1, 16)
     L = grid_L()
     times = []
     for k in range(args.warmup + args.steps):
-        _, dt = oracle_sample([Xh[i] for i in range(S)], workers)
+        _, dt = oracle_sample(Xh, S, workers)
         if k >= args.warmup:
             times.append(dt)
     ms = 1e3 * statistics.fmean(times)
@@ -694,7 +732,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--batch", type=int, default=4096, help="problems per GPU per step")
-    ap.add_argument("--cpu-sample", type=int, default=48, help="problems timed on the oracle")
+    ap.add_argument("--cpu-sample", type=int, default=3072,
+                    help="problems timed on the oracle for cpu_baseline (peak indices compared on all)")
+    ap.add_argument("--parity-full", type=int, default=48,
+                    help="problems whose whole spectra are compared with the oracle (dB, Eq. 4)")
+    ap.add_argument("--reference-sample", type=int, default=256, help="--impl reference: problems per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["paper-density", "uneven", "large-array", "learned"],
                     default="paper-density")
