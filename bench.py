@@ -336,16 +336,30 @@ def run_gpu(args):
         Pg = P[:full].cpu().numpy()
         ig = idx[:S].cpu().numpy()
         cg = cnt[:S].cpu().numpy()
-        worst_db, agree = 0.0, 0
+        worst_db, agree, differ = 0.0, 0, []
         eq4 = {a: [] for a in ALGS}
         for i, a, io, Po, sto in res:
-            agree += list(ig[i, a, :cg[i, a]]) == list(io)
+            same = list(ig[i, a, :cg[i, a]]) == list(io)
+            agree += same
+            if not same:
+                differ.append((i, a, list(io)))
             if Po is not None:
                 Pi = Pg[i, a].astype(np.float64)
                 worst_db = max(worst_db, float(np.max(np.abs(10 * np.log10(Pi / Po.astype(np.float64))))))
                 eq4[a].append(eq4_percent(Pi, Po))
+        # a disagreement is a tie within tolerance when the oracle's own margin between the two
+        # candidate points is below 1e-4 relative (the FP32 path's error bound near a peak)
+        ties = 0
+        for i, a, io in differ[:64]:
+            import oracle
+            Po = oracle.solve(Xh[i], D, a, LO, STEP, L)["P"]
+            gi = [int(k) for k in ig[i, a, :cg[i, a]]]
+            ks = sorted(set(gi) ^ set(io))
+            ties += all(abs(Po[k] - max(Po[k - 1], Po[k + 1])) / Po[k] < 1e-4 or
+                        any(abs(Po[k] - Po[j]) / Po[k] < 1e-4 for j in ks if j != k) for k in ks)
         names = {0: "PHD", 1: "MUSIC", 2: "EV", 3: "MN"}
         result["parity"] = {"sampled_solves": len(res), "peak_index_agreement": agree,
+                            "disagreements_tie_within_1e-4": f"{ties}/{len(differ)}",
                             "spectra_compared": full * nalg, "max_db_err": worst_db,
                             "eq4_percent_max": {names[a]: max(v) for a, v in eq4.items() if v},
                             "eq4_percent_mean": {names[a]: statistics.fmean(v) for a, v in eq4.items() if v}}
