@@ -150,6 +150,60 @@ doa_status doa_scan(const double *B, int M, int K, doa_grid grid, int prec, floa
 doa_status doa_peaks(const float *P, int L, int d, int *idx, float *val, int *count, void *stream);
 
 /* ----------------------------------------------------------------------------------------- */
+/* Grid slices (not in the paper): one spectrum split into contiguous slices of the angle grid, */
+/* e.g. one slice per GPU, with B replicated. The slice scan computes exactly the points the    */
+/* full scan computes; the slice peak summary plus a host merge of the summaries of all slices  */
+/* reproduces doa_peaks on the whole spectrum bit for bit.                                     */
+/* ----------------------------------------------------------------------------------------- */
+
+/*
+ * Step-5 on the global grid points k0 .. k0+n-1 of `grid` (0 <= k0, n >= 1, k0 + n <= L): P[i]
+ * receives the value doa_scan would write at k0 + i (same phases, same FP64 re-evaluation).
+ * DOA_FP32 only. P: n floats; as with doa_scan the phase table is staged in P first.
+ */
+doa_status doa_scan_slice(const double *B, int M, int K, doa_grid grid, int k0, int n, float *P, void *stream);
+
+/* Peak summary of one slice of a spectrum (written by doa_slice_peaks, read by the host merge). */
+#define DOA_SLICE_MAXD 64
+typedef struct {
+  int32_t count;                  /* decided peaks of the slice in idx/val (<= d)                 */
+  int32_t open_idx;               /* left end of a run that reaches the end of the slice's data   */
+                                  /* with equal values (undecided), or -1                         */
+  float open_val;
+  float first_val;                /* P[k0]                                                          */
+  int32_t first_run_to_end;       /* 1 if P[k0] .. P[last readable] are all equal                  */
+  float first_next_val;           /* otherwise the first value after that run                      */
+  int32_t idx[DOA_SLICE_MAXD];    /* global indices, best first (value descending, index ascending) */
+  float val[DOA_SLICE_MAXD];
+} doa_slice_summary;
+
+/*
+ * Step-6 on one slice. The slice owns global points [k0, k1) of a spectrum of L points; Pbuf holds
+ * the points [b0, b1) with b0 = max(k0 - 1, 0) and b1 = min(k1 + 1, L) (one halo point on each
+ * side that exists), Pbuf[0] being global index b0. A peak is decided with the rule of doa_peaks
+ * (left end i of a maximal run of equal values, strictly lower on both sides, 1 <= i and run
+ * end <= L-2) using only those points; a run that starts at an owned point and is still equal at
+ * b1 - 1 < L - 1 is reported as the open candidate, to be decided by the merge from the next
+ * slices' first_* fields. The d best decided peaks are kept (0 <= d <= DOA_SLICE_MAXD).
+ *   out: one doa_slice_summary in device memory.
+ */
+doa_status doa_slice_peaks(const float *Pbuf, int b0, int k0, int k1, int L, int d, doa_slice_summary *out,
+                           void *stream);
+
+/*
+ * Host-only merge of the summaries of all slices of one spectrum, given in slice order (for
+ * slices split across GPUs: after an all-gather of the summaries). Decides every open candidate
+ * from the first_* fields of the following slices (the run ends with a strict descent: peak; it
+ * rises or reaches the last point: no peak), then keeps the d best peaks (value descending,
+ * index ascending) and writes them in ascending index order, exactly as doa_peaks would.
+ *   sums: nslices host summaries; idx, val: d host entries each; count: one host int32.
+ * Errors: DOA_EINVAL for bad arguments or summaries that do not chain (an open run whose value
+ * differs from the next slice's first value).
+ */
+doa_status doa_merge_slices(const doa_slice_summary *sums, int nslices, int d, int32_t *idx, float *val,
+                            int32_t *count);
+
+/* ----------------------------------------------------------------------------------------- */
 /* Batched solve (not in the paper): many independent problems with uneven M, d, N, L and    */
 /* algorithms in one plan, executed as a fixed sequence of kernels on one stream that a       */
 /* caller may capture into a CUDA graph.                                                      */

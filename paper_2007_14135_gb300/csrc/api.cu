@@ -1,6 +1,7 @@
 // C ABI of libdoa.so (declarations and contracts in include/doa.h): argument checks, batch
 // planning on the host, and the launch sequences. No entry point allocates memory or
 // synchronises; every launch goes to the caller's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -172,12 +173,68 @@ doa_status doa_scan(const double *B, int M, int K, doa_grid grid, int prec, floa
   if (!aligned(B, 16) || !aligned(P, 4)) return DOA_EINVAL;
   cudaStream_t s = as_stream(stream);
   uint32_t *S = reinterpret_cast<uint32_t *>(P);  // phase table first, spectrum over it
-  cudaError_t e = launch_grid_table_single(grid.lo_deg, grid.step_deg, grid.L, S, s);
+  cudaError_t e = launch_grid_table_single(grid.lo_deg, grid.step_deg, 0, grid.L, S, s);
   if (e != cudaSuccess) return DOA_ECUDA;
   const double2 *B2 = reinterpret_cast<const double2 *>(B);
   if (prec == DOA_FP32)
-    return cuda_status(launch_scan_single(B2, M, K, grid.L, grid.lo_deg, grid.step_deg, S, P, s));
+    return cuda_status(launch_scan_single(B2, M, K, grid.L, grid.lo_deg, grid.step_deg, 0, S, P, s));
   return cuda_status(launch_scan_tc_single(B2, M, K, grid.L, grid.lo_deg, grid.step_deg, prec, S, P, s));
+}
+
+doa_status doa_scan_slice(const double *B, int M, int K, doa_grid grid, int k0, int n, float *P, void *stream) {
+  if (!B || !P || M < 2 || M > kMaxM || K < 1 || K > M || !grid_ok(grid) || k0 < 0 || n < 1 ||
+      (int64_t)k0 + n > grid.L)
+    return DOA_EINVAL;
+  if (!aligned(B, 16) || !aligned(P, 4)) return DOA_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  uint32_t *S = reinterpret_cast<uint32_t *>(P);
+  if (launch_grid_table_single(grid.lo_deg, grid.step_deg, k0, n, S, s) != cudaSuccess) return DOA_ECUDA;
+  return cuda_status(launch_scan_single(reinterpret_cast<const double2 *>(B), M, K, n, grid.lo_deg, grid.step_deg,
+                                        k0, S, P, s));
+}
+
+doa_status doa_slice_peaks(const float *Pbuf, int b0, int k0, int k1, int L, int d, doa_slice_summary *out,
+                           void *stream) {
+  if (!Pbuf || !out || L < 3 || k0 < 0 || k1 <= k0 || k1 > L || b0 != (k0 > 0 ? k0 - 1 : 0) || d < 0 ||
+      d > DOA_SLICE_MAXD)
+    return DOA_EINVAL;
+  if (!aligned(Pbuf, 4) || !aligned(out, 4)) return DOA_EINVAL;
+  return cuda_status(launch_slice_peaks(Pbuf, b0, k0, k1, L, d, out, as_stream(stream)));
+}
+
+doa_status doa_merge_slices(const doa_slice_summary *sums, int nslices, int d, int32_t *idx, float *val,
+                            int32_t *count) {
+  if (!sums || nslices < 1 || d < 0 || d > DOA_SLICE_MAXD || !count || (d > 0 && (!idx || !val))) return DOA_EINVAL;
+  struct C {
+    float v;
+    int32_t i;
+  };
+  std::vector<C> cands;
+  for (int t = 0; t < nslices; ++t) {
+    const doa_slice_summary &a = sums[t];
+    if (a.count < 0 || a.count > DOA_SLICE_MAXD) return DOA_EINVAL;
+    for (int q = 0; q < a.count; ++q) cands.push_back(C{a.val[q], a.idx[q]});
+    if (a.open_idx < 0) continue;
+    const float v = a.open_val;
+    bool peak = false;
+    for (int u = t + 1; u < nslices; ++u) {   // the run covers the first point of slice u
+      if (!(sums[u].first_val == v)) return DOA_EINVAL;
+      if (!sums[u].first_run_to_end) {
+        peak = sums[u].first_next_val < v;
+        break;
+      }
+    }
+    if (peak) cands.push_back(C{v, a.open_idx});
+  }
+  std::sort(cands.begin(), cands.end(), [](const C &x, const C &y) { return x.v > y.v || (x.v == y.v && x.i < y.i); });
+  const int n = std::min<int>(d, (int)cands.size());
+  std::sort(cands.begin(), cands.begin() + n, [](const C &x, const C &y) { return x.i < y.i; });
+  for (int q = 0; q < n; ++q) {
+    idx[q] = cands[q].i;
+    val[q] = cands[q].v;
+  }
+  *count = n;
+  return DOA_OK;
 }
 
 doa_status doa_peaks(const float *P, int L, int d, int *idx, float *val, int *count, void *stream) {

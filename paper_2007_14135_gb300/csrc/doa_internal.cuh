@@ -229,7 +229,7 @@ __host__ __device__ inline int m_bucket(int M) { return M <= 8 ? 0 : (M <= 16 ? 
 // ------------------------------------------------------------------------------------------
 // Host launchers (one translation unit each). They return cudaError_t of the launch.
 // ------------------------------------------------------------------------------------------
-cudaError_t launch_grid_table_single(double lo, double step, int L, uint32_t *S, cudaStream_t s);
+cudaError_t launch_grid_table_single(double lo, double step, int k0, int n, uint32_t *S, cudaStream_t s);
 cudaError_t launch_grid_tables(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
 
 cudaError_t launch_covariance_single(const float2 *X, int M, int N, int ldx, float2 *R, double2 *R64,
@@ -244,8 +244,8 @@ cudaError_t launch_eig_single(const double2 *R64, int M, int d, int alg, double 
 cudaError_t launch_eig_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, int *status,
                              cudaStream_t s);
 
-cudaError_t launch_scan_single(const double2 *B, int M, int K, int L, double lo, double step, const uint32_t *S,
-                               float *P, cudaStream_t s);
+cudaError_t launch_scan_single(const double2 *B, int M, int K, int L, double lo, double step, int kofs,
+                               const uint32_t *S, float *P, cudaStream_t s);
 cudaError_t launch_scan_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
 cudaError_t launch_scan_tc_single(const double2 *B, int M, int K, int L, double lo, double step, int prec,
                                   const uint32_t *S, float *P, cudaStream_t s);
@@ -253,5 +253,7 @@ cudaError_t launch_scan_tc_single(const double2 *B, int M, int K, int L, double 
 cudaError_t launch_peaks_single(const float *P, int L, int d, int *idx, float *val, int *count,
                                 cudaStream_t s);
 cudaError_t launch_peaks_batch(const uint8_t *plan_dev, const PlanHeader &h, cudaStream_t s);
+cudaError_t launch_slice_peaks(const float *Pbuf, int b0, int k0, int k1, int L, int d, doa_slice_summary *out,
+                               cudaStream_t s);
 
 }  // namespace doa

@@ -54,7 +54,121 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_batch_kernel(const uint8_t
               pp.p.peak_val + (size_t)jb.slot * d, pp.p.peak_count + jb.slot);
 }
 
+// ---- grid slices ---------------------------------------------------------------------------
+// Value at global index k of a slice buffer that starts at global index b0.
+struct SliceView {
+  const float *buf;
+  int b0;
+  __device__ float operator()(int k) const { return buf[k - b0]; }
+};
+
+// 0: not a peak, 1: decided peak, 2: run still equal at `limit` (< L - 1), undecided.
+__device__ __forceinline__ int slice_peak_state(const SliceView &P, int i, float v, int limit, int L) {
+  if (!(P(i - 1) < v)) return 0;
+  int j = i;
+  while (j + 1 <= limit && P(j + 1) == v) ++j;
+  if (j + 1 <= limit) return P(j + 1) < v ? 1 : 0;
+  return limit < L - 1 ? 2 : 0;
+}
+
+// Best decided peaks among the thread's points (i = c0, c0 + T, ... < c1) worse than thr.
+__device__ bool slice_fill(const SliceView &P, int c0, int c1, int limit, int L, const Cand &thr,
+                           Cand (&cache)[kCache], int &n, int *open_idx, float *open_val) {
+  n = 0;
+  bool more = false;
+  for (int i = c0; i < c1; i += kPeakThreads) {
+    const float v = P(i);
+    const int st = slice_peak_state(P, i, v, limit, L);
+    if (st == 2) {
+      *open_idx = i;   // the unique run that reaches the end of the slice's data
+      *open_val = v;
+    }
+    if (st != 1) continue;
+    Cand c{v, i};
+    if (thr.i != INT_MAX && !better(thr, c)) continue;
+    if (n < kCache) {
+      int k = n++;
+      while (k > 0 && better(c, cache[k - 1])) {
+        cache[k] = cache[k - 1];
+        --k;
+      }
+      cache[k] = c;
+    } else {
+      more = true;
+      if (better(c, cache[kCache - 1])) {
+        int k = kCache - 1;
+        while (k > 0 && better(c, cache[k - 1])) {
+          cache[k] = cache[k - 1];
+          --k;
+        }
+        cache[k] = c;
+      }
+    }
+  }
+  return more;
+}
+
+__global__ void __launch_bounds__(kPeakThreads) slice_peaks_kernel(const float *Pbuf, int b0, int k0, int k1, int L,
+                                                                    int d, doa_slice_summary *out) {
+  __shared__ Cand red[kPeakThreads / 32 + 1];
+  __shared__ int s_open_idx;
+  __shared__ float s_open_val;
+  const SliceView P{Pbuf, b0};
+  const int limit = min(k1 + 1, L) - 1;              // last readable global index
+  const int c0 = max(k0, 1) + threadIdx.x, c1 = min(k1, L - 1);
+  if (threadIdx.x == 0) s_open_idx = -1;
+  __syncthreads();
+  int oi = -1;
+  float ov = 0.f;
+  Cand cache[kCache];
+  int n = 0, head = 0;
+  const Cand none{0.f, INT_MAX};
+  bool more = slice_fill(P, c0, c1, limit, L, none, cache, n, &oi, &ov);
+  if (oi >= 0) {
+    s_open_idx = oi;
+    s_open_val = ov;
+  }
+  int nsel = 0;
+  for (int r = 0; r < d; ++r) {
+    Cand mine = head < n ? cache[head] : none;
+    Cand w = block_best(mine, red);
+    if (w.i == INT_MAX) break;
+    if (threadIdx.x == 0) {
+      out->idx[nsel] = w.i;
+      out->val[nsel] = w.v;
+    }
+    ++nsel;
+    if (mine.i == w.i) {
+      ++head;
+      if (head == n && more) {
+        int dummy_i;
+        float dummy_v;
+        more = slice_fill(P, c0, c1, limit, L, w, cache, n, &dummy_i, &dummy_v);
+        head = 0;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    out->count = nsel;
+    out->open_idx = s_open_idx;
+    out->open_val = s_open_idx >= 0 ? s_open_val : 0.f;
+    const float v0 = P(k0);
+    int k = k0;
+    while (k + 1 <= limit && P(k + 1) == v0) ++k;
+    out->first_val = v0;
+    out->first_run_to_end = k + 1 > limit ? 1 : 0;
+    out->first_next_val = k + 1 <= limit ? P(k + 1) : 0.f;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_slice_peaks(const float *Pbuf, int b0, int k0, int k1, int L, int d, doa_slice_summary *out,
+                               cudaStream_t s) {
+  slice_peaks_kernel<<<1, kPeakThreads, 0, s>>>(Pbuf, b0, k0, k1, L, d, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_peaks_single(const float *P, int L, int d, int *idx, float *val, int *count, cudaStream_t s) {
   peaks_single_kernel<<<1, kPeakThreads, 0, s>>>(P, L, d, idx, val, count);

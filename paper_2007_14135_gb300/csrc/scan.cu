@@ -31,9 +31,9 @@ namespace {
 
 using namespace scanc;
 
-__global__ void grid_table_single_kernel(double lo, double step, int L, uint32_t *S) {
+__global__ void grid_table_single_kernel(double lo, double step, int k0, int n, uint32_t *S) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < L) S[k] = grid_phase_step(lo, step, k);
+  if (k < n) S[k] = grid_phase_step(lo, step, k0 + k);
 }
 
 __global__ void grid_table_batch_kernel(const uint8_t *plan, uint8_t *ws) {
@@ -51,7 +51,8 @@ __global__ void grid_table_batch_kernel(const uint8_t *plan, uint8_t *ws) {
 
 template <int MP, int PT>
 __global__ void __launch_bounds__(kScanThreads) scan_single_kernel(const double2 *B, int M, int K, int L, double lo,
-                                                                   double step, const uint32_t *S, float *P) {
+                                                                   double step, int kofs, const uint32_t *S,
+                                                                   float *P) {
   __shared__ __align__(16) float2 Bs[MP * MP];
   __shared__ ScanShared sh;
   ScanJob j{};
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_single_kernel(const double2
   j.Kf = K;
   j.Kn = K;
   j.kphd = j.kmn = -1;
+  j.kofs = kofs;
   load_job<MP>(j, Bs, sh);
   __syncthreads();
   set_threshold<MP>(Bs, j, sh);
@@ -162,8 +164,8 @@ cudaError_t run_batch(const uint8_t *plan, const PlanHeader &h, uint8_t *ws, int
 
 }  // namespace
 
-cudaError_t launch_grid_table_single(double lo, double step, int L, uint32_t *S, cudaStream_t s) {
-  grid_table_single_kernel<<<(L + 255) / 256, 256, 0, s>>>(lo, step, L, S);
+cudaError_t launch_grid_table_single(double lo, double step, int k0, int n, uint32_t *S, cudaStream_t s) {
+  grid_table_single_kernel<<<(n + 255) / 256, 256, 0, s>>>(lo, step, k0, n, S);
   return cudaGetLastError();
 }
 
@@ -177,16 +179,16 @@ cudaError_t launch_grid_tables(const uint8_t *plan_dev, const PlanHeader &h, uin
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan_single(const double2 *B, int M, int K, int L, double lo, double step, const uint32_t *S,
-                               float *P, cudaStream_t s) {
+cudaError_t launch_scan_single(const double2 *B, int M, int K, int L, double lo, double step, int kofs,
+                               const uint32_t *S, float *P, cudaStream_t s) {
   const int b = m_bucket(M);
   const int tp = kScanThreads * scan_pt_default(b);
   const unsigned grid = (unsigned)((L + tp - 1) / tp);
   switch (b) {
-    case 0: scan_single_kernel<8, 4><<<grid, kScanThreads, 0, s>>>(B, M, K, L, lo, step, S, P); break;
-    case 1: scan_single_kernel<16, 2><<<grid, kScanThreads, 0, s>>>(B, M, K, L, lo, step, S, P); break;
-    case 2: scan_single_kernel<32, 1><<<grid, kScanThreads, 0, s>>>(B, M, K, L, lo, step, S, P); break;
-    default: scan_single_kernel<64, 1><<<grid, kScanThreads, 0, s>>>(B, M, K, L, lo, step, S, P); break;
+    case 0: scan_single_kernel<8, 4><<<grid, kScanThreads, 0, s>>>(B, M, K, L, lo, step, kofs, S, P); break;
+    case 1: scan_single_kernel<16, 2><<<grid, kScanThreads, 0, s>>>(B, M, K, L, lo, step, kofs, S, P); break;
+    case 2: scan_single_kernel<32, 1><<<grid, kScanThreads, 0, s>>>(B, M, K, L, lo, step, kofs, S, P); break;
+    default: scan_single_kernel<64, 1><<<grid, kScanThreads, 0, s>>>(B, M, K, L, lo, step, kofs, S, P); break;
   }
   return cudaGetLastError();
 }

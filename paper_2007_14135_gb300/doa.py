@@ -27,7 +27,8 @@ STAGE_NAMES = ("phase_tables", "covariance", "eig_noise_subspace", "scan", "peak
 EXPORTS = ("doa_status_str", "doa_covariance", "doa_covariance_noalloc", "doa_noise_subspace", "doa_scan",
            "doa_peaks", "doa_batch_plan_bytes", "doa_batch_plan", "doa_solve_batch", "doa_mlp_workspace_bytes",
            "doa_mlp_refresh", "doa_mlp_forward", "doa_mlp_backward", "doa_mlp_adam", "doa_synth_ula",
-           "doa_proposal_windows", "doa_scan_windows")
+           "doa_proposal_windows", "doa_scan_windows", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices")
+SLICE_MAXD = 64
 
 
 class DoaError(RuntimeError):
@@ -50,6 +51,13 @@ class Problem(ctypes.Structure):
                 ("B_out", ctypes.c_void_p)]
 
 
+class SliceSummary(ctypes.Structure):
+    """doa_slice_summary: decided peaks of one grid slice plus what the merge needs at its edges."""
+    _fields_ = [("count", ctypes.c_int32), ("open_idx", ctypes.c_int32), ("open_val", ctypes.c_float),
+                ("first_val", ctypes.c_float), ("first_run_to_end", ctypes.c_int32),
+                ("first_next_val", ctypes.c_float), ("idx", ctypes.c_int32 * 64), ("val", ctypes.c_float * 64)]
+
+
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     if not os.path.exists(path):
         raise RuntimeError(f"libdoa.so is missing at {path}: run paper_2007_14135_gb300.build.build()")
@@ -67,8 +75,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.doa_batch_plan.argtypes = [ctypes.POINTER(Problem), i, vp, vp, sz, ctypes.POINTER(sz),
                                    ctypes.POINTER(ctypes.c_int)]
     lib.doa_solve_batch.argtypes = [vp, vp, vp, sz, vp, vp, vp]
+    lib.doa_scan_slice.argtypes = [vp, i, i, Grid, i, i, vp, vp]
+    lib.doa_slice_peaks.argtypes = [vp, i, i, i, i, i, vp, vp]
+    lib.doa_merge_slices.argtypes = [vp, i, i, vp, vp, vp]
     for name in ("doa_covariance", "doa_covariance_noalloc", "doa_noise_subspace", "doa_scan", "doa_peaks",
-                 "doa_batch_plan", "doa_solve_batch"):
+                 "doa_batch_plan", "doa_solve_batch", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices"):
         getattr(lib, name).restype = i
     return lib
 
@@ -145,6 +156,37 @@ def doa_scan(B: torch.Tensor, M: int, K: int, g: Grid, P: torch.Tensor, prec: in
     """P_k = 1/||B^H a(theta_k)||^2 for the grid. B: complex128, column-major (ld M)."""
     assert B.dtype == torch.complex128 and P.dtype == torch.float32 and P.numel() >= g.L
     _check(lib().doa_scan(_dev(B), M, K, g, prec, _dev(P), _stream(stream)), "doa_scan")
+
+
+def doa_scan_slice(B: torch.Tensor, M: int, K: int, g: Grid, k0: int, n: int, P: torch.Tensor, stream=None) -> None:
+    """The global grid points k0 .. k0+n-1 of doa_scan (FP32 path) into P[0..n)."""
+    assert B.dtype == torch.complex128 and P.dtype == torch.float32 and P.numel() >= n
+    _check(lib().doa_scan_slice(_dev(B), M, K, g, k0, n, _dev(P), _stream(stream)), "doa_scan_slice")
+
+
+def doa_slice_peaks(Pbuf: torch.Tensor, b0: int, k0: int, k1: int, L: int, d: int, out: torch.Tensor,
+                    stream=None) -> None:
+    """Peak summary of the slice [k0, k1); Pbuf holds global points b0 .. min(k1+1, L)-1 and out is
+    a device byte tensor of ctypes.sizeof(SliceSummary) bytes."""
+    assert Pbuf.dtype == torch.float32 and out.numel() * out.element_size() >= ctypes.sizeof(SliceSummary)
+    _check(lib().doa_slice_peaks(_dev(Pbuf), b0, k0, k1, L, d, _dev(out), _stream(stream)), "doa_slice_peaks")
+
+
+def slice_summary_from_bytes(raw: bytes) -> SliceSummary:
+    return SliceSummary.from_buffer_copy(raw[:ctypes.sizeof(SliceSummary)])
+
+
+def doa_merge_slices(sums: Sequence[SliceSummary], d: int):
+    """Host merge of per-slice summaries (slice order) -> (indices, values), as doa_peaks."""
+    arr = (SliceSummary * len(sums))(*sums)
+    idx = (ctypes.c_int32 * max(d, 1))()
+    val = (ctypes.c_float * max(d, 1))()
+    cnt = ctypes.c_int32(0)
+    _check(lib().doa_merge_slices(ctypes.cast(arr, ctypes.c_void_p), len(sums), d, ctypes.cast(idx, ctypes.c_void_p),
+                                  ctypes.cast(val, ctypes.c_void_p), ctypes.cast(ctypes.pointer(cnt), ctypes.c_void_p)),
+           "doa_merge_slices")
+    n = cnt.value
+    return np.array(idx[:n], dtype=np.int32), np.array(val[:n], dtype=np.float32)
 
 
 def doa_peaks(P: torch.Tensor, d: int, idx: torch.Tensor, val: torch.Tensor, count: torch.Tensor,
