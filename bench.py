@@ -175,7 +175,7 @@ def run_gpu(args):
         build.build()
     if world > 1:
         dist.barrier()
-    from paper_2007_14135_gb300 import doa
+    from paper_2007_14135_gb300 import doa, shard
 
     B, L = args.batch, grid_L()
     nalg = len(ALGS)
@@ -226,9 +226,7 @@ def run_gpu(args):
     stage_ms = [statistics.fmean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
                 for i in range(doa.BATCH_STAGES)]
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = shard.max_over_ranks(ms, device=dev)
 
     # ---- end to end through the C ABI from pinned host buffers: H2D of X, solve, D2H of the peaks
     Xpin = torch.from_numpy(Xh).pin_memory()
@@ -261,9 +259,7 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1) / args.steps
     if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        e2e_ms = shard.max_over_ranks(e2e_ms, device=dev)
 
     points = B * nalg * L * world
     solves = B * nalg * world
@@ -389,7 +385,7 @@ def run_uneven(args):
         build.build()
     if world > 1:
         dist.barrier()
-    from paper_2007_14135_gb300 import autotune, doa
+    from paper_2007_14135_gb300 import autotune, doa, shard
     dev = torch.device("cuda", local)
     Xd = torch.from_numpy(buf).to(dev)
     Ls = np.array([s.L for s in specs], dtype=np.int64)
@@ -450,9 +446,7 @@ def run_uneven(args):
     clk = clocks.stop()
     ms = t0.elapsed_time(t1) / args.steps
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = shard.max_over_ranks(ms, device=dev)
     points = int(Ls.sum()) * world
     # end to end: pinned H2D of all snapshots + graph + D2H of peaks and status
     Xpin = torch.from_numpy(buf).pin_memory()
