@@ -105,3 +105,37 @@ def test_autotuner_picks_allowed_tiles_and_persists(env, tmp_path):
         assert set(entry["eig_ms"]) == set(autotune.EIG_CANDIDATES[b])
         assert em[b] in autotune.EIG_CANDIDATES[b]
     assert autotune.tune(probs, path=path) == (pts, em)    # second call: from the table, no timing
+
+
+def test_streamed_batch_matches_resident_solve(env):
+    """Chunks streamed through two buffer sets (upload, solve and download on three streams) give
+    the peaks and status of one resident doa_solve_batch over the same problems."""
+    torch, doa = env
+    from paper_2007_14135_gb300 import streamed
+    B, M, N, d, L = 48, 16, 1024, 4, 1801
+    insts = [synth.custom(M, d, N, None, 10.0, 0.1, seed=500 + i) for i in range(B)]
+    Xh = np.stack([inst.X for inst in insts]).astype(np.complex64)
+    g = doa.grid(-90.0, 0.1, L)
+    X = torch.from_numpy(Xh).cuda()
+    P = torch.empty((B, 4, L), dtype=torch.float32, device="cuda")
+    idx = torch.full((B, 4, d), -1, dtype=torch.int32, device="cuda")
+    val = torch.zeros((B, 4, d), dtype=torch.float32, device="cuda")
+    cnt = torch.zeros((B, 4), dtype=torch.int32, device="cuda")
+    st = torch.full((B,), -1, dtype=torch.int32, device="cuda")
+    probs = [doa.make_problem(X[i], d, 0xF, g, P[i], idx[i], val[i], cnt[i]) for i in range(B)]
+    plan = doa.BatchPlan(probs)
+    doa.doa_solve_batch(plan, doa.workspace(plan), st)
+    torch.cuda.synchronize()
+    sb = streamed.StreamedBatch(M, N, d, 0xF, g, 16)
+    Xpin = torch.from_numpy(Xh).pin_memory()
+    oi = torch.full((B, 4, d), -7, dtype=torch.int32).pin_memory()
+    ov = torch.zeros((B, 4, d), dtype=torch.float32).pin_memory()
+    oc = torch.zeros((B, 4), dtype=torch.int32).pin_memory()
+    os_ = torch.full((B,), -7, dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        ev = sb.enqueue(Xpin, oi, ov, oc, os_)
+    ev.synchronize()
+    assert np.array_equal(os_.numpy(), st.cpu().numpy()) and np.all(os_.numpy() == 0)
+    assert np.array_equal(oc.numpy(), cnt.cpu().numpy())
+    assert np.array_equal(oi.numpy(), idx.cpu().numpy()) and np.array_equal(ov.numpy(), val.cpu().numpy())
+    assert np.array_equal(sb.spectra(2).cpu().numpy(), P[32:48].cpu().numpy())
