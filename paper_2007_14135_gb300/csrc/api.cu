@@ -47,13 +47,15 @@ bool problem_ok(const doa_problem &p) {
   if (p.alg_mask == 0u || p.alg_mask > 15u) return false;
   if (p.d > 0 && (!p.peak_idx || !p.peak_val)) return false;
   if (!p.peak_count) return false;
-  if (p.prec != DOA_FP32) return false;
+  // scan form: FP32 (CUDA cores) or split operands on the tensor cores (M <= 32)
+  if (p.prec != DOA_FP32 && !((p.prec == DOA_BF16X3 || p.prec == DOA_FP16X3) && p.M <= kTcBatchMaxM)) return false;
   return grid_ok(p.grid);
 }
 
 struct PlanSizes {
   int nprob = 0, njobs = 0, ngrids = 0, ncov = 0, nreduce = 0;
   int cov_class[kCovClasses] = {0, 0, 0, 0};
+  int tc = 0;
   int eig[kNumBuckets] = {0, 0, 0, 0};
   int scan[kNumBuckets] = {0, 0, 0, 0};
 };
@@ -80,7 +82,10 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
     sz.nreduce += chunks > 1;
     sz.eig[m_bucket(p.M)] += 1;
     sz.njobs += __builtin_popcount(p.alg_mask);
-    sz.scan[m_bucket(p.M)] += 1;
+    if (p.prec == DOA_FP32)
+      sz.scan[m_bucket(p.M)] += 1;
+    else
+      sz.tc += 1;
     int g = -1;
     for (size_t k = 0; k < grids.size(); ++k)
       if (same_grid(grids[k], p.grid)) {
@@ -98,7 +103,7 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
 }
 
 struct PlanOffsets {
-  int64_t prob, job, grid, cov, reduce, eig[kNumBuckets], scan[kNumBuckets], total;
+  int64_t prob, job, grid, cov, reduce, eig[kNumBuckets], scan[kNumBuckets], tc, total;
 };
 
 PlanOffsets plan_offsets(const PlanSizes &sz) {
@@ -122,6 +127,8 @@ PlanOffsets plan_offsets(const PlanSizes &sz) {
     o.scan[b] = at;
     at = round_up(at + (int64_t)sz.scan[b] * 4, 16);
   }
+  o.tc = at;
+  at = round_up(at + (int64_t)sz.tc * 4, 16);
   o.total = at;
   return o;
 }
@@ -280,6 +287,8 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     eig[b] = reinterpret_cast<int32_t *>(base + o.eig[b]);
     scan[b] = reinterpret_cast<int32_t *>(base + o.scan[b]);
   }
+  int32_t *tcl = reinterpret_cast<int32_t *>(base + o.tc);
+  h.off_tc = o.tc;
   h.magic = kPlanMagic;
   for (int b = 0; b < kNumBuckets; ++b) h.scan_pt[b] = pt[b];
   h.nprob = sz.nprob;
@@ -347,10 +356,17 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     factor_layout(p, q);
     q.fac_off = ws;
     ws = round_up(ws + factor_bytes(M), 256);
-    const int tp = kScanThreads * pt[b];
-    q.tile_start = tiles[b];
-    tiles[b] += (p.grid.L + tp - 1) / tp;
-    scan[b][is[b]++] = i;
+    if (p.prec == DOA_FP32) {
+      const int tp = kScanThreads * pt[b];
+      q.tile_start = tiles[b];
+      tiles[b] += (p.grid.L + tp - 1) / tp;
+      scan[b][is[b]++] = i;
+    } else {
+      q.tile_start = h.tc_tiles;
+      h.tc_tiles += (p.grid.L + 127) / 128;
+      tcl[h.tc_jobs++] = i;
+      h.tc_cols = std::max(h.tc_cols, tc_batch_cols(q.Kf));
+    }
   }
   for (int b = 0; b < kNumBuckets; ++b) {
     h.eig_mats[b] = (tuning && tuning->eig_mats[b] != 0) ? tuning->eig_mats[b] : eig_mats_default(b, sz.eig[b]);
@@ -380,6 +396,7 @@ doa_status doa_solve_batch(const void *plan_host, const void *plan_dev, void *ws
   if (!mark(1) || launch_covariance_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
   if (!mark(2) || launch_eig_batch(pd, h, w, status, s) != cudaSuccess) return DOA_ECUDA;
   if (!mark(3) || launch_scan_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
+  if (h.tc_jobs > 0 && launch_scan_tc_batch(pd, h, w, status, s) != cudaSuccess) return DOA_ECUDA;
   if (!mark(4) || launch_peaks_batch(pd, h, s) != cudaSuccess) return DOA_ECUDA;
   if (!mark(5)) return DOA_ECUDA;
   return DOA_OK;

@@ -194,6 +194,11 @@ struct PlanHeader {
   int32_t eig_mats[kNumBuckets];         // matrices per Jacobi warp, per M bucket
   int32_t cov_first[kCovClasses + 1];    // covariance items sorted by class: class c owns
                                          // items [cov_first[c], cov_first[c + 1])
+  // problems scanned on the tensor cores (prec BF16X3 / FP16X3, M <= 32), in their own list
+  int32_t tc_jobs;
+  int32_t tc_cols;                       // TMEM columns a CTA allocates (covers every tc problem)
+  int64_t tc_tiles;                      // 128-point tiles over all tc problems
+  int64_t off_tc;                        // byte offset of the tc problem list
 };
 
 // The Python binding reads these header fields by position (int32 index 22 = scan_pt, 58 = eig_mats).
@@ -201,6 +206,7 @@ static_assert(offsetof(PlanHeader, scan_pt) == 88, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, scan_tiles) == 56, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, eig_mats) == 232, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, cov_first) == 248, "PlanHeader layout changed");
+static_assert(offsetof(PlanHeader, tc_jobs) == 268, "PlanHeader layout changed");
 
 // Scan tiles: kScanThreads threads, each evaluating PT consecutive grid points (tile shape
 // 128 x PT). PT is chosen per M bucket (the autotuner's knob); the register budget limits it
@@ -247,6 +253,16 @@ cudaError_t launch_eig_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8
 cudaError_t launch_scan_single(const double2 *B, int M, int K, int L, double lo, double step, int kofs,
                                const uint32_t *S, float *P, cudaStream_t s);
 cudaError_t launch_scan_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
+cudaError_t launch_scan_tc_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, int *status,
+                                 cudaStream_t s);
+// Tensor-core batch scan: tiles of 128 points; problems with M <= 32 only.
+constexpr int kTcBatchMaxM = 32;
+__host__ __device__ inline int tc_batch_cols(int Kf) {   // TMEM columns: two accumulators of N
+  const int N = (2 * Kf + 31) / 32 * 32;
+  int p2 = 32;
+  while (p2 < 2 * N) p2 <<= 1;
+  return p2;
+}
 cudaError_t launch_scan_tc_single(const double2 *B, int M, int K, int L, double lo, double step, int prec,
                                   const uint32_t *S, float *P, cudaStream_t s);
 

@@ -1,0 +1,441 @@
+// Step-5 of the batch on the tensor cores (problems with doa_problem.prec = DOA_FP16X3 or
+// DOA_BF16X3, M <= 32): the shared-contraction scan of scan_common.cuh (one steering block per
+// tile of 128 grid points against the problem's whole factor F, readouts MUSIC / EV / PHD / MN)
+// done as the real GEMM of scan_tc.cu:
+//   A (128 x KD): rows = grid points, [Re a_0, Im a_0, Re a_1, ...] split into hi + lo halves;
+//   W (N x KD):   real embedding of F (rows 2c, 2c+1 give Re y_c, Im y_c), scaled by a power of two
+//                 so that its entries are at most 1, split into hi + lo;
+//   D (128 x N) in TMEM, FP32: hi*hi (+ hi*lo + lo*hi; FP16: the cross terms, scaled by 2^11, in a
+//   second accumulator).
+// KD = 64 (2 M rounded up to one 128-byte swizzle atom), N = 2 Kf rounded up to 32.
+//
+// Per CTA (256 threads, two per grid point; two CTAs per SM): for each tile of its runs of tiles,
+// the threads write the steering block into the swizzled K-major layout, one thread issues the
+// MMAs and commits them to an mbarrier (bounded wait), the 8 warps read the accumulator rows
+// (warp w: TMEM lanes 32 (w % 4).., half w / 4 of the columns) and form the readouts.
+// Accuracy: a readout below c^2 sum_k w_k ||f_k||^2 (c from the split's per-term error, so that
+// the others stay within 1e-3 relative) is re-evaluated by a warp in FP32 with exact integer
+// phases, and where the FP32 value is below the FP32 path's threshold, in FP64
+// (refine_point_warp), exactly as the CUDA-core scan does.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <float.h>
+
+#include "doa_internal.cuh"
+#include "scan_common.cuh"
+#include "tc_common.cuh"
+
+namespace doa {
+namespace {
+
+using namespace tc;
+using namespace scanc;
+
+constexpr int kTbThreads = 256;
+constexpr int kTbWarps = kTbThreads / 32;
+constexpr int kTbKD = 64;                          // K extent (one swizzle atom)
+constexpr int kTbMaxCols = kTcBatchMaxM + 1;       // Kf <= M + 1
+constexpr int kTbMaxN = (2 * kTbMaxCols + 31) / 32 * 32;
+constexpr int kTbRun = 8;                          // consecutive tiles per run
+
+// dynamic shared memory layout (bytes from a 1024-aligned base)
+constexpr int kOffAhi = 0;
+constexpr int kOffAlo = kOffAhi + kTcRows * 128;
+constexpr int kOffWhi = kOffAlo + kTcRows * 128;
+constexpr int kOffWlo = kOffWhi + kTbMaxN * 128;
+constexpr int kOffB32 = kOffWlo + kTbMaxN * 128;                        // Kf x 32 float2
+constexpr int kOffPh64 = kOffB32 + kTbMaxCols * kTcBatchMaxM * 8;        // per warp 32 double2
+constexpr int kOffYb = kOffPh64 + kTbWarps * kTcBatchMaxM * 16;          // per warp kMaxCols float2
+constexpr int kOffPh32 = kOffYb + kTbWarps * kMaxCols * 8;               // per warp 32 float2
+constexpr int kOffRed = kOffPh32 + kTbWarps * kTcBatchMaxM * 8;          // 128 x 2 float4
+constexpr int kTbSmem = kOffRed + kTcRows * 2 * 16 + 1024;
+
+struct TbShared {
+  uint64_t mbar;
+  uint32_t tmem;
+  int nflag;
+  int flags[kTcRows];
+  uint32_t sk[kTcRows];
+  float w32[kTcBatchMaxM];
+  float thr32[4], thrtc[4];
+  float scale2;
+  int maxbits;
+};
+
+// FP32 re-evaluation of all readouts of one point by a warp (lanes: phasors, then columns).
+__device__ __forceinline__ void readouts32_warp(const float2 *B32, int MPs, int M, const ScanJob &j, const float *w32,
+                                                uint32_t Sk, float2 *ph, float (&d)[4]) {
+  const int lane = threadIdx.x & 31;
+  for (int m = lane; m < M; m += 32) ph[m] = phasor_q32((uint32_t)m * Sk);
+  __syncwarp();
+  float dm = 0.f, de = 0.f, dp = 0.f, dn = 0.f;
+  for (int col = lane; col < j.Kf; col += 32) {
+    float yr = 0.f, yi = 0.f;
+    const float2 *b = B32 + col * MPs;
+    for (int m = 0; m < M; ++m) {
+      const float2 bb = b[m], a = ph[m];
+      yr = fmaf(bb.x, a.x, fmaf(bb.y, a.y, yr));
+      yi = fmaf(bb.x, a.y, fmaf(-bb.y, a.x, yi));
+    }
+    const float n = fmaf(yr, yr, yi * yi);
+    if (col < j.Kn) {
+      dm += n;
+      de = fmaf(w32[col], n, de);
+    }
+    if (col == j.kphd) dp = n;
+    if (col == j.kmn) dn = n;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    dm += __shfl_xor_sync(0xffffffffu, dm, off);
+    de += __shfl_xor_sync(0xffffffffu, de, off);
+    dp += __shfl_xor_sync(0xffffffffu, dp, off);
+    dn += __shfl_xor_sync(0xffffffffu, dn, off);
+  }
+  d[kRoPhd] = dp;
+  d[kRoMusic] = dm;
+  d[kRoEv] = de;
+  d[kRoMn] = dn;
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kTbThreads, 2) scan_tc_batch_kernel(const uint8_t *plan, uint8_t *ws, int *status) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ TbShared sh;
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
+  const int nunits = h->tc_jobs;
+  const int64_t ntiles = h->tc_tiles;
+  const int32_t *list = reinterpret_cast<const int32_t *>(plan + h->off_tc);
+  const PlanProblem *probs = reinterpret_cast<const PlanProblem *>(plan + h->off_prob);
+  const PlanGrid *grids = reinterpret_cast<const PlanGrid *>(plan + h->off_grid);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint8_t *ahi = sm + kOffAhi, *alo = sm + kOffAlo, *whi = sm + kOffWhi, *wlo = sm + kOffWlo;
+  float2 *B32 = reinterpret_cast<float2 *>(sm + kOffB32);
+  double2 *ph64 = reinterpret_cast<double2 *>(sm + kOffPh64) + warp * kTcBatchMaxM;
+  float2 *yb = reinterpret_cast<float2 *>(sm + kOffYb) + warp * kMaxCols;
+  float2 *ph32 = reinterpret_cast<float2 *>(sm + kOffPh32) + warp * kTcBatchMaxM;
+  float4 *red = reinterpret_cast<float4 *>(sm + kOffRed);
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sh.mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sh.nflag = 0;
+  }
+  const int cols = h->tc_cols;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem)),
+                 "r"(cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sh.tmem;
+
+  bool ok = true;
+  uint32_t iter = 0;
+  int pending = -1;   // parity of a commit whose wait ran out
+  int cur = -1;
+  ScanJob j{};
+  const PlanProblem *pp = nullptr;
+  const PlanGrid *g = nullptr;
+  int prec = DOA_FP16X3, MPs = 16, N = 32;
+  uint32_t idesc = 0;
+
+  for (int64_t run = blockIdx.x; run * kTbRun < ntiles; run += gridDim.x) {
+    const int64_t t_begin = run * kTbRun, t_end = min(ntiles, t_begin + kTbRun);
+    int u = 0, hi = nunits - 1;
+    while (u < hi) {  // last problem with tile_start <= t_begin
+      int mid = (u + hi + 1) >> 1;
+      if (probs[list[mid]].tile_start <= t_begin) u = mid; else hi = mid - 1;
+    }
+    for (int64_t t = t_begin; t < t_end; ++t) {
+      while (u + 1 < nunits && probs[list[u + 1]].tile_start <= t) ++u;
+      if (u != cur) {
+        // ---- problem setup: FP32 factor, weights, thresholds, scaled split W
+        pp = &probs[list[u]];
+        g = &grids[pp->grid_id];
+        j.F = reinterpret_cast<const double2 *>(ws + pp->fac_off);
+        j.w = pp->Kn > 0 && pp->slot[DOA_EV] >= 0
+                  ? reinterpret_cast<const double *>(ws + pp->fac_off) + 2 * pp->p.M * (pp->p.M + 1)
+                  : nullptr;
+        j.S64 = reinterpret_cast<const uint64_t *>(ws + g->S64_off);
+        for (int r = 0; r < 4; ++r) j.P[r] = pp->slot[r] >= 0 ? pp->p.P + (size_t)pp->slot[r] * g->L : nullptr;
+        j.lo = g->lo;
+        j.step = g->step;
+        j.M = pp->p.M;
+        j.Kf = pp->Kf;
+        j.Kn = pp->Kn;
+        j.kphd = pp->kphd;
+        j.kmn = pp->kmn;
+        j.kofs = 0;
+        prec = pp->p.prec;
+        MPs = (j.M + 15) / 16 * 16;
+        N = (2 * j.Kf + 31) / 32 * 32;
+        idesc = inst_desc(prec == DOA_FP16X3 ? 0 : 1, N);
+        __syncthreads();   // previous tile's readers of W / B32 are done
+        if (tid == 0) sh.maxbits = 0;
+        __syncthreads();
+        float mx = 0.f;
+        for (int e = tid; e < j.Kf * MPs; e += kTbThreads) {
+          const int k = e / MPs, m = e % MPs;
+          float2 v = make_float2(0.f, 0.f);
+          if (m < j.M) {
+            const double2 b = j.F[(size_t)k * j.M + m];
+            v = make_float2((float)b.x, (float)b.y);
+          }
+          B32[e] = v;
+          mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+        for (int k = tid; k < j.Kn; k += kTbThreads) sh.w32[k] = j.w ? (float)j.w[k] : 1.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if (lane == 0) atomicMax(&sh.maxbits, __float_as_int(mx));
+        __syncthreads();
+        if (warp == 0) {
+          // E_r from s_k = sum_m |f_mk| (FP32 threshold), N2_r from ||f_k||^2 (tensor threshold)
+          float em = 0.f, ee = 0.f, nm = 0.f, ne = 0.f;
+          for (int k = lane; k < j.Kf; k += 32) {
+            float n1 = 0.f, q2 = 0.f;
+            for (int m = 0; m < j.M; ++m) {
+              const float2 b = B32[k * MPs + m];
+              const float a2 = b.x * b.x + b.y * b.y;
+              q2 += a2;
+              n1 += sqrtf(a2);
+            }
+            const float e = n1 * n1;
+            if (k < j.Kn) {
+              em += e;
+              ee += sh.w32[k] * e;
+              nm += q2;
+              ne += sh.w32[k] * q2;
+            }
+            const float gam = prec == DOA_FP16X3 ? 1.0e-6f : 8.0e-6f;
+            const float c = 2.8f * gam / 1.0e-3f;
+            if (k == j.kphd) {
+              sh.thr32[kRoPhd] = kRefineC * e;
+              sh.thrtc[kRoPhd] = c * c * q2;
+            }
+            if (k == j.kmn) {
+              sh.thr32[kRoMn] = kRefineC * e;
+              sh.thrtc[kRoMn] = c * c * q2;
+            }
+          }
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            em += __shfl_xor_sync(0xffffffffu, em, off);
+            ee += __shfl_xor_sync(0xffffffffu, ee, off);
+            nm += __shfl_xor_sync(0xffffffffu, nm, off);
+            ne += __shfl_xor_sync(0xffffffffu, ne, off);
+          }
+          if (lane == 0) {
+            const float gam = prec == DOA_FP16X3 ? 1.0e-6f : 8.0e-6f;
+            const float c = 2.8f * gam / 1.0e-3f;
+            sh.thr32[kRoMusic] = kRefineC * em;
+            sh.thr32[kRoEv] = kRefineC * ee;
+            sh.thrtc[kRoMusic] = c * c * nm;
+            sh.thrtc[kRoEv] = c * c * ne;
+          }
+        }
+        int ex = 0;
+        frexpf(fmaxf(__int_as_float(sh.maxbits), FLT_MIN), &ex);
+        const float wscale = ldexpf(1.f, -ex);
+        if (tid == 0) sh.scale2 = ldexpf(1.f, 2 * ex);
+        for (int e = tid; e < N * kTbKD; e += kTbThreads) {
+          const int n = e / kTbKD, kap = e % kTbKD;
+          const int col = n >> 1, m = kap >> 1;
+          float w = 0.f;
+          if (col < j.Kf && m < j.M) {
+            const float2 b = B32[col * MPs + m];
+            const bool re_out = (n & 1) == 0, re_in = (kap & 1) == 0;
+            w = (re_out ? (re_in ? b.x : b.y) : (re_in ? -b.y : b.x)) * wscale;
+          }
+          uint16_t hv, lv;
+          split16(w, prec, hv, lv);
+          const uint32_t off = sw128(n, kap);
+          *reinterpret_cast<uint16_t *>(whi + off) = hv;
+          *reinterpret_cast<uint16_t *>(wlo + off) = lv;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        cur = u;
+      }
+      const int L = g->L;
+      const int k0 = (int)(t - pp->tile_start) * kTcRows;
+      const uint32_t *S = reinterpret_cast<const uint32_t *>(ws + g->S_off);
+      // ---- steering block: row pt, elements [part * MPs / 2, (part + 1) * MPs / 2), 4 per chunk
+      {
+        const int pt = tid >> 1, part = tid & 1;
+        const int k = k0 + pt;
+        const uint32_t Sk = k < L ? S[k] : 0u;
+        if (part == 0) sh.sk[pt] = Sk;
+        const int mh = MPs / 2, m0 = part * mh;
+        for (int c = 0; c < mh; c += 4) {
+          uint16_t hs[8], ls[8];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 v = phasor_q32((uint32_t)(m0 + c + q) * Sk);
+            split16(v.x, prec, hs[2 * q], ls[2 * q]);
+            split16(v.y, prec, hs[2 * q + 1], ls[2 * q + 1]);
+          }
+          const uint32_t off = sw128(pt, 2 * (m0 + c));
+          uint4 vh, vl;
+          vh.x = hs[0] | ((uint32_t)hs[1] << 16);
+          vh.y = hs[2] | ((uint32_t)hs[3] << 16);
+          vh.z = hs[4] | ((uint32_t)hs[5] << 16);
+          vh.w = hs[6] | ((uint32_t)hs[7] << 16);
+          vl.x = ls[0] | ((uint32_t)ls[1] << 16);
+          vl.y = ls[2] | ((uint32_t)ls[3] << 16);
+          vl.z = ls[4] | ((uint32_t)ls[5] << 16);
+          vl.w = ls[6] | ((uint32_t)ls[7] << 16);
+          *reinterpret_cast<uint4 *>(ahi + off) = vh;
+          *reinterpret_cast<uint4 *>(alo + off) = vl;
+        }
+        for (int kap = 2 * MPs + part * 8; kap < kTbKD; kap += 16) {   // K padding
+          const uint32_t off = sw128(pt, kap);
+          *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(0, 0, 0, 0);
+          *reinterpret_cast<uint4 *>(alo + off) = make_uint4(0, 0, 0, 0);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      // ---- MMAs (one thread)
+      if (tid == 0 && ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t b_ahi = smem_u32(ahi), b_alo = smem_u32(alo), b_whi = smem_u32(whi), b_wlo = smem_u32(wlo);
+        for (int kk = 0; kk < kTbKD / 16; ++kk) {
+          const uint32_t off = (uint32_t)kk * 32;
+          const uint32_t acc = kk > 0 ? 1u : 0u;
+          mma(tmem, smem_desc(b_ahi + off), smem_desc(b_whi + off), idesc, acc);
+          if (prec == DOA_BF16X3) {
+            mma(tmem, smem_desc(b_ahi + off), smem_desc(b_wlo + off), idesc, 1u);
+            mma(tmem, smem_desc(b_alo + off), smem_desc(b_whi + off), idesc, 1u);
+          } else {
+            mma(tmem + (uint32_t)N, smem_desc(b_ahi + off), smem_desc(b_wlo + off), idesc, acc);
+            mma(tmem + (uint32_t)N, smem_desc(b_alo + off), smem_desc(b_whi + off), idesc, 1u);
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&sh.mbar))
+                     : "memory");
+      }
+      const bool was_ok = ok;
+      const bool done = ok && mbar_wait(smem_u32(&sh.mbar), iter & 1u);
+      ok = __syncthreads_and(done);
+      if (was_ok && !ok) pending = (int)(iter & 1u);
+      ++iter;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // ---- epilogue: readout partial sums of each row over this warp's half of the columns
+      const int q = warp & 3, cs = warp >> 2;
+      const int row = q * 32 + lane;
+      float4 part = make_float4(0.f, 0.f, 0.f, 0.f);   // (MUSIC, EV, PHD, MN)
+      if (ok) {
+        const int half = N / 2;
+        for (int c0 = cs * half; c0 < (cs + 1) * half; c0 += 8) {
+          float v[8];
+          tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+          if (prec == DOA_FP16X3) {
+            float w[8];
+            tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(N + c0), w);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = fmaf(w[i], 4.8828125e-4f, v[i]);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int col = c0 / 2 + i;
+            const float n = fmaf(v[2 * i], v[2 * i], v[2 * i + 1] * v[2 * i + 1]);
+            if (col < j.Kn) {
+              part.x += n;
+              part.y = fmaf(sh.w32[col], n, part.y);
+            }
+            if (col == j.kphd) part.z = n;
+            if (col == j.kmn) part.w = n;
+          }
+        }
+      }
+      red[row * 2 + cs] = part;
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      if (tid < kTcRows) {
+        const int k = k0 + tid;
+        if (k < L) {
+          if (!ok) {
+            const float nan = __int_as_float(0x7fc00000);   // timed-out tile: NaN marks it
+            for (int r = 0; r < 4; ++r)
+              if (j.P[r]) j.P[r][k] = nan;
+          } else {
+            const float4 a = red[tid * 2], b = red[tid * 2 + 1];
+            const float s2 = sh.scale2;
+            float den[4];
+            den[kRoMusic] = (a.x + b.x) * s2;
+            den[kRoEv] = (a.y + b.y) * s2;
+            den[kRoPhd] = (a.z + b.z) * s2;
+            den[kRoMn] = (a.w + b.w) * s2;
+            bool flag = false;
+            for (int r = 0; r < 4; ++r)
+              if (j.P[r]) {
+                j.P[r][k] = recip_out(den[r]);
+                flag = flag || den[r] < sh.thrtc[r];
+              }
+            if (flag) sh.flags[atomicAdd(&sh.nflag, 1)] = k;
+          }
+        }
+      }
+      __syncthreads();
+      // ---- re-evaluation of the flagged points: FP32 by a warp, FP64 below the FP32 threshold
+      const int nf = sh.nflag;
+      for (int i = warp; i < nf; i += kTbWarps) {
+        const int k = sh.flags[i];
+        float d[4];
+        readouts32_warp(B32, MPs, j.M, j, sh.w32, sh.sk[k - k0], ph32, d);
+        bool need64 = false;
+        for (int r = 0; r < 4; ++r) need64 = need64 || (j.P[r] && d[r] < sh.thr32[r]);
+        if (need64) {
+          refine_point_warp(j, k, sh.w32, ph64, yb);
+        } else if (lane == 0) {
+          for (int r = 0; r < 4; ++r)
+            if (j.P[r]) j.P[r][k] = recip_out(d[r]);
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        sh.nflag = 0;
+        if (!ok && status) status[list[u]] = DOA_ETIMEOUT;
+      }
+    }
+  }
+  // a timed-out commit may still be in flight: give it one more bounded wait before freeing TMEM
+  if (pending >= 0) mbar_wait(smem_u32(&sh.mbar), (uint32_t)pending);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+}
+
+int g_tb_sms = 0;
+
+}  // namespace
+
+cudaError_t launch_scan_tc_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, int *status,
+                                 cudaStream_t s) {
+  if (h.tc_jobs == 0 || h.tc_tiles == 0) return cudaSuccess;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(scan_tc_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTbSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (g_tb_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_tb_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_tb_sms <= 0) g_tb_sms = 1;
+  }
+  const int64_t runs = (h.tc_tiles + kTbRun - 1) / kTbRun;
+  int64_t grid = (int64_t)g_tb_sms * 2;
+  if (grid > runs) grid = runs;
+  scan_tc_batch_kernel<<<(unsigned)grid, kTbThreads, kTbSmem, s>>>(plan_dev, ws, status);
+  return cudaGetLastError();
+}
+
+}  // namespace doa

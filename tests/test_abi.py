@@ -159,3 +159,22 @@ def test_batch_plan_eig_mats(libdoa):
             got = list(buf[:256].view(np.int32)[58:62])
             # default with one problem per bucket: no packing
             assert got == [v if v else 1 for v in em], (em, got)
+
+
+def test_batch_plan_tensor_scan_problems(libdoa):
+    """Split-precision scan forms are planned into their own tensor-core list (M <= 32 only)."""
+    import numpy as np
+    ok = [_prob(libdoa, M=16, prec=3), _prob(libdoa, M=32, d=5, prec=2), _prob(libdoa, M=8, d=2)]
+    arr = (libdoa.Problem * 3)(*ok)
+    n = libdoa.lib().doa_batch_plan_bytes(arr, 3)
+    assert n > 0
+    buf = np.zeros(n, np.uint8)
+    ws = ctypes.c_size_t(0)
+    assert libdoa.lib().doa_batch_plan(arr, 3, None, buf.ctypes.data, n, ctypes.byref(ws), None) == 0
+    h32 = buf[:512].view(np.int32)
+    assert h32[67] == 2                       # tc_jobs
+    assert h32[68] == 128                     # TMEM columns: Kf = 13 -> N = 32 per accumulator; 27 -> 64 -> 128
+    assert list(h32[10:14]) == [1, 0, 0, 0]   # FP32 scan lists hold only the M = 8 problem
+    for bad in (_prob(libdoa, M=33, prec=3), _prob(libdoa, M=16, prec=1), _prob(libdoa, M=16, prec=4)):
+        arr = (libdoa.Problem * 1)(bad)
+        assert libdoa.lib().doa_batch_plan_bytes(arr, 1) == 0

@@ -194,7 +194,7 @@ def test_single_calls_c1(env):
         assert idx.tolist() == ref["idx"].tolist()
 
 
-def _batch_solve(torch, doa, insts, masks):
+def _batch_solve(torch, doa, insts, masks, prec=0):
     tensors, probs = [], []
     for inst, mask in zip(insts, masks):
         nalg = bin(mask).count("1")
@@ -205,7 +205,8 @@ def _batch_solve(torch, doa, insts, masks):
         cnt = torch.zeros(nalg, dtype=torch.int32, device="cuda")
         ev = torch.empty(inst.M, dtype=torch.float64, device="cuda")
         tensors.append((X, P, idx, val, cnt, ev))
-        probs.append(doa.make_problem(X, inst.d, mask, doa.grid(inst.lo, inst.step, inst.L), P, idx, val, cnt, ev))
+        probs.append(doa.make_problem(X, inst.d, mask, doa.grid(inst.lo, inst.step, inst.L), P, idx, val, cnt, ev,
+                                      prec=prec))
     plan = doa.BatchPlan(probs)
     ws = doa.workspace(plan)
     status = torch.full((len(insts),), -1, dtype=torch.int32, device="cuda")
@@ -214,8 +215,8 @@ def _batch_solve(torch, doa, insts, masks):
     return tensors, status.cpu().numpy()
 
 
-def _check_batch(torch, doa, insts, masks):
-    tensors, status = _batch_solve(torch, doa, insts, masks)
+def _check_batch(torch, doa, insts, masks, prec=0):
+    tensors, status = _batch_solve(torch, doa, insts, masks, prec)
     assert np.all(status == 0), status
     worst = 0.0
     for inst, mask, t in zip(insts, masks, tensors):
@@ -318,6 +319,24 @@ def test_batch_every_algorithm_subset(env):
     insts.append(synth.custom(5, 0, 64, [], 0.0, 0.5, seed=931))     # d = 0: E_n = all of V, valph = e1
     masks.append(0xF)
     _check_batch(torch, doa, insts, masks)
+
+
+@pytest.mark.parametrize("prec", [2, 3])   # DOA_BF16X3, DOA_FP16X3
+def test_batch_tensor_core_scan(env, prec):
+    """Split-operand tcgen05 scan in the batch (shared contraction, four readouts, FP32 then FP64
+    re-evaluation of the near-null points): every spectrum within 0.01 dB of the oracle and the
+    same peaks, over every algorithm subset and M up to 32."""
+    torch, doa = env
+    insts = [synth.paper_density(i) for i in range(4)]
+    masks = [0xF] * 4
+    Ms = [8, 12, 16, 32, 5]
+    for mask in range(1, 16):
+        M = Ms[mask % len(Ms)]
+        insts.append(synth.custom(M, 1 + mask % 3, 1500 + 37 * mask, None, 5.0 + mask, 0.1, seed=700 + mask))
+        masks.append(mask)
+    insts.append(synth.custom(5, 0, 64, [], 0.0, 0.5, seed=731))     # d = 0: Kf = M + 1
+    masks.append(0xF)
+    _check_batch(torch, doa, insts, masks, prec)
 
 
 def test_batch_edge_shapes(env):
