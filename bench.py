@@ -150,6 +150,38 @@ def oracle_sample(Xh, S, workers, full=0):
     return res, dt
 
 
+def parity_summary(res, ig, cg, Pg, Xh, L):
+    """Peak agreement of the GPU results (ig, cg: peak indices / counts of the sampled problems;
+    Pg: spectra of the first problems) with the oracle's `res`, ties classified, dB and Eq. 4."""
+    import oracle
+    worst_db, agree, differ = 0.0, 0, []
+    eq4 = {a: [] for a in ALGS}
+    for i, a, io, Po, sto in res:
+        same = list(ig[i, a, :cg[i, a]]) == list(io)
+        agree += same
+        if not same:
+            differ.append((i, a, list(io)))
+        if Po is not None and i < len(Pg):
+            Pi = Pg[i, a].astype(np.float64)
+            worst_db = max(worst_db, float(np.max(np.abs(10 * np.log10(Pi / Po.astype(np.float64))))))
+            eq4[a].append(eq4_percent(Pi, Po))
+    # a disagreement is a tie within tolerance when the oracle's values at the differing indices
+    # are within 1e-4 relative (the FP32 path's error bound near a peak)
+    ties = 0
+    for i, a, io in differ[:64]:
+        Po = oracle.solve(Xh[i], D, a, LO, STEP, L)["P"]
+        gi = [int(k) for k in ig[i, a, :cg[i, a]]]
+        ks = sorted(set(gi) ^ set(io))
+        ties += all(abs(Po[k] - max(Po[k - 1], Po[k + 1])) / Po[k] < 1e-4 or
+                    any(abs(Po[k] - Po[j]) / Po[k] < 1e-4 for j in ks if j != k) for k in ks)
+    names = {0: "PHD", 1: "MUSIC", 2: "EV", 3: "MN"}
+    return {"sampled_solves": len(res), "peak_index_agreement": agree,
+            "disagreements_tie_within_1e-4": f"{ties}/{len(differ)}",
+            "spectra_compared": sum(len(v) for v in eq4.values()), "max_db_err": worst_db,
+            "eq4_percent_max": {names[a]: max(v) for a, v in eq4.items() if v},
+            "eq4_percent_mean": {names[a]: statistics.fmean(v) for a, v in eq4.items() if v}}
+
+
 def eq4_percent(P_meas, P_truth):
     """Eq. 4: 100/N sum |y_meas - y_truth| / |y_truth| over the N spectrum points."""
     P_meas, P_truth = np.asarray(P_meas, np.float64), np.asarray(P_truth, np.float64)
@@ -333,36 +365,43 @@ def run_gpu(args):
         result["cpu_baseline"] = {"value": pts / dt, "unit": "points/s", "cores": workers, "kind": "oracle",
                                   "sample": f"first {S} problems of the batch x 4 algorithms ({pts} points)",
                                   "seconds": round(dt, 3)}
-        Pg = P[:full].cpu().numpy()
-        ig = idx[:S].cpu().numpy()
-        cg = cnt[:S].cpu().numpy()
-        worst_db, agree, differ = 0.0, 0, []
-        eq4 = {a: [] for a in ALGS}
-        for i, a, io, Po, sto in res:
-            same = list(ig[i, a, :cg[i, a]]) == list(io)
-            agree += same
-            if not same:
-                differ.append((i, a, list(io)))
-            if Po is not None:
-                Pi = Pg[i, a].astype(np.float64)
-                worst_db = max(worst_db, float(np.max(np.abs(10 * np.log10(Pi / Po.astype(np.float64))))))
-                eq4[a].append(eq4_percent(Pi, Po))
-        # a disagreement is a tie within tolerance when the oracle's own margin between the two
-        # candidate points is below 1e-4 relative (the FP32 path's error bound near a peak)
-        ties = 0
-        for i, a, io in differ[:64]:
-            import oracle
-            Po = oracle.solve(Xh[i], D, a, LO, STEP, L)["P"]
-            gi = [int(k) for k in ig[i, a, :cg[i, a]]]
-            ks = sorted(set(gi) ^ set(io))
-            ties += all(abs(Po[k] - max(Po[k - 1], Po[k + 1])) / Po[k] < 1e-4 or
-                        any(abs(Po[k] - Po[j]) / Po[k] < 1e-4 for j in ks if j != k) for k in ks)
-        names = {0: "PHD", 1: "MUSIC", 2: "EV", 3: "MN"}
-        result["parity"] = {"sampled_solves": len(res), "peak_index_agreement": agree,
-                            "disagreements_tie_within_1e-4": f"{ties}/{len(differ)}",
-                            "spectra_compared": full * nalg, "max_db_err": worst_db,
-                            "eq4_percent_max": {names[a]: max(v) for a, v in eq4.items() if v},
-                            "eq4_percent_mean": {names[a]: statistics.fmean(v) for a, v in eq4.items() if v}}
+        result["parity"] = parity_summary(res, idx[:S].cpu().numpy(), cnt[:S].cpu().numpy(),
+                                          P[:full].cpu().numpy(), Xh, L)
+
+    # ---- the same batch with the scan on the tensor cores (FP16x3 split operands) and with the
+    # FP64 Jacobi: time, stage times and the same parity check against the oracle
+    if rank == 0 and world == 1 and not args.no_forms:
+        forms = {}
+        for name, prec, eprec in (("fp16x3_scan", doa.FP16X3, doa.EIG_DOUBLE_FLOAT),
+                                  ("fp64_jacobi", doa.FP32, doa.EIG_FP64)):
+            fprobs = [doa.make_problem(X[i], D, 0xF, g, P[i], idx[i], val[i], cnt[i], prec=prec, eig_prec=eprec)
+                      for i in range(B)]
+            fplan = doa.BatchPlan(fprobs, device=str(dev))
+            fws = doa.workspace(fplan, device=str(dev))
+            for _ in range(args.warmup):
+                doa.doa_solve_batch(fplan, fws, status, stream=stream)
+            fev = [[torch.cuda.Event(enable_timing=True) for _ in range(nst)] for _ in range(args.steps)]
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            f0.record(stream)
+            for k in range(args.steps):
+                doa.doa_solve_batch(fplan, fws, status, stage_events=fev[k], stream=stream)
+            f1.record(stream)
+            torch.cuda.synchronize(dev)
+            fms = f0.elapsed_time(f1) / args.steps
+            fst = [statistics.fmean(fev[k][i].elapsed_time(fev[k][i + 1]) for k in range(args.steps))
+                   for i in range(doa.BATCH_STAGES)]
+            info = {"ms_per_step": fms, "points_per_s": points / (fms / 1e3), "solves_per_s": solves / (fms / 1e3),
+                    "stages_ms": {n: round(v, 4) for n, v in zip(doa.STAGE_NAMES, fst)},
+                    "status_ok": bool(np.all(status.cpu().numpy() == 0))}
+            if "parity" in result:
+                S = min(args.cpu_sample, B)
+                full = min(args.parity_full, S)
+                info["parity"] = parity_summary(res, idx[:S].cpu().numpy(), cnt[:S].cpu().numpy(),
+                                                P[:full].cpu().numpy(), Xh, L)
+            forms[name] = info
+            del fplan, fws, fprobs
+        result["forms"] = forms
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -751,6 +790,7 @@ def main():
     ap.add_argument("--reference-sample", type=int, default=256, help="--impl reference: problems per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-chunk", type=int, default=1024, help="problems per streamed chunk in the e2e leg")
+    ap.add_argument("--no-forms", action="store_true", help="skip the tensor-core scan and FP64-Jacobi forms")
     ap.add_argument("--workload", choices=["paper-density", "uneven", "large-array", "learned"],
                     default="paper-density")
     ap.add_argument("--train", type=int, default=1 << 20, help="learned workload: training instances")

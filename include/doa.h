@@ -209,6 +209,13 @@ doa_status doa_merge_slices(const doa_slice_summary *sums, int nslices, int d, i
 /* caller may capture into a CUDA graph.                                                      */
 /* ----------------------------------------------------------------------------------------- */
 
+/* Arithmetic of the batch's Jacobi eigensolver (single calls always use FP64). GB300 issues FP64
+ * at about 1/64 of its FP32 rate, so the default runs the same rotations in double-float
+ * arithmetic (pairs of FP32 numbers, ~48 significant bits) on the FP32 pipe; DOA_EIG_FP64 runs
+ * them in FP64. Either way the noise eigenvectors are then checked for orthonormality in FP64
+ * (max |E_n^H E_n - I| <= 1e-10, else the problem's status is DOA_ENOCONV). */
+typedef enum { DOA_EIG_DOUBLE_FLOAT = 0, DOA_EIG_FP64 = 1 } doa_eig_prec;
+
 /* One problem of a batch. All pointers are device pointers owned by the caller. */
 typedef struct {
   const float *X;        /* M x N complex64 row-major, row stride ldx                        */
@@ -225,6 +232,8 @@ typedef struct {
                          /* of R / tr(R) as (re, im) pairs (the proposal network's input)     */
   double *B_out;         /* nullable: copy of the factor B of the first algorithm in          */
                          /* alg_mask (M x K complex128, column-major, ld M)                   */
+  int32_t eig_prec;      /* doa_eig_prec of the batch's Jacobi                                */
+  int32_t reserved;
 } doa_problem;
 
 /* Launch-shape knobs of a plan, per M bucket (M <= 8, <= 16, <= 32, <= 64); 0 = default. */

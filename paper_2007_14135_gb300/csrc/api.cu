@@ -45,6 +45,7 @@ bool problem_ok(const doa_problem &p) {
   if (p.M < 2 || p.M > kMaxM || p.d < 0 || p.d >= p.M || p.N < 1 || p.ldx < p.N) return false;
   if (!p.X || !aligned(p.X, 8) || !p.P || !aligned(p.P, 4)) return false;
   if (p.alg_mask == 0u || p.alg_mask > 15u) return false;
+  if (p.eig_prec != DOA_EIG_DOUBLE_FLOAT && p.eig_prec != DOA_EIG_FP64) return false;
   if (p.d > 0 && (!p.peak_idx || !p.peak_val)) return false;
   if (!p.peak_count) return false;
   // scan form: FP32 (CUDA cores) or split operands on the tensor cores (M <= 32)

@@ -546,6 +546,32 @@ __device__ int build_factor(int M, int d, int alg, EigSmem<NP> &s, double2 *__re
   return 0;
 }
 
+// FP64 check that the noise eigenvectors are orthonormal: max |E_n^H E_n - I| <= kOrthoTol.
+constexpr double kOrthoTol = 1e-10;
+
+template <int NP>
+__device__ bool noise_orthonormal(int M, int d, EigSmem<NP> &s) {
+  constexpr int T = grp_threads<NP>();
+  using g = Grp<T>;
+  const int lane = g::id();
+  const int Kn = M - d;
+  bool ok = true;
+  for (int e = lane; e < Kn * Kn; e += T) {
+    const int a = e / Kn, b = e % Kn;
+    if (a > b) continue;
+    const int ca = s.order[d + a], cb = s.order[d + b];
+    double gr = 0.0, gi = 0.0;
+    for (int r = 0; r < M; ++r) {   // conj(V[r][ca]) * V[r][cb]
+      const double2 x = s.V[r][ca], y = s.V[r][cb];
+      gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+      gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+    }
+    if (a == b) gr -= 1.0;
+    ok = ok && fabs(gr) <= kOrthoTol && fabs(gi) <= kOrthoTol;
+  }
+  return g::all(ok);
+}
+
 // Writes a batch problem's scan factor F (columns as laid out by the plan: E_n, or v_min; then
 // valph) and the EV weights w_c = 1 / lambda_{d+c}; returns 0 or a doa_status.
 template <int NP>
@@ -630,7 +656,12 @@ __global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_batch_kernel(const u
     Ms[j] = prob[j] >= 0 ? probs[prob[j]].p.M : 0;
     Rs[j] = prob[j] >= 0 ? reinterpret_cast<const double2 *>(ws + probs[prob[j]].r64_off) : nullptr;
   }
-  jacobi_group_df<NP, G>(mats, Ms, Rs, res);
+  bool fp64 = false;   // a group runs FP64 when any of its problems asks for it
+  for (int j = 0; j < G; ++j) fp64 = fp64 || (prob[j] >= 0 && probs[prob[j]].p.eig_prec == DOA_EIG_FP64);
+  if (fp64)
+    jacobi_group<NP, G>(mats, Ms, Rs, res);
+  else
+    jacobi_group_df<NP, G>(mats, Ms, Rs, res);
   for (int j = 0; j < G; ++j) {
     if (prob[j] < 0) continue;
     const PlanProblem &pp = probs[prob[j]];
@@ -658,6 +689,7 @@ __global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_batch_kernel(const u
       if (pp.p.evals)
         for (int i = lane; i < M; i += T) pp.p.evals[i] = s.lam[s.order[i]];
       st = build_scan_factor<NP>(pp, s, F, w);
+      if (!noise_orthonormal<NP>(M, d, s) && !st) st = DOA_ENOCONV;
       if (pp.p.B_out) build_factor<NP>(M, d, jobs[pp.first_job].alg, s, reinterpret_cast<double2 *>(pp.p.B_out));
     } else {
       st = -res[j];

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libdoa.so")
 
 PHD, MUSIC, EV, MN = 0, 1, 2, 3
 FP32, BF16, BF16X3, FP16X3 = 0, 1, 2, 3
+EIG_DOUBLE_FLOAT, EIG_FP64 = 0, 1
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ERANK, ENONFINITE, ETIMEOUT = range(8)
 NOALLOC_SCRATCH_BYTES = 4 << 20
 BATCH_STAGES = 5
@@ -48,7 +49,7 @@ class Problem(ctypes.Structure):
                 ("evals", ctypes.c_void_p), ("grid", Grid), ("M", ctypes.c_int32),
                 ("N", ctypes.c_int32), ("ldx", ctypes.c_int32), ("d", ctypes.c_int32),
                 ("alg_mask", ctypes.c_uint32), ("prec", ctypes.c_int32), ("features", ctypes.c_void_p),
-                ("B_out", ctypes.c_void_p)]
+                ("B_out", ctypes.c_void_p), ("eig_prec", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class SliceSummary(ctypes.Structure):
@@ -199,12 +200,12 @@ def doa_peaks(P: torch.Tensor, d: int, idx: torch.Tensor, val: torch.Tensor, cou
 def make_problem(X: torch.Tensor, d: int, alg_mask: int, g: Grid, P: torch.Tensor, peak_idx: torch.Tensor,
                  peak_val: torch.Tensor, peak_count: torch.Tensor, evals: Optional[torch.Tensor] = None,
                  prec: int = FP32, features: Optional[torch.Tensor] = None,
-                 B_out: Optional[torch.Tensor] = None) -> Problem:
+                 B_out: Optional[torch.Tensor] = None, eig_prec: int = 0) -> Problem:
     """Descriptor of one problem; the tensors must outlive every solve that uses it."""
     assert X.dtype == torch.complex64 and X.dim() == 2 and X.stride(1) == 1
     M, N = X.shape
     return Problem(_dev(X), _dev(P), _dev(peak_idx), _dev(peak_val), _dev(peak_count), _dev(evals), g,
-                   M, N, X.stride(0), d, alg_mask, prec, _dev(features), _dev(B_out))
+                   M, N, X.stride(0), d, alg_mask, prec, _dev(features), _dev(B_out), eig_prec, 0)
 
 
 class Tuning(ctypes.Structure):

@@ -194,7 +194,7 @@ def test_single_calls_c1(env):
         assert idx.tolist() == ref["idx"].tolist()
 
 
-def _batch_solve(torch, doa, insts, masks, prec=0):
+def _batch_solve(torch, doa, insts, masks, prec=0, eig_prec=0):
     tensors, probs = [], []
     for inst, mask in zip(insts, masks):
         nalg = bin(mask).count("1")
@@ -206,7 +206,7 @@ def _batch_solve(torch, doa, insts, masks, prec=0):
         ev = torch.empty(inst.M, dtype=torch.float64, device="cuda")
         tensors.append((X, P, idx, val, cnt, ev))
         probs.append(doa.make_problem(X, inst.d, mask, doa.grid(inst.lo, inst.step, inst.L), P, idx, val, cnt, ev,
-                                      prec=prec))
+                                      prec=prec, eig_prec=eig_prec))
     plan = doa.BatchPlan(probs)
     ws = doa.workspace(plan)
     status = torch.full((len(insts),), -1, dtype=torch.int32, device="cuda")
@@ -215,8 +215,8 @@ def _batch_solve(torch, doa, insts, masks, prec=0):
     return tensors, status.cpu().numpy()
 
 
-def _check_batch(torch, doa, insts, masks, prec=0):
-    tensors, status = _batch_solve(torch, doa, insts, masks, prec)
+def _check_batch(torch, doa, insts, masks, prec=0, eig_prec=0):
+    tensors, status = _batch_solve(torch, doa, insts, masks, prec, eig_prec)
     assert np.all(status == 0), status
     worst = 0.0
     for inst, mask, t in zip(insts, masks, tensors):
@@ -337,6 +337,20 @@ def test_batch_tensor_core_scan(env, prec):
     insts.append(synth.custom(5, 0, 64, [], 0.0, 0.5, seed=731))     # d = 0: Kf = M + 1
     masks.append(0xF)
     _check_batch(torch, doa, insts, masks, prec)
+
+
+def test_batch_fp64_jacobi(env):
+    """The batch's FP64 Jacobi (doa_problem.eig_prec = DOA_EIG_FP64) meets the same bar, and its
+    spectra agree with the default double-float Jacobi's to far inside the tolerance."""
+    torch, doa = env
+    insts = [synth.paper_density(i) for i in range(3)] + [synth.custom(32, 6, 3000, None, 12.0, 0.1, seed=41),
+                                                          synth.custom(8, 2, 900, None, 8.0, 0.1, seed=42)]
+    masks = [0xF] * len(insts)
+    _check_batch(torch, doa, insts, masks, eig_prec=1)
+    a, _ = _batch_solve(torch, doa, insts, masks, eig_prec=1)
+    b, _ = _batch_solve(torch, doa, insts, masks, eig_prec=0)
+    for ta, tb in zip(a, b):
+        assert db_error(ta[1].cpu().numpy(), tb[1].cpu().numpy().astype(np.float64)) < 1e-3
 
 
 def test_batch_edge_shapes(env):
