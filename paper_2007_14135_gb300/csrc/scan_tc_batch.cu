@@ -264,33 +264,44 @@ __global__ void __launch_bounds__(kTbThreads, 2) scan_tc_batch_kernel(const uint
       const int L = g->L;
       const int k0 = (int)(t - pp->tile_start) * kTcRows;
       const uint32_t *S = reinterpret_cast<const uint32_t *>(ws + g->S_off);
-      // ---- steering block: row pt, elements [part * MPs / 2, (part + 1) * MPs / 2), 4 per chunk
+      // ---- steering block: row pt, elements [part * MPs / 2, (part + 1) * MPs / 2), 4 per 16-byte
+      // chunk. Phasors of the chunk's first element from its exact phase, the other three as its
+      // product with a_1, a_2, a_3 (also exact-phase polynomials); (re, im) pairs are split with
+      // packed conversions straight into the 32-bit (re, im) halves of the swizzled row.
       {
         const int pt = tid >> 1, part = tid & 1;
         const int k = k0 + pt;
         const uint32_t Sk = k < L ? S[k] : 0u;
         if (part == 0) sh.sk[pt] = Sk;
         const int mh = MPs / 2, m0 = part * mh;
+        const float2 z1 = phasor_q32(Sk), z2 = phasor_q32(2u * Sk), z3 = phasor_q32(3u * Sk);
         for (int c = 0; c < mh; c += 4) {
-          uint16_t hs[8], ls[8];
+          const float2 a0 = (m0 + c) == 0 ? make_float2(1.f, 0.f) : phasor_q32((uint32_t)(m0 + c) * Sk);
+          float2 v[4];
+          v[0] = a0;
+          v[1] = make_float2(fmaf(a0.x, z1.x, -a0.y * z1.y), fmaf(a0.x, z1.y, a0.y * z1.x));
+          v[2] = make_float2(fmaf(a0.x, z2.x, -a0.y * z2.y), fmaf(a0.x, z2.y, a0.y * z2.x));
+          v[3] = make_float2(fmaf(a0.x, z3.x, -a0.y * z3.y), fmaf(a0.x, z3.y, a0.y * z3.x));
+          uint32_t hw[4], lw[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const float2 v = phasor_q32((uint32_t)(m0 + c + q) * Sk);
-            split16(v.x, prec, hs[2 * q], ls[2 * q]);
-            split16(v.y, prec, hs[2 * q + 1], ls[2 * q + 1]);
+            if (prec == DOA_FP16X3) {
+              const __half2 h2 = __floats2half2_rn(v[q].x, v[q].y);
+              const float2 b = __half22float2(h2);
+              const __half2 l2 = __floats2half2_rn((v[q].x - b.x) * 2048.0f, (v[q].y - b.y) * 2048.0f);
+              hw[q] = *reinterpret_cast<const uint32_t *>(&h2);
+              lw[q] = *reinterpret_cast<const uint32_t *>(&l2);
+            } else {
+              const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[q].x, v[q].y);
+              const float2 b = __bfloat1622float2(h2);
+              const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[q].x - b.x, v[q].y - b.y);
+              hw[q] = *reinterpret_cast<const uint32_t *>(&h2);
+              lw[q] = *reinterpret_cast<const uint32_t *>(&l2);
+            }
           }
           const uint32_t off = sw128(pt, 2 * (m0 + c));
-          uint4 vh, vl;
-          vh.x = hs[0] | ((uint32_t)hs[1] << 16);
-          vh.y = hs[2] | ((uint32_t)hs[3] << 16);
-          vh.z = hs[4] | ((uint32_t)hs[5] << 16);
-          vh.w = hs[6] | ((uint32_t)hs[7] << 16);
-          vl.x = ls[0] | ((uint32_t)ls[1] << 16);
-          vl.y = ls[2] | ((uint32_t)ls[3] << 16);
-          vl.z = ls[4] | ((uint32_t)ls[5] << 16);
-          vl.w = ls[6] | ((uint32_t)ls[7] << 16);
-          *reinterpret_cast<uint4 *>(ahi + off) = vh;
-          *reinterpret_cast<uint4 *>(alo + off) = vl;
+          *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4 *>(alo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
         for (int kap = 2 * MPs + part * 8; kap < kTbKD; kap += 16) {   // K padding
           const uint32_t off = sw128(pt, kap);
@@ -320,9 +331,10 @@ __global__ void __launch_bounds__(kTbThreads, 2) scan_tc_batch_kernel(const uint
                          smem_u32(&sh.mbar))
                      : "memory");
       }
+      // one thread polls the mbarrier; the others wait at the barrier without taking issue slots
       const bool was_ok = ok;
-      const bool done = ok && mbar_wait(smem_u32(&sh.mbar), iter & 1u);
-      ok = __syncthreads_and(done);
+      const bool done = tid != 0 || (ok && mbar_wait(smem_u32(&sh.mbar), iter & 1u));
+      ok = __syncthreads_and(done && ok);
       if (was_ok && !ok) pending = (int)(iter & 1u);
       ++iter;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
