@@ -257,10 +257,10 @@ cudaError_t launch_scan_tc_batch(const uint8_t *plan_dev, const PlanHeader &h, u
                                  cudaStream_t s);
 // Tensor-core batch scan: tiles of 128 points; problems with M <= 32 only.
 constexpr int kTcBatchMaxM = 32;
-__host__ __device__ inline int tc_batch_cols(int Kf) {   // TMEM columns: two accumulators of N
+__host__ __device__ inline int tc_batch_cols(int Kf) {   // TMEM columns: 2 buffers x 2 accumulators of N
   const int N = (2 * Kf + 31) / 32 * 32;
   int p2 = 32;
-  while (p2 < 2 * N) p2 <<= 1;
+  while (p2 < 4 * N) p2 <<= 1;
   return p2;
 }
 cudaError_t launch_scan_tc_single(const double2 *B, int M, int K, int L, double lo, double step, int prec,

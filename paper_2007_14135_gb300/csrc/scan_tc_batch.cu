@@ -9,10 +9,12 @@
 //   second accumulator).
 // KD = 64 (2 M rounded up to one 128-byte swizzle atom), N = 2 Kf rounded up to 32.
 //
-// Per CTA (256 threads, two per grid point; two CTAs per SM): for each tile of its runs of tiles,
-// the threads write the steering block into the swizzled K-major layout, one thread issues the
-// MMAs and commits them to an mbarrier (bounded wait), the 8 warps read the accumulator rows
-// (warp w: TMEM lanes 32 (w % 4).., half w / 4 of the columns) and form the readouts.
+// Per CTA (256 threads, two per grid point; two CTAs per SM while their TMEM fits): a software
+// pipeline over consecutive tiles of one problem with two steering buffers and two accumulator
+// sets — the threads write tile i+1's steering block into the swizzled K-major layout and one
+// thread issues its MMAs (committed to that buffer's mbarrier, bounded wait) while the 8 warps
+// read tile i's accumulator rows back (warp w: TMEM lanes 32 (w % 4).., half w / 4 of the
+// columns) and form the readouts.
 // Accuracy: a readout below c^2 sum_k w_k ||f_k||^2 (c from the split's per-term error, so that
 // the others stay within 1e-3 relative) is re-evaluated by a warp in FP32 with exact integer
 // phases, and where the FP32 value is below the FP32 path's threshold, in FP64
@@ -36,26 +38,28 @@ constexpr int kTbWarps = kTbThreads / 32;
 constexpr int kTbKD = 64;                          // K extent (one swizzle atom)
 constexpr int kTbMaxCols = kTcBatchMaxM + 1;       // Kf <= M + 1
 constexpr int kTbMaxN = (2 * kTbMaxCols + 31) / 32 * 32;
-constexpr int kTbRun = 8;                          // consecutive tiles per run
+constexpr int kTbRun = 16;                         // consecutive tiles per run
 
 // dynamic shared memory layout (bytes from a 1024-aligned base)
-constexpr int kOffAhi = 0;
-constexpr int kOffAlo = kOffAhi + kTcRows * 128;
-constexpr int kOffWhi = kOffAlo + kTcRows * 128;
+constexpr int kABytes = kTcRows * 128;                                 // one 128 x 64 16-bit operand
+constexpr int kOffA = 0;                                                // [buffer][hi, lo]
+constexpr int kOffWhi = kOffA + 4 * kABytes;
 constexpr int kOffWlo = kOffWhi + kTbMaxN * 128;
 constexpr int kOffB32 = kOffWlo + kTbMaxN * 128;                        // Kf x 32 float2
 constexpr int kOffPh64 = kOffB32 + kTbMaxCols * kTcBatchMaxM * 8;        // per warp 32 double2
-constexpr int kOffYb = kOffPh64 + kTbWarps * kTcBatchMaxM * 16;          // per warp kMaxCols float2
-constexpr int kOffPh32 = kOffYb + kTbWarps * kMaxCols * 8;               // per warp 32 float2
+constexpr int kYbCols = kTbMaxCols + 1;
+constexpr int kOffYb = kOffPh64 + kTbWarps * kTcBatchMaxM * 16;          // per warp kYbCols float2
+constexpr int kOffPh32 = kOffYb + kTbWarps * kYbCols * 8;                // per warp 32 float2
 constexpr int kOffRed = kOffPh32 + kTbWarps * kTcBatchMaxM * 8;          // 128 x 2 float4
 constexpr int kTbSmem = kOffRed + kTcRows * 2 * 16 + 1024;
+static_assert(2 * (kTbSmem + 2048) <= 228 * 1024, "two CTAs per SM");
 
 struct TbShared {
-  uint64_t mbar;
+  uint64_t mbar[2];
   uint32_t tmem;
   int nflag;
   int flags[kTcRows];
-  uint32_t sk[kTcRows];
+  uint32_t sk[2 * kTcRows];
   float w32[kTcBatchMaxM];
   float thr32[4], thrtc[4];
   float scale2;
@@ -110,15 +114,17 @@ __global__ void __launch_bounds__(kTbThreads, 2) scan_tc_batch_kernel(const uint
   const PlanProblem *probs = reinterpret_cast<const PlanProblem *>(plan + h->off_prob);
   const PlanGrid *grids = reinterpret_cast<const PlanGrid *>(plan + h->off_grid);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint8_t *ahi = sm + kOffAhi, *alo = sm + kOffAlo, *whi = sm + kOffWhi, *wlo = sm + kOffWlo;
+  uint8_t *whi = sm + kOffWhi, *wlo = sm + kOffWlo;
   float2 *B32 = reinterpret_cast<float2 *>(sm + kOffB32);
   double2 *ph64 = reinterpret_cast<double2 *>(sm + kOffPh64) + warp * kTcBatchMaxM;
-  float2 *yb = reinterpret_cast<float2 *>(sm + kOffYb) + warp * kMaxCols;
+  float2 *yb = reinterpret_cast<float2 *>(sm + kOffYb) + warp * kYbCols;
   float2 *ph32 = reinterpret_cast<float2 *>(sm + kOffPh32) + warp * kTcBatchMaxM;
   float4 *red = reinterpret_cast<float4 *>(sm + kOffRed);
+  auto a_hi = [&](int b) { return sm + kOffA + (2 * b) * kABytes; };
+  auto a_lo = [&](int b) { return sm + kOffA + (2 * b + 1) * kABytes; };
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sh.mbar)));
+    for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sh.mbar[b])));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sh.nflag = 0;
   }
@@ -134,14 +140,87 @@ __global__ void __launch_bounds__(kTbThreads, 2) scan_tc_batch_kernel(const uint
   const uint32_t tmem = sh.tmem;
 
   bool ok = true;
-  uint32_t iter = 0;
-  int pending = -1;   // parity of a commit whose wait ran out
+  uint32_t phase[2] = {0u, 0u};   // next parity to wait for, per mbarrier
+  int pending = -1;               // mbarrier whose wait ran out (its commit may still land)
+  uint32_t pending_parity = 0u;
   int cur = -1;
   ScanJob j{};
   const PlanProblem *pp = nullptr;
   const PlanGrid *g = nullptr;
   int prec = DOA_FP16X3, MPs = 16, N = 32;
   uint32_t idesc = 0;
+
+  // steering block of tile t into buffer b (row pt, elements [part * MPs / 2, (part + 1) * MPs / 2),
+  // 4 per 16-byte chunk: the chunk's first phasor from its exact phase, the others as its products
+  // with a_1, a_2, a_3; (re, im) pairs split with packed conversions into the swizzled row)
+  auto gen = [&](int b, int64_t t) {
+    const int L = g->L;
+    const int k0 = (int)(t - pp->tile_start) * kTcRows;
+    const uint32_t *S = reinterpret_cast<const uint32_t *>(ws + g->S_off);
+    uint8_t *ahi = a_hi(b), *alo = a_lo(b);
+    const int pt = tid >> 1, part = tid & 1;
+    const int k = k0 + pt;
+    const uint32_t Sk = k < L ? S[k] : 0u;
+    if (part == 0) sh.sk[b * kTcRows + pt] = Sk;
+    const int mh = MPs / 2, m0 = part * mh;
+    const float2 z1 = phasor_q32(Sk), z2 = phasor_q32(2u * Sk), z3 = phasor_q32(3u * Sk);
+    for (int c = 0; c < mh; c += 4) {
+      const float2 a0 = (m0 + c) == 0 ? make_float2(1.f, 0.f) : phasor_q32((uint32_t)(m0 + c) * Sk);
+      float2 v[4];
+      v[0] = a0;
+      v[1] = make_float2(fmaf(a0.x, z1.x, -a0.y * z1.y), fmaf(a0.x, z1.y, a0.y * z1.x));
+      v[2] = make_float2(fmaf(a0.x, z2.x, -a0.y * z2.y), fmaf(a0.x, z2.y, a0.y * z2.x));
+      v[3] = make_float2(fmaf(a0.x, z3.x, -a0.y * z3.y), fmaf(a0.x, z3.y, a0.y * z3.x));
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (prec == DOA_FP16X3) {
+          const __half2 h2 = __floats2half2_rn(v[q].x, v[q].y);
+          const float2 bk = __half22float2(h2);
+          const __half2 l2 = __floats2half2_rn((v[q].x - bk.x) * 2048.0f, (v[q].y - bk.y) * 2048.0f);
+          hw[q] = *reinterpret_cast<const uint32_t *>(&h2);
+          lw[q] = *reinterpret_cast<const uint32_t *>(&l2);
+        } else {
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[q].x, v[q].y);
+          const float2 bk = __bfloat1622float2(h2);
+          const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[q].x - bk.x, v[q].y - bk.y);
+          hw[q] = *reinterpret_cast<const uint32_t *>(&h2);
+          lw[q] = *reinterpret_cast<const uint32_t *>(&l2);
+        }
+      }
+      const uint32_t off = sw128(pt, 2 * (m0 + c));
+      *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4 *>(alo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+    for (int kap = 2 * MPs + part * 8; kap < kTbKD; kap += 16) {   // K padding
+      const uint32_t off = sw128(pt, kap);
+      *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4 *>(alo + off) = make_uint4(0, 0, 0, 0);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  };
+  // MMAs of buffer b into accumulator set b (thread 0; after a barrier that follows gen(b))
+  auto issue = [&](int b) {
+    if (tid != 0 || !ok) return;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t b_ahi = smem_u32(a_hi(b)), b_alo = smem_u32(a_lo(b)), b_whi = smem_u32(whi), b_wlo = smem_u32(wlo);
+    const uint32_t acc0 = tmem + (uint32_t)(b * 2 * N);
+    for (int kk = 0; kk < kTbKD / 16; ++kk) {
+      const uint32_t off = (uint32_t)kk * 32;
+      const uint32_t acc = kk > 0 ? 1u : 0u;
+      mma(acc0, smem_desc(b_ahi + off), smem_desc(b_whi + off), idesc, acc);
+      if (prec == DOA_BF16X3) {
+        mma(acc0, smem_desc(b_ahi + off), smem_desc(b_wlo + off), idesc, 1u);
+        mma(acc0, smem_desc(b_alo + off), smem_desc(b_whi + off), idesc, 1u);
+      } else {
+        mma(acc0 + (uint32_t)N, smem_desc(b_ahi + off), smem_desc(b_wlo + off), idesc, acc);
+        mma(acc0 + (uint32_t)N, smem_desc(b_alo + off), smem_desc(b_whi + off), idesc, 1u);
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(&sh.mbar[b]))
+                 : "memory");
+  };
 
   for (int64_t run = blockIdx.x; run * kTbRun < ntiles; run += gridDim.x) {
     const int64_t t_begin = run * kTbRun, t_end = min(ntiles, t_begin + kTbRun);
@@ -150,10 +229,11 @@ __global__ void __launch_bounds__(kTbThreads, 2) scan_tc_batch_kernel(const uint
       int mid = (u + hi + 1) >> 1;
       if (probs[list[mid]].tile_start <= t_begin) u = mid; else hi = mid - 1;
     }
-    for (int64_t t = t_begin; t < t_end; ++t) {
+    for (int64_t t = t_begin; t < t_end;) {
       while (u + 1 < nunits && probs[list[u + 1]].tile_start <= t) ++u;
+      const int64_t seg_end = (u + 1 < nunits) ? min(t_end, probs[list[u + 1]].tile_start) : t_end;
       if (u != cur) {
-        // ---- problem setup: FP32 factor, weights, thresholds, scaled split W
+        // ---- problem setup (no MMA in flight here): FP32 factor, weights, thresholds, split W
         pp = &probs[list[u]];
         g = &grids[pp->grid_id];
         j.F = reinterpret_cast<const double2 *>(ws + pp->fac_off);
@@ -174,7 +254,7 @@ __global__ void __launch_bounds__(kTbThreads, 2) scan_tc_batch_kernel(const uint
         MPs = (j.M + 15) / 16 * 16;
         N = (2 * j.Kf + 31) / 32 * 32;
         idesc = inst_desc(prec == DOA_FP16X3 ? 0 : 1, N);
-        __syncthreads();   // previous tile's readers of W / B32 are done
+        __syncthreads();
         if (tid == 0) sh.maxbits = 0;
         __syncthreads();
         float mx = 0.f;
@@ -182,8 +262,8 @@ __global__ void __launch_bounds__(kTbThreads, 2) scan_tc_batch_kernel(const uint
           const int k = e / MPs, m = e % MPs;
           float2 v = make_float2(0.f, 0.f);
           if (m < j.M) {
-            const double2 b = j.F[(size_t)k * j.M + m];
-            v = make_float2((float)b.x, (float)b.y);
+            const double2 bb = j.F[(size_t)k * j.M + m];
+            v = make_float2((float)bb.x, (float)bb.y);
           }
           B32[e] = v;
           mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
@@ -195,12 +275,14 @@ __global__ void __launch_bounds__(kTbThreads, 2) scan_tc_batch_kernel(const uint
         __syncthreads();
         if (warp == 0) {
           // E_r from s_k = sum_m |f_mk| (FP32 threshold), N2_r from ||f_k||^2 (tensor threshold)
+          const float gam = prec == DOA_FP16X3 ? 1.0e-6f : 8.0e-6f;
+          const float c = 2.8f * gam / 1.0e-3f;
           float em = 0.f, ee = 0.f, nm = 0.f, ne = 0.f;
           for (int k = lane; k < j.Kf; k += 32) {
             float n1 = 0.f, q2 = 0.f;
             for (int m = 0; m < j.M; ++m) {
-              const float2 b = B32[k * MPs + m];
-              const float a2 = b.x * b.x + b.y * b.y;
+              const float2 bb = B32[k * MPs + m];
+              const float a2 = bb.x * bb.x + bb.y * bb.y;
               q2 += a2;
               n1 += sqrtf(a2);
             }
@@ -211,8 +293,6 @@ __global__ void __launch_bounds__(kTbThreads, 2) scan_tc_batch_kernel(const uint
               nm += q2;
               ne += sh.w32[k] * q2;
             }
-            const float gam = prec == DOA_FP16X3 ? 1.0e-6f : 8.0e-6f;
-            const float c = 2.8f * gam / 1.0e-3f;
             if (k == j.kphd) {
               sh.thr32[kRoPhd] = kRefineC * e;
               sh.thrtc[kRoPhd] = c * c * q2;
@@ -230,8 +310,6 @@ __global__ void __launch_bounds__(kTbThreads, 2) scan_tc_batch_kernel(const uint
             ne += __shfl_xor_sync(0xffffffffu, ne, off);
           }
           if (lane == 0) {
-            const float gam = prec == DOA_FP16X3 ? 1.0e-6f : 8.0e-6f;
-            const float c = 2.8f * gam / 1.0e-3f;
             sh.thr32[kRoMusic] = kRefineC * em;
             sh.thr32[kRoEv] = kRefineC * ee;
             sh.thrtc[kRoMusic] = c * c * nm;
@@ -247,9 +325,9 @@ __global__ void __launch_bounds__(kTbThreads, 2) scan_tc_batch_kernel(const uint
           const int col = n >> 1, m = kap >> 1;
           float w = 0.f;
           if (col < j.Kf && m < j.M) {
-            const float2 b = B32[col * MPs + m];
+            const float2 bb = B32[col * MPs + m];
             const bool re_out = (n & 1) == 0, re_in = (kap & 1) == 0;
-            w = (re_out ? (re_in ? b.x : b.y) : (re_in ? -b.y : b.x)) * wscale;
+            w = (re_out ? (re_in ? bb.x : bb.y) : (re_in ? -bb.y : bb.x)) * wscale;
           }
           uint16_t hv, lv;
           split16(w, prec, hv, lv);
@@ -261,164 +339,111 @@ __global__ void __launch_bounds__(kTbThreads, 2) scan_tc_batch_kernel(const uint
         __syncthreads();
         cur = u;
       }
-      const int L = g->L;
-      const int k0 = (int)(t - pp->tile_start) * kTcRows;
-      const uint32_t *S = reinterpret_cast<const uint32_t *>(ws + g->S_off);
-      // ---- steering block: row pt, elements [part * MPs / 2, (part + 1) * MPs / 2), 4 per 16-byte
-      // chunk. Phasors of the chunk's first element from its exact phase, the other three as its
-      // product with a_1, a_2, a_3 (also exact-phase polynomials); (re, im) pairs are split with
-      // packed conversions straight into the 32-bit (re, im) halves of the swizzled row.
-      {
-        const int pt = tid >> 1, part = tid & 1;
-        const int k = k0 + pt;
-        const uint32_t Sk = k < L ? S[k] : 0u;
-        if (part == 0) sh.sk[pt] = Sk;
-        const int mh = MPs / 2, m0 = part * mh;
-        const float2 z1 = phasor_q32(Sk), z2 = phasor_q32(2u * Sk), z3 = phasor_q32(3u * Sk);
-        for (int c = 0; c < mh; c += 4) {
-          const float2 a0 = (m0 + c) == 0 ? make_float2(1.f, 0.f) : phasor_q32((uint32_t)(m0 + c) * Sk);
-          float2 v[4];
-          v[0] = a0;
-          v[1] = make_float2(fmaf(a0.x, z1.x, -a0.y * z1.y), fmaf(a0.x, z1.y, a0.y * z1.x));
-          v[2] = make_float2(fmaf(a0.x, z2.x, -a0.y * z2.y), fmaf(a0.x, z2.y, a0.y * z2.x));
-          v[3] = make_float2(fmaf(a0.x, z3.x, -a0.y * z3.y), fmaf(a0.x, z3.y, a0.y * z3.x));
-          uint32_t hw[4], lw[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (prec == DOA_FP16X3) {
-              const __half2 h2 = __floats2half2_rn(v[q].x, v[q].y);
-              const float2 b = __half22float2(h2);
-              const __half2 l2 = __floats2half2_rn((v[q].x - b.x) * 2048.0f, (v[q].y - b.y) * 2048.0f);
-              hw[q] = *reinterpret_cast<const uint32_t *>(&h2);
-              lw[q] = *reinterpret_cast<const uint32_t *>(&l2);
-            } else {
-              const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[q].x, v[q].y);
-              const float2 b = __bfloat1622float2(h2);
-              const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[q].x - b.x, v[q].y - b.y);
-              hw[q] = *reinterpret_cast<const uint32_t *>(&h2);
-              lw[q] = *reinterpret_cast<const uint32_t *>(&l2);
-            }
-          }
-          const uint32_t off = sw128(pt, 2 * (m0 + c));
-          *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-          *reinterpret_cast<uint4 *>(alo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-        }
-        for (int kap = 2 * MPs + part * 8; kap < kTbKD; kap += 16) {   // K padding
-          const uint32_t off = sw128(pt, kap);
-          *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(0, 0, 0, 0);
-          *reinterpret_cast<uint4 *>(alo + off) = make_uint4(0, 0, 0, 0);
-        }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      // ---- software pipeline over the segment's tiles: the steering block of tile i+1 is built
+      // and its MMAs issued while tile i's accumulator is read back and its readouts formed
+      gen(0, t);
       __syncthreads();
-      // ---- MMAs (one thread)
-      if (tid == 0 && ok) {
+      issue(0);
+      for (int64_t i = 0; t + i < seg_end; ++i) {
+        const int b = (int)(i & 1);
+        const bool has_next = t + i + 1 < seg_end;
+        if (has_next) gen(b ^ 1, t + i + 1);
+        const bool was_ok = ok;
+        const bool done = tid != 0 || (ok && mbar_wait(smem_u32(&sh.mbar[b]), phase[b]));
+        ok = __syncthreads_and(done && ok);
+        if (was_ok && !ok) {
+          pending = b;
+          pending_parity = phase[b];
+        }
+        phase[b] ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t b_ahi = smem_u32(ahi), b_alo = smem_u32(alo), b_whi = smem_u32(whi), b_wlo = smem_u32(wlo);
-        for (int kk = 0; kk < kTbKD / 16; ++kk) {
-          const uint32_t off = (uint32_t)kk * 32;
-          const uint32_t acc = kk > 0 ? 1u : 0u;
-          mma(tmem, smem_desc(b_ahi + off), smem_desc(b_whi + off), idesc, acc);
-          if (prec == DOA_BF16X3) {
-            mma(tmem, smem_desc(b_ahi + off), smem_desc(b_wlo + off), idesc, 1u);
-            mma(tmem, smem_desc(b_alo + off), smem_desc(b_whi + off), idesc, 1u);
-          } else {
-            mma(tmem + (uint32_t)N, smem_desc(b_ahi + off), smem_desc(b_wlo + off), idesc, acc);
-            mma(tmem + (uint32_t)N, smem_desc(b_alo + off), smem_desc(b_whi + off), idesc, 1u);
-          }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&sh.mbar))
-                     : "memory");
-      }
-      // one thread polls the mbarrier; the others wait at the barrier without taking issue slots
-      const bool was_ok = ok;
-      const bool done = tid != 0 || (ok && mbar_wait(smem_u32(&sh.mbar), iter & 1u));
-      ok = __syncthreads_and(done && ok);
-      if (was_ok && !ok) pending = (int)(iter & 1u);
-      ++iter;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // ---- epilogue: readout partial sums of each row over this warp's half of the columns
-      const int q = warp & 3, cs = warp >> 2;
-      const int row = q * 32 + lane;
-      float4 part = make_float4(0.f, 0.f, 0.f, 0.f);   // (MUSIC, EV, PHD, MN)
-      if (ok) {
-        const int half = N / 2;
-        for (int c0 = cs * half; c0 < (cs + 1) * half; c0 += 8) {
-          float v[8];
-          tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-          if (prec == DOA_FP16X3) {
-            float w[8];
-            tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(N + c0), w);
+        if (has_next) issue(b ^ 1);
+        // epilogue of tile t + i: readout partial sums of each row over this warp's column half
+        const int L = g->L;
+        const int k0 = (int)(t + i - pp->tile_start) * kTcRows;
+        const int q = warp & 3, cs = warp >> 2;
+        const int row = q * 32 + lane;
+        float4 part = make_float4(0.f, 0.f, 0.f, 0.f);   // (MUSIC, EV, PHD, MN)
+        if (ok) {
+          const int half = N / 2;
+          const uint32_t acc0 = tmem + (uint32_t)(b * 2 * N) + ((uint32_t)(q * 32) << 16);
+          for (int c0 = cs * half; c0 < (cs + 1) * half; c0 += 8) {
+            float v[8];
+            tmem_ld8(acc0 + (uint32_t)c0, v);
+            if (prec == DOA_FP16X3) {
+              float w[8];
+              tmem_ld8(acc0 + (uint32_t)(N + c0), w);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = fmaf(w[i], 4.8828125e-4f, v[i]);
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int col = c0 / 2 + i;
-            const float n = fmaf(v[2 * i], v[2 * i], v[2 * i + 1] * v[2 * i + 1]);
-            if (col < j.Kn) {
-              part.x += n;
-              part.y = fmaf(sh.w32[col], n, part.y);
+              for (int x = 0; x < 8; ++x) v[x] = fmaf(w[x], 4.8828125e-4f, v[x]);
             }
-            if (col == j.kphd) part.z = n;
-            if (col == j.kmn) part.w = n;
-          }
-        }
-      }
-      red[row * 2 + cs] = part;
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();
-      if (tid < kTcRows) {
-        const int k = k0 + tid;
-        if (k < L) {
-          if (!ok) {
-            const float nan = __int_as_float(0x7fc00000);   // timed-out tile: NaN marks it
-            for (int r = 0; r < 4; ++r)
-              if (j.P[r]) j.P[r][k] = nan;
-          } else {
-            const float4 a = red[tid * 2], b = red[tid * 2 + 1];
-            const float s2 = sh.scale2;
-            float den[4];
-            den[kRoMusic] = (a.x + b.x) * s2;
-            den[kRoEv] = (a.y + b.y) * s2;
-            den[kRoPhd] = (a.z + b.z) * s2;
-            den[kRoMn] = (a.w + b.w) * s2;
-            bool flag = false;
-            for (int r = 0; r < 4; ++r)
-              if (j.P[r]) {
-                j.P[r][k] = recip_out(den[r]);
-                flag = flag || den[r] < sh.thrtc[r];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+              const int col = c0 / 2 + x;
+              const float n = fmaf(v[2 * x], v[2 * x], v[2 * x + 1] * v[2 * x + 1]);
+              if (col < j.Kn) {
+                part.x += n;
+                part.y = fmaf(sh.w32[col], n, part.y);
               }
-            if (flag) sh.flags[atomicAdd(&sh.nflag, 1)] = k;
+              if (col == j.kphd) part.z = n;
+              if (col == j.kmn) part.w = n;
+            }
           }
         }
-      }
-      __syncthreads();
-      // ---- re-evaluation of the flagged points: FP32 by a warp, FP64 below the FP32 threshold
-      const int nf = sh.nflag;
-      for (int i = warp; i < nf; i += kTbWarps) {
-        const int k = sh.flags[i];
-        float d[4];
-        readouts32_warp(B32, MPs, j.M, j, sh.w32, sh.sk[k - k0], ph32, d);
-        bool need64 = false;
-        for (int r = 0; r < 4; ++r) need64 = need64 || (j.P[r] && d[r] < sh.thr32[r]);
-        if (need64) {
-          refine_point_warp(j, k, sh.w32, ph64, yb);
-        } else if (lane == 0) {
-          for (int r = 0; r < 4; ++r)
-            if (j.P[r]) j.P[r][k] = recip_out(d[r]);
+        red[row * 2 + cs] = part;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid < kTcRows) {
+          const int k = k0 + tid;
+          if (k < L) {
+            if (!ok) {
+              const float nan = __int_as_float(0x7fc00000);   // timed-out tile: NaN marks it
+              for (int r = 0; r < 4; ++r)
+                if (j.P[r]) j.P[r][k] = nan;
+            } else {
+              const float4 a = red[tid * 2], c2 = red[tid * 2 + 1];
+              const float s2 = sh.scale2;
+              float den[4];
+              den[kRoMusic] = (a.x + c2.x) * s2;
+              den[kRoEv] = (a.y + c2.y) * s2;
+              den[kRoPhd] = (a.z + c2.z) * s2;
+              den[kRoMn] = (a.w + c2.w) * s2;
+              bool flag = false;
+              for (int r = 0; r < 4; ++r)
+                if (j.P[r]) {
+                  j.P[r][k] = recip_out(den[r]);
+                  flag = flag || den[r] < sh.thrtc[r];
+                }
+              if (flag) sh.flags[atomicAdd(&sh.nflag, 1)] = k;
+            }
+          }
+        }
+        __syncthreads();
+        // re-evaluation of the flagged points: FP32 by a warp, FP64 below the FP32 threshold
+        const int nf = sh.nflag;
+        for (int f = warp; f < nf; f += kTbWarps) {
+          const int k = sh.flags[f];
+          float d[4];
+          readouts32_warp(B32, MPs, j.M, j, sh.w32, sh.sk[b * kTcRows + (k - k0)], ph32, d);
+          bool need64 = false;
+          for (int r = 0; r < 4; ++r) need64 = need64 || (j.P[r] && d[r] < sh.thr32[r]);
+          if (need64) {
+            refine_point_warp(j, k, sh.w32, ph64, yb);
+          } else if (lane == 0) {
+            for (int r = 0; r < 4; ++r)
+              if (j.P[r]) j.P[r][k] = recip_out(d[r]);
+          }
+        }
+        __syncthreads();
+        if (tid == 0) {
+          sh.nflag = 0;
+          if (!ok && status) status[list[u]] = DOA_ETIMEOUT;
         }
       }
-      __syncthreads();
-      if (tid == 0) {
-        sh.nflag = 0;
-        if (!ok && status) status[list[u]] = DOA_ETIMEOUT;
-      }
+      t = seg_end;
     }
   }
-  // a timed-out commit may still be in flight: give it one more bounded wait before freeing TMEM
-  if (pending >= 0) mbar_wait(smem_u32(&sh.mbar), (uint32_t)pending);
+  // a commit whose wait ran out may still land: one more bounded wait before TMEM is freed
+  if (pending >= 0) mbar_wait(smem_u32(&sh.mbar[pending]), pending_parity);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
@@ -444,7 +469,7 @@ cudaError_t launch_scan_tc_batch(const uint8_t *plan_dev, const PlanHeader &h, u
     if (g_tb_sms <= 0) g_tb_sms = 1;
   }
   const int64_t runs = (h.tc_tiles + kTbRun - 1) / kTbRun;
-  int64_t grid = (int64_t)g_tb_sms * 2;
+  int64_t grid = (int64_t)g_tb_sms * (h.tc_cols <= 256 ? 2 : 1);   // TMEM: 512 columns per SM
   if (grid > runs) grid = runs;
   scan_tc_batch_kernel<<<(unsigned)grid, kTbThreads, kTbSmem, s>>>(plan_dev, ws, status);
   return cudaGetLastError();

@@ -173,7 +173,7 @@ def test_batch_plan_tensor_scan_problems(libdoa):
     assert libdoa.lib().doa_batch_plan(arr, 3, None, buf.ctypes.data, n, ctypes.byref(ws), None) == 0
     h32 = buf[:512].view(np.int32)
     assert h32[67] == 2                       # tc_jobs
-    assert h32[68] == 128                     # TMEM columns: Kf = 13 -> N = 32 per accumulator; 27 -> 64 -> 128
+    assert h32[68] == 256                     # TMEM columns: 2 buffers x 2 accumulators x N (N = 64 for Kf = 28)
     assert list(h32[10:14]) == [1, 0, 0, 0]   # FP32 scan lists hold only the M = 8 problem
     for bad in (_prob(libdoa, M=33, prec=3), _prob(libdoa, M=16, prec=1), _prob(libdoa, M=16, prec=4)):
         arr = (libdoa.Problem * 1)(bad)
