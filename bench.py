@@ -441,8 +441,9 @@ def run_uneven(args):
     probs = []
     for i, s in enumerate(specs):
         X = Xd[int(offs[i]):int(offs[i]) + s.M * s.N].view(s.M, s.N)
+        prec = doa.FP16X3 if (args.tc_min_m and s.M >= args.tc_min_m and s.M <= 32) else doa.FP32
         probs.append(doa.make_problem(X, s.d, 1 << s.alg, doa.grid(LO, s.step, s.L), P[int(p_off[i]):int(p_off[i] + s.L)],
-                                      idx[i], val[i], cnt[i:i + 1]))
+                                      idx[i], val[i], cnt[i:i + 1], prec=prec))
     tune_log = []
     scan_pt, eig_mats = (autotune.tune(probs, device=str(dev), log=tune_log) if not args.no_tune
                          else (list(autotune.DEFAULT), [0, 0, 0, 0]))
@@ -520,7 +521,9 @@ def run_uneven(args):
         "config": {"workload": f"uneven batch: {len(specs)} problems, M in {{8,12,16,32}}, d in U{{1..M/2}}, "
                                f"N in U{{256..8192}}, step in {{0.1,0.01,0.001}} deg, one algorithm each",
                    "batch_per_gpu": len(specs), "points_per_gpu": int(Ls.sum()), "graph": True,
-                   "scan_pt": scan_pt, "eig_mats": plan.eig_mats, "l2": f"inputs {buf.nbytes / 1e9:.2f} GB > 129 MB L2 (no flush needed)",
+                   "scan_pt": scan_pt, "eig_mats": plan.eig_mats,
+                   "tensor_scan": (f"FP16x3 for M >= {args.tc_min_m}" if args.tc_min_m else "none"),
+                   "l2": f"inputs {buf.nbytes / 1e9:.2f} GB > 129 MB L2 (no flush needed)",
                    "parallelism": f"replicas x{world}"},
         "solves_per_s": len(specs) * world / (ms / 1e3),
         "gpu_launches": plan.launches() * args.steps,
@@ -796,6 +799,8 @@ def main():
     ap.add_argument("--train", type=int, default=1 << 20, help="learned workload: training instances")
     ap.add_argument("--epochs", type=int, default=12, help="learned workload: training epochs")
     ap.add_argument("--no-tune", action="store_true", help="uneven workload: default scan tiles")
+    ap.add_argument("--tc-min-m", type=int, default=0,
+                    help="uneven workload: problems with M >= this (<= 32) scan on the tensor cores (FP16x3)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
