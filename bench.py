@@ -372,10 +372,11 @@ def run_gpu(args):
     # FP64 Jacobi: time, stage times and the same parity check against the oracle
     if rank == 0 and world == 1 and not args.no_forms:
         forms = {}
-        for name, prec, eprec in (("fp16x3_scan", doa.FP16X3, doa.EIG_DOUBLE_FLOAT),
-                                  ("fp64_jacobi", doa.FP32, doa.EIG_FP64)):
-            fprobs = [doa.make_problem(X[i], D, 0xF, g, P[i], idx[i], val[i], cnt[i], prec=prec, eig_prec=eprec)
-                      for i in range(B)]
+        for name, prec, eprec, polish in (("fp16x3_scan", doa.FP16X3, doa.EIG_DOUBLE_FLOAT, False),
+                                          ("fp64_jacobi", doa.FP32, doa.EIG_FP64, False),
+                                          ("peak_polish", doa.FP32, doa.EIG_DOUBLE_FLOAT, True)):
+            fprobs = [doa.make_problem(X[i], D, 0xF, g, P[i], idx[i], val[i], cnt[i], prec=prec, eig_prec=eprec,
+                                       polish=polish) for i in range(B)]
             fplan = doa.BatchPlan(fprobs, device=str(dev))
             fws = doa.workspace(fplan, device=str(dev))
             for _ in range(args.warmup):

@@ -233,8 +233,13 @@ typedef struct {
   double *B_out;         /* nullable: copy of the factor B of the first algorithm in          */
                          /* alg_mask (M x K complex128, column-major, ld M)                   */
   int32_t eig_prec;      /* doa_eig_prec of the batch's Jacobi                                */
-  int32_t reserved;
+  int32_t flags;         /* DOA_FLAG_* bits                                                   */
 } doa_problem;
+
+/* Peak polish: after Step-6 the spectrum is re-evaluated in FP64 (steering and contraction) at
+ * the picked peaks and their two neighbours on each side, and the peaks are picked again, so a
+ * near tie between neighbouring grid points is decided as the FP64 spectrum decides it. */
+#define DOA_FLAG_POLISH_PEAKS 1
 
 /* Launch-shape knobs of a plan, per M bucket (M <= 8, <= 16, <= 32, <= 64); 0 = default. */
 typedef struct {

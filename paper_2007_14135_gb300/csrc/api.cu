@@ -46,6 +46,7 @@ bool problem_ok(const doa_problem &p) {
   if (!p.X || !aligned(p.X, 8) || !p.P || !aligned(p.P, 4)) return false;
   if (p.alg_mask == 0u || p.alg_mask > 15u) return false;
   if (p.eig_prec != DOA_EIG_DOUBLE_FLOAT && p.eig_prec != DOA_EIG_FP64) return false;
+  if (p.flags & ~DOA_FLAG_POLISH_PEAKS) return false;
   if (p.d > 0 && (!p.peak_idx || !p.peak_val)) return false;
   if (!p.peak_count) return false;
   // scan form: FP32 (CUDA cores) or split operands on the tensor cores (M <= 32)
@@ -355,6 +356,7 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     }
     q.njobs = slot;
     factor_layout(p, q);
+    if (p.flags & DOA_FLAG_POLISH_PEAKS) ++h.npolish;
     q.fac_off = ws;
     ws = round_up(ws + factor_bytes(M), 256);
     if (p.prec == DOA_FP32) {
@@ -399,6 +401,9 @@ doa_status doa_solve_batch(const void *plan_host, const void *plan_dev, void *ws
   if (!mark(3) || launch_scan_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
   if (h.tc_jobs > 0 && launch_scan_tc_batch(pd, h, w, status, s) != cudaSuccess) return DOA_ECUDA;
   if (!mark(4) || launch_peaks_batch(pd, h, s) != cudaSuccess) return DOA_ECUDA;
+  if (h.npolish > 0 &&
+      (launch_polish_batch(pd, h, w, s) != cudaSuccess || launch_peaks_batch(pd, h, s) != cudaSuccess))
+    return DOA_ECUDA;
   if (!mark(5)) return DOA_ECUDA;
   return DOA_OK;
 }

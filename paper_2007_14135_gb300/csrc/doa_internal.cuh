@@ -199,14 +199,18 @@ struct PlanHeader {
   int32_t tc_cols;                       // TMEM columns a CTA allocates (covers every tc problem)
   int64_t tc_tiles;                      // 128-point tiles over all tc problems
   int64_t off_tc;                        // byte offset of the tc problem list
+  int32_t npolish;                       // problems with DOA_FLAG_POLISH_PEAKS
+  int32_t pad2;
 };
 
-// The Python binding reads these header fields by position (int32 index 22 = scan_pt, 58 = eig_mats).
+// The Python binding reads these header fields by position (int32 index 22 = scan_pt, 58 = eig_mats,
+// 62 = cov_first, 67 = tc_jobs, 74 = npolish).
 static_assert(offsetof(PlanHeader, scan_pt) == 88, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, scan_tiles) == 56, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, eig_mats) == 232, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, cov_first) == 248, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, tc_jobs) == 268, "PlanHeader layout changed");
+static_assert(offsetof(PlanHeader, npolish) == 296, "PlanHeader layout changed");
 
 // Scan tiles: kScanThreads threads, each evaluating PT consecutive grid points (tile shape
 // 128 x PT). PT is chosen per M bucket (the autotuner's knob); the register budget limits it
@@ -269,6 +273,7 @@ cudaError_t launch_scan_tc_single(const double2 *B, int M, int K, int L, double 
 cudaError_t launch_peaks_single(const float *P, int L, int d, int *idx, float *val, int *count,
                                 cudaStream_t s);
 cudaError_t launch_peaks_batch(const uint8_t *plan_dev, const PlanHeader &h, cudaStream_t s);
+cudaError_t launch_polish_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
 cudaError_t launch_slice_peaks(const float *Pbuf, int b0, int k0, int k1, int L, int d, doa_slice_summary *out,
                                cudaStream_t s);
 

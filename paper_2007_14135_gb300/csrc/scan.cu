@@ -137,6 +137,49 @@ __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t 
   }
 }
 
+// Peak polish (DOA_FLAG_POLISH_PEAKS): one warp per (problem, algorithm) job re-evaluates, with
+// the FP64 steering and contraction of refine_point_warp, every readout of the problem at the
+// job's picked peaks and their two neighbours on each side; the peaks are then picked again.
+constexpr int kPolishWarps = 4;
+
+__global__ void __launch_bounds__(32 * kPolishWarps) polish_batch_kernel(const uint8_t *plan, uint8_t *ws) {
+  __shared__ double2 ph[kPolishWarps][kMaxM];
+  __shared__ float2 yb[kPolishWarps][kMaxCols];
+  __shared__ float w32[kPolishWarps][kMaxM];
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int job = blockIdx.x * kPolishWarps + warp;
+  if (job >= h->njobs) return;
+  const PlanJob &jb = reinterpret_cast<const PlanJob *>(plan + h->off_job)[job];
+  const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[jb.prob];
+  if (!(pp.p.flags & DOA_FLAG_POLISH_PEAKS) || pp.p.d < 1) return;
+  const PlanGrid &g = reinterpret_cast<const PlanGrid *>(plan + h->off_grid)[pp.grid_id];
+  ScanJob j{};
+  j.F = reinterpret_cast<const double2 *>(ws + pp.fac_off);
+  j.w = pp.Kn > 0 && pp.slot[DOA_EV] >= 0
+            ? reinterpret_cast<const double *>(ws + pp.fac_off) + 2 * pp.p.M * (pp.p.M + 1)
+            : nullptr;
+  j.S64 = reinterpret_cast<const uint64_t *>(ws + g.S64_off);
+  for (int r = 0; r < 4; ++r) j.P[r] = pp.slot[r] >= 0 ? pp.p.P + (size_t)pp.slot[r] * g.L : nullptr;
+  j.lo = g.lo;
+  j.step = g.step;
+  j.M = pp.p.M;
+  j.Kf = pp.Kf;
+  j.Kn = pp.Kn;
+  j.kphd = pp.kphd;
+  j.kmn = pp.kmn;
+  j.kofs = 0;
+  for (int c = lane; c < j.Kn; c += 32) w32[warp][c] = j.w ? (float)j.w[c] : 1.f;
+  __syncwarp();
+  const int d = pp.p.d, L = g.L;
+  const int n = pp.p.peak_count[jb.slot];
+  const int32_t *idx = pp.p.peak_idx + (size_t)jb.slot * d;
+  for (int q = 0; q < n && q < d; ++q) {
+    const int k0 = idx[q];
+    for (int k = max(k0 - 2, 0); k <= min(k0 + 2, L - 1); ++k) refine_point_warp(j, k, w32[warp], ph[warp], yb[warp]);
+  }
+}
+
 int g_num_sms = 0;
 
 int num_sms() {
@@ -190,6 +233,12 @@ cudaError_t launch_scan_single(const double2 *B, int M, int K, int L, double lo,
     case 2: scan_single_kernel<32, 1><<<grid, kScanThreads, 0, s>>>(B, M, K, L, lo, step, kofs, S, P); break;
     default: scan_single_kernel<64, 1><<<grid, kScanThreads, 0, s>>>(B, M, K, L, lo, step, kofs, S, P); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_polish_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s) {
+  if (h.njobs == 0) return cudaSuccess;
+  polish_batch_kernel<<<(h.njobs + kPolishWarps - 1) / kPolishWarps, 32 * kPolishWarps, 0, s>>>(plan_dev, ws);
   return cudaGetLastError();
 }
 

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libdoa.so")
 PHD, MUSIC, EV, MN = 0, 1, 2, 3
 FP32, BF16, BF16X3, FP16X3 = 0, 1, 2, 3
 EIG_DOUBLE_FLOAT, EIG_FP64 = 0, 1
+FLAG_POLISH_PEAKS = 1
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ERANK, ENONFINITE, ETIMEOUT = range(8)
 NOALLOC_SCRATCH_BYTES = 4 << 20
 BATCH_STAGES = 5
@@ -49,7 +50,7 @@ class Problem(ctypes.Structure):
                 ("evals", ctypes.c_void_p), ("grid", Grid), ("M", ctypes.c_int32),
                 ("N", ctypes.c_int32), ("ldx", ctypes.c_int32), ("d", ctypes.c_int32),
                 ("alg_mask", ctypes.c_uint32), ("prec", ctypes.c_int32), ("features", ctypes.c_void_p),
-                ("B_out", ctypes.c_void_p), ("eig_prec", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("B_out", ctypes.c_void_p), ("eig_prec", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class SliceSummary(ctypes.Structure):
@@ -200,12 +201,13 @@ def doa_peaks(P: torch.Tensor, d: int, idx: torch.Tensor, val: torch.Tensor, cou
 def make_problem(X: torch.Tensor, d: int, alg_mask: int, g: Grid, P: torch.Tensor, peak_idx: torch.Tensor,
                  peak_val: torch.Tensor, peak_count: torch.Tensor, evals: Optional[torch.Tensor] = None,
                  prec: int = FP32, features: Optional[torch.Tensor] = None,
-                 B_out: Optional[torch.Tensor] = None, eig_prec: int = 0) -> Problem:
+                 B_out: Optional[torch.Tensor] = None, eig_prec: int = 0, polish: bool = False) -> Problem:
     """Descriptor of one problem; the tensors must outlive every solve that uses it."""
     assert X.dtype == torch.complex64 and X.dim() == 2 and X.stride(1) == 1
     M, N = X.shape
     return Problem(_dev(X), _dev(P), _dev(peak_idx), _dev(peak_val), _dev(peak_count), _dev(evals), g,
-                   M, N, X.stride(0), d, alg_mask, prec, _dev(features), _dev(B_out), eig_prec, 0)
+                   M, N, X.stride(0), d, alg_mask, prec, _dev(features), _dev(B_out), eig_prec,
+                   FLAG_POLISH_PEAKS if polish else 0)
 
 
 class Tuning(ctypes.Structure):
@@ -248,15 +250,19 @@ class BatchPlan:
     def header_index(field: str) -> int:
         """int32 index of a PlanHeader field (layout of csrc/doa_internal.cuh)."""
         order = {"magic": 0, "nprob": 1, "njobs": 2, "ngrids": 3, "ncov": 4, "nreduce": 5, "eig_count": 6,
-                 "scan_jobs": 10, "scan_tiles": 14, "scan_pt": 22, "eig_mats": 58}
+                 "scan_jobs": 10, "scan_tiles": 14, "scan_pt": 22, "eig_mats": 58, "cov_first": 62, "tc_jobs": 67,
+                 "npolish": 74}
         return order[field]
 
     def launches(self) -> int:
         """Kernels one doa_solve_batch of this plan launches."""
-        h = self.host[:256].view(np.int32)
+        h = self.host[:512].view(np.int32)
+        cf = [int(v) for v in h[62:67]]                       # cov_first: classes MB = 2, 3, 4, other
+        cov = sum(2 for c in range(3) if cf[c + 1] > cf[c]) + int(cf[4] > cf[3]) + int(h[5] > 0)
         eig_b = sum(int(c) > 0 for c in h[6:10])
-        scan_b = sum(int(c) > 0 for c in h[10:14])
-        return 1 + 1 + int(h[5] > 0) + eig_b + scan_b + 1
+        scan_b = sum(int(c) > 0 for c in h[10:14]) + int(h[67] > 0)
+        peaks = 1 + (2 if int(h[74]) > 0 else 0)
+        return 1 + cov + eig_b + scan_b + peaks
 
 
 def doa_solve_batch(plan: BatchPlan, ws: torch.Tensor, status: torch.Tensor, stage_events=None,

@@ -194,7 +194,7 @@ def test_single_calls_c1(env):
         assert idx.tolist() == ref["idx"].tolist()
 
 
-def _batch_solve(torch, doa, insts, masks, prec=0, eig_prec=0):
+def _batch_solve(torch, doa, insts, masks, prec=0, eig_prec=0, polish=False):
     tensors, probs = [], []
     for inst, mask in zip(insts, masks):
         nalg = bin(mask).count("1")
@@ -206,7 +206,7 @@ def _batch_solve(torch, doa, insts, masks, prec=0, eig_prec=0):
         ev = torch.empty(inst.M, dtype=torch.float64, device="cuda")
         tensors.append((X, P, idx, val, cnt, ev))
         probs.append(doa.make_problem(X, inst.d, mask, doa.grid(inst.lo, inst.step, inst.L), P, idx, val, cnt, ev,
-                                      prec=prec, eig_prec=eig_prec))
+                                      prec=prec, eig_prec=eig_prec, polish=polish))
     plan = doa.BatchPlan(probs)
     ws = doa.workspace(plan)
     status = torch.full((len(insts),), -1, dtype=torch.int32, device="cuda")
@@ -351,6 +351,28 @@ def test_batch_fp64_jacobi(env):
     b, _ = _batch_solve(torch, doa, insts, masks, eig_prec=0)
     for ta, tb in zip(a, b):
         assert db_error(ta[1].cpu().numpy(), tb[1].cpu().numpy().astype(np.float64)) < 1e-3
+
+
+def test_batch_peak_polish(env):
+    """With DOA_FLAG_POLISH_PEAKS the points around every picked peak carry FP64-accurate values,
+    so the peak indices equal the oracle's up to ties below float resolution (1e-6 relative)."""
+    torch, doa = env
+    insts = [synth.paper_density(i) for i in range(12)]
+    masks = [0xF] * len(insts)
+    tensors, status = _batch_solve(torch, doa, insts, masks, polish=True)
+    assert np.all(status == 0)
+    for inst, t in zip(insts, tensors):
+        P = t[1].cpu().numpy().reshape(-1, inst.L)
+        idx = t[2].cpu().numpy().reshape(-1, inst.d)
+        cnt = t[4].cpu().numpy()
+        for alg in range(4):
+            ref = oracle.solve(inst.X, inst.d, alg, inst.lo, inst.step, inst.L)
+            assert db_error(P[alg], ref["P"]) < DB_TOL
+            ok, ties = compare_peaks(idx[alg][:cnt[alg]], ref["idx"], ref["P"], 1e-6)
+            assert ok, (inst.seed, alg, ties)
+            for k in idx[alg][:cnt[alg]]:   # polished points: FP64 values rounded once to float
+                for q in range(max(k - 2, 0), min(k + 3, inst.L)):
+                    assert abs(P[alg][q] / ref["P"][q] - 1.0) < 2e-7
 
 
 def test_batch_edge_shapes(env):
