@@ -137,21 +137,23 @@ __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t 
   }
 }
 
-// Peak polish (DOA_FLAG_POLISH_PEAKS): one warp per (problem, algorithm) job re-evaluates, with
-// the FP64 steering and contraction of refine_point_warp, every readout of the problem at the
-// job's picked peaks and their two neighbours on each side; the peaks are then picked again.
+// Peak polish (DOA_FLAG_POLISH_PEAKS): one warp per problem re-evaluates, with the FP64
+// steering and contraction of refine_point_warp, every readout of the problem at the union of
+// its algorithms' picked peaks and their two neighbours on each side (each point once); the
+// peaks are then picked again.
 constexpr int kPolishWarps = 4;
+constexpr int kPolishMax = 4 * kMaxM;
 
 __global__ void __launch_bounds__(32 * kPolishWarps) polish_batch_kernel(const uint8_t *plan, uint8_t *ws) {
   __shared__ double2 ph[kPolishWarps][kMaxM];
   __shared__ float2 yb[kPolishWarps][kMaxCols];
   __shared__ float w32[kPolishWarps][kMaxM];
+  __shared__ int pk[kPolishWarps][kPolishMax];
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int job = blockIdx.x * kPolishWarps + warp;
-  if (job >= h->njobs) return;
-  const PlanJob &jb = reinterpret_cast<const PlanJob *>(plan + h->off_job)[job];
-  const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[jb.prob];
+  const int prob = blockIdx.x * kPolishWarps + warp;
+  if (prob >= h->nprob) return;
+  const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[prob];
   if (!(pp.p.flags & DOA_FLAG_POLISH_PEAKS) || pp.p.d < 1) return;
   const PlanGrid &g = reinterpret_cast<const PlanGrid *>(plan + h->off_grid)[pp.grid_id];
   ScanJob j{};
@@ -170,13 +172,31 @@ __global__ void __launch_bounds__(32 * kPolishWarps) polish_batch_kernel(const u
   j.kmn = pp.kmn;
   j.kofs = 0;
   for (int c = lane; c < j.Kn; c += 32) w32[warp][c] = j.w ? (float)j.w[c] : 1.f;
-  __syncwarp();
   const int d = pp.p.d, L = g.L;
-  const int n = pp.p.peak_count[jb.slot];
-  const int32_t *idx = pp.p.peak_idx + (size_t)jb.slot * d;
-  for (int q = 0; q < n && q < d; ++q) {
-    const int k0 = idx[q];
-    for (int k = max(k0 - 2, 0); k <= min(k0 + 2, L - 1); ++k) refine_point_warp(j, k, w32[warp], ph[warp], yb[warp]);
+  int n = 0;
+  if (lane == 0) {   // the algorithms' peaks, sorted, each once
+    for (int s = 0; s < pp.njobs; ++s) {
+      const int cnt = min(pp.p.peak_count[s], d);
+      for (int q = 0; q < cnt; ++q) {
+        const int k = pp.p.peak_idx[(size_t)s * d + q];
+        int a = n;
+        while (a > 0 && pk[warp][a - 1] > k) --a;
+        if (a > 0 && pk[warp][a - 1] == k) continue;
+        for (int b = n; b > a; --b) pk[warp][b] = pk[warp][b - 1];
+        pk[warp][a] = k;
+        ++n;
+      }
+    }
+  }
+  n = __shfl_sync(0xffffffffu, n, 0);
+  __syncwarp();
+  int last = -1;
+  for (int i = 0; i < n; ++i) {
+    const int k0 = pk[warp][i];
+    for (int k = max(max(k0 - 2, last + 1), 0); k <= min(k0 + 2, L - 1); ++k) {
+      refine_point_warp(j, k, w32[warp], ph[warp], yb[warp]);
+      last = k;
+    }
   }
 }
 
@@ -237,8 +257,8 @@ cudaError_t launch_scan_single(const double2 *B, int M, int K, int L, double lo,
 }
 
 cudaError_t launch_polish_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s) {
-  if (h.njobs == 0) return cudaSuccess;
-  polish_batch_kernel<<<(h.njobs + kPolishWarps - 1) / kPolishWarps, 32 * kPolishWarps, 0, s>>>(plan_dev, ws);
+  if (h.nprob == 0) return cudaSuccess;
+  polish_batch_kernel<<<(h.nprob + kPolishWarps - 1) / kPolishWarps, 32 * kPolishWarps, 0, s>>>(plan_dev, ws);
   return cudaGetLastError();
 }
 
