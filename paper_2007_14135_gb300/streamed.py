@@ -19,7 +19,7 @@ from . import doa
 
 class StreamedBatch:
     def __init__(self, M: int, N: int, d: int, alg_mask: int, grid: doa.Grid, chunk: int, device: str = "cuda",
-                 tuning_scan_pt=None, tuning_eig_mats=None):
+                 tuning_scan_pt=None, tuning_eig_mats=None, polish: bool = False):
         self.M, self.N, self.d, self.mask, self.grid, self.chunk = M, N, d, alg_mask, grid, chunk
         self.nalg = bin(alg_mask).count("1")
         self.dev = torch.device(device)
@@ -35,7 +35,7 @@ class StreamedBatch:
                 "status": torch.empty(chunk, dtype=torch.int32, device=self.dev),
             }
             s["probs"] = [doa.make_problem(s["X"][i], d, alg_mask, grid, s["P"][i], s["idx"][i], s["val"][i],
-                                           s["cnt"][i]) for i in range(chunk)]
+                                           s["cnt"][i], polish=polish) for i in range(chunk)]
             s["plan"] = doa.BatchPlan(s["probs"], device=str(self.dev), scan_pt=tuning_scan_pt,
                                       eig_mats=tuning_eig_mats)
             s["ws"] = doa.workspace(s["plan"], device=str(self.dev))
