@@ -301,6 +301,10 @@ def run_gpu(args):
     solves = B * nalg * world
     value = points / (ms / 1e3)
 
+    # ---- measured FMA issue rates (context for the derived ALU peak below)
+    fp32_meas = doa.probe_fma_tflops(False, device=str(dev))
+    fp64_meas = doa.probe_fma_tflops(True, device=str(dev), iters=1 << 10)
+
     # ---- roofline of the dominant stage
     peaks_json = load_peaks()
     hbm_peak = peaks_json.get("hbm_gbs", 6800.0)
@@ -350,6 +354,8 @@ def run_gpu(args):
         "gpu_launches": launches_per_step * args.steps,
         "stages": stage_info,
         "roofline": roof,
+        "alu_peaks_measured": {"fp32_fma_tflops": round(fp32_meas, 2), "fp64_fma_tflops": round(fp64_meas, 3),
+                               "how": "doa_probe_fma: 8 independent FMA chains per thread on every SM, best of 5"},
         "e2e": {"value": points / (e2e_ms / 1e3), "unit": "points/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                 "how": f"pinned host X to device in {B // chunk} chunks of {chunk} problems, uploads and "

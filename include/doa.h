@@ -150,6 +150,18 @@ doa_status doa_scan(const double *B, int M, int K, doa_grid grid, int prec, floa
 doa_status doa_peaks(const float *P, int L, int d, int *idx, float *val, int *count, void *stream);
 
 /* ----------------------------------------------------------------------------------------- */
+/* Measurement utility (not in the paper)                                                      */
+/* ----------------------------------------------------------------------------------------- */
+
+/*
+ * FMA issue-rate probe: `blocks` CTAs of 256 threads, each thread 8 independent chains of `iters`
+ * dependent FMAs in FP32 (fp64 = 0) or FP64 (fp64 = 1); *flops (host) receives the flop count of
+ * the launch (2 per FMA). out: device buffer of blocks x 256 floats / doubles (the chain sums).
+ * The caller times the launch (events on `stream`) to get FLOP/s.
+ */
+doa_status doa_probe_fma(int fp64, int blocks, int iters, void *out, double *flops, void *stream);
+
+/* ----------------------------------------------------------------------------------------- */
 /* Grid slices (not in the paper): one spectrum split into contiguous slices of the angle grid, */
 /* e.g. one slice per GPU, with B replicated. The slice scan computes exactly the points the    */
 /* full scan computes; the slice peak summary plus a host merge of the summaries of all slices  */

@@ -29,7 +29,7 @@ STAGE_NAMES = ("phase_tables", "covariance", "eig_noise_subspace", "scan", "peak
 EXPORTS = ("doa_status_str", "doa_covariance", "doa_covariance_noalloc", "doa_noise_subspace", "doa_scan",
            "doa_peaks", "doa_batch_plan_bytes", "doa_batch_plan", "doa_solve_batch", "doa_mlp_workspace_bytes",
            "doa_mlp_refresh", "doa_mlp_forward", "doa_mlp_backward", "doa_mlp_adam", "doa_synth_ula",
-           "doa_proposal_windows", "doa_scan_windows", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices")
+           "doa_proposal_windows", "doa_scan_windows", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices", "doa_probe_fma")
 SLICE_MAXD = 64
 
 
@@ -80,8 +80,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.doa_scan_slice.argtypes = [vp, i, i, Grid, i, i, vp, vp]
     lib.doa_slice_peaks.argtypes = [vp, i, i, i, i, i, vp, vp]
     lib.doa_merge_slices.argtypes = [vp, i, i, vp, vp, vp]
+    lib.doa_probe_fma.argtypes = [i, i, i, vp, ctypes.POINTER(ctypes.c_double), vp]
     for name in ("doa_covariance", "doa_covariance_noalloc", "doa_noise_subspace", "doa_scan", "doa_peaks",
-                 "doa_batch_plan", "doa_solve_batch", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices"):
+                 "doa_batch_plan", "doa_solve_batch", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices", "doa_probe_fma"):
         getattr(lib, name).restype = i
     return lib
 
@@ -189,6 +190,24 @@ def doa_merge_slices(sums: Sequence[SliceSummary], d: int):
            "doa_merge_slices")
     n = cnt.value
     return np.array(idx[:n], dtype=np.int32), np.array(val[:n], dtype=np.float32)
+
+
+def probe_fma_tflops(fp64: bool, device: str = "cuda", iters: int = 1 << 14, reps: int = 5) -> float:
+    """Measured FMA issue rate (TFLOP/s, best of `reps`) of FP32 or FP64 chains on every SM."""
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    blocks = sms * 8
+    out = torch.empty(blocks * 256, dtype=torch.float64 if fp64 else torch.float32, device=device)
+    flops = ctypes.c_double(0.0)
+    best = 0.0
+    for _ in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _check(lib().doa_probe_fma(1 if fp64 else 0, blocks, iters, _dev(out), ctypes.byref(flops), _stream(None)),
+               "doa_probe_fma")
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, flops.value / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return best
 
 
 def doa_peaks(P: torch.Tensor, d: int, idx: torch.Tensor, val: torch.Tensor, count: torch.Tensor,
