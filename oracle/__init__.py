@@ -14,6 +14,9 @@ compiles it with gcc on first use and exposes NumPy-friendly wrappers:
   scan        -- Table 2 Step-5 with the steering vector of Eq. 2 (half-wavelength ULA)
   peaks       -- Table 2 Step-6
   solve       -- Steps 1-6 for one snapshot matrix and one algorithm
+  scan_geometry / peaks2d / solve_geometry
+              -- Steps 5-6 (and 1-6) for an arbitrary array geometry on an azimuth x elevation grid,
+                 steering vector of Eq. 2 as printed (Sec. 4.2's circular array)
 
 The MLP oracle used for the learned proposal lives in ``oracle/mlp.py`` (NumPy, FP64).
 """
@@ -66,6 +69,10 @@ def _load():
             lib.oracle_peaks.restype = i
             lib.oracle_solve.argtypes = [p, i, i, i, i, i, d, d, i, p, p, p, p, p]
             lib.oracle_solve.restype = i
+            lib.oracle_scan_geometry.argtypes = [p, i, p, d, d, i, d, d, i, p]
+            lib.oracle_scan_geometry.restype = None
+            lib.oracle_peaks2d.argtypes = [p, i, i, i, i, p, p]
+            lib.oracle_peaks2d.restype = i
             _lib = lib
     return _lib
 
@@ -151,3 +158,62 @@ def solve(X: np.ndarray, D: int, alg: int, lo: float, step: float, L: int):
     status = -r if r < 0 else 0
     n = r if r >= 0 else 0
     return dict(P=P, evals=ev, C=C, idx=idx[:n].copy(), val=val[:n].copy(), status=status)
+
+
+def uca_positions(M: int, radius_wl: float) -> np.ndarray:
+    """Element positions (x, y, z) in wavelengths of an M-element uniform circular array of the
+    given radius in the z = 0 plane, element m at angle 2 pi m / M from the +y axis towards +x
+    (so that its azimuth matches the theta of Eq. 2). Returns float64 (M, 3)."""
+    ang = 2.0 * np.pi * np.arange(M, dtype=np.float64) / M
+    pos = np.zeros((M, 3), dtype=np.float64)
+    pos[:, 0] = radius_wl * np.sin(ang)
+    pos[:, 1] = radius_wl * np.cos(ang)
+    return pos
+
+
+def steering_geometry(pos: np.ndarray, theta_deg: float, phi_deg: float) -> np.ndarray:
+    """Eq. 2 steering vector for positions in wavelengths (the same formula as the C scan, in
+    NumPy, used to synthesise exact covariances in the tests)."""
+    t, p = np.deg2rad(theta_deg), np.deg2rad(phi_deg)
+    u = np.array([np.sin(t) * np.sin(p), np.cos(t) * np.sin(p), np.cos(p)])
+    return np.exp(2j * np.pi * (np.asarray(pos, dtype=np.float64) @ u))
+
+
+def scan_geometry(C: np.ndarray, pos: np.ndarray, az_lo: float, az_step: float, La: int,
+                  el_lo: float, el_step: float, Le: int) -> np.ndarray:
+    """P[l, k] = 1 / (a^H C a) at azimuth az_lo + k az_step, elevation el_lo + l el_step (degrees),
+    steering of Eq. 2 for the element positions pos (M x 3, wavelengths). Returns float64 (Le, La)."""
+    C = np.ascontiguousarray(C, dtype=np.complex128)
+    M = C.shape[0]
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(M, 3)
+    P = np.empty((Le, La), dtype=np.float64)
+    _load().oracle_scan_geometry(_ptr(C), M, _ptr(pos), float(az_lo), float(az_step), int(La), float(el_lo),
+                                 float(el_step), int(Le), _ptr(P))
+    return P
+
+
+def peaks2d(P: np.ndarray, D: int, wrap_az: bool):
+    """Strict 8-neighbour maxima of an (Le, La) spectrum (azimuth wraps when wrap_az), the D largest
+    (ties: lower flat index), returned as flat indices l*La + k in ascending order with values."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    Le, La = P.shape
+    idx = np.empty(max(D, 1), dtype=np.int32)
+    val = np.empty(max(D, 1), dtype=np.float64)
+    n = _load().oracle_peaks2d(_ptr(P), La, Le, int(bool(wrap_az)), D, _ptr(idx), _ptr(val))
+    return idx[:n].copy(), val[:n].copy()
+
+
+def solve_geometry(X: np.ndarray, D: int, alg: int, pos: np.ndarray, az_lo: float, az_step: float, La: int,
+                   el_lo: float, el_step: float, Le: int, wrap_az: bool):
+    """Steps 1-6 on an azimuth x elevation grid for an arbitrary geometry. Returns dict(P, evals, C,
+    idx, val, status) with P of shape (Le, La) and idx flat indices."""
+    R = covariance(X)
+    ev, V, sweeps = eigh(R)
+    if sweeps < 0:
+        return dict(P=None, evals=ev, C=None, idx=np.empty(0, np.int32), val=np.empty(0), status=4)
+    C, st = weighting(ev, V, D, alg)
+    if st != 0:
+        return dict(P=None, evals=ev, C=C, idx=np.empty(0, np.int32), val=np.empty(0), status=st)
+    P = scan_geometry(C, pos, az_lo, az_step, La, el_lo, el_step, Le)
+    idx, val = peaks2d(P, D, wrap_az)
+    return dict(P=P, evals=ev, C=C, idx=idx, val=val, status=0)

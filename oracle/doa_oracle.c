@@ -357,3 +357,103 @@ int oracle_solve(const float *X, int M, int N, int ldx, int D, int alg, double l
   free(R);
   return status ? -status : count;
 }
+
+/* ---------------------------------------------------------------------------------------------
+ * Step-5 for an arbitrary array geometry on an azimuth x elevation grid (Eq. 2 as printed):
+ *   a_m(theta, phi) = exp{ j 2 pi / lambda (x_m sin theta sin phi + y_m cos theta sin phi
+ *                                           + z_m cos phi) },
+ * theta = azimuth, phi = elevation, both in degrees; pos holds (x_m, y_m, z_m) in wavelengths.
+ * Grid: theta_k = az_lo + k az_step (k < La), phi_l = el_lo + l el_step (l < Le); P is Le x La
+ * row-major (row l = one azimuth sweep at elevation phi_l). invP = a^H C a with the explicit C.
+ * ------------------------------------------------------------------------------------------- */
+void oracle_scan_geometry(const double *C, int M, const double *pos, double az_lo, double az_step, int La,
+                          double el_lo, double el_step, int Le, double *P) {
+  double complex *Cm = (double complex *)malloc(sizeof(double complex) * M * M);
+  double complex *a = (double complex *)malloc(sizeof(double complex) * M);
+  for (int i = 0; i < M * M; ++i) Cm[i] = C[2 * i] + I * C[2 * i + 1];
+  for (int l = 0; l < Le; ++l) {
+    double lstep = (double)l * el_step;
+    double phi = (el_lo + lstep) * (ORACLE_PI / 180.0);
+    for (int k = 0; k < La; ++k) {
+      double kstep = (double)k * az_step;
+      double theta = (az_lo + kstep) * (ORACLE_PI / 180.0);
+      double u = sin(theta) * sin(phi), v = cos(theta) * sin(phi), w = cos(phi);
+      for (int m = 0; m < M; ++m) {
+        double t = pos[3 * m] * u + pos[3 * m + 1] * v + pos[3 * m + 2] * w;
+        double phase = 2.0 * ORACLE_PI * t;
+        a[m] = cos(phase) + I * sin(phase);
+      }
+      double complex invP = 0.0;
+      for (int i = 0; i < M; ++i) {
+        double complex row = 0.0;
+        for (int j = 0; j < M; ++j) row += Cm[i * M + j] * a[j];
+        invP += conj(a[i]) * row;
+      }
+      double re = creal(invP);
+      P[(size_t)l * La + k] = (re > 0.0) ? 1.0 / re : INFINITY;
+    }
+  }
+  free(a);
+  free(Cm);
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Step-6 on an Le x La azimuth-elevation spectrum (row-major, row = elevation). A peak is a point
+ * strictly larger than every one of its 8 neighbours; in azimuth the neighbours wrap around when
+ * wrap_az != 0 (the azimuth grid closes the circle), in elevation rows outside the grid do not
+ * exist. The D largest (equal values: lower flat index l*La + k first) are returned as flat
+ * indices in ascending order. Returns the count (<= D).
+ * ------------------------------------------------------------------------------------------- */
+int oracle_peaks2d(const double *P, int La, int Le, int wrap_az, int D, int *idx, double *val) {
+  int cap = 0, n = 0;
+  int *cand = NULL;
+  for (int l = 0; l < Le; ++l)
+    for (int k = 0; k < La; ++k) {
+      double v = P[(size_t)l * La + k];
+      int peak = 1, nbrs = 0;
+      for (int dl = -1; dl <= 1 && peak; ++dl)
+        for (int dk = -1; dk <= 1 && peak; ++dk) {
+          if (dl == 0 && dk == 0) continue;
+          int ll = l + dl, kk = k + dk;
+          if (ll < 0 || ll >= Le) continue;
+          if (kk < 0 || kk >= La) {
+            if (!wrap_az) continue;
+            kk = (kk + La) % La;
+          }
+          ++nbrs;
+          if (!(P[(size_t)ll * La + kk] < v)) peak = 0;
+        }
+      if (peak && nbrs > 0) {
+        if (n == cap) {
+          cap = cap ? 2 * cap : 64;
+          cand = (int *)realloc(cand, sizeof(int) * cap);
+        }
+        cand[n++] = l * La + k;
+      }
+    }
+  for (int a = 1; a < n; ++a) {   /* value descending, flat index ascending */
+    int cur = cand[a];
+    int b = a - 1;
+    while (b >= 0 && (P[cand[b]] < P[cur])) {
+      cand[b + 1] = cand[b];
+      --b;
+    }
+    cand[b + 1] = cur;
+  }
+  int count = n < D ? n : D;
+  for (int a = 1; a < count; ++a) {
+    int cur = cand[a];
+    int b = a - 1;
+    while (b >= 0 && cand[b] > cur) {
+      cand[b + 1] = cand[b];
+      --b;
+    }
+    cand[b + 1] = cur;
+  }
+  for (int a = 0; a < count; ++a) {
+    idx[a] = cand[a];
+    val[a] = P[cand[a]];
+  }
+  free(cand);
+  return count;
+}
