@@ -20,6 +20,9 @@
  *     y = z = 0, phi = 90 deg): a_m(theta) = exp(+j*pi*m*sin(theta)), m = 0..M-1, theta in
  *     degrees from broadside. Element 0 is the reference element of MN.
  *   - The scan grid is theta_k = lo_deg + k*step_deg, k = 0..L-1, evaluated in FP64.
+ *   - Other geometries (any element positions; Eq. 2 as printed) are scanned over an
+ *     azimuth x elevation grid by doa_scan_geometry / doa_peaks2d and by batch problems that
+ *     carry a doa_geometry (see below).
  *   - Argument errors are reported synchronously by the return value and enqueue nothing.
  *     Launch failures return DOA_ECUDA. Numerical problems found on the device (no
  *     convergence, rank loss, non-finite data) are written to the caller's `info`/`status`
@@ -64,6 +67,28 @@ typedef struct {
   int32_t L;
   int32_t reserved;
 } doa_grid;
+
+/*
+ * Array geometry and elevation grid of a 2-D (azimuth x elevation) scan with the steering vector
+ * of Eq. 2 as printed:
+ *   a_m(theta, phi) = exp{ j 2 pi (x_m sin(theta) sin(phi) + y_m cos(theta) sin(phi) + z_m cos(phi)) }
+ * theta = azimuth (the columns: a doa_grid of La points), phi = the elevation angle of Eq. 2 (the
+ * rows: phi_l = el_lo_deg + l * el_step_deg, l < Le; phi = 90 deg is the plane z = 0, where
+ * Sec. 5.1 takes its accuracy scans). Positions (x_m, y_m, z_m) are in wavelengths. The spectrum
+ * is Le x La row-major (flat index l * La + k); peaks are reported as flat indices.
+ *   pos      : DEVICE pointer to M x 3 finite doubles (x_m, y_m, z_m), element by element; NULL in
+ *              a batch problem means the 1-D half-wavelength ULA scan. 8-byte aligned.
+ *   wrap_az  : 1 if the azimuth grid closes the circle (its first and last columns are
+ *              neighbours for peak finding), else 0.
+ *   Sizes    : 1 <= La, Le <= 2^24, La * Le <= 2^30.
+ */
+typedef struct {
+  const double *pos;
+  double el_lo_deg;
+  double el_step_deg;
+  int32_t Le;
+  int32_t wrap_az;
+} doa_geometry;
 
 /* Human-readable name of a status code (static string, never NULL). */
 const char *doa_status_str(int status);
@@ -148,6 +173,29 @@ doa_status doa_scan(const double *B, int M, int K, doa_grid grid, int prec, floa
  *   idx, val : d entries each (entries past *count are left untouched); count: one int32.
  */
 doa_status doa_peaks(const float *P, int L, int d, int *idx, float *val, int *count, void *stream);
+
+/*
+ * Step-5 for an arbitrary geometry on an azimuth x elevation grid (Eq. 2 as printed):
+ * P[l * La + k] = 1 / ||B^H a(theta_k, phi_l)||^2.
+ *   B     : M x K complex128 column-major, ld M, as for doa_scan. 1 <= K <= M.
+ *   az    : azimuth grid (La = az.L >= 1 columns); geom: positions and elevation rows (pos != NULL).
+ *   P     : La * Le floats, 4-byte aligned.
+ * FP32 on CUDA cores: direction angles in FP32 half turns, phases t_m = p_m . u in turns from the
+ * positions relative to their centroid (a common phase, which leaves ||B^H a|| unchanged), phasors
+ * from the fraction of t_m as a 32-bit phase. Points whose denominator falls below a threshold
+ * derived from the geometry's phase-error bound are re-evaluated in FP64 (warp per point).
+ */
+doa_status doa_scan_geometry(const double *B, int M, int K, doa_grid az, doa_geometry geom, float *P,
+                             void *stream);
+
+/*
+ * Step-6 on an Le x La azimuth x elevation spectrum: a peak is a point strictly larger than each
+ * of its (up to 8) neighbours, rows outside the grid absent, columns wrapping when wrap_az; the d
+ * largest (equal values: lower flat index first), written as flat indices in ascending order.
+ *   idx, val : d entries each; count: one int32. 0 <= d < 64.
+ */
+doa_status doa_peaks2d(const float *P, int La, int Le, int wrap_az, int d, int *idx, float *val, int *count,
+                       void *stream);
 
 /* ----------------------------------------------------------------------------------------- */
 /* Measurement utility (not in the paper)                                                      */
@@ -246,6 +294,9 @@ typedef struct {
                          /* alg_mask (M x K complex128, column-major, ld M)                   */
   int32_t eig_prec;      /* doa_eig_prec of the batch's Jacobi                                */
   int32_t flags;         /* DOA_FLAG_* bits                                                   */
+  doa_geometry geom;     /* geom.pos == NULL: the 1-D ULA scan over `grid`. Otherwise a 2-D   */
+                         /* scan, `grid` the azimuth columns: P holds nalg x (Le x La) floats, */
+                         /* peaks are flat indices, prec must be DOA_FP32 and flags 0          */
 } doa_problem;
 
 /* Peak polish: after Step-6 the spectrum is re-evaluated in FP64 (steering and contraction) at

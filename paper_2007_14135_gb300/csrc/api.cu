@@ -41,6 +41,17 @@ bool grid_ok(const doa_grid &g) {
          g.step_deg != 0.0;
 }
 
+// Azimuth columns and geometry of a 2-D scan (doa_geometry): sizes, finite angles, positions.
+bool geometry_ok(const doa_grid &az, const doa_geometry &g) {
+  const int64_t La = az.L, Le = g.Le;
+  if (!g.pos || !aligned(g.pos, 8) || La < 1 || Le < 1 || La > (1 << 24) || Le > (1 << 24) || La * Le > (1 << 30))
+    return false;
+  if (!std::isfinite(az.lo_deg) || !std::isfinite(az.step_deg) || !std::isfinite(g.el_lo_deg) ||
+      !std::isfinite(g.el_step_deg))
+    return false;
+  return g.wrap_az == 0 || g.wrap_az == 1;
+}
+
 bool problem_ok(const doa_problem &p) {
   if (p.M < 2 || p.M > kMaxM || p.d < 0 || p.d >= p.M || p.N < 1 || p.ldx < p.N) return false;
   if (!p.X || !aligned(p.X, 8) || !p.P || !aligned(p.P, 4)) return false;
@@ -49,9 +60,15 @@ bool problem_ok(const doa_problem &p) {
   if (p.flags & ~DOA_FLAG_POLISH_PEAKS) return false;
   if (p.d > 0 && (!p.peak_idx || !p.peak_val)) return false;
   if (!p.peak_count) return false;
+  if (p.geom.pos)   // 2-D scan: FP32 on CUDA cores, no peak polish
+    return p.prec == DOA_FP32 && p.flags == 0 && geometry_ok(p.grid, p.geom);
   // scan form: FP32 (CUDA cores) or split operands on the tensor cores (M <= 32)
   if (p.prec != DOA_FP32 && !((p.prec == DOA_BF16X3 || p.prec == DOA_FP16X3) && p.M <= kTcBatchMaxM)) return false;
   return grid_ok(p.grid);
+}
+
+int64_t spectrum_points(const doa_problem &p) {
+  return p.geom.pos ? (int64_t)p.grid.L * p.geom.Le : (int64_t)p.grid.L;
 }
 
 struct PlanSizes {
@@ -60,6 +77,7 @@ struct PlanSizes {
   int tc = 0;
   int eig[kNumBuckets] = {0, 0, 0, 0};
   int scan[kNumBuckets] = {0, 0, 0, 0};
+  int geo[kNumBuckets] = {0, 0, 0, 0};
 };
 
 bool same_grid(const doa_grid &a, const doa_grid &b) {
@@ -84,6 +102,11 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
     sz.nreduce += chunks > 1;
     sz.eig[m_bucket(p.M)] += 1;
     sz.njobs += __builtin_popcount(p.alg_mask);
+    if (p.geom.pos) {   // 2-D scan: no ULA phase table
+      sz.geo[m_bucket(p.M)] += 1;
+      grid_of[i] = -1;
+      continue;
+    }
     if (p.prec == DOA_FP32)
       sz.scan[m_bucket(p.M)] += 1;
     else
@@ -105,7 +128,7 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
 }
 
 struct PlanOffsets {
-  int64_t prob, job, grid, cov, reduce, eig[kNumBuckets], scan[kNumBuckets], tc, total;
+  int64_t prob, job, grid, cov, reduce, eig[kNumBuckets], scan[kNumBuckets], tc, geo[kNumBuckets], total;
 };
 
 PlanOffsets plan_offsets(const PlanSizes &sz) {
@@ -131,6 +154,10 @@ PlanOffsets plan_offsets(const PlanSizes &sz) {
   }
   o.tc = at;
   at = round_up(at + (int64_t)sz.tc * 4, 16);
+  for (int b = 0; b < kNumBuckets; ++b) {
+    o.geo[b] = at;
+    at = round_up(at + (int64_t)sz.geo[b] * 4, 16);
+  }
   o.total = at;
   return o;
 }
@@ -251,6 +278,23 @@ doa_status doa_peaks(const float *P, int L, int d, int *idx, float *val, int *co
   return cuda_status(launch_peaks_single(P, L, d, idx, val, count, as_stream(stream)));
 }
 
+doa_status doa_scan_geometry(const double *B, int M, int K, doa_grid az, doa_geometry geom, float *P, void *stream) {
+  if (!B || !P || M < 2 || M > kMaxM || K < 1 || K > M || !geometry_ok(az, geom)) return DOA_EINVAL;
+  if (!aligned(B, 16) || !aligned(P, 4)) return DOA_EINVAL;
+  return cuda_status(launch_scan_geometry_single(reinterpret_cast<const double2 *>(B), M, K, geom.pos, az.lo_deg,
+                                                 az.step_deg, az.L, geom.el_lo_deg, geom.el_step_deg, geom.Le, P,
+                                                 as_stream(stream)));
+}
+
+doa_status doa_peaks2d(const float *P, int La, int Le, int wrap_az, int d, int *idx, float *val, int *count,
+                       void *stream) {
+  if (!P || !count || La < 1 || Le < 1 || La > (1 << 24) || Le > (1 << 24) || (int64_t)La * Le > (1 << 30) ||
+      (wrap_az != 0 && wrap_az != 1) || d < 0 || d >= kMaxM || (d > 0 && (!idx || !val)))
+    return DOA_EINVAL;
+  if (!aligned(P, 4)) return DOA_EINVAL;
+  return cuda_status(launch_peaks2d_single(P, La, Le, wrap_az, d, idx, val, count, as_stream(stream)));
+}
+
 size_t doa_batch_plan_bytes(const doa_problem *probs, int nprob) {
   if (!probs || nprob < 1) return 0;
   PlanSizes sz;
@@ -291,6 +335,11 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
   }
   int32_t *tcl = reinterpret_cast<int32_t *>(base + o.tc);
   h.off_tc = o.tc;
+  int32_t *geo[kNumBuckets];
+  for (int b = 0; b < kNumBuckets; ++b) {
+    geo[b] = reinterpret_cast<int32_t *>(base + o.geo[b]);
+    h.off_geo[b] = o.geo[b];
+  }
   h.magic = kPlanMagic;
   for (int b = 0; b < kNumBuckets; ++b) h.scan_pt[b] = pt[b];
   h.nprob = sz.nprob;
@@ -335,6 +384,7 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     const int64_t mm = (int64_t)M * M * 16;
     q.r64_off = ws;
     ws = round_up(ws + mm, 256);
+    q.npts = (int32_t)spectrum_points(p);
     q.nchunks = (p.N + kCovChunk - 1) / kCovChunk;
     q.part_off = ws;
     if (q.nchunks > 1) {
@@ -359,7 +409,12 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     if (p.flags & DOA_FLAG_POLISH_PEAKS) ++h.npolish;
     q.fac_off = ws;
     ws = round_up(ws + factor_bytes(M), 256);
-    if (p.prec == DOA_FP32) {
+    if (p.geom.pos) {
+      const int tp = kScanThreads * pt[b];
+      q.tile_start = h.geo_tiles[b];
+      h.geo_tiles[b] += (q.npts + tp - 1) / tp;
+      geo[b][h.geo_jobs[b]++] = i;
+    } else if (p.prec == DOA_FP32) {
       const int tp = kScanThreads * pt[b];
       q.tile_start = tiles[b];
       tiles[b] += (p.grid.L + tp - 1) / tp;
@@ -400,6 +455,7 @@ doa_status doa_solve_batch(const void *plan_host, const void *plan_dev, void *ws
   if (!mark(2) || launch_eig_batch(pd, h, w, status, s) != cudaSuccess) return DOA_ECUDA;
   if (!mark(3) || launch_scan_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
   if (h.tc_jobs > 0 && launch_scan_tc_batch(pd, h, w, status, s) != cudaSuccess) return DOA_ECUDA;
+  if (launch_scan_geometry_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
   if (!mark(4) || launch_peaks_batch(pd, h, s) != cudaSuccess) return DOA_ECUDA;
   if (h.npolish > 0 &&
       (launch_polish_batch(pd, h, w, s) != cudaSuccess || launch_peaks_batch(pd, h, s) != cudaSuccess))

@@ -153,6 +153,8 @@ struct PlanProblem {
   int32_t Kf, Kn;         // factor columns; columns read by MUSIC / EV (E_n), 0 if neither
   int32_t kphd, kmn;      // columns read by PHD (v_min) and MN (valph), -1 if absent
   int32_t slot[4];        // output row of each algorithm (doa_alg order), -1 if not requested
+  int32_t npts;           // points of one spectrum: L, or La x Le for a geometry problem
+  int32_t pad;
 };
 
 // Bytes of a problem's scan factor area: F (M x (M+1) complex128) + EV weights (M doubles).
@@ -201,16 +203,21 @@ struct PlanHeader {
   int64_t off_tc;                        // byte offset of the tc problem list
   int32_t npolish;                       // problems with DOA_FLAG_POLISH_PEAKS
   int32_t pad2;
+  // problems with an explicit geometry (2-D azimuth x elevation scans), per M bucket
+  int32_t geo_jobs[kNumBuckets];
+  int64_t geo_tiles[kNumBuckets];
+  int64_t off_geo[kNumBuckets];
 };
 
 // The Python binding reads these header fields by position (int32 index 22 = scan_pt, 58 = eig_mats,
-// 62 = cov_first, 67 = tc_jobs, 74 = npolish).
+// 62 = cov_first, 67 = tc_jobs, 74 = npolish, 76 = geo_jobs).
 static_assert(offsetof(PlanHeader, scan_pt) == 88, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, scan_tiles) == 56, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, eig_mats) == 232, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, cov_first) == 248, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, tc_jobs) == 268, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, npolish) == 296, "PlanHeader layout changed");
+static_assert(offsetof(PlanHeader, geo_jobs) == 304, "PlanHeader layout changed");
 
 // Scan tiles: kScanThreads threads, each evaluating PT consecutive grid points (tile shape
 // 128 x PT). PT is chosen per M bucket (the autotuner's knob); the register budget limits it
@@ -270,8 +277,15 @@ __host__ __device__ inline int tc_batch_cols(int Kf) {   // TMEM columns: 2 buff
 cudaError_t launch_scan_tc_single(const double2 *B, int M, int K, int L, double lo, double step, int prec,
                                   const uint32_t *S, float *P, cudaStream_t s);
 
+cudaError_t launch_scan_geometry_single(const double2 *B, int M, int K, const double *pos, double az_lo,
+                                        double az_step, int La, double el_lo, double el_step, int Le, float *P,
+                                        cudaStream_t s);
+cudaError_t launch_scan_geometry_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
+
 cudaError_t launch_peaks_single(const float *P, int L, int d, int *idx, float *val, int *count,
                                 cudaStream_t s);
+cudaError_t launch_peaks2d_single(const float *P, int La, int Le, int wrap_az, int d, int *idx, float *val,
+                                  int *count, cudaStream_t s);
 cudaError_t launch_peaks_batch(const uint8_t *plan_dev, const PlanHeader &h, cudaStream_t s);
 cudaError_t launch_polish_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
 cudaError_t launch_slice_peaks(const float *Pbuf, int b0, int k0, int k1, int L, int d, doa_slice_summary *out,

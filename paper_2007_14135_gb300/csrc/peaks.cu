@@ -19,9 +19,8 @@ namespace {
 
 using namespace pk;
 
-__device__ void peaks_block(const float *__restrict__ P, int L, int d, int *idx, float *val, int *count) {
-  __shared__ Cand sel[kMaxM];
-  const int nsel = select_top(P, L, d, sel);
+// Writes the nsel selected peaks in ascending index order (thread 0).
+__device__ void write_sel(Cand *sel, int nsel, int *idx, float *val, int *count) {
   if (threadIdx.x == 0) {
     for (int a = 1; a < nsel; ++a) {
       Cand c = sel[a];
@@ -40,6 +39,24 @@ __device__ void peaks_block(const float *__restrict__ P, int L, int d, int *idx,
   }
 }
 
+__device__ void peaks_block(const float *__restrict__ P, int L, int d, int *idx, float *val, int *count) {
+  __shared__ Cand sel[kMaxM];
+  const int nsel = select_top(P, L, d, sel);
+  write_sel(sel, nsel, idx, val, count);
+}
+
+__device__ void peaks2d_block(const float *__restrict__ P, int La, int Le, bool wrap, int d, int *idx, float *val,
+                              int *count) {
+  __shared__ Cand sel[kMaxM];
+  const int nsel = select_top2d(P, La, Le, wrap, d, sel);
+  write_sel(sel, nsel, idx, val, count);
+}
+
+__global__ void __launch_bounds__(kPeakThreads) peaks2d_single_kernel(const float *P, int La, int Le, int wrap, int d,
+                                                                      int *idx, float *val, int *count) {
+  peaks2d_block(P, La, Le, wrap != 0, d, idx, val, count);
+}
+
 __global__ void __launch_bounds__(kPeakThreads) peaks_single_kernel(const float *P, int L, int d, int *idx, float *val,
                                                                     int *count) {
   peaks_block(P, L, d, idx, val, count);
@@ -49,9 +66,13 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_batch_kernel(const uint8_t
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
   const PlanJob &jb = reinterpret_cast<const PlanJob *>(plan + h->off_job)[blockIdx.x];
   const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[jb.prob];
-  const int L = pp.p.grid.L, d = pp.p.d;
-  peaks_block(pp.p.P + (size_t)jb.slot * L, L, d, pp.p.peak_idx + (size_t)jb.slot * d,
-              pp.p.peak_val + (size_t)jb.slot * d, pp.p.peak_count + jb.slot);
+  const int L = pp.npts, d = pp.p.d;
+  if (pp.p.geom.pos)
+    peaks2d_block(pp.p.P + (size_t)jb.slot * L, pp.p.grid.L, pp.p.geom.Le, pp.p.geom.wrap_az != 0, d,
+                  pp.p.peak_idx + (size_t)jb.slot * d, pp.p.peak_val + (size_t)jb.slot * d, pp.p.peak_count + jb.slot);
+  else
+    peaks_block(pp.p.P + (size_t)jb.slot * L, L, d, pp.p.peak_idx + (size_t)jb.slot * d,
+                pp.p.peak_val + (size_t)jb.slot * d, pp.p.peak_count + jb.slot);
 }
 
 // ---- grid slices ---------------------------------------------------------------------------
@@ -172,6 +193,12 @@ cudaError_t launch_slice_peaks(const float *Pbuf, int b0, int k0, int k1, int L,
 
 cudaError_t launch_peaks_single(const float *P, int L, int d, int *idx, float *val, int *count, cudaStream_t s) {
   peaks_single_kernel<<<1, kPeakThreads, 0, s>>>(P, L, d, idx, val, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_peaks2d_single(const float *P, int La, int Le, int wrap_az, int d, int *idx, float *val,
+                                  int *count, cudaStream_t s) {
+  peaks2d_single_kernel<<<1, kPeakThreads, 0, s>>>(P, La, Le, wrap_az, d, idx, val, count);
   return cudaGetLastError();
 }
 

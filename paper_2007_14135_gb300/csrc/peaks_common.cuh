@@ -116,15 +116,16 @@ inline __device__ Cand block_best(Cand c, Cand *red) {
   return w;
 }
 
-// Selects the d best peaks of P[0..L) (value descending, index ascending) into sel[0..n),
-// n returned (identical in every thread). All threads of the block must call it.
-__device__ __forceinline__ int select_top(const float *__restrict__ P, int L, int d, Cand *sel) {
+// d rounds of a block arg-max over the threads' caches. fill(thr, cache, n) fills a thread's cache
+// with its best peaks worse than thr (thr.i == INT_MAX: any) and returns whether more exist.
+// Selected peaks go to sel[0..n) (value descending, index ascending); n is returned in every thread.
+template <class Fill>
+__device__ __forceinline__ int select_rounds(int d, Cand *sel, Fill fill) {
   __shared__ Cand red[kPeakThreads / 32 + 1];
-  const int c0 = 1 + threadIdx.x, c1 = L - 1;
   Cand cache[kCache];
   int n = 0, head = 0;
   const Cand none{0.f, INT_MAX};
-  bool more = fill(P, L, c0, c1, kPeakThreads, none, cache, n);
+  bool more = fill(none, cache, n);
   int nsel = 0;
   for (int r = 0; r < d; ++r) {
     Cand mine = head < n ? cache[head] : none;
@@ -135,13 +136,86 @@ __device__ __forceinline__ int select_top(const float *__restrict__ P, int L, in
     if (mine.i == w.i) {
       ++head;
       if (head == n && more) {
-        more = fill(P, L, c0, c1, kPeakThreads, w, cache, n);
+        more = fill(w, cache, n);
         head = 0;
       }
     }
   }
   __syncthreads();
   return nsel;
+}
+
+// Selects the d best peaks of P[0..L) (value descending, index ascending) into sel[0..n),
+// n returned (identical in every thread). All threads of the block must call it.
+__device__ __forceinline__ int select_top(const float *__restrict__ P, int L, int d, Cand *sel) {
+  const int c0 = 1 + threadIdx.x, c1 = L - 1;
+  return select_rounds(d, sel, [&](const Cand &thr, Cand (&cache)[kCache], int &n) {
+    return fill(P, L, c0, c1, kPeakThreads, thr, cache, n);
+  });
+}
+
+// ---- 2-D (azimuth x elevation) spectra ---------------------------------------------------------
+// A point of an Le x La row-major spectrum is a peak when it is strictly larger than each of its
+// neighbours (the up to 8 points at row and column distance <= 1; rows outside the grid are absent,
+// columns wrap around when wrap) and it has at least one.
+inline __device__ bool is_peak2d(const float *__restrict__ P, int La, int Le, bool wrap, int l, int k, float v) {
+  int nb = 0;
+  for (int dl = -1; dl <= 1; ++dl) {
+    const int ll = l + dl;
+    if (ll < 0 || ll >= Le) continue;
+    for (int dk = -1; dk <= 1; ++dk) {
+      if (dl == 0 && dk == 0) continue;
+      int kk = k + dk;
+      if (kk < 0 || kk >= La) {
+        if (!wrap) continue;
+        kk = kk < 0 ? kk + La : kk - La;
+      }
+      ++nb;
+      if (!(P[(size_t)ll * La + kk] < v)) return false;
+    }
+  }
+  return nb > 0;
+}
+
+// Best 2-D peaks among the flat points i = c0, c0 + stride, ... < n worse than thr.
+inline __device__ bool fill2d(const float *__restrict__ P, int La, int Le, bool wrap, int c0, int stride,
+                              const Cand &thr, Cand (&cache)[kCache], int &n) {
+  n = 0;
+  bool more = false;
+  const int npts = La * Le;
+  for (int i = c0; i < npts; i += stride) {
+    const float v = P[i];
+    const int l = i / La, k = i - l * La;
+    if (!is_peak2d(P, La, Le, wrap, l, k, v)) continue;
+    Cand c{v, i};
+    if (thr.i != INT_MAX && !better(thr, c)) continue;
+    if (n < kCache) {
+      int q = n++;
+      while (q > 0 && better(c, cache[q - 1])) {
+        cache[q] = cache[q - 1];
+        --q;
+      }
+      cache[q] = c;
+    } else {
+      more = true;
+      if (better(c, cache[kCache - 1])) {
+        int q = kCache - 1;
+        while (q > 0 && better(c, cache[q - 1])) {
+          cache[q] = cache[q - 1];
+          --q;
+        }
+        cache[q] = c;
+      }
+    }
+  }
+  return more;
+}
+
+__device__ __forceinline__ int select_top2d(const float *__restrict__ P, int La, int Le, bool wrap, int d, Cand *sel) {
+  const int c0 = threadIdx.x;
+  return select_rounds(d, sel, [&](const Cand &thr, Cand (&cache)[kCache], int &n) {
+    return fill2d(P, La, Le, wrap, c0, kPeakThreads, thr, cache, n);
+  });
 }
 
 }  // namespace pk

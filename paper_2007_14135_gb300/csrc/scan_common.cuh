@@ -104,17 +104,26 @@ __device__ __forceinline__ uint64_t phase64_of_point(const ScanJob &j, int k) {
 
 __device__ __forceinline__ float recip_out(float den) { return __frcp_rn(fmaxf(den, FLT_MIN)); }
 
+// FP64 steering source of the ULA scans: the exact 64-bit phase m * S64_k of element m.
+struct UlaSource {
+  const ScanJob *j;
+  __device__ __forceinline__ uint64_t prep(int k) const { return phase64_of_point(*j, k); }
+  __device__ __forceinline__ double2 phasor(uint64_t step, int m) const { return phasor_q64((uint64_t)m * step); }
+};
+
 // Re-evaluation of local point k by one whole warp with the steering vector and the contraction
-// in FP64: phasors from the exact 64-bit phase m * S64 (lane m), then y_c = f_c^H a with LPC
-// lanes per column (LPC = the largest power of two with Kf * LPC <= 32, so one pass covers the
-// columns when it can), each lane summing a contiguous run of elements and the LPC partial sums
-// combined by shuffles. The cancellation that makes the FP32 result inaccurate happens inside
-// y_c; the readouts sum |y_c|^2 >= 0 and are formed from y_c rounded once to FP32.
-inline __device__ void refine_point_warp(const ScanJob &j, int k, const float *w32, double2 *ph, float2 *yb) {
+// in FP64: phasors from the source (lane m), then y_c = f_c^H a with LPC lanes per column (LPC =
+// the largest power of two with Kf * LPC <= 32, so one pass covers the columns when it can), each
+// lane summing a contiguous run of elements and the LPC partial sums combined by shuffles. The
+// cancellation that makes the FP32 result inaccurate happens inside y_c; the readouts sum
+// |y_c|^2 >= 0 and are formed from y_c rounded once to FP32.
+template <class Src>
+inline __device__ void refine_point_warp_src(const ScanJob &j, int k, const Src &src, const float *w32, double2 *ph,
+                                             float2 *yb) {
   const int lane = threadIdx.x & 31;
-  const uint64_t step = phase64_of_point(j, k);
+  const auto st = src.prep(k);
   const int M = j.M, Kf = j.Kf;
-  for (int m = lane; m < M; m += 32) ph[m] = phasor_q64((uint64_t)m * step);
+  for (int m = lane; m < M; m += 32) ph[m] = src.phasor(st, m);
   __syncwarp();
   int lpc = 1;
   while (lpc < 32 && Kf * lpc * 2 <= 32 && lpc < M) lpc <<= 1;
@@ -166,14 +175,19 @@ inline __device__ void refine_point_warp(const ScanJob &j, int k, const float *w
   __syncwarp();
 }
 
+inline __device__ void refine_point_warp(const ScanJob &j, int k, const float *w32, double2 *ph, float2 *yb) {
+  refine_point_warp_src(j, k, UlaSource{&j}, w32, ph, yb);
+}
+
 // Same computation by a single thread (only when a tile's queue overflows).
-inline __device__ void refine_point_thread(const ScanJob &j, int k, const float *w32) {
-  const uint64_t step = phase64_of_point(j, k);
+template <class Src>
+inline __device__ void refine_point_thread_src(const ScanJob &j, int k, const Src &src, const float *w32) {
+  const auto st = src.prep(k);
   float dm = 0.f, de = 0.f, dp = 0.f, dn = 0.f;
   for (int col = 0; col < j.Kf; ++col) {
     double yr = 0.0, yi = 0.0;
     for (int m = 0; m < j.M; ++m) {
-      const double2 a = phasor_q64((uint64_t)m * step);
+      const double2 a = src.phasor(st, m);
       const double2 b = j.F[(size_t)col * j.M + m];
       yr = fma(b.x, a.x, fma(b.y, a.y, yr));
       yi = fma(b.x, a.y, fma(-b.y, a.x, yi));
@@ -194,14 +208,20 @@ inline __device__ void refine_point_thread(const ScanJob &j, int k, const float 
 }
 
 // Drains the tile's refinement queue (all threads of the CTA call this).
-__device__ __forceinline__ void drain_refinements(const ScanJob &j, ScanShared &sh) {
+template <class Src>
+__device__ __forceinline__ void drain_refinements_src(const ScanJob &j, const Src &src, ScanShared &sh) {
   __syncthreads();
   const int n = min(sh.nflag, kFlagCap);
   const int warp = threadIdx.x >> 5;
-  for (int i = warp; i < n; i += kScanWarps) refine_point_warp(j, sh.flags[i], sh.w32, sh.ph[warp], sh.yb[warp]);
+  for (int i = warp; i < n; i += kScanWarps)
+    refine_point_warp_src(j, sh.flags[i], src, sh.w32, sh.ph[warp], sh.yb[warp]);
   __syncthreads();
   if (threadIdx.x == 0) sh.nflag = 0;
   __syncthreads();
+}
+
+__device__ __forceinline__ void drain_refinements(const ScanJob &j, ScanShared &sh) {
+  drain_refinements_src(j, UlaSource{&j}, sh);
 }
 
 template <int PT>
@@ -217,33 +237,12 @@ __device__ __forceinline__ void store_row(float *P, int L, int k0, const float (
   }
 }
 
-// Evaluates the local points k0 .. k0+PT-1 (those < L) of one job. S may alias a P row of a
-// single-readout job: each thread reads its own phase steps before it writes its own outputs.
-// Points where any readout falls below its refinement threshold are queued for drain_refinements.
-template <int MP, int PT>
-__device__ __forceinline__ void scan_points(const float2 *Bs, const ScanJob &j, const uint32_t *S, int L, int k0,
-                                            ScanShared &sh) {
-  // Steering phasors a_m, m = 4i + r: a_{4i} and a_r (r = 1..3) from their exact integer phases,
-  // the rest as the product a_{4i} a_r (one FP32 complex multiply of two polynomial phasors).
-  static_assert(MP % 4 == 0, "MP is a multiple of 4");
-  float2 a[PT][MP];
-#pragma unroll
-  for (int q = 0; q < PT; ++q) {
-    const uint32_t step = (k0 + q < L) ? S[k0 + q] : 0u;
-    a[q][0] = make_float2(1.f, 0.f);
-#pragma unroll
-    for (int r = 1; r < 4; ++r) a[q][r] = phasor_q32((uint32_t)r * step);
-#pragma unroll
-    for (int i = 1; i < MP / 4; ++i) {
-      const float2 A = phasor_q32((uint32_t)(4 * i) * step);
-      a[q][4 * i] = A;
-#pragma unroll
-      for (int r = 1; r < 4; ++r) {
-        const float2 z = a[q][r];
-        a[q][4 * i + r] = make_float2(fmaf(A.x, z.x, -A.y * z.y), fmaf(A.x, z.y, A.y * z.x));
-      }
-    }
-  }
+// Contracts the PT x MP phasor block a (points k0 .. k0+PT-1 of a job, those < L) with the factor
+// and writes the readouts. Points where any readout falls below its refinement threshold are
+// queued for drain_refinements_src (or, on queue overflow, re-evaluated in place from src).
+template <int MP, int PT, class Src>
+__device__ __forceinline__ void contract_points(const float2 *Bs, const ScanJob &j, const float2 (&a)[PT][MP], int L,
+                                                int k0, ScanShared &sh, const Src &src) {
   float dm[PT], de[PT], dp[PT], dn[PT], n[PT];
 #pragma unroll
   for (int q = 0; q < PT; ++q) dm[q] = de[q] = dp[q] = dn[q] = n[q] = 0.f;
@@ -328,7 +327,37 @@ __device__ __forceinline__ void scan_points(const float2 *Bs, const ScanJob &j, 
   // queue overflow (more than kFlagCap small denominators in one tile): refine in place
 #pragma unroll
   for (int q = 0; q < PT; ++q)
-    if (pos[q] >= kFlagCap) refine_point_thread(j, k0 + q, sh.w32);
+    if (pos[q] >= kFlagCap) refine_point_thread_src(j, k0 + q, src, sh.w32);
+}
+
+// Evaluates the local points k0 .. k0+PT-1 (those < L) of one job. S may alias a P row of a
+// single-readout job: each thread reads its own phase steps before it writes its own outputs.
+// Points where any readout falls below its refinement threshold are queued for drain_refinements.
+template <int MP, int PT>
+__device__ __forceinline__ void scan_points(const float2 *Bs, const ScanJob &j, const uint32_t *S, int L, int k0,
+                                            ScanShared &sh) {
+  // Steering phasors a_m, m = 4i + r: a_{4i} and a_r (r = 1..3) from their exact integer phases,
+  // the rest as the product a_{4i} a_r (one FP32 complex multiply of two polynomial phasors).
+  static_assert(MP % 4 == 0, "MP is a multiple of 4");
+  float2 a[PT][MP];
+#pragma unroll
+  for (int q = 0; q < PT; ++q) {
+    const uint32_t step = (k0 + q < L) ? S[k0 + q] : 0u;
+    a[q][0] = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int r = 1; r < 4; ++r) a[q][r] = phasor_q32((uint32_t)r * step);
+#pragma unroll
+    for (int i = 1; i < MP / 4; ++i) {
+      const float2 A = phasor_q32((uint32_t)(4 * i) * step);
+      a[q][4 * i] = A;
+#pragma unroll
+      for (int r = 1; r < 4; ++r) {
+        const float2 z = a[q][r];
+        a[q][4 * i + r] = make_float2(fmaf(A.x, z.x, -A.y * z.y), fmaf(A.x, z.y, A.y * z.x));
+      }
+    }
+  }
+  contract_points<MP, PT>(Bs, j, a, L, k0, sh, UlaSource{&j});
 }
 
 }  // namespace scanc

@@ -29,7 +29,8 @@ STAGE_NAMES = ("phase_tables", "covariance", "eig_noise_subspace", "scan", "peak
 EXPORTS = ("doa_status_str", "doa_covariance", "doa_covariance_noalloc", "doa_noise_subspace", "doa_scan",
            "doa_peaks", "doa_batch_plan_bytes", "doa_batch_plan", "doa_solve_batch", "doa_mlp_workspace_bytes",
            "doa_mlp_refresh", "doa_mlp_forward", "doa_mlp_backward", "doa_mlp_adam", "doa_synth_ula",
-           "doa_proposal_windows", "doa_scan_windows", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices", "doa_probe_fma")
+           "doa_proposal_windows", "doa_scan_windows", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices", "doa_probe_fma",
+           "doa_scan_geometry", "doa_peaks2d")
 SLICE_MAXD = 64
 
 
@@ -44,13 +45,21 @@ class Grid(ctypes.Structure):
                 ("L", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class Geometry(ctypes.Structure):
+    """doa_geometry: element positions (device, M x 3 FP64, wavelengths) and the elevation rows of a
+    2-D azimuth x elevation scan; pos = NULL means the 1-D ULA scan."""
+    _fields_ = [("pos", ctypes.c_void_p), ("el_lo_deg", ctypes.c_double), ("el_step_deg", ctypes.c_double),
+                ("Le", ctypes.c_int32), ("wrap_az", ctypes.c_int32)]
+
+
 class Problem(ctypes.Structure):
     _fields_ = [("X", ctypes.c_void_p), ("P", ctypes.c_void_p), ("peak_idx", ctypes.c_void_p),
                 ("peak_val", ctypes.c_void_p), ("peak_count", ctypes.c_void_p),
                 ("evals", ctypes.c_void_p), ("grid", Grid), ("M", ctypes.c_int32),
                 ("N", ctypes.c_int32), ("ldx", ctypes.c_int32), ("d", ctypes.c_int32),
                 ("alg_mask", ctypes.c_uint32), ("prec", ctypes.c_int32), ("features", ctypes.c_void_p),
-                ("B_out", ctypes.c_void_p), ("eig_prec", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("B_out", ctypes.c_void_p), ("eig_prec", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("geom", Geometry)]
 
 
 class SliceSummary(ctypes.Structure):
@@ -81,8 +90,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.doa_slice_peaks.argtypes = [vp, i, i, i, i, i, vp, vp]
     lib.doa_merge_slices.argtypes = [vp, i, i, vp, vp, vp]
     lib.doa_probe_fma.argtypes = [i, i, i, vp, ctypes.POINTER(ctypes.c_double), vp]
+    lib.doa_scan_geometry.argtypes = [vp, i, i, Grid, Geometry, vp, vp]
+    lib.doa_peaks2d.argtypes = [vp, i, i, i, i, vp, vp, vp, vp]
     for name in ("doa_covariance", "doa_covariance_noalloc", "doa_noise_subspace", "doa_scan", "doa_peaks",
-                 "doa_batch_plan", "doa_solve_batch", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices", "doa_probe_fma"):
+                 "doa_batch_plan", "doa_solve_batch", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices", "doa_probe_fma",
+                 "doa_scan_geometry", "doa_peaks2d"):
         getattr(lib, name).restype = i
     return lib
 
@@ -122,6 +134,12 @@ def _dev(t: Optional[torch.Tensor]) -> Optional[int]:
 
 def grid(lo: float, step: float, L: int) -> Grid:
     return Grid(float(lo), float(step), int(L), 0)
+
+
+def geometry(pos: torch.Tensor, el_lo: float, el_step: float, Le: int, wrap_az: bool) -> Geometry:
+    """doa_geometry for device positions pos (float64, (M, 3), contiguous; must outlive its use)."""
+    assert pos.dtype == torch.float64 and pos.is_contiguous() and pos.dim() == 2 and pos.shape[1] == 3
+    return Geometry(_dev(pos), float(el_lo), float(el_step), int(Le), 1 if wrap_az else 0)
 
 
 # ------------------------------------------------------------------------------------ stages
@@ -216,17 +234,31 @@ def doa_peaks(P: torch.Tensor, d: int, idx: torch.Tensor, val: torch.Tensor, cou
     _check(lib().doa_peaks(_dev(P), L, d, _dev(idx), _dev(val), _dev(count), _stream(stream)), "doa_peaks")
 
 
+def doa_scan_geometry(B: torch.Tensor, M: int, K: int, az: Grid, geom: Geometry, P: torch.Tensor,
+                      stream=None) -> None:
+    """2-D scan P[l * La + k] over azimuth az (columns) and the rows of geom (Eq. 2 as printed)."""
+    _check(lib().doa_scan_geometry(_dev(B), M, K, az, geom, _dev(P), _stream(stream)), "doa_scan_geometry")
+
+
+def doa_peaks2d(P: torch.Tensor, La: int, Le: int, wrap_az: bool, d: int, idx: torch.Tensor, val: torch.Tensor,
+                count: torch.Tensor, stream=None) -> None:
+    _check(lib().doa_peaks2d(_dev(P), La, Le, 1 if wrap_az else 0, d, _dev(idx), _dev(val), _dev(count),
+                             _stream(stream)), "doa_peaks2d")
+
+
 # ------------------------------------------------------------------------------------ batch
 def make_problem(X: torch.Tensor, d: int, alg_mask: int, g: Grid, P: torch.Tensor, peak_idx: torch.Tensor,
                  peak_val: torch.Tensor, peak_count: torch.Tensor, evals: Optional[torch.Tensor] = None,
                  prec: int = FP32, features: Optional[torch.Tensor] = None,
-                 B_out: Optional[torch.Tensor] = None, eig_prec: int = 0, polish: bool = False) -> Problem:
-    """Descriptor of one problem; the tensors must outlive every solve that uses it."""
+                 B_out: Optional[torch.Tensor] = None, eig_prec: int = 0, polish: bool = False,
+                 geom: Optional[Geometry] = None) -> Problem:
+    """Descriptor of one problem; the tensors must outlive every solve that uses it. With geom the
+    problem is a 2-D scan: g is the azimuth grid, P holds nalg x (Le x La) floats."""
     assert X.dtype == torch.complex64 and X.dim() == 2 and X.stride(1) == 1
     M, N = X.shape
     return Problem(_dev(X), _dev(P), _dev(peak_idx), _dev(peak_val), _dev(peak_count), _dev(evals), g,
                    M, N, X.stride(0), d, alg_mask, prec, _dev(features), _dev(B_out), eig_prec,
-                   FLAG_POLISH_PEAKS if polish else 0)
+                   FLAG_POLISH_PEAKS if polish else 0, geom if geom is not None else Geometry(None, 0.0, 0.0, 0, 0))
 
 
 class Tuning(ctypes.Structure):
@@ -270,7 +302,7 @@ class BatchPlan:
         """int32 index of a PlanHeader field (layout of csrc/doa_internal.cuh)."""
         order = {"magic": 0, "nprob": 1, "njobs": 2, "ngrids": 3, "ncov": 4, "nreduce": 5, "eig_count": 6,
                  "scan_jobs": 10, "scan_tiles": 14, "scan_pt": 22, "eig_mats": 58, "cov_first": 62, "tc_jobs": 67,
-                 "npolish": 74}
+                 "npolish": 74, "geo_jobs": 76}
         return order[field]
 
     def launches(self) -> int:
@@ -279,7 +311,7 @@ class BatchPlan:
         cf = [int(v) for v in h[62:67]]                       # cov_first: classes MB = 2, 3, 4, other
         cov = sum(2 for c in range(3) if cf[c + 1] > cf[c]) + int(cf[4] > cf[3]) + int(h[5] > 0)
         eig_b = sum(int(c) > 0 for c in h[6:10])
-        scan_b = sum(int(c) > 0 for c in h[10:14]) + int(h[67] > 0)
+        scan_b = sum(int(c) > 0 for c in h[10:14]) + int(h[67] > 0) + sum(int(c) > 0 for c in h[76:80])
         peaks = 1 + (2 if int(h[74]) > 0 else 0)
         return 1 + cov + eig_b + scan_b + peaks
 

@@ -11,6 +11,10 @@ Sources are unit-power circular complex Gaussian, s ~ CN(0, 1) = (g1 + j g2)/sqr
 independent (uncorrelated narrowband sources); noise is white CN(0, sigma^2) per element with
 sigma^2 = 10^(-SNR/10), one SNR per instance shared by all sources.
 
+Other geometries (Sec. 4.2's uniform circular array) use Eq. 2 as printed: element positions
+(x_m, y_m, z_m) in wavelengths and a source at azimuth theta, elevation angle phi has response
+exp{j 2 pi (x_m sin(theta) sin(phi) + y_m cos(theta) sin(phi) + z_m cos(phi))}.
+
 Random numbers come from NumPy's Philox4x32-10 counter-based generator (Salmon et al.,
 SC'11) keyed by the instance seed, so every instance is reproducible on any machine.
 """
@@ -310,3 +314,97 @@ def proposal_params(count: int, seed: int, dmax: int = 6):
     ang = np.where(mask, lo + u + sep * np.arange(dmax)[None, :], 0.0).astype(np.float32)
     snr = rng.uniform(-5.0, 20.0, size=count).astype(np.float32)
     return d, ang, snr
+
+
+# ---------------------------------------------------------------------------------------------
+# Arbitrary geometry (Eq. 2 as printed) and the paper's circular-array scenario (Sec. 4.2)
+# ---------------------------------------------------------------------------------------------
+SPEED_OF_LIGHT = 299792458.0
+
+
+def uca_positions(M: int, radius_wl: float) -> np.ndarray:
+    """(M, 3) float64 positions in wavelengths of a uniform circular array in the plane z = 0,
+    element m at angle 2 pi m / M from the +y axis towards +x."""
+    ang = 2.0 * np.pi * np.arange(M, dtype=np.float64) / M
+    pos = np.zeros((M, 3), dtype=np.float64)
+    pos[:, 0] = radius_wl * np.sin(ang)
+    pos[:, 1] = radius_wl * np.cos(ang)
+    return pos
+
+
+def _geometry_response(pos: np.ndarray, az_deg: Sequence[float], el_deg: Sequence[float]) -> np.ndarray:
+    """(M, d) complex128 responses of sources at (azimuth, elevation angle) pairs (Eq. 2)."""
+    t, p = np.deg2rad(np.asarray(az_deg, np.float64)), np.deg2rad(np.asarray(el_deg, np.float64))
+    u = np.stack([np.sin(t) * np.sin(p), np.cos(t) * np.sin(p), np.cos(p)])     # (3, d)
+    return np.exp(2j * np.pi * (np.asarray(pos, np.float64) @ u))
+
+
+def snapshots_geometry(rng: np.random.Generator, pos: np.ndarray, N: int, az_deg: Sequence[float],
+                       el_deg: Sequence[float], snr_db: float) -> np.ndarray:
+    """X = A S + W as complex64 (M, N) for an arbitrary geometry (same source and noise model as
+    `snapshots`)."""
+    M, d = pos.shape[0], len(az_deg)
+    sigma = math.sqrt(10.0 ** (-snr_db / 10.0))
+    inv_sqrt2 = 1.0 / math.sqrt(2.0)
+    if d > 0:
+        g = rng.standard_normal((2, d, N), dtype=np.float32)
+        S = (g[0].astype(np.float64) + 1j * g[1].astype(np.float64)) * inv_sqrt2
+        X = _geometry_response(pos, az_deg, el_deg) @ S
+    else:
+        X = np.zeros((M, N), dtype=np.complex128)
+    w = rng.standard_normal((2, M, N), dtype=np.float32)
+    X += (w[0].astype(np.float64) + 1j * w[1].astype(np.float64)) * (sigma * inv_sqrt2)
+    return X.astype(np.complex64)
+
+
+@dataclasses.dataclass
+class GeoInstance:
+    """One snapshot matrix of an arbitrary geometry with its azimuth x elevation scan grid."""
+    X: np.ndarray            # complex64 (M, N)
+    M: int
+    d: int
+    N: int
+    pos: np.ndarray          # (M, 3) float64, wavelengths
+    az: np.ndarray           # true azimuths (deg)
+    el: np.ndarray           # true elevation angles (deg)
+    snr_db: float
+    az_lo: float             # columns theta_k = az_lo + k az_step, k < La
+    az_step: float
+    La: int
+    el_lo: float             # rows phi_l = el_lo + l el_step, l < Le
+    el_step: float
+    Le: int
+    wrap_az: bool            # the azimuth grid closes the circle
+    seed: int
+
+
+def paper_uca(i: int, base_seed: int = 20071420, N: int = 1024, Le: int = 90) -> GeoInstance:
+    """The paper's scenario (Sec. 4.2): 8 omnidirectional elements on a circle of radius 10 m at
+    15 MHz (radius 10 f / c = 0.5003 wavelengths), two uncorrelated unit-power sources, SNR 15 dB.
+    The source angles of its Fig. 4 are not given: azimuths are drawn U[0, 360) at least 30 deg
+    apart on the circle, elevation angles U[10, 90]. N is not given either (1024 here). Scan:
+    azimuth 0:1:359 (closing the circle) x elevation angle (91 - Le):1:90, the Le rows ending at the
+    array plane (Le = 1 is the single row at 90 deg of Sec. 5.1, Le = 90 the 360 x 90 scan of
+    Tables 8 and 10)."""
+    seed = base_seed + i
+    rng = _rng(seed)
+    M, d, snr = 8, 2, 15.0
+    radius = 10.0 * 15e6 / SPEED_OF_LIGHT
+    a0 = float(rng.uniform(0.0, 360.0))
+    a1 = (a0 + float(rng.uniform(30.0, 330.0))) % 360.0
+    az = np.array([a0, a1])
+    el = rng.uniform(10.0, 90.0, size=2)
+    pos = uca_positions(M, radius)
+    X = snapshots_geometry(rng, pos, N, az, el, snr)
+    return GeoInstance(X, M, d, N, pos, az, el, snr, 0.0, 1.0, 360, float(91 - Le), 1.0, Le, True, seed)
+
+
+def geometry_custom(pos: np.ndarray, d: int, N: int, snr_db: float, az_lo: float, az_step: float, La: int,
+                    el_lo: float, el_step: float, Le: int, wrap_az: bool, seed: int) -> GeoInstance:
+    """Arbitrary-geometry instance for tests: d sources at azimuth U[0, 360), elevation U[5, 85]."""
+    rng = _rng(seed)
+    az = rng.uniform(0.0, 360.0, size=d)
+    el = rng.uniform(5.0, 85.0, size=d)
+    X = snapshots_geometry(rng, np.asarray(pos, np.float64), N, az, el, snr_db)
+    return GeoInstance(X, pos.shape[0], d, N, np.asarray(pos, np.float64), az, el, snr_db, az_lo, az_step, La, el_lo,
+                       el_step, Le, wrap_az, seed)

@@ -61,3 +61,26 @@ def compare_peaks(idx_gpu, idx_ref, P_ref, bound):
     diff = sorted(set(a) ^ set(b))
     ties = [(k, peak_margin(P_ref, k)) for k in diff if 1 <= k < len(P_ref) - 1]
     return all(m < bound for _, m in ties), ties
+
+
+def peak_margin2d(P, La, Le, wrap, i):
+    """Relative margin of a 2-D peak (flat index i of an Le x La spectrum) over its neighbours."""
+    P = np.asarray(P, np.float64).reshape(Le, La)
+    l, k = divmod(int(i), La)
+    nb = []
+    for dl in (-1, 0, 1):
+        for dk in (-1, 0, 1):
+            if (dl or dk) and 0 <= l + dl < Le and (wrap or 0 <= k + dk < La):
+                nb.append(P[l + dl, (k + dk) % La])
+    return float((P[l, k] - max(nb)) / P[l, k]) if nb else 0.0
+
+
+def compare_peaks2d(idx_gpu, idx_ref, P_ref, La, Le, wrap, bound):
+    """2-D counterpart of compare_peaks: the flat index sets agree, or every disagreement is a tie
+    within `bound` (margin of the oracle's point over its neighbours, or of the GPU's pick)."""
+    a, b = list(idx_gpu), list(idx_ref)
+    if a == b:
+        return True, []
+    diff = sorted(set(a) ^ set(b))
+    ties = [(k, peak_margin2d(P_ref, La, Le, wrap, k)) for k in diff]
+    return all(abs(m) < bound for _, m in ties), ties

@@ -178,3 +178,61 @@ def test_batch_plan_tensor_scan_problems(libdoa):
     for bad in (_prob(libdoa, M=33, prec=3), _prob(libdoa, M=16, prec=1), _prob(libdoa, M=16, prec=4)):
         arr = (libdoa.Problem * 1)(bad)
         assert libdoa.lib().doa_batch_plan_bytes(arr, 1) == 0
+
+
+def test_geometry_argument_errors(libdoa):
+    L = libdoa.lib()
+    fake = ctypes.c_void_p(0x10000)
+    az = libdoa.grid(0.0, 1.0, 360)
+
+    def geo(pos=0x20000, Le=90, wrap=1, el_lo=1.0, el_step=1.0):
+        return libdoa.Geometry(pos, el_lo, el_step, Le, wrap)
+
+    assert L.doa_scan_geometry(fake, 8, 0, az, geo(), fake, None) == libdoa.EINVAL        # K < 1
+    assert L.doa_scan_geometry(fake, 8, 9, az, geo(), fake, None) == libdoa.EINVAL        # K > M
+    assert L.doa_scan_geometry(fake, 8, 6, az, geo(pos=None), fake, None) == libdoa.EINVAL
+    assert L.doa_scan_geometry(fake, 8, 6, az, geo(pos=0x20004), fake, None) == libdoa.EINVAL   # 8-byte alignment
+    assert L.doa_scan_geometry(fake, 8, 6, az, geo(Le=0), fake, None) == libdoa.EINVAL
+    assert L.doa_scan_geometry(fake, 8, 6, az, geo(wrap=2), fake, None) == libdoa.EINVAL
+    assert L.doa_scan_geometry(fake, 8, 6, az, geo(el_step=float("nan")), fake, None) == libdoa.EINVAL
+    assert L.doa_scan_geometry(fake, 8, 6, libdoa.grid(0.0, 1.0, 0), geo(), fake, None) == libdoa.EINVAL
+    assert L.doa_scan_geometry(fake, 8, 6, libdoa.grid(0.0, 1.0, 1 << 16), geo(Le=1 << 15), fake, None) == libdoa.EINVAL
+    assert L.doa_scan_geometry(fake, 8, 6, az, geo(), ctypes.c_void_p(0x10002), None) == libdoa.EINVAL
+    assert L.doa_peaks2d(fake, 0, 5, 0, 1, fake, fake, fake, None) == libdoa.EINVAL
+    assert L.doa_peaks2d(fake, 5, 5, 3, 1, fake, fake, fake, None) == libdoa.EINVAL
+    assert L.doa_peaks2d(fake, 5, 5, 0, 64, fake, fake, fake, None) == libdoa.EINVAL
+    assert L.doa_peaks2d(fake, 5, 5, 0, 1, None, fake, fake, None) == libdoa.EINVAL
+    assert L.doa_peaks2d(fake, 5, 5, 0, 1, fake, fake, None, None) == libdoa.EINVAL
+
+
+def test_batch_plan_geometry_problems(libdoa):
+    """Problems with a geometry go to their own per-bucket scan lists (tiles over La x Le points),
+    need no ULA phase table, and must be FP32 without peak polish."""
+    import numpy as np
+
+    def gprob(M=8, La=360, Le=90, **kw):
+        p = _prob(libdoa, M=M, N=1024, d=2, mask=0xF, L=La, step=1.0)
+        p.grid = libdoa.grid(0.0, 1.0, La)
+        p.geom = libdoa.Geometry(0x20000, 1.0, 1.0, Le, 1)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+    probs = [gprob(), _prob(libdoa, M=8, d=2, L=1801, step=0.1), gprob(M=16, La=97, Le=13), gprob(La=1, Le=1)]
+    arr = (libdoa.Problem * 4)(*probs)
+    n = libdoa.lib().doa_batch_plan_bytes(arr, 4)
+    assert n > 0
+    buf = np.zeros(n, np.uint8)
+    ws = ctypes.c_size_t(0)
+    assert libdoa.lib().doa_batch_plan(arr, 4, None, buf.ctypes.data, n, ctypes.byref(ws), None) == 0
+    h32 = buf[:512].view(np.int32)
+    h64 = buf[:512].view(np.int64)
+    assert h32[3] == 1                                  # ngrids: only the ULA problem's grid
+    assert list(h32[10:14]) == [1, 0, 0, 0]             # ULA scan lists
+    assert list(h32[76:80]) == [2, 1, 0, 0]             # geometry scan lists per M bucket
+    pt = list(h32[22:26])
+    assert list(h64[40:44]) == [-(-(360 * 90) // (128 * pt[0])) + 1, -(-(97 * 13) // (128 * pt[1])), 0, 0]
+    assert libdoa.BatchPlan.header_index("geo_jobs") == 76
+    for bad in (gprob(prec=3), gprob(flags=1), gprob(Le=0), gprob(La=0), gprob(La=1 << 16, Le=1 << 15)):
+        one = (libdoa.Problem * 1)(bad)
+        assert libdoa.lib().doa_batch_plan_bytes(one, 1) == 0
