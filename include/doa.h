@@ -180,13 +180,18 @@ doa_status doa_peaks(const float *P, int L, int d, int *idx, float *val, int *co
  *   B     : M x K complex128 column-major, ld M, as for doa_scan. 1 <= K <= M.
  *   az    : azimuth grid (La = az.L >= 1 columns); geom: positions and elevation rows (pos != NULL).
  *   P     : La * Le floats, 4-byte aligned.
- * FP32 on CUDA cores: direction angles in FP32 half turns, phases t_m = p_m . u in turns from the
- * positions relative to their centroid (a common phase, which leaves ||B^H a|| unchanged), phasors
- * from the fraction of t_m as a 32-bit phase. Points whose denominator falls below a threshold
- * derived from the geometry's phase-error bound are re-evaluated in FP64 (warp per point).
+ *   ws    : device scratch of doa_scan_geometry_ws_bytes(La, Le) bytes (24 per azimuth and per
+ *           elevation row), 16-byte aligned; it receives the grid's sin / cos tables (DOA_ENOMEM if
+ *           ws_bytes is smaller).
+ * FP32 on CUDA cores: sin and cos of every grid angle evaluated once in FP64 and rounded, phases
+ * t_m = p_m . u in turns from the positions relative to their centroid (a common phase, which
+ * leaves ||B^H a|| unchanged), phasors from the fraction of t_m as a 32-bit phase. Points whose
+ * denominator falls below a threshold derived from the geometry's phase-error bound are
+ * re-evaluated in FP64 (warp per point).
  */
-doa_status doa_scan_geometry(const double *B, int M, int K, doa_grid az, doa_geometry geom, float *P,
-                             void *stream);
+size_t doa_scan_geometry_ws_bytes(int La, int Le);
+doa_status doa_scan_geometry(const double *B, int M, int K, doa_grid az, doa_geometry geom, float *P, void *ws,
+                             size_t ws_bytes, void *stream);
 
 /*
  * Step-6 on an Le x La azimuth x elevation spectrum: a peak is a point strictly larger than each

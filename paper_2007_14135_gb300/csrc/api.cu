@@ -78,16 +78,31 @@ struct PlanSizes {
   int eig[kNumBuckets] = {0, 0, 0, 0};
   int scan[kNumBuckets] = {0, 0, 0, 0};
   int geo[kNumBuckets] = {0, 0, 0, 0};
+  int ngeo_grids = 0;
 };
+
 
 bool same_grid(const doa_grid &a, const doa_grid &b) {
   return a.L == b.L && std::memcmp(&a.lo_deg, &b.lo_deg, sizeof(double)) == 0 &&
          std::memcmp(&a.step_deg, &b.step_deg, sizeof(double)) == 0;
 }
 
+// A geometry problem's azimuth x elevation grid (the key of its trigonometric tables).
+struct GeoGridKey {
+  doa_grid az;
+  double el_lo, el_step;
+  int32_t Le;
+};
+
+bool same_geo_grid(const GeoGridKey &a, const doa_problem &p) {
+  return same_grid(a.az, p.grid) && a.Le == p.geom.Le &&
+         std::memcmp(&a.el_lo, &p.geom.el_lo_deg, sizeof(double)) == 0 &&
+         std::memcmp(&a.el_step, &p.geom.el_step_deg, sizeof(double)) == 0;
+}
+
 // Counts the plan's arrays; returns false on an invalid problem.
 bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<doa_grid> &grids,
-                std::vector<int> &grid_of, int *bad_index) {
+                std::vector<int> &grid_of, std::vector<GeoGridKey> &geo_grids, int *bad_index) {
   sz.nprob = nprob;
   grid_of.resize(nprob);
   for (int i = 0; i < nprob; ++i) {
@@ -102,9 +117,19 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
     sz.nreduce += chunks > 1;
     sz.eig[m_bucket(p.M)] += 1;
     sz.njobs += __builtin_popcount(p.alg_mask);
-    if (p.geom.pos) {   // 2-D scan: no ULA phase table
+    if (p.geom.pos) {   // 2-D scan: trigonometric tables of its azimuth x elevation grid
       sz.geo[m_bucket(p.M)] += 1;
-      grid_of[i] = -1;
+      int g = -1;
+      for (size_t k = 0; k < geo_grids.size(); ++k)
+        if (same_geo_grid(geo_grids[k], p)) {
+          g = (int)k;
+          break;
+        }
+      if (g < 0) {
+        g = (int)geo_grids.size();
+        geo_grids.push_back(GeoGridKey{p.grid, p.geom.el_lo_deg, p.geom.el_step_deg, p.geom.Le});
+      }
+      grid_of[i] = g;
       continue;
     }
     if (p.prec == DOA_FP32)
@@ -124,11 +149,12 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
     grid_of[i] = g;
   }
   sz.ngrids = (int)grids.size();
+  sz.ngeo_grids = (int)geo_grids.size();
   return true;
 }
 
 struct PlanOffsets {
-  int64_t prob, job, grid, cov, reduce, eig[kNumBuckets], scan[kNumBuckets], tc, geo[kNumBuckets], total;
+  int64_t prob, job, grid, cov, reduce, eig[kNumBuckets], scan[kNumBuckets], tc, geo[kNumBuckets], geo_grid, total;
 };
 
 PlanOffsets plan_offsets(const PlanSizes &sz) {
@@ -158,6 +184,8 @@ PlanOffsets plan_offsets(const PlanSizes &sz) {
     o.geo[b] = at;
     at = round_up(at + (int64_t)sz.geo[b] * 4, 16);
   }
+  o.geo_grid = at;
+  at = round_up(at + (int64_t)sz.ngeo_grids * sizeof(PlanGeoGrid), 16);
   o.total = at;
   return o;
 }
@@ -278,12 +306,19 @@ doa_status doa_peaks(const float *P, int L, int d, int *idx, float *val, int *co
   return cuda_status(launch_peaks_single(P, L, d, idx, val, count, as_stream(stream)));
 }
 
-doa_status doa_scan_geometry(const double *B, int M, int K, doa_grid az, doa_geometry geom, float *P, void *stream) {
-  if (!B || !P || M < 2 || M > kMaxM || K < 1 || K > M || !geometry_ok(az, geom)) return DOA_EINVAL;
-  if (!aligned(B, 16) || !aligned(P, 4)) return DOA_EINVAL;
+size_t doa_scan_geometry_ws_bytes(int La, int Le) {
+  if (La < 1 || Le < 1) return 0;
+  return (size_t)geo_table_bytes(La, Le);
+}
+
+doa_status doa_scan_geometry(const double *B, int M, int K, doa_grid az, doa_geometry geom, float *P, void *ws,
+                             size_t ws_bytes, void *stream) {
+  if (!B || !P || !ws || M < 2 || M > kMaxM || K < 1 || K > M || !geometry_ok(az, geom)) return DOA_EINVAL;
+  if (!aligned(B, 16) || !aligned(P, 4) || !aligned(ws, 16)) return DOA_EINVAL;
+  if (ws_bytes < (size_t)geo_table_bytes(az.L, geom.Le)) return DOA_ENOMEM;
   return cuda_status(launch_scan_geometry_single(reinterpret_cast<const double2 *>(B), M, K, geom.pos, az.lo_deg,
                                                  az.step_deg, az.L, geom.el_lo_deg, geom.el_step_deg, geom.Le, P,
-                                                 as_stream(stream)));
+                                                 static_cast<uint8_t *>(ws), as_stream(stream)));
 }
 
 doa_status doa_peaks2d(const float *P, int La, int Le, int wrap_az, int d, int *idx, float *val, int *count,
@@ -300,7 +335,8 @@ size_t doa_batch_plan_bytes(const doa_problem *probs, int nprob) {
   PlanSizes sz;
   std::vector<doa_grid> grids;
   std::vector<int> grid_of;
-  if (!count_plan(probs, nprob, sz, grids, grid_of, nullptr)) return 0;
+  std::vector<GeoGridKey> geo_grids;
+  if (!count_plan(probs, nprob, sz, grids, grid_of, geo_grids, nullptr)) return 0;
   return (size_t)plan_offsets(sz).total;
 }
 
@@ -317,7 +353,8 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
   PlanSizes sz;
   std::vector<doa_grid> grids;
   std::vector<int> grid_of;
-  if (!count_plan(probs, nprob, sz, grids, grid_of, bad_index)) return DOA_EINVAL;
+  std::vector<GeoGridKey> geo_grids;
+  if (!count_plan(probs, nprob, sz, grids, grid_of, geo_grids, bad_index)) return DOA_EINVAL;
   const PlanOffsets o = plan_offsets(sz);
   if (!plan || plan_bytes < (size_t)o.total) return DOA_ENOMEM;
   uint8_t *base = static_cast<uint8_t *>(plan);
@@ -368,6 +405,25 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     ws = round_up(ws + (int64_t)grids[g].L * 8, 256);
     h.grid_points += grids[g].L;
   }
+  // workspace: trigonometric tables of the geometry grids (FP64 then FP32 entries)
+  PlanGeoGrid *pgg = reinterpret_cast<PlanGeoGrid *>(base + o.geo_grid);
+  h.off_geo_grid = o.geo_grid;
+  h.ngeo_grids = sz.ngeo_grids;
+  for (int g = 0; g < sz.ngeo_grids; ++g) {
+    const GeoGridKey &k = geo_grids[g];
+    PlanGeoGrid &e = pgg[g];
+    e.az_lo = k.az.lo_deg;
+    e.az_step = k.az.step_deg;
+    e.el_lo = k.el_lo;
+    e.el_step = k.el_step;
+    e.La = k.az.L;
+    e.Le = k.Le;
+    e.t64_off = ws;
+    ws = round_up(ws + 16 * ((int64_t)e.La + e.Le), 256);
+    e.t32_off = ws;
+    ws = round_up(ws + 8 * ((int64_t)e.La + e.Le), 256);
+    h.geo_grid_points = std::max(h.geo_grid_points, e.La + e.Le);
+  }
   int icov[kCovClasses], ired = 0, ijob = 0;
   h.cov_first[0] = 0;
   for (int c = 0; c < kCovClasses; ++c) {
@@ -393,7 +449,8 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     }
     for (int c = 0; c < q.nchunks; ++c) cov[icov[cov_class(M)]++] = PlanCovItem{i, c};
     eig[b][ie[b]++] = i;
-    q.grid_id = grid_of[i];
+    q.grid_id = p.geom.pos ? -1 : grid_of[i];
+    q.geo_grid = p.geom.pos ? grid_of[i] : -1;
     q.first_job = ijob;
     int slot = 0;
     for (int a = 0; a < 4; ++a) {
@@ -450,7 +507,8 @@ doa_status doa_solve_batch(const void *plan_host, const void *plan_dev, void *ws
   auto mark = [&](int i) -> bool {
     return !stage_events || cudaEventRecord(static_cast<cudaEvent_t>(stage_events[i]), s) == cudaSuccess;
   };
-  if (!mark(0) || launch_grid_tables(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
+  if (!mark(0) || launch_grid_tables(pd, h, w, s) != cudaSuccess || launch_geo_tables(pd, h, w, s) != cudaSuccess)
+    return DOA_ECUDA;
   if (!mark(1) || launch_covariance_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
   if (!mark(2) || launch_eig_batch(pd, h, w, status, s) != cudaSuccess) return DOA_ECUDA;
   if (!mark(3) || launch_scan_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;

@@ -154,7 +154,7 @@ struct PlanProblem {
   int32_t kphd, kmn;      // columns read by PHD (v_min) and MN (valph), -1 if absent
   int32_t slot[4];        // output row of each algorithm (doa_alg order), -1 if not requested
   int32_t npts;           // points of one spectrum: L, or La x Le for a geometry problem
-  int32_t pad;
+  int32_t geo_grid;       // geometry problems: index of the azimuth x elevation grid's tables
 };
 
 // Bytes of a problem's scan factor area: F (M x (M+1) complex128) + EV weights (M doubles).
@@ -173,6 +173,16 @@ struct PlanGrid {
   int32_t pad;
   int64_t S_off;          // byte offset of the phase table (L x uint32) in the workspace
   int64_t S64_off;        // byte offset of the 64-bit phase table (L x uint64) in the workspace
+};
+
+// Azimuth x elevation grid of geometry problems, with its trigonometric tables in the workspace:
+// (sin, cos) of theta_k = az_lo + k az_step (k < La) followed by those of phi_l = el_lo + l el_step
+// (l < Le), evaluated in FP64 (rounded multiply, rounded add, then sincospi of the angle / 180).
+struct PlanGeoGrid {
+  double az_lo, az_step, el_lo, el_step;
+  int32_t La, Le;
+  int64_t t32_off;        // float2[La + Le], the FP64 values rounded once
+  int64_t t64_off;        // double2[La + Le]
 };
 
 struct PlanCovItem {
@@ -207,10 +217,13 @@ struct PlanHeader {
   int32_t geo_jobs[kNumBuckets];
   int64_t geo_tiles[kNumBuckets];
   int64_t off_geo[kNumBuckets];
+  int32_t ngeo_grids;                    // distinct azimuth x elevation grids
+  int32_t geo_grid_points;               // largest La + Le among them
+  int64_t off_geo_grid;
 };
 
 // The Python binding reads these header fields by position (int32 index 22 = scan_pt, 58 = eig_mats,
-// 62 = cov_first, 67 = tc_jobs, 74 = npolish, 76 = geo_jobs).
+// 62 = cov_first, 67 = tc_jobs, 74 = npolish, 76 = geo_jobs, 96 = ngeo_grids).
 static_assert(offsetof(PlanHeader, scan_pt) == 88, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, scan_tiles) == 56, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, eig_mats) == 232, "PlanHeader layout changed");
@@ -218,6 +231,7 @@ static_assert(offsetof(PlanHeader, cov_first) == 248, "PlanHeader layout changed
 static_assert(offsetof(PlanHeader, tc_jobs) == 268, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, npolish) == 296, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, geo_jobs) == 304, "PlanHeader layout changed");
+static_assert(offsetof(PlanHeader, ngeo_grids) == 384, "PlanHeader layout changed");
 
 // Scan tiles: kScanThreads threads, each evaluating PT consecutive grid points (tile shape
 // 128 x PT). PT is chosen per M bucket (the autotuner's knob); the register budget limits it
@@ -277,9 +291,12 @@ __host__ __device__ inline int tc_batch_cols(int Kf) {   // TMEM columns: 2 buff
 cudaError_t launch_scan_tc_single(const double2 *B, int M, int K, int L, double lo, double step, int prec,
                                   const uint32_t *S, float *P, cudaStream_t s);
 
+// Bytes of the trigonometric tables of an La x Le geometry grid (float2 and double2 per angle).
+__host__ __device__ inline int64_t geo_table_bytes(int64_t La, int64_t Le) { return 24 * (La + Le); }
 cudaError_t launch_scan_geometry_single(const double2 *B, int M, int K, const double *pos, double az_lo,
                                         double az_step, int La, double el_lo, double el_step, int Le, float *P,
-                                        cudaStream_t s);
+                                        uint8_t *ws, cudaStream_t s);
+cudaError_t launch_geo_tables(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
 cudaError_t launch_scan_geometry_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
 
 cudaError_t launch_peaks_single(const float *P, int L, int d, int *idx, float *val, int *count,

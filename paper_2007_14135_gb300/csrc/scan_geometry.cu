@@ -8,22 +8,24 @@
 // span rows) and the contraction and readouts are those of the ULA scan (scan_common.cuh): one
 // factor F = [E_n | valph] per problem feeds MUSIC, EV, PHD and MN.
 //
-// FP32 steering. The direction angles are formed in half turns, h = h0 + k hs with h0 reduced to
-// [-1, 1) and h0, hs split into FP32 hi + lo parts (two roundings, relative 2 eps, whatever the
-// step), and sincospif reduces them exactly. The element phase t_m = p_m . (u, v, w) (turns) uses the positions relative to their
-// centroid: that subtracts a common phase from every element, which leaves ||F^H a|| unchanged and
-// keeps |t_m| at most the array's radius. The fraction t_m - rint(t_m) becomes a 32-bit phase and
-// phasor_q32 turns it into cos + j sin.
+// Trigonometric tables. sin and cos of every azimuth theta_k and elevation angle phi_l of the
+// grid are evaluated once per grid in FP64 (rounded multiply and add for the angle, then sincospi
+// of angle / 180) and kept as FP64 and as FP32 (rounded once) in the workspace; a point reads
+// its row's and column's entries, u = sin(theta) sin(phi), v = cos(theta) sin(phi), w = cos(phi).
+//
+// FP32 steering. The element phase t_m = p_m . (u, v, w) (turns) uses the positions relative to
+// their centroid: that subtracts a common phase from every element, which leaves ||F^H a||
+// unchanged and keeps |t_m| at most the array's radius. The fraction t_m - rint(t_m) becomes a
+// 32-bit phase and phasor_q32 turns it into cos + j sin.
 //
 // Refinement. The FP32 phasor error is bounded (in units of eps = 2^-24) by
-//   eps_a = 2 pi rho (2 pi (x_az + x_el) + 9) + 3,
-// where rho = max_m (|x_m| + |y_m| + |z_m|) of the centred positions and x_az, x_el bound the
-// half-turn arguments over the grid: each argument is rounded twice (2 eps x), sincospif adds an
-// ulp (2 eps), the direction cosines one product, the positions one rounding and the phase three
-// fma roundings (each eps rho), and phasor_q32 about 3 eps. With
-// the factor's own rounding, eps_a + 3 per term replaces the 4 eps per term of the ULA scan, so the
-// refinement thresholds of scan_common.cuh scale by ((eps_a + 3) / 4)^2. Points below them are
-// re-evaluated with FP64 angles (sincospi), FP64 phases and the FP64 factor (warp per point).
+//   eps_a = 2 pi rho (3 + 1 + 3) + 3,
+// where rho = max_m (|x_m| + |y_m| + |z_m|) of the centred positions: the direction cosines carry
+// 3 eps (two table roundings and the product), the positions one rounding and the phase three fma
+// roundings (each eps rho), and phasor_q32 about 3 eps. With the factor's own rounding, eps_a + 3
+// per term replaces the 4 eps per term of the ULA scan, so the refinement thresholds of
+// scan_common.cuh scale by ((eps_a + 3) / 4)^2. Points below them are re-evaluated with the FP64
+// tables, FP64 phases and the FP64 factor (warp per point).
 #include <float.h>
 
 #include "doa_internal.cuh"
@@ -36,34 +38,56 @@ using namespace scanc;
 
 struct GeoParams {
   const double *pos;     // M x 3 FP64 positions (wavelengths)
-  double az_lo, az_step, el_lo, el_step;
+  const float2 *t32;     // (sin, cos): La azimuths, then Le elevation angles
+  const double2 *t64;
   int La, Le;
 };
 
 struct GeoShared {
   float4 p32[kMaxM];     // centred positions in FP32 (x, y, z, 0); rows >= M zero
   double cen[3];         // centroid (FP64)
-  float a0h, a0l, ash, asl;  // azimuth origin and step in half turns, hi + lo
-  float e0h, e0l, esh, esl;  // elevation origin and step in half turns, hi + lo
 };
+
+// (sin, cos) table entry e of a grid: e < La the azimuth theta_e, else the elevation angle
+// phi_(e - La), each angle as lo + index * step in FP64 (rounded multiply, rounded add).
+__device__ __forceinline__ void geo_table_entry(double az_lo, double az_step, int La, double el_lo, double el_step,
+                                                int e, float2 *t32, double2 *t64) {
+  const double ang = e < La ? __dadd_rn(az_lo, __dmul_rn((double)e, az_step))
+                            : __dadd_rn(el_lo, __dmul_rn((double)(e - La), el_step));
+  double sn, cs;
+  sincospi(ang / 180.0, &sn, &cs);
+  t64[e] = make_double2(sn, cs);
+  t32[e] = make_float2((float)sn, (float)cs);
+}
+
+__global__ void geo_table_single_kernel(double az_lo, double az_step, int La, double el_lo, double el_step, int Le,
+                                        float2 *t32, double2 *t64) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < La + Le) geo_table_entry(az_lo, az_step, La, el_lo, el_step, e, t32, t64);
+}
+
+__global__ void geo_table_batch_kernel(const uint8_t *plan, uint8_t *ws) {
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
+  const PlanGeoGrid g = reinterpret_cast<const PlanGeoGrid *>(plan + h->off_geo_grid)[blockIdx.y];
+  float2 *t32 = reinterpret_cast<float2 *>(ws + g.t32_off);
+  double2 *t64 = reinterpret_cast<double2 *>(ws + g.t64_off);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < g.La + g.Le; e += gridDim.x * blockDim.x)
+    geo_table_entry(g.az_lo, g.az_step, g.La, g.el_lo, g.el_step, e, t32, t64);
+}
 
 // FP64 steering source of the refinement: flat point i -> (u, v, w), then the phase of element m.
 struct GeoSource {
   const double *pos;
+  const double2 *t64;
   double cx, cy, cz;
-  double az_lo, az_step, el_lo, el_step;
   int La;
   struct Dir {
     double u, v, w;
   };
   __device__ __forceinline__ Dir prep(int i) const {
     const int l = i / La, k = i - l * La;
-    const double th = __dadd_rn(az_lo, __dmul_rn((double)k, az_step));
-    const double ph = __dadd_rn(el_lo, __dmul_rn((double)l, el_step));
-    double st, ct, sp, cp;
-    sincospi(th / 180.0, &st, &ct);
-    sincospi(ph / 180.0, &sp, &cp);
-    return Dir{st * sp, ct * sp, cp};
+    const double2 a = t64[k], e = t64[La + l];
+    return Dir{a.x * e.x, a.y * e.x, e.y};
   }
   __device__ __forceinline__ double2 phasor(const Dir &d, int m) const {
     const double t = (pos[3 * m] - cx) * d.u + (pos[3 * m + 1] - cy) * d.v + (pos[3 * m + 2] - cz) * d.w;
@@ -72,13 +96,8 @@ struct GeoSource {
   }
 };
 
-__device__ __forceinline__ void split_f(double x, float &hi, float &lo) {
-  hi = (float)x;
-  lo = (float)(x - (double)hi);
-}
-
-// Per-job constants: centroid, FP32 positions, angle splits, and the scaled thresholds. Every
-// thread of the CTA calls it after load_job; it ends with a barrier.
+// Per-job constants: centroid, FP32 positions and the scaled thresholds. Every thread of the CTA
+// calls it after load_job; it ends with a barrier.
 template <int MP>
 __device__ void geo_setup(const float2 *Bs, const ScanJob &j, const GeoParams &g, GeoShared &gs, ScanShared &sh) {
   if (threadIdx.x == 0) {
@@ -91,14 +110,6 @@ __device__ void geo_setup(const float2 *Bs, const ScanJob &j, const GeoParams &g
     gs.cen[0] = cx / j.M;
     gs.cen[1] = cy / j.M;
     gs.cen[2] = cz / j.M;
-    double a0 = g.az_lo / 180.0, e0 = g.el_lo / 180.0;
-    a0 -= 2.0 * rint(0.5 * a0);
-    e0 -= 2.0 * rint(0.5 * e0);
-    const double as = g.az_step / 180.0, es = g.el_step / 180.0;
-    split_f(a0, gs.a0h, gs.a0l);
-    split_f(as, gs.ash, gs.asl);
-    split_f(e0, gs.e0h, gs.e0l);
-    split_f(es, gs.esh, gs.esl);
   }
   __syncthreads();
   for (int m = threadIdx.x; m < MP; m += blockDim.x) {
@@ -115,10 +126,7 @@ __device__ void geo_setup(const float2 *Bs, const ScanJob &j, const GeoParams &g
     for (int m = 0; m < j.M; ++m)
       rho = fmax(rho, fabs(g.pos[3 * m] - gs.cen[0]) + fabs(g.pos[3 * m + 1] - gs.cen[1]) +
                           fabs(g.pos[3 * m + 2] - gs.cen[2]));
-    const double xa = fabs(g.az_lo / 180.0 - 2.0 * rint(g.az_lo / 360.0)) + (g.La - 1) * fabs(g.az_step / 180.0);
-    const double xe = fabs(g.el_lo / 180.0 - 2.0 * rint(g.el_lo / 360.0)) + (g.Le - 1) * fabs(g.el_step / 180.0);
-    const double kPi = 3.141592653589793;
-    const double ea = 2.0 * kPi * rho * (2.0 * kPi * (xa + xe) + 9.0) + 3.0;
+    const double ea = 2.0 * 3.141592653589793 * rho * 7.0 + 3.0;
     double sc = (ea + 3.0) / 4.0;
     sc = fmax(sc * sc, 1.0);
     for (int r = 0; r < 4; ++r) sh.thr[r] = (float)(sh.thr[r] * sc);
@@ -127,20 +135,17 @@ __device__ void geo_setup(const float2 *Bs, const ScanJob &j, const GeoParams &g
 }
 
 template <int MP, int PT>
-__device__ __forceinline__ void geo_points(const float2 *Bs, const ScanJob &j, const GeoShared &gs, int La, int npts,
-                                           int i0, ScanShared &sh, const GeoSource &src) {
+__device__ __forceinline__ void geo_points(const float2 *Bs, const ScanJob &j, const GeoShared &gs,
+                                           const float2 *__restrict__ t32, int La, int Le, int npts, int i0,
+                                           ScanShared &sh, const GeoSource &src) {
   static_assert(MP % 4 == 0, "MP is a multiple of 4");
   float2 a[PT][MP];
   int l = i0 / La, k = i0 - l * La;
 #pragma unroll
   for (int q = 0; q < PT; ++q) {
-    const float kf = (float)k, lf = (float)l;
-    const float ha = fmaf(kf, gs.ash, gs.a0h) + fmaf(kf, gs.asl, gs.a0l);
-    const float he = fmaf(lf, gs.esh, gs.e0h) + fmaf(lf, gs.esl, gs.e0l);
-    float sa, ca, se, ce;
-    sincospif(ha, &sa, &ca);
-    sincospif(he, &se, &ce);
-    const float u = sa * se, v = ca * se, w = ce;
+    // points past the end (l >= Le) read a valid entry and are never stored
+    const float2 ta = __ldg(t32 + k), te = __ldg(t32 + La + min(l, Le - 1));
+    const float u = ta.x * te.x, v = ta.y * te.x, w = te.y;
 #pragma unroll
     for (int m = 0; m < MP; ++m) {
       const float4 p = gs.p32[m];
@@ -159,13 +164,10 @@ __device__ __forceinline__ void geo_points(const float2 *Bs, const ScanJob &j, c
 __device__ __forceinline__ GeoSource make_source(const GeoParams &g, const GeoShared &gs) {
   GeoSource s;
   s.pos = g.pos;
+  s.t64 = g.t64;
   s.cx = gs.cen[0];
   s.cy = gs.cen[1];
   s.cz = gs.cen[2];
-  s.az_lo = g.az_lo;
-  s.az_step = g.az_step;
-  s.el_lo = g.el_lo;
-  s.el_step = g.el_step;
   s.La = g.La;
   return s;
 }
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_geometry_single_kernel(cons
   const int npts = g.La * g.Le;
   const GeoSource src = make_source(g, gs);
   const int i0 = (blockIdx.x * kScanThreads + threadIdx.x) * PT;
-  geo_points<MP, PT>(Bs, j, gs, g.La, npts, i0, sh, src);
+  geo_points<MP, PT>(Bs, j, gs, g.t32, g.La, g.Le, npts, i0, sh, src);
   drain_refinements_src(j, src, sh);
 }
 
@@ -208,6 +210,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_geometry_batch_kernel(const
   const int64_t ntiles = h->geo_tiles[bucket];
   const int32_t *list = reinterpret_cast<const int32_t *>(plan + h->off_geo[bucket]);
   const PlanProblem *probs = reinterpret_cast<const PlanProblem *>(plan + h->off_prob);
+  const PlanGeoGrid *geo_grids = reinterpret_cast<const PlanGeoGrid *>(plan + h->off_geo_grid);
   constexpr int TP = kScanThreads * PT;
   int cur = -1;
   ScanJob j{};
@@ -238,13 +241,12 @@ __global__ void __launch_bounds__(kScanThreads) scan_geometry_batch_kernel(const
         j.kphd = pp->kphd;
         j.kmn = pp->kmn;
         j.kofs = 0;
+        const PlanGeoGrid &gg = geo_grids[pp->geo_grid];
         g.pos = pp->p.geom.pos;
-        g.az_lo = pp->p.grid.lo_deg;
-        g.az_step = pp->p.grid.step_deg;
-        g.el_lo = pp->p.geom.el_lo_deg;
-        g.el_step = pp->p.geom.el_step_deg;
-        g.La = pp->p.grid.L;
-        g.Le = pp->p.geom.Le;
+        g.t32 = reinterpret_cast<const float2 *>(ws + gg.t32_off);
+        g.t64 = reinterpret_cast<const double2 *>(ws + gg.t64_off);
+        g.La = gg.La;
+        g.Le = gg.Le;
         __syncthreads();
         load_job<MP>(j, Bs, sh);
         __syncthreads();
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_geometry_batch_kernel(const
         cur = u;
       }
       const int i0 = (int)(t - pp->tile_start) * TP + threadIdx.x * PT;
-      geo_points<MP, PT>(Bs, j, gs, g.La, pp->npts, i0, sh, src);
+      geo_points<MP, PT>(Bs, j, gs, g.t32, g.La, g.Le, pp->npts, i0, sh, src);
       drain_refinements_src(j, src, sh);
     }
   }
@@ -289,8 +291,11 @@ cudaError_t run_geo_batch(const uint8_t *plan, const PlanHeader &h, uint8_t *ws,
 
 cudaError_t launch_scan_geometry_single(const double2 *B, int M, int K, const double *pos, double az_lo,
                                         double az_step, int La, double el_lo, double el_step, int Le, float *P,
-                                        cudaStream_t s) {
-  GeoParams g{pos, az_lo, az_step, el_lo, el_step, La, Le};
+                                        uint8_t *ws, cudaStream_t s) {
+  double2 *t64 = reinterpret_cast<double2 *>(ws);
+  float2 *t32 = reinterpret_cast<float2 *>(ws + 16 * ((int64_t)La + Le));
+  geo_table_single_kernel<<<(La + Le + 255) / 256, 256, 0, s>>>(az_lo, az_step, La, el_lo, el_step, Le, t32, t64);
+  GeoParams g{pos, t32, t64, La, Le};
   const int b = m_bucket(M);
   const int pt = scan_pt_default(b);
   const int64_t npts = (int64_t)La * Le;
@@ -301,6 +306,13 @@ cudaError_t launch_scan_geometry_single(const double2 *B, int M, int K, const do
     case 2: scan_geometry_single_kernel<32, 1><<<grid, kScanThreads, 0, s>>>(B, M, K, g, P); break;
     default: scan_geometry_single_kernel<64, 1><<<grid, kScanThreads, 0, s>>>(B, M, K, g, P); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_geo_tables(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s) {
+  if (h.ngeo_grids == 0) return cudaSuccess;
+  const int bx = (h.geo_grid_points + 255) / 256;
+  geo_table_batch_kernel<<<dim3(bx, h.ngeo_grids), 256, 0, s>>>(plan_dev, ws);
   return cudaGetLastError();
 }
 

@@ -30,7 +30,7 @@ EXPORTS = ("doa_status_str", "doa_covariance", "doa_covariance_noalloc", "doa_no
            "doa_peaks", "doa_batch_plan_bytes", "doa_batch_plan", "doa_solve_batch", "doa_mlp_workspace_bytes",
            "doa_mlp_refresh", "doa_mlp_forward", "doa_mlp_backward", "doa_mlp_adam", "doa_synth_ula",
            "doa_proposal_windows", "doa_scan_windows", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices", "doa_probe_fma",
-           "doa_scan_geometry", "doa_peaks2d")
+           "doa_scan_geometry", "doa_scan_geometry_ws_bytes", "doa_peaks2d")
 SLICE_MAXD = 64
 
 
@@ -90,11 +90,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.doa_slice_peaks.argtypes = [vp, i, i, i, i, i, vp, vp]
     lib.doa_merge_slices.argtypes = [vp, i, i, vp, vp, vp]
     lib.doa_probe_fma.argtypes = [i, i, i, vp, ctypes.POINTER(ctypes.c_double), vp]
-    lib.doa_scan_geometry.argtypes = [vp, i, i, Grid, Geometry, vp, vp]
+    lib.doa_scan_geometry.argtypes = [vp, i, i, Grid, Geometry, vp, vp, sz, vp]
+    lib.doa_scan_geometry_ws_bytes.argtypes = [i, i]
+    lib.doa_scan_geometry_ws_bytes.restype = sz
     lib.doa_peaks2d.argtypes = [vp, i, i, i, i, vp, vp, vp, vp]
     for name in ("doa_covariance", "doa_covariance_noalloc", "doa_noise_subspace", "doa_scan", "doa_peaks",
                  "doa_batch_plan", "doa_solve_batch", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices", "doa_probe_fma",
-                 "doa_scan_geometry", "doa_peaks2d"):
+                 "doa_scan_geometry", "doa_scan_geometry_ws_bytes", "doa_peaks2d"):
         getattr(lib, name).restype = i
     return lib
 
@@ -235,9 +237,14 @@ def doa_peaks(P: torch.Tensor, d: int, idx: torch.Tensor, val: torch.Tensor, cou
 
 
 def doa_scan_geometry(B: torch.Tensor, M: int, K: int, az: Grid, geom: Geometry, P: torch.Tensor,
-                      stream=None) -> None:
-    """2-D scan P[l * La + k] over azimuth az (columns) and the rows of geom (Eq. 2 as printed)."""
-    _check(lib().doa_scan_geometry(_dev(B), M, K, az, geom, _dev(P), _stream(stream)), "doa_scan_geometry")
+                      ws: Optional[torch.Tensor] = None, stream=None) -> None:
+    """2-D scan P[l * La + k] over azimuth az (columns) and the rows of geom (Eq. 2 as printed).
+    ws: device scratch for the grid's sin / cos tables (allocated here when None)."""
+    need = lib().doa_scan_geometry_ws_bytes(az.L, geom.Le)
+    if ws is None:
+        ws = torch.empty(max(need, 16), dtype=torch.uint8, device=B.device)
+    _check(lib().doa_scan_geometry(_dev(B), M, K, az, geom, _dev(P), _dev(ws), ws.numel() * ws.element_size(),
+                                   _stream(stream)), "doa_scan_geometry")
 
 
 def doa_peaks2d(P: torch.Tensor, La: int, Le: int, wrap_az: bool, d: int, idx: torch.Tensor, val: torch.Tensor,
@@ -302,7 +309,7 @@ class BatchPlan:
         """int32 index of a PlanHeader field (layout of csrc/doa_internal.cuh)."""
         order = {"magic": 0, "nprob": 1, "njobs": 2, "ngrids": 3, "ncov": 4, "nreduce": 5, "eig_count": 6,
                  "scan_jobs": 10, "scan_tiles": 14, "scan_pt": 22, "eig_mats": 58, "cov_first": 62, "tc_jobs": 67,
-                 "npolish": 74, "geo_jobs": 76}
+                 "npolish": 74, "geo_jobs": 76, "ngeo_grids": 96}
         return order[field]
 
     def launches(self) -> int:
@@ -313,7 +320,7 @@ class BatchPlan:
         eig_b = sum(int(c) > 0 for c in h[6:10])
         scan_b = sum(int(c) > 0 for c in h[10:14]) + int(h[67] > 0) + sum(int(c) > 0 for c in h[76:80])
         peaks = 1 + (2 if int(h[74]) > 0 else 0)
-        return 1 + cov + eig_b + scan_b + peaks
+        return int(h[3] > 0) + int(h[96] > 0) + cov + eig_b + scan_b + peaks
 
 
 def doa_solve_batch(plan: BatchPlan, ws: torch.Tensor, status: torch.Tensor, stage_events=None,

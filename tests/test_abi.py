@@ -188,16 +188,20 @@ def test_geometry_argument_errors(libdoa):
     def geo(pos=0x20000, Le=90, wrap=1, el_lo=1.0, el_step=1.0):
         return libdoa.Geometry(pos, el_lo, el_step, Le, wrap)
 
-    assert L.doa_scan_geometry(fake, 8, 0, az, geo(), fake, None) == libdoa.EINVAL        # K < 1
-    assert L.doa_scan_geometry(fake, 8, 9, az, geo(), fake, None) == libdoa.EINVAL        # K > M
-    assert L.doa_scan_geometry(fake, 8, 6, az, geo(pos=None), fake, None) == libdoa.EINVAL
-    assert L.doa_scan_geometry(fake, 8, 6, az, geo(pos=0x20004), fake, None) == libdoa.EINVAL   # 8-byte alignment
-    assert L.doa_scan_geometry(fake, 8, 6, az, geo(Le=0), fake, None) == libdoa.EINVAL
-    assert L.doa_scan_geometry(fake, 8, 6, az, geo(wrap=2), fake, None) == libdoa.EINVAL
-    assert L.doa_scan_geometry(fake, 8, 6, az, geo(el_step=float("nan")), fake, None) == libdoa.EINVAL
-    assert L.doa_scan_geometry(fake, 8, 6, libdoa.grid(0.0, 1.0, 0), geo(), fake, None) == libdoa.EINVAL
-    assert L.doa_scan_geometry(fake, 8, 6, libdoa.grid(0.0, 1.0, 1 << 16), geo(Le=1 << 15), fake, None) == libdoa.EINVAL
-    assert L.doa_scan_geometry(fake, 8, 6, az, geo(), ctypes.c_void_p(0x10002), None) == libdoa.EINVAL
+    assert L.doa_scan_geometry(fake, 8, 0, az, geo(), fake, fake, 1 << 20, None) == libdoa.EINVAL   # K < 1
+    assert L.doa_scan_geometry(fake, 8, 9, az, geo(), fake, fake, 1 << 20, None) == libdoa.EINVAL        # K > M
+    assert L.doa_scan_geometry(fake, 8, 6, az, geo(pos=None), fake, fake, 1 << 20, None) == libdoa.EINVAL
+    assert L.doa_scan_geometry(fake, 8, 6, az, geo(pos=0x20004), fake, fake, 1 << 20, None) == libdoa.EINVAL   # 8-byte alignment
+    assert L.doa_scan_geometry(fake, 8, 6, az, geo(Le=0), fake, fake, 1 << 20, None) == libdoa.EINVAL
+    assert L.doa_scan_geometry(fake, 8, 6, az, geo(wrap=2), fake, fake, 1 << 20, None) == libdoa.EINVAL
+    assert L.doa_scan_geometry(fake, 8, 6, az, geo(el_step=float("nan")), fake, fake, 1 << 20, None) == libdoa.EINVAL
+    assert L.doa_scan_geometry(fake, 8, 6, libdoa.grid(0.0, 1.0, 0), geo(), fake, fake, 1 << 20, None) == libdoa.EINVAL
+    assert L.doa_scan_geometry(fake, 8, 6, libdoa.grid(0.0, 1.0, 1 << 16), geo(Le=1 << 15), fake, fake, 1 << 20, None) == libdoa.EINVAL
+    assert L.doa_scan_geometry(fake, 8, 6, az, geo(), ctypes.c_void_p(0x10002), fake, 1 << 20, None) == libdoa.EINVAL
+    assert L.doa_scan_geometry(fake, 8, 6, az, geo(), fake, None, 1 << 20, None) == libdoa.EINVAL    # no scratch
+    assert L.doa_scan_geometry(fake, 8, 6, az, geo(), fake, ctypes.c_void_p(0x10008), 1 << 20, None) == libdoa.EINVAL
+    assert L.doa_scan_geometry(fake, 8, 6, az, geo(), fake, fake, 24 * 450 - 1, None) == libdoa.ENOMEM
+    assert L.doa_scan_geometry_ws_bytes(360, 90) == 24 * 450 and L.doa_scan_geometry_ws_bytes(0, 90) == 0
     assert L.doa_peaks2d(fake, 0, 5, 0, 1, fake, fake, fake, None) == libdoa.EINVAL
     assert L.doa_peaks2d(fake, 5, 5, 3, 1, fake, fake, fake, None) == libdoa.EINVAL
     assert L.doa_peaks2d(fake, 5, 5, 0, 64, fake, fake, fake, None) == libdoa.EINVAL
@@ -228,6 +232,7 @@ def test_batch_plan_geometry_problems(libdoa):
     h32 = buf[:512].view(np.int32)
     h64 = buf[:512].view(np.int64)
     assert h32[3] == 1                                  # ngrids: only the ULA problem's grid
+    assert h32[96] == 3                                 # geometry grids: 360 x 90, 97 x 13, 1 x 1
     assert list(h32[10:14]) == [1, 0, 0, 0]             # ULA scan lists
     assert list(h32[76:80]) == [2, 1, 0, 0]             # geometry scan lists per M bucket
     pt = list(h32[22:26])
