@@ -778,14 +778,15 @@ def run_uca(args):
         build.build()
     if world > 1:
         dist.barrier()
-    from paper_2007_14135_gb300 import doa, shard
+    from paper_2007_14135_gb300 import autotune, doa, shard
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     Mu, du = g0.M, g0.d
+    tune_log = []
     pos = torch.from_numpy(np.ascontiguousarray(g0.pos)).to(dev)
     az = doa.grid(g0.az_lo, g0.az_step, g0.La)
 
-    def build_batch(X, rows):
+    def build_batch(X, rows, tuning=None):
         npts = g0.La * rows
         P = torch.empty((X.shape[0], npts), dtype=torch.float32, device=dev)
         idx = torch.empty((X.shape[0], du), dtype=torch.int32, device=dev)
@@ -794,7 +795,10 @@ def run_uca(args):
         geom = doa.geometry(pos, float(91 - rows), 1.0, rows, True)
         probs = [doa.make_problem(X[i], du, 1 << doa.MUSIC, az, P[i], idx[i], val[i], cnt[i:i + 1], geom=geom)
                  for i in range(X.shape[0])]
-        plan = doa.BatchPlan(probs, device=str(dev))
+        if tuning == "tune":
+            tuning = autotune.tune(probs, device=str(dev), log=tune_log)
+        sp, em = tuning if tuning else (None, None)
+        plan = doa.BatchPlan(probs, device=str(dev), scan_pt=sp, eig_mats=em)
         ws = doa.workspace(plan, device=str(dev))
         status = torch.empty(X.shape[0], dtype=torch.int32, device=dev)
         return dict(P=P, idx=idx, val=val, cnt=cnt, plan=plan, ws=ws, status=status, probs=probs)
@@ -823,7 +827,7 @@ def run_uca(args):
         return e0.elapsed_time(e1) / steps
 
     X = torch.from_numpy(Xh).to(dev)
-    bt = build_batch(X, Le)
+    bt = build_batch(X, Le, None if args.no_tune else "tune")
     nst = doa.BATCH_STAGES + 1
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nst)] for _ in range(3)]
     for k in range(3):
@@ -900,7 +904,14 @@ def run_uca(args):
                 o.copy_(t, non_blocking=True)
             torch.cuda.synchronize(dev)
             wall.append(time.perf_counter() - a)
+        sev = [[torch.cuda.Event(enable_timing=True) for _ in range(nst)] for _ in range(20)]
+        for k in range(20):
+            doa.doa_solve_batch(b1["plan"], b1["ws"], b1["status"], stage_events=sev[k], stream=stream)
+        torch.cuda.synchronize(dev)
+        sstage = {n: round(statistics.median(sev[k][i].elapsed_time(sev[k][i + 1]) for k in range(5, 20)), 4)
+                  for i, n in enumerate(doa.STAGE_NAMES)}
         single = {"device_ms": lat, "host_to_host_ms_median": 1e3 * statistics.median(wall),
+                  "stages_ms_eager": sstage,
                   "paper_table10_ms": {"GTX 1660 Ti (Config-1)": 0.924, "GTX 1050 (Config-2)": 1.447},
                   "launches": b1["plan"].launches()}
         del b1, g1
@@ -933,7 +944,7 @@ def run_uca(args):
         "dtype": "f32", "data": "synthetic (seeded Eq. 1 snapshots of an 8-element UCA, Philox)",
         "config": {"workload": f"paper-uca batch: {B} problems, 8-element UCA r=10 m at 15 MHz, d=2, SNR 15 dB, "
                                f"N=1024, MUSIC, azimuth 0:1:359 x elevation {91 - Le}:1:90 ({npts} points)",
-                   "batch_per_gpu": B, "graph": True,
+                   "batch_per_gpu": B, "graph": True, "scan_pt": bt["plan"].scan_pt, "eig_mats": bt["plan"].eig_mats,
                    "l2": f"inputs {Xh.nbytes / 1e9:.2f} GB > 129 MB L2 (no flush needed)",
                    "parallelism": f"replicas x{world}"},
         "solves_per_s": B * world / (ms / 1e3),
@@ -942,10 +953,11 @@ def run_uca(args):
         "dominant_stage": doa.STAGE_NAMES[dom],
         "roofline": {"bound": "alu", "achieved": stage_info["scan"]["achieved"], "peak": round(FP32_PEAK_TFLOPS, 2),
                      "unit": "TFLOP/s", "frac": stage_info["scan"]["frac"], "traffic": None,
-                     "kernel": "scan_geometry_batch_kernel<8,4>",
+                     "kernel": f"scan_geometry_batch_kernel<8,{bt['plan'].scan_pt[0]}>",
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"},
         "single_solve": single,
         "table10": table10,
+        "autotune": tune_log,
         "e2e": {"value": points / (e2e_ms / 1e3), "unit": "points/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "clocks": clk,
@@ -1057,7 +1069,7 @@ def main():
     ap.add_argument("--train", type=int, default=1 << 20, help="learned workload: training instances")
     ap.add_argument("--epochs", type=int, default=40, help="learned workload: training epochs")
     ap.add_argument("--lr-decay", type=float, default=0.92, help="learned workload: learning-rate factor per epoch")
-    ap.add_argument("--no-tune", action="store_true", help="uneven workload: default scan tiles")
+    ap.add_argument("--no-tune", action="store_true", help="uneven and paper-uca workloads: default launch shapes")
     ap.add_argument("--la-forms", default="", help="large-array workload: comma list of forms (default all)")
     ap.add_argument("--tc-min-m", type=int, default=0,
                     help="uneven workload: problems with M >= this (<= 32) scan on the tensor cores (FP16x3)")

@@ -39,11 +39,19 @@ def _bucket(M: int) -> int:
 
 
 def _keys(problems: Sequence[doa.Problem], device) -> Dict[int, str]:
+    """Cache key per occupied bucket: GPU, bucket, decades of the problem count and of the mean
+    points x algorithms per problem, and the scan kind (ULA, 2-D geometry, or both)."""
     name = torch.cuda.get_device_name(device).replace(" ", "_")
     Ls: Dict[int, List[int]] = {}
+    kinds: Dict[int, set] = {}
     for p in problems:
-        Ls.setdefault(_bucket(p.M), []).append(int(p.grid.L) * bin(int(p.alg_mask)).count("1"))
+        b = _bucket(p.M)
+        geo = bool(p.geom.pos)
+        pts = int(p.grid.L) * (int(p.geom.Le) if geo else 1)
+        Ls.setdefault(b, []).append(pts * bin(int(p.alg_mask)).count("1"))
+        kinds.setdefault(b, set()).add("geo" if geo else "ula")
     return {b: f"{name}|M{b}|n1e{int(round(math.log10(len(v))))}|L1e{int(round(math.log10(max(1.0, sum(v) / len(v)))))}"
+               f"|{'+'.join(sorted(kinds[b]))}"
             for b, v in Ls.items()}
 
 

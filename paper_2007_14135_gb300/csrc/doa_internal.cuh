@@ -46,15 +46,11 @@ __device__ __forceinline__ uint64_t phase_step64_of_sin(double s) {
   return (uint64_t)__double2ll_rn(s * 4611686018427387904.0) << 1;   // 2^62
 }
 
-// exp(j*pi*phi*2^-31) for a 32-bit phase phi (a fraction of a full turn: 2^32 = 2 pi).
-// The top two bits (rounded) select the quadrant; the signed remainder f in [-1/2, 1/2) of a
-// quarter turn is evaluated with the Taylor series of sin and cos about 0 in the variable
-// x = (pi/2) f, |x| <= pi/4, through x^9 and x^10 (Lagrange remainders below 2e-9 and 2e-10).
+// exp(j (pi/2) (quad + f)) for a quarter-turn count quad (mod 4) and a remainder f in [-1/2, 1/2]
+// of a quarter turn: the Taylor series of sin and cos about 0 in x = (pi/2) f, |x| <= pi/4, through
+// x^9 and x^10 (Lagrange remainders below 2e-9 and 2e-10), then a rotation by quad quarter turns.
 // Coefficients are (pi/2)^n / n! folded so that the polynomials take f directly.
-__device__ __forceinline__ float2 phasor_q32(uint32_t phi) {
-  uint32_t quad = (phi + 0x20000000u) >> 30;             // nearest quarter turn, 0..3
-  int32_t rem = (int32_t)(phi - (quad << 30));            // [-2^29, 2^29)
-  float f = (float)rem * 9.31322574615478515625e-10f;     // * 2^-30 -> [-0.5, 0.5)
+__device__ __forceinline__ float2 phasor_quarter_core(float f, uint32_t quad) {
   float f2 = f * f;
   // sin((pi/2) f) = f*(s1 + f2*(s3 + f2*(s5 + f2*(s7 + f2*s9))))
   const float s1 = 1.5707963267948966f, s3 = -0.6459640975062462f, s5 = 0.07969262624616704f,
@@ -78,6 +74,27 @@ __device__ __forceinline__ float2 phasor_q32(uint32_t phi) {
   if ((quad + 1u) & 2u) re = -re;   // quad 1 or 2
   if (quad & 2u) im = -im;          // quad 2 or 3
   return make_float2(re, im);
+}
+
+// exp(j*pi*phi*2^-31) for a 32-bit phase phi (a fraction of a full turn: 2^32 = 2 pi).
+// The top two bits (rounded) select the quadrant; the signed remainder f in [-1/2, 1/2) of a
+// quarter turn goes to phasor_quarter_core.
+__device__ __forceinline__ float2 phasor_q32(uint32_t phi) {
+  uint32_t quad = (phi + 0x20000000u) >> 30;             // nearest quarter turn, 0..3
+  int32_t rem = (int32_t)(phi - (quad << 30));            // [-2^29, 2^29)
+  float f = (float)rem * 9.31322574615478515625e-10f;     // * 2^-30 -> [-0.5, 0.5)
+  return phasor_quarter_core(f, quad);
+}
+
+// exp(j (pi/2) t4) for a phase t4 in quarter turns, |t4| < 2^22. Adding 1.5 * 2^23 rounds t4 to
+// the nearest integer q (ties to even) and leaves q mod 2^22 in the low mantissa bits, so the
+// quadrant is those bits mod 4 and the remainder t4 - q in [-1/2, 1/2] is exact: no conversion
+// instructions.
+__device__ __forceinline__ float2 phasor_quarter(float t4) {
+  const float big = 12582912.0f;                          // 1.5 * 2^23
+  const float y = __fadd_rn(t4, big);
+  const float q = __fsub_rn(y, big);
+  return phasor_quarter_core(__fsub_rn(t4, q), __float_as_uint(y) & 3u);
 }
 
 // FP64 counterpart for refinement: exp(j 2 pi phi 2^-64) for a 64-bit phase phi (fraction of a

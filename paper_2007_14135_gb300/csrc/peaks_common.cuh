@@ -158,37 +158,21 @@ __device__ __forceinline__ int select_top(const float *__restrict__ P, int L, in
 // A point of an Le x La row-major spectrum is a peak when it is strictly larger than each of its
 // neighbours (the up to 8 points at row and column distance <= 1; rows outside the grid are absent,
 // columns wrap around when wrap) and it has at least one.
-inline __device__ bool is_peak2d(const float *__restrict__ P, int La, int Le, bool wrap, int l, int k, float v) {
-  int nb = 0;
-  for (int dl = -1; dl <= 1; ++dl) {
-    const int ll = l + dl;
-    if (ll < 0 || ll >= Le) continue;
-    for (int dk = -1; dk <= 1; ++dk) {
-      if (dl == 0 && dk == 0) continue;
-      int kk = k + dk;
-      if (kk < 0 || kk >= La) {
-        if (!wrap) continue;
-        kk = kk < 0 ? kk + La : kk - La;
-      }
-      ++nb;
-      if (!(P[(size_t)ll * La + kk] < v)) return false;
-    }
-  }
-  return nb > 0;
-}
 
-// Best 2-D peaks among the flat points i = c0, c0 + stride, ... < n worse than thr.
+// Best 2-D peaks among the flat points i = c0, c0 + stride, ... < La * Le worse than thr. The row
+// and column of i advance by the stride's quotient and remainder (no division per point); four
+// points per step load their value and row neighbours first, and only the points that beat both
+// row neighbours look at the rows above and below.
 inline __device__ bool fill2d(const float *__restrict__ P, int La, int Le, bool wrap, int c0, int stride,
                               const Cand &thr, Cand (&cache)[kCache], int &n) {
   n = 0;
   bool more = false;
   const int npts = La * Le;
-  for (int i = c0; i < npts; i += stride) {
-    const float v = P[i];
-    const int l = i / La, k = i - l * La;
-    if (!is_peak2d(P, La, Le, wrap, l, k, v)) continue;
+  const int sl = stride / La, sk = stride - sl * La;
+  int l = c0 / La, k = c0 - l * La;
+  auto consider = [&](int i, float v) {
     Cand c{v, i};
-    if (thr.i != INT_MAX && !better(thr, c)) continue;
+    if (thr.i != INT_MAX && !better(thr, c)) return;
     if (n < kCache) {
       int q = n++;
       while (q > 0 && better(c, cache[q - 1])) {
@@ -206,6 +190,53 @@ inline __device__ bool fill2d(const float *__restrict__ P, int La, int Le, bool 
         }
         cache[q] = c;
       }
+    }
+  };
+  // value of the row neighbour at column kk of row l (kk = -1 or La: wrapped, or absent = -inf)
+  auto row_nb = [&](int row, int kk) -> float {
+    if (kk < 0 || kk >= La) {
+      if (!wrap) return -INFINITY;
+      kk = kk < 0 ? kk + La : kk - La;
+    }
+    return P[(size_t)row * La + kk];
+  };
+  auto advance = [&](int &ll, int &kk) {
+    ll += sl;
+    kk += sk;
+    if (kk >= La) {
+      kk -= La;
+      ++ll;
+    }
+  };
+  int i = c0;
+  while (i < npts) {
+    float v[4], lv[4], rv[4];
+    int li[4], ki[4], ii[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      ii[u] = i;
+      li[u] = l;
+      ki[u] = k;
+      const bool in = i < npts;
+      v[u] = in ? P[i] : -INFINITY;
+      lv[u] = in ? row_nb(l, k - 1) : 0.f;
+      rv[u] = in ? row_nb(l, k + 1) : 0.f;
+      i += stride;
+      advance(l, k);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (ii[u] >= npts || !(lv[u] < v[u]) || !(rv[u] < v[u])) continue;
+      // the row neighbours are smaller (or absent); a point with no neighbour at all is no peak
+      bool pk = La > 1 || wrap || Le > 1;
+      for (int dl = -1; dl <= 1 && pk; dl += 2) {
+        const int row = li[u] + dl;
+        if (row < 0 || row >= Le) continue;
+        if (!(P[(size_t)row * La + ki[u]] < v[u]) || !(row_nb(row, ki[u] - 1) < v[u]) ||
+            !(row_nb(row, ki[u] + 1) < v[u]))
+          pk = false;
+      }
+      if (pk) consider(ii[u], v[u]);
     }
   }
   return more;

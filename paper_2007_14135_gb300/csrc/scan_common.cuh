@@ -19,7 +19,7 @@ namespace doa {
 namespace scanc {
 
 constexpr float kRefineC = 3.7e-6f;   // (4 * 4 eps32 / 5e-4)^2
-constexpr int kFlagCap = 256;          // queued refinements per tile (overflow: refined in place)
+constexpr int kFlagCap = 1024;         // queued refinements per drain (overflow: refined in place)
 constexpr int kScanWarps = kScanThreads / 32;
 constexpr int kMaxCols = kMaxM + 1;    // E_n (up to M columns when d = 0) plus valph
 
@@ -324,7 +324,7 @@ __device__ __forceinline__ void contract_points(const float2 *Bs, const ScanJob 
       if (pos[q] < kFlagCap) sh.flags[pos[q]] = k0 + q;
     }
   }
-  // queue overflow (more than kFlagCap small denominators in one tile): refine in place
+  // queue overflow (more than kFlagCap small denominators before a drain): refine in place
 #pragma unroll
   for (int q = 0; q < PT; ++q)
     if (pos[q] >= kFlagCap) refine_point_thread_src(j, k0 + q, src, sh.w32);

@@ -13,10 +13,11 @@
 // of angle / 180) and kept as FP64 and as FP32 (rounded once) in the workspace; a point reads
 // its row's and column's entries, u = sin(theta) sin(phi), v = cos(theta) sin(phi), w = cos(phi).
 //
-// FP32 steering. The element phase t_m = p_m . (u, v, w) (turns) uses the positions relative to
-// their centroid: that subtracts a common phase from every element, which leaves ||F^H a||
-// unchanged and keeps |t_m| at most the array's radius. The fraction t_m - rint(t_m) becomes a
-// 32-bit phase and phasor_q32 turns it into cos + j sin.
+// FP32 steering. The element phase t_m = p_m . (u, v, w) uses the positions relative to their
+// centroid: that subtracts a common phase from every element, which leaves ||F^H a|| unchanged and
+// keeps |t_m| at most the array's radius. Positions are held times 4, so the phase comes out in
+// quarter turns and phasor_quarter splits it into a quadrant and a remainder without conversions
+// (positions up to 2^20 wavelengths from the centroid).
 //
 // Refinement. The FP32 phasor error is bounded (in units of eps = 2^-24) by
 //   eps_a = 2 pi rho (3 + 1 + 3) + 3,
@@ -44,7 +45,7 @@ struct GeoParams {
 };
 
 struct GeoShared {
-  float4 p32[kMaxM];     // centred positions in FP32 (x, y, z, 0); rows >= M zero
+  float4 p32[kMaxM];     // 4 x centred positions in FP32 (x, y, z, 0); rows >= M zero
   double cen[3];         // centroid (FP64)
 };
 
@@ -115,8 +116,8 @@ __device__ void geo_setup(const float2 *Bs, const ScanJob &j, const GeoParams &g
   for (int m = threadIdx.x; m < MP; m += blockDim.x) {
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
     if (m < j.M)
-      p = make_float4((float)(g.pos[3 * m] - gs.cen[0]), (float)(g.pos[3 * m + 1] - gs.cen[1]),
-                      (float)(g.pos[3 * m + 2] - gs.cen[2]), 0.f);
+      p = make_float4((float)(4.0 * (g.pos[3 * m] - gs.cen[0])), (float)(4.0 * (g.pos[3 * m + 1] - gs.cen[1])),
+                      (float)(4.0 * (g.pos[3 * m + 2] - gs.cen[2])), 0.f);
     gs.p32[m] = p;
   }
   set_threshold<MP>(Bs, j, sh);
@@ -149,9 +150,7 @@ __device__ __forceinline__ void geo_points(const float2 *Bs, const ScanJob &j, c
 #pragma unroll
     for (int m = 0; m < MP; ++m) {
       const float4 p = gs.p32[m];
-      const float t = fmaf(p.x, u, fmaf(p.y, v, p.z * w));
-      const float f = t - rintf(t);                                   // [-1/2, 1/2] turn
-      a[q][m] = phasor_q32((uint32_t)__float2int_rn(f * 4294967296.0f));
+      a[q][m] = phasor_quarter(fmaf(p.x, u, fmaf(p.y, v, p.z * w)));   // phase in quarter turns
     }
     if (++k == La) {
       k = 0;
@@ -159,6 +158,11 @@ __device__ __forceinline__ void geo_points(const float2 *Bs, const ScanJob &j, c
     }
   }
   contract_points<MP, PT>(Bs, j, a, npts, i0, sh, src);
+}
+
+// Re-evaluates the queued points of the current job in FP64 (warp per point).
+__device__ __forceinline__ void geo_drain(const ScanJob &j, const GeoSource &src, ScanShared &sh) {
+  drain_refinements_src(j, src, sh);
 }
 
 __device__ __forceinline__ GeoSource make_source(const GeoParams &g, const GeoShared &gs) {
@@ -192,11 +196,13 @@ __global__ void __launch_bounds__(kScanThreads) scan_geometry_single_kernel(cons
   const GeoSource src = make_source(g, gs);
   const int i0 = (blockIdx.x * kScanThreads + threadIdx.x) * PT;
   geo_points<MP, PT>(Bs, j, gs, g.t32, g.La, g.Le, npts, i0, sh, src);
-  drain_refinements_src(j, src, sh);
+  geo_drain(j, src, sh);
 }
 
 // Batched: the tiles of the geometry problems of one M bucket, dealt in runs of kRun tiles like the
-// ULA batch scan (run r to CTA r mod gridDim).
+// ULA batch scan (run r to CTA r mod gridDim). Flagged points accumulate over a run and are
+// re-evaluated when the run ends or its problem changes, so the warps share the FP64 work of
+// many tiles and meet at a barrier once per run rather than once per tile.
 constexpr int kRun = 16;
 
 template <int MP, int PT>
@@ -227,6 +233,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_geometry_batch_kernel(const
     for (int64_t t = t_begin; t < t_end; ++t) {
       while (u + 1 < nunits && probs[list[u + 1]].tile_start <= t) ++u;
       if (u != cur) {
+        if (cur >= 0) geo_drain(j, src, sh);
         pp = &probs[list[u]];
         const int npts = pp->npts;
         j.F = reinterpret_cast<const double2 *>(ws + pp->fac_off);
@@ -256,8 +263,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_geometry_batch_kernel(const
       }
       const int i0 = (int)(t - pp->tile_start) * TP + threadIdx.x * PT;
       geo_points<MP, PT>(Bs, j, gs, g.t32, g.La, g.Le, pp->npts, i0, sh, src);
-      drain_refinements_src(j, src, sh);
     }
+    geo_drain(j, src, sh);
   }
 }
 
