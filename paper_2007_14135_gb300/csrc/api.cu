@@ -514,9 +514,10 @@ doa_status doa_solve_batch(const void *plan_host, const void *plan_dev, void *ws
   if (!mark(3) || launch_scan_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
   if (h.tc_jobs > 0 && launch_scan_tc_batch(pd, h, w, status, s) != cudaSuccess) return DOA_ECUDA;
   if (launch_scan_geometry_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
-  if (!mark(4) || launch_peaks_batch(pd, h, s) != cudaSuccess) return DOA_ECUDA;
+  if (!mark(4) || launch_peaks_batch(pd, h, true, true, s) != cudaSuccess) return DOA_ECUDA;
+  // peak polish applies to ULA problems only (geometry problems reject the flag)
   if (h.npolish > 0 &&
-      (launch_polish_batch(pd, h, w, s) != cudaSuccess || launch_peaks_batch(pd, h, s) != cudaSuccess))
+      (launch_polish_batch(pd, h, w, s) != cudaSuccess || launch_peaks_batch(pd, h, true, false, s) != cudaSuccess))
     return DOA_ECUDA;
   if (!mark(5)) return DOA_ECUDA;
   return DOA_OK;

@@ -62,17 +62,26 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_single_kernel(const float 
   peaks_block(P, L, d, idx, val, count);
 }
 
+// One CTA per (problem, algorithm) job; the 1-D and 2-D rules run as separate kernels (each skips
+// the other kind's jobs) so that each keeps its own register budget.
 __global__ void __launch_bounds__(kPeakThreads) peaks_batch_kernel(const uint8_t *plan) {
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
   const PlanJob &jb = reinterpret_cast<const PlanJob *>(plan + h->off_job)[blockIdx.x];
   const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[jb.prob];
+  if (pp.p.geom.pos) return;
   const int L = pp.npts, d = pp.p.d;
-  if (pp.p.geom.pos)
-    peaks2d_block(pp.p.P + (size_t)jb.slot * L, pp.p.grid.L, pp.p.geom.Le, pp.p.geom.wrap_az != 0, d,
-                  pp.p.peak_idx + (size_t)jb.slot * d, pp.p.peak_val + (size_t)jb.slot * d, pp.p.peak_count + jb.slot);
-  else
-    peaks_block(pp.p.P + (size_t)jb.slot * L, L, d, pp.p.peak_idx + (size_t)jb.slot * d,
-                pp.p.peak_val + (size_t)jb.slot * d, pp.p.peak_count + jb.slot);
+  peaks_block(pp.p.P + (size_t)jb.slot * L, L, d, pp.p.peak_idx + (size_t)jb.slot * d,
+              pp.p.peak_val + (size_t)jb.slot * d, pp.p.peak_count + jb.slot);
+}
+
+__global__ void __launch_bounds__(kPeakThreads) peaks2d_batch_kernel(const uint8_t *plan) {
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
+  const PlanJob &jb = reinterpret_cast<const PlanJob *>(plan + h->off_job)[blockIdx.x];
+  const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[jb.prob];
+  if (!pp.p.geom.pos) return;
+  const int L = pp.npts, d = pp.p.d;
+  peaks2d_block(pp.p.P + (size_t)jb.slot * L, pp.p.grid.L, pp.p.geom.Le, pp.p.geom.wrap_az != 0, d,
+                pp.p.peak_idx + (size_t)jb.slot * d, pp.p.peak_val + (size_t)jb.slot * d, pp.p.peak_count + jb.slot);
 }
 
 // ---- grid slices ---------------------------------------------------------------------------
@@ -202,8 +211,11 @@ cudaError_t launch_peaks2d_single(const float *P, int La, int Le, int wrap_az, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_peaks_batch(const uint8_t *plan_dev, const PlanHeader &h, cudaStream_t s) {
-  if (h.njobs > 0) peaks_batch_kernel<<<h.njobs, kPeakThreads, 0, s>>>(plan_dev);
+cudaError_t launch_peaks_batch(const uint8_t *plan_dev, const PlanHeader &h, bool ula, bool geo, cudaStream_t s) {
+  int ngeo = 0;
+  for (int b = 0; b < kNumBuckets; ++b) ngeo += h.geo_jobs[b];
+  if (h.njobs > 0 && ula && ngeo < h.nprob) peaks_batch_kernel<<<h.njobs, kPeakThreads, 0, s>>>(plan_dev);
+  if (h.njobs > 0 && geo && ngeo > 0) peaks2d_batch_kernel<<<h.njobs, kPeakThreads, 0, s>>>(plan_dev);
   return cudaGetLastError();
 }
 

@@ -319,7 +319,8 @@ class BatchPlan:
         cov = sum(2 for c in range(3) if cf[c + 1] > cf[c]) + int(cf[4] > cf[3]) + int(h[5] > 0)
         eig_b = sum(int(c) > 0 for c in h[6:10])
         scan_b = sum(int(c) > 0 for c in h[10:14]) + int(h[67] > 0) + sum(int(c) > 0 for c in h[76:80])
-        peaks = 1 + (2 if int(h[74]) > 0 else 0)
+        ngeo = sum(int(c) for c in h[76:80])
+        peaks = int(ngeo < int(h[1])) + int(ngeo > 0) + (2 if int(h[74]) > 0 else 0)
         return int(h[3] > 0) + int(h[96] > 0) + cov + eig_b + scan_b + peaks
 
 
