@@ -17,6 +17,8 @@ compiles it with gcc on first use and exposes NumPy-friendly wrappers:
   scan_geometry / peaks2d / solve_geometry
               -- Steps 5-6 (and 1-6) for an arbitrary array geometry on an azimuth x elevation grid,
                  steering vector of Eq. 2 as printed (Sec. 4.2's circular array)
+  refine_peak / refine_peak2d
+              -- sub-grid refinement of a picked peak: the local minimiser of a^H C a next to it
 
 The MLP oracle used for the learned proposal lives in ``oracle/mlp.py`` (NumPy, FP64).
 """
@@ -73,6 +75,10 @@ def _load():
             lib.oracle_scan_geometry.restype = None
             lib.oracle_peaks2d.argtypes = [p, i, i, i, i, p, p]
             lib.oracle_peaks2d.restype = i
+            lib.oracle_refine_peak.argtypes = [p, i, d, d, i, p]
+            lib.oracle_refine_peak.restype = d
+            lib.oracle_refine_peak2d.argtypes = [p, i, p, d, d, i, d, d, i, p, p]
+            lib.oracle_refine_peak2d.restype = None
             _lib = lib
     return _lib
 
@@ -217,3 +223,26 @@ def solve_geometry(X: np.ndarray, D: int, alg: int, pos: np.ndarray, az_lo: floa
     P = scan_geometry(C, pos, az_lo, az_step, La, el_lo, el_step, Le)
     idx, val = peaks2d(P, D, wrap_az)
     return dict(P=P, evals=ev, C=C, idx=idx, val=val, status=0)
+
+
+def refine_peak(C: np.ndarray, lo: float, step: float, k: int):
+    """Local minimiser (degrees) of a^H C a in the bracket around grid peak k of the ULA scan
+    (bracketed Newton). Returns (theta, steps)."""
+    C = np.ascontiguousarray(C, dtype=np.complex128)
+    it = ctypes.c_int(0)
+    th = _load().oracle_refine_peak(_ptr(C), C.shape[0], float(lo), float(step), int(k), ctypes.byref(it))
+    return th, it.value
+
+
+def refine_peak2d(C: np.ndarray, pos: np.ndarray, az_lo: float, az_step: float, La: int, el_lo: float,
+                  el_step: float, flat: int):
+    """Local minimiser (azimuth, elevation degrees) of a^H C a in the box around the 2-D grid peak
+    with flat index l*La + k (damped Newton). Returns ((theta, phi), steps)."""
+    C = np.ascontiguousarray(C, dtype=np.complex128)
+    M = C.shape[0]
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(M, 3)
+    out = np.zeros(2, dtype=np.float64)
+    it = ctypes.c_int(0)
+    _load().oracle_refine_peak2d(_ptr(C), M, _ptr(pos), float(az_lo), float(az_step), int(La), float(el_lo),
+                                 float(el_step), int(flat), _ptr(out), ctypes.byref(it))
+    return (float(out[0]), float(out[1])), it.value

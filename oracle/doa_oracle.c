@@ -457,3 +457,210 @@ int oracle_peaks2d(const double *P, int La, int Le, int wrap_az, int D, int *idx
   free(cand);
   return count;
 }
+
+/* ---------------------------------------------------------------------------------------------
+ * Sub-grid refinement of a Step-6 peak (beyond the paper, which stops at grid resolution): the
+ * local minimiser of den(theta) = a(theta)^H C a(theta) next to grid peak k of the ULA scan,
+ * found by Newton's method on den'(theta) = 0 (theta in radians), kept inside the bracket
+ * [theta_{k-1}, theta_{k+1}]: each step first shrinks the bracket by the sign of den' (den' > 0:
+ * the minimiser lies to the left); when den'' > 0 and the Newton step -den'/den'' is shorter than
+ * 1e-13 rad it takes it and stops; otherwise it moves to the Newton point if that lies strictly
+ * inside the bracket, else to the bracket's midpoint, and stops when that move is shorter than
+ * 1e-13 rad or after 60 steps. With a_m = exp(j pi m sin theta):
+ *   a'_m  = j pi m cos(theta) a_m,
+ *   a''_m = (-j pi m sin(theta) - (pi m cos(theta))^2) a_m,
+ *   den'  = 2 Re(a'^H C a),   den'' = 2 Re(a''^H C a) + 2 a'^H C a'.
+ * Returns the refined angle in degrees; *iters receives the steps taken.
+ * ------------------------------------------------------------------------------------------- */
+static void oracle_den_derivs(const double complex *Cm, int M, double th, double *f, double *f1, double *f2) {
+  double complex *a = (double complex *)malloc(sizeof(double complex) * 3 * M);
+  double complex *a1 = a + M, *a2 = a + 2 * M;
+  double s = sin(th), c = cos(th);
+  for (int m = 0; m < M; ++m) {
+    double phase = ORACLE_PI * (double)m * s;
+    a[m] = cos(phase) + I * sin(phase);
+    double pm = ORACLE_PI * (double)m;
+    a1[m] = (I * pm * c) * a[m];
+    a2[m] = (-I * pm * s - (pm * c) * (pm * c)) * a[m];
+  }
+  double complex q0 = 0.0, q1 = 0.0, q2 = 0.0, q11 = 0.0;
+  for (int i = 0; i < M; ++i) {
+    double complex row0 = 0.0, row1 = 0.0;
+    for (int j = 0; j < M; ++j) {
+      row0 += Cm[i * M + j] * a[j];
+      row1 += Cm[i * M + j] * a1[j];
+    }
+    q0 += conj(a[i]) * row0;
+    q1 += conj(a1[i]) * row0;
+    q2 += conj(a2[i]) * row0;
+    q11 += conj(a1[i]) * row1;
+  }
+  *f = creal(q0);
+  *f1 = 2.0 * creal(q1);
+  *f2 = 2.0 * creal(q2) + 2.0 * creal(q11);
+  free(a);
+}
+
+double oracle_refine_peak(const double *C, int M, double lo, double step, int k, int *iters) {
+  double complex *Cm = (double complex *)malloc(sizeof(double complex) * M * M);
+  for (int i = 0; i < M * M; ++i) Cm[i] = C[2 * i] + I * C[2 * i + 1];
+  const double d2r = ORACLE_PI / 180.0;
+  double t0 = lo + (double)(k - 1) * step, t1 = lo + (double)k * step, t2 = lo + (double)(k + 1) * step;
+  double x_lo = fmin(t0, t2) * d2r, x_hi = fmax(t0, t2) * d2r, x = t1 * d2r;
+  int it = 0;
+  for (; it < 60; ++it) {
+    double f, f1, f2;
+    oracle_den_derivs(Cm, M, x, &f, &f1, &f2);
+    if (f1 > 0.0) x_hi = x; else x_lo = x;
+    if (f2 > 0.0 && fabs(f1) < 1e-13 * f2) {
+      x -= f1 / f2;
+      ++it;
+      break;
+    }
+    double xn = (f2 > 0.0) ? x - f1 / f2 : NAN;
+    if (!(xn > x_lo && xn < x_hi)) xn = 0.5 * (x_lo + x_hi);
+    double dx = fabs(xn - x);
+    x = xn;
+    if (dx < 1e-13) {
+      ++it;
+      break;
+    }
+  }
+  if (iters) *iters = it;
+  free(Cm);
+  return x / d2r;
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Sub-grid refinement of a 2-D peak (flat index l * La + k of the azimuth x elevation scan, Eq. 2
+ * as printed): the local minimiser of den(theta, phi) = a^H C a inside the box theta_k +- |az step|,
+ * phi_l +- |el step|, by damped Newton. With t_m = p_m . u(theta, phi) (turns),
+ *   a_m = exp(j 2 pi t_m),  a_i = j 2 pi t_i a,  a_ij = (j 2 pi t_ij - 4 pi^2 t_i t_j) a,
+ *   g_i = 2 Re(a_i^H C a),  H_ij = 2 Re(a_ij^H C a) + 2 Re(a_i^H C a_j),
+ * where t_i, t_ij are t's derivatives through u = (sin th sin ph, cos th sin ph, cos ph). A step
+ * is d = -H^-1 g when H is positive definite, else the steepest-descent direction scaled to the box
+ * half-width. A Newton step shorter than 1e-6 rad in both angles is taken as it is (the quadratic
+ * end game, where den itself is below its rounding noise); any other step is halved (up to 40
+ * times) until den does not increase. The point is clamped into the box; the iteration stops when
+ * a step moves both angles by less than 1e-13 rad, when no halving decreases den, or after 60
+ * steps. out[0] = azimuth, out[1] = elevation (degrees).
+ * ------------------------------------------------------------------------------------------- */
+static double oracle_den2d(const double complex *Cm, int M, const double *pos, double th, double ph, double g[2],
+                           double H[3]) {
+  double complex *a = (double complex *)malloc(sizeof(double complex) * 6 * M);
+  double complex *at = a + M, *ap = a + 2 * M, *att = a + 3 * M, *atp = a + 4 * M, *app = a + 5 * M;
+  const double st = sin(th), ct = cos(th), sp = sin(ph), cp = cos(ph);
+  const double u[3] = {st * sp, ct * sp, cp};
+  const double ut[3] = {ct * sp, -st * sp, 0.0};
+  const double up[3] = {st * cp, ct * cp, -sp};
+  const double utt[3] = {-st * sp, -ct * sp, 0.0};
+  const double utp[3] = {ct * cp, -st * cp, 0.0};
+  const double upp[3] = {-st * sp, -ct * sp, -cp};
+  const double tp = 2.0 * ORACLE_PI;
+  for (int m = 0; m < M; ++m) {
+    const double *p = pos + 3 * m;
+    double t = p[0] * u[0] + p[1] * u[1] + p[2] * u[2];
+    double t_t = p[0] * ut[0] + p[1] * ut[1] + p[2] * ut[2];
+    double t_p = p[0] * up[0] + p[1] * up[1] + p[2] * up[2];
+    double t_tt = p[0] * utt[0] + p[1] * utt[1] + p[2] * utt[2];
+    double t_tp = p[0] * utp[0] + p[1] * utp[1] + p[2] * utp[2];
+    double t_pp = p[0] * upp[0] + p[1] * upp[1] + p[2] * upp[2];
+    a[m] = cos(tp * t) + I * sin(tp * t);
+    at[m] = (I * tp * t_t) * a[m];
+    ap[m] = (I * tp * t_p) * a[m];
+    att[m] = (I * tp * t_tt - tp * tp * t_t * t_t) * a[m];
+    atp[m] = (I * tp * t_tp - tp * tp * t_t * t_p) * a[m];
+    app[m] = (I * tp * t_pp - tp * tp * t_p * t_p) * a[m];
+  }
+  double complex q0 = 0, qt = 0, qp = 0, qtt = 0, qtp = 0, qpp = 0, rtt = 0, rtp = 0, rpp = 0;
+  for (int i = 0; i < M; ++i) {
+    double complex r0 = 0, rt = 0, rp = 0;
+    for (int j = 0; j < M; ++j) {
+      r0 += Cm[i * M + j] * a[j];
+      rt += Cm[i * M + j] * at[j];
+      rp += Cm[i * M + j] * ap[j];
+    }
+    q0 += conj(a[i]) * r0;
+    qt += conj(at[i]) * r0;
+    qp += conj(ap[i]) * r0;
+    qtt += conj(att[i]) * r0;
+    qtp += conj(atp[i]) * r0;
+    qpp += conj(app[i]) * r0;
+    rtt += conj(at[i]) * rt;
+    rtp += conj(at[i]) * rp;
+    rpp += conj(ap[i]) * rp;
+  }
+  if (g) {
+    g[0] = 2.0 * creal(qt);
+    g[1] = 2.0 * creal(qp);
+    H[0] = 2.0 * creal(qtt) + 2.0 * creal(rtt);
+    H[1] = 2.0 * creal(qtp) + 2.0 * creal(rtp);
+    H[2] = 2.0 * creal(qpp) + 2.0 * creal(rpp);
+  }
+  free(a);
+  return creal(q0);
+}
+
+void oracle_refine_peak2d(const double *C, int M, const double *pos, double az_lo, double az_step, int La,
+                          double el_lo, double el_step, int flat, double *out, int *iters) {
+  double complex *Cm = (double complex *)malloc(sizeof(double complex) * M * M);
+  for (int i = 0; i < M * M; ++i) Cm[i] = C[2 * i] + I * C[2 * i + 1];
+  const double d2r = ORACLE_PI / 180.0;
+  const int l = flat / La, k = flat - l * La;
+  double x[2] = {(az_lo + (double)k * az_step) * d2r, (el_lo + (double)l * el_step) * d2r};
+  const double hw[2] = {fabs(az_step) * d2r, fabs(el_step) * d2r};
+  const double bl[2] = {x[0] - hw[0], x[1] - hw[1]}, bh[2] = {x[0] + hw[0], x[1] + hw[1]};
+  int it = 0;
+  for (; it < 60; ++it) {
+    double g[2], H[3];
+    double f = oracle_den2d(Cm, M, pos, x[0], x[1], g, H);
+    double det = H[0] * H[2] - H[1] * H[1];
+    double d[2];
+    if (H[0] > 0.0 && det > 0.0) {
+      d[0] = -(H[2] * g[0] - H[1] * g[1]) / det;
+      d[1] = -(H[0] * g[1] - H[1] * g[0]) / det;
+      if (fmax(fabs(d[0]), fabs(d[1])) < 1e-6) {
+        double xn0 = fmin(fmax(x[0] + d[0], bl[0]), bh[0]), xn1 = fmin(fmax(x[1] + d[1], bl[1]), bh[1]);
+        double mv = fmax(fabs(xn0 - x[0]), fabs(xn1 - x[1]));
+        x[0] = xn0;
+        x[1] = xn1;
+        if (mv < 1e-13) {
+          ++it;
+          break;
+        }
+        continue;
+      }
+    } else {
+      double gn = sqrt(g[0] * g[0] + g[1] * g[1]);
+      double w = fmax(hw[0], hw[1]);
+      d[0] = gn > 0.0 ? -g[0] / gn * w : 0.0;
+      d[1] = gn > 0.0 ? -g[1] / gn * w : 0.0;
+    }
+    double t = 1.0, xn[2] = {x[0], x[1]};
+    int accepted = 0;
+    for (int h = 0; h <= 40; ++h) {
+      xn[0] = fmin(fmax(x[0] + t * d[0], bl[0]), bh[0]);
+      xn[1] = fmin(fmax(x[1] + t * d[1], bl[1]), bh[1]);
+      if (oracle_den2d(Cm, M, pos, xn[0], xn[1], NULL, NULL) <= f) {
+        accepted = 1;
+        break;
+      }
+      t *= 0.5;
+    }
+    if (!accepted) {
+      ++it;
+      break;
+    }
+    double mv = fmax(fabs(xn[0] - x[0]), fabs(xn[1] - x[1]));
+    x[0] = xn[0];
+    x[1] = xn[1];
+    if (mv < 1e-13) {
+      ++it;
+      break;
+    }
+  }
+  if (iters) *iters = it;
+  out[0] = x[0] / d2r;
+  out[1] = x[1] / d2r;
+  free(Cm);
+}
