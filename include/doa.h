@@ -202,6 +202,27 @@ doa_status doa_scan_geometry(const double *B, int M, int K, doa_grid az, doa_geo
 doa_status doa_peaks2d(const float *P, int La, int Le, int wrap_az, int d, int *idx, float *val, int *count,
                        void *stream);
 
+/*
+ * Sub-grid refinement of picked peaks (beyond Step-6, which stops at the grid): for each peak the
+ * local minimiser, in FP64, of den = ||B^H a||^2 (= a^H C a) next to it.
+ *   ULA: bracketed Newton on den'(theta) = 0 inside [theta_{k-1}, theta_{k+1}] (steps shrink the
+ *        bracket by the sign of den'; Newton point inside the bracket, else its midpoint; stop
+ *        below a 1e-13 rad move, 60 steps at most). theta: count angles in degrees.
+ *   2-D (doa_refine_peaks2d, Eq. 2 as printed): damped Newton in (azimuth, elevation) inside the
+ *        box of one grid step around the peak (Newton step when the Hessian is positive definite,
+ *        else steepest descent scaled to the box; halving until den does not increase; Newton
+ *        steps below 1e-6 rad taken as they are). out: count (azimuth, elevation) pairs, degrees.
+ *   B, M, K : factor as for doa_scan / doa_scan_geometry (all K columns, unweighted).
+ *   idx     : device peak indices (as written by doa_peaks / doa_peaks2d); count: device int32
+ *             number of peaks; cap: capacity of idx / the output (min(*count, cap) are refined).
+ * Batch problems get the same per algorithm (its readout's columns and weights) through
+ * doa_problem.peak_angle.
+ */
+doa_status doa_refine_peaks(const double *B, int M, int K, doa_grid grid, const int *idx, const int *count,
+                            int cap, double *theta, void *stream);
+doa_status doa_refine_peaks2d(const double *B, int M, int K, doa_grid az, doa_geometry geom, const int *idx,
+                              const int *count, int cap, double *out, void *stream);
+
 /* ----------------------------------------------------------------------------------------- */
 /* Measurement utility (not in the paper)                                                      */
 /* ----------------------------------------------------------------------------------------- */
@@ -302,6 +323,9 @@ typedef struct {
   doa_geometry geom;     /* geom.pos == NULL: the 1-D ULA scan over `grid`. Otherwise a 2-D   */
                          /* scan, `grid` the azimuth columns: P holds nalg x (Le x La) floats, */
                          /* peaks are flat indices, prec must be DOA_FP32 and flags 0          */
+  double *peak_angle;    /* nullable: sub-grid refined peak angles in degrees (see            */
+                         /* doa_refine_peaks): nalg x d (ULA) or nalg x d x 2 (geometry:       */
+                         /* azimuth, elevation), entries past peak_count untouched             */
 } doa_problem;
 
 /* Peak polish: after Step-6 the spectrum is re-evaluated in FP64 (steering and contraction) at

@@ -59,6 +59,7 @@ bool problem_ok(const doa_problem &p) {
   if (p.eig_prec != DOA_EIG_DOUBLE_FLOAT && p.eig_prec != DOA_EIG_FP64) return false;
   if (p.flags & ~DOA_FLAG_POLISH_PEAKS) return false;
   if (p.d > 0 && (!p.peak_idx || !p.peak_val)) return false;
+  if (p.peak_angle && !aligned(p.peak_angle, 8)) return false;
   if (!p.peak_count) return false;
   if (p.geom.pos)   // 2-D scan: FP32 on CUDA cores, no peak polish
     return p.prec == DOA_FP32 && p.flags == 0 && geometry_ok(p.grid, p.geom);
@@ -330,6 +331,25 @@ doa_status doa_peaks2d(const float *P, int La, int Le, int wrap_az, int d, int *
   return cuda_status(launch_peaks2d_single(P, La, Le, wrap_az, d, idx, val, count, as_stream(stream)));
 }
 
+doa_status doa_refine_peaks(const double *B, int M, int K, doa_grid grid, const int *idx, const int *count,
+                            int cap, double *theta, void *stream) {
+  if (!B || !idx || !count || !theta || M < 2 || M > kMaxM || K < 1 || K > M || !grid_ok(grid) || cap < 1)
+    return DOA_EINVAL;
+  if (!aligned(B, 16) || !aligned(idx, 4) || !aligned(count, 4) || !aligned(theta, 8)) return DOA_EINVAL;
+  return cuda_status(launch_refine_single(reinterpret_cast<const double2 *>(B), M, K, grid.lo_deg, grid.step_deg,
+                                          nullptr, 0.0, 0.0, grid.L, idx, count, cap, theta, as_stream(stream)));
+}
+
+doa_status doa_refine_peaks2d(const double *B, int M, int K, doa_grid az, doa_geometry geom, const int *idx,
+                              const int *count, int cap, double *out, void *stream) {
+  if (!B || !idx || !count || !out || M < 2 || M > kMaxM || K < 1 || K > M || !geometry_ok(az, geom) || cap < 1)
+    return DOA_EINVAL;
+  if (!aligned(B, 16) || !aligned(idx, 4) || !aligned(count, 4) || !aligned(out, 8)) return DOA_EINVAL;
+  return cuda_status(launch_refine_single(reinterpret_cast<const double2 *>(B), M, K, az.lo_deg, az.step_deg,
+                                          geom.pos, geom.el_lo_deg, geom.el_step_deg, az.L, idx, count, cap, out,
+                                          as_stream(stream)));
+}
+
 size_t doa_batch_plan_bytes(const doa_problem *probs, int nprob) {
   if (!probs || nprob < 1) return 0;
   PlanSizes sz;
@@ -464,6 +484,7 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     q.njobs = slot;
     factor_layout(p, q);
     if (p.flags & DOA_FLAG_POLISH_PEAKS) ++h.npolish;
+    if (p.peak_angle) ++h.nrefine;
     q.fac_off = ws;
     ws = round_up(ws + factor_bytes(M), 256);
     if (p.geom.pos) {
@@ -519,6 +540,7 @@ doa_status doa_solve_batch(const void *plan_host, const void *plan_dev, void *ws
   if (h.npolish > 0 &&
       (launch_polish_batch(pd, h, w, s) != cudaSuccess || launch_peaks_batch(pd, h, true, false, s) != cudaSuccess))
     return DOA_ECUDA;
+  if (launch_refine_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
   if (!mark(5)) return DOA_ECUDA;
   return DOA_OK;
 }

@@ -237,10 +237,12 @@ struct PlanHeader {
   int32_t ngeo_grids;                    // distinct azimuth x elevation grids
   int32_t geo_grid_points;               // largest La + Le among them
   int64_t off_geo_grid;
+  int32_t nrefine;                       // problems with a peak_angle output (sub-grid refinement)
+  int32_t pad4;
 };
 
 // The Python binding reads these header fields by position (int32 index 22 = scan_pt, 58 = eig_mats,
-// 62 = cov_first, 67 = tc_jobs, 74 = npolish, 76 = geo_jobs, 96 = ngeo_grids).
+// 62 = cov_first, 67 = tc_jobs, 74 = npolish, 76 = geo_jobs, 96 = ngeo_grids, 100 = nrefine).
 static_assert(offsetof(PlanHeader, scan_pt) == 88, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, scan_tiles) == 56, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, eig_mats) == 232, "PlanHeader layout changed");
@@ -249,6 +251,7 @@ static_assert(offsetof(PlanHeader, tc_jobs) == 268, "PlanHeader layout changed")
 static_assert(offsetof(PlanHeader, npolish) == 296, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, geo_jobs) == 304, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, ngeo_grids) == 384, "PlanHeader layout changed");
+static_assert(offsetof(PlanHeader, nrefine) == 400, "PlanHeader layout changed");
 
 // Scan tiles: kScanThreads threads, each evaluating PT consecutive grid points (tile shape
 // 128 x PT). PT is chosen per M bucket (the autotuner's knob); the register budget limits it
@@ -323,6 +326,11 @@ cudaError_t launch_peaks2d_single(const float *P, int La, int Le, int wrap_az, i
 // ula / geo: launch the 1-D and / or the 2-D peak kernel (each only when the plan has such jobs).
 cudaError_t launch_peaks_batch(const uint8_t *plan_dev, const PlanHeader &h, bool ula, bool geo, cudaStream_t s);
 cudaError_t launch_polish_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
+cudaError_t launch_refine_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
+// pos == null: ULA grid (lo, step); else geometry with azimuth (lo, step, La) and elevation (el_lo, el_step).
+cudaError_t launch_refine_single(const double2 *B, int M, int K, double lo, double step, const double *pos,
+                                 double el_lo, double el_step, int La, const int *idx, const int *count, int cap,
+                                 double *out, cudaStream_t s);
 cudaError_t launch_slice_peaks(const float *Pbuf, int b0, int k0, int k1, int L, int d, doa_slice_summary *out,
                                cudaStream_t s);
 

@@ -30,7 +30,8 @@ EXPORTS = ("doa_status_str", "doa_covariance", "doa_covariance_noalloc", "doa_no
            "doa_peaks", "doa_batch_plan_bytes", "doa_batch_plan", "doa_solve_batch", "doa_mlp_workspace_bytes",
            "doa_mlp_refresh", "doa_mlp_forward", "doa_mlp_backward", "doa_mlp_adam", "doa_synth_ula",
            "doa_proposal_windows", "doa_scan_windows", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices", "doa_probe_fma",
-           "doa_scan_geometry", "doa_scan_geometry_ws_bytes", "doa_peaks2d")
+           "doa_scan_geometry", "doa_scan_geometry_ws_bytes", "doa_peaks2d", "doa_refine_peaks",
+           "doa_refine_peaks2d")
 SLICE_MAXD = 64
 
 
@@ -59,7 +60,7 @@ class Problem(ctypes.Structure):
                 ("N", ctypes.c_int32), ("ldx", ctypes.c_int32), ("d", ctypes.c_int32),
                 ("alg_mask", ctypes.c_uint32), ("prec", ctypes.c_int32), ("features", ctypes.c_void_p),
                 ("B_out", ctypes.c_void_p), ("eig_prec", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("geom", Geometry)]
+                ("geom", Geometry), ("peak_angle", ctypes.c_void_p)]
 
 
 class SliceSummary(ctypes.Structure):
@@ -94,9 +95,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.doa_scan_geometry_ws_bytes.argtypes = [i, i]
     lib.doa_scan_geometry_ws_bytes.restype = sz
     lib.doa_peaks2d.argtypes = [vp, i, i, i, i, vp, vp, vp, vp]
+    lib.doa_refine_peaks.argtypes = [vp, i, i, Grid, vp, vp, i, vp, vp]
+    lib.doa_refine_peaks2d.argtypes = [vp, i, i, Grid, Geometry, vp, vp, i, vp, vp]
     for name in ("doa_covariance", "doa_covariance_noalloc", "doa_noise_subspace", "doa_scan", "doa_peaks",
                  "doa_batch_plan", "doa_solve_batch", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices", "doa_probe_fma",
-                 "doa_scan_geometry", "doa_scan_geometry_ws_bytes", "doa_peaks2d"):
+                 "doa_scan_geometry", "doa_scan_geometry_ws_bytes", "doa_peaks2d", "doa_refine_peaks",
+           "doa_refine_peaks2d"):
         getattr(lib, name).restype = i
     return lib
 
@@ -247,6 +251,22 @@ def doa_scan_geometry(B: torch.Tensor, M: int, K: int, az: Grid, geom: Geometry,
                                    _stream(stream)), "doa_scan_geometry")
 
 
+def doa_refine_peaks(B: torch.Tensor, M: int, K: int, g: Grid, idx: torch.Tensor, count: torch.Tensor,
+                     theta: torch.Tensor, stream=None) -> None:
+    """Sub-grid refinement (FP64 bracketed Newton) of the peaks idx[:count] of a ULA scan."""
+    assert theta.dtype == torch.float64
+    _check(lib().doa_refine_peaks(_dev(B), M, K, g, _dev(idx), _dev(count), min(idx.numel(), theta.numel()),
+                                  _dev(theta), _stream(stream)), "doa_refine_peaks")
+
+
+def doa_refine_peaks2d(B: torch.Tensor, M: int, K: int, az: Grid, geom: Geometry, idx: torch.Tensor,
+                       count: torch.Tensor, out: torch.Tensor, stream=None) -> None:
+    """Sub-grid refinement (FP64 damped Newton) of 2-D peaks: out holds (azimuth, elevation) pairs."""
+    assert out.dtype == torch.float64
+    _check(lib().doa_refine_peaks2d(_dev(B), M, K, az, geom, _dev(idx), _dev(count), min(idx.numel(), out.numel() // 2),
+                                    _dev(out), _stream(stream)), "doa_refine_peaks2d")
+
+
 def doa_peaks2d(P: torch.Tensor, La: int, Le: int, wrap_az: bool, d: int, idx: torch.Tensor, val: torch.Tensor,
                 count: torch.Tensor, stream=None) -> None:
     _check(lib().doa_peaks2d(_dev(P), La, Le, 1 if wrap_az else 0, d, _dev(idx), _dev(val), _dev(count),
@@ -258,14 +278,15 @@ def make_problem(X: torch.Tensor, d: int, alg_mask: int, g: Grid, P: torch.Tenso
                  peak_val: torch.Tensor, peak_count: torch.Tensor, evals: Optional[torch.Tensor] = None,
                  prec: int = FP32, features: Optional[torch.Tensor] = None,
                  B_out: Optional[torch.Tensor] = None, eig_prec: int = 0, polish: bool = False,
-                 geom: Optional[Geometry] = None) -> Problem:
+                 geom: Optional[Geometry] = None, peak_angle: Optional[torch.Tensor] = None) -> Problem:
     """Descriptor of one problem; the tensors must outlive every solve that uses it. With geom the
     problem is a 2-D scan: g is the azimuth grid, P holds nalg x (Le x La) floats."""
     assert X.dtype == torch.complex64 and X.dim() == 2 and X.stride(1) == 1
     M, N = X.shape
     return Problem(_dev(X), _dev(P), _dev(peak_idx), _dev(peak_val), _dev(peak_count), _dev(evals), g,
                    M, N, X.stride(0), d, alg_mask, prec, _dev(features), _dev(B_out), eig_prec,
-                   FLAG_POLISH_PEAKS if polish else 0, geom if geom is not None else Geometry(None, 0.0, 0.0, 0, 0))
+                   FLAG_POLISH_PEAKS if polish else 0, geom if geom is not None else Geometry(None, 0.0, 0.0, 0, 0),
+                   _dev(peak_angle))
 
 
 class Tuning(ctypes.Structure):
@@ -309,7 +330,7 @@ class BatchPlan:
         """int32 index of a PlanHeader field (layout of csrc/doa_internal.cuh)."""
         order = {"magic": 0, "nprob": 1, "njobs": 2, "ngrids": 3, "ncov": 4, "nreduce": 5, "eig_count": 6,
                  "scan_jobs": 10, "scan_tiles": 14, "scan_pt": 22, "eig_mats": 58, "cov_first": 62, "tc_jobs": 67,
-                 "npolish": 74, "geo_jobs": 76, "ngeo_grids": 96}
+                 "npolish": 74, "geo_jobs": 76, "ngeo_grids": 96, "nrefine": 100}
         return order[field]
 
     def launches(self) -> int:
@@ -321,7 +342,7 @@ class BatchPlan:
         scan_b = sum(int(c) > 0 for c in h[10:14]) + int(h[67] > 0) + sum(int(c) > 0 for c in h[76:80])
         ngeo = sum(int(c) for c in h[76:80])
         peaks = int(ngeo < int(h[1])) + int(ngeo > 0) + (2 if int(h[74]) > 0 else 0)
-        return int(h[3] > 0) + int(h[96] > 0) + cov + eig_b + scan_b + peaks
+        return int(h[3] > 0) + int(h[96] > 0) + cov + eig_b + scan_b + peaks + int(h[100] > 0)
 
 
 def doa_solve_batch(plan: BatchPlan, ws: torch.Tensor, status: torch.Tensor, stage_events=None,
