@@ -44,11 +44,14 @@ def workload_name(batch):
             f"grid -90:{STEP}:90 deg (L={grid_L()}), PHD+MUSIC+EV+MN on each")
 
 
-# DRAM bytes (read + write) per launch of the dominant kernels on the 4096-problem paper-density
-# step: ncu captures of the 1024-problem case (profiles/paper_density_batch_kernels_ncu.md) scaled
-# by 4 (every problem is an independent, equal unit). Reset an entry to None when its kernel changes.
+# DRAM bytes (read + write) per launch of the dominant kernels: ncu captures of a smaller case scaled
+# to the bench's batch by the problem count (every problem is an independent, equal unit):
+# paper density from 1024 problems x 4 (profiles/paper_density_batch_kernels_ncu.md), the circular
+# array from 2048 problems x 2 (profiles/paper_uca_geometry_scan_ncu.md). Reset an entry to None
+# when its kernel changes.
 TRAFFIC_BYTES = {
     "scan_batch_kernel<16,2>": 4 * (4.137728e6 + 235.058176e6),
+    "scan_geometry_batch_kernel<8,2>": None,
 }
 
 
@@ -871,7 +874,11 @@ def run_uca(args):
         return e0.elapsed_time(e1) / steps
 
     X = torch.from_numpy(Xh).to(dev)
-    bt = build_batch(X, Le, None if args.no_tune else "tune")
+    if args.scan_pt:
+        fixed = ([int(v) for v in args.scan_pt.split(",")], None)
+        bt = build_batch(X, Le, fixed)
+    else:
+        bt = build_batch(X, Le, None if args.no_tune else "tune")
     nst = doa.BATCH_STAGES + 1
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nst)] for _ in range(3)]
     for k in range(3):
@@ -996,7 +1003,9 @@ def run_uca(args):
         "stages": stage_info,
         "dominant_stage": doa.STAGE_NAMES[dom],
         "roofline": {"bound": "alu", "achieved": stage_info["scan"]["achieved"], "peak": round(FP32_PEAK_TFLOPS, 2),
-                     "unit": "TFLOP/s", "frac": stage_info["scan"]["frac"], "traffic": None,
+                     "unit": "TFLOP/s", "frac": stage_info["scan"]["frac"],
+                     "traffic": (TRAFFIC_BYTES.get(f"scan_geometry_batch_kernel<8,{bt['plan'].scan_pt[0]}>") or 0) * B / 4096
+                     or None,
                      "kernel": f"scan_geometry_batch_kernel<8,{bt['plan'].scan_pt[0]}>",
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"},
         "single_solve": single,
@@ -1110,6 +1119,8 @@ def main():
     ap.add_argument("--workload", choices=["paper-density", "uneven", "large-array", "learned", "paper-uca"],
                     default="paper-density")
     ap.add_argument("--uca-rows", type=int, default=90, help="paper-uca workload: elevation rows (360 x rows grid)")
+    ap.add_argument("--scan-pt", default="", help="paper-uca workload: fixed scan points per thread per M bucket, "
+                                                  "e.g. 2,2,1,1 (no autotuning)")
     ap.add_argument("--train", type=int, default=1 << 20, help="learned workload: training instances")
     ap.add_argument("--epochs", type=int, default=40, help="learned workload: training epochs")
     ap.add_argument("--lr-decay", type=float, default=0.92, help="learned workload: learning-rate factor per epoch")

@@ -24,6 +24,9 @@
 // One warp per (problem, algorithm) job: lanes own elements for the steering vector and its
 // derivatives (shared memory), then factor columns for the contractions, and a shuffle reduction
 // gives every lane the same den, gradient and Hessian, so all lanes take the same decisions.
+// In the batch the iteration starts from the vertex of the parabola through the FP32 spectrum's
+// 1/P at the peak and its neighbours (per axis in 2-D), which leaves Newton one or two steps; the
+// local minimiser it converges to does not depend on the start.
 #include <float.h>
 #include <math_constants.h>
 
@@ -48,8 +51,18 @@ struct RefineJob {
   const double *pos;
   double cx, cy, cz;
   double az_lo, az_step, el_lo, el_step;
-  int La;
+  int La, Le, wrap;
+  const float *P;        // the job's FP32 spectrum (start point), or null: start at the grid point
 };
+
+// Offset, in grid steps, of the vertex of the parabola through 1/P at points a, b (the peak), c;
+// 0 when the three do not bracket a minimum of 1/P.
+__device__ __forceinline__ double vertex_offset(float pa, float pb, float pc) {
+  const double da = 1.0 / (double)pa, db = 1.0 / (double)pb, dc = 1.0 / (double)pc;
+  const double curv = da - 2.0 * db + dc;
+  if (!(curv > 0.0) || !(db <= da) || !(db <= dc)) return 0.0;
+  return fmin(fmax(0.5 * (da - dc) / curv, -0.9), 0.9);
+}
 
 struct RefShared {
   double2 v[6][kMaxM];   // a and its derivatives (1-D: a, a', a''; 2-D: a, a_t, a_p, a_tt, a_tp, a_pp)
@@ -124,6 +137,7 @@ __device__ double refine_ula_warp(const RefineJob &j, int k, RefShared &sh) {
   const double t1 = __dadd_rn(j.lo, __dmul_rn((double)k, j.step));
   const double t2 = __dadd_rn(j.lo, __dmul_rn((double)(k + 1), j.step));
   double x_lo = __dmul_rn(fmin(t0, t2), kD2R), x_hi = __dmul_rn(fmax(t0, t2), kD2R), x = __dmul_rn(t1, kD2R);
+  if (j.P) x = (t1 + vertex_offset(j.P[k - 1], j.P[k], j.P[k + 1]) * j.step) * kD2R;
   for (int it = 0; it < kRefMaxIter; ++it) {
     double f, f1, f2;
     ula_eval(j, x, sh, f, f1, f2);
@@ -211,6 +225,14 @@ __device__ void refine_geo_warp(const RefineJob &j, int flat, RefShared &sh, dou
   double x1 = __dmul_rn(__dadd_rn(j.el_lo, __dmul_rn((double)l, j.el_step)), kD2R);
   const double hw0 = fabs(j.az_step) * kD2R, hw1 = fabs(j.el_step) * kD2R;
   const double bl0 = x0 - hw0, bh0 = x0 + hw0, bl1 = x1 - hw1, bh1 = x1 + hw1;
+  if (j.P) {
+    const float pc = j.P[flat];
+    const int km = k > 0 ? k - 1 : (j.wrap ? j.La - 1 : -1), kp = k + 1 < j.La ? k + 1 : (j.wrap ? 0 : -1);
+    if (km >= 0 && kp >= 0 && km != kp)
+      x0 += vertex_offset(j.P[(size_t)l * j.La + km], pc, j.P[(size_t)l * j.La + kp]) * j.az_step * kD2R;
+    if (l > 0 && l + 1 < j.Le)
+      x1 += vertex_offset(j.P[(size_t)(l - 1) * j.La + k], pc, j.P[(size_t)(l + 1) * j.La + k]) * j.el_step * kD2R;
+  }
   for (int it = 0; it < kRefMaxIter; ++it) {
     double g[2], H[3];
     const double f = geo_eval(j, x0, x1, true, sh, g, H);
@@ -316,7 +338,10 @@ __global__ void __launch_bounds__(32 * kRefWarps) refine_batch_kernel(const uint
     j.el_lo = pp.p.geom.el_lo_deg;
     j.el_step = pp.p.geom.el_step_deg;
     j.La = pp.p.grid.L;
+    j.Le = pp.p.geom.Le;
+    j.wrap = pp.p.geom.wrap_az;
   }
+  j.P = pp.p.P + (size_t)jb.slot * pp.npts;
   const int d = pp.p.d;
   const int n = min(pp.p.peak_count[jb.slot], d);
   const int per = j.pos ? 2 : 1;
