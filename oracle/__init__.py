@@ -19,6 +19,7 @@ compiles it with gcc on first use and exposes NumPy-friendly wrappers:
                  steering vector of Eq. 2 as printed (Sec. 4.2's circular array)
   refine_peak / refine_peak2d
               -- sub-grid refinement of a picked peak: the local minimiser of a^H C a next to it
+  model_order -- MDL / AIC source-count estimates from the eigenvalues (Wax & Kailath)
 
 The MLP oracle used for the learned proposal lives in ``oracle/mlp.py`` (NumPy, FP64).
 """
@@ -79,6 +80,8 @@ def _load():
             lib.oracle_refine_peak.restype = d
             lib.oracle_refine_peak2d.argtypes = [p, i, p, d, d, i, d, d, i, p, p]
             lib.oracle_refine_peak2d.restype = None
+            lib.oracle_model_order.argtypes = [p, i, i, p, p, p, p]
+            lib.oracle_model_order.restype = None
             _lib = lib
     return _lib
 
@@ -246,3 +249,15 @@ def refine_peak2d(C: np.ndarray, pos: np.ndarray, az_lo: float, az_step: float, 
     _load().oracle_refine_peak2d(_ptr(C), M, _ptr(pos), float(az_lo), float(az_step), int(La), float(el_lo),
                                  float(el_step), int(flat), _ptr(out), ctypes.byref(it))
     return (float(out[0]), float(out[1])), it.value
+
+
+def model_order(evals: np.ndarray, N: int):
+    """MDL and AIC estimates of the number of sources from descending eigenvalues and the snapshot
+    count. Returns (mdl, aic, mdl_values, aic_values)."""
+    ev = np.ascontiguousarray(evals, dtype=np.float64)
+    M = ev.shape[0]
+    mv = np.empty(M)
+    av = np.empty(M)
+    m, a = ctypes.c_int(0), ctypes.c_int(0)
+    _load().oracle_model_order(_ptr(ev), M, int(N), ctypes.byref(m), ctypes.byref(a), _ptr(mv), _ptr(av))
+    return m.value, a.value, mv, av

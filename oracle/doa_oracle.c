@@ -664,3 +664,45 @@ void oracle_refine_peak2d(const double *C, int M, const double *pos, double az_l
   out[1] = x[1] / d2r;
   free(Cm);
 }
+
+/* ---------------------------------------------------------------------------------------------
+ * Model-order estimation (beyond the paper, whose Table 2 takes D as given): the information
+ * criteria of Wax and Kailath (1985) for complex data from the sample eigenvalues lambda_0 >= ...
+ * >= lambda_{M-1} of R and the snapshot count N. For k assumed sources the M - k smallest
+ * eigenvalues are the noise ones; with their arithmetic mean a(k) and geometric mean g(k),
+ *   L(k)   = N (M - k) log(a(k) / g(k))           (>= 0, zero when they are all equal),
+ *   MDL(k) = L(k) + k (2M - k) log(N) / 2,
+ *   AIC(k) = 2 L(k) + 2 k (2M - k),
+ * for k = 0 .. M-1; the estimates are the k of the smallest value (the smaller k on a tie). A
+ * non-positive noise eigenvalue makes L(k) = +inf. mdl_val / aic_val (nullable) receive the M
+ * criterion values.
+ * ------------------------------------------------------------------------------------------- */
+void oracle_model_order(const double *evals, int M, int N, int *mdl, int *aic, double *mdl_val, double *aic_val) {
+  int best_m = 0, best_a = 0;
+  double vm = INFINITY, va = INFINITY;
+  for (int k = 0; k < M; ++k) {
+    int n = M - k;
+    double s = 0.0, ls = 0.0;
+    int bad = 0;
+    for (int i = k; i < M; ++i) {
+      s += evals[i];
+      if (evals[i] > 0.0) ls += log(evals[i]); else bad = 1;
+    }
+    double L = bad ? INFINITY : (double)N * (double)n * (log(s / (double)n) - ls / (double)n);
+    double pen = (double)k * (double)(2 * M - k);
+    double m = L + 0.5 * pen * log((double)N);
+    double a = 2.0 * L + 2.0 * pen;
+    if (mdl_val) mdl_val[k] = m;
+    if (aic_val) aic_val[k] = a;
+    if (m < vm) {
+      vm = m;
+      best_m = k;
+    }
+    if (a < va) {
+      va = a;
+      best_a = k;
+    }
+  }
+  *mdl = best_m;
+  *aic = best_a;
+}
