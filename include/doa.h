@@ -203,6 +203,18 @@ doa_status doa_peaks2d(const float *P, int La, int Le, int wrap_az, int d, int *
                        void *stream);
 
 /*
+ * Model-order estimation (Table 2 takes D as given; these are Wax and Kailath's information
+ * criteria for complex data): for k = 0..M-1 assumed sources, with a and g the arithmetic and
+ * geometric means of the M-k smallest eigenvalues,
+ *   L(k) = N (M-k) log(a/g)  (+inf when one of them is not positive),
+ *   MDL(k) = L(k) + k (2M-k) log(N) / 2,   AIC(k) = 2 L(k) + 2 k (2M-k);
+ * *mdl and *aic receive the argmin (the smaller k on a tie), in FP64.
+ *   evals : M device doubles, descending (as written by doa_noise_subspace); N: snapshots.
+ *   mdl, aic : device int32 (either may be NULL).
+ */
+doa_status doa_model_order(const double *evals, int M, int N, int *mdl, int *aic, void *stream);
+
+/*
  * Sub-grid refinement of picked peaks (beyond Step-6, which stops at the grid): for each peak the
  * local minimiser, in FP64, of den = ||B^H a||^2 (= a^H C a) next to it.
  *   ULA: bracketed Newton on den'(theta) = 0 inside [theta_{k-1}, theta_{k+1}] (steps shrink the
@@ -326,6 +338,8 @@ typedef struct {
   double *peak_angle;    /* nullable: sub-grid refined peak angles in degrees (see            */
                          /* doa_refine_peaks): nalg x d (ULA) or nalg x d x 2 (geometry:       */
                          /* azimuth, elevation), entries past peak_count untouched             */
+  int32_t *order_est;    /* nullable: 2 int32, the MDL and AIC source-count estimates from     */
+                         /* the eigenvalues (see doa_model_order); d itself stays as given     */
 } doa_problem;
 
 /* Peak polish: after Step-6 the spectrum is re-evaluated in FP64 (steering and contraction) at

@@ -60,6 +60,7 @@ bool problem_ok(const doa_problem &p) {
   if (p.flags & ~DOA_FLAG_POLISH_PEAKS) return false;
   if (p.d > 0 && (!p.peak_idx || !p.peak_val)) return false;
   if (p.peak_angle && !aligned(p.peak_angle, 8)) return false;
+  if (p.order_est && !aligned(p.order_est, 4)) return false;
   if (!p.peak_count) return false;
   if (p.geom.pos)   // 2-D scan: FP32 on CUDA cores, no peak polish
     return p.prec == DOA_FP32 && p.flags == 0 && geometry_ok(p.grid, p.geom);
@@ -329,6 +330,12 @@ doa_status doa_peaks2d(const float *P, int La, int Le, int wrap_az, int d, int *
     return DOA_EINVAL;
   if (!aligned(P, 4)) return DOA_EINVAL;
   return cuda_status(launch_peaks2d_single(P, La, Le, wrap_az, d, idx, val, count, as_stream(stream)));
+}
+
+doa_status doa_model_order(const double *evals, int M, int N, int *mdl, int *aic, void *stream) {
+  if (!evals || M < 1 || M > kMaxM || N < 1 || (!mdl && !aic)) return DOA_EINVAL;
+  if (!aligned(evals, 8) || (mdl && !aligned(mdl, 4)) || (aic && !aligned(aic, 4))) return DOA_EINVAL;
+  return cuda_status(launch_model_order_single(evals, M, N, mdl, aic, as_stream(stream)));
 }
 
 doa_status doa_refine_peaks(const double *B, int M, int K, doa_grid grid, const int *idx, const int *count,

@@ -292,6 +292,7 @@ cudaError_t launch_covariance_tc_single(const float2 *X, int M, int N, int ldx, 
 
 cudaError_t launch_eig_single(const double2 *R64, int M, int d, int alg, double *evals, double2 *B,
                               int *K_out, int *info, cudaStream_t s);
+cudaError_t launch_model_order_single(const double *evals, int M, int N, int *mdl, int *aic, cudaStream_t s);
 cudaError_t launch_eig_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, int *status,
                              cudaStream_t s);
 

@@ -18,6 +18,8 @@
 // (8 matrices of M <= 8, 4 of M <= 16, 2 of M <= 32); a matrix of M <= 64 gets a whole CTA.
 // The element updates of each matrix are spread over all threads of its group. A and V live in shared memory with a padded row stride
 // (NP + 1 complex128) so that column accesses by consecutive lanes hit distinct banks.
+#include <math_constants.h>
+
 #include "doa_internal.cuh"
 
 namespace doa {
@@ -572,6 +574,51 @@ __device__ bool noise_orthonormal(int M, int d, EigSmem<NP> &s) {
   return g::all(ok);
 }
 
+// Model-order estimates (Wax and Kailath's criteria for complex data) from the sorted eigenvalues:
+// for k assumed sources, L(k) = N (M-k) log(a/g) over the M-k smallest eigenvalues (arithmetic and
+// geometric means; +inf when one is not positive), MDL(k) = L + k(2M-k) log(N)/2, AIC(k) = 2L +
+// 2k(2M-k); out[0] = argmin MDL, out[1] = argmin AIC (the smaller k on a tie). The group's lanes
+// take one k each; the criterion values go to the A matrix's first row (no longer needed here).
+template <int NP>
+__device__ void model_order(int M, int N, EigSmem<NP> &s, int32_t *out) {
+  constexpr int T = grp_threads<NP>();
+  using g = Grp<T>;
+  const int lane = g::id();
+  const double logN = log((double)N);
+  for (int k = lane; k < M; k += T) {
+    const int n = M - k;
+    double sum = 0.0, ls = 0.0;
+    bool bad = false;
+    for (int i = k; i < M; ++i) {
+      const double l = s.lam[s.order[i]];
+      sum += l;
+      if (l > 0.0) ls += log(l); else bad = true;
+    }
+    const double L = bad ? CUDART_INF : (double)N * (double)n * (log(sum / (double)n) - ls / (double)n);
+    const double pen = (double)k * (double)(2 * M - k);
+    s.A[0][k] = make_double2(L + 0.5 * pen * logN, 2.0 * L + 2.0 * pen);
+  }
+  g::sync();
+  if (lane == 0) {
+    int bm = 0, ba = 0;
+    double vm = CUDART_INF, va = CUDART_INF;
+    for (int k = 0; k < M; ++k) {
+      const double2 v = s.A[0][k];
+      if (v.x < vm) {
+        vm = v.x;
+        bm = k;
+      }
+      if (v.y < va) {
+        va = v.y;
+        ba = k;
+      }
+    }
+    out[0] = bm;
+    out[1] = ba;
+  }
+  g::sync();
+}
+
 // Writes a batch problem's scan factor F (columns as laid out by the plan: E_n, or v_min; then
 // valph) and the EV weights w_c = 1 / lambda_{d+c}; returns 0 or a doa_status.
 template <int NP>
@@ -691,6 +738,10 @@ __global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_batch_kernel(const u
       st = build_scan_factor<NP>(pp, s, F, w);
       if (!noise_orthonormal<NP>(M, d, s) && !st) st = DOA_ENOCONV;
       if (pp.p.B_out) build_factor<NP>(M, d, jobs[pp.first_job].alg, s, reinterpret_cast<double2 *>(pp.p.B_out));
+      if (pp.p.order_est) {
+        Grp<T>::sync();
+        model_order<NP>(M, pp.p.N, s, pp.p.order_est);
+      }
     } else {
       st = -res[j];
       // a failed decomposition leaves a zero factor, so the scan writes the 1/FLT_MIN sentinel
@@ -737,6 +788,49 @@ cudaError_t run_batch(const uint8_t *plan, const PlanHeader &h, uint8_t *ws, int
 }
 
 }  // namespace
+
+namespace {
+__global__ void __launch_bounds__(32) model_order_single_kernel(const double *evals, int M, int N, int *mdl, int *aic) {
+  __shared__ double2 v[kMaxM];
+  const int lane = threadIdx.x;
+  const double logN = log((double)N);
+  for (int k = lane; k < M; k += 32) {
+    const int n = M - k;
+    double sum = 0.0, ls = 0.0;
+    bool bad = false;
+    for (int i = k; i < M; ++i) {
+      const double l = evals[i];
+      sum += l;
+      if (l > 0.0) ls += log(l); else bad = true;
+    }
+    const double L = bad ? CUDART_INF : (double)N * (double)n * (log(sum / (double)n) - ls / (double)n);
+    const double pen = (double)k * (double)(2 * M - k);
+    v[k] = make_double2(L + 0.5 * pen * logN, 2.0 * L + 2.0 * pen);
+  }
+  __syncwarp();
+  if (lane == 0) {
+    int bm = 0, ba = 0;
+    double vm = CUDART_INF, va = CUDART_INF;
+    for (int k = 0; k < M; ++k) {
+      if (v[k].x < vm) {
+        vm = v[k].x;
+        bm = k;
+      }
+      if (v[k].y < va) {
+        va = v[k].y;
+        ba = k;
+      }
+    }
+    if (mdl) *mdl = bm;
+    if (aic) *aic = ba;
+  }
+}
+}  // namespace
+
+cudaError_t launch_model_order_single(const double *evals, int M, int N, int *mdl, int *aic, cudaStream_t s) {
+  model_order_single_kernel<<<1, 32, 0, s>>>(evals, M, N, mdl, aic);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_eig_single(const double2 *R64, int M, int d, int alg, double *evals, double2 *B, int *K_out,
                               int *info, cudaStream_t s) {
