@@ -51,7 +51,7 @@ def workload_name(batch):
 # when its kernel changes.
 TRAFFIC_BYTES = {
     "scan_batch_kernel<16,2>": 4 * (4.137728e6 + 235.058176e6),
-    "scan_geometry_batch_kernel<8,2>": None,
+    "scan_geometry_batch_kernel<8,2>": 2 * (2.72384e6 + 205.792256e6),
 }
 
 
