@@ -20,6 +20,9 @@ compiles it with gcc on first use and exposes NumPy-friendly wrappers:
   refine_peak / refine_peak2d
               -- sub-grid refinement of a picked peak: the local minimiser of a^H C a next to it
   model_order -- MDL / AIC source-count estimates from the eigenvalues (Wax & Kailath)
+  root_polynomial / root_music
+              -- the ULA scan's denominator as a polynomial on the unit circle and its roots
+                 (numpy.roots as the root finder)
 
 The MLP oracle used for the learned proposal lives in ``oracle/mlp.py`` (NumPy, FP64).
 """
@@ -261,3 +264,29 @@ def model_order(evals: np.ndarray, N: int):
     m, a = ctypes.c_int(0), ctypes.c_int(0)
     _load().oracle_model_order(_ptr(ev), M, int(N), ctypes.byref(m), ctypes.byref(a), _ptr(mv), _ptr(av))
     return m.value, a.value, mv, av
+
+
+def root_polynomial(C: np.ndarray) -> np.ndarray:
+    """Coefficients of the root form of the ULA scan's denominator: on |z| = 1, with z = e^{j pi sin
+    theta}, a(theta)^H C a(theta) = sum_l c_l z^l, c_l = sum over the l-th diagonal (j - i = l) of C.
+    Returned highest power first (numpy.roots order) for z^{M-1} D(z), degree 2M-2."""
+    C = np.asarray(C, dtype=np.complex128)
+    M = C.shape[0]
+    c = np.zeros(2 * M - 1, dtype=np.complex128)          # c[l + M - 1] = c_l
+    for i in range(M):
+        for j in range(M):
+            c[j - i + M - 1] += C[i, j]
+    return c[::-1].copy()
+
+
+def root_music(C: np.ndarray, d: int):
+    """Root-MUSIC on the ULA: the roots of z^{M-1} D(z) (numpy.roots: companion-matrix eigenvalues)
+    come in pairs z, 1/conj(z); the d roots with |z| <= 1 closest to the unit circle give the
+    angles theta = asin(arg(z) / pi) (degrees, ascending). Returns (angles, selected roots)."""
+    roots = np.roots(root_polynomial(C))
+    inside = roots[np.abs(roots) <= 1.0]
+    order = np.argsort(-np.abs(inside), kind="stable")
+    pick = inside[order[:d]]
+    ang = np.degrees(np.arcsin(np.clip(np.angle(pick) / np.pi, -1.0, 1.0)))
+    o = np.argsort(ang)
+    return ang[o], pick[o]
