@@ -215,6 +215,18 @@ doa_status doa_peaks2d(const float *P, int La, int Le, int wrap_az, int d, int *
 doa_status doa_model_order(const double *evals, int M, int N, int *mdl, int *aic, void *stream);
 
 /*
+ * Root form of the ULA scan (root-MUSIC for the MUSIC factor; any factor B works the same way): on
+ * |z| = 1, z = e^{j pi sin theta}, ||B^H a||^2 = sum_{l=-(M-1)}^{M-1} c_l z^l with
+ * c_l = sum_k sum_n B_nk conj(B_{n+l,k}); the roots of the degree-(2M-2) polynomial z^{M-1} D(z)
+ * pair up as z, 1/conj(z), and the d roots with |z| <= 1 closest to the unit circle give
+ * theta = asin(arg(z) / pi). Roots by the Aberth-Ehrlich iteration in FP64 (converged when every
+ * correction is below 1e-14 max(1, |z|), 400 iterations at most).
+ *   B, M, K : as for doa_scan.  d: 1 <= d < M.  theta: d device doubles (ascending, degrees; NaN
+ *   when the iteration fails).  info: device int32, 0 or -DOA_ENOCONV.
+ */
+doa_status doa_root_music(const double *B, int M, int K, int d, double *theta, int *info, void *stream);
+
+/*
  * Sub-grid refinement of picked peaks (beyond Step-6, which stops at the grid): for each peak the
  * local minimiser, in FP64, of den = ||B^H a||^2 (= a^H C a) next to it.
  *   ULA: bracketed Newton on den'(theta) = 0 inside [theta_{k-1}, theta_{k+1}] (steps shrink the
@@ -340,6 +352,9 @@ typedef struct {
                          /* azimuth, elevation), entries past peak_count untouched             */
   int32_t *order_est;    /* nullable: 2 int32, the MDL and AIC source-count estimates from     */
                          /* the eigenvalues (see doa_model_order); d itself stays as given     */
+  double *root_angle;    /* nullable, ULA problems only: nalg x d angles (degrees, ascending)   */
+                         /* from the roots of the scan's polynomial (see doa_root_music);      */
+                         /* status DOA_ENOCONV (angles NaN) if the root iteration fails        */
 } doa_problem;
 
 /* Peak polish: after Step-6 the spectrum is re-evaluated in FP64 (steering and contraction) at

@@ -61,6 +61,7 @@ bool problem_ok(const doa_problem &p) {
   if (p.d > 0 && (!p.peak_idx || !p.peak_val)) return false;
   if (p.peak_angle && !aligned(p.peak_angle, 8)) return false;
   if (p.order_est && !aligned(p.order_est, 4)) return false;
+  if (p.root_angle && (!aligned(p.root_angle, 8) || p.geom.pos || p.d < 1)) return false;
   if (!p.peak_count) return false;
   if (p.geom.pos)   // 2-D scan: FP32 on CUDA cores, no peak polish
     return p.prec == DOA_FP32 && p.flags == 0 && geometry_ok(p.grid, p.geom);
@@ -332,6 +333,13 @@ doa_status doa_peaks2d(const float *P, int La, int Le, int wrap_az, int d, int *
   return cuda_status(launch_peaks2d_single(P, La, Le, wrap_az, d, idx, val, count, as_stream(stream)));
 }
 
+doa_status doa_root_music(const double *B, int M, int K, int d, double *theta, int *info, void *stream) {
+  if (!B || !theta || !info || M < 2 || M > kMaxM || K < 1 || K > M || d < 1 || d >= M) return DOA_EINVAL;
+  if (!aligned(B, 16) || !aligned(theta, 8) || !aligned(info, 4)) return DOA_EINVAL;
+  return cuda_status(launch_roots_single(reinterpret_cast<const double2 *>(B), M, K, d, theta, info,
+                                         as_stream(stream)));
+}
+
 doa_status doa_model_order(const double *evals, int M, int N, int *mdl, int *aic, void *stream) {
   if (!evals || M < 1 || M > kMaxM || N < 1 || (!mdl && !aic)) return DOA_EINVAL;
   if (!aligned(evals, 8) || (mdl && !aligned(mdl, 4)) || (aic && !aligned(aic, 4))) return DOA_EINVAL;
@@ -492,6 +500,7 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     factor_layout(p, q);
     if (p.flags & DOA_FLAG_POLISH_PEAKS) ++h.npolish;
     if (p.peak_angle) ++h.nrefine;
+    if (p.root_angle) ++h.nroots;
     q.fac_off = ws;
     ws = round_up(ws + factor_bytes(M), 256);
     if (p.geom.pos) {
@@ -548,6 +557,7 @@ doa_status doa_solve_batch(const void *plan_host, const void *plan_dev, void *ws
       (launch_polish_batch(pd, h, w, s) != cudaSuccess || launch_peaks_batch(pd, h, true, false, s) != cudaSuccess))
     return DOA_ECUDA;
   if (launch_refine_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
+  if (launch_roots_batch(pd, h, w, status, s) != cudaSuccess) return DOA_ECUDA;
   if (!mark(5)) return DOA_ECUDA;
   return DOA_OK;
 }

@@ -238,11 +238,12 @@ struct PlanHeader {
   int32_t geo_grid_points;               // largest La + Le among them
   int64_t off_geo_grid;
   int32_t nrefine;                       // problems with a peak_angle output (sub-grid refinement)
-  int32_t pad4;
+  int32_t nroots;                        // problems with a root_angle output (root form of the scan)
 };
 
 // The Python binding reads these header fields by position (int32 index 22 = scan_pt, 58 = eig_mats,
-// 62 = cov_first, 67 = tc_jobs, 74 = npolish, 76 = geo_jobs, 96 = ngeo_grids, 100 = nrefine).
+// 62 = cov_first, 67 = tc_jobs, 74 = npolish, 76 = geo_jobs, 96 = ngeo_grids, 100 = nrefine,
+// 101 = nroots).
 static_assert(offsetof(PlanHeader, scan_pt) == 88, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, scan_tiles) == 56, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, eig_mats) == 232, "PlanHeader layout changed");
@@ -252,6 +253,7 @@ static_assert(offsetof(PlanHeader, npolish) == 296, "PlanHeader layout changed")
 static_assert(offsetof(PlanHeader, geo_jobs) == 304, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, ngeo_grids) == 384, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, nrefine) == 400, "PlanHeader layout changed");
+static_assert(offsetof(PlanHeader, nroots) == 404, "PlanHeader layout changed");
 
 // Scan tiles: kScanThreads threads, each evaluating PT consecutive grid points (tile shape
 // 128 x PT). PT is chosen per M bucket (the autotuner's knob); the register budget limits it
@@ -327,6 +329,8 @@ cudaError_t launch_peaks2d_single(const float *P, int La, int Le, int wrap_az, i
 // ula / geo: launch the 1-D and / or the 2-D peak kernel (each only when the plan has such jobs).
 cudaError_t launch_peaks_batch(const uint8_t *plan_dev, const PlanHeader &h, bool ula, bool geo, cudaStream_t s);
 cudaError_t launch_polish_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
+cudaError_t launch_roots_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, int *status, cudaStream_t s);
+cudaError_t launch_roots_single(const double2 *B, int M, int K, int d, double *theta, int *info, cudaStream_t s);
 cudaError_t launch_refine_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
 // pos == null: ULA grid (lo, step); else geometry with azimuth (lo, step, La) and elevation (el_lo, el_step).
 cudaError_t launch_refine_single(const double2 *B, int M, int K, double lo, double step, const double *pos,

@@ -1,0 +1,212 @@
+// Root form of the ULA scan (root-MUSIC; beyond the paper, which evaluates the spectrum on a grid).
+// On the unit circle, with z = e^{j pi sin theta}, the scan's denominator is a Laurent polynomial:
+//   a(theta)^H C a(theta) = sum_{l=-(M-1)}^{M-1} c_l z^l,   c_l = sum_{j-i=l} C_ij,
+// and with C = sum_k w_k f_k f_k^H (the readout's factor columns and weights, Table 3),
+//   c_l = sum_k w_k sum_n f_nk conj(f_{n+l,k}).
+// z^{M-1} D(z) is a polynomial of degree 2M-2 whose roots pair up as z, 1/conj(z); the d roots with
+// |z| <= 1 closest to the unit circle give the estimates theta = asin(arg(z) / pi).
+//
+// Roots by the Aberth-Ehrlich iteration in FP64 (simultaneous Newton corrections with the
+// repulsion sum over the other roots), all corrections computed from the previous iterate, started
+// on the unit circle at angles 2 pi i / n + 0.4; converged when every correction is below
+// 1e-14 max(1, |z|); 400 iterations at most (else DOA_ENOCONV). One warp per (problem, algorithm)
+// job: lanes own coefficients, then roots; the selection runs on lane 0.
+#include <math_constants.h>
+
+#include "doa_internal.cuh"
+
+namespace doa {
+namespace {
+
+constexpr int kRootWarps = 4;
+constexpr int kMaxDeg = 2 * kMaxM - 2;
+constexpr int kRootMaxIter = 400;
+
+struct RootShared {
+  double2 a[kMaxDeg + 1];   // polynomial coefficients, a[t] multiplies z^t
+  double2 z[kMaxDeg];       // current roots
+  double2 w[kMaxDeg];       // corrections of this iteration
+};
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double inv = 1.0 / (b.x * b.x + b.y * b.y);
+  return make_double2((a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv);
+}
+
+struct RootJob {
+  const double2 *F;   // factor, column-major, ld M
+  const double *w;    // EV weights or null
+  int M, Kf, Kn, kphd, kmn, alg, d;
+};
+
+__device__ __forceinline__ double root_weight(const RootJob &j, int c) {
+  switch (j.alg) {
+    case DOA_MUSIC: return c < j.Kn ? 1.0 : 0.0;
+    case DOA_EV: return c < j.Kn ? (j.w ? j.w[c] : 1.0) : 0.0;
+    case DOA_PHD: return c == j.kphd ? 1.0 : 0.0;
+    case DOA_MN: return c == j.kmn ? 1.0 : 0.0;
+    default: return c < j.Kf ? 1.0 : 0.0;
+  }
+}
+
+// Writes the d angles (degrees, ascending) of one job to out; returns 0 or DOA_ENOCONV.
+__device__ int root_music_warp(const RootJob &j, RootShared &sh, double *out) {
+  const int lane = threadIdx.x & 31;
+  const int M = j.M, n = 2 * M - 2;
+  // coefficients: a[t] = c_{t - (M-1)}
+  for (int t = lane; t <= n; t += 32) {
+    const int l = t - (M - 1);
+    double cr = 0.0, ci = 0.0;
+    for (int c = 0; c < j.Kf; ++c) {
+      const double wc = root_weight(j, c);
+      if (wc == 0.0) continue;
+      const double2 *f = j.F + (size_t)c * M;
+      double sr = 0.0, si = 0.0;
+      for (int q = max(0, -l); q < M && q + l < M; ++q) {   // f_q conj(f_{q+l})
+        const double2 x = f[q], y = f[q + l];
+        sr = fma(x.x, y.x, fma(x.y, y.y, sr));
+        si = fma(x.y, y.x, fma(-x.x, y.y, si));
+      }
+      cr = fma(wc, sr, cr);
+      ci = fma(wc, si, ci);
+    }
+    sh.a[t] = make_double2(cr, ci);
+  }
+  for (int i = lane; i < n; i += 32) {
+    double s, c;
+    sincos(2.0 * CUDART_PI * (double)i / (double)n + 0.4, &s, &c);
+    sh.z[i] = make_double2(c, s);
+  }
+  __syncwarp();
+  int st = DOA_ENOCONV;
+  const double2 lead = sh.a[n];
+  if (lead.x * lead.x + lead.y * lead.y > 0.0) {
+    for (int it = 0; it < kRootMaxIter; ++it) {
+      bool small = true;
+      for (int i = lane; i < n; i += 32) {
+        const double2 zi = sh.z[i];
+        double2 p = sh.a[n], dp = make_double2(0.0, 0.0);
+        for (int t = n - 1; t >= 0; --t) {          // Horner for p and p'
+          dp = cadd(cmul(dp, zi), p);
+          p = cadd(cmul(p, zi), sh.a[t]);
+        }
+        double2 rep = make_double2(0.0, 0.0);       // sum_{k != i} 1 / (z_i - z_k)
+        for (int k = 0; k < n; ++k) {
+          if (k == i) continue;
+          rep = cadd(rep, cdiv(make_double2(1.0, 0.0), csub(zi, sh.z[k])));
+        }
+        const double2 ratio = cdiv(p, dp);
+        const double2 den = csub(make_double2(1.0, 0.0), cmul(ratio, rep));
+        const double2 wi = cdiv(ratio, den);
+        sh.w[i] = wi;
+        const double mag = sqrt(wi.x * wi.x + wi.y * wi.y), zm = sqrt(zi.x * zi.x + zi.y * zi.y);
+        small = small && (mag <= 1e-14 * fmax(1.0, zm));
+        small = small && isfinite(mag);
+      }
+      __syncwarp();
+      for (int i = lane; i < n; i += 32) sh.z[i] = csub(sh.z[i], sh.w[i]);
+      __syncwarp();
+      if (__all_sync(0xffffffffu, small)) {
+        st = 0;
+        break;
+      }
+    }
+  }
+  if (lane == 0) {
+    // the d roots with |z| <= 1 of largest modulus (lower index on a tie), then angles ascending
+    double sel[kMaxM];
+    int ns = 0;
+    if (st == 0) {
+      int taken[kMaxM];
+      for (int q = 0; q < j.d; ++q) {
+        int best = -1;
+        double bm = -1.0;
+        for (int i = 0; i < n; ++i) {
+          const double2 zi = sh.z[i];
+          const double m = sqrt(zi.x * zi.x + zi.y * zi.y);
+          if (!(m <= 1.0) || !(m > bm)) continue;
+          bool used = false;
+          for (int r = 0; r < ns; ++r) used = used || taken[r] == i;
+          if (used) continue;
+          best = i;
+          bm = m;
+        }
+        if (best < 0) break;
+        taken[ns] = best;
+        const double2 zb = sh.z[best];
+        const double sx = fmin(fmax(atan2(zb.y, zb.x) / CUDART_PI, -1.0), 1.0);
+        sel[ns++] = asin(sx) * (180.0 / CUDART_PI);
+      }
+      for (int a = 1; a < ns; ++a) {
+        const double v = sel[a];
+        int b = a - 1;
+        while (b >= 0 && sel[b] > v) {
+          sel[b + 1] = sel[b];
+          --b;
+        }
+        sel[b + 1] = v;
+      }
+      if (ns < j.d) st = DOA_ENOCONV;
+    }
+    for (int q = 0; q < j.d; ++q) out[q] = q < ns ? sel[q] : CUDART_NAN;
+  }
+  __syncwarp();
+  return st;
+}
+
+__global__ void __launch_bounds__(32 * kRootWarps) roots_batch_kernel(const uint8_t *plan, uint8_t *ws, int *status) {
+  __shared__ RootShared sh[kRootWarps];
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
+  const int warp = threadIdx.x >> 5;
+  const int job = blockIdx.x * kRootWarps + warp;
+  if (job >= h->njobs) return;
+  const PlanJob &jb = reinterpret_cast<const PlanJob *>(plan + h->off_job)[job];
+  const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[jb.prob];
+  if (!pp.p.root_angle || pp.p.d < 1) return;
+  if (status[jb.prob] != 0) return;     // no decomposition to root
+  RootJob j{};
+  j.F = reinterpret_cast<const double2 *>(ws + pp.fac_off);
+  j.w = pp.Kn > 0 && pp.slot[DOA_EV] >= 0
+            ? reinterpret_cast<const double *>(ws + pp.fac_off) + 2 * pp.p.M * (pp.p.M + 1)
+            : nullptr;
+  j.M = pp.p.M;
+  j.Kf = pp.Kf;
+  j.Kn = pp.Kn;
+  j.kphd = pp.kphd;
+  j.kmn = pp.kmn;
+  j.alg = jb.alg;
+  j.d = pp.p.d;
+  const int st = root_music_warp(j, sh[warp], pp.p.root_angle + (size_t)jb.slot * pp.p.d);
+  if (st && (threadIdx.x & 31) == 0) atomicCAS(status + jb.prob, 0, st);
+}
+
+__global__ void __launch_bounds__(32) roots_single_kernel(RootJob j, double *theta, int *info) {
+  __shared__ RootShared sh;
+  const int st = root_music_warp(j, sh, theta);
+  if (threadIdx.x == 0) *info = st ? -st : 0;
+}
+
+}  // namespace
+
+cudaError_t launch_roots_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, int *status, cudaStream_t s) {
+  if (h.nroots == 0 || h.njobs == 0) return cudaSuccess;
+  roots_batch_kernel<<<(h.njobs + kRootWarps - 1) / kRootWarps, 32 * kRootWarps, 0, s>>>(plan_dev, ws, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_roots_single(const double2 *B, int M, int K, int d, double *theta, int *info, cudaStream_t s) {
+  RootJob j{};
+  j.F = B;
+  j.M = M;
+  j.Kf = K;
+  j.Kn = K;
+  j.kphd = j.kmn = -1;
+  j.alg = -1;
+  j.d = d;
+  roots_single_kernel<<<1, 32, 0, s>>>(j, theta, info);
+  return cudaGetLastError();
+}
+
+}  // namespace doa

@@ -31,7 +31,7 @@ EXPORTS = ("doa_status_str", "doa_covariance", "doa_covariance_noalloc", "doa_no
            "doa_mlp_refresh", "doa_mlp_forward", "doa_mlp_backward", "doa_mlp_adam", "doa_synth_ula",
            "doa_proposal_windows", "doa_scan_windows", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices", "doa_probe_fma",
            "doa_scan_geometry", "doa_scan_geometry_ws_bytes", "doa_peaks2d", "doa_refine_peaks",
-           "doa_refine_peaks2d", "doa_model_order")
+           "doa_refine_peaks2d", "doa_model_order", "doa_root_music")
 SLICE_MAXD = 64
 
 
@@ -60,7 +60,8 @@ class Problem(ctypes.Structure):
                 ("N", ctypes.c_int32), ("ldx", ctypes.c_int32), ("d", ctypes.c_int32),
                 ("alg_mask", ctypes.c_uint32), ("prec", ctypes.c_int32), ("features", ctypes.c_void_p),
                 ("B_out", ctypes.c_void_p), ("eig_prec", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("geom", Geometry), ("peak_angle", ctypes.c_void_p), ("order_est", ctypes.c_void_p)]
+                ("geom", Geometry), ("peak_angle", ctypes.c_void_p), ("order_est", ctypes.c_void_p),
+                ("root_angle", ctypes.c_void_p)]
 
 
 class SliceSummary(ctypes.Structure):
@@ -97,11 +98,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.doa_peaks2d.argtypes = [vp, i, i, i, i, vp, vp, vp, vp]
     lib.doa_refine_peaks.argtypes = [vp, i, i, Grid, vp, vp, i, vp, vp]
     lib.doa_model_order.argtypes = [vp, i, i, vp, vp, vp]
+    lib.doa_root_music.argtypes = [vp, i, i, i, vp, vp, vp]
     lib.doa_refine_peaks2d.argtypes = [vp, i, i, Grid, Geometry, vp, vp, i, vp, vp]
     for name in ("doa_covariance", "doa_covariance_noalloc", "doa_noise_subspace", "doa_scan", "doa_peaks",
                  "doa_batch_plan", "doa_solve_batch", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices", "doa_probe_fma",
                  "doa_scan_geometry", "doa_scan_geometry_ws_bytes", "doa_peaks2d", "doa_refine_peaks",
-           "doa_refine_peaks2d", "doa_model_order"):
+           "doa_refine_peaks2d", "doa_model_order", "doa_root_music"):
         getattr(lib, name).restype = i
     return lib
 
@@ -252,6 +254,13 @@ def doa_scan_geometry(B: torch.Tensor, M: int, K: int, az: Grid, geom: Geometry,
                                    _stream(stream)), "doa_scan_geometry")
 
 
+def doa_root_music(B: torch.Tensor, M: int, K: int, d: int, theta: torch.Tensor, info: torch.Tensor,
+                   stream=None) -> None:
+    """Root form of the ULA scan: d angles (degrees, ascending) from the polynomial's roots."""
+    assert theta.dtype == torch.float64 and theta.numel() >= d
+    _check(lib().doa_root_music(_dev(B), M, K, d, _dev(theta), _dev(info), _stream(stream)), "doa_root_music")
+
+
 def doa_model_order(evals: torch.Tensor, N: int, out: torch.Tensor, stream=None) -> None:
     """MDL and AIC source-count estimates (out: 2 int32 on the device) from descending eigenvalues."""
     _check(lib().doa_model_order(_dev(evals), evals.numel(), N, _dev(out), out.data_ptr() + 4, _stream(stream)),
@@ -286,7 +295,7 @@ def make_problem(X: torch.Tensor, d: int, alg_mask: int, g: Grid, P: torch.Tenso
                  prec: int = FP32, features: Optional[torch.Tensor] = None,
                  B_out: Optional[torch.Tensor] = None, eig_prec: int = 0, polish: bool = False,
                  geom: Optional[Geometry] = None, peak_angle: Optional[torch.Tensor] = None,
-                 order_est: Optional[torch.Tensor] = None) -> Problem:
+                 order_est: Optional[torch.Tensor] = None, root_angle: Optional[torch.Tensor] = None) -> Problem:
     """Descriptor of one problem; the tensors must outlive every solve that uses it. With geom the
     problem is a 2-D scan: g is the azimuth grid, P holds nalg x (Le x La) floats."""
     assert X.dtype == torch.complex64 and X.dim() == 2 and X.stride(1) == 1
@@ -294,7 +303,7 @@ def make_problem(X: torch.Tensor, d: int, alg_mask: int, g: Grid, P: torch.Tenso
     return Problem(_dev(X), _dev(P), _dev(peak_idx), _dev(peak_val), _dev(peak_count), _dev(evals), g,
                    M, N, X.stride(0), d, alg_mask, prec, _dev(features), _dev(B_out), eig_prec,
                    FLAG_POLISH_PEAKS if polish else 0, geom if geom is not None else Geometry(None, 0.0, 0.0, 0, 0),
-                   _dev(peak_angle), _dev(order_est))
+                   _dev(peak_angle), _dev(order_est), _dev(root_angle))
 
 
 class Tuning(ctypes.Structure):
@@ -338,7 +347,7 @@ class BatchPlan:
         """int32 index of a PlanHeader field (layout of csrc/doa_internal.cuh)."""
         order = {"magic": 0, "nprob": 1, "njobs": 2, "ngrids": 3, "ncov": 4, "nreduce": 5, "eig_count": 6,
                  "scan_jobs": 10, "scan_tiles": 14, "scan_pt": 22, "eig_mats": 58, "cov_first": 62, "tc_jobs": 67,
-                 "npolish": 74, "geo_jobs": 76, "ngeo_grids": 96, "nrefine": 100}
+                 "npolish": 74, "geo_jobs": 76, "ngeo_grids": 96, "nrefine": 100, "nroots": 101}
         return order[field]
 
     def launches(self) -> int:
@@ -350,7 +359,7 @@ class BatchPlan:
         scan_b = sum(int(c) > 0 for c in h[10:14]) + int(h[67] > 0) + sum(int(c) > 0 for c in h[76:80])
         ngeo = sum(int(c) for c in h[76:80])
         peaks = int(ngeo < int(h[1])) + int(ngeo > 0) + (2 if int(h[74]) > 0 else 0)
-        return int(h[3] > 0) + int(h[96] > 0) + cov + eig_b + scan_b + peaks + int(h[100] > 0)
+        return int(h[3] > 0) + int(h[96] > 0) + cov + eig_b + scan_b + peaks + int(h[100] > 0) + int(h[101] > 0)
 
 
 def doa_solve_batch(plan: BatchPlan, ws: torch.Tensor, status: torch.Tensor, stage_events=None,
