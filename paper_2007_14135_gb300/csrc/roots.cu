@@ -8,9 +8,12 @@
 //
 // Roots by the Aberth-Ehrlich iteration in FP64 (simultaneous Newton corrections with the
 // repulsion sum over the other roots), all corrections computed from the previous iterate, started
-// on the unit circle at angles 2 pi i / n + 0.4; converged when every correction is below
-// 1e-14 max(1, |z|); 400 iterations at most (else DOA_ENOCONV). One warp per (problem, algorithm)
-// job: lanes own coefficients, then roots; the selection runs on lane 0.
+// on the unit circle at angles 2 pi i / n + 0.4; a root counts as converged when its correction is
+// below 1e-14 max(1, |z|) or when |p(z)| is within the rounding bound of its Horner evaluation,
+// 8 n eps sum_t |a_t| |z|^t (clustered roots -- the pairs z, 1/conj(z) near the circle -- cannot be
+// resolved further); the iteration ends when all have, 400 iterations at most (else DOA_ENOCONV).
+// One warp per (problem, algorithm) job: lanes own coefficients, then roots; the selection runs on
+// lane 0.
 #include <math_constants.h>
 
 #include "doa_internal.cuh"
@@ -87,10 +90,13 @@ __device__ int root_music_warp(const RootJob &j, RootShared &sh, double *out) {
       bool small = true;
       for (int i = lane; i < n; i += 32) {
         const double2 zi = sh.z[i];
+        const double zm = sqrt(zi.x * zi.x + zi.y * zi.y);
         double2 p = sh.a[n], dp = make_double2(0.0, 0.0);
-        for (int t = n - 1; t >= 0; --t) {          // Horner for p and p'
+        double pe = sqrt(sh.a[n].x * sh.a[n].x + sh.a[n].y * sh.a[n].y);
+        for (int t = n - 1; t >= 0; --t) {          // Horner for p, p' and the bound sum |a_t| |z|^t
           dp = cadd(cmul(dp, zi), p);
           p = cadd(cmul(p, zi), sh.a[t]);
+          pe = fma(pe, zm, sqrt(sh.a[t].x * sh.a[t].x + sh.a[t].y * sh.a[t].y));
         }
         double2 rep = make_double2(0.0, 0.0);       // sum_{k != i} 1 / (z_i - z_k)
         for (int k = 0; k < n; ++k) {
@@ -101,9 +107,9 @@ __device__ int root_music_warp(const RootJob &j, RootShared &sh, double *out) {
         const double2 den = csub(make_double2(1.0, 0.0), cmul(ratio, rep));
         const double2 wi = cdiv(ratio, den);
         sh.w[i] = wi;
-        const double mag = sqrt(wi.x * wi.x + wi.y * wi.y), zm = sqrt(zi.x * zi.x + zi.y * zi.y);
-        small = small && (mag <= 1e-14 * fmax(1.0, zm));
-        small = small && isfinite(mag);
+        const double mag = sqrt(wi.x * wi.x + wi.y * wi.y);
+        const double res = sqrt(p.x * p.x + p.y * p.y);
+        small = small && isfinite(mag) && (mag <= 1e-14 * fmax(1.0, zm) || res <= 8.0 * n * 1.1102230246251565e-16 * pe);
       }
       __syncwarp();
       for (int i = lane; i < n; i += 32) sh.z[i] = csub(sh.z[i], sh.w[i]);
