@@ -11,9 +11,9 @@
 // on the unit circle at angles 2 pi i / n + 0.4; a root counts as converged when its correction is
 // below 1e-14 max(1, |z|) or when |p(z)| is within the rounding bound of its Horner evaluation,
 // 8 n eps sum_t |a_t| |z|^t (clustered roots -- the pairs z, 1/conj(z) near the circle -- cannot be
-// resolved further); the iteration ends when all have, 400 iterations at most (else DOA_ENOCONV).
-// One warp per (problem, algorithm) job: lanes own coefficients, then roots; the selection runs on
-// lane 0.
+// resolved further). A converged root keeps its value and takes no further correction; the
+// iteration ends when all have converged, 400 iterations at most (else DOA_ENOCONV). One warp per
+// (problem, algorithm) job: lanes own coefficients, then roots; the selection runs on lane 0.
 #include <math_constants.h>
 
 #include "doa_internal.cuh"
@@ -27,15 +27,21 @@ constexpr int kRootMaxIter = 400;
 
 struct RootShared {
   double2 a[kMaxDeg + 1];   // polynomial coefficients, a[t] multiplies z^t
+  double am[kMaxDeg + 1];   // |a_t| (for the rounding bound of the Horner evaluation)
   double2 z[kMaxDeg];       // current roots
   double2 w[kMaxDeg];       // corrections of this iteration
+  int conv[kMaxDeg];        // root converged (its correction is no longer computed)
 };
 
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
-  const double inv = 1.0 / (b.x * b.x + b.y * b.y);
+  const double inv = __drcp_rn(b.x * b.x + b.y * b.y);
   return make_double2((a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv);
+}
+__device__ __forceinline__ double2 crcp(double2 b) {   // 1 / b
+  const double inv = __drcp_rn(b.x * b.x + b.y * b.y);
+  return make_double2(b.x * inv, -b.y * inv);
 }
 
 struct RootJob {
@@ -76,11 +82,14 @@ __device__ int root_music_warp(const RootJob &j, RootShared &sh, double *out) {
       ci = fma(wc, si, ci);
     }
     sh.a[t] = make_double2(cr, ci);
+    sh.am[t] = sqrt(cr * cr + ci * ci);
   }
   for (int i = lane; i < n; i += 32) {
     double s, c;
     sincos(2.0 * CUDART_PI * (double)i / (double)n + 0.4, &s, &c);
     sh.z[i] = make_double2(c, s);
+    sh.w[i] = make_double2(0.0, 0.0);
+    sh.conv[i] = 0;
   }
   __syncwarp();
   int st = DOA_ENOCONV;
@@ -89,19 +98,20 @@ __device__ int root_music_warp(const RootJob &j, RootShared &sh, double *out) {
     for (int it = 0; it < kRootMaxIter; ++it) {
       bool small = true;
       for (int i = lane; i < n; i += 32) {
+        if (sh.conv[i]) continue;                    // converged: no more correction
         const double2 zi = sh.z[i];
         const double zm = sqrt(zi.x * zi.x + zi.y * zi.y);
         double2 p = sh.a[n], dp = make_double2(0.0, 0.0);
-        double pe = sqrt(sh.a[n].x * sh.a[n].x + sh.a[n].y * sh.a[n].y);
+        double pe = sh.am[n];
         for (int t = n - 1; t >= 0; --t) {          // Horner for p, p' and the bound sum |a_t| |z|^t
           dp = cadd(cmul(dp, zi), p);
           p = cadd(cmul(p, zi), sh.a[t]);
-          pe = fma(pe, zm, sqrt(sh.a[t].x * sh.a[t].x + sh.a[t].y * sh.a[t].y));
+          pe = fma(pe, zm, sh.am[t]);
         }
         double2 rep = make_double2(0.0, 0.0);       // sum_{k != i} 1 / (z_i - z_k)
         for (int k = 0; k < n; ++k) {
           if (k == i) continue;
-          rep = cadd(rep, cdiv(make_double2(1.0, 0.0), csub(zi, sh.z[k])));
+          rep = cadd(rep, crcp(csub(zi, sh.z[k])));
         }
         const double2 ratio = cdiv(p, dp);
         const double2 den = csub(make_double2(1.0, 0.0), cmul(ratio, rep));
@@ -109,10 +119,15 @@ __device__ int root_music_warp(const RootJob &j, RootShared &sh, double *out) {
         sh.w[i] = wi;
         const double mag = sqrt(wi.x * wi.x + wi.y * wi.y);
         const double res = sqrt(p.x * p.x + p.y * p.y);
-        small = small && isfinite(mag) && (mag <= 1e-14 * fmax(1.0, zm) || res <= 8.0 * n * 1.1102230246251565e-16 * pe);
+        const bool ok = isfinite(mag) && (mag <= 1e-14 * fmax(1.0, zm) || res <= 8.0 * n * 1.1102230246251565e-16 * pe);
+        small = small && ok;
+        if (ok) sh.conv[i] = 1;
       }
       __syncwarp();
-      for (int i = lane; i < n; i += 32) sh.z[i] = csub(sh.z[i], sh.w[i]);
+      for (int i = lane; i < n; i += 32) {
+        sh.z[i] = csub(sh.z[i], sh.w[i]);
+        sh.w[i] = make_double2(0.0, 0.0);
+      }
       __syncwarp();
       if (__all_sync(0xffffffffu, small)) {
         st = 0;
