@@ -6,10 +6,12 @@
 // z^{M-1} D(z) is a polynomial of degree 2M-2 whose roots pair up as z, 1/conj(z); the d roots with
 // |z| <= 1 closest to the unit circle give the estimates theta = asin(arg(z) / pi).
 //
-// Roots by the Aberth-Ehrlich iteration in FP64 (simultaneous Newton corrections with the
-// repulsion sum over the other roots), all corrections computed from the previous iterate, started
-// on the unit circle at angles 2 pi i / n + 0.4; a root counts as converged when its correction is
-// below 1e-14 max(1, |z|) or when |p(z)| is within the rounding bound of its Horner evaluation,
+// Roots by the Aberth-Ehrlich iteration (simultaneous Newton corrections with the repulsion sum
+// over the other roots), all corrections computed from the previous iterate, started on the unit
+// circle at angles 2 pi i / n + 0.4: first in FP32 on the rounded coefficients (to corrections of
+// 1e-6 |z| or the FP32 rounding bound), then in FP64 from there; in FP64 a root counts as converged
+// when its correction is below 1e-14 max(1, |z|) or when |p(z)| is within the rounding bound of its
+// Horner evaluation,
 // 8 n eps sum_t |a_t| |z|^t (clustered roots -- the pairs z, 1/conj(z) near the circle -- cannot be
 // resolved further). A converged root keeps its value and takes no further correction; the
 // iteration ends when all have converged, 400 iterations at most (else DOA_ENOCONV). One warp per
@@ -26,6 +28,10 @@ constexpr int kMaxDeg = 2 * kMaxM - 2;
 constexpr int kRootMaxIter = 400;
 
 struct RootShared {
+  float2 af[kMaxDeg + 1];   // the coefficients rounded to FP32 (first phase)
+  float amf[kMaxDeg + 1];
+  float2 zf[kMaxDeg];
+  float2 wf[kMaxDeg];
   double2 a[kMaxDeg + 1];   // polynomial coefficients, a[t] multiplies z^t
   double am[kMaxDeg + 1];   // |a_t| (for the rounding bound of the Horner evaluation)
   double2 z[kMaxDeg];       // current roots
@@ -34,6 +40,15 @@ struct RootShared {
 };
 
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 fcmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 fcadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 fcsub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 fcdiv(float2 a, float2 b) {
+  const float inv = __frcp_rn(fmaf(b.x, b.x, b.y * b.y));
+  return make_float2(fmaf(a.x, b.x, a.y * b.y) * inv, fmaf(a.y, b.x, -a.x * b.y) * inv);
+}
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
   const double inv = __drcp_rn(b.x * b.x + b.y * b.y);
@@ -83,18 +98,74 @@ __device__ int root_music_warp(const RootJob &j, RootShared &sh, double *out) {
     }
     sh.a[t] = make_double2(cr, ci);
     sh.am[t] = sqrt(cr * cr + ci * ci);
+    sh.af[t] = make_float2((float)cr, (float)ci);
+    sh.amf[t] = (float)sh.am[t];
   }
   for (int i = lane; i < n; i += 32) {
-    double s, c;
-    sincos(2.0 * CUDART_PI * (double)i / (double)n + 0.4, &s, &c);
-    sh.z[i] = make_double2(c, s);
-    sh.w[i] = make_double2(0.0, 0.0);
+    float s, c;
+    sincosf(6.283185307179586f * (float)i / (float)n + 0.4f, &s, &c);
+    sh.zf[i] = make_float2(c, s);
+    sh.wf[i] = make_float2(0.f, 0.f);
     sh.conv[i] = 0;
   }
   __syncwarp();
   int st = DOA_ENOCONV;
   const double2 lead = sh.a[n];
-  if (lead.x * lead.x + lead.y * lead.y > 0.0) {
+  const bool usable = lead.x * lead.x + lead.y * lead.y > 0.0;
+  // first phase, FP32 (the FP64 rate is 1/73 of FP32 here): corrections down to 1e-6 |z| or the
+  // FP32 rounding bound of p(z); the FP64 phase then polishes the same roots
+  if (usable) {
+    for (int it = 0; it < kRootMaxIter; ++it) {
+      bool small = true;
+      for (int i = lane; i < n; i += 32) {
+        if (sh.conv[i]) continue;
+        const float2 zi = sh.zf[i];
+        const float zm = sqrtf(fmaf(zi.x, zi.x, zi.y * zi.y));
+        float2 p = sh.af[n], dp = make_float2(0.f, 0.f);
+        float pe = sh.amf[n];
+        for (int t = n - 1; t >= 0; --t) {
+          dp = fcadd(fcmul(dp, zi), p);
+          p = fcadd(fcmul(p, zi), sh.af[t]);
+          pe = fmaf(pe, zm, sh.amf[t]);
+        }
+        float2 rep = make_float2(0.f, 0.f);
+        for (int k = 0; k < n; ++k) {
+          if (k == i) continue;
+          rep = fcadd(rep, fcdiv(make_float2(1.f, 0.f), fcsub(zi, sh.zf[k])));
+        }
+        const float2 ratio = fcdiv(p, dp);
+        const float2 wi = fcdiv(ratio, fcsub(make_float2(1.f, 0.f), fcmul(ratio, rep)));
+        sh.wf[i] = wi;
+        const float mag = sqrtf(fmaf(wi.x, wi.x, wi.y * wi.y)), res = sqrtf(fmaf(p.x, p.x, p.y * p.y));
+        const bool ok = isfinite(mag) && (mag <= 1e-6f * fmaxf(1.f, zm) || res <= 8.f * n * 5.9604645e-08f * pe);
+        small = small && ok;
+        if (ok) sh.conv[i] = 1;
+      }
+      __syncwarp();
+      for (int i = lane; i < n; i += 32) {
+        sh.zf[i] = fcsub(sh.zf[i], sh.wf[i]);
+        sh.wf[i] = make_float2(0.f, 0.f);
+      }
+      __syncwarp();
+      if (__all_sync(0xffffffffu, small)) break;
+    }
+  }
+  bool finite_start = true;
+  for (int i = lane; i < n; i += 32) finite_start = finite_start && isfinite(sh.zf[i].x) && isfinite(sh.zf[i].y);
+  finite_start = __all_sync(0xffffffffu, finite_start);
+  for (int i = lane; i < n; i += 32) {
+    if (finite_start) {
+      sh.z[i] = make_double2((double)sh.zf[i].x, (double)sh.zf[i].y);
+    } else {
+      double s, c;
+      sincos(2.0 * CUDART_PI * (double)i / (double)n + 0.4, &s, &c);
+      sh.z[i] = make_double2(c, s);
+    }
+    sh.w[i] = make_double2(0.0, 0.0);
+    sh.conv[i] = 0;
+  }
+  __syncwarp();
+  if (usable) {
     for (int it = 0; it < kRootMaxIter; ++it) {
       bool small = true;
       for (int i = lane; i < n; i += 32) {
