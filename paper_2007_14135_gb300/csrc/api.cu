@@ -526,6 +526,11 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     h.scan_jobs[b] = sz.scan[b];
     h.scan_tiles[b] = tiles[b];
   }
+  h.next_val_off = -1;
+  if (h.npolish > 0) {   // the polish reads, per job, the best peak value below the selection
+    h.next_val_off = ws;
+    ws = round_up(ws + 4 * (int64_t)sz.njobs, 256);
+  }
   h.ws_bytes = ws;
   *ws_bytes = (size_t)ws;
   return DOA_OK;
@@ -551,10 +556,10 @@ doa_status doa_solve_batch(const void *plan_host, const void *plan_dev, void *ws
   if (!mark(3) || launch_scan_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
   if (h.tc_jobs > 0 && launch_scan_tc_batch(pd, h, w, status, s) != cudaSuccess) return DOA_ECUDA;
   if (launch_scan_geometry_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
-  if (!mark(4) || launch_peaks_batch(pd, h, true, true, s) != cudaSuccess) return DOA_ECUDA;
+  if (!mark(4) || launch_peaks_batch(pd, h, w, true, true, s) != cudaSuccess) return DOA_ECUDA;
   // peak polish applies to ULA problems only (geometry problems reject the flag)
   if (h.npolish > 0 &&
-      (launch_polish_batch(pd, h, w, s) != cudaSuccess || launch_peaks_batch(pd, h, true, false, s) != cudaSuccess))
+      (launch_polish_batch(pd, h, w, s) != cudaSuccess || launch_peaks_batch(pd, h, w, true, false, s) != cudaSuccess))
     return DOA_ECUDA;
   if (launch_refine_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
   if (launch_roots_batch(pd, h, w, status, s) != cudaSuccess) return DOA_ECUDA;

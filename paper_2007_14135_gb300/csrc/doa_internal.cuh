@@ -239,6 +239,8 @@ struct PlanHeader {
   int64_t off_geo_grid;
   int32_t nrefine;                       // problems with a peak_angle output (sub-grid refinement)
   int32_t nroots;                        // problems with a root_angle output (root form of the scan)
+  int64_t next_val_off;                  // workspace byte offset of one float per job: the value of
+                                         // the best peak below the d selected (peak polish), or -1
 };
 
 // The Python binding reads these header fields by position (int32 index 22 = scan_pt, 58 = eig_mats,
@@ -327,7 +329,8 @@ cudaError_t launch_peaks_single(const float *P, int L, int d, int *idx, float *v
 cudaError_t launch_peaks2d_single(const float *P, int La, int Le, int wrap_az, int d, int *idx, float *val,
                                   int *count, cudaStream_t s);
 // ula / geo: launch the 1-D and / or the 2-D peak kernel (each only when the plan has such jobs).
-cudaError_t launch_peaks_batch(const uint8_t *plan_dev, const PlanHeader &h, bool ula, bool geo, cudaStream_t s);
+cudaError_t launch_peaks_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, bool ula, bool geo,
+                               cudaStream_t s);
 cudaError_t launch_polish_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
 cudaError_t launch_roots_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, int *status, cudaStream_t s);
 cudaError_t launch_roots_single(const double2 *B, int M, int K, int d, double *theta, int *info, cudaStream_t s);

@@ -39,9 +39,16 @@ __device__ void write_sel(Cand *sel, int nsel, int *idx, float *val, int *count)
   }
 }
 
-__device__ void peaks_block(const float *__restrict__ P, int L, int d, int *idx, float *val, int *count) {
-  __shared__ Cand sel[kMaxM];
-  const int nsel = select_top(P, L, d, sel);
+// next (nullable): receives the value of the (d+1)-th best peak (-inf if there is none).
+__device__ void peaks_block(const float *__restrict__ P, int L, int d, int *idx, float *val, int *count,
+                            float *next = nullptr) {
+  __shared__ Cand sel[kMaxM + 1];
+  const int want = next ? d + 1 : d;
+  int nsel = select_top(P, L, want, sel);
+  if (next) {
+    if (threadIdx.x == 0) *next = nsel > d ? sel[d].v : -INFINITY;
+    nsel = min(nsel, d);
+  }
   write_sel(sel, nsel, idx, val, count);
 }
 
@@ -64,14 +71,17 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_single_kernel(const float 
 
 // One CTA per (problem, algorithm) job; the 1-D and 2-D rules run as separate kernels (each skips
 // the other kind's jobs) so that each keeps its own register budget.
-__global__ void __launch_bounds__(kPeakThreads) peaks_batch_kernel(const uint8_t *plan) {
+__global__ void __launch_bounds__(kPeakThreads) peaks_batch_kernel(const uint8_t *plan, uint8_t *ws) {
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
   const PlanJob &jb = reinterpret_cast<const PlanJob *>(plan + h->off_job)[blockIdx.x];
   const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[jb.prob];
   if (pp.p.geom.pos) return;
   const int L = pp.npts, d = pp.p.d;
+  float *next = (pp.p.flags & DOA_FLAG_POLISH_PEAKS) && h->next_val_off >= 0
+                    ? reinterpret_cast<float *>(ws + h->next_val_off) + blockIdx.x
+                    : nullptr;
   peaks_block(pp.p.P + (size_t)jb.slot * L, L, d, pp.p.peak_idx + (size_t)jb.slot * d,
-              pp.p.peak_val + (size_t)jb.slot * d, pp.p.peak_count + jb.slot);
+              pp.p.peak_val + (size_t)jb.slot * d, pp.p.peak_count + jb.slot, next);
 }
 
 __global__ void __launch_bounds__(kPeakThreads) peaks2d_batch_kernel(const uint8_t *plan) {
@@ -211,10 +221,11 @@ cudaError_t launch_peaks2d_single(const float *P, int La, int Le, int wrap_az, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_peaks_batch(const uint8_t *plan_dev, const PlanHeader &h, bool ula, bool geo, cudaStream_t s) {
+cudaError_t launch_peaks_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, bool ula, bool geo,
+                               cudaStream_t s) {
   int ngeo = 0;
   for (int b = 0; b < kNumBuckets; ++b) ngeo += h.geo_jobs[b];
-  if (h.njobs > 0 && ula && ngeo < h.nprob) peaks_batch_kernel<<<h.njobs, kPeakThreads, 0, s>>>(plan_dev);
+  if (h.njobs > 0 && ula && ngeo < h.nprob) peaks_batch_kernel<<<h.njobs, kPeakThreads, 0, s>>>(plan_dev, ws);
   if (h.njobs > 0 && geo && ngeo > 0) peaks2d_batch_kernel<<<h.njobs, kPeakThreads, 0, s>>>(plan_dev);
   return cudaGetLastError();
 }

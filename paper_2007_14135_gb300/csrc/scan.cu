@@ -140,9 +140,18 @@ __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t 
 // Peak polish (DOA_FLAG_POLISH_PEAKS): one warp per problem re-evaluates, with the FP64
 // steering and contraction of refine_point_warp, every readout of the problem at the union of
 // its algorithms' picked peaks and their two neighbours on each side (each point once); the
-// peaks are then picked again.
+// peaks are then picked again. A peak whose outcome the FP32 values already decide is skipped:
+// the FP32 spectrum is within kPolishCertain / 2 (relative) of the FP64 one, so when every pair of
+// consecutive points from k-3 to k+3 differs by more than kPolishCertain, and the algorithm's
+// weakest selected peak exceeds its best unselected one by more than that, re-evaluating in FP64
+// cannot change which points are peaks or which are selected.
 constexpr int kPolishWarps = 4;
 constexpr int kPolishMax = 4 * kMaxM;
+constexpr float kPolishCertain = 2e-3f;   // twice the FP32 path's relative error bound (5e-4), doubled
+
+__device__ __forceinline__ bool order_certain(float a, float b) {
+  return fabsf(a - b) > kPolishCertain * fmaxf(a, b);
+}
 
 __global__ void __launch_bounds__(32 * kPolishWarps) polish_batch_kernel(const uint8_t *plan, uint8_t *ws) {
   __shared__ double2 ph[kPolishWarps][kMaxM];
@@ -173,12 +182,24 @@ __global__ void __launch_bounds__(32 * kPolishWarps) polish_batch_kernel(const u
   j.kofs = 0;
   for (int c = lane; c < j.Kn; c += 32) w32[warp][c] = j.w ? (float)j.w[c] : 1.f;
   const int d = pp.p.d, L = g.L;
+  const float *next = h->next_val_off >= 0 ? reinterpret_cast<const float *>(ws + h->next_val_off) : nullptr;
   int n = 0;
-  if (lane == 0) {   // the algorithms' peaks, sorted, each once
+  if (lane == 0) {   // the algorithms' undecided peaks, sorted, each once
     for (int s = 0; s < pp.njobs; ++s) {
       const int cnt = min(pp.p.peak_count[s], d);
+      const float *Ps = pp.p.P + (size_t)s * L;
+      bool boundary = true;             // the selection is decided by the FP32 values
+      if (cnt == d && next) {
+        float vmin = INFINITY;
+        for (int q = 0; q < cnt; ++q) vmin = fminf(vmin, pp.p.peak_val[(size_t)s * d + q]);
+        const float nv = next[pp.first_job + s];
+        boundary = !(nv > -INFINITY) || (vmin > nv && order_certain(vmin, nv));
+      }
       for (int q = 0; q < cnt; ++q) {
         const int k = pp.p.peak_idx[(size_t)s * d + q];
+        bool decided = boundary && next;
+        for (int i = max(k - 3, 0); decided && i < min(k + 3, L - 1); ++i) decided = order_certain(Ps[i], Ps[i + 1]);
+        if (decided) continue;
         int a = n;
         while (a > 0 && pk[warp][a - 1] > k) --a;
         if (a > 0 && pk[warp][a - 1] == k) continue;
