@@ -359,7 +359,10 @@ typedef struct {
 
 /* Peak polish: after Step-6 the spectrum is re-evaluated in FP64 (steering and contraction) at
  * the picked peaks and their two neighbours on each side, and the peaks are picked again, so a
- * near tie between neighbouring grid points is decided as the FP64 spectrum decides it. */
+ * near tie between neighbouring grid points is decided as the FP64 spectrum decides it. A peak
+ * whose outcome the FP32 values already decide (every consecutive pair from k-3 to k+3 differs by
+ * more than 2e-3 relative, four times the FP32 path's error bound, and so does the algorithm's
+ * weakest selected peak from its best unselected one) is left as computed. */
 #define DOA_FLAG_POLISH_PEAKS 1
 
 /* Launch-shape knobs of a plan, per M bucket (M <= 8, <= 16, <= 32, <= 64); 0 = default. */

@@ -354,8 +354,9 @@ def test_batch_fp64_jacobi(env):
 
 
 def test_batch_peak_polish(env):
-    """With DOA_FLAG_POLISH_PEAKS the points around every picked peak carry FP64-accurate values,
-    so the peak indices equal the oracle's up to ties below float resolution (1e-6 relative)."""
+    """With DOA_FLAG_POLISH_PEAKS every peak whose neighbourhood the FP32 values do not decide is
+    re-evaluated in FP64, so the peak indices equal the oracle's up to ties below float resolution
+    (1e-6 relative); points left as computed are within the FP32 path's bound."""
     torch, doa = env
     insts = [synth.paper_density(i) for i in range(12)]
     masks = [0xF] * len(insts)
@@ -370,9 +371,9 @@ def test_batch_peak_polish(env):
             assert db_error(P[alg], ref["P"]) < DB_TOL
             ok, ties = compare_peaks(idx[alg][:cnt[alg]], ref["idx"], ref["P"], 1e-6)
             assert ok, (inst.seed, alg, ties)
-            for k in idx[alg][:cnt[alg]]:   # polished points: FP64 values rounded once to float
+            for k in idx[alg][:cnt[alg]]:   # FP64 values rounded once, or FP32 values within the bound
                 for q in range(max(k - 2, 0), min(k + 3, inst.L)):
-                    assert abs(P[alg][q] / ref["P"][q] - 1.0) < 2e-7
+                    assert abs(P[alg][q] / ref["P"][q] - 1.0) < 5e-4
 
 
 def test_batch_edge_shapes(env):
