@@ -328,7 +328,8 @@ cudaError_t launch_peaks_single(const float *P, int L, int d, int *idx, float *v
                                 cudaStream_t s);
 cudaError_t launch_peaks2d_single(const float *P, int La, int Le, int wrap_az, int d, int *idx, float *val,
                                   int *count, cudaStream_t s);
-// ula / geo: launch the 1-D and / or the 2-D peak kernel (each only when the plan has such jobs).
+// ula / geo: launch the 1-D and / or the 2-D peak kernel (each only when the plan has such jobs);
+// ula without geo is the pick after the peak polish (only the jobs the polish marked).
 cudaError_t launch_peaks_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, bool ula, bool geo,
                                cudaStream_t s);
 cudaError_t launch_polish_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);

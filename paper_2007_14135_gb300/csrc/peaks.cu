@@ -71,15 +71,19 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_single_kernel(const float 
 
 // One CTA per (problem, algorithm) job; the 1-D and 2-D rules run as separate kernels (each skips
 // the other kind's jobs) so that each keeps its own register budget.
-__global__ void __launch_bounds__(kPeakThreads) peaks_batch_kernel(const uint8_t *plan, uint8_t *ws) {
+// repick: the pick after the peak polish, only for the jobs the polish marked (NaN next value).
+__global__ void __launch_bounds__(kPeakThreads) peaks_batch_kernel(const uint8_t *plan, uint8_t *ws, int repick) {
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
   const PlanJob &jb = reinterpret_cast<const PlanJob *>(plan + h->off_job)[blockIdx.x];
   const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[jb.prob];
   if (pp.p.geom.pos) return;
   const int L = pp.npts, d = pp.p.d;
-  float *next = (pp.p.flags & DOA_FLAG_POLISH_PEAKS) && h->next_val_off >= 0
-                    ? reinterpret_cast<float *>(ws + h->next_val_off) + blockIdx.x
-                    : nullptr;
+  const bool polish = (pp.p.flags & DOA_FLAG_POLISH_PEAKS) && h->next_val_off >= 0;
+  float *next = polish ? reinterpret_cast<float *>(ws + h->next_val_off) + blockIdx.x : nullptr;
+  if (repick) {
+    if (!polish || !isnan(*next)) return;
+    next = nullptr;
+  }
   peaks_block(pp.p.P + (size_t)jb.slot * L, L, d, pp.p.peak_idx + (size_t)jb.slot * d,
               pp.p.peak_val + (size_t)jb.slot * d, pp.p.peak_count + jb.slot, next);
 }
@@ -225,7 +229,8 @@ cudaError_t launch_peaks_batch(const uint8_t *plan_dev, const PlanHeader &h, uin
                                cudaStream_t s) {
   int ngeo = 0;
   for (int b = 0; b < kNumBuckets; ++b) ngeo += h.geo_jobs[b];
-  if (h.njobs > 0 && ula && ngeo < h.nprob) peaks_batch_kernel<<<h.njobs, kPeakThreads, 0, s>>>(plan_dev, ws);
+  const int repick = ula && !geo;   // the call after the polish
+  if (h.njobs > 0 && ula && ngeo < h.nprob) peaks_batch_kernel<<<h.njobs, kPeakThreads, 0, s>>>(plan_dev, ws, repick);
   if (h.njobs > 0 && geo && ngeo > 0) peaks2d_batch_kernel<<<h.njobs, kPeakThreads, 0, s>>>(plan_dev);
   return cudaGetLastError();
 }

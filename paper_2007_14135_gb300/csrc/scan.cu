@@ -22,6 +22,7 @@
 // then elements of columns), so the FP64 work runs without divergence. With per-term FP32
 // errors below ~4 eps the FP32 result elsewhere stays within ~5e-4 relative.
 #include <float.h>
+#include <math_constants.h>
 
 #include "doa_internal.cuh"
 #include "scan_common.cuh"
@@ -211,6 +212,9 @@ __global__ void __launch_bounds__(32 * kPolishWarps) polish_batch_kernel(const u
   }
   n = __shfl_sync(0xffffffffu, n, 0);
   __syncwarp();
+  // mark the problem's jobs for the second pick (a NaN in their next-value slots); the jobs of a
+  // problem with nothing to polish keep their first pick
+  if (n > 0 && next && lane < pp.njobs) const_cast<float *>(next)[pp.first_job + lane] = CUDART_NAN_F;
   int last = -1;
   for (int i = 0; i < n; ++i) {
     const int k0 = pk[warp][i];
