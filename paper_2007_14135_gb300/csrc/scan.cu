@@ -22,6 +22,8 @@
 // then elements of columns), so the FP64 work runs without divergence. With per-term FP32
 // errors below ~4 eps the FP32 result elsewhere stays within ~5e-4 relative.
 #include <float.h>
+
+#include <algorithm>
 #include <math_constants.h>
 
 #include "doa_internal.cuh"
@@ -80,10 +82,11 @@ __global__ void __launch_bounds__(kScanThreads) scan_single_kernel(const double2
 // mostly share a problem (its factor stays in shared memory), while the runs of problems of
 // different cost (columns, M) spread evenly over the CTAs. The problem of a run's first tile
 // comes from a binary search on the problems' first tiles, the following ones by stepping.
-constexpr int kRun = 16;
+constexpr int kRun = 16;   // longest run (large batches); small ones use shorter runs so every SM gets one
 
 template <int MP, int PT>
-__global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t *plan, uint8_t *ws, int bucket) {
+__global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t *plan, uint8_t *ws, int bucket,
+                                                                  int run_len) {
   __shared__ __align__(16) float2 Bs[(MP + 1) * MP];
   __shared__ ScanShared sh;
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
@@ -97,8 +100,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t 
   ScanJob j{};
   const PlanProblem *pp = nullptr;
   const PlanGrid *g = nullptr;
-  for (int64_t run = blockIdx.x; run * kRun < ntiles; run += gridDim.x) {
-    const int64_t t_begin = run * kRun, t_end = min(ntiles, t_begin + kRun);
+  for (int64_t run = blockIdx.x; run * run_len < ntiles; run += gridDim.x) {
+    const int64_t t_begin = run * run_len, t_end = min(ntiles, t_begin + run_len);
     int u = 0, hi = nunits - 1;
     while (u < hi) {  // last problem with tile_start <= t_begin
       int mid = (u + hi + 1) >> 1;
@@ -244,9 +247,10 @@ cudaError_t run_batch(const uint8_t *plan, const PlanHeader &h, uint8_t *ws, int
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_batch_kernel<MP, PT>, kScanThreads, 0);
   if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)num_sms() * per_sm;
-  if (grid > tiles) grid = tiles;
-  scan_batch_kernel<MP, PT><<<(unsigned)grid, kScanThreads, 0, s>>>(plan, ws, bucket);
+  const int64_t cap = (int64_t)num_sms() * per_sm;
+  const int run_len = (int)std::min<int64_t>(kRun, std::max<int64_t>(1, (tiles + cap - 1) / cap));
+  const int64_t grid = std::min<int64_t>(cap, (tiles + run_len - 1) / run_len);
+  scan_batch_kernel<MP, PT><<<(unsigned)grid, kScanThreads, 0, s>>>(plan, ws, bucket, run_len);
   return cudaGetLastError();
 }
 

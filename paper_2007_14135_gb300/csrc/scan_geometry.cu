@@ -29,6 +29,8 @@
 // tables, FP64 phases and the FP64 factor (warp per point).
 #include <float.h>
 
+#include <algorithm>
+
 #include "doa_internal.cuh"
 #include "scan_common.cuh"
 
@@ -203,11 +205,11 @@ __global__ void __launch_bounds__(kScanThreads) scan_geometry_single_kernel(cons
 // ULA batch scan (run r to CTA r mod gridDim). Flagged points accumulate over a run and are
 // re-evaluated when the run ends or its problem changes, so the warps share the FP64 work of
 // many tiles and meet at a barrier once per run rather than once per tile.
-constexpr int kRun = 16;
+constexpr int kRun = 16;   // longest run (large batches); small ones use shorter runs so every SM gets one
 
 template <int MP, int PT>
 __global__ void __launch_bounds__(kScanThreads) scan_geometry_batch_kernel(const uint8_t *plan, uint8_t *ws,
-                                                                           int bucket) {
+                                                                           int bucket, int run_len) {
   __shared__ __align__(16) float2 Bs[(MP + 1) * MP];
   __shared__ ScanShared sh;
   __shared__ GeoShared gs;
@@ -223,8 +225,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_geometry_batch_kernel(const
   GeoParams g{};
   GeoSource src{};
   const PlanProblem *pp = nullptr;
-  for (int64_t run = blockIdx.x; run * kRun < ntiles; run += gridDim.x) {
-    const int64_t t_begin = run * kRun, t_end = min(ntiles, t_begin + kRun);
+  for (int64_t run = blockIdx.x; run * run_len < ntiles; run += gridDim.x) {
+    const int64_t t_begin = run * run_len, t_end = min(ntiles, t_begin + run_len);
     int u = 0, hi = nunits - 1;
     while (u < hi) {  // last problem with tile_start <= t_begin
       int mid = (u + hi + 1) >> 1;
@@ -287,10 +289,10 @@ cudaError_t run_geo_batch(const uint8_t *plan, const PlanHeader &h, uint8_t *ws,
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_geometry_batch_kernel<MP, PT>, kScanThreads, 0);
   if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)num_sms() * per_sm;
-  const int64_t runs = (tiles + kRun - 1) / kRun;
-  if (grid > runs) grid = runs;
-  scan_geometry_batch_kernel<MP, PT><<<(unsigned)grid, kScanThreads, 0, s>>>(plan, ws, bucket);
+  const int64_t cap = (int64_t)num_sms() * per_sm;
+  const int run_len = (int)std::min<int64_t>(kRun, std::max<int64_t>(1, (tiles + cap - 1) / cap));
+  const int64_t grid = std::min<int64_t>(cap, (tiles + run_len - 1) / run_len);
+  scan_geometry_batch_kernel<MP, PT><<<(unsigned)grid, kScanThreads, 0, s>>>(plan, ws, bucket, run_len);
   return cudaGetLastError();
 }
 
