@@ -207,14 +207,70 @@ inline __device__ void refine_point_thread_src(const ScanJob &j, int k, const Sr
   if (j.P[kRoMn]) j.P[kRoMn][k] = recip_out(dn);
 }
 
-// Drains the tile's refinement queue (all threads of the CTA call this).
+// Re-evaluation of several points per warp for small factors: a sub-warp of W lanes per point
+// (W = 8 or 16, 32 / W points at once; needs M <= W and Kf <= W). Lanes own the phasors a_m
+// (m = lane in the sub-warp), then one factor column each (y_c = f_c^H a over all M elements in
+// FP64), and the readouts are sums over the sub-warp of |y_c|^2 from y_c rounded once to FP32,
+// as in refine_point_warp_src. Every lane of the warp runs the same number of steps (a sub-warp
+// without a point works on a copy of the first and does not store).
+template <int W, class Src>
+inline __device__ void refine_points_subwarp(const ScanJob &j, const int *ks, int cnt, const Src &src,
+                                             const float *w32, double2 *ph) {
+  const int lane = threadIdx.x & 31, sub = lane % W, grp = lane / W;
+  const bool live = grp < cnt;
+  const int k = ks[live ? grp : 0];
+  const auto st = src.prep(k);
+  double2 *mine = ph + grp * W;
+  if (sub < j.M) mine[sub] = src.phasor(st, sub);
+  __syncwarp();
+  float n = 0.f;
+  if (sub < j.Kf) {
+    const double2 *f = j.F + (size_t)sub * j.M;
+    double yr = 0.0, yi = 0.0;
+    for (int m = 0; m < j.M; ++m) {
+      const double2 b = f[m], a = mine[m];     // conj(b) * a
+      yr = fma(b.x, a.x, fma(b.y, a.y, yr));
+      yi = fma(b.x, a.y, fma(-b.y, a.x, yi));
+    }
+    const float fr = (float)yr, fi = (float)yi;
+    n = fmaf(fr, fr, fi * fi);
+  }
+  float dm = sub < j.Kn ? n : 0.f;
+  float de = sub < j.Kn ? w32[sub] * n : 0.f;
+#pragma unroll
+  for (int off = W / 2; off > 0; off >>= 1) {
+    dm += __shfl_xor_sync(0xffffffffu, dm, off);
+    de += __shfl_xor_sync(0xffffffffu, de, off);
+  }
+  const int base = grp * W;
+  const float dp = __shfl_sync(0xffffffffu, n, base + (j.kphd >= 0 ? j.kphd : 0));
+  const float dn = __shfl_sync(0xffffffffu, n, base + (j.kmn >= 0 ? j.kmn : 0));
+  if (live && sub == 0) {
+    if (j.P[kRoMusic]) j.P[kRoMusic][k] = recip_out(dm);
+    if (j.P[kRoEv]) j.P[kRoEv][k] = recip_out(de);
+    if (j.P[kRoPhd]) j.P[kRoPhd][k] = recip_out(dp);
+    if (j.P[kRoMn]) j.P[kRoMn][k] = recip_out(dn);
+  }
+  __syncwarp();
+}
+
+// Drains the tile's refinement queue (all threads of the CTA call this): several points per warp
+// when the factor is small enough, else one point per warp.
 template <class Src>
 __device__ __forceinline__ void drain_refinements_src(const ScanJob &j, const Src &src, ScanShared &sh) {
   __syncthreads();
   const int n = min(sh.nflag, kFlagCap);
   const int warp = threadIdx.x >> 5;
-  for (int i = warp; i < n; i += kScanWarps)
-    refine_point_warp_src(j, sh.flags[i], src, sh.w32, sh.ph[warp], sh.yb[warp]);
+  if (j.M <= 8 && j.Kf <= 8) {
+    for (int i = warp * 4; i < n; i += kScanWarps * 4)
+      refine_points_subwarp<8>(j, sh.flags + i, min(4, n - i), src, sh.w32, sh.ph[warp]);
+  } else if (j.M <= 16 && j.Kf <= 16) {
+    for (int i = warp * 2; i < n; i += kScanWarps * 2)
+      refine_points_subwarp<16>(j, sh.flags + i, min(2, n - i), src, sh.w32, sh.ph[warp]);
+  } else {
+    for (int i = warp; i < n; i += kScanWarps)
+      refine_point_warp_src(j, sh.flags[i], src, sh.w32, sh.ph[warp], sh.yb[warp]);
+  }
   __syncthreads();
   if (threadIdx.x == 0) sh.nflag = 0;
   __syncthreads();
