@@ -1154,7 +1154,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--batch", type=int, default=4096, help="problems per GPU per step")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="problems per GPU per step (default: 4096; large-array 32 replicas; learned 65536 instances)")
     ap.add_argument("--cpu-sample", type=int, default=3072,
                     help="problems timed on the oracle for cpu_baseline (peak indices compared on all)")
     ap.add_argument("--parity-full", type=int, default=48,
@@ -1176,6 +1177,8 @@ def main():
     ap.add_argument("--tc-min-m", type=int, default=0,
                     help="uneven workload: problems with M >= this (<= 32) scan on the tensor cores (FP16x3)")
     args = ap.parse_args()
+    if args.batch is None:
+        args.batch = {"large-array": 32, "learned": 65536}.get(args.workload, 4096)
     if args.warmup < 3 and args.impl == "gpu":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
