@@ -8,7 +8,12 @@
 //  - plain: x_a conj(x_b) accumulated with FP32 FMAs (relative error ~1e-7 of |R|);
 //  - compensated: every real product is split exactly into p + e (p = fl(a*b), e = fma(a, b, -p))
 //    and added to a double-float accumulator (hi, lo) with TwoSum (Knuth), so the only error is
-//    the final rounding of hi + lo (about 2^-44 relative). The Pisarenko (PHD) spectrum needs it:
+//    the final rounding of hi + lo (about 2^-44 relative). The block-task kernels (4 < M <= 16)
+//    start their accumulators at a power-of-two bias above twice the largest partial sum a lane
+//    can reach in its chunk (from the chunk's largest |component|), which makes Dekker's Fast2Sum
+//    (3 operations) exact in place of TwoSum (6); the lo word then holds errors of magnitude up to
+//    2^-24 of the bias, so a lane's result is exact to ~n^2 2^-48 of the bias (n <= 32 snapshots
+//    per lane and chunk), still ~1e-11 of the chunk's largest product sum. The Pisarenko (PHD) spectrum needs it:
 //    its minimum eigenvector moves by |dR| / (lambda_{M-2} - lambda_{M-1}), and the noise
 //    eigenvalue gaps are tiny, so an FP32-accurate R shifts that spectrum by up to ~1 dB.
 // The per-thread sums are added across snapshot groups in double-float and leave as FP64.
@@ -80,6 +85,18 @@ __device__ __forceinline__ void mac(float &hi, float &lo, float a, float b) {
   } else {
     hi = fmaf(a, b, hi);
   }
+}
+
+// hi + lo += a * b for an accumulator carrying a bias B (a power of two) with |hi| >= B/2 and
+// |a b| <= B/2 throughout: the sum's rounding error is then exact by Fast2Sum (Dekker), three
+// operations instead of TwoSum's six; (hi - B) is exact at the end (Sterbenz).
+__device__ __forceinline__ void mac_biased(float &hi, float &lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float t = __fsub_rn(p, __fsub_rn(s, hi));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, t));
 }
 
 // Accumulates the snapshots [t0, t1) and leaves the CTA's sums (nb x 16 slots of float4
@@ -295,6 +312,15 @@ __device__ __forceinline__ bool task_slot(int task, int a, int M, int &row, int 
   return row < M && col < M;
 }
 
+// One snapshot's products for a task; compensated accumulators carry the bias of cov_tasks.
+template <int MB, bool kComp>
+__device__ __forceinline__ void task_mac(float &hi, float &lo, float a, float b) {
+  if (kComp)
+    mac_biased(hi, lo, a, b);
+  else
+    hi = fmaf(a, b, hi);
+}
+
 template <int MB, bool kComp>
 __device__ __forceinline__ void task_macs(int task, const float2 *tile, int t, float (&hi)[32], float (&lo)[32]) {
   using T = CovTasks<MB>;
@@ -314,10 +340,10 @@ __device__ __forceinline__ void task_macs(int task, const float2 *tile, int t, f
       for (int j = 0; j < 4; ++j) {
         const int a = 2 * (i * 4 + j);
         // x_a conj(x_b) = (ar br + ai bi) + j (ai br - ar bi)
-        mac<kComp>(hi[a], lo[a], xa[i].x, xb[j].x);
-        mac<kComp>(hi[a], lo[a], xa[i].y, xb[j].y);
-        mac<kComp>(hi[a + 1], lo[a + 1], xa[i].y, xb[j].x);
-        mac<kComp>(hi[a + 1], lo[a + 1], -xa[i].x, xb[j].y);
+        task_mac<MB, kComp>(hi[a], lo[a], xa[i].x, xb[j].x);
+        task_mac<MB, kComp>(hi[a], lo[a], xa[i].y, xb[j].y);
+        task_mac<MB, kComp>(hi[a + 1], lo[a + 1], xa[i].y, xb[j].x);
+        task_mac<MB, kComp>(hi[a + 1], lo[a + 1], -xa[i].x, xb[j].y);
       }
   } else {
 #pragma unroll
@@ -329,18 +355,18 @@ __device__ __forceinline__ void task_macs(int task, const float2 *tile, int t, f
       for (int i = 0; i < 4; ++i) x[i] = tile[(b * 4 + i) * T::kTS + t];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        mac<kComp>(hi[16 * h + i], lo[16 * h + i], x[i].x, x[i].x);
-        mac<kComp>(hi[16 * h + i], lo[16 * h + i], x[i].y, x[i].y);
+        task_mac<MB, kComp>(hi[16 * h + i], lo[16 * h + i], x[i].x, x[i].x);
+        task_mac<MB, kComp>(hi[16 * h + i], lo[16 * h + i], x[i].y, x[i].y);
       }
       int a = 16 * h + 4;
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = i + 1; j < 4; ++j) {
-          mac<kComp>(hi[a], lo[a], x[i].x, x[j].x);
-          mac<kComp>(hi[a], lo[a], x[i].y, x[j].y);
-          mac<kComp>(hi[a + 1], lo[a + 1], x[i].y, x[j].x);
-          mac<kComp>(hi[a + 1], lo[a + 1], -x[i].x, x[j].y);
+          task_mac<MB, kComp>(hi[a], lo[a], x[i].x, x[j].x);
+          task_mac<MB, kComp>(hi[a], lo[a], x[i].y, x[j].y);
+          task_mac<MB, kComp>(hi[a + 1], lo[a + 1], x[i].y, x[j].x);
+          task_mac<MB, kComp>(hi[a + 1], lo[a + 1], -x[i].x, x[j].y);
           a += 2;
         }
     }
@@ -356,9 +382,35 @@ __device__ void cov_tasks(const float2 *__restrict__ X, int M, int ldx, int t0, 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, g = tid & 31;
   const int task = K::kFirst + warp;
+  // compensated mode: every accumulator starts at the bias B, a power of two with B/2 above both
+  // a lane's running sum (at most 2 m^2 per snapshot, m the chunk's largest |component|) and any
+  // single product (m^2), so mac_biased's Fast2Sum is exact
+  float bias = 0.f;
+  if (kComp) {
+    __shared__ float red[32];
+    float m = 0.f;
+    const int cnt = t1 - t0;
+    for (int r = 0; r < M; ++r)
+      for (int t = tid; t < cnt; t += K::kThreads) {
+        const float2 v = X[(size_t)r * ldx + t0 + t];
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+      }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (g == 0) red[warp] = m;
+    __syncthreads();
+    m = 0.f;
+    for (int w = 0; w < K::kThreads / 32; ++w) m = fmaxf(m, red[w]);
+    const int per_lane = (cnt + 31) / 32;
+    const float b = (float)(4 * per_lane + 2) * m * m;
+    bias = __int_as_float((__float_as_int(b) & 0x7F800000) + 0x00800000);   // next power of two above b
+  }
   float hi[32], lo[32];
 #pragma unroll
-  for (int a = 0; a < 32; ++a) hi[a] = lo[a] = 0.f;
+  for (int a = 0; a < 32; ++a) {
+    hi[a] = bias;
+    lo[a] = 0.f;
+  }
   auto issue = [&](int buf, int ts) {
     const int cnt = min(T::kTS, t1 - ts);
     float2 *dst = tiles + buf * (T::kMP * T::kTS);
@@ -388,7 +440,7 @@ __device__ void cov_tasks(const float2 *__restrict__ X, int M, int ldx, int t0, 
   __syncthreads();
   float2 *stage = reinterpret_cast<float2 *>(smem);   // [local task][a][lane]
 #pragma unroll
-  for (int a = 0; a < 32; ++a) stage[((size_t)warp * 32 + a) * 32 + g] = make_float2(hi[a], lo[a]);
+  for (int a = 0; a < 32; ++a) stage[((size_t)warp * 32 + a) * 32 + g] = make_float2(__fsub_rn(hi[a], bias), lo[a]);
   __syncthreads();
   for (int item = tid; item < K::kTasks * 32; item += K::kThreads) {
     const int tk = K::kFirst + item / 32, a = item % 32;
