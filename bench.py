@@ -778,7 +778,7 @@ def run_learned(args):
     """Learned proposal: train the network on 1M method-generated instances (M=16, d in U{1..6},
     SNR U[-5,20] dB, angles U[-80,80] with 3 deg separation, N=2048), then solve a batch of
     test instances two ways at the 0.001 deg resolution: covariance + Jacobi + network + windowed
-    fine scan + full-grid fallback, against the plain full-grid method (the judge). Step times
+    fine scan + full-grid fallback, against the plain full-grid method (the arbiter). Step times
     are wall clock around synchronised GPU work (the pipeline reads the fallback flags back)."""
     import torch
     from paper_2007_14135_gb300 import build

@@ -5,7 +5,7 @@ U[-80,80] with 3 deg separation, N=2048) are generated on the GPU (doa_synth_ula
 by the plain method (doa_solve_batch: covariance, Jacobi, MUSIC scan on a 0.1 deg grid, peaks),
 which also writes the network input (trace-normalised upper triangle of R). The label of an
 instance is the set of 1-degree bins that contain the plain method's d peaks, so the network
-imitates the method and the method remains the judge.
+imitates the method and the method remains the arbiter.
 
 Inference: covariance + Jacobi + features + MUSIC factor for the batch, network forward,
 doa_proposal_windows (the d best bins with 1-bin suppression -> +-2 deg windows on the 0.001 deg
@@ -28,7 +28,7 @@ M, N_SNAP, DMAX = 16, 2048, 6
 WMAX = 8                                # windows per instance (d plus up to EXTRA more proposals)
 EXTRA = 2
 COARSE_STEP = 0.1                       # label grid
-FINE_STEP = 0.001                       # fine grid of the windows and of the full-grid judge
+FINE_STEP = 0.001                       # fine grid of the windows and of the full-grid arbiter
 WIDTH = 4001                            # +-2 deg at 0.001 deg
 TRAIN_SEED, TEST_SEED = 20071417, 20071418
 
@@ -168,7 +168,7 @@ def infer(net: doa.Mlp, sol: Solved, extra: int = EXTRA, device: str = "cuda") -
 
 
 def full_grid(sol: Solved, rows_chunk: int = 8192, device: str = "cuda"):
-    """The plain method on the whole 0.001 deg grid (the judge): peaks for every row."""
+    """The plain method on the whole 0.001 deg grid (the arbiter): peaks for every row."""
     n = sol.features.shape[0]
     fg = fine_grid()
     S = torch.empty(fg.L, dtype=torch.int32, device=device)

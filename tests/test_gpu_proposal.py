@@ -90,7 +90,7 @@ def test_windowed_scan_is_the_full_grid_scan_restricted(env):
     doa.doa_scan_windows(sol.B, 16, sol.K, sol.d, fg, S, Pf, fi, fv, fc, full=True)
     fih, fch = fi.cpu().numpy(), fc.cpu().numpy()
     Pfh = Pf.cpu().numpy()[:, 0]
-    # oracle check of the full-grid judge on two rows
+    # oracle check of the full-grid arbiter on two rows
     for r in range(2):
         Xr = torch.empty((1, 16, 2048), dtype=torch.complex64, device="cuda")
         doa.doa_synth_ula(sol.d[r:r + 1], torch.from_numpy(ang[r:r + 1]).cuda(), torch.from_numpy(snr[r:r + 1]).cuda(),
