@@ -384,10 +384,34 @@ __device__ void cov_tasks(const float2 *__restrict__ X, int M, int ldx, int t0, 
   const int task = K::kFirst + warp;
   // compensated mode: every accumulator starts at the bias B, a power of two with B/2 above both
   // a lane's running sum (at most 2 m^2 per snapshot, m the chunk's largest |component|) and any
-  // single product (m^2), so mac_biased's Fast2Sum is exact. m comes from a first pass over the
-  // chunk through the same double-buffered cp.async tiles (latency hidden; the second pass then
-  // finds the chunk in L2).
-  auto issue_tile = [&](int buf, int ts) {
+  // single product (m^2), so mac_biased's Fast2Sum is exact
+  float bias = 0.f;
+  if (kComp) {
+    __shared__ float red[32];
+    float m = 0.f;
+    const int cnt = t1 - t0;
+    for (int r = 0; r < M; ++r)
+      for (int t = tid; t < cnt; t += K::kThreads) {
+        const float2 v = X[(size_t)r * ldx + t0 + t];
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+      }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (g == 0) red[warp] = m;
+    __syncthreads();
+    m = 0.f;
+    for (int w = 0; w < K::kThreads / 32; ++w) m = fmaxf(m, red[w]);
+    const int per_lane = (cnt + 31) / 32;
+    const float b = (float)(4 * per_lane + 2) * m * m;
+    bias = __int_as_float((__float_as_int(b) & 0x7F800000) + 0x00800000);   // next power of two above b
+  }
+  float hi[32], lo[32];
+#pragma unroll
+  for (int a = 0; a < 32; ++a) {
+    hi[a] = bias;
+    lo[a] = 0.f;
+  }
+  auto issue = [&](int buf, int ts) {
     const int cnt = min(T::kTS, t1 - ts);
     float2 *dst = tiles + buf * (T::kMP * T::kTS);
     for (int e = tid; e < T::kMP * T::kTS; e += K::kThreads) {
@@ -397,50 +421,12 @@ __device__ void cov_tasks(const float2 *__restrict__ X, int M, int ldx, int t0, 
     }
     cp_async_commit();
   };
-  float bias = 0.f;
-  if (kComp) {
-    __shared__ float red[32];
-    float m = 0.f;
-    if (t0 < t1) issue_tile(0, t0);
-    int pbuf = 0;
-    for (int ts = t0; ts < t1; ts += T::kTS, pbuf ^= 1) {
-      if (ts + T::kTS < t1) {
-        issue_tile(pbuf ^ 1, ts + T::kTS);
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
-      __syncthreads();
-      const float2 *tile = tiles + pbuf * (T::kMP * T::kTS);
-      for (int e = tid; e < T::kMP * T::kTS; e += K::kThreads) {   // padding entries are zero
-        const float2 v = tile[e];
-        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
-      }
-      __syncthreads();
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-    if (g == 0) red[warp] = m;
-    __syncthreads();
-    m = 0.f;
-    for (int w = 0; w < K::kThreads / 32; ++w) m = fmaxf(m, red[w]);
-    const int per_lane = (t1 - t0 + 31) / 32;
-    const float b = (float)(4 * per_lane + 2) * m * m;
-    bias = __int_as_float((__float_as_int(b) & 0x7F800000) + 0x00800000);   // next power of two above b
-    __syncthreads();
-  }
-  float hi[32], lo[32];
-#pragma unroll
-  for (int a = 0; a < 32; ++a) {
-    hi[a] = bias;
-    lo[a] = 0.f;
-  }
-  if (t0 < t1) issue_tile(0, t0);
+  if (t0 < t1) issue(0, t0);
   int buf = 0;
   for (int ts = t0; ts < t1; ts += T::kTS, buf ^= 1) {
     const int cnt = min(T::kTS, t1 - ts);
     if (ts + T::kTS < t1) {
-      issue_tile(buf ^ 1, ts + T::kTS);
+      issue(buf ^ 1, ts + T::kTS);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
