@@ -68,3 +68,27 @@ def test_model_order_batch(env):
         m2, a2, mv2, av2 = oracle.model_order(t[5].cpu().numpy(), inst.N)
         for g, w, vals in ((got[0], m2, mv2), (got[1], a2, av2)):
             assert g == w or abs(vals[g] - vals[w]) <= 1e-12 * abs(vals[w])
+
+
+def test_model_order_rank_deficient(env):
+    """N < M: the smallest eigenvalues are (numerically) zero or tiny; the GPU estimate equals the
+    oracle's on the GPU's own eigenvalues."""
+    torch, doa = env
+    inst = synth.custom(12, 2, 5, None, 10.0, 1.0, seed=861)
+    X = torch.from_numpy(inst.X).cuda()
+    P = torch.empty(inst.L, dtype=torch.float32, device="cuda")
+    idx = torch.full((2,), -1, dtype=torch.int32, device="cuda")
+    val = torch.zeros(2, dtype=torch.float32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ev = torch.empty(12, dtype=torch.float64, device="cuda")
+    est = torch.full((2,), -1, dtype=torch.int32, device="cuda")
+    prob = doa.make_problem(X, 2, 1 << 1, doa.grid(inst.lo, inst.step, inst.L), P, idx, val, cnt, ev, order_est=est)
+    plan = doa.BatchPlan([prob])
+    ws = doa.workspace(plan)
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    doa.doa_solve_batch(plan, ws, status)
+    torch.cuda.synchronize()
+    m2, a2, mv, av = oracle.model_order(ev.cpu().numpy(), inst.N)
+    got = est.cpu().numpy()
+    for g, w, vals in ((got[0], m2, mv), (got[1], a2, av)):
+        assert g == w or abs(vals[g] - vals[w]) <= 1e-12 * abs(vals[w]) or (np.isinf(vals[g]) and np.isinf(vals[w]))

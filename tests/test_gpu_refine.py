@@ -150,3 +150,100 @@ def test_refine_batch_geometry(env):
                 (wt, wp), _ = oracle.refine_peak2d(ref["C"], g.pos, g.az_lo, g.az_step, g.La, g.el_lo, g.el_step, int(k))
                 worst = max(worst, abs(ang[slot, q, 0] - wt), abs(ang[slot, q, 1] - wp))
     assert worst < 1e-6, worst
+
+
+def test_refine2d_in_plane_sources(env):
+    """Sources in the array plane (elevation angle 90, the last grid row): the refinement box
+    reaches past the grid's last row and the planar array's spectrum is symmetric about 90, so
+    the refined elevation is 90 to within the iteration's tolerance; the GPU matches the oracle."""
+    torch, doa = env
+    pos = synth.uca_positions(8, 0.5)
+    rng_seed = 31
+    g = synth.geometry_custom(pos, 2, 4096, 20.0, 0.0, 1.0, 360, 1.0, 1.0, 90, True, seed=rng_seed)
+    # overwrite the sources: two in-plane directions
+    from paper_2007_14135_gb300.synth import _rng, snapshots_geometry
+    g.az, g.el = np.array([40.3, 200.7]), np.array([90.0, 90.0])
+    g.X = snapshots_geometry(_rng(rng_seed), pos, 4096, g.az, g.el, 20.0)
+    X = torch.from_numpy(g.X).cuda()
+    P = torch.empty(g.La * g.Le, dtype=torch.float32, device="cuda")
+    idx = torch.full((2,), -1, dtype=torch.int32, device="cuda")
+    val = torch.zeros(2, dtype=torch.float32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ang = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+    posd = torch.from_numpy(np.ascontiguousarray(pos)).cuda()
+    geom = doa.geometry(posd, g.el_lo, g.el_step, g.Le, True)
+    prob = doa.make_problem(X, 2, 1 << MUSIC, doa.grid(g.az_lo, g.az_step, g.La), P, idx, val, cnt, geom=geom,
+                            peak_angle=ang)
+    plan = doa.BatchPlan([prob])
+    ws = doa.workspace(plan)
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    doa.doa_solve_batch(plan, ws, status)
+    torch.cuda.synchronize()
+    assert status.item() == 0
+    ref = oracle.solve_geometry(g.X, 2, MUSIC, pos, g.az_lo, g.az_step, g.La, g.el_lo, g.el_step, g.Le, True)
+    gi = list(idx.cpu().numpy()[:cnt.item()])
+    assert gi == list(ref["idx"])
+    a = ang.cpu().numpy().reshape(2, 2)
+    for q, k in enumerate(gi):
+        assert k // g.La == g.Le - 1                     # the peaks sit on the in-plane row
+        (wt, wp), _ = oracle.refine_peak2d(ref["C"], pos, g.az_lo, g.az_step, g.La, g.el_lo, g.el_step, int(k))
+        assert abs(a[q, 0] - wt) < 1e-6 and abs(a[q, 1] - wp) < 1e-6
+        assert abs(a[q, 1] - 90.0) < 1e-6
+
+
+def test_all_outputs_together(env):
+    """ULA and geometry problems in one plan with every optional output at once (refined angles,
+    root angles for the ULA ones, model-order estimates, B_out, eigenvalues, peak polish on the ULA
+    ones): each output equals what the same problem gives alone."""
+    torch, doa = env
+    ulas = [synth.custom(16, 4, 4096, None, 15.0, 0.05, seed=41), synth.custom(3, 2, 500, None, 10.0, 0.5, seed=42)]
+    geo = synth.paper_uca(30, Le=30)
+
+    def ula_problem(inst, keep, polish=True, extras=True):
+        X = torch.from_numpy(inst.X).cuda()
+        t = dict(X=X, P=torch.empty(4 * inst.L, dtype=torch.float32, device="cuda"),
+                 idx=torch.full((4 * inst.d,), -1, dtype=torch.int32, device="cuda"),
+                 val=torch.zeros(4 * inst.d, dtype=torch.float32, device="cuda"),
+                 cnt=torch.zeros(4, dtype=torch.int32, device="cuda"),
+                 ang=torch.full((4 * inst.d,), float("nan"), dtype=torch.float64, device="cuda"),
+                 ra=torch.full((4 * inst.d,), float("nan"), dtype=torch.float64, device="cuda"),
+                 oe=torch.full((2,), -1, dtype=torch.int32, device="cuda"),
+                 ev=torch.empty(inst.M, dtype=torch.float64, device="cuda"))
+        keep.append(t)
+        return doa.make_problem(X, inst.d, 0xF, doa.grid(inst.lo, inst.step, inst.L), t["P"], t["idx"], t["val"],
+                                t["cnt"], t["ev"], polish=polish, peak_angle=t["ang"] if extras else None,
+                                root_angle=t["ra"] if extras else None, order_est=t["oe"] if extras else None)
+
+    def geo_problem(g, keep):
+        X = torch.from_numpy(g.X).cuda()
+        posd = torch.from_numpy(np.ascontiguousarray(g.pos)).cuda()
+        t = dict(X=X, pos=posd, P=torch.empty(g.La * g.Le, dtype=torch.float32, device="cuda"),
+                 idx=torch.full((2,), -1, dtype=torch.int32, device="cuda"),
+                 val=torch.zeros(2, dtype=torch.float32, device="cuda"),
+                 cnt=torch.zeros(1, dtype=torch.int32, device="cuda"),
+                 ang=torch.full((4,), float("nan"), dtype=torch.float64, device="cuda"),
+                 oe=torch.full((2,), -1, dtype=torch.int32, device="cuda"))
+        keep.append(t)
+        geom = doa.geometry(posd, g.el_lo, g.el_step, g.Le, True)
+        return doa.make_problem(X, 2, 1 << MUSIC, doa.grid(g.az_lo, g.az_step, g.La), t["P"], t["idx"], t["val"],
+                                t["cnt"], geom=geom, peak_angle=t["ang"], order_est=t["oe"])
+
+    def solve(probs):
+        plan = doa.BatchPlan(probs)
+        ws = doa.workspace(plan)
+        st = torch.full((len(probs),), -1, dtype=torch.int32, device="cuda")
+        doa.doa_solve_batch(plan, ws, st)
+        torch.cuda.synchronize()
+        assert np.all(st.cpu().numpy() == 0)
+
+    keep_all = []
+    solve([ula_problem(ulas[0], keep_all), geo_problem(geo, keep_all), ula_problem(ulas[1], keep_all)])
+    for inst_or_geo, t_all, maker in ((ulas[0], keep_all[0], "ula"), (geo, keep_all[1], "geo"), (ulas[1], keep_all[2], "ula")):
+        keep_one = []
+        solve([ula_problem(inst_or_geo, keep_one) if maker == "ula" else geo_problem(inst_or_geo, keep_one)])
+        t_one = keep_one[0]
+        for key in t_all:
+            if key in ("X", "pos"):
+                continue
+            a, b = t_all[key].cpu().numpy(), t_one[key].cpu().numpy()
+            assert np.array_equal(a, b, equal_nan=True), (maker, key)

@@ -60,3 +60,20 @@ def test_root_music_batch(env):
             ref = oracle.solve(inst.X, inst.d, alg, inst.lo, inst.step, inst.L)
             want, _ = oracle.root_music(ref["C"], inst.d)
             np.testing.assert_allclose(ra[alg], want, rtol=0, atol=1e-6, err_msg=f"seed {inst.seed} alg {alg}")
+
+
+@pytest.mark.parametrize("M,d", [(3, 2), (5, 4), (8, 7)])
+def test_root_music_one_noise_vector(env, M, d):
+    """d = M - 1: one noise eigenvector, a degree 2M-2 polynomial with M-1 roots inside."""
+    torch, doa = env
+    inst = synth.custom(M, d, 2000, np.linspace(-50, 50, d) + 0.3, 20.0, 1.0, seed=950 + M)
+    ev, V, _ = oracle.eigh(oracle.covariance(inst.X))
+    Bf = factor_from_decomposition(ev, V, d, MUSIC)
+    B = torch.from_numpy(np.ascontiguousarray(Bf.T).reshape(-1)).cuda()
+    th = torch.full((d,), -99.0, dtype=torch.float64, device="cuda")
+    info = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    doa.doa_root_music(B, M, 1, d, th, info)
+    torch.cuda.synchronize()
+    assert info.item() == 0
+    want, _ = oracle.root_music(Bf @ Bf.conj().T, d)
+    np.testing.assert_allclose(th.cpu().numpy(), want, rtol=0, atol=1e-6)
