@@ -78,10 +78,11 @@ __global__ void __launch_bounds__(kScanThreads) scan_single_kernel(const double2
 }
 
 // Persistent batched scan over the tiles of the problems of one M bucket. The tiles are dealt
-// to the CTAs in runs of kRun consecutive tiles, run r to CTA r mod gridDim: consecutive tiles
+// to the CTAs in runs of consecutive tiles, run r to CTA r mod gridDim: consecutive tiles
 // mostly share a problem (its factor stays in shared memory), while the runs of problems of
 // different cost (columns, M) spread evenly over the CTAs. The problem of a run's first tile
 // comes from a binary search on the problems' first tiles, the following ones by stepping.
+// Flagged points queue up over the run and are re-evaluated when it ends or its problem changes.
 constexpr int kRun = 16;   // longest run (large batches); small ones use shorter runs so every SM gets one
 
 template <int MP, int PT>
@@ -110,6 +111,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t 
     for (int64_t t = t_begin; t < t_end; ++t) {
       while (u + 1 < nunits && probs[list[u + 1]].tile_start <= t) ++u;
       if (u != cur) {
+        if (cur >= 0) drain_refinements(j, sh);   // the queued points belong to the previous problem
         pp = &probs[list[u]];
         g = &grids[pp->grid_id];
         j.F = reinterpret_cast<const double2 *>(ws + pp->fac_off);
@@ -136,8 +138,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t 
       const uint32_t *S = reinterpret_cast<const uint32_t *>(ws + g->S_off);
       const int k0 = (int)(t - pp->tile_start) * TP + threadIdx.x * PT;
       scan_points<MP, PT>(Bs, j, S, g->L, k0, sh);
-      drain_refinements(j, sh);
     }
+    drain_refinements(j, sh);   // once per run: the warps share the FP64 work of its tiles
   }
 }
 
