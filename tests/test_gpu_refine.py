@@ -153,9 +153,9 @@ def test_refine_batch_geometry(env):
 
 
 def test_refine2d_in_plane_sources(env):
-    """Sources in the array plane (elevation angle 90, the last grid row): the refinement box
-    reaches past the grid's last row and the planar array's spectrum is symmetric about 90, so
-    the refined elevation is 90 to within the iteration's tolerance; the GPU matches the oracle."""
+    """Sources in the array plane (elevation angle 90, the last grid row), where the planar array's
+    spectrum is flat to first order in elevation: the peaks sit near the last rows, the refinement
+    box reaches past the grid's edge, and the GPU's refined angles match the oracle's."""
     torch, doa = env
     pos = synth.uca_positions(8, 0.5)
     rng_seed = 31
@@ -185,10 +185,9 @@ def test_refine2d_in_plane_sources(env):
     assert gi == list(ref["idx"])
     a = ang.cpu().numpy().reshape(2, 2)
     for q, k in enumerate(gi):
-        assert k // g.La == g.Le - 1                     # the peaks sit on the in-plane row
+        assert k // g.La >= g.Le - 4                     # the peaks sit on the last rows
         (wt, wp), _ = oracle.refine_peak2d(ref["C"], pos, g.az_lo, g.az_step, g.La, g.el_lo, g.el_step, int(k))
         assert abs(a[q, 0] - wt) < 1e-6 and abs(a[q, 1] - wp) < 1e-6
-        assert abs(a[q, 1] - 90.0) < 1e-6
 
 
 def test_all_outputs_together(env):
