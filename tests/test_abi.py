@@ -241,3 +241,42 @@ def test_batch_plan_geometry_problems(libdoa):
     for bad in (gprob(prec=3), gprob(flags=1), gprob(Le=0), gprob(La=0), gprob(La=1 << 16, Le=1 << 15)):
         one = (libdoa.Problem * 1)(bad)
         assert libdoa.lib().doa_batch_plan_bytes(one, 1) == 0
+
+
+def test_batch_plan_optional_outputs(libdoa):
+    """Refined angles, root angles and model-order outputs: counted in the plan header, the root
+    form only on ULA problems, misaligned outputs rejected; the launch count follows."""
+    import numpy as np
+
+    def plan_of(probs):
+        arr = (libdoa.Problem * len(probs))(*probs)
+        n = libdoa.lib().doa_batch_plan_bytes(arr, len(probs))
+        if n == 0:
+            return None
+        buf = np.zeros(n, np.uint8)
+        ws = ctypes.c_size_t(0)
+        assert libdoa.lib().doa_batch_plan(arr, len(probs), None, buf.ctypes.data, n, ctypes.byref(ws), None) == 0
+        return buf, ws.value
+
+    base = _prob(libdoa, M=8, d=2, L=1801, step=0.1)
+    with_all = _prob(libdoa, M=8, d=2, L=1801, step=0.1, peak_angle=0x700000, root_angle=0x710000, order_est=0x720000)
+    buf0, ws0 = plan_of([base])
+    buf1, ws1 = plan_of([with_all, base])
+    h1 = buf1[:512].view(np.int32)
+    assert h1[100] == 1 and h1[101] == 1                 # nrefine, nroots
+    assert buf0[:512].view(np.int32)[100] == 0
+    geo = _prob(libdoa, M=8, d=2, L=360, step=1.0)
+    geo.geom = libdoa.Geometry(0x20000, 1.0, 1.0, 90, 1)
+    geo_ok = _prob(libdoa, M=8, d=2, L=360, step=1.0, peak_angle=0x700000, order_est=0x720000)
+    geo_ok.geom = libdoa.Geometry(0x20000, 1.0, 1.0, 90, 1)
+    assert plan_of([geo_ok]) is not None                 # refinement and model order on a geometry problem
+    geo.root_angle = 0x710000
+    assert plan_of([geo]) is None                        # the root form needs the ULA
+    for field, value in (("peak_angle", 0x700004), ("root_angle", 0x710004), ("order_est", 0x720002)):
+        bad = _prob(libdoa, M=8, d=2, L=1801, step=0.1, **{field: value})
+        assert plan_of([bad]) is None, field
+    # polish: the plan reserves one float per job for the value below the selection
+    pol = _prob(libdoa, M=8, d=2, L=1801, step=0.1, flags=1)
+    bufp, wsp = plan_of([pol])
+    assert wsp >= ws0 + 4 * 4 - 256 and bufp[:512].view(np.int64)[51] >= 0     # next_val_off
+    assert buf0[:512].view(np.int64)[51] == -1
