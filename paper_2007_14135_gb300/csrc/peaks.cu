@@ -4,11 +4,12 @@
 // P[i-1] < P[i] and P[j+1] < P[j]. The D largest peaks are selected (equal values: lower
 // index first) and written in ascending index order.
 //
-// Thread t owns the interior points 1 + t, 1 + t + 256, ... (coalesced loads) and keeps its best
-// kCache peaks in registers. Selection runs D rounds of a block-wide arg-max (warp shuffles, then
-// one warp over the warp winners); the winning thread pops its head and, if its cache runs dry
-// while it still has peaks, rescans its points for the next ones below its last selected peak. This realises the
-// shared-memory max-reduction that the paper names as future work for Step-6 (Sec. 6).
+// Thread t owns the aligned quads of four points t, t + 256, ... (16-byte coalesced loads) and
+// keeps its best kCache peaks in registers. Each warp picks its D best in D rounds of a warp
+// arg-max (the winning lane pops its head and, if its cache runs dry while it still has peaks,
+// rescans its quads for the next ones below its last selected peak); one warp then merges the
+// warps' lists. This realises the shared-memory max-reduction that the paper names as future work
+// for Step-6 (Sec. 6).
 #include <climits>
 
 #include "doa_internal.cuh"
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_single_kernel(const float 
 // One CTA per (problem, algorithm) job; the 1-D and 2-D rules run as separate kernels (each skips
 // the other kind's jobs) so that each keeps its own register budget.
 // repick: the pick after the peak polish, only for the jobs the polish marked (NaN next value).
-__global__ void __launch_bounds__(kPeakThreads) peaks_batch_kernel(const uint8_t *plan, uint8_t *ws, int repick) {
+__global__ void __launch_bounds__(kPeakThreads, 5) peaks_batch_kernel(const uint8_t *plan, uint8_t *ws, int repick) {
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
   const PlanJob &jb = reinterpret_cast<const PlanJob *>(plan + h->off_job)[blockIdx.x];
   const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[jb.prob];
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_batch_kernel(const uint8_t
               pp.p.peak_val + (size_t)jb.slot * d, pp.p.peak_count + jb.slot, next);
 }
 
-__global__ void __launch_bounds__(kPeakThreads) peaks2d_batch_kernel(const uint8_t *plan) {
+__global__ void __launch_bounds__(kPeakThreads, 5) peaks2d_batch_kernel(const uint8_t *plan) {
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
   const PlanJob &jb = reinterpret_cast<const PlanJob *>(plan + h->off_job)[blockIdx.x];
   const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[jb.prob];
@@ -128,26 +129,7 @@ __device__ bool slice_fill(const SliceView &P, int c0, int c1, int limit, int L,
       *open_val = v;
     }
     if (st != 1) continue;
-    Cand c{v, i};
-    if (thr.i != INT_MAX && !better(thr, c)) continue;
-    if (n < kCache) {
-      int k = n++;
-      while (k > 0 && better(c, cache[k - 1])) {
-        cache[k] = cache[k - 1];
-        --k;
-      }
-      cache[k] = c;
-    } else {
-      more = true;
-      if (better(c, cache[kCache - 1])) {
-        int k = kCache - 1;
-        while (k > 0 && better(c, cache[k - 1])) {
-          cache[k] = cache[k - 1];
-          --k;
-        }
-        cache[k] = c;
-      }
-    }
+    cache_insert(Cand{v, i}, thr, cache, n, more);
   }
   return more;
 }
