@@ -1,8 +1,9 @@
 // Block-wide peak search and top-d selection shared by doa_peaks and the windowed scan.
 // A peak is the left end i of a maximal run [i..j] of equal values with 1 <= i, j <= L-2,
 // P[i-1] < P[i] and P[j+1] < P[j] (Table 2 Step-6). Each thread owns every kPeakThreads-th aligned
-// quad of four points and keeps its best kCache peaks in registers; d rounds of a block arg-max
-// pick the winners, a thread rescanning its quads only when its cache runs dry.
+// quad of four points and keeps its best kCache peaks in registers; d rounds of a warp arg-max pick
+// each warp's winners (a thread rescanning its quads only when its cache runs dry), and one warp
+// merges the warps' lists.
 #pragma once
 
 #include <climits>
