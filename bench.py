@@ -51,7 +51,7 @@ def workload_name(batch):
 # when its kernel changes.
 TRAFFIC_BYTES = {
     "scan_batch_kernel<16,2>": 4 * (4.274432e6 + 234.934528e6),
-    "scan_geometry_batch_kernel<8,4>": 2 * (2.256896e6 + 204.855040e6),
+    "scan_geometry_batch_kernel<8,4>": None,   # changed since its capture: reads shared steering tables
     "scan_geometry_batch_kernel<8,2>": None,
 }
 

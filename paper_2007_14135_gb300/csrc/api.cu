@@ -82,6 +82,7 @@ struct PlanSizes {
   int scan[kNumBuckets] = {0, 0, 0, 0};
   int geo[kNumBuckets] = {0, 0, 0, 0};
   int ngeo_grids = 0;
+  int ngeo_steer = 0;
 };
 
 
@@ -103,11 +104,25 @@ bool same_geo_grid(const GeoGridKey &a, const doa_problem &p) {
          std::memcmp(&a.el_step, &p.geom.el_step_deg, sizeof(double)) == 0;
 }
 
-// Counts the plan's arrays; returns false on an invalid problem.
+// Geometry problems that pass the same positions pointer with the same grid and M share one FP32
+// steering table (when at least two do, and the table is at most kSteerMaxBytes).
+struct SteerKey {
+  const double *pos;
+  int geo_grid, M, count;
+};
+constexpr int64_t kSteerMaxBytes = int64_t(1) << 28;
+
+int64_t steer_ldt(const GeoGridKey &g) { return round_up((int64_t)g.az.L * g.Le, kSteerAlign); }
+int steer_rows(int M) { return 8 << m_bucket(M); }
+
+// Counts the plan's arrays; returns false on an invalid problem. steer_of[i]: the shared steering
+// table of geometry problem i, or -1.
 bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<doa_grid> &grids,
-                std::vector<int> &grid_of, std::vector<GeoGridKey> &geo_grids, int *bad_index) {
+                std::vector<int> &grid_of, std::vector<GeoGridKey> &geo_grids, std::vector<SteerKey> &steers,
+                std::vector<int> &steer_of, int *bad_index) {
   sz.nprob = nprob;
   grid_of.resize(nprob);
+  steer_of.assign(nprob, -1);
   for (int i = 0; i < nprob; ++i) {
     const doa_problem &p = probs[i];
     if (!problem_ok(p)) {
@@ -133,6 +148,18 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
         geo_grids.push_back(GeoGridKey{p.grid, p.geom.el_lo_deg, p.geom.el_step_deg, p.geom.Le});
       }
       grid_of[i] = g;
+      int st = -1;
+      for (size_t k = 0; k < steers.size(); ++k)
+        if (steers[k].pos == p.geom.pos && steers[k].geo_grid == g && steers[k].M == p.M) {
+          st = (int)k;
+          break;
+        }
+      if (st < 0) {
+        st = (int)steers.size();
+        steers.push_back(SteerKey{p.geom.pos, g, p.M, 0});
+      }
+      ++steers[st].count;
+      steer_of[i] = st;
       continue;
     }
     if (p.prec == DOA_FP32)
@@ -153,11 +180,27 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
   }
   sz.ngrids = (int)grids.size();
   sz.ngeo_grids = (int)geo_grids.size();
+  // keep the tables that two or more problems read; renumber them in order of first use
+  std::vector<int> keep(steers.size(), -1);
+  std::vector<SteerKey> kept;
+  for (size_t k = 0; k < steers.size(); ++k) {
+    const SteerKey &t = steers[k];
+    if (t.count >= 2 && 8 * steer_rows(t.M) * steer_ldt(geo_grids[t.geo_grid]) <= kSteerMaxBytes &&
+        kept.size() < 65535) {   // one grid row of the table kernel per table
+      keep[k] = (int)kept.size();
+      kept.push_back(t);
+    }
+  }
+  for (int i = 0; i < nprob; ++i)
+    if (steer_of[i] >= 0) steer_of[i] = keep[steer_of[i]];
+  steers.swap(kept);
+  sz.ngeo_steer = (int)steers.size();
   return true;
 }
 
 struct PlanOffsets {
-  int64_t prob, job, grid, cov, reduce, eig[kNumBuckets], scan[kNumBuckets], tc, geo[kNumBuckets], geo_grid, total;
+  int64_t prob, job, grid, cov, reduce, eig[kNumBuckets], scan[kNumBuckets], tc, geo[kNumBuckets], geo_grid,
+      geo_steer, total;
 };
 
 PlanOffsets plan_offsets(const PlanSizes &sz) {
@@ -189,6 +232,8 @@ PlanOffsets plan_offsets(const PlanSizes &sz) {
   }
   o.geo_grid = at;
   at = round_up(at + (int64_t)sz.ngeo_grids * sizeof(PlanGeoGrid), 16);
+  o.geo_steer = at;
+  at = round_up(at + (int64_t)sz.ngeo_steer * sizeof(PlanGeoSteer), 16);
   o.total = at;
   return o;
 }
@@ -371,7 +416,9 @@ size_t doa_batch_plan_bytes(const doa_problem *probs, int nprob) {
   std::vector<doa_grid> grids;
   std::vector<int> grid_of;
   std::vector<GeoGridKey> geo_grids;
-  if (!count_plan(probs, nprob, sz, grids, grid_of, geo_grids, nullptr)) return 0;
+  std::vector<SteerKey> steers;
+  std::vector<int> steer_of;
+  if (!count_plan(probs, nprob, sz, grids, grid_of, geo_grids, steers, steer_of, nullptr)) return 0;
   return (size_t)plan_offsets(sz).total;
 }
 
@@ -389,7 +436,9 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
   std::vector<doa_grid> grids;
   std::vector<int> grid_of;
   std::vector<GeoGridKey> geo_grids;
-  if (!count_plan(probs, nprob, sz, grids, grid_of, geo_grids, bad_index)) return DOA_EINVAL;
+  std::vector<SteerKey> steers;
+  std::vector<int> steer_of;
+  if (!count_plan(probs, nprob, sz, grids, grid_of, geo_grids, steers, steer_of, bad_index)) return DOA_EINVAL;
   const PlanOffsets o = plan_offsets(sz);
   if (!plan || plan_bytes < (size_t)o.total) return DOA_ENOMEM;
   uint8_t *base = static_cast<uint8_t *>(plan);
@@ -459,6 +508,23 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     ws = round_up(ws + 8 * ((int64_t)e.La + e.Le), 256);
     h.geo_grid_points = std::max(h.geo_grid_points, e.La + e.Le);
   }
+  // workspace: shared FP32 steering tables (float2[MP][ldt] each)
+  PlanGeoSteer *pst = reinterpret_cast<PlanGeoSteer *>(base + o.geo_steer);
+  h.off_geo_steer = o.geo_steer;
+  h.ngeo_steer = sz.ngeo_steer;
+  for (int t = 0; t < sz.ngeo_steer; ++t) {
+    const SteerKey &k = steers[t];
+    PlanGeoSteer &e = pst[t];
+    e.pos = k.pos;
+    e.geo_grid = k.geo_grid;
+    e.M = k.M;
+    e.MP = steer_rows(k.M);
+    e.npts = geo_grids[k.geo_grid].az.L * geo_grids[k.geo_grid].Le;
+    e.ldt = (int32_t)steer_ldt(geo_grids[k.geo_grid]);
+    e.tab_off = ws;
+    ws = round_up(ws + 8 * (int64_t)e.MP * e.ldt, 256);
+    h.steer_max_ldt = std::max(h.steer_max_ldt, e.ldt);
+  }
   int icov[kCovClasses], ired = 0, ijob = 0;
   h.cov_first[0] = 0;
   for (int c = 0; c < kCovClasses; ++c) {
@@ -486,6 +552,7 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     eig[b][ie[b]++] = i;
     q.grid_id = p.geom.pos ? -1 : grid_of[i];
     q.geo_grid = p.geom.pos ? grid_of[i] : -1;
+    q.geo_steer = p.geom.pos ? steer_of[i] : -1;
     q.first_job = ijob;
     int slot = 0;
     for (int a = 0; a < 4; ++a) {

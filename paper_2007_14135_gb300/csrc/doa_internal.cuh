@@ -172,6 +172,7 @@ struct PlanProblem {
   int32_t slot[4];        // output row of each algorithm (doa_alg order), -1 if not requested
   int32_t npts;           // points of one spectrum: L, or La x Le for a geometry problem
   int32_t geo_grid;       // geometry problems: index of the azimuth x elevation grid's tables
+  int32_t geo_steer;      // geometry problems: index of the shared FP32 steering table, or -1
 };
 
 // Bytes of a problem's scan factor area: F (M x (M+1) complex128) + EV weights (M doubles).
@@ -201,6 +202,19 @@ struct PlanGeoGrid {
   int64_t t32_off;        // float2[La + Le], the FP64 values rounded once
   int64_t t64_off;        // double2[La + Le]
 };
+
+// FP32 steering table of the geometry problems that pass the same positions pointer, grid and M:
+// a_m at every point of the grid, rows m < MP (rows >= M zero), written once per solve from the
+// FP64 phases and read by the scan instead of evaluating the phasors for each problem.
+struct PlanGeoSteer {
+  const double *pos;      // the problems' element positions (M x 3, FP64, wavelengths)
+  int32_t geo_grid;       // their azimuth x elevation grid
+  int32_t M, MP;          // elements; table rows (the M bucket's padded size)
+  int32_t npts, ldt;      // points of the grid; row stride (npts rounded up to kSteerAlign)
+  int32_t pad;
+  int64_t tab_off;        // workspace byte offset of float2[MP][ldt]
+};
+constexpr int kSteerAlign = 1024;   // row stride multiple: every scan tile's points lie inside a row
 
 struct PlanCovItem {
   int32_t prob;
@@ -241,11 +255,14 @@ struct PlanHeader {
   int32_t nroots;                        // problems with a root_angle output (root form of the scan)
   int64_t next_val_off;                  // workspace byte offset of one float per job: the value of
                                          // the best peak below the d selected (peak polish), or -1
+  int32_t ngeo_steer;                    // shared FP32 steering tables of geometry problems
+  int32_t steer_max_ldt;                 // largest row stride among them
+  int64_t off_geo_steer;
 };
 
 // The Python binding reads these header fields by position (int32 index 22 = scan_pt, 58 = eig_mats,
 // 62 = cov_first, 67 = tc_jobs, 74 = npolish, 76 = geo_jobs, 96 = ngeo_grids, 100 = nrefine,
-// 101 = nroots).
+// 101 = nroots, 104 = ngeo_steer).
 static_assert(offsetof(PlanHeader, scan_pt) == 88, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, scan_tiles) == 56, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, eig_mats) == 232, "PlanHeader layout changed");
@@ -256,6 +273,7 @@ static_assert(offsetof(PlanHeader, geo_jobs) == 304, "PlanHeader layout changed"
 static_assert(offsetof(PlanHeader, ngeo_grids) == 384, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, nrefine) == 400, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, nroots) == 404, "PlanHeader layout changed");
+static_assert(offsetof(PlanHeader, ngeo_steer) == 416, "PlanHeader layout changed");
 
 // Scan tiles: kScanThreads threads, each evaluating PT consecutive grid points (tile shape
 // 128 x PT). PT is chosen per M bucket (the autotuner's knob); the register budget limits it

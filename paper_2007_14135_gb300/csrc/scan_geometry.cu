@@ -27,6 +27,11 @@
 // per term replaces the 4 eps per term of the ULA scan, so the refinement thresholds of
 // scan_common.cuh scale by ((eps_a + 3) / 4)^2. Points below them are re-evaluated with the FP64
 // tables, FP64 phases and the FP64 factor (warp per point).
+//
+// Shared steering tables (batch). Geometry problems that pass the same positions pointer with the
+// same grid and M read their phasors from one FP32 table, written once per solve from the FP64
+// phases of the refinement (each component rounded once, an error well inside eps_a), instead of
+// evaluating them per problem: the phasors are about half of a point's instructions.
 #include <float.h>
 
 #include <algorithm>
@@ -78,7 +83,8 @@ __global__ void geo_table_batch_kernel(const uint8_t *plan, uint8_t *ws) {
     geo_table_entry(g.az_lo, g.az_step, g.La, g.el_lo, g.el_step, e, t32, t64);
 }
 
-// FP64 steering source of the refinement: flat point i -> (u, v, w), then the phase of element m.
+// FP64 steering source of the refinement and of the shared tables: flat point i -> (u, v, w), then
+// the phase of element m.
 struct GeoSource {
   const double *pos;
   const double2 *t64;
@@ -98,6 +104,48 @@ struct GeoSource {
     return phasor_q64((uint64_t)__double2ll_rn(f * 4611686018427387904.0) << 2);   // f * 2^64
   }
 };
+
+// Shared steering table t of the plan (blockIdx.y): tab[m * ldt + i] = a_m at flat point i, the
+// FP64 phasor of the refinement rounded to FP32; rows m >= M and points i >= npts are zero.
+__global__ void geo_steer_kernel(const uint8_t *plan, uint8_t *ws) {
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
+  const PlanGeoSteer st = reinterpret_cast<const PlanGeoSteer *>(plan + h->off_geo_steer)[blockIdx.y];
+  const PlanGeoGrid g = reinterpret_cast<const PlanGeoGrid *>(plan + h->off_geo_grid)[st.geo_grid];
+  __shared__ double cen[3];
+  if (threadIdx.x == 0) {
+    double cx = 0.0, cy = 0.0, cz = 0.0;
+    for (int m = 0; m < st.M; ++m) {
+      cx += st.pos[3 * m];
+      cy += st.pos[3 * m + 1];
+      cz += st.pos[3 * m + 2];
+    }
+    cen[0] = cx / st.M;
+    cen[1] = cy / st.M;
+    cen[2] = cz / st.M;
+  }
+  __syncthreads();
+  GeoSource src;
+  src.pos = st.pos;
+  src.t64 = reinterpret_cast<const double2 *>(ws + g.t64_off);
+  src.cx = cen[0];
+  src.cy = cen[1];
+  src.cz = cen[2];
+  src.La = g.La;
+  float2 *tab = reinterpret_cast<float2 *>(ws + st.tab_off);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < st.ldt; i += gridDim.x * blockDim.x) {
+    const bool in = i < st.npts;
+    GeoSource::Dir d{0.0, 0.0, 0.0};
+    if (in) d = src.prep(i);
+    for (int m = 0; m < st.MP; ++m) {
+      float2 v = make_float2(0.f, 0.f);
+      if (in && m < st.M) {
+        const double2 a = src.phasor(d, m);
+        v = make_float2((float)a.x, (float)a.y);
+      }
+      tab[(size_t)m * st.ldt + i] = v;
+    }
+  }
+}
 
 // Per-job constants: centroid, FP32 positions and the scaled thresholds. Every thread of the CTA
 // calls it after load_job; it ends with a barrier.
@@ -137,12 +185,35 @@ __device__ void geo_setup(const float2 *Bs, const ScanJob &j, const GeoParams &g
   __syncthreads();
 }
 
+// tab (nullable): the problem's shared steering table (row stride ldt, a multiple of every tile's
+// point count, so the PT points of a thread lie inside each row and start on a 2 * PT float
+// boundary); without it the phasors are evaluated here.
 template <int MP, int PT>
 __device__ __forceinline__ void geo_points(const float2 *Bs, const ScanJob &j, const GeoShared &gs,
                                            const float2 *__restrict__ t32, int La, int Le, int npts, int i0,
-                                           ScanShared &sh, const GeoSource &src) {
+                                           ScanShared &sh, const GeoSource &src,
+                                           const float2 *__restrict__ tab = nullptr, int ldt = 0) {
   static_assert(MP % 4 == 0, "MP is a multiple of 4");
   float2 a[PT][MP];
+  if (tab) {
+#pragma unroll
+    for (int m = 0; m < MP; ++m) {
+      const float2 *row = tab + (size_t)m * ldt + i0;
+      if constexpr (PT % 2 == 0) {
+#pragma unroll
+        for (int q2 = 0; q2 < PT / 2; ++q2) {
+          const float4 v = __ldg(reinterpret_cast<const float4 *>(row) + q2);
+          a[2 * q2][m] = make_float2(v.x, v.y);
+          a[2 * q2 + 1][m] = make_float2(v.z, v.w);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < PT; ++q) a[q][m] = __ldg(row + q);
+      }
+    }
+    contract_points<MP, PT>(Bs, j, a, npts, i0, sh, src);
+    return;
+  }
   int l = i0 / La, k = i0 - l * La;
 #pragma unroll
   for (int q = 0; q < PT; ++q) {
@@ -219,12 +290,16 @@ __global__ void __launch_bounds__(kScanThreads) scan_geometry_batch_kernel(const
   const int32_t *list = reinterpret_cast<const int32_t *>(plan + h->off_geo[bucket]);
   const PlanProblem *probs = reinterpret_cast<const PlanProblem *>(plan + h->off_prob);
   const PlanGeoGrid *geo_grids = reinterpret_cast<const PlanGeoGrid *>(plan + h->off_geo_grid);
+  const PlanGeoSteer *steers = reinterpret_cast<const PlanGeoSteer *>(plan + h->off_geo_steer);
   constexpr int TP = kScanThreads * PT;
+  static_assert(kSteerAlign % TP == 0, "a tile's points lie inside one steering-table row");
   int cur = -1;
   ScanJob j{};
   GeoParams g{};
   GeoSource src{};
   const PlanProblem *pp = nullptr;
+  const float2 *tab = nullptr;
+  int ldt = 0;
   for (int64_t run = blockIdx.x; run * run_len < ntiles; run += gridDim.x) {
     const int64_t t_begin = run * run_len, t_end = min(ntiles, t_begin + run_len);
     int u = 0, hi = nunits - 1;
@@ -256,6 +331,13 @@ __global__ void __launch_bounds__(kScanThreads) scan_geometry_batch_kernel(const
         g.t64 = reinterpret_cast<const double2 *>(ws + gg.t64_off);
         g.La = gg.La;
         g.Le = gg.Le;
+        tab = nullptr;
+        ldt = 0;
+        if (pp->geo_steer >= 0) {
+          const PlanGeoSteer &st = steers[pp->geo_steer];
+          tab = reinterpret_cast<const float2 *>(ws + st.tab_off);
+          ldt = st.ldt;
+        }
         __syncthreads();
         load_job<MP>(j, Bs, sh);
         __syncthreads();
@@ -264,7 +346,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_geometry_batch_kernel(const
         cur = u;
       }
       const int i0 = (int)(t - pp->tile_start) * TP + threadIdx.x * PT;
-      geo_points<MP, PT>(Bs, j, gs, g.t32, g.La, g.Le, pp->npts, i0, sh, src);
+      geo_points<MP, PT>(Bs, j, gs, g.t32, g.La, g.Le, pp->npts, i0, sh, src, tab, ldt);
     }
     geo_drain(j, src, sh);
   }
@@ -322,6 +404,10 @@ cudaError_t launch_geo_tables(const uint8_t *plan_dev, const PlanHeader &h, uint
   if (h.ngeo_grids == 0) return cudaSuccess;
   const int bx = (h.geo_grid_points + 255) / 256;
   geo_table_batch_kernel<<<dim3(bx, h.ngeo_grids), 256, 0, s>>>(plan_dev, ws);
+  if (h.ngeo_steer > 0) {   // the shared steering tables read the FP64 sin / cos tables just written
+    const int sx = std::min(2 * num_sms(), (h.steer_max_ldt + 255) / 256);
+    geo_steer_kernel<<<dim3(sx, h.ngeo_steer), 256, 0, s>>>(plan_dev, ws);
+  }
   return cudaGetLastError();
 }
 

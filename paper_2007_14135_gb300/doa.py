@@ -347,7 +347,8 @@ class BatchPlan:
         """int32 index of a PlanHeader field (layout of csrc/doa_internal.cuh)."""
         order = {"magic": 0, "nprob": 1, "njobs": 2, "ngrids": 3, "ncov": 4, "nreduce": 5, "eig_count": 6,
                  "scan_jobs": 10, "scan_tiles": 14, "scan_pt": 22, "eig_mats": 58, "cov_first": 62, "tc_jobs": 67,
-                 "npolish": 74, "geo_jobs": 76, "ngeo_grids": 96, "nrefine": 100, "nroots": 101}
+                 "npolish": 74, "geo_jobs": 76, "ngeo_grids": 96, "nrefine": 100, "nroots": 101,
+                 "ngeo_steer": 104}
         return order[field]
 
     def launches(self) -> int:
@@ -359,7 +360,8 @@ class BatchPlan:
         scan_b = sum(int(c) > 0 for c in h[10:14]) + int(h[67] > 0) + sum(int(c) > 0 for c in h[76:80])
         ngeo = sum(int(c) for c in h[76:80])
         peaks = int(ngeo < int(h[1])) + int(ngeo > 0) + (2 if int(h[74]) > 0 else 0)
-        return int(h[3] > 0) + int(h[96] > 0) + cov + eig_b + scan_b + peaks + int(h[100] > 0) + int(h[101] > 0)
+        return (int(h[3] > 0) + int(h[96] > 0) + int(h[104] > 0) + cov + eig_b + scan_b + peaks + int(h[100] > 0)
+                + int(h[101] > 0))
 
 
 def doa_solve_batch(plan: BatchPlan, ws: torch.Tensor, status: torch.Tensor, stage_events=None,

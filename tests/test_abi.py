@@ -280,3 +280,45 @@ def test_batch_plan_optional_outputs(libdoa):
     bufp, wsp = plan_of([pol])
     assert wsp >= ws0 + 4 * 4 - 256 and bufp[:512].view(np.int64)[51] >= 0     # next_val_off
     assert buf0[:512].view(np.int64)[51] == -1
+
+
+def test_batch_plan_shared_steering_tables(libdoa):
+    """Geometry problems that pass the same positions pointer with the same grid and M share one FP32
+    steering table (float2[MP][ldt], ldt = La x Le rounded up to 1024) in the workspace; a problem
+    alone with its key gets none."""
+    import numpy as np
+
+    def gprob(M=8, La=360, Le=90, pos=0x20000):
+        p = _prob(libdoa, M=M, N=1024, d=2, mask=0xF, L=La, step=1.0)
+        p.grid = libdoa.grid(0.0, 1.0, La)
+        p.geom = libdoa.Geometry(pos, 1.0, 1.0, Le, 1)
+        return p
+
+    def plan_of(probs):
+        arr = (libdoa.Problem * len(probs))(*probs)
+        n = libdoa.lib().doa_batch_plan_bytes(arr, len(probs))
+        buf = np.zeros(n, np.uint8)
+        ws = ctypes.c_size_t(0)
+        assert libdoa.lib().doa_batch_plan(arr, len(probs), None, buf.ctypes.data, n, ctypes.byref(ws), None) == 0
+        return buf, ws.value
+
+    shared = [gprob(), gprob(), gprob(M=16), gprob(pos=0x30000), gprob(La=97, Le=13), gprob(La=97, Le=13)]
+    alone = [gprob(pos=0x20000 + 0x1000 * i) for i in range(4)] + [gprob(La=97, Le=13, pos=0x40000),
+                                                                    gprob(La=97, Le=13, pos=0x41000)]
+    alone[2] = gprob(M=16, pos=0x22000)
+    bs, wss = plan_of(shared)
+    ba, wsa = plan_of(alone)
+    hs, ha = bs[:512].view(np.int32), ba[:512].view(np.int32)
+    assert libdoa.BatchPlan.header_index("ngeo_steer") == 104
+    assert hs[104] == 2 and ha[104] == 0                  # (pos, 360 x 90, M=8) and (pos, 97 x 13, M=8)
+    assert hs[105] == 32768                                # largest row stride: 32 400 rounded up to 1024
+    assert wss - wsa == 8 * 8 * 32768 + 8 * 8 * 2048        # both tables, MP = 8 rows each
+    off = int(bs[:512].view(np.int64)[53])                 # off_geo_steer
+    ent = bs[off:off + 80]
+    assert int(ent[:8].view(np.int64)[0]) == 0x20000       # positions pointer
+    geo_grid, M, MP, npts, ldt = ent[8:28].view(np.int32)
+    assert (M, MP, npts, ldt) == (8, 8, 32400, 32768)
+    geo_grid2, M2, MP2, npts2, ldt2 = ent[48:68].view(np.int32)
+    assert (M2, MP2, npts2, ldt2) == (8, 8, 97 * 13, 2048) and geo_grid2 != geo_grid
+    tab0, tab1 = int(ent[32:40].view(np.int64)[0]), int(ent[72:80].view(np.int64)[0])
+    assert tab0 % 256 == 0 and tab1 >= tab0 + 8 * 8 * 32768

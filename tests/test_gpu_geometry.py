@@ -193,6 +193,43 @@ def test_batch_paper_uca(env):
         _check_geo(g, 0xF, t, worst)
 
 
+def test_batch_shared_array(env):
+    """Problems that pass one positions tensor share an FP32 steering table written once per solve
+    (360 x 90 and 360 x 1 grids, four algorithms); a problem with its own copy of the same array
+    evaluates its phasors in the scan. All spectra within 0.01 dB of the oracle, same 2-D peaks."""
+    torch, doa = env
+    insts = [synth.paper_uca(20 + i) for i in range(4)] + [synth.paper_uca(30 + i, Le=1) for i in range(2)]
+    posd = torch.from_numpy(np.ascontiguousarray(insts[0].pos)).cuda()
+    for g in insts:
+        assert np.array_equal(g.pos, insts[0].pos)
+    keep, probs = [], []
+    for g in insts:
+        npts = g.La * g.Le
+        X = torch.from_numpy(g.X).cuda()
+        P = torch.empty(4 * npts, dtype=torch.float32, device="cuda")
+        idx = torch.full((4 * g.d,), -1, dtype=torch.int32, device="cuda")
+        val = torch.zeros(4 * g.d, dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(4, dtype=torch.int32, device="cuda")
+        ev = torch.empty(g.M, dtype=torch.float64, device="cuda")
+        keep.append((X, P, idx, val, cnt, ev, posd))
+        geom = doa.geometry(posd, g.el_lo, g.el_step, g.Le, g.wrap_az)
+        probs.append(doa.make_problem(X, g.d, 0xF, doa.grid(g.az_lo, g.az_step, g.La), P, idx, val, cnt, ev,
+                                      geom=geom))
+    own, keep_own = synth.paper_uca(40), []
+    probs.insert(2, _geo_problem(torch, doa, own, 0xF, keep_own))
+    plan = doa.BatchPlan(probs)
+    assert int(plan.host[:512].view(np.int32)[doa.BatchPlan.header_index("ngeo_steer")]) == 2
+    ws = doa.workspace(plan)
+    status = torch.full((len(probs),), -1, dtype=torch.int32, device="cuda")
+    doa.doa_solve_batch(plan, ws, status)
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    worst = [0.0]
+    for g, t in zip(insts, keep):
+        _check_geo(g, 0xF, t, worst)
+    _check_geo(own, 0xF, keep_own[0], worst)
+
+
 def test_batch_mixed_geometry_and_ula(env):
     """Geometry problems of every M bucket next to ULA problems in one plan: both kinds match the
     oracle, so the two scan paths and the two peak rules coexist in the same launches."""
