@@ -346,7 +346,10 @@ typedef struct {
   int32_t flags;         /* DOA_FLAG_* bits                                                   */
   doa_geometry geom;     /* geom.pos == NULL: the 1-D ULA scan over `grid`. Otherwise a 2-D   */
                          /* scan, `grid` the azimuth columns: P holds nalg x (Le x La) floats, */
-                         /* peaks are flat indices, prec must be DOA_FP32 and flags 0          */
+                         /* peaks are flat indices, prec must be DOA_FP32 and flags 0.         */
+                         /* Problems that pass the same geom.pos pointer with the same grid    */
+                         /* and M share one FP32 steering table in the workspace (written once */
+                         /* per solve; pass one pointer for one physical array)                */
   double *peak_angle;    /* nullable: sub-grid refined peak angles in degrees (see            */
                          /* doa_refine_peaks): nalg x d (ULA) or nalg x d x 2 (geometry:       */
                          /* azimuth, elevation), entries past peak_count untouched             */
