@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
+#include <unordered_map>
 #include <vector>
 
 #include "doa_internal.cuh"
@@ -112,6 +114,17 @@ struct SteerKey {
 };
 constexpr int64_t kSteerMaxBytes = int64_t(1) << 28;
 
+struct SteerHash {
+  uintptr_t pos;
+  int geo_grid, M;
+  bool operator==(const SteerHash &o) const { return pos == o.pos && geo_grid == o.geo_grid && M == o.M; }
+  struct Hasher {
+    size_t operator()(const SteerHash &k) const {
+      return std::hash<uintptr_t>()(k.pos) ^ (std::hash<int64_t>()(((int64_t)k.geo_grid << 8) | k.M) * 0x9e3779b97f4a7c15ull);
+    }
+  };
+};
+
 int64_t steer_ldt(const GeoGridKey &g) { return round_up((int64_t)g.az.L * g.Le, kSteerAlign); }
 int steer_rows(int M) { return 8 << m_bucket(M); }
 
@@ -123,6 +136,7 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
   sz.nprob = nprob;
   grid_of.resize(nprob);
   steer_of.assign(nprob, -1);
+  std::unordered_map<SteerHash, int, SteerHash::Hasher> steer_index;
   for (int i = 0; i < nprob; ++i) {
     const doa_problem &p = probs[i];
     if (!problem_ok(p)) {
@@ -148,15 +162,16 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
         geo_grids.push_back(GeoGridKey{p.grid, p.geom.el_lo_deg, p.geom.el_step_deg, p.geom.Le});
       }
       grid_of[i] = g;
-      int st = -1;
-      for (size_t k = 0; k < steers.size(); ++k)
-        if (steers[k].pos == p.geom.pos && steers[k].geo_grid == g && steers[k].M == p.M) {
-          st = (int)k;
-          break;
-        }
-      if (st < 0) {
+      // (pointer, grid, M) -> key index; a hash map, since every problem may bring its own pointer
+      const SteerHash key{reinterpret_cast<uintptr_t>(p.geom.pos), g, p.M};
+      auto it = steer_index.find(key);
+      int st;
+      if (it == steer_index.end()) {
         st = (int)steers.size();
         steers.push_back(SteerKey{p.geom.pos, g, p.M, 0});
+        steer_index.emplace(key, st);
+      } else {
+        st = it->second;
       }
       ++steers[st].count;
       steer_of[i] = st;

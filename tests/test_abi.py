@@ -322,3 +322,30 @@ def test_batch_plan_shared_steering_tables(libdoa):
     assert (M2, MP2, npts2, ldt2) == (8, 8, 97 * 13, 2048) and geo_grid2 != geo_grid
     tab0, tab1 = int(ent[32:40].view(np.int64)[0]), int(ent[72:80].view(np.int64)[0])
     assert tab0 % 256 == 0 and tab1 >= tab0 + 8 * 8 * 32768
+
+
+def test_batch_plan_many_distinct_arrays(libdoa):
+    """40 000 geometry problems, each with its own positions pointer except two pairs: the plan
+    finds the two shared tables among all the keys, and planning stays fast (the key lookup is a
+    hash map, not a scan over the keys seen so far)."""
+    import time
+    import numpy as np
+
+    n = 40000
+    base = _prob(libdoa, M=8, N=256, d=2, mask=1 << 1, L=36, step=10.0)
+    base.grid = libdoa.grid(0.0, 10.0, 36)
+    arr = (libdoa.Problem * n)()
+    for i in range(n):
+        arr[i] = base
+        arr[i].geom = libdoa.Geometry(0x10000000 + 64 * i, 1.0, 10.0, 9, 1)
+    arr[7].geom = libdoa.Geometry(0x10000000 + 64 * 3, 1.0, 10.0, 9, 1)          # shares with problem 3
+    arr[n - 1].geom = libdoa.Geometry(0x10000000 + 64 * 100, 1.0, 10.0, 9, 1)    # shares with problem 100
+    t0 = time.perf_counter()
+    nb = libdoa.lib().doa_batch_plan_bytes(arr, n)
+    buf = np.zeros(nb, np.uint8)
+    ws = ctypes.c_size_t(0)
+    assert libdoa.lib().doa_batch_plan(arr, n, None, buf.ctypes.data, nb, ctypes.byref(ws), None) == 0
+    elapsed = time.perf_counter() - t0
+    h = buf[:512].view(np.int32)
+    assert h[104] == 2 and h[105] == 1024                 # two tables, 36 x 9 points rounded up to 1024
+    assert elapsed < 1.0, elapsed                          # ~15 ms measured; a key scan takes seconds
