@@ -87,12 +87,6 @@ struct PlanSizes {
   int ngeo_steer = 0;
 };
 
-
-bool same_grid(const doa_grid &a, const doa_grid &b) {
-  return a.L == b.L && std::memcmp(&a.lo_deg, &b.lo_deg, sizeof(double)) == 0 &&
-         std::memcmp(&a.step_deg, &b.step_deg, sizeof(double)) == 0;
-}
-
 // A geometry problem's azimuth x elevation grid (the key of its trigonometric tables).
 struct GeoGridKey {
   doa_grid az;
@@ -100,10 +94,33 @@ struct GeoGridKey {
   int32_t Le;
 };
 
-bool same_geo_grid(const GeoGridKey &a, const doa_problem &p) {
-  return same_grid(a.az, p.grid) && a.Le == p.geom.Le &&
-         std::memcmp(&a.el_lo, &p.geom.el_lo_deg, sizeof(double)) == 0 &&
-         std::memcmp(&a.el_step, &p.geom.el_step_deg, sizeof(double)) == 0;
+// Bit-exact key of a grid (azimuth or ULA grid, plus the elevation rows of a 2-D grid): two grids
+// share their tables only when every double matches bit for bit.
+struct GridHash {
+  uint64_t lo, step, el_lo, el_step;
+  int32_t L, Le;
+  bool operator==(const GridHash &o) const {
+    return lo == o.lo && step == o.step && el_lo == o.el_lo && el_step == o.el_step && L == o.L && Le == o.Le;
+  }
+  struct Hasher {
+    size_t operator()(const GridHash &k) const {
+      uint64_t h = 0x9e3779b97f4a7c15ull;
+      for (uint64_t v : {k.lo, k.step, k.el_lo, k.el_step, ((uint64_t)(uint32_t)k.L << 32) | (uint32_t)k.Le})
+        h = (h ^ v) * 0x100000001b3ull + (h >> 29);
+      return (size_t)h;
+    }
+  };
+};
+
+GridHash grid_hash(const doa_grid &g, double el_lo, double el_step, int32_t Le) {
+  GridHash k{};
+  std::memcpy(&k.lo, &g.lo_deg, 8);
+  std::memcpy(&k.step, &g.step_deg, 8);
+  std::memcpy(&k.el_lo, &el_lo, 8);
+  std::memcpy(&k.el_step, &el_step, 8);
+  k.L = g.L;
+  k.Le = Le;
+  return k;
 }
 
 // Geometry problems that pass the same positions pointer with the same grid and M share one FP32
@@ -137,6 +154,7 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
   grid_of.resize(nprob);
   steer_of.assign(nprob, -1);
   std::unordered_map<SteerHash, int, SteerHash::Hasher> steer_index;
+  std::unordered_map<GridHash, int, GridHash::Hasher> grid_index, geo_index;
   for (int i = 0; i < nprob; ++i) {
     const doa_problem &p = probs[i];
     if (!problem_ok(p)) {
@@ -151,15 +169,15 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
     sz.njobs += __builtin_popcount(p.alg_mask);
     if (p.geom.pos) {   // 2-D scan: trigonometric tables of its azimuth x elevation grid
       sz.geo[m_bucket(p.M)] += 1;
-      int g = -1;
-      for (size_t k = 0; k < geo_grids.size(); ++k)
-        if (same_geo_grid(geo_grids[k], p)) {
-          g = (int)k;
-          break;
-        }
-      if (g < 0) {
+      const GridHash gkey = grid_hash(p.grid, p.geom.el_lo_deg, p.geom.el_step_deg, p.geom.Le);
+      auto git = geo_index.find(gkey);
+      int g;
+      if (git == geo_index.end()) {
         g = (int)geo_grids.size();
         geo_grids.push_back(GeoGridKey{p.grid, p.geom.el_lo_deg, p.geom.el_step_deg, p.geom.Le});
+        geo_index.emplace(gkey, g);
+      } else {
+        g = git->second;
       }
       grid_of[i] = g;
       // (pointer, grid, M) -> key index; a hash map, since every problem may bring its own pointer
@@ -181,15 +199,15 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
       sz.scan[m_bucket(p.M)] += 1;
     else
       sz.tc += 1;
-    int g = -1;
-    for (size_t k = 0; k < grids.size(); ++k)
-      if (same_grid(grids[k], p.grid)) {
-        g = (int)k;
-        break;
-      }
-    if (g < 0) {
+    const GridHash ukey = grid_hash(p.grid, 0.0, 0.0, 0);
+    auto uit = grid_index.find(ukey);
+    int g;
+    if (uit == grid_index.end()) {
       g = (int)grids.size();
       grids.push_back(p.grid);
+      grid_index.emplace(ukey, g);
+    } else {
+      g = uit->second;
     }
     grid_of[i] = g;
   }
