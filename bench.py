@@ -1183,9 +1183,11 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Eq. 1 ULA snapshots, Philox)",
-        "config": {"workload": workload_name(S) + " (oracle sample per step)", "batch_per_gpu": S},
+        "config": {"workload": workload_name(args.batch), "batch_per_gpu": args.batch, "M": M, "d": D,
+                   "N": N_SNAP, "L": L, "algorithms": ["PHD", "MUSIC", "EV", "MN"],
+                   "parallelism": "oracle on host cores (rank 0)"},
         "cpu_baseline": {"value": value, "unit": "points/s", "cores": workers, "kind": "oracle",
-                         "sample": f"{S} problems x 4 algorithms per step"},
+                         "sample": f"each step: the first {S} of the {args.batch} problems x 4 algorithms"},
         "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(result), flush=True)
