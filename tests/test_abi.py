@@ -349,3 +349,19 @@ def test_batch_plan_many_distinct_arrays(libdoa):
     h = buf[:512].view(np.int32)
     assert h[104] == 2 and h[105] == 1024                 # two tables, 36 x 9 points rounded up to 1024
     assert elapsed < 1.0, elapsed                          # ~15 ms measured; a key scan takes seconds
+
+
+def test_binding_has_no_host_fallback(libdoa):
+    """Host tensors are refused before any call reaches the library: the stages run only in the CUDA
+    kernels, and there is no CPU path to fall back to."""
+    import torch
+    X = torch.zeros(4, 16, dtype=torch.complex64)
+    R = torch.zeros(4, 4, dtype=torch.complex128)
+    P = torch.zeros(181, dtype=torch.float32)
+    idx = torch.zeros(2, dtype=torch.int32)
+    val = torch.zeros(2, dtype=torch.float32)
+    cnt = torch.zeros(1, dtype=torch.int32)
+    with pytest.raises(ValueError):
+        libdoa.doa_covariance(X, R64=R)
+    with pytest.raises(ValueError):
+        libdoa.doa_peaks(P, 2, idx, val, cnt)
