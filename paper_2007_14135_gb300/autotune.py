@@ -38,18 +38,31 @@ def _bucket(M: int) -> int:
     return 0 if M <= 8 else (1 if M <= 16 else (2 if M <= 32 else 3))
 
 
-def _keys(problems: Sequence[doa.Problem], device) -> Dict[int, str]:
+def _keys(problems: Sequence[doa.Problem], device, gpu_name: Optional[str] = None) -> Dict[int, str]:
     """Cache key per occupied bucket: GPU, bucket, decades of the problem count and of the mean
-    points x algorithms per problem, and the scan kind (ULA, 2-D geometry, or both)."""
-    name = torch.cuda.get_device_name(device).replace(" ", "_")
+    points x algorithms per problem, and the scan kind (ULA, 2-D geometry evaluating its own
+    phasors, 2-D geometry reading a steering table shared with other problems, or a mix)."""
+    name = (gpu_name or torch.cuda.get_device_name(device)).replace(" ", "_")
     Ls: Dict[int, List[int]] = {}
     kinds: Dict[int, set] = {}
+    # the plan shares a steering table among problems with one positions pointer, grid and M
+    def tab_key(p):
+        return (int(p.geom.pos), p.grid.lo_deg, p.grid.step_deg, int(p.grid.L), p.geom.el_lo_deg,
+                p.geom.el_step_deg, int(p.geom.Le), int(p.M))
+
+    uses: Dict[tuple, int] = {}
+    for p in problems:
+        if p.geom.pos:
+            uses[tab_key(p)] = uses.get(tab_key(p), 0) + 1
     for p in problems:
         b = _bucket(p.M)
         geo = bool(p.geom.pos)
         pts = int(p.grid.L) * (int(p.geom.Le) if geo else 1)
         Ls.setdefault(b, []).append(pts * bin(int(p.alg_mask)).count("1"))
-        kinds.setdefault(b, set()).add("geo" if geo else "ula")
+        if geo:
+            kinds.setdefault(b, set()).add("geotab" if uses[tab_key(p)] >= 2 else "geo")
+        else:
+            kinds.setdefault(b, set()).add("ula")
     return {b: f"{name}|M{b}|n1e{int(round(math.log10(len(v))))}|L1e{int(round(math.log10(max(1.0, sum(v) / len(v)))))}"
                f"|{'+'.join(sorted(kinds[b]))}"
             for b, v in Ls.items()}
