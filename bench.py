@@ -1085,6 +1085,9 @@ def run_uca(args):
         "config": {"workload": f"paper-uca batch: {B} problems, 8-element UCA r=10 m at 15 MHz, d=2, SNR 15 dB, "
                                f"N=1024, MUSIC, azimuth 0:1:359 x elevation {91 - Le}:1:90 ({npts} points)",
                    "batch_per_gpu": B, "graph": True, "scan_pt": bt["plan"].scan_pt, "eig_mats": bt["plan"].eig_mats,
+                   "steering_tables": int(bt["plan"].host[:512].view(np.int32)[doa.BatchPlan.header_index("ngeo_steer")]),
+                   "steering": "one FP32 table per (array, grid, M), written each step from FP64 phases, shared by "
+                               "the problems that pass the same positions",
                    "l2": f"inputs {Xh.nbytes / 1e9:.2f} GB > 129 MB L2 (no flush needed)",
                    "parallelism": f"replicas x{world}"},
         "solves_per_s": B * world / (ms / 1e3),
