@@ -20,6 +20,8 @@ compiles it with gcc on first use and exposes NumPy-friendly wrappers:
   refine_peak / refine_peak2d
               -- sub-grid refinement of a picked peak: the local minimiser of a^H C a next to it
   model_order -- MDL / AIC source-count estimates from the eigenvalues (Wax & Kailath)
+  svd_data    -- Step-2 as an SVD of the snapshot matrix X itself (one-sided Jacobi on its rows):
+                 the eigenpairs of R = X X^H / N without forming R
   root_polynomial / root_music
               -- the ULA scan's denominator as a polynomial on the unit circle and its roots
                  (numpy.roots as the root finder)
@@ -85,6 +87,8 @@ def _load():
             lib.oracle_refine_peak2d.restype = None
             lib.oracle_model_order.argtypes = [p, i, i, p, p, p, p]
             lib.oracle_model_order.restype = None
+            lib.oracle_svd_data.argtypes = [p, i, i, i, d, i, p, p]
+            lib.oracle_svd_data.restype = i
             _lib = lib
     return _lib
 
@@ -290,3 +294,17 @@ def root_music(C: np.ndarray, d: int):
     ang = np.degrees(np.arcsin(np.clip(np.angle(pick) / np.pi, -1.0, 1.0)))
     o = np.argsort(ang)
     return ang[o], pick[o]
+
+
+def svd_data(X: np.ndarray, tol: float = 1e-15, max_sweeps: int = 100):
+    """One-sided Jacobi SVD of the M x N snapshot matrix X (complex64 or complex128; complex64 is
+    promoted exactly). Returns (evals, U, sweeps) in the form of eigh: the eigenvalues S_k^2 / N of
+    R = X X^H / N descending, U with the left singular vectors as columns, and the sweep count
+    (negative: the sweep cap was reached)."""
+    X = np.ascontiguousarray(X, dtype=np.complex128)
+    assert X.ndim == 2
+    M, N = X.shape
+    ev = np.empty(M, dtype=np.float64)
+    Ut = np.empty((M, M), dtype=np.complex128)   # row i = singular vector i (column-major U)
+    sweeps = _load().oracle_svd_data(_ptr(X), M, N, N, tol, max_sweeps, _ptr(ev), _ptr(Ut))
+    return ev, Ut.T.copy(), sweeps

@@ -15,6 +15,7 @@
  *   Step-4  weighting matrix C (explicit M x M)    Table 3 (Step-4 rows)
  *   Step-5  pseudospectrum P = 1 / (a^H C a)       Table 2 Step-5, steering vector Eq. 2
  *   Step-6  peak finding and selection of D peaks  Table 2 Step-6
+ *   Step-2 as an SVD of X itself (one-sided Jacobi on its rows, R never formed): oracle_svd_data
  *
  * Readings where the paper is silent (each one is listed in the design notes):
  *   - steering vector: Eq. 2 for a uniform linear array on the x axis with half-wavelength
@@ -705,4 +706,99 @@ void oracle_model_order(const double *evals, int M, int N, int *mdl, int *aic, d
   }
   *mdl = best_m;
   *aic = best_a;
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Step-2 taken as an SVD of the data (the paper computes Step-2 as an SVD; here of X itself, not
+ * of R): one-sided Jacobi (Hestenes 1958) on the M rows of X. Rows y_p, y_q of Y (initially X)
+ * are rotated, Y <- J^H Y and U <- U J, with the Hermitian Jacobi rotation of oracle_eigh built
+ * from the Gram entries alpha = ||y_p||^2, beta = ||y_q||^2, gamma = y_p y_q^H, each recomputed
+ * from the rows in FP64 (R is never formed). Pairs row by row; a pair is rotated when
+ * |gamma| > tol * sqrt(alpha beta) (and gamma != 0); the iteration stops after the first sweep
+ * that rotates nothing. Then X = U S V^H with S_k = ||y_k||, and the eigenvalues of R = X X^H / N
+ * (Eq. 3) are S_k^2 / N with eigenvectors the columns of U.
+ *
+ * X: M x N complex128, row-major, interleaved, row stride ldx complex elements (callers with
+ * complex64 snapshots promote them exactly). Output as oracle_eigh: evals[M] descending (stable),
+ * U column-major interleaved. Returns the number of sweeps, or -ORACLE_ENOCONV.
+ * ------------------------------------------------------------------------------------------- */
+int oracle_svd_data(const double *X, int M, int N, int ldx, double tol, int max_sweeps, double *evals, double *U) {
+  double complex *Y = (double complex *)malloc(sizeof(double complex) * (size_t)M * N);
+  double complex *W = (double complex *)malloc(sizeof(double complex) * M * M);
+  for (int i = 0; i < M; ++i) {
+    for (int t = 0; t < N; ++t)
+      Y[(size_t)i * N + t] = X[2 * ((size_t)i * ldx + t)] + I * X[2 * ((size_t)i * ldx + t) + 1];
+    for (int j = 0; j < M; ++j) W[i * M + j] = (i == j) ? 1.0 : 0.0; /* row-major: W[i*M+j] = U(i,j) */
+  }
+  int sweeps = 0, converged = 0;
+  while (sweeps < max_sweeps) {
+    ++sweeps;
+    int rotations = 0;
+    for (int p = 0; p < M - 1; ++p) {
+      for (int q = p + 1; q < M; ++q) {
+        const double complex *yp = Y + (size_t)p * N, *yq = Y + (size_t)q * N;
+        double alpha = 0.0, beta = 0.0;
+        double complex gamma = 0.0;
+        for (int t = 0; t < N; ++t) {
+          alpha += creal(yp[t] * conj(yp[t]));
+          beta += creal(yq[t] * conj(yq[t]));
+          gamma += yp[t] * conj(yq[t]);
+        }
+        double mag = cabs(gamma);
+        if (mag == 0.0 || mag <= tol * sqrt(alpha * beta)) continue;
+        ++rotations;
+        double complex ph = gamma / mag;
+        double tau = (beta - alpha) / (2.0 * mag);
+        double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        double c = 1.0 / sqrt(1.0 + tt * tt);
+        double s = tt * c;
+        /* Y <- J^H Y : rows p and q */
+        for (int t = 0; t < N; ++t) {
+          double complex xp = Y[(size_t)p * N + t], xq = Y[(size_t)q * N + t];
+          Y[(size_t)p * N + t] = c * xp - s * ph * xq;
+          Y[(size_t)q * N + t] = s * conj(ph) * xp + c * xq;
+        }
+        /* U <- U J : columns p and q */
+        for (int r = 0; r < M; ++r) {
+          double complex xp = W[r * M + p], xq = W[r * M + q];
+          W[r * M + p] = c * xp - s * conj(ph) * xq;
+          W[r * M + q] = s * ph * xp + c * xq;
+        }
+      }
+    }
+    if (rotations == 0) {
+      converged = 1;
+      break;
+    }
+  }
+  double *nrm = (double *)malloc(sizeof(double) * M);
+  for (int i = 0; i < M; ++i) {
+    double a = 0.0;
+    for (int t = 0; t < N; ++t) a += creal(Y[(size_t)i * N + t] * conj(Y[(size_t)i * N + t]));
+    nrm[i] = a / (double)N;
+  }
+  int *order = (int *)malloc(sizeof(int) * M);
+  for (int i = 0; i < M; ++i) order[i] = i;
+  for (int i = 1; i < M; ++i) {
+    int cur = order[i];
+    int j = i - 1;
+    while (j >= 0 && nrm[order[j]] < nrm[cur]) {
+      order[j + 1] = order[j];
+      --j;
+    }
+    order[j + 1] = cur;
+  }
+  for (int i = 0; i < M; ++i) {
+    int src = order[i];
+    evals[i] = nrm[src];
+    for (int r = 0; r < M; ++r) {
+      U[2 * (i * M + r)] = creal(W[r * M + src]);
+      U[2 * (i * M + r) + 1] = cimag(W[r * M + src]);
+    }
+  }
+  free(order);
+  free(nrm);
+  free(W);
+  free(Y);
+  return converged ? sweeps : -ORACLE_ENOCONV;
 }
