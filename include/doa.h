@@ -368,6 +368,15 @@ typedef struct {
  * weakest selected peak from its best unselected one) is left as computed. */
 #define DOA_FLAG_POLISH_PEAKS 1
 
+/* Covariance arithmetic of a batch problem. Problems with M <= 16, a 16-byte aligned X, an even
+ * ldx and N <= 2^21 compute R on the tensor cores by default: every sample is scaled by one power
+ * of two and cut into six 7-bit slices (exact in BF16), every slice product and every window of
+ * 960 snapshots of their sums is exact in the FP32 accumulators, and the windows are added in
+ * 64-bit integers, so R is exact to about 2^-40 of the largest sample magnitude squared and does
+ * not depend on the order of the additions. This flag selects the compensated CUDA-core
+ * accumulation instead (the form every other problem uses). */
+#define DOA_FLAG_COV_CUDA_CORE 2
+
 /* Launch-shape knobs of a plan, per M bucket (M <= 8, <= 16, <= 32, <= 64); 0 = default. */
 typedef struct {
   int32_t scan_pt[4];    /* grid points per scan thread (tile = 128 threads x scan_pt points).  */
@@ -376,6 +385,10 @@ typedef struct {
   int32_t eig_mats[4];   /* matrices per Jacobi warp. Allowed {1, 2, 4, 8}, {1, 2, 4}, {1, 2},   */
                          /* {1} (a lane per rotation pair); default: 1 unless the bucket holds   */
                          /* enough problems to keep ~24 packed warps per SM busy.               */
+  int32_t scan_group[4]; /* FP32 ULA problems that share a grid are scanned together in groups  */
+                         /* of this many (one steering generation per tile of the grid for the   */
+                         /* whole group, each problem's factor contracted in turn); 1 scans every */
+                         /* problem alone. Allowed powers of two 1..64; default 32.              */
 } doa_tuning;
 
 /*

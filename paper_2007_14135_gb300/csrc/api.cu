@@ -59,18 +59,26 @@ bool problem_ok(const doa_problem &p) {
   if (!p.X || !aligned(p.X, 8) || !p.P || !aligned(p.P, 4)) return false;
   if (p.alg_mask == 0u || p.alg_mask > 15u) return false;
   if (p.eig_prec != DOA_EIG_DOUBLE_FLOAT && p.eig_prec != DOA_EIG_FP64) return false;
-  if (p.flags & ~DOA_FLAG_POLISH_PEAKS) return false;
+  if (p.flags & ~(DOA_FLAG_POLISH_PEAKS | DOA_FLAG_COV_CUDA_CORE)) return false;
   if (p.d > 0 && (!p.peak_idx || !p.peak_val)) return false;
   if (p.peak_angle && !aligned(p.peak_angle, 8)) return false;
   if (p.order_est && !aligned(p.order_est, 4)) return false;
   if (p.root_angle && (!aligned(p.root_angle, 8) || p.geom.pos || p.d < 1)) return false;
   if (!p.peak_count) return false;
   if (p.geom.pos)   // 2-D scan: FP32 on CUDA cores, no peak polish
-    return p.prec == DOA_FP32 && p.flags == 0 && geometry_ok(p.grid, p.geom);
+    return p.prec == DOA_FP32 && (p.flags & DOA_FLAG_POLISH_PEAKS) == 0 && geometry_ok(p.grid, p.geom);
   // scan form: FP32 (CUDA cores) or split operands on the tensor cores (M <= 32)
   if (p.prec != DOA_FP32 && !((p.prec == DOA_BF16X3 || p.prec == DOA_FP16X3) && p.M <= kTcBatchMaxM)) return false;
   return grid_ok(p.grid);
 }
+
+// Covariance on the tensor cores (exact BF16 slices, covariance_tc_batch.cu): M <= 16, whole-row
+// bulk copies (16-byte aligned X, even row stride), N within the range of its 64-bit sums.
+bool cov_tc_ok(const doa_problem &p) {
+  return p.M <= kCovTcMaxM && !(p.flags & DOA_FLAG_COV_CUDA_CORE) && aligned(p.X, 16) && (p.ldx & 1) == 0 &&
+         p.N <= kCovTcMaxN;
+}
+int cov_tc_class(int M) { return M <= 8 ? 0 : 1; }
 
 int64_t spectrum_points(const doa_problem &p) {
   return p.geom.pos ? (int64_t)p.grid.L * p.geom.Le : (int64_t)p.grid.L;
@@ -79,6 +87,7 @@ int64_t spectrum_points(const doa_problem &p) {
 struct PlanSizes {
   int nprob = 0, njobs = 0, ngrids = 0, ncov = 0, nreduce = 0;
   int cov_class[kCovClasses] = {0, 0, 0, 0};
+  int covtc[2] = {0, 0};
   int tc = 0;
   int eig[kNumBuckets] = {0, 0, 0, 0};
   int scan[kNumBuckets] = {0, 0, 0, 0};
@@ -161,10 +170,14 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
       if (bad_index) *bad_index = i;
       return false;
     }
-    int chunks = (p.N + kCovChunk - 1) / kCovChunk;
-    sz.ncov += chunks;
-    sz.cov_class[cov_class(p.M)] += chunks;
-    sz.nreduce += chunks > 1;
+    if (cov_tc_ok(p)) {
+      sz.covtc[cov_tc_class(p.M)] += 1;
+    } else {
+      int chunks = (p.N + kCovChunk - 1) / kCovChunk;
+      sz.ncov += chunks;
+      sz.cov_class[cov_class(p.M)] += chunks;
+      sz.nreduce += chunks > 1;
+    }
     sz.eig[m_bucket(p.M)] += 1;
     sz.njobs += __builtin_popcount(p.alg_mask);
     if (p.geom.pos) {   // 2-D scan: trigonometric tables of its azimuth x elevation grid
@@ -233,7 +246,7 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
 
 struct PlanOffsets {
   int64_t prob, job, grid, cov, reduce, eig[kNumBuckets], scan[kNumBuckets], tc, geo[kNumBuckets], geo_grid,
-      geo_steer, total;
+      geo_steer, covtc[2], sg[kNumBuckets], sgl[kNumBuckets], total;
 };
 
 PlanOffsets plan_offsets(const PlanSizes &sz) {
@@ -267,6 +280,18 @@ PlanOffsets plan_offsets(const PlanSizes &sz) {
   at = round_up(at + (int64_t)sz.ngeo_grids * sizeof(PlanGeoGrid), 16);
   o.geo_steer = at;
   at = round_up(at + (int64_t)sz.ngeo_steer * sizeof(PlanGeoSteer), 16);
+  for (int c = 0; c < 2; ++c) {
+    o.covtc[c] = at;
+    at = round_up(at + (int64_t)sz.covtc[c] * 4, 16);
+  }
+  // grid-shared scan groups and lists: room for every FP32 ULA problem of the bucket (the grouping
+  // depends on the tuning, the plan size must not)
+  for (int b = 0; b < kNumBuckets; ++b) {
+    o.sg[b] = at;
+    at = round_up(at + (int64_t)sz.scan[b] * sizeof(PlanScanGroup), 16);
+    o.sgl[b] = at;
+    at = round_up(at + (int64_t)sz.scan[b] * 4, 16);
+  }
   o.total = at;
   return o;
 }
@@ -464,6 +489,7 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     pt[b] = (tuning && tuning->scan_pt[b] != 0) ? tuning->scan_pt[b] : scan_pt_default(b);
     if (!scan_pt_allowed(b, pt[b])) return DOA_EINVAL;
     if (tuning && tuning->eig_mats[b] != 0 && !eig_mats_allowed(b, tuning->eig_mats[b])) return DOA_EINVAL;
+    if (tuning && tuning->scan_group[b] != 0 && !scan_group_allowed(tuning->scan_group[b])) return DOA_EINVAL;
   }
   PlanSizes sz;
   std::vector<doa_grid> grids;
@@ -558,6 +584,16 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     ws = round_up(ws + 8 * (int64_t)e.MP * e.ldt, 256);
     h.steer_max_ldt = std::max(h.steer_max_ldt, e.ldt);
   }
+  // tensor-core covariance lists and their per-problem marks in the workspace
+  int32_t *covtc[2];
+  int icovtc[2] = {0, 0};
+  for (int c = 0; c < 2; ++c) {
+    covtc[c] = reinterpret_cast<int32_t *>(base + o.covtc[c]);
+    h.off_covtc[c] = o.covtc[c];
+    h.ncovtc[c] = sz.covtc[c];
+  }
+  h.covtc_flag_off = ws;
+  ws = round_up(ws + 4 * (int64_t)(sz.covtc[0] + sz.covtc[1]), 256);
   int icov[kCovClasses], ired = 0, ijob = 0;
   h.cov_first[0] = 0;
   for (int c = 0; c < kCovClasses; ++c) {
@@ -566,6 +602,21 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
   }
   int ie[kNumBuckets] = {0, 0, 0, 0}, is[kNumBuckets] = {0, 0, 0, 0};
   int64_t tiles[kNumBuckets] = {0, 0, 0, 0};
+  // grid-shared scan: FP32 ULA problems of a bucket whose grid at least one other such problem
+  // shares go to groups of sg_size[b]; sharers[g * kNumBuckets + b] lists them in problem order
+  int sgsize[kNumBuckets];
+  for (int b = 0; b < kNumBuckets; ++b) {
+    sgsize[b] = (tuning && tuning->scan_group[b] != 0) ? tuning->scan_group[b] : kScanGroupDefault;
+    h.sg_size[b] = sgsize[b];
+  }
+  auto ula_fp32 = [](const doa_problem &p) { return !p.geom.pos && p.prec == DOA_FP32; };
+  std::vector<std::vector<int32_t>> sharers((size_t)sz.ngrids * kNumBuckets);
+  for (int i = 0; i < nprob; ++i)
+    if (ula_fp32(probs[i])) sharers[(size_t)grid_of[i] * kNumBuckets + m_bucket(probs[i].M)].push_back(i);
+  auto grouped = [&](int i) {
+    const int b = m_bucket(probs[i].M);
+    return ula_fp32(probs[i]) && sgsize[b] > 1 && sharers[(size_t)grid_of[i] * kNumBuckets + b].size() >= 2;
+  };
   for (int i = 0; i < nprob; ++i) {
     const doa_problem &p = probs[i];
     PlanProblem &q = pp[i];
@@ -575,13 +626,18 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     q.r64_off = ws;
     ws = round_up(ws + mm, 256);
     q.npts = (int32_t)spectrum_points(p);
-    q.nchunks = (p.N + kCovChunk - 1) / kCovChunk;
     q.part_off = ws;
-    if (q.nchunks > 1) {
-      ws = round_up(ws + mm * q.nchunks, 256);
-      reduce[ired++] = i;
+    if (cov_tc_ok(p)) {
+      q.nchunks = 0;
+      covtc[cov_tc_class(M)][icovtc[cov_tc_class(M)]++] = i;
+    } else {
+      q.nchunks = (p.N + kCovChunk - 1) / kCovChunk;
+      if (q.nchunks > 1) {
+        ws = round_up(ws + mm * q.nchunks, 256);
+        reduce[ired++] = i;
+      }
+      for (int c = 0; c < q.nchunks; ++c) cov[icov[cov_class(M)]++] = PlanCovItem{i, c};
     }
-    for (int c = 0; c < q.nchunks; ++c) cov[icov[cov_class(M)]++] = PlanCovItem{i, c};
     eig[b][ie[b]++] = i;
     q.grid_id = p.geom.pos ? -1 : grid_of[i];
     q.geo_grid = p.geom.pos ? grid_of[i] : -1;
@@ -608,6 +664,8 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
       q.tile_start = h.geo_tiles[b];
       h.geo_tiles[b] += (q.npts + tp - 1) / tp;
       geo[b][h.geo_jobs[b]++] = i;
+    } else if (grouped(i)) {
+      q.tile_start = 0;   // scanned by its group (grid-shared scan)
     } else if (p.prec == DOA_FP32) {
       const int tp = kScanThreads * pt[b];
       q.tile_start = tiles[b];
@@ -620,11 +678,36 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
       h.tc_cols = std::max(h.tc_cols, tc_batch_cols(q.Kf));
     }
   }
+  // longest problems first, so the static round-robin over SMs ends evenly (stable: equal N keep order)
+  for (int c = 0; c < 2; ++c)
+    std::stable_sort(covtc[c], covtc[c] + sz.covtc[c], [&](int32_t a, int32_t b) { return probs[a].N > probs[b].N; });
   for (int b = 0; b < kNumBuckets; ++b) {
     h.eig_mats[b] = (tuning && tuning->eig_mats[b] != 0) ? tuning->eig_mats[b] : eig_mats_default(b, sz.eig[b]);
     h.eig_count[b] = sz.eig[b];
-    h.scan_jobs[b] = sz.scan[b];
+    h.scan_jobs[b] = is[b];
     h.scan_tiles[b] = tiles[b];
+  }
+  // the groups, grid by grid, sg_size problems each (the last one of a grid may be smaller)
+  for (int b = 0; b < kNumBuckets; ++b) {
+    PlanScanGroup *grp = reinterpret_cast<PlanScanGroup *>(base + o.sg[b]);
+    int32_t *sgl = reinterpret_cast<int32_t *>(base + o.sgl[b]);
+    h.off_sg[b] = o.sg[b];
+    h.off_sgl[b] = o.sgl[b];
+    const int tp = kScanThreads * pt[b];
+    for (int g = 0; g < sz.ngrids; ++g) {
+      const std::vector<int32_t> &v = sharers[(size_t)g * kNumBuckets + b];
+      if (sgsize[b] <= 1 || v.size() < 2) continue;
+      for (size_t f = 0; f < v.size(); f += (size_t)sgsize[b]) {
+        PlanScanGroup &e = grp[h.sg_groups[b]++];
+        e.grid_id = g;
+        e.first = h.sg_probs[b];
+        e.count = (int32_t)std::min<size_t>((size_t)sgsize[b], v.size() - f);
+        e.tiles = (grids[g].L + tp - 1) / tp;
+        e.unit_start = h.sg_units[b];
+        h.sg_units[b] += e.tiles;
+        for (int q = 0; q < e.count; ++q) sgl[h.sg_probs[b]++] = v[f + q];
+      }
+    }
   }
   h.next_val_off = -1;
   if (h.npolish > 0) {   // the polish reads, per job, the best peak value below the selection

@@ -544,17 +544,62 @@ __global__ void covariance_reduce_batch(const uint8_t *plan, uint8_t *ws) {
   }
 }
 
+// Batch fixup of the tensor-core covariance (covariance_tc_batch.cu): a listed problem that kernel
+// marked (a sample beyond its scaling range, non-finite data, a bounded wait that ran out) is
+// recomputed here with the compensated accumulation, one CTA per problem, chunk by chunk, the chunk
+// sums added in FP64 in chunk order. Unmarked problems cost one flag read.
+constexpr int kFixupSlots = 160;   // output slots of M <= 16 (10 blocks of 4 x 4)
+
+__global__ void __launch_bounds__(kCovThreads) covariance_fixup_kernel(const uint8_t *plan, uint8_t *ws) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ double2 acc[kFixupSlots];
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
+  const int n0 = h->ncovtc[0], total = n0 + h->ncovtc[1];
+  const int32_t *flags = reinterpret_cast<const int32_t *>(ws + h->covtc_flag_off);
+  for (int f = blockIdx.x; f < total; f += gridDim.x) {
+    if (flags[f] == 0) continue;
+    const int prob = f < n0 ? reinterpret_cast<const int32_t *>(plan + h->off_covtc[0])[f]
+                            : reinterpret_cast<const int32_t *>(plan + h->off_covtc[1])[f - n0];
+    const PlanProblem &pp = reinterpret_cast<const PlanProblem *>(plan + h->off_prob)[prob];
+    const int M = pp.p.M, N = pp.p.N;
+    const float2 *X = reinterpret_cast<const float2 *>(pp.p.X);
+    CovLayout lay(M);
+    for (int e = threadIdx.x; e < lay.nout(); e += kCovThreads) acc[e] = make_double2(0.0, 0.0);
+    for (int t0 = 0; t0 < N; t0 += kCovChunk) {
+      const float4 *part = cov_accumulate<true>(X, pp.p.ldx, t0, min(N, t0 + kCovChunk), lay, smem);
+      for (int e = threadIdx.x; e < lay.nout(); e += kCovThreads) {
+        const double2 v = slot_value(part[e]);
+        acc[e].x += v.x;
+        acc[e].y += v.y;
+      }
+    }
+    double2 *R64 = reinterpret_cast<double2 *>(ws + pp.r64_off);
+    const double inv_n = 1.0 / (double)N;
+    for (int e = threadIdx.x; e < lay.nout(); e += kCovThreads) {
+      int row, col;
+      if (slot_rc(lay, e, row, col)) store_r(M, row, col, acc[e], inv_n, nullptr, R64);
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_covariance_fixup(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s) {
+  const int total = h.ncovtc[0] + h.ncovtc[1];
+  if (total == 0) return cudaSuccess;
+  static_assert(kCovTcMaxM <= 16, "fixup slots cover M <= 16");
+  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void *>(covariance_fixup_kernel), kSmemBytes);
+  if (e != cudaSuccess) return e;
+  const int grid = total < 2 * device_sm_count() ? total : 2 * device_sm_count();
+  covariance_fixup_kernel<<<grid, kCovThreads, kSmemBytes, s>>>(plan_dev, ws);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_covariance_single(const float2 *X, int M, int N, int ldx, float2 *R, double2 *R64,
                                      cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(covariance_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void *>(covariance_cluster_kernel), kSmemBytes);
+  if (e != cudaSuccess) return e;
   int chunks = (N + kCovChunk - 1) / kCovChunk;
   int nc = chunks < kMaxCluster ? chunks : kMaxCluster;
   int per = (N + nc - 1) / nc;
@@ -576,13 +621,8 @@ cudaError_t launch_covariance_single(const float2 *X, int M, int N, int ldx, flo
 template <int MB, int kKind>
 cudaError_t launch_tasks_kind(const uint8_t *plan_dev, int first, int n, uint8_t *ws, cudaStream_t s) {
   using K = CovKind<MB, kKind>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(covariance_tasks_kernel<MB, kKind>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, K::kSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void *>(covariance_tasks_kernel<MB, kKind>), K::kSmem);
+  if (e != cudaSuccess) return e;
   covariance_tasks_kernel<MB, kKind><<<n, K::kThreads, K::kSmem, s>>>(plan_dev, ws, first);
   return cudaGetLastError();
 }
@@ -598,14 +638,8 @@ cudaError_t launch_tasks(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *
 
 cudaError_t launch_covariance_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws,
                                     cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(covariance_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  cudaError_t e;
+  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void *>(covariance_batch_kernel), kSmemBytes);
+  if (e != cudaSuccess) return e;
   if ((e = launch_tasks<2>(plan_dev, h, ws, s)) != cudaSuccess) return e;
   if ((e = launch_tasks<3>(plan_dev, h, ws, s)) != cudaSuccess) return e;
   if ((e = launch_tasks<4>(plan_dev, h, ws, s)) != cudaSuccess) return e;
@@ -613,7 +647,10 @@ cudaError_t launch_covariance_batch(const uint8_t *plan_dev, const PlanHeader &h
   if (ngen > 0)
     covariance_batch_kernel<<<ngen, kCovThreads, kSmemBytes, s>>>(plan_dev, ws, h.cov_first[kCovClasses - 1]);
   if (h.nreduce > 0) covariance_reduce_batch<<<h.nreduce, 256, 0, s>>>(plan_dev, ws);
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // problems with M <= 16: tensor cores, then the recomputation of any it marked
+  if ((e = launch_covariance_tc_batch(plan_dev, h, ws, s)) != cudaSuccess) return e;
+  return launch_covariance_fixup(plan_dev, h, ws, s);
 }
 
 }  // namespace doa

@@ -1,0 +1,607 @@
+// Step-1 of the batch (Sec. 3.1, Eq. 3) on the tensor cores: R = X X^H / N for every problem with
+// M <= 16, exact to about 2^-40 of the largest snapshot magnitude squared.
+//
+// Exact slices. A problem's samples are scaled by one power of two (from the first stage's largest
+// |component|, with one bit of headroom) so that |w| <= 64, and each w is cut into six slices
+//     w = s_0 + s_1 + ... + s_5 + r,   s_k = n_k 2^(-7k), n_k integer, |n_k| <= 64, |r| <= 2^-36,
+// by rounding to the nearest multiple of 2^(-7k) (one FP32 add and subtract of 1.5 * 2^(23-7k)).
+// Every slice is exact in BF16, every slice product exact in FP32, and a window of 960 snapshots
+// sums fewer than 960 * 64 * 64 < 2^22 units of 2^(-7(i+j)), so the tensor core's FP32 accumulator
+// holds the exact integer sum of slice pair (i, j) over the window. The pairs with i + j <= 5 are
+// kept (the dropped ones and r are below 2^-40 of the largest product).
+//
+// Planar GEMM. Slice k of a problem is a block of 2 MP operand rows (Re plane: elements 0..MP-1,
+// then the Im plane), K = snapshots. With D = [slices of A] [slices of B]^T, the four real
+// products of a block pair give P_ij = X_i X_j^H:
+//     Re P_ij = RR + II,   Im P_ij = IR - RI.
+// One UMMA per 16 snapshots covers all 12 unordered pairs {i, j}, i + j <= 5:
+//     MP = 16: A = [s4 s0 s1 s2] (128 rows), B = [s0 s1 s2 s3 s5] (N = 160);
+//     MP = 8 : A = [s0 .. s5, pad] (128 rows), B = [s0 s1 s2] (N = 48).
+// The operand rows are stored once per stage so that A and B are overlapping windows of them.
+//
+// Combination. Each readout thread owns one A row (slice i, plane p, element a) and adds its
+// designated blocks (each unordered pair once, the diagonal pair with weight 1, the others with
+// weight 2) to 64-bit integer sums U'(a, b) in units of 2^-28 (level-5 pairs rounded to that
+// unit), so the chunk sums combine exactly and in any order; at the end of the problem
+//     R = (U' + U'^H) / 2 * 2^-28 * u0^2 / N   (u0 the scaling unit),
+// written to the workspace as FP64 (full Hermitian matrix, zero imaginary diagonal).
+//
+// Roles (one persistent CTA per SM, static round-robin over the problems, longest first):
+//   warps 0-3  producers: slice one stage (64 snapshots) into the operand ring (128B-swizzled,
+//              K-major); the first stage of a problem also fixes its scaling unit;
+//   warp 4     one thread: TMA bulk copies (cp.async.bulk) of each stage's M rows into a staging
+//              ring (rows 528 bytes apart, so the producers' 16-byte loads hit distinct banks);
+//   warp 5     one thread: the MMAs, one accumulation window (15 stages) per TMEM buffer (two
+//              buffers), committed to the operand ring and to the buffer's mbarrier;
+//   warps 6-9  TMEM readout (warp w reads lanes 32 (w % 4) ..), int64 sums, per-problem finalize.
+// A sample beyond the scaling unit's range (or a non-finite one) marks the problem; a problem that
+// times out in a bounded wait marks every problem of its CTA. Marked problems are recomputed by the
+// compensated CUDA-core kernel (covariance_fixup) launched right after this one.
+#include <limits.h>
+
+#include "doa_internal.cuh"
+#include "tc_common.cuh"
+
+namespace doa {
+namespace {
+
+using namespace tc;
+
+constexpr int kCbSnap = 64;          // snapshots per stage (64 BF16 = one 128-byte operand row)
+constexpr int kCbStg = 8;            // staging ring depth (about 66 KB of reads in flight per SM)
+constexpr int kCbOps = 4;            // operand ring depth
+constexpr int kCbWin = 15;           // stages per exact accumulation window (960 snapshots)
+constexpr int kCbRowPitch = 528;     // staging bytes per element row (512 + 16)
+constexpr int kCbThreads = 320;
+constexpr int kCbRing = 8;           // scaling-unit ring (producers -> readout)
+constexpr int kCbAccCols = 256;      // TMEM columns per accumulator buffer
+
+// Slicing constants 1.5 * 2^(23 - 7k): adding and subtracting one rounds to a multiple of 2^(-7k).
+__device__ __forceinline__ float slice_magic(int k) {
+  return __uint_as_float((uint32_t)(127 + 23 - 7 * k) << 23) * 1.5f;
+}
+
+template <int MP>
+struct CbShape;
+
+template <>
+struct CbShape<16> {
+  static constexpr int kRows = 192;                  // storage rows: s4 s0 s1 s2 s3 s5 (32 each)
+  static constexpr int kBlock = 32;
+  static constexpr int kBStart = 32;                 // B starts at storage row 32 (s0)
+  static constexpr int kN = 160;
+  static constexpr int kSN = 8;                      // snapshots per producer task
+  __host__ __device__ static constexpr int block_of(int k) { return k == 4 ? 0 : (k == 5 ? 5 : k + 1); }
+  __host__ __device__ static constexpr int a_slice(int blk) { return blk == 0 ? 4 : blk - 1; }   // A row block
+  __host__ __device__ static constexpr int b_slice(int cb) { return cb == 4 ? 5 : cb; }          // B col block
+  static constexpr int kBBlocks = 5;
+  // each unordered pair {i, j}, i + j <= 5, once: (i, j) with i <= j, and (4, 0), (4, 1)
+  __host__ __device__ static constexpr bool designated(int i, int j) {
+    return i + j <= 5 && (i <= j || i == 4);
+  }
+};
+
+template <>
+struct CbShape<8> {
+  static constexpr int kRows = 128;                  // s0 .. s5 (16 each) then 32 rows of zeros
+  static constexpr int kBlock = 16;
+  static constexpr int kBStart = 0;
+  static constexpr int kN = 48;
+  static constexpr int kSN = 4;
+  __host__ __device__ static constexpr int block_of(int k) { return k; }
+  __host__ __device__ static constexpr int a_slice(int blk) { return blk; }                      // 6, 7: padding
+  __host__ __device__ static constexpr int b_slice(int cb) { return cb; }
+  __host__ __device__ static constexpr bool designated(int i, int j) { return i <= 5 && i + j <= 5 && i >= j; }
+};
+
+template <int MP>
+struct CbLayout {
+  using S = CbShape<MP>;
+  static constexpr int kStgBytes = MP * kCbRowPitch;
+  static constexpr int kOpBytes = S::kRows * 128;
+  static constexpr int kOffOp = 0;                                        // 1024-aligned stages
+  static constexpr int kOffStg = kOffOp + kCbOps * kOpBytes;
+  static constexpr int kOffU = kOffStg + kCbStg * ((kStgBytes + 127) / 128 * 128);
+  static constexpr int kUBytes = MP * MP * 16;                           // int64 (re, im)
+  // at least 116 KB, so that no two CTAs share an SM (each allocates all 512 TMEM columns)
+  static constexpr int kSmem = (kOffU + kUBytes + 1024) > 118784 ? (kOffU + kUBytes + 1024) : 118784;
+};
+
+struct CbShared {
+  uint64_t full[kCbStg], empty[kCbStg], opfull[kCbOps], opempty[kCbOps], accfull[2], accempty[2];
+  uint64_t efull[kCbRing], eempty[kCbRing], fin;
+  uint64_t pred[2];           // producers' first-stage maximum exchange (count 4 warps)
+  uint64_t rb[2];             // readout warps' finalize steps (count 4 warps)
+  uint32_t tmem;
+  int abort;
+  int eexp[kCbRing];          // scaling exponent k of the problem in ring slot (or INT_MIN: marked)
+  float red[2][4];            // producers' first-stage maxima (double-buffered by problem parity)
+};
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void arrive_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+// Bounded wait that also gives up as soon as another role has given up.
+__device__ __forceinline__ bool cb_wait(uint32_t mbar, uint32_t parity, volatile int *abort) {
+  uint32_t done = 0;
+  for (int it = 0; it < kWaitIters && !done; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (!done && (it & 255) == 255 && *abort) break;
+  }
+  if (!done) *abort = 1;
+  return done != 0;
+}
+
+// Wait of a whole warp: every lane waits (bounded) and the outcome is made warp-uniform, so a lane
+// that gave up never diverges from the others into a warp-collective instruction.
+__device__ __forceinline__ bool warp_wait(uint32_t mbar, uint32_t parity, volatile int *abort) {
+  return __all_sync(0xffffffffu, cb_wait(mbar, parity, abort));
+}
+
+// Warp-granular barrier on an mbarrier of count 4 (one arrival per warp), bounded like every wait.
+__device__ __forceinline__ bool warp_bar(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) arrive(smem_u32(bar));
+  return warp_wait(smem_u32(bar), parity, abort);
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t addr, uint32_t (&r)[N]);
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t addr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t addr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Integer n of a TMEM value n * 2^(-7L), |n| < 2^22: adding 1.5 * 2^23 leaves n + 2^22 in the low
+// mantissa bits.
+template <int L>
+__device__ __forceinline__ int exact_int(uint32_t bits) {
+  const float v = __fmaf_rn(__uint_as_float(bits), __uint_as_float((uint32_t)(127 + 7 * L) << 23), 12582912.0f);
+  return (int)(__float_as_uint(v) - 0x4B400000u);
+}
+// n in units of 2^-28 of w^2, times 2 for an off-diagonal pair (L = 5 rounded to the unit).
+template <int L, bool kOff>
+__device__ __forceinline__ long long to_acc(int n) {
+  constexpr int sh = 28 - 7 * L + (kOff ? 1 : 0);
+  if constexpr (sh >= 0)
+    return (long long)n << sh;
+  else
+    return (long long)((n + (1 << (-sh - 1))) >> (-sh));
+}
+
+// Adds block (i, j) of the accumulator columns [MP re | MP im] of this thread's row to U'.
+template <int MP, int I, int J>
+__device__ __forceinline__ void add_block(const uint32_t (&v)[2 * MP], bool im_row, long long (&ure)[MP],
+                                          long long (&uim)[MP]) {
+  constexpr int L = I + J;
+#pragma unroll
+  for (int b = 0; b < MP; ++b) {
+    const long long xr = to_acc<L, I != J>(exact_int<L>(v[b]));        // (row plane) x Re b
+    const long long xi = to_acc<L, I != J>(exact_int<L>(v[MP + b]));   // (row plane) x Im b
+    // Re row: Re += RR, Im -= RI.  Im row: Re += II, Im += IR.
+    ure[b] += im_row ? xi : xr;
+    uim[b] += im_row ? xr : -xi;
+  }
+}
+
+template <int MP, int I>
+__device__ __forceinline__ void read_row_slice(uint32_t taddr, bool im_row, long long (&ure)[MP], long long (&uim)[MP]) {
+  using S = CbShape<MP>;
+#pragma unroll
+  for (int cb = 0; cb < S::kBBlocks; ++cb) {
+    constexpr int dummy = 0;
+    (void)dummy;
+    const int J = S::b_slice(cb);
+    if (!S::designated(I, J)) continue;
+    uint32_t v[2 * MP];
+    tmem_ld<2 * MP>(taddr + (uint32_t)(cb * S::kBlock), v);
+    // J is a compile-time value of the unrolled loop; dispatch it to the template
+    switch (J) {
+      case 0: if constexpr (S::designated(I, 0)) add_block<MP, I, 0>(v, im_row, ure, uim); break;
+      case 1: if constexpr (S::designated(I, 1)) add_block<MP, I, 1>(v, im_row, ure, uim); break;
+      case 2: if constexpr (S::designated(I, 2)) add_block<MP, I, 2>(v, im_row, ure, uim); break;
+      case 3: if constexpr (S::designated(I, 3)) add_block<MP, I, 3>(v, im_row, ure, uim); break;
+      case 5: if constexpr (S::designated(I, 5)) add_block<MP, I, 5>(v, im_row, ure, uim); break;
+      default: break;
+    }
+  }
+}
+
+// Rows of slices 6 and 7 (MP = 8 padding) are never read; a warp whose two half-warps hold
+// different slices loads every block either needs (tcgen05.ld is warp-collective) and each half
+// keeps its own.
+template <int MP>
+__device__ __forceinline__ void read_window(uint32_t taddr, int quarter, int lane, long long (&ure)[MP],
+                                            long long (&uim)[MP]);
+
+template <>
+__device__ __forceinline__ void read_window<16>(uint32_t taddr, int quarter, int lane, long long (&ure)[16],
+                                                long long (&uim)[16]) {
+  const bool im_row = lane >= 16;
+  switch (quarter) {   // A row block = TMEM lane quarter: s4, s0, s1, s2
+    case 0: read_row_slice<16, 4>(taddr, im_row, ure, uim); break;
+    case 1: read_row_slice<16, 0>(taddr, im_row, ure, uim); break;
+    case 2: read_row_slice<16, 1>(taddr, im_row, ure, uim); break;
+    default: read_row_slice<16, 2>(taddr, im_row, ure, uim); break;
+  }
+}
+
+template <int I0>
+__device__ __forceinline__ void read_pair8(uint32_t taddr, int lane, long long (&ure)[8], long long (&uim)[8]) {
+  // lanes 0-15: slice I0, lanes 16-31: slice I0 + 1; within a slice block rows 0-7 Re, 8-15 Im
+  const bool hi = lane >= 16;
+  const bool im_row = (lane & 8) != 0;
+#pragma unroll
+  for (int cb = 0; cb < 3; ++cb) {
+    const bool need0 = CbShape<8>::designated(I0, cb), need1 = CbShape<8>::designated(I0 + 1, cb);
+    if (!need0 && !need1) continue;
+    uint32_t v[16];
+    tmem_ld<16>(taddr + (uint32_t)(cb * 16), v);
+    switch (cb) {
+      case 0:
+        if (!hi) { if constexpr (CbShape<8>::designated(I0, 0)) add_block<8, I0, 0>(v, im_row, ure, uim); }
+        else { if constexpr (CbShape<8>::designated(I0 + 1, 0)) add_block<8, I0 + 1, 0>(v, im_row, ure, uim); }
+        break;
+      case 1:
+        if (!hi) { if constexpr (CbShape<8>::designated(I0, 1)) add_block<8, I0, 1>(v, im_row, ure, uim); }
+        else { if constexpr (CbShape<8>::designated(I0 + 1, 1)) add_block<8, I0 + 1, 1>(v, im_row, ure, uim); }
+        break;
+      default:
+        if (!hi) { if constexpr (CbShape<8>::designated(I0, 2)) add_block<8, I0, 2>(v, im_row, ure, uim); }
+        else { if constexpr (CbShape<8>::designated(I0 + 1, 2)) add_block<8, I0 + 1, 2>(v, im_row, ure, uim); }
+        break;
+    }
+  }
+}
+
+template <>
+__device__ __forceinline__ void read_window<8>(uint32_t taddr, int quarter, int lane, long long (&ure)[8],
+                                               long long (&uim)[8]) {
+  switch (quarter) {   // A row blocks 2q, 2q + 1 = slices 2q, 2q + 1 (quarter 3: padding)
+    case 0: read_pair8<0>(taddr, lane, ure, uim); break;
+    case 1: read_pair8<2>(taddr, lane, ure, uim); break;
+    case 2: read_pair8<4>(taddr, lane, ure, uim); break;
+    default: break;
+  }
+}
+
+template <int MP>
+__global__ void __launch_bounds__(kCbThreads, 1) covariance_tc_batch_kernel(const uint8_t *plan, uint8_t *ws, int cls) {
+  using S = CbShape<MP>;
+  using Lay = CbLayout<MP>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ CbShared sh;
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
+  const PlanProblem *probs = reinterpret_cast<const PlanProblem *>(plan + h->off_prob);
+  const int32_t *list = reinterpret_cast<const int32_t *>(plan + h->off_covtc[cls]);
+  const int count = h->ncovtc[cls];
+  int32_t *flags = reinterpret_cast<int32_t *>(ws + h->covtc_flag_off) + (cls == 0 ? 0 : h->ncovtc[0]);
+  long long *U = reinterpret_cast<long long *>(sm + Lay::kOffU);   // [MP][MP][re, im]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  volatile int *abort = &sh.abort;
+
+  // zero the operand ring (MP = 8: its padding rows are read by the MMAs) and U
+  for (int e = tid * 16; e < Lay::kOffStg; e += kCbThreads * 16) *reinterpret_cast<uint4 *>(sm + e) = make_uint4(0, 0, 0, 0);
+  for (int e = tid; e < MP * MP * 2; e += kCbThreads) U[e] = 0;
+  if (tid == 0) {
+    auto init = [](uint64_t *b, int n, int cnt) {
+      for (int i = 0; i < n; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b + i)), "r"(cnt));
+    };
+    init(sh.full, kCbStg, 1);
+    init(sh.empty, kCbStg, 4);
+    init(sh.opfull, kCbOps, 4);
+    init(sh.opempty, kCbOps, 1);
+    init(sh.accfull, 2, 1);
+    init(sh.accempty, 2, 4);
+    init(sh.efull, kCbRing, 1);
+    init(sh.eempty, kCbRing, 4);
+    init(&sh.fin, 1, 1);
+    init(sh.pred, 2, 4);
+    init(sh.rb, 2, 4);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sh.abort = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sh.tmem;
+
+  if (warp < 4) {
+    // ---------------------------------------------------------------- producers
+    constexpr int SN = S::kSN;                   // snapshots per task; tasks: MP rows x (64 / SN)
+    const int m = tid % MP, c = tid / MP;        // row, chunk (a quarter-warp spans 8 rows)
+    uint32_t g = 0;                              // stage counter
+    int kth = 0;                                 // problem counter of this CTA
+    for (int pi = blockIdx.x; pi < count && !*abort; pi += gridDim.x, ++kth) {
+      const PlanProblem &pp = probs[list[pi]];
+      const int M = pp.p.M, N = pp.p.N, ldx = pp.p.ldx;
+      const float2 *X = reinterpret_cast<const float2 *>(pp.p.X);
+      const int nst = (N + kCbSnap - 1) / kCbSnap;
+      float scale = 0.f;
+      bool bad = false;
+      for (int s = 0; s < nst; ++s, ++g) {
+        const int ss = g % kCbStg, os = g % kCbOps;
+        if (!warp_wait(smem_u32(&sh.full[ss]), (g / kCbStg) & 1u, abort)) break;
+        // this task's SN snapshots of row m (zeros past N and for rows >= M)
+        float re[SN], im[SN];
+        const int t0 = s * kCbSnap, cnt = min(kCbSnap, N - t0), cb = cnt & ~1;
+        const float *stg = reinterpret_cast<const float *>(sm + Lay::kOffStg + ss * ((Lay::kStgBytes + 127) / 128 * 128) +
+                                                           m * kCbRowPitch) + 2 * c * SN;
+#pragma unroll
+        for (int q = 0; q < SN / 2; ++q) {
+          const int t = c * SN + 2 * q;
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (m < M) {
+            if (t + 1 < cb) {
+              v = *reinterpret_cast<const float4 *>(stg + 4 * q);
+            } else {
+              if (t < cnt) {
+                const float2 a = t < cb ? *reinterpret_cast<const float2 *>(stg + 4 * q) : X[(size_t)m * ldx + t0 + t];
+                v.x = a.x;
+                v.y = a.y;
+              }
+              if (t + 1 < cnt) {
+                const float2 a = X[(size_t)m * ldx + t0 + t + 1];
+                v.z = a.x;
+                v.w = a.y;
+              }
+            }
+          }
+          re[2 * q] = v.x;
+          im[2 * q] = v.y;
+          re[2 * q + 1] = v.z;
+          im[2 * q + 1] = v.w;
+        }
+        __syncwarp();
+        if (lane == 0) arrive(smem_u32(&sh.empty[ss]));
+        if (s == 0) {
+          // scaling unit from the first stage's largest |component|: 2^(k-1) <= mx < 2^k,
+          // u0 = 2^(k-5), so |w| = |x| / u0 <= 64 for |x| <= 2^(k+1) (one bit of headroom)
+          float mx = 0.f;
+#pragma unroll
+          for (int q = 0; q < SN; ++q) mx = fmaxf(mx, fmaxf(fabsf(re[q]), fabsf(im[q])));
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+          if (lane == 0) sh.red[kth & 1][warp] = mx;
+          if (!warp_bar(&sh.pred[kth & 1], (uint32_t)((kth >> 1) & 1), abort)) break;
+          mx = fmaxf(fmaxf(sh.red[kth & 1][0], sh.red[kth & 1][1]), fmaxf(sh.red[kth & 1][2], sh.red[kth & 1][3]));
+          const int eb = (int)((__float_as_uint(mx) >> 23) & 0xffu);
+          bad = eb < 4 || eb > 254;                       // zero, subnormal, tiny or non-finite
+          const int k = eb - 126;
+          scale = bad ? 0.f : __uint_as_float((uint32_t)(258 - eb) << 23);   // 2^(5 - k)
+          if (tid == 0) {
+            const int r = kth % kCbRing;
+            if (kth >= kCbRing) cb_wait(smem_u32(&sh.eempty[r]), (uint32_t)((kth / kCbRing - 1) & 1), abort);
+            sh.eexp[r] = bad ? INT_MIN : k;
+            arrive(smem_u32(&sh.efull[r]));
+          }
+        }
+        // operand slot free (the MMAs of its previous stage are done)
+        if (g >= (uint32_t)kCbOps && !warp_wait(smem_u32(&sh.opempty[os]), (g / kCbOps - 1) & 1u, abort)) break;
+        uint8_t *op = sm + Lay::kOffOp + os * Lay::kOpBytes;
+        float rr[SN], ri[SN];
+#pragma unroll
+        for (int q = 0; q < SN; ++q) {
+          rr[q] = __fmul_rn(re[q], scale);
+          ri[q] = __fmul_rn(im[q], scale);
+          bad |= !(fabsf(rr[q]) <= 64.f) || !(fabsf(ri[q]) <= 64.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const float C = slice_magic(k);
+          uint32_t pr[SN / 2], pim[SN / 2];
+#pragma unroll
+          for (int q = 0; q < SN; q += 2) {
+            const float s0 = __fsub_rn(__fadd_rn(rr[q], C), C), s1 = __fsub_rn(__fadd_rn(rr[q + 1], C), C);
+            const float t0_ = __fsub_rn(__fadd_rn(ri[q], C), C), t1 = __fsub_rn(__fadd_rn(ri[q + 1], C), C);
+            if (k < 5) {
+              rr[q] = __fsub_rn(rr[q], s0);
+              rr[q + 1] = __fsub_rn(rr[q + 1], s1);
+              ri[q] = __fsub_rn(ri[q], t0_);
+              ri[q + 1] = __fsub_rn(ri[q + 1], t1);
+            }
+            const __nv_bfloat162 a = __floats2bfloat162_rn(s0, s1), b = __floats2bfloat162_rn(t0_, t1);
+            pr[q / 2] = *reinterpret_cast<const uint32_t *>(&a);
+            pim[q / 2] = *reinterpret_cast<const uint32_t *>(&b);
+          }
+          const int rre = S::block_of(k) * S::kBlock + m, rim = rre + MP;
+          if constexpr (SN == 8) {
+            *reinterpret_cast<uint4 *>(op + sw128(rre, 8 * c)) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
+            *reinterpret_cast<uint4 *>(op + sw128(rim, 8 * c)) = make_uint4(pim[0], pim[1], pim[2], pim[3]);
+          } else {
+            *reinterpret_cast<uint2 *>(op + sw128(rre, 4 * c)) = make_uint2(pr[0], pr[1]);
+            *reinterpret_cast<uint2 *>(op + sw128(rim, 4 * c)) = make_uint2(pim[0], pim[1]);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) arrive(smem_u32(&sh.opfull[os]));
+      }
+      // a sample outside the unit's range (or a non-finite one): recompute the problem elsewhere
+      if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&flags[pi], 1);
+    }
+  } else if (warp == 4) {
+    // ---------------------------------------------------------------- TMA: staging copies
+    if (lane == 0) {
+      uint32_t g = 0;
+      for (int pi = blockIdx.x; pi < count && !*abort; pi += gridDim.x) {
+        const PlanProblem &pp = probs[list[pi]];
+        const int M = pp.p.M, N = pp.p.N, ldx = pp.p.ldx;
+        const float2 *X = reinterpret_cast<const float2 *>(pp.p.X);
+        const int nst = (N + kCbSnap - 1) / kCbSnap;
+        flags[pi] = 0;   // ordered before the producers' marks by the first stage's mbarrier
+        for (int s = 0; s < nst; ++s, ++g) {
+          const int ss = g % kCbStg;
+          if (g >= (uint32_t)kCbStg && !cb_wait(smem_u32(&sh.empty[ss]), (g / kCbStg - 1) & 1u, abort)) break;
+          const int t0 = s * kCbSnap, cb = min(kCbSnap, N - t0) & ~1;
+          const uint32_t dst = smem_u32(sm + Lay::kOffStg + ss * ((Lay::kStgBytes + 127) / 128 * 128));
+          arrive_tx(smem_u32(&sh.full[ss]), (uint32_t)(M * cb * 8));
+          if (cb > 0)
+            for (int m = 0; m < M; ++m)
+              bulk_copy(dst + m * kCbRowPitch, X + (size_t)m * ldx + t0, (uint32_t)(cb * 8), smem_u32(&sh.full[ss]));
+        }
+      }
+      // let every copy in flight land before the CTA can exit
+      if (*abort)
+        for (uint32_t q = g > (uint32_t)kCbStg ? g - kCbStg : 0u; q < g; ++q)
+          mbar_wait(smem_u32(&sh.full[q % kCbStg]), (q / kCbStg) & 1u);
+    }
+    __syncwarp();
+  } else if (warp == 5) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = inst_desc(1, S::kN);
+      uint32_t g = 0, gw = 0;
+      for (int pi = blockIdx.x; pi < count && !*abort; pi += gridDim.x) {
+        const int N = probs[list[pi]].p.N;
+        const int nst = (N + kCbSnap - 1) / kCbSnap, nwin = (nst + kCbWin - 1) / kCbWin;
+        for (int w = 0; w < nwin && !*abort; ++w, ++gw) {
+          const int buf = gw & 1;
+          if (gw >= 2u && !cb_wait(smem_u32(&sh.accempty[buf]), ((gw >> 1) - 1) & 1u, abort)) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int s1 = min(nst, (w + 1) * kCbWin);
+          for (int s = w * kCbWin; s < s1; ++s, ++g) {
+            const int os = g % kCbOps;
+            if (!cb_wait(smem_u32(&sh.opfull[os]), (g / kCbOps) & 1u, abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t pa = smem_u32(sm + Lay::kOffOp + os * Lay::kOpBytes), pb = pa + S::kBStart * 128;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              mma(tmem + (uint32_t)(buf * kCbAccCols), smem_desc(pa + kk * 32), smem_desc(pb + kk * 32), idesc,
+                  (s > w * kCbWin || kk > 0) ? 1u : 0u);
+            commit(smem_u32(&sh.opempty[os]));
+          }
+          commit(smem_u32(&sh.accfull[buf]));
+        }
+      }
+      // every MMA of this thread done before the CTA releases TMEM and shared memory
+      commit(smem_u32(&sh.fin));
+      mbar_wait(smem_u32(&sh.fin), 0u);
+    }
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------------- TMEM readout and finalize
+    const int q = warp & 3;                                    // TMEM lane quarter
+    const int rt = tid - 6 * 32;                               // 0..127
+    uint32_t gw = 0;
+    int kth = 0;
+    for (int pi = blockIdx.x; pi < count && !*abort; pi += gridDim.x, ++kth) {
+      const PlanProblem &pp = probs[list[pi]];
+      const int M = pp.p.M, N = pp.p.N;
+      const int nst = (N + kCbSnap - 1) / kCbSnap, nwin = (nst + kCbWin - 1) / kCbWin;
+      long long ure[MP], uim[MP];
+#pragma unroll
+      for (int b = 0; b < MP; ++b) ure[b] = uim[b] = 0;
+      bool ok = true;
+      for (int w = 0; w < nwin; ++w, ++gw) {
+        const int buf = gw & 1;
+        if (!warp_wait(smem_u32(&sh.accfull[buf]), (gw >> 1) & 1u, abort)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        read_window<MP>(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * kCbAccCols), q, lane, ure, uim);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) arrive(smem_u32(&sh.accempty[buf]));
+      }
+      if (!ok) break;
+      // finalize: U' = sum over this problem's rows, R = (U' + U'^H) / 2 scaled
+      const int r = kth % kCbRing;
+      if (!warp_wait(smem_u32(&sh.efull[r]), (uint32_t)((kth / kCbRing) & 1), abort)) break;
+      const int kexp = sh.eexp[r];
+      // every thread has zeroed its entries of U (previous problem) before anyone adds to it
+      if (!warp_bar(&sh.rb[0], (uint32_t)(kth & 1), abort)) break;
+      // my row: element a (lanes within the slice block); padding rows add nothing
+      const int a = MP == 16 ? (lane & 15) : (lane & 7);
+#pragma unroll
+      for (int b = 0; b < MP; ++b) {
+        if (ure[b] != 0) atomicAdd(reinterpret_cast<unsigned long long *>(&U[(a * MP + b) * 2]), (unsigned long long)ure[b]);
+        if (uim[b] != 0) atomicAdd(reinterpret_cast<unsigned long long *>(&U[(a * MP + b) * 2 + 1]), (unsigned long long)uim[b]);
+      }
+      if (!warp_bar(&sh.rb[1], (uint32_t)(kth & 1), abort)) break;
+      if (lane == 0) arrive(smem_u32(&sh.eempty[r]));
+      // one thread per pair (ea <= eb): both entries of R from U'(ea, eb) and U'(eb, ea), then zeroed
+      double2 *R64 = reinterpret_cast<double2 *>(ws + pp.r64_off);
+      const double sc = kexp == INT_MIN ? 0.0 : ldexp(1.0, 2 * kexp - 10 - 29) / (double)N;
+      for (int e = rt; e < M * M; e += 128) {
+        const int ea = e / M, eb = e % M;
+        if (ea > eb) continue;
+        long long *u1 = &U[(ea * MP + eb) * 2], *u2 = &U[(eb * MP + ea) * 2];
+        const long long re = u1[0] + u2[0], im = u1[1] - u2[1];
+        if (kexp != INT_MIN) {   // a marked problem is rewritten by the fixup kernel
+          R64[ea * M + eb] = make_double2((double)re * sc, ea == eb ? 0.0 : (double)im * sc);
+          R64[eb * M + ea] = make_double2((double)re * sc, ea == eb ? 0.0 : -(double)im * sc);
+        }
+        u1[0] = u1[1] = u2[0] = u2[1] = 0;
+      }
+    }
+  }
+
+  // -------------------------------------------------------------------- teardown
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (*abort && tid == 0)   // every problem of this CTA goes to the fixup kernel
+    for (int pi = blockIdx.x; pi < count; pi += gridDim.x) flags[pi] = 2;
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+template <int MP>
+cudaError_t launch_class(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, int cls, cudaStream_t s) {
+  const int n = h.ncovtc[cls];
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void *>(covariance_tc_batch_kernel<MP>), CbLayout<MP>::kSmem);
+  if (e != cudaSuccess) return e;
+  const int grid = n < device_sm_count() ? n : device_sm_count();   // one CTA per SM (512 TMEM columns)
+  covariance_tc_batch_kernel<MP><<<grid, kCbThreads, CbLayout<MP>::kSmem, s>>>(plan_dev, ws, cls);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_covariance_tc_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s) {
+  cudaError_t e = launch_class<8>(plan_dev, h, ws, 0, s);
+  if (e != cudaSuccess) return e;
+  return launch_class<16>(plan_dev, h, ws, 1, s);
+}
+
+}  // namespace doa

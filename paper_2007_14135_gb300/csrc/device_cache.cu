@@ -1,0 +1,43 @@
+// Per-device host state of the launchers: the dynamic shared-memory limit of each kernel (a
+// function attribute applies to one device's context) and the SM count. Both are looked up once
+// per (device, kernel) under a mutex, so several host threads and several GPUs may launch.
+#include <mutex>
+#include <set>
+#include <utility>
+
+#include "doa_internal.cuh"
+
+namespace doa {
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+std::set<std::pair<int, const void *>> g_attr_done;   // (device, kernel) with its limit raised
+int g_sms[kMaxDevices] = {};
+
+}  // namespace
+
+cudaError_t ensure_smem_attr(const void *func, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (g_attr_done.count({dev, func})) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) g_attr_done.insert({dev, func});
+  return e;
+}
+
+int device_sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 1;
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (g_sms[dev] <= 0) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    g_sms[dev] = n > 0 ? n : 1;
+  }
+  return g_sms[dev];
+}
+
+}  // namespace doa

@@ -175,8 +175,21 @@ struct PlanProblem {
   int32_t geo_steer;      // geometry problems: index of the shared FP32 steering table, or -1
 };
 
-// Bytes of a problem's scan factor area: F (M x (M+1) complex128) + EV weights (M doubles).
-__host__ __device__ inline int64_t factor_bytes(int M) { return (int64_t)M * (M + 1) * 16 + (int64_t)M * 8; }
+// The Python binding reads problem i's R offset (r64_off) from the plan record at
+// off_prob + i * sizeof(PlanProblem).
+static_assert(offsetof(PlanProblem, r64_off) == sizeof(doa_problem), "PlanProblem layout changed");
+static_assert(sizeof(PlanProblem) == sizeof(doa_problem) + 96, "PlanProblem layout changed");
+
+__host__ __device__ inline int m_bucket(int M) { return M <= 8 ? 0 : (M <= 16 ? 1 : (M <= 32 ? 2 : 3)); }
+__host__ __device__ inline int scan_mp(int M) { return 8 << m_bucket(M); }   // padded rows of the FP32 scan
+
+// A problem's scan factor area: F (M x (M+1) complex128, column-major) and the EV weights (M
+// doubles), then at fac32_off(M) the FP32 copy the grid-shared scan reads: F32 (M+1 columns of
+// scan_mp(M) float2, rows >= M zero), w32 (scan_mp(M) floats) and the four readout thresholds.
+__host__ __device__ inline int64_t fac32_off(int M) { return ((int64_t)M * (M + 1) * 16 + (int64_t)M * 8 + 15) / 16 * 16; }
+__host__ __device__ inline int64_t factor_bytes(int M) {
+  return fac32_off(M) + (int64_t)(M + 1) * scan_mp(M) * 8 + (int64_t)scan_mp(M) * 4 + 16;
+}
 
 struct PlanJob {          // one (problem, algorithm) pair: a spectrum and its peaks
   int32_t prob;
@@ -215,6 +228,21 @@ struct PlanGeoSteer {
   int64_t tab_off;        // workspace byte offset of float2[MP][ldt]
 };
 constexpr int kSteerAlign = 1024;   // row stride multiple: every scan tile's points lie inside a row
+
+// Grid-shared FP32 scan: ULA problems of one M bucket that share a grid are scanned in groups; a
+// unit is one tile of the grid for every problem of a group (the tile's steering phasors are
+// generated once and contracted with each problem's factor in turn). Units are numbered group by
+// group from unit_start.
+struct PlanScanGroup {
+  int32_t grid_id;
+  int32_t first;          // first entry of the group in the bucket's problem list
+  int32_t count;          // problems in the group (<= kScanGroupMax)
+  int32_t tiles;          // tiles of kScanThreads x scan_pt points covering the grid
+  int64_t unit_start;
+};
+constexpr int kScanGroupMax = 64;       // problems per group (a queued point's problem fits a byte)
+constexpr int kScanGroupDefault = 32;
+__host__ __device__ inline bool scan_group_allowed(int g) { return g >= 1 && g <= kScanGroupMax && (g & (g - 1)) == 0; }
 
 struct PlanCovItem {
   int32_t prob;
@@ -258,11 +286,26 @@ struct PlanHeader {
   int32_t ngeo_steer;                    // shared FP32 steering tables of geometry problems
   int32_t steer_max_ldt;                 // largest row stride among them
   int64_t off_geo_steer;
+  // problems whose covariance runs on the tensor cores (exact BF16 slices), M <= 8 and 8 < M <= 16;
+  // their lists hold problem indices, longest N first
+  int32_t ncovtc[2];
+  int64_t off_covtc[2];
+  int64_t covtc_flag_off;                // workspace byte offset of one int32 per listed problem
+                                         // (class 0 then class 1): 0 done, else recomputed by
+                                         // the compensated CUDA-core fixup kernel
+  // grid-shared FP32 scan, per M bucket (problems in these groups are not in the per-problem lists)
+  int32_t sg_size[kNumBuckets];          // problems per group (1: every problem scanned alone)
+  int32_t sg_groups[kNumBuckets];
+  int64_t sg_units[kNumBuckets];
+  int64_t off_sg[kNumBuckets];           // PlanScanGroup arrays
+  int64_t off_sgl[kNumBuckets];          // their problem lists
+  int32_t sg_probs[kNumBuckets];         // problems in the groups
 };
 
 // The Python binding reads these header fields by position (int32 index 22 = scan_pt, 58 = eig_mats,
 // 62 = cov_first, 67 = tc_jobs, 74 = npolish, 76 = geo_jobs, 96 = ngeo_grids, 100 = nrefine,
-// 101 = nroots, 104 = ngeo_steer).
+// 101 = nroots, 104 = ngeo_steer, 108 = ncovtc, 114 = covtc_flag_off (int64), 116 = sg_size,
+// 120 = sg_groups, 124 = sg_units (int64), 148 = sg_probs).
 static_assert(offsetof(PlanHeader, scan_pt) == 88, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, scan_tiles) == 56, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, eig_mats) == 232, "PlanHeader layout changed");
@@ -274,6 +317,12 @@ static_assert(offsetof(PlanHeader, ngeo_grids) == 384, "PlanHeader layout change
 static_assert(offsetof(PlanHeader, nrefine) == 400, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, nroots) == 404, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, ngeo_steer) == 416, "PlanHeader layout changed");
+static_assert(offsetof(PlanHeader, off_prob) == 120, "PlanHeader layout changed");
+static_assert(offsetof(PlanHeader, ncovtc) == 432, "PlanHeader layout changed");
+static_assert(offsetof(PlanHeader, covtc_flag_off) == 456, "PlanHeader layout changed");
+static_assert(offsetof(PlanHeader, sg_size) == 464 && offsetof(PlanHeader, sg_units) == 496 &&
+                  offsetof(PlanHeader, sg_probs) == 592,
+              "PlanHeader layout changed");
 
 // Scan tiles: kScanThreads threads, each evaluating PT consecutive grid points (tile shape
 // 128 x PT). PT is chosen per M bucket (the autotuner's knob); the register budget limits it
@@ -297,7 +346,17 @@ __host__ __device__ inline int eig_mats_default(int bucket, int count) {
   return g;
 }
 
-__host__ __device__ inline int m_bucket(int M) { return M <= 8 ? 0 : (M <= 16 ? 1 : (M <= 32 ? 2 : 3)); }
+// Tensor-core batch covariance: problems with M <= kCovTcMaxM, a 16-byte aligned X and an even
+// row stride (whole-row bulk copies), and N <= kCovTcMaxN (range of its 64-bit sums).
+constexpr int kCovTcMaxM = 16;
+constexpr int kCovTcMaxN = 1 << 21;
+
+// ------------------------------------------------------------------------------------------
+// Per-device host state (device_cache.cu): the dynamic shared-memory limit of a kernel, raised
+// once per device, and the device's SM count.
+// ------------------------------------------------------------------------------------------
+cudaError_t ensure_smem_attr(const void *func, int bytes);
+int device_sm_count();
 
 // ------------------------------------------------------------------------------------------
 // Host launchers (one translation unit each). They return cudaError_t of the launch.
@@ -309,6 +368,10 @@ cudaError_t launch_covariance_single(const float2 *X, int M, int N, int ldx, flo
                                      cudaStream_t s);
 cudaError_t launch_covariance_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws,
                                     cudaStream_t s);
+cudaError_t launch_covariance_tc_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
+// Recomputes, with the compensated CUDA-core accumulation, the listed problems the tensor-core
+// kernel marked (sample beyond its scaling range, non-finite data, or a bounded wait that ran out).
+cudaError_t launch_covariance_fixup(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
 cudaError_t launch_covariance_tc_single(const float2 *X, int M, int N, int ldx, int prec, float2 *R, double2 *R64,
                                         cudaStream_t s);
 

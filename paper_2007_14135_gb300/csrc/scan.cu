@@ -77,6 +77,26 @@ __global__ void __launch_bounds__(kScanThreads) scan_single_kernel(const double2
   drain_refinements(j, sh);
 }
 
+// Scan job of a ULA problem of the batch on its grid (factor and EV weights in the workspace).
+__device__ __forceinline__ ScanJob ula_job(const PlanProblem &pp, const PlanGrid &g, const uint8_t *ws) {
+  ScanJob j{};
+  j.F = reinterpret_cast<const double2 *>(ws + pp.fac_off);
+  j.w = pp.Kn > 0 && pp.slot[DOA_EV] >= 0
+            ? reinterpret_cast<const double *>(ws + pp.fac_off) + 2 * pp.p.M * (pp.p.M + 1)
+            : nullptr;
+  j.S64 = reinterpret_cast<const uint64_t *>(ws + g.S64_off);
+  for (int r = 0; r < 4; ++r) j.P[r] = pp.slot[r] >= 0 ? pp.p.P + (size_t)pp.slot[r] * g.L : nullptr;
+  j.lo = g.lo;
+  j.step = g.step;
+  j.M = pp.p.M;
+  j.Kf = pp.Kf;
+  j.Kn = pp.Kn;
+  j.kphd = pp.kphd;
+  j.kmn = pp.kmn;
+  j.kofs = 0;
+  return j;
+}
+
 // Persistent batched scan over the tiles of the problems of one M bucket. The tiles are dealt
 // to the CTAs in runs of consecutive tiles, run r to CTA r mod gridDim: consecutive tiles
 // mostly share a problem (its factor stays in shared memory), while the runs of problems of
@@ -114,20 +134,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t 
         if (cur >= 0) drain_refinements(j, sh);   // the queued points belong to the previous problem
         pp = &probs[list[u]];
         g = &grids[pp->grid_id];
-        j.F = reinterpret_cast<const double2 *>(ws + pp->fac_off);
-        j.w = pp->Kn > 0 && pp->slot[DOA_EV] >= 0
-                  ? reinterpret_cast<const double *>(ws + pp->fac_off) + 2 * pp->p.M * (pp->p.M + 1)
-                  : nullptr;
-        j.S64 = reinterpret_cast<const uint64_t *>(ws + g->S64_off);
-        for (int r = 0; r < 4; ++r) j.P[r] = pp->slot[r] >= 0 ? pp->p.P + (size_t)pp->slot[r] * g->L : nullptr;
-        j.lo = g->lo;
-        j.step = g->step;
-        j.M = pp->p.M;
-        j.Kf = pp->Kf;
-        j.Kn = pp->Kn;
-        j.kphd = pp->kphd;
-        j.kmn = pp->kmn;
-        j.kofs = 0;
+        j = ula_job(*pp, *g, ws);
         __syncthreads();
         load_job<MP>(j, Bs, sh);
         __syncthreads();
@@ -140,6 +147,116 @@ __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t 
       scan_points<MP, PT>(Bs, j, S, g->L, k0, sh);
     }
     drain_refinements(j, sh);   // once per run: the warps share the FP64 work of its tiles
+  }
+}
+
+// Grid-shared scan (problems of one M bucket that share a grid, in groups of up to
+// kScanGroupMax). A unit is one tile of the grid for every problem of a group: the CTA generates
+// the tile's steering phasors once, keeps them in registers and contracts them with the factor of
+// each problem of the group in turn, so the phasor polynomials cost 1 / count of the per-problem
+// scan and nearly every instruction left is a contraction FMA. Each problem's FP32 factor, EV
+// weights and thresholds were written once per solve by scan_prep_kernel (the same values the
+// per-problem scan computes), so every point gets bit for bit the spectrum of the per-problem
+// scan. Flagged points of all the group's problems queue up with their problem's position in the
+// group and are re-evaluated in FP64 when the unit ends.
+
+// FP32 copy of each grouped problem's factor (one warp per problem): F32, w32, thresholds.
+template <int MP>
+__global__ void __launch_bounds__(kScanThreads) scan_prep_kernel(const uint8_t *plan, uint8_t *ws, int bucket) {
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
+  const int32_t *list = reinterpret_cast<const int32_t *>(plan + h->off_sgl[bucket]);
+  const PlanProblem *probs = reinterpret_cast<const PlanProblem *>(plan + h->off_prob);
+  const int i = blockIdx.x * kScanWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i >= h->sg_probs[bucket]) return;
+  const PlanProblem &pp = probs[list[i]];
+  const int M = pp.p.M, Kf = pp.Kf, Kn = pp.Kn;
+  const double2 *F = reinterpret_cast<const double2 *>(ws + pp.fac_off);
+  const double *w = pp.Kn > 0 && pp.slot[DOA_EV] >= 0 ? reinterpret_cast<const double *>(F + M * (M + 1)) : nullptr;
+  float2 *F32 = reinterpret_cast<float2 *>(ws + pp.fac_off + fac32_off(M));
+  float *w32 = reinterpret_cast<float *>(F32 + (M + 1) * MP);
+  for (int e = lane; e < Kf * MP; e += 32) {
+    const int k = e / MP, m = e % MP;
+    float2 v = make_float2(0.f, 0.f);
+    if (m < M) {
+      const double2 b = F[(size_t)k * M + m];
+      v = make_float2((float)b.x, (float)b.y);
+    }
+    F32[e] = v;
+  }
+  for (int k = lane; k < Kn; k += 32) w32[k] = w ? (float)w[k] : 1.f;
+  __syncwarp();
+  float thr[4] = {0.f, 0.f, 0.f, 0.f};
+  job_thresholds<MP>(F32, w32, Kf, Kn, pp.kphd, pp.kmn, thr);
+  if (lane < 4) w32[MP + lane] = thr[lane];
+}
+
+template <int MP, int PT>
+__global__ void __launch_bounds__(kScanThreads) scan_shared_kernel(const uint8_t *plan, uint8_t *ws, int bucket) {
+  __shared__ __align__(16) float2 Bs[(MP + 1) * MP];
+  __shared__ float w32s[MP], thrs[4];
+  __shared__ uint8_t tags[kFlagCap];
+  __shared__ ScanShared sh;
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
+  const PlanScanGroup *groups = reinterpret_cast<const PlanScanGroup *>(plan + h->off_sg[bucket]);
+  const int ngroups = h->sg_groups[bucket];
+  const int64_t nunits = h->sg_units[bucket];
+  const int32_t *list = reinterpret_cast<const int32_t *>(plan + h->off_sgl[bucket]);
+  const PlanProblem *probs = reinterpret_cast<const PlanProblem *>(plan + h->off_prob);
+  const PlanGrid *grids = reinterpret_cast<const PlanGrid *>(plan + h->off_grid);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  constexpr int TP = kScanThreads * PT;
+  if (tid == 0) sh.nflag = 0;
+  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+    int gi = 0, hi = ngroups - 1;
+    while (gi < hi) {  // last group with unit_start <= u
+      const int mid = (gi + hi + 1) >> 1;
+      if (groups[mid].unit_start <= u) gi = mid; else hi = mid - 1;
+    }
+    const PlanScanGroup gr = groups[gi];
+    const PlanGrid &g = grids[gr.grid_id];
+    const int L = g.L, k0 = (int)(u - gr.unit_start) * TP + tid * PT;
+    float2 a[PT][MP];
+    ula_phasors<MP, PT>(reinterpret_cast<const uint32_t *>(ws + g.S_off), L, k0, a);
+    for (int i = 0; i < gr.count; ++i) {
+      const PlanProblem &pp = probs[list[gr.first + i]];
+      const ScanJob j = ula_job(pp, g, ws);
+      const uint8_t *f32 = ws + pp.fac_off + fac32_off(j.M);
+      __syncthreads();   // the previous problem's contraction has finished reading Bs
+      const float4 *src4 = reinterpret_cast<const float4 *>(f32);
+      float4 *dst4 = reinterpret_cast<float4 *>(Bs);
+      for (int e = tid; e < j.Kf * MP / 2; e += kScanThreads) dst4[e] = src4[e];
+      const float *wg = reinterpret_cast<const float *>(f32 + (size_t)(j.M + 1) * MP * 8);
+      for (int k = tid; k < j.Kn; k += kScanThreads) w32s[k] = wg[k];
+      if (tid < 4) thrs[tid] = wg[MP + tid];
+      __syncthreads();
+      contract_points<MP, PT, UlaSource, true>(Bs, j, a, L, k0, sh, UlaSource{&j}, w32s, thrs, tags, i);
+    }
+    // FP64 re-evaluation of the unit's flagged points, several per warp for small factors; the
+    // queue holds the points of each problem together (problems run one after the other)
+    __syncthreads();
+    const int n = min(sh.nflag, kFlagCap);
+    for (int i0 = warp * 4; i0 < n; i0 += kScanWarps * 4) {
+      const int end = min(i0 + 4, n);
+      for (int c0 = i0; c0 < end;) {
+        const int tag = tags[c0];
+        int c1 = c0 + 1;
+        while (c1 < end && tags[c1] == tag) ++c1;
+        const PlanProblem &pp = probs[list[gr.first + tag]];
+        const ScanJob j = ula_job(pp, g, ws);
+        const float *wg = reinterpret_cast<const float *>(ws + pp.fac_off + fac32_off(j.M) + (size_t)(j.M + 1) * MP * 8);
+        const UlaSource src{&j};
+        if (j.M <= 8 && j.Kf <= 8) {
+          refine_points_subwarp<8>(j, sh.flags + c0, c1 - c0, src, wg, sh.ph[warp]);
+        } else if (j.M <= 16 && j.Kf <= 16) {
+          for (int c = c0; c < c1; c += 2) refine_points_subwarp<16>(j, sh.flags + c, min(2, c1 - c), src, wg, sh.ph[warp]);
+        } else {
+          for (int c = c0; c < c1; ++c) refine_point_warp_src(j, sh.flags[c], src, wg, sh.ph[warp], sh.yb[warp]);
+        }
+        c0 = c1;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) sh.nflag = 0;
   }
 }
 
@@ -293,8 +410,43 @@ cudaError_t launch_polish_batch(const uint8_t *plan_dev, const PlanHeader &h, ui
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s) {
+template <int MP, int PT>
+cudaError_t run_shared(const uint8_t *plan, const PlanHeader &h, uint8_t *ws, int bucket, cudaStream_t s) {
+  if (h.sg_units[bucket] == 0) return cudaSuccess;
+  scan_prep_kernel<MP><<<(h.sg_probs[bucket] + kScanWarps - 1) / kScanWarps, kScanThreads, 0, s>>>(plan, ws, bucket);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_shared_kernel<MP, PT>, kScanThreads, 0);
+  if (per_sm < 1) per_sm = 1;
+  const int64_t grid = std::min<int64_t>((int64_t)num_sms() * per_sm, h.sg_units[bucket]);
+  scan_shared_kernel<MP, PT><<<(unsigned)grid, kScanThreads, 0, s>>>(plan, ws, bucket);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_scan_shared(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s) {
   cudaError_t e;
+  switch (h.scan_pt[0]) {
+    case 1: e = run_shared<8, 1>(plan_dev, h, ws, 0, s); break;
+    case 2: e = run_shared<8, 2>(plan_dev, h, ws, 0, s); break;
+    default: e = run_shared<8, 4>(plan_dev, h, ws, 0, s); break;
+  }
+  if (e != cudaSuccess) return e;
+  switch (h.scan_pt[1]) {
+    case 1: e = run_shared<16, 1>(plan_dev, h, ws, 1, s); break;
+    case 4: e = run_shared<16, 4>(plan_dev, h, ws, 1, s); break;
+    default: e = run_shared<16, 2>(plan_dev, h, ws, 1, s); break;
+  }
+  if (e != cudaSuccess) return e;
+  if (h.scan_pt[2] == 2)
+    e = run_shared<32, 2>(plan_dev, h, ws, 2, s);
+  else
+    e = run_shared<32, 1>(plan_dev, h, ws, 2, s);
+  if (e != cudaSuccess) return e;
+  return run_shared<64, 1>(plan_dev, h, ws, 3, s);
+}
+
+cudaError_t launch_scan_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s) {
+  cudaError_t e = launch_scan_shared(plan_dev, h, ws, s);
+  if (e != cudaSuccess) return e;
   switch (h.scan_pt[0]) {
     case 1: e = run_batch<8, 1>(plan_dev, h, ws, 0, s); break;
     case 2: e = run_batch<8, 2>(plan_dev, h, ws, 0, s); break;

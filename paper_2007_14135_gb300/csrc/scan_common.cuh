@@ -64,33 +64,48 @@ __device__ __forceinline__ void load_job(const ScanJob &j, float2 *Bs, ScanShare
 // Threshold of readout r = kRefineC * E_r with s_k = sum_m |f_mk| (FP32 factor):
 // E_MUSIC = sum_{k<Kn} s_k^2, E_EV = sum_{k<Kn} w_k s_k^2, E_PHD = s_kphd^2, E_MN = s_kmn^2.
 // (A bound of ~4 eps per term on y_k gives den a relative error below ~5e-4 above it.)
+// Computed by the 32 lanes of one warp (every lane returns the same values); thr[r] of an absent
+// readout is left as it was.
+template <int MP>
+__device__ __forceinline__ void job_thresholds(const float2 *F32, const float *w32, int Kf, int Kn, int kphd, int kmn,
+                                               float (&thr)[4]) {
+  const int lane = threadIdx.x & 31;
+  float em = 0.f, ee = 0.f, ep = -1.f, en = -1.f;
+  for (int k = lane; k < Kf; k += 32) {
+    float n1 = 0.f;
+    for (int m = 0; m < MP; ++m) {
+      const float2 b = F32[k * MP + m];
+      n1 = __fadd_rn(n1, __fsqrt_rn(__fmaf_rn(b.x, b.x, __fmul_rn(b.y, b.y))));
+    }
+    const float e = __fmul_rn(n1, n1);
+    if (k < Kn) {
+      em = __fadd_rn(em, e);
+      ee = __fmaf_rn(w32[k], e, ee);
+    }
+    if (k == kphd) ep = e;
+    if (k == kmn) en = e;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    em = __fadd_rn(em, __shfl_xor_sync(0xffffffffu, em, off));
+    ee = __fadd_rn(ee, __shfl_xor_sync(0xffffffffu, ee, off));
+    ep = fmaxf(ep, __shfl_xor_sync(0xffffffffu, ep, off));
+    en = fmaxf(en, __shfl_xor_sync(0xffffffffu, en, off));
+  }
+  thr[kRoMusic] = __fmul_rn(kRefineC, em);
+  thr[kRoEv] = __fmul_rn(kRefineC, ee);
+  if (kphd >= 0) thr[kRoPhd] = __fmul_rn(kRefineC, ep);
+  if (kmn >= 0) thr[kRoMn] = __fmul_rn(kRefineC, en);
+}
+
 template <int MP>
 __device__ __forceinline__ void set_threshold(const float2 *Bs, const ScanJob &j, ScanShared &sh) {
   if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    float em = 0.f, ee = 0.f;
-    for (int k = lane; k < j.Kf; k += 32) {
-      float n1 = 0.f;
-      for (int m = 0; m < MP; ++m) {
-        float2 b = Bs[k * MP + m];
-        n1 += sqrtf(b.x * b.x + b.y * b.y);
-      }
-      const float e = n1 * n1;
-      if (k < j.Kn) {
-        em += e;
-        ee += sh.w32[k] * e;
-      }
-      if (k == j.kphd) sh.thr[kRoPhd] = kRefineC * e;
-      if (k == j.kmn) sh.thr[kRoMn] = kRefineC * e;
-    }
+    float thr[4] = {0.f, 0.f, 0.f, 0.f};
+    job_thresholds<MP>(Bs, sh.w32, j.Kf, j.Kn, j.kphd, j.kmn, thr);
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      em += __shfl_xor_sync(0xffffffffu, em, off);
-      ee += __shfl_xor_sync(0xffffffffu, ee, off);
-    }
-    if (lane == 0) {
-      sh.thr[kRoMusic] = kRefineC * em;
-      sh.thr[kRoEv] = kRefineC * ee;
+      for (int r = 0; r < 4; ++r) sh.thr[r] = thr[r];
       sh.nflag = 0;
     }
   }
@@ -296,9 +311,14 @@ __device__ __forceinline__ void store_row(float *P, int L, int k0, const float (
 // Contracts the PT x MP phasor block a (points k0 .. k0+PT-1 of a job, those < L) with the factor
 // and writes the readouts. Points where any readout falls below its refinement threshold are
 // queued for drain_refinements_src (or, on queue overflow, re-evaluated in place from src).
-template <int MP, int PT, class Src>
+// kExt: the EV weights and thresholds come from w32x / thrx instead of sh, and every queued point
+// also records `tag` in tags[] (the grid-shared scan queues the points of several problems).
+template <int MP, int PT, class Src, bool kExt = false>
 __device__ __forceinline__ void contract_points(const float2 *Bs, const ScanJob &j, const float2 (&a)[PT][MP], int L,
-                                                int k0, ScanShared &sh, const Src &src) {
+                                                int k0, ScanShared &sh, const Src &src, const float *w32x = nullptr,
+                                                const float *thrx = nullptr, uint8_t *tags = nullptr, int tag = 0) {
+  const float *w32 = kExt ? w32x : sh.w32;
+  const float *thr_ = kExt ? thrx : sh.thr;
   float dm[PT], de[PT], dp[PT], dn[PT], n[PT];
 #pragma unroll
   for (int q = 0; q < PT; ++q) dm[q] = de[q] = dp[q] = dn[q] = n[q] = 0.f;
@@ -330,7 +350,7 @@ __device__ __forceinline__ void contract_points(const float2 *Bs, const ScanJob 
   // E_n columns: MUSIC and EV sums (PHD, when present, reads the last of them)
   for (int k = 0; k < Kn; ++k) {
     column(k);
-    const float w = sh.w32[k];
+    const float w = w32[k];
 #pragma unroll
     for (int q = 0; q < PT; ++q) {
       dm[q] += n[q];
@@ -359,7 +379,7 @@ __device__ __forceinline__ void contract_points(const float2 *Bs, const ScanJob 
   float out[PT];
 #define DOA_READOUT(R, DEN)                                                   \
   if (j.P[R]) {                                                               \
-    const float thr = sh.thr[R];                                              \
+    const float thr = thr_[R];                                                \
     _Pragma("unroll") for (int q = 0; q < PT; ++q) {                          \
       out[q] = __frcp_rn(fmaxf(DEN[q], FLT_MIN));                              \
       flag[q] = flag[q] || DEN[q] < thr;                                      \
@@ -377,25 +397,24 @@ __device__ __forceinline__ void contract_points(const float2 *Bs, const ScanJob 
     pos[q] = -1;
     if (k0 + q < L && flag[q]) {
       pos[q] = atomicAdd(&sh.nflag, 1);
-      if (pos[q] < kFlagCap) sh.flags[pos[q]] = k0 + q;
+      if (pos[q] < kFlagCap) {
+        sh.flags[pos[q]] = k0 + q;
+        if (kExt) tags[pos[q]] = (uint8_t)tag;
+      }
     }
   }
   // queue overflow (more than kFlagCap small denominators before a drain): refine in place
 #pragma unroll
   for (int q = 0; q < PT; ++q)
-    if (pos[q] >= kFlagCap) refine_point_thread_src(j, k0 + q, src, sh.w32);
+    if (pos[q] >= kFlagCap) refine_point_thread_src(j, k0 + q, src, w32);
 }
 
-// Evaluates the local points k0 .. k0+PT-1 (those < L) of one job. S may alias a P row of a
-// single-readout job: each thread reads its own phase steps before it writes its own outputs.
-// Points where any readout falls below its refinement threshold are queued for drain_refinements.
+// Steering phasors of the points k0 .. k0+PT-1 (those < L; the others get phase 0) from their
+// 32-bit phase steps: a_m, m = 4i + r: a_{4i} and a_r (r = 1..3) from their exact integer phases,
+// the rest as the product a_{4i} a_r (one FP32 complex multiply of two polynomial phasors).
 template <int MP, int PT>
-__device__ __forceinline__ void scan_points(const float2 *Bs, const ScanJob &j, const uint32_t *S, int L, int k0,
-                                            ScanShared &sh) {
-  // Steering phasors a_m, m = 4i + r: a_{4i} and a_r (r = 1..3) from their exact integer phases,
-  // the rest as the product a_{4i} a_r (one FP32 complex multiply of two polynomial phasors).
+__device__ __forceinline__ void ula_phasors(const uint32_t *S, int L, int k0, float2 (&a)[PT][MP]) {
   static_assert(MP % 4 == 0, "MP is a multiple of 4");
-  float2 a[PT][MP];
 #pragma unroll
   for (int q = 0; q < PT; ++q) {
     const uint32_t step = (k0 + q < L) ? S[k0 + q] : 0u;
@@ -413,6 +432,16 @@ __device__ __forceinline__ void scan_points(const float2 *Bs, const ScanJob &j, 
       }
     }
   }
+}
+
+// Evaluates the local points k0 .. k0+PT-1 (those < L) of one job. S may alias a P row of a
+// single-readout job: each thread reads its own phase steps before it writes its own outputs.
+// Points where any readout falls below its refinement threshold are queued for drain_refinements.
+template <int MP, int PT>
+__device__ __forceinline__ void scan_points(const float2 *Bs, const ScanJob &j, const uint32_t *S, int L, int k0,
+                                            ScanShared &sh) {
+  float2 a[PT][MP];
+  ula_phasors<MP, PT>(S, L, k0, a);
   contract_points<MP, PT>(Bs, j, a, L, k0, sh, UlaSource{&j});
 }
 

@@ -20,6 +20,7 @@ PHD, MUSIC, EV, MN = 0, 1, 2, 3
 FP32, BF16, BF16X3, FP16X3 = 0, 1, 2, 3
 EIG_DOUBLE_FLOAT, EIG_FP64 = 0, 1
 FLAG_POLISH_PEAKS = 1
+FLAG_COV_CUDA_CORE = 2
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ERANK, ENONFINITE, ETIMEOUT = range(8)
 NOALLOC_SCRATCH_BYTES = 4 << 20
 BATCH_STAGES = 5
@@ -295,35 +296,40 @@ def make_problem(X: torch.Tensor, d: int, alg_mask: int, g: Grid, P: torch.Tenso
                  prec: int = FP32, features: Optional[torch.Tensor] = None,
                  B_out: Optional[torch.Tensor] = None, eig_prec: int = 0, polish: bool = False,
                  geom: Optional[Geometry] = None, peak_angle: Optional[torch.Tensor] = None,
-                 order_est: Optional[torch.Tensor] = None, root_angle: Optional[torch.Tensor] = None) -> Problem:
+                 order_est: Optional[torch.Tensor] = None, root_angle: Optional[torch.Tensor] = None,
+                 cov_cuda_core: bool = False) -> Problem:
     """Descriptor of one problem; the tensors must outlive every solve that uses it. With geom the
-    problem is a 2-D scan: g is the azimuth grid, P holds nalg x (Le x La) floats."""
+    problem is a 2-D scan: g is the azimuth grid, P holds nalg x (Le x La) floats. cov_cuda_core
+    selects the compensated CUDA-core covariance instead of the tensor-core one (M <= 16)."""
     assert X.dtype == torch.complex64 and X.dim() == 2 and X.stride(1) == 1
     M, N = X.shape
     return Problem(_dev(X), _dev(P), _dev(peak_idx), _dev(peak_val), _dev(peak_count), _dev(evals), g,
                    M, N, X.stride(0), d, alg_mask, prec, _dev(features), _dev(B_out), eig_prec,
-                   FLAG_POLISH_PEAKS if polish else 0, geom if geom is not None else Geometry(None, 0.0, 0.0, 0, 0),
+                   (FLAG_POLISH_PEAKS if polish else 0) | (FLAG_COV_CUDA_CORE if cov_cuda_core else 0), geom if geom is not None else Geometry(None, 0.0, 0.0, 0, 0),
                    _dev(peak_angle), _dev(order_est), _dev(root_angle))
 
 
 class Tuning(ctypes.Structure):
     """doa_tuning: per-M-bucket launch shapes (0 = default)."""
-    _fields_ = [("scan_pt", ctypes.c_int32 * 4), ("eig_mats", ctypes.c_int32 * 4)]
+    _fields_ = [("scan_pt", ctypes.c_int32 * 4), ("eig_mats", ctypes.c_int32 * 4), ("scan_group", ctypes.c_int32 * 4)]
 
 
 class BatchPlan:
     """Host plan bytes, their device copy, and the workspace size (doa_batch_plan).
 
     scan_pt: None or 4 ints (grid points per scan thread for M <= 8, 16, 32, 64; 0 = default).
-    eig_mats: None or 4 ints (matrices per Jacobi warp per bucket; 0 = default)."""
+    eig_mats: None or 4 ints (matrices per Jacobi warp per bucket; 0 = default).
+    scan_group: None or 4 ints (problems sharing a grid scanned together per bucket; 1 = each alone;
+    0 = default)."""
 
     def __init__(self, problems: Sequence[Problem], device: str = "cuda", scan_pt: Optional[Sequence[int]] = None,
-                 eig_mats: Optional[Sequence[int]] = None):
+                 eig_mats: Optional[Sequence[int]] = None, scan_group: Optional[Sequence[int]] = None):
         arr = (Problem * len(problems))(*problems)
         tun = None
-        if scan_pt is not None or eig_mats is not None:
+        if scan_pt is not None or eig_mats is not None or scan_group is not None:
             tun = Tuning((ctypes.c_int32 * 4)(*[int(v) for v in (scan_pt or (0, 0, 0, 0))]),
-                         (ctypes.c_int32 * 4)(*[int(v) for v in (eig_mats or (0, 0, 0, 0))]))
+                         (ctypes.c_int32 * 4)(*[int(v) for v in (eig_mats or (0, 0, 0, 0))]),
+                         (ctypes.c_int32 * 4)(*[int(v) for v in (scan_group or (0, 0, 0, 0))]))
         tun_ptr = None if tun is None else ctypes.cast(ctypes.pointer(tun), ctypes.c_void_p)
         n = lib().doa_batch_plan_bytes(arr, len(problems))
         ws = ctypes.c_size_t(0)
@@ -339,6 +345,7 @@ class BatchPlan:
         hdr = self.host[:256].view(np.int32)
         self.scan_pt = [int(v) for v in hdr[self.header_index("scan_pt"):][:4]]
         self.eig_mats = [int(v) for v in hdr[self.header_index("eig_mats"):][:4]]
+        self.scan_group = [int(v) for v in self.host[:1024].view(np.int32)[116:120]]
         self.dev = torch.from_numpy(self.host).to(device)
         self.problems = arr
 
@@ -348,7 +355,7 @@ class BatchPlan:
         order = {"magic": 0, "nprob": 1, "njobs": 2, "ngrids": 3, "ncov": 4, "nreduce": 5, "eig_count": 6,
                  "scan_jobs": 10, "scan_tiles": 14, "scan_pt": 22, "eig_mats": 58, "cov_first": 62, "tc_jobs": 67,
                  "npolish": 74, "geo_jobs": 76, "ngeo_grids": 96, "nrefine": 100, "nroots": 101,
-                 "ngeo_steer": 104}
+                 "ngeo_steer": 104, "ncovtc": 108, "covtc_flag_off": 114}
         return order[field]
 
     def launches(self) -> int:
@@ -360,8 +367,27 @@ class BatchPlan:
         scan_b = sum(int(c) > 0 for c in h[10:14]) + int(h[67] > 0) + sum(int(c) > 0 for c in h[76:80])
         ngeo = sum(int(c) for c in h[76:80])
         peaks = int(ngeo < int(h[1])) + int(ngeo > 0) + (2 if int(h[74]) > 0 else 0)
-        return (int(h[3] > 0) + int(h[96] > 0) + int(h[104] > 0) + cov + eig_b + scan_b + peaks + int(h[100] > 0)
-                + int(h[101] > 0))
+        covtc = int(h[108] > 0) + int(h[109] > 0)
+        covtc += int(covtc > 0)                                # the fixup kernel after them
+        return (int(h[3] > 0) + int(h[96] > 0) + int(h[104] > 0) + cov + covtc + eig_b + scan_b + peaks
+                + int(h[100] > 0) + int(h[101] > 0))
+
+    def covariance(self, ws: torch.Tensor, i: int) -> torch.Tensor:
+        """Problem i's covariance R (M x M complex128) in the workspace after a solve (a view)."""
+        off_prob = int(self.host[:512][120:128].view(np.int64)[0])
+        rec = off_prob + i * (ctypes.sizeof(Problem) + 96)
+        r64 = int(self.host[rec + ctypes.sizeof(Problem):rec + ctypes.sizeof(Problem) + 8].view(np.int64)[0])
+        M = int(self.problems[i].M)
+        return ws[r64:r64 + 16 * M * M].view(torch.complex128).view(M, M)
+
+    def covtc_marks(self, ws: torch.Tensor) -> torch.Tensor:
+        """The tensor-core covariance's per-problem marks from the workspace after a solve (0: done on
+        the tensor cores; 1: a sample outside the scaling range; 2: a bounded wait ran out; marked
+        problems were recomputed by the CUDA-core fixup)."""
+        h = self.host[:512]
+        n = int(h[432:440].view(np.int32).sum())
+        off = int(h[456:464].view(np.int64)[0])
+        return ws[off:off + 4 * n].view(torch.int32)
 
 
 def doa_solve_batch(plan: BatchPlan, ws: torch.Tensor, status: torch.Tensor, stage_events=None,

@@ -83,17 +83,46 @@ def test_batch_plan_layout(libdoa):
     assert bad.value == -1
     hdr = buf[:64].view(np.int32)
     assert hdr[0] == 0x444F4131            # magic
-    assert list(hdr[1:6]) == [3, 4 + 1 + 2, 2, 4 + 1 + 3, 2]   # nprob, njobs, ngrids, ncov, nreduce
-    # workspace: 32- and 64-bit phase tables per grid, then per problem R, the
-    # covariance partials and one scan factor (M x (M+1) complex128 + M EV weights), each
-    # allocation rounded up to 256 bytes
-    def factor(M):
-        return M * (M + 1) * 16 + M * 8
-    need = (18001 + 1801) * 12 + (16 * 16 * 16) * (1 + 4) + factor(16) + (8 * 8 * 16) + factor(8) \
+    # nprob, njobs, ngrids, ncov, nreduce: problems with M <= 16 take the tensor-core covariance,
+    # so only the M = 33 problem has CUDA-core chunk items (3) and a partial-sum reduction
+    assert list(hdr[1:6]) == [3, 4 + 1 + 2, 2, 3, 1]
+    full = buf.view(np.int32)
+    assert list(full[108:110]) == [1, 1]   # ncovtc: one problem with M <= 8, one with 8 < M <= 16
+    off0, off1 = (int(v) for v in buf[440:456].view(np.int64))
+    assert buf[off0:off0 + 4].view(np.int32)[0] == 1 and buf[off1:off1 + 4].view(np.int32)[0] == 0
+    # workspace: 32- and 64-bit phase tables per grid, one int32 mark per tensor-core problem, then
+    # per problem R, the covariance partials (CUDA-core problems with more than one chunk) and one
+    # scan factor (M x (M+1) complex128 + M EV weights), each allocation rounded up to 256 bytes
+    def factor(M):   # FP64 factor and EV weights, then the FP32 copy (padded rows), w32, thresholds
+        mp = 8 if M <= 8 else 16 if M <= 16 else 32 if M <= 32 else 64
+        return (M * (M + 1) * 16 + M * 8 + 15) // 16 * 16 + (M + 1) * mp * 8 + mp * 4 + 16
+    need = (18001 + 1801) * 12 + 8 + (16 * 16 * 16) + factor(16) + (8 * 8 * 16) + factor(8) \
         + (33 * 33 * 16) * (1 + 3) + factor(33)
     assert ws.value >= need and ws.value < need + 256 * 12
     # too small a buffer
     assert libdoa.lib().doa_batch_plan(arr, 3, None, buf.ctypes.data, n - 1, ctypes.byref(ws), None) == libdoa.ENOMEM
+
+
+def test_batch_plan_covariance_forms(libdoa):
+    """The tensor-core covariance takes M <= 16 problems with a 16-byte aligned X, an even ldx and
+    N <= 2^21, longest first; DOA_FLAG_COV_CUDA_CORE and the other problems keep the CUDA-core items."""
+    import numpy as np
+    probs = [_prob(libdoa, N=1000), _prob(libdoa, N=5000), _prob(libdoa, N=3000, flags=libdoa.FLAG_COV_CUDA_CORE),
+             _prob(libdoa, M=12, N=2000, X=0x100008), _prob(libdoa, M=12, N=2000, ldx=2001),
+             _prob(libdoa, M=4, N=300, d=2), _prob(libdoa, M=16, N=(1 << 21) + 2, ldx=(1 << 21) + 2)]
+    arr = (libdoa.Problem * len(probs))(*probs)
+    n = libdoa.lib().doa_batch_plan_bytes(arr, len(probs))
+    buf = np.zeros(n, np.uint8)
+    ws = ctypes.c_size_t(0)
+    assert libdoa.lib().doa_batch_plan(arr, len(probs), None, buf.ctypes.data, n, ctypes.byref(ws), None) == 0
+    full = buf.view(np.int32)
+    assert list(full[108:110]) == [1, 2]
+    off0, off1 = (int(v) for v in buf[440:456].view(np.int64))
+    assert list(buf[off0:off0 + 4].view(np.int32)) == [5]
+    assert list(buf[off1:off1 + 8].view(np.int32)) == [1, 0]          # N = 5000 before N = 1000
+    # CUDA-core chunks: 3000 (flag), 2000 (misaligned X), 2000 (odd ldx), 2^21 + 2 (too long)
+    chunks = 3 + 2 + 2 + ((1 << 21) + 2 + 1023) // 1024
+    assert full[4] == chunks and full[5] == 4
 
 
 @pytest.mark.parametrize("field,value", [("M", 1), ("M", 65), ("d", 16), ("d", -1), ("N", 0), ("ldx", 100),

@@ -53,6 +53,45 @@ def test_tile_shapes_give_identical_spectra(env):
         assert np.array_equal(a, b)
 
 
+def test_grid_shared_scan_is_bit_identical(env):
+    """Problems that share a grid are scanned in groups (one steering generation per tile for the
+    whole group). Every M bucket, every algorithm subset, groups of 2 and 32 with ragged last
+    groups and a grid used by one problem only: each spectrum and peak set is bit for bit the one
+    of the per-problem scan (groups of 1), which the parity tests hold to the oracle."""
+    torch, doa = env
+    Ms = [4, 8, 12, 16, 24, 32, 40, 64]
+    tensors, probs = [], []
+    for i in range(70):
+        M = Ms[i % len(Ms)]
+        step = 0.1 if i % 5 else 0.25            # two shared grids ...
+        if i == 69:
+            step = 0.3                           # ... and one grid of a single problem
+        inst = synth.custom(M, 1 + i % 3, 700 + 13 * i, None, 10.0, step, seed=7300 + i)
+        mask = 1 + i % 15
+        nalg = bin(mask).count("1")
+        X = torch.from_numpy(inst.X).cuda()
+        P = torch.empty(nalg * inst.L, dtype=torch.float32, device="cuda")
+        idx = torch.full((nalg * inst.d,), -1, dtype=torch.int32, device="cuda")
+        val = torch.zeros(nalg * inst.d, dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(nalg, dtype=torch.int32, device="cuda")
+        tensors.append((X, P, idx, val, cnt))
+        probs.append(doa.make_problem(X, inst.d, mask, doa.grid(inst.lo, inst.step, inst.L), P, idx, val, cnt))
+    outs = []
+    for group in (1, 2, 32):
+        plan = doa.BatchPlan(probs, scan_group=[group] * 4)
+        assert plan.scan_group == [group] * 4
+        ws = doa.workspace(plan)
+        status = torch.full((plan.nprob,), -1, dtype=torch.int32, device="cuda")
+        doa.doa_solve_batch(plan, ws, status)
+        torch.cuda.synchronize()
+        assert np.all(status.cpu().numpy() == 0)
+        outs.append([[t[k].cpu().numpy().copy() for k in (1, 2, 4)] for t in tensors])
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y)
+
+
 def test_graph_replay_matches_direct_call_and_oracle(env):
     torch, doa = env
     insts, tensors, probs = _uneven(torch, doa, n=32)
