@@ -834,12 +834,14 @@ def run_learned(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 scan, bf16 network", "data": "synthetic (GPU Philox, Eq. 1)",
         "config": {"workload": f"learned proposal: {n} test instances M=16, d in U{{1..6}}, SNR U[-5,20] dB, "
                                f"angles U[-80,80] sep 3 deg, N=2048, 0.001 deg grid (L=180001), MUSIC; +-2 deg "
-                               f"windows (d+1 proposals), full-grid fallback", "train_instances": args.train,
+                               f"windows (d+1 proposals), judge on the 0.1 deg full-grid spectrum, full-grid "
+                               f"fallback", "train_instances": args.train,
                    "epochs": args.epochs},
         "solves_per_s": n / (ms_l / 1e3),
         "plain": {"ms_per_step": ms_p, "points_per_s": full_pts / (ms_p / 1e3), "solves_per_s": n / (ms_p / 1e3)},
         "speedup_vs_plain": ms_p / ms_l,
         "agreement_with_full_grid": float(same.mean()), "fallback_rate": float(inf.fallback.mean()),
+        "judge_fallback_rate": float(inf.judged.mean()),
         "points_evaluated_ratio": full_pts / inf.points,
         "training": {"data_s": t_gen, "train_s": t_train, "adam_steps": steps_train,
                      "loss_first_last": [hist[0], hist[-1]]},

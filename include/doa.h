@@ -42,7 +42,7 @@ extern "C" {
 typedef enum {
   DOA_OK = 0,
   DOA_EINVAL = 1,      /* bad argument (size, null or misaligned pointer, unknown enum)     */
-  DOA_ENOMEM = 2,      /* caller-provided workspace too small                                */
+  DOA_ENOMEM = 2,      /* caller-provided workspace, or the library's own scratch, too small */
   DOA_ECUDA = 3,       /* a CUDA launch or runtime call failed                               */
   DOA_ENOCONV = 4,     /* Jacobi sweep cap reached                                           */
   DOA_ERANK = 5,       /* EV with a non-positive noise eigenvalue, MN with e1^H P_n e1 == 0 */
@@ -112,9 +112,11 @@ doa_status doa_covariance(const float *X, int M, int N, int ldx, float *R, doubl
                           void *stream);
 
 /*
- * Covariance for callers that cannot allocate: same computation and result as doa_covariance
- * (compensated FP32 accumulation, FP64 output; chunk sums combined in chunk order), but with no
- * allocation and no caller workspace. The paper has no counterpart.
+ * Covariance for callers that cannot allocate: the accuracy of doa_covariance with DOA_FP32 (exact
+ * FP32 products accumulated in compensated double-float, FP64 sums, about 2^-44 relative), with no
+ * allocation and no caller workspace. It splits the snapshots into 1024-snapshot chunks added in
+ * chunk order by a second kernel, where doa_covariance splits them over up to 8 cluster CTAs, so
+ * the two agree to that accuracy, not bit for bit. The paper has no counterpart.
  *   Who needs it: code that must not call cudaMalloc once running -- a fixed-memory real-time
  *   processing loop (cudaMalloc can synchronise the device and take driver locks), a host
  *   framework that forbids allocation after start-up, or a caller without its own allocator.
@@ -215,6 +217,37 @@ doa_status doa_peaks2d(const float *P, int La, int Le, int wrap_az, int d, int *
 doa_status doa_model_order(const double *evals, int M, int N, int *mdl, int *aic, void *stream);
 
 /*
+ * Step-2 of Table 2 as an SVD of the snapshot matrix X itself (the paper's Step-2 is a Jacobi SVD,
+ * Sec. 4.2), R = X X^H / N never formed: one-sided Jacobi (Hestenes) on the M rows of X. Rows
+ * y_p, y_q are rotated, Y <- J^H Y and U <- U J, by the Hermitian Jacobi rotation of
+ * doa_noise_subspace built from alpha = ||y_p||^2, beta = ||y_q||^2, gamma = y_p y_q^H; pairs in
+ * row-cyclic order; a pair is rotated when |gamma| > tol sqrt(alpha beta); the iteration stops
+ * after the first sweep that rotates nothing. Then X = U S V^H, and the eigenvalues of R are
+ * S_k^2 / N with eigenvectors the columns of U. Small singular values keep their relative
+ * accuracy (R's eigenvalues below ~1e-16 of the largest do not).
+ * GPU form: the rows live in an FP64 copy Y of X in ws; each sweep is one pass over Y on all SMs
+ * that applies the previous sweep's rotations and forms the Gram matrix Y Y^H in FP64, then the
+ * sweep's rotations run on that Gram matrix in one CTA (its pair entries are the rotated Gram
+ * entries, formed afresh from the rows once per sweep).
+ *   X          : M x N snapshots, row-major with row stride ldx (>= N) elements: complex64
+ *                (x_c128 = 0, 8-byte aligned) or complex128 (x_c128 = 1, 16-byte aligned).
+ *   tol        : rotation threshold (> 0; 1e-15 is the usual choice). max_sweeps: 1..1000.
+ *   evals      : M device doubles, descending (equal values in index order).
+ *   U          : M x M complex128, column-major (ld M): column k is the singular vector of evals[k].
+ *   info       : one device int32: the sweep count, or -DOA_ENOCONV when max_sweeps sweeps still
+ *                rotated (outputs then hold the last sweep's Gram diagonal and rotations).
+ *   ws         : device scratch of doa_svd_data_ws_bytes(M, N) bytes, 16-byte aligned (about
+ *                16 M N bytes: the FP64 rows, plus the partial Gram matrices); DOA_ENOMEM if
+ *                ws_bytes is smaller. The call enqueues 2 * max_sweeps kernels; those after
+ *                convergence return at once.
+ * Errors: DOA_EINVAL for M outside [2, 64], N < 1, ldx < N, a NULL or misaligned pointer, or a
+ * bad tol / max_sweeps.
+ */
+size_t doa_svd_data_ws_bytes(int M, int N);
+doa_status doa_svd_data(const void *X, int x_c128, int M, int N, int ldx, double tol, int max_sweeps,
+                        double *evals, double *U, int *info, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * Root form of the ULA scan (root-MUSIC for the MUSIC factor; any factor B works the same way): on
  * |z| = 1, z = e^{j pi sin theta}, ||B^H a||^2 = sum_{l=-(M-1)}^{M-1} c_l z^l with
  * c_l = sum_k sum_n B_nk conj(B_{n+l,k}); the roots of the degree-(2M-2) polynomial z^{M-1} D(z)
@@ -253,9 +286,10 @@ doa_status doa_refine_peaks2d(const double *B, int M, int K, doa_grid az, doa_ge
 
 /*
  * FMA issue-rate probe: `blocks` CTAs of 256 threads, each thread 8 independent chains of `iters`
- * dependent FMAs in FP32 (fp64 = 0) or FP64 (fp64 = 1); *flops (host) receives the flop count of
- * the launch (2 per FMA). out: device buffer of blocks x 256 floats / doubles (the chain sums).
- * The caller times the launch (events on `stream`) to get FLOP/s.
+ * dependent FMAs: mode (fp64) 0 = FP32 FFMA, 1 = FP64 DFMA, 2 = paired FP32 (fma.rn.f32x2, two FMAs
+ * per instruction); *flops (host) receives the flop count of the launch (2 per FMA). out: device
+ * buffer of blocks x 256 floats (doubles for mode 1), the chain sums. The caller times the launch
+ * (events on `stream`) to get FLOP/s.
  */
 doa_status doa_probe_fma(int fp64, int blocks, int iters, void *out, double *flops, void *stream);
 
@@ -512,6 +546,27 @@ doa_status doa_scan_windows(const double *B, int M, const int32_t *K, const int3
                             int nrows, int dmax, doa_grid fine, const int32_t *win_first, int width, int full,
                             uint32_t *S, float *Pwin, int32_t *idx, float *val, int32_t *count,
                             int32_t *fallback, void *stream);
+
+/*
+ * Judge of the learned proposal against the plain full-grid method. Every local maximum of the
+ * row's coarse full-grid spectrum Pc (the plain MUSIC scan on `coarse`, e.g. 0.1 deg, computed for
+ * the whole batch) marks where a fine-grid peak can lie; where no learned window covers the fine
+ * points within jwidth / 2 of it, a judge window of jwidth fine points centred on it is scanned
+ * (the same points, bit for bit, as the full fine-grid scan). fallback[b] is set to 1 (never
+ * cleared) when the row has fewer than d[b] selected peaks, more than 16 uncovered maxima, or a
+ * judge-window point at least as high as its weakest selected peak: then a full-grid peak at least
+ * that high lies outside every learned window and the row must be rescanned on the full grid.
+ *   B, M, K, d : factors as for doa_scan_windows (M <= 16), batch rows.
+ *   Pc         : batch x coarse.L floats.  win_first, dmax, width: the learned windows.
+ *   val, count : the windowed peaks (batch x dmax values, batch counts) from doa_scan_windows.
+ *   judge_first: batch x 16 int32 (written: judge window starts, -1 unused).
+ *   S          : fine.L uint32 scratch;  Pjudge: batch x 16 x jwidth float scratch.
+ */
+doa_status doa_proposal_judge(const double *B, int M, const int32_t *K, const int32_t *d, int batch,
+                              const float *Pc, doa_grid coarse, doa_grid fine, const int32_t *win_first,
+                              int dmax, int width, const float *val, const int32_t *count, int jwidth,
+                              int32_t *judge_first, uint32_t *S, float *Pjudge, int32_t *fallback,
+                              void *stream);
 
 #ifdef __cplusplus
 }

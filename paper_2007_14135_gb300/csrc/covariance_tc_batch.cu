@@ -27,13 +27,16 @@
 // written to the workspace as FP64 (full Hermitian matrix, zero imaginary diagonal).
 //
 // Roles (one persistent CTA per SM, static round-robin over the problems, longest first):
-//   warps 0-3  producers: slice one stage (64 snapshots) into the operand ring (128B-swizzled,
+//   warps 0-7  producers: slice one stage (64 snapshots) into the operand ring (128B-swizzled,
 //              K-major); the first stage of a problem also fixes its scaling unit;
-//   warp 4     one thread: TMA bulk copies (cp.async.bulk) of each stage's M rows into a staging
-//              ring (rows 528 bytes apart, so the producers' 16-byte loads hit distinct banks);
-//   warp 5     one thread: the MMAs, one accumulation window (15 stages) per TMEM buffer (two
-//              buffers), committed to the operand ring and to the buffer's mbarrier;
-//   warps 6-9  TMEM readout (warp w reads lanes 32 (w % 4) ..), int64 sums, per-problem finalize.
+//   warps 8-11 TMEM readout (warp w reads lanes 32 (w % 4) ..), int64 sums, per-problem finalize;
+//   warp 13    one thread: TMA bulk copies (cp.async.bulk) of 256 snapshots of each of the M rows
+//              per staging stage (one copy per row: the copy engine's cost is per request, so few
+//              large requests keep enough bytes in flight), rows 2064 bytes apart so that the
+//              producers' 16-byte loads hit distinct banks; each staging stage feeds four operand
+//              stages;
+//   warp 12    one thread: the MMAs, one accumulation window (15 stages) per TMEM buffer (two
+//              buffers), committed to the operand ring and to the buffer's mbarrier.
 // A sample beyond the scaling unit's range (or a non-finite one) marks the problem; a problem that
 // times out in a bounded wait marks every problem of its CTA. Marked problems are recomputed by the
 // compensated CUDA-core kernel (covariance_fixup) launched right after this one.
@@ -47,18 +50,49 @@ namespace {
 
 using namespace tc;
 
-constexpr int kCbSnap = 64;          // snapshots per stage (64 BF16 = one 128-byte operand row)
-constexpr int kCbStg = 8;            // staging ring depth (about 66 KB of reads in flight per SM)
+constexpr int kCbSnap = 64;          // snapshots per operand stage (64 BF16 = one 128-byte operand row)
+constexpr int kCbStgSnap = 256;      // snapshots per staging stage (one bulk copy of 2 KB per row)
+constexpr int kCbSub = kCbStgSnap / kCbSnap;
+constexpr int kCbStg = 3;            // staging ring depth (99 KB of reads in flight per SM at M = 16)
 constexpr int kCbOps = 4;            // operand ring depth
-constexpr int kCbWin = 15;           // stages per exact accumulation window (960 snapshots)
-constexpr int kCbRowPitch = 528;     // staging bytes per element row (512 + 16)
-constexpr int kCbThreads = 320;
+constexpr int kCbWin = 15;           // operand stages per exact accumulation window (960 snapshots)
+constexpr int kCbRowPitch = 2064;    // staging bytes per element row (2048 + 16)
+// Warp w issues from SM sub-partition w % 4. The readout warps take one per sub-partition (warp
+// w reads TMEM lanes 32 (w % 4) ..); the MMA issuer shares sub-partition 0 with the readout of
+// slice 4 (two blocks), away from the readout of slice 0 (five blocks, sub-partition 1).
+constexpr int kCbProdWarps = 8;     // producer warps 0-7
+constexpr int kCbReadWarp0 = 8;     // readout warps 8-11
+constexpr int kCbMmaWarp = 12, kCbTmaWarp = 13;
+constexpr int kCbThreads = 32 * 14;
 constexpr int kCbRing = 8;           // scaling-unit ring (producers -> readout)
 constexpr int kCbAccCols = 256;      // TMEM columns per accumulator buffer
 
 // Slicing constants 1.5 * 2^(23 - 7k): adding and subtracting one rounds to a multiple of 2^(-7k).
 __device__ __forceinline__ float slice_magic(int k) {
   return __uint_as_float((uint32_t)(127 + 23 - 7 * k) << 23) * 1.5f;
+}
+
+// Paired FP32 arithmetic (two IEEE round-to-nearest operations per instruction), on the values of
+// two consecutive snapshots held as one 64-bit register pair.
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+  return (uint64_t)__float_as_uint(lo) | ((uint64_t)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float lo2(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float hi2(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
 }
 
 template <int MP>
@@ -70,7 +104,7 @@ struct CbShape<16> {
   static constexpr int kBlock = 32;
   static constexpr int kBStart = 32;                 // B starts at storage row 32 (s0)
   static constexpr int kN = 160;
-  static constexpr int kSN = 8;                      // snapshots per producer task
+  static constexpr int kSN = 4;                      // snapshots per producer task
   __host__ __device__ static constexpr int block_of(int k) { return k == 4 ? 0 : (k == 5 ? 5 : k + 1); }
   __host__ __device__ static constexpr int a_slice(int blk) { return blk == 0 ? 4 : blk - 1; }   // A row block
   __host__ __device__ static constexpr int b_slice(int cb) { return cb == 4 ? 5 : cb; }          // B col block
@@ -87,17 +121,18 @@ struct CbShape<8> {
   static constexpr int kBlock = 16;
   static constexpr int kBStart = 0;
   static constexpr int kN = 48;
-  static constexpr int kSN = 4;
+  static constexpr int kSN = 2;
   __host__ __device__ static constexpr int block_of(int k) { return k; }
   __host__ __device__ static constexpr int a_slice(int blk) { return blk; }                      // 6, 7: padding
   __host__ __device__ static constexpr int b_slice(int cb) { return cb; }
+  static constexpr int kBBlocks = 3;
   __host__ __device__ static constexpr bool designated(int i, int j) { return i <= 5 && i + j <= 5 && i >= j; }
 };
 
 template <int MP>
 struct CbLayout {
   using S = CbShape<MP>;
-  static constexpr int kStgBytes = MP * kCbRowPitch;
+  static constexpr int kStgBytes = MP * kCbRowPitch;   // one staging stage (a multiple of 128 bytes)
   static constexpr int kOpBytes = S::kRows * 128;
   static constexpr int kOffOp = 0;                                        // 1024-aligned stages
   static constexpr int kOffStg = kOffOp + kCbOps * kOpBytes;
@@ -115,7 +150,7 @@ struct CbShared {
   uint32_t tmem;
   int abort;
   int eexp[kCbRing];          // scaling exponent k of the problem in ring slot (or INT_MIN: marked)
-  float red[2][4];            // producers' first-stage maxima (double-buffered by problem parity)
+  float red[2][kCbProdWarps];  // producers' first-stage maxima (double-buffered by problem parity)
 };
 
 __device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
@@ -150,11 +185,24 @@ __device__ __forceinline__ bool cb_wait(uint32_t mbar, uint32_t parity, volatile
 
 // Wait of a whole warp: every lane waits (bounded) and the outcome is made warp-uniform, so a lane
 // that gave up never diverges from the others into a warp-collective instruction.
+// Lane 0 polls; once the phase has completed every lane tests it once (non-blocking) for its own
+// acquire of the data the phase guards. The phase cannot move on meanwhile: its next completion
+// needs an arrival from this warp.
 __device__ __forceinline__ bool warp_wait(uint32_t mbar, uint32_t parity, volatile int *abort) {
-  return __all_sync(0xffffffffu, cb_wait(mbar, parity, abort));
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) ok = cb_wait(mbar, parity, abort) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok) return false;
+  uint32_t done = 0;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return __all_sync(0xffffffffu, done != 0);
 }
 
-// Warp-granular barrier on an mbarrier of count 4 (one arrival per warp), bounded like every wait.
+// Warp-granular barrier on an mbarrier with one arrival per participating warp, bounded like every wait.
 __device__ __forceinline__ bool warp_bar(uint64_t *bar, uint32_t parity, volatile int *abort) {
   __syncwarp();
   if ((threadIdx.x & 31) == 0) arrive(smem_u32(bar));
@@ -185,116 +233,46 @@ __device__ __forceinline__ void tmem_ld<32>(uint32_t addr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Integer n of a TMEM value n * 2^(-7L), |n| < 2^22: adding 1.5 * 2^23 leaves n + 2^22 in the low
-// mantissa bits.
-template <int L>
-__device__ __forceinline__ int exact_int(uint32_t bits) {
-  const float v = __fmaf_rn(__uint_as_float(bits), __uint_as_float((uint32_t)(127 + 7 * L) << 23), 12582912.0f);
-  return (int)(__float_as_uint(v) - 0x4B400000u);
-}
-// n in units of 2^-28 of w^2, times 2 for an off-diagonal pair (L = 5 rounded to the unit).
-template <int L, bool kOff>
-__device__ __forceinline__ long long to_acc(int n) {
-  constexpr int sh = 28 - 7 * L + (kOff ? 1 : 0);
-  if constexpr (sh >= 0)
-    return (long long)n << sh;
-  else
-    return (long long)((n + (1 << (-sh - 1))) >> (-sh));
-}
-
-// Adds block (i, j) of the accumulator columns [MP re | MP im] of this thread's row to U'.
-template <int MP, int I, int J>
-__device__ __forceinline__ void add_block(const uint32_t (&v)[2 * MP], bool im_row, long long (&ure)[MP],
-                                          long long (&uim)[MP]) {
-  constexpr int L = I + J;
+// One designated block (i, j) of this thread's accumulator row, columns [MP Re | MP Im] of the
+// B slice: each value is n 2^(-7L), L = i + j, |n| < 2^22, so adding 1.5 * 2^23 to n leaves it in
+// the low mantissa bits; it enters U' in units of 2^-28 of w^2, doubled for an off-diagonal pair
+// (shift 28 - 7L + off; level 5 is rounded to that unit). mul = 2^(7L), or 0 for a lane that does
+// not need the block (its n is then 0). Re row: Re += RR, Im -= RI; Im row: Re += II, Im += IR.
+template <int MP>
+__device__ __forceinline__ void add_block(const uint32_t (&v)[2 * MP], float mul, int sh, bool im_row,
+                                          long long (&ure)[MP], long long (&uim)[MP]) {
+  const int rsh = sh < 0 ? -sh : 0, lsh = sh > 0 ? sh : 0;
+  const int half = rsh > 0 ? 1 << (rsh - 1) : 0;
 #pragma unroll
   for (int b = 0; b < MP; ++b) {
-    const long long xr = to_acc<L, I != J>(exact_int<L>(v[b]));        // (row plane) x Re b
-    const long long xi = to_acc<L, I != J>(exact_int<L>(v[MP + b]));   // (row plane) x Im b
-    // Re row: Re += RR, Im -= RI.  Im row: Re += II, Im += IR.
+    const int nr = (int)(__float_as_uint(__fmaf_rn(__uint_as_float(v[b]), mul, 12582912.0f)) - 0x4B400000u);
+    const int ni = (int)(__float_as_uint(__fmaf_rn(__uint_as_float(v[MP + b]), mul, 12582912.0f)) - 0x4B400000u);
+    const long long xr = (long long)((nr + half) >> rsh) << lsh;   // (row plane) x Re b
+    const long long xi = (long long)((ni + half) >> rsh) << lsh;   // (row plane) x Im b
     ure[b] += im_row ? xi : xr;
     uim[b] += im_row ? xr : -xi;
   }
 }
 
-template <int MP, int I>
-__device__ __forceinline__ void read_row_slice(uint32_t taddr, bool im_row, long long (&ure)[MP], long long (&uim)[MP]) {
-  using S = CbShape<MP>;
-#pragma unroll
-  for (int cb = 0; cb < S::kBBlocks; ++cb) {
-    constexpr int dummy = 0;
-    (void)dummy;
-    const int J = S::b_slice(cb);
-    if (!S::designated(I, J)) continue;
-    uint32_t v[2 * MP];
-    tmem_ld<2 * MP>(taddr + (uint32_t)(cb * S::kBlock), v);
-    // J is a compile-time value of the unrolled loop; dispatch it to the template
-    switch (J) {
-      case 0: if constexpr (S::designated(I, 0)) add_block<MP, I, 0>(v, im_row, ure, uim); break;
-      case 1: if constexpr (S::designated(I, 1)) add_block<MP, I, 1>(v, im_row, ure, uim); break;
-      case 2: if constexpr (S::designated(I, 2)) add_block<MP, I, 2>(v, im_row, ure, uim); break;
-      case 3: if constexpr (S::designated(I, 3)) add_block<MP, I, 3>(v, im_row, ure, uim); break;
-      case 5: if constexpr (S::designated(I, 5)) add_block<MP, I, 5>(v, im_row, ure, uim); break;
-      default: break;
-    }
-  }
-}
-
-// Rows of slices 6 and 7 (MP = 8 padding) are never read; a warp whose two half-warps hold
-// different slices loads every block either needs (tcgen05.ld is warp-collective) and each half
-// keeps its own.
+// Adds one window of this thread's accumulator row to U'. The thread's A slice i comes from its
+// TMEM lane; the B slices are walked at run time (one copy of the unrolled block code) and loaded
+// with one warp-collective tcgen05.ld when any lane of the warp needs the block.
 template <int MP>
 __device__ __forceinline__ void read_window(uint32_t taddr, int quarter, int lane, long long (&ure)[MP],
-                                            long long (&uim)[MP]);
-
-template <>
-__device__ __forceinline__ void read_window<16>(uint32_t taddr, int quarter, int lane, long long (&ure)[16],
-                                                long long (&uim)[16]) {
-  const bool im_row = lane >= 16;
-  switch (quarter) {   // A row block = TMEM lane quarter: s4, s0, s1, s2
-    case 0: read_row_slice<16, 4>(taddr, im_row, ure, uim); break;
-    case 1: read_row_slice<16, 0>(taddr, im_row, ure, uim); break;
-    case 2: read_row_slice<16, 1>(taddr, im_row, ure, uim); break;
-    default: read_row_slice<16, 2>(taddr, im_row, ure, uim); break;
-  }
-}
-
-template <int I0>
-__device__ __forceinline__ void read_pair8(uint32_t taddr, int lane, long long (&ure)[8], long long (&uim)[8]) {
-  // lanes 0-15: slice I0, lanes 16-31: slice I0 + 1; within a slice block rows 0-7 Re, 8-15 Im
-  const bool hi = lane >= 16;
-  const bool im_row = (lane & 8) != 0;
-#pragma unroll
-  for (int cb = 0; cb < 3; ++cb) {
-    const bool need0 = CbShape<8>::designated(I0, cb), need1 = CbShape<8>::designated(I0 + 1, cb);
-    if (!need0 && !need1) continue;
-    uint32_t v[16];
-    tmem_ld<16>(taddr + (uint32_t)(cb * 16), v);
-    switch (cb) {
-      case 0:
-        if (!hi) { if constexpr (CbShape<8>::designated(I0, 0)) add_block<8, I0, 0>(v, im_row, ure, uim); }
-        else { if constexpr (CbShape<8>::designated(I0 + 1, 0)) add_block<8, I0 + 1, 0>(v, im_row, ure, uim); }
-        break;
-      case 1:
-        if (!hi) { if constexpr (CbShape<8>::designated(I0, 1)) add_block<8, I0, 1>(v, im_row, ure, uim); }
-        else { if constexpr (CbShape<8>::designated(I0 + 1, 1)) add_block<8, I0 + 1, 1>(v, im_row, ure, uim); }
-        break;
-      default:
-        if (!hi) { if constexpr (CbShape<8>::designated(I0, 2)) add_block<8, I0, 2>(v, im_row, ure, uim); }
-        else { if constexpr (CbShape<8>::designated(I0 + 1, 2)) add_block<8, I0 + 1, 2>(v, im_row, ure, uim); }
-        break;
-    }
-  }
-}
-
-template <>
-__device__ __forceinline__ void read_window<8>(uint32_t taddr, int quarter, int lane, long long (&ure)[8],
-                                               long long (&uim)[8]) {
-  switch (quarter) {   // A row blocks 2q, 2q + 1 = slices 2q, 2q + 1 (quarter 3: padding)
-    case 0: read_pair8<0>(taddr, lane, ure, uim); break;
-    case 1: read_pair8<2>(taddr, lane, ure, uim); break;
-    case 2: read_pair8<4>(taddr, lane, ure, uim); break;
-    default: break;
+                                            long long (&uim)[MP]) {
+  using S = CbShape<MP>;
+  const int blk = (32 * quarter + lane) / S::kBlock;        // A row block of this lane
+  const int i = S::a_slice(blk);                            // MP = 8: blocks 6, 7 are padding (i > 5)
+  const bool im_row = (lane % S::kBlock) >= MP;
+  for (int cb = 0; cb < CbShape<MP>::kBBlocks; ++cb) {
+    const int j = S::b_slice(cb);
+    const bool need = i <= 5 && S::designated(i, j);
+    if (!__any_sync(0xffffffffu, need)) continue;
+    uint32_t v[2 * MP];
+    tmem_ld<2 * MP>(taddr + (uint32_t)(cb * S::kBlock), v);
+    const int L = need ? i + j : 0;   // a lane without the block adds n = 0
+    const float mul = need ? __uint_as_float((uint32_t)(127 + 7 * L) << 23) : 0.f;
+    add_block<MP>(v, mul, 28 - 7 * L + (need && i != j ? 1 : 0), im_row, ure, uim);
   }
 }
 
@@ -322,15 +300,15 @@ __global__ void __launch_bounds__(kCbThreads, 1) covariance_tc_batch_kernel(cons
       for (int i = 0; i < n; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b + i)), "r"(cnt));
     };
     init(sh.full, kCbStg, 1);
-    init(sh.empty, kCbStg, 4);
-    init(sh.opfull, kCbOps, 4);
+    init(sh.empty, kCbStg, kCbProdWarps);
+    init(sh.opfull, kCbOps, kCbProdWarps);
     init(sh.opempty, kCbOps, 1);
     init(sh.accfull, 2, 1);
     init(sh.accempty, 2, 4);
     init(sh.efull, kCbRing, 1);
     init(sh.eempty, kCbRing, 4);
     init(&sh.fin, 1, 1);
-    init(sh.pred, 2, 4);
+    init(sh.pred, 2, kCbProdWarps);
     init(sh.rb, 2, 4);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sh.abort = 0;
@@ -345,11 +323,17 @@ __global__ void __launch_bounds__(kCbThreads, 1) covariance_tc_batch_kernel(cons
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = sh.tmem;
 
-  if (warp < 4) {
+  if (warp < kCbProdWarps) {
     // ---------------------------------------------------------------- producers
-    constexpr int SN = S::kSN;                   // snapshots per task; tasks: MP rows x (64 / SN)
-    const int m = tid % MP, c = tid / MP;        // row, chunk (a quarter-warp spans 8 rows)
-    uint32_t g = 0;                              // stage counter
+    // tasks: MP rows x (64 / SN) chunks of SN snapshots, one per thread. A quarter-warp takes 8
+    // consecutive rows of one chunk (its 16-byte staging loads then fall on distinct banks, the
+    // rows being 528 bytes apart), and the two quarter-warps of a half-warp take two neighbouring
+    // chunks (its 8-byte operand stores fill both halves of each swizzled 16-byte slot).
+    constexpr int SN = S::kSN;
+    const int qw = tid >> 3, r8 = tid & 7;
+    const int m = MP == 16 ? r8 + 8 * ((qw >> 1) & 1) : r8;
+    const int c = MP == 16 ? (qw & 1) + 2 * (qw >> 2) : qw;
+    uint32_t g = 0, gs = 0;                      // operand and staging stage counters
     int kth = 0;                                 // problem counter of this CTA
     for (int pi = blockIdx.x; pi < count && !*abort; pi += gridDim.x, ++kth) {
       const PlanProblem &pp = probs[list[pi]];
@@ -357,32 +341,28 @@ __global__ void __launch_bounds__(kCbThreads, 1) covariance_tc_batch_kernel(cons
       const float2 *X = reinterpret_cast<const float2 *>(pp.p.X);
       const int nst = (N + kCbSnap - 1) / kCbSnap;
       float scale = 0.f;
-      bool bad = false;
-      for (int s = 0; s < nst; ++s, ++g) {
-        const int ss = g % kCbStg, os = g % kCbOps;
-        if (!warp_wait(smem_u32(&sh.full[ss]), (g / kCbStg) & 1u, abort)) break;
-        // this task's SN snapshots of row m (zeros past N and for rows >= M)
+      bool bad = false, live = true;
+      for (int s = 0; s < nst && live; ++s, ++g) {
+        const int sub = s % kCbSub, ss = gs % kCbStg, os = g % kCbOps;
+        if (sub == 0 && !warp_wait(smem_u32(&sh.full[ss]), (gs / kCbStg) & 1u, abort)) break;
+        // this task's SN snapshots of row m (zeros past N and for rows >= M); t counts snapshots
+        // from the start of the staging stage, whose first cb arrived by bulk copy
         float re[SN], im[SN];
-        const int t0 = s * kCbSnap, cnt = min(kCbSnap, N - t0), cb = cnt & ~1;
-        const float *stg = reinterpret_cast<const float *>(sm + Lay::kOffStg + ss * ((Lay::kStgBytes + 127) / 128 * 128) +
-                                                           m * kCbRowPitch) + 2 * c * SN;
+        const int t0 = (s - sub) * kCbSnap, cnt = min(kCbStgSnap, N - t0), cb = cnt & ~1;
+        const float *stg = reinterpret_cast<const float *>(sm + Lay::kOffStg + ss * Lay::kStgBytes +
+                                                           m * kCbRowPitch) + 2 * (sub * kCbSnap + c * SN);
 #pragma unroll
         for (int q = 0; q < SN / 2; ++q) {
-          const int t = c * SN + 2 * q;
+          const int t = sub * kCbSnap + c * SN + 2 * q;
           float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
           if (m < M) {
             if (t + 1 < cb) {
               v = *reinterpret_cast<const float4 *>(stg + 4 * q);
             } else {
-              if (t < cnt) {
-                const float2 a = t < cb ? *reinterpret_cast<const float2 *>(stg + 4 * q) : X[(size_t)m * ldx + t0 + t];
+              if (t < cnt) {   // t >= cb: the odd last snapshot, outside the bulk copy
+                const float2 a = X[(size_t)m * ldx + t0 + t];
                 v.x = a.x;
                 v.y = a.y;
-              }
-              if (t + 1 < cnt) {
-                const float2 a = X[(size_t)m * ldx + t0 + t + 1];
-                v.z = a.x;
-                v.w = a.y;
               }
             }
           }
@@ -391,8 +371,11 @@ __global__ void __launch_bounds__(kCbThreads, 1) covariance_tc_batch_kernel(cons
           re[2 * q + 1] = v.z;
           im[2 * q + 1] = v.w;
         }
-        __syncwarp();
-        if (lane == 0) arrive(smem_u32(&sh.empty[ss]));
+        if (sub == kCbSub - 1 || s == nst - 1) {   // the staging stage has been read: release it
+          __syncwarp();
+          if (lane == 0) arrive(smem_u32(&sh.empty[ss]));
+          ++gs;
+        }
         if (s == 0) {
           // scaling unit from the first stage's largest |component|: 2^(k-1) <= mx < 2^k,
           // u0 = 2^(k-5), so |w| = |x| / u0 <= 64 for |x| <= 2^(k+1) (one bit of headroom)
@@ -403,7 +386,9 @@ __global__ void __launch_bounds__(kCbThreads, 1) covariance_tc_batch_kernel(cons
           for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
           if (lane == 0) sh.red[kth & 1][warp] = mx;
           if (!warp_bar(&sh.pred[kth & 1], (uint32_t)((kth >> 1) & 1), abort)) break;
-          mx = fmaxf(fmaxf(sh.red[kth & 1][0], sh.red[kth & 1][1]), fmaxf(sh.red[kth & 1][2], sh.red[kth & 1][3]));
+          mx = 0.f;
+#pragma unroll
+          for (int w = 0; w < kCbProdWarps; ++w) mx = fmaxf(mx, sh.red[kth & 1][w]);
           const int eb = (int)((__float_as_uint(mx) >> 23) & 0xffu);
           bad = eb < 4 || eb > 254;                       // zero, subnormal, tiny or non-finite
           const int k = eb - 126;
@@ -416,40 +401,44 @@ __global__ void __launch_bounds__(kCbThreads, 1) covariance_tc_batch_kernel(cons
           }
         }
         // operand slot free (the MMAs of its previous stage are done)
-        if (g >= (uint32_t)kCbOps && !warp_wait(smem_u32(&sh.opempty[os]), (g / kCbOps - 1) & 1u, abort)) break;
+        if (g >= (uint32_t)kCbOps && !warp_wait(smem_u32(&sh.opempty[os]), (g / kCbOps - 1) & 1u, abort)) {
+          live = false;
+          break;
+        }
         uint8_t *op = sm + Lay::kOffOp + os * Lay::kOpBytes;
-        float rr[SN], ri[SN];
+        // w = x * scale, pairs of consecutive snapshots in 64-bit registers
+        const uint64_t sc2 = pack2(scale, scale);
+        uint64_t wr[SN / 2], wi[SN / 2];
 #pragma unroll
-        for (int q = 0; q < SN; ++q) {
-          rr[q] = __fmul_rn(re[q], scale);
-          ri[q] = __fmul_rn(im[q], scale);
-          bad |= !(fabsf(rr[q]) <= 64.f) || !(fabsf(ri[q]) <= 64.f);
+        for (int q = 0; q < SN / 2; ++q) {
+          wr[q] = mul2(pack2(re[2 * q], re[2 * q + 1]), sc2);
+          wi[q] = mul2(pack2(im[2 * q], im[2 * q + 1]), sc2);
+          bad |= !(fabsf(lo2(wr[q])) <= 64.f) || !(fabsf(hi2(wr[q])) <= 64.f) || !(fabsf(lo2(wi[q])) <= 64.f) ||
+                 !(fabsf(hi2(wi[q])) <= 64.f);
         }
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-          const float C = slice_magic(k);
+          const float Cf = slice_magic(k);
+          const uint64_t C = pack2(Cf, Cf);
           uint32_t pr[SN / 2], pim[SN / 2];
 #pragma unroll
-          for (int q = 0; q < SN; q += 2) {
-            const float s0 = __fsub_rn(__fadd_rn(rr[q], C), C), s1 = __fsub_rn(__fadd_rn(rr[q + 1], C), C);
-            const float t0_ = __fsub_rn(__fadd_rn(ri[q], C), C), t1 = __fsub_rn(__fadd_rn(ri[q + 1], C), C);
+          for (int q = 0; q < SN / 2; ++q) {
+            const uint64_t sr = sub2(add2(wr[q], C), C), si = sub2(add2(wi[q], C), C);
             if (k < 5) {
-              rr[q] = __fsub_rn(rr[q], s0);
-              rr[q + 1] = __fsub_rn(rr[q + 1], s1);
-              ri[q] = __fsub_rn(ri[q], t0_);
-              ri[q + 1] = __fsub_rn(ri[q + 1], t1);
+              wr[q] = sub2(wr[q], sr);
+              wi[q] = sub2(wi[q], si);
             }
-            const __nv_bfloat162 a = __floats2bfloat162_rn(s0, s1), b = __floats2bfloat162_rn(t0_, t1);
-            pr[q / 2] = *reinterpret_cast<const uint32_t *>(&a);
-            pim[q / 2] = *reinterpret_cast<const uint32_t *>(&b);
+            const __nv_bfloat162 a = __floats2bfloat162_rn(lo2(sr), hi2(sr)), b = __floats2bfloat162_rn(lo2(si), hi2(si));
+            pr[q] = *reinterpret_cast<const uint32_t *>(&a);
+            pim[q] = *reinterpret_cast<const uint32_t *>(&b);
           }
           const int rre = S::block_of(k) * S::kBlock + m, rim = rre + MP;
-          if constexpr (SN == 8) {
-            *reinterpret_cast<uint4 *>(op + sw128(rre, 8 * c)) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
-            *reinterpret_cast<uint4 *>(op + sw128(rim, 8 * c)) = make_uint4(pim[0], pim[1], pim[2], pim[3]);
-          } else {
+          if constexpr (SN == 4) {
             *reinterpret_cast<uint2 *>(op + sw128(rre, 4 * c)) = make_uint2(pr[0], pr[1]);
             *reinterpret_cast<uint2 *>(op + sw128(rim, 4 * c)) = make_uint2(pim[0], pim[1]);
+          } else {
+            *reinterpret_cast<uint32_t *>(op + sw128(rre, 2 * c)) = pr[0];
+            *reinterpret_cast<uint32_t *>(op + sw128(rim, 2 * c)) = pim[0];
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -459,21 +448,21 @@ __global__ void __launch_bounds__(kCbThreads, 1) covariance_tc_batch_kernel(cons
       // a sample outside the unit's range (or a non-finite one): recompute the problem elsewhere
       if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&flags[pi], 1);
     }
-  } else if (warp == 4) {
+  } else if (warp == kCbTmaWarp) {
     // ---------------------------------------------------------------- TMA: staging copies
     if (lane == 0) {
-      uint32_t g = 0;
+      uint32_t g = 0;   // staging stages issued
       for (int pi = blockIdx.x; pi < count && !*abort; pi += gridDim.x) {
         const PlanProblem &pp = probs[list[pi]];
         const int M = pp.p.M, N = pp.p.N, ldx = pp.p.ldx;
         const float2 *X = reinterpret_cast<const float2 *>(pp.p.X);
-        const int nst = (N + kCbSnap - 1) / kCbSnap;
+        const int nstg = (N + kCbStgSnap - 1) / kCbStgSnap;
         flags[pi] = 0;   // ordered before the producers' marks by the first stage's mbarrier
-        for (int s = 0; s < nst; ++s, ++g) {
+        for (int st = 0; st < nstg; ++st, ++g) {
           const int ss = g % kCbStg;
           if (g >= (uint32_t)kCbStg && !cb_wait(smem_u32(&sh.empty[ss]), (g / kCbStg - 1) & 1u, abort)) break;
-          const int t0 = s * kCbSnap, cb = min(kCbSnap, N - t0) & ~1;
-          const uint32_t dst = smem_u32(sm + Lay::kOffStg + ss * ((Lay::kStgBytes + 127) / 128 * 128));
+          const int t0 = st * kCbStgSnap, cb = min(kCbStgSnap, N - t0) & ~1;
+          const uint32_t dst = smem_u32(sm + Lay::kOffStg + ss * Lay::kStgBytes);
           arrive_tx(smem_u32(&sh.full[ss]), (uint32_t)(M * cb * 8));
           if (cb > 0)
             for (int m = 0; m < M; ++m)
@@ -486,7 +475,7 @@ __global__ void __launch_bounds__(kCbThreads, 1) covariance_tc_batch_kernel(cons
           mbar_wait(smem_u32(&sh.full[q % kCbStg]), (q / kCbStg) & 1u);
     }
     __syncwarp();
-  } else if (warp == 5) {
+  } else if (warp == kCbMmaWarp) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       const uint32_t idesc = inst_desc(1, S::kN);
@@ -521,7 +510,7 @@ __global__ void __launch_bounds__(kCbThreads, 1) covariance_tc_batch_kernel(cons
   } else {
     // ---------------------------------------------------------------- TMEM readout and finalize
     const int q = warp & 3;                                    // TMEM lane quarter
-    const int rt = tid - 6 * 32;                               // 0..127
+    const int rt = tid - 32 * kCbReadWarp0;                    // 0..127
     uint32_t gw = 0;
     int kth = 0;
     for (int pi = blockIdx.x; pi < count && !*abort; pi += gridDim.x, ++kth) {

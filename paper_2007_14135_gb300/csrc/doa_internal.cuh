@@ -185,10 +185,11 @@ __host__ __device__ inline int scan_mp(int M) { return 8 << m_bucket(M); }   // 
 
 // A problem's scan factor area: F (M x (M+1) complex128, column-major) and the EV weights (M
 // doubles), then at fac32_off(M) the FP32 copy the grid-shared scan reads: F32 (M+1 columns of
-// scan_mp(M) float2, rows >= M zero), w32 (scan_mp(M) floats) and the four readout thresholds.
+// scan_mp(M) elements (bx, bx, by, by), rows >= M zero), w32 (scan_mp(M) floats) and the four
+// readout thresholds.
 __host__ __device__ inline int64_t fac32_off(int M) { return ((int64_t)M * (M + 1) * 16 + (int64_t)M * 8 + 15) / 16 * 16; }
 __host__ __device__ inline int64_t factor_bytes(int M) {
-  return fac32_off(M) + (int64_t)(M + 1) * scan_mp(M) * 8 + (int64_t)scan_mp(M) * 4 + 16;
+  return fac32_off(M) + (int64_t)(M + 1) * scan_mp(M) * 16 + (int64_t)scan_mp(M) * 4 + 16;
 }
 
 struct PlanJob {          // one (problem, algorithm) pair: a spectrum and its peaks

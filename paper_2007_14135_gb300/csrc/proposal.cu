@@ -300,6 +300,90 @@ __global__ void __launch_bounds__(pk::kPeakThreads) window_peaks_kernel(const fl
   }
 }
 
+// Judge of the learned proposal against the plain full-grid method (one warp per row): every
+// local maximum of the row's coarse full-grid spectrum (interior: strictly above its left
+// neighbour, at least its right one; the ends when they are at least their neighbour) marks where
+// a fine-grid peak can lie. One that no learned window covers with a margin of jwidth / 2 fine
+// points on each side gets a judge window of jwidth points centred on it (at most kJudgeMax per
+// row; more marks the row for the full-grid fallback).
+constexpr int kJudgeMax = 16;
+
+__global__ void judge_windows_kernel(const float *Pc, int Lc, double clo, double cstep, double flo, double fstep, int Lf,
+                                     const int32_t *win_first, int dmax, int width, int jwidth, int batch,
+                                     int32_t *judge_first, int32_t *fallback) {
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (r >= batch) return;
+  const float *p = Pc + (size_t)r * Lc;
+  int n = 0;
+  bool over = false;
+  for (int k0 = 0; k0 < Lc; k0 += 32) {
+    const int k = k0 + lane;
+    bool cand = false;
+    if (k < Lc) {
+      const float v = p[k];
+      const bool left = k == 0 || v > p[k - 1];
+      const bool right = k == Lc - 1 || v >= p[k + 1];
+      cand = (k == 0 ? v >= p[min(1, Lc - 1)] : left) && right;
+    }
+    bool need = false;
+    int first = 0;
+    if (cand) {
+      const double theta = __dadd_rn(clo, __dmul_rn((double)k, cstep));
+      const long long c = llrint((theta - flo) / fstep);
+      long long f = c - jwidth / 2;
+      if (f > (long long)Lf - jwidth) f = (long long)Lf - jwidth;
+      if (f < 0) f = 0;
+      first = (int)f;
+      need = true;
+      for (int w = 0; w < dmax && need; ++w) {
+        const int a = win_first[(size_t)r * dmax + w];
+        if (a >= 0 && a <= first && first + jwidth <= a + width) need = false;
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    const int pos = n + __popc(m & ((1u << lane) - 1u));
+    if (need) {
+      if (pos < kJudgeMax)
+        judge_first[(size_t)r * kJudgeMax + pos] = first;
+      else
+        over = true;
+    }
+    n += __popc(m);
+  }
+  for (int w = n + lane; w < kJudgeMax; w += 32) judge_first[(size_t)r * kJudgeMax + w] = -1;
+  if (__any_sync(0xffffffffu, over) && lane == 0) fallback[r] = 1;
+}
+
+// One CTA per row: the row falls back to the full grid when it has fewer than d selected peaks, or
+// when any point of its judge windows reaches its weakest selected peak (a peak of the full-grid
+// spectrum at least that high lies outside every learned window).
+__global__ void judge_compare_kernel(const float *Pj, const int32_t *judge_first, int jwidth, int Lf, const float *val,
+                                     const int32_t *count, const int32_t *d, int dmax, int32_t *fallback) {
+  __shared__ float s_w;
+  __shared__ int s_hit;
+  const int r = blockIdx.x;
+  if (threadIdx.x == 0) {
+    const int c = count[r];
+    float w = FLT_MAX;
+    for (int a = 0; a < c && a < dmax; ++a) w = fminf(w, val[(size_t)r * dmax + a]);
+    s_w = w;
+    s_hit = c < d[r];
+  }
+  __syncthreads();
+  const float W = s_w;
+  bool hit = false;
+  for (int w = 0; w < kJudgeMax && !s_hit; ++w) {
+    const int first = judge_first[(size_t)r * kJudgeMax + w];
+    if (first < 0) break;
+    const int len = min(jwidth, Lf - first);
+    const float *P = Pj + ((size_t)r * kJudgeMax + w) * (size_t)jwidth;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) hit = hit || P[k] >= W;
+    if (__syncthreads_or(hit) && threadIdx.x == 0) s_hit = 1;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && s_hit) fallback[r] = 1;
+}
+
 __global__ void phase_table_kernel(double lo, double step, int L, uint32_t *S) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < L) S[k] = grid_phase_step(lo, step, k);
@@ -361,5 +445,37 @@ extern "C" doa_status doa_scan_windows(const double *B, int M, const int32_t *K,
         full, S, Pwin, tiles);
   window_peaks_kernel<<<nrows, pk::kPeakThreads, 0, s>>>(Pwin, rows, d, dmax, fine.L, win_first, width, full, idx, val,
                                                    count, fallback);
+  return cudaGetLastError() == cudaSuccess ? DOA_OK : DOA_ECUDA;
+}
+
+extern "C" doa_status doa_proposal_judge(const double *B, int M, const int32_t *K, const int32_t *d, int batch,
+                                         const float *Pc, doa_grid coarse, doa_grid fine, const int32_t *win_first,
+                                         int dmax, int width, const float *val, const int32_t *count, int jwidth,
+                                         int32_t *judge_first, uint32_t *S, float *Pjudge, int32_t *fallback,
+                                         void *stream) {
+  if (!B || !K || !d || !Pc || !win_first || !val || !count || !judge_first || !S || !Pjudge || !fallback ||
+      batch < 1 || M < 2 || M > 16 || dmax < 1 || dmax > 64 || coarse.L < 3 || fine.L < 3 ||
+      !(coarse.step_deg > 0.0) || !(fine.step_deg > 0.0) || width < 3 || width > fine.L || jwidth < 3 ||
+      jwidth > fine.L)
+    return DOA_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int threads = 256, warps = threads / 32;
+  judge_windows_kernel<<<(batch + warps - 1) / warps, threads, 0, s>>>(
+      Pc, coarse.L, coarse.lo_deg, coarse.step_deg, fine.lo_deg, fine.step_deg, fine.L, win_first, dmax, width,
+      jwidth, batch, judge_first, fallback);
+  phase_table_kernel<<<(fine.L + 255) / 256, 256, 0, s>>>(fine.lo_deg, fine.step_deg, fine.L, S);
+  const int tp = kScanThreads * 2;
+  const int tiles = (jwidth + tp - 1) / tp;
+  const long long blocks = (long long)batch * kJudgeMax * tiles;
+  if (blocks > INT_MAX) return DOA_EINVAL;
+  if (M <= 8)
+    scan_windows_kernel<8, 2><<<(unsigned)blocks, kScanThreads, 0, s>>>(
+        reinterpret_cast<const double2 *>(B), M, K, nullptr, kJudgeMax, fine.lo_deg, fine.step_deg, fine.L,
+        judge_first, jwidth, 0, S, Pjudge, tiles);
+  else
+    scan_windows_kernel<16, 2><<<(unsigned)blocks, kScanThreads, 0, s>>>(
+        reinterpret_cast<const double2 *>(B), M, K, nullptr, kJudgeMax, fine.lo_deg, fine.step_deg, fine.L,
+        judge_first, jwidth, 0, S, Pjudge, tiles);
+  judge_compare_kernel<<<batch, 256, 0, s>>>(Pjudge, judge_first, jwidth, fine.L, val, count, d, dmax, fallback);
   return cudaGetLastError() == cudaSuccess ? DOA_OK : DOA_ECUDA;
 }

@@ -108,7 +108,11 @@ constexpr int kRun = 16;   // longest run (large batches); small ones use shorte
 template <int MP, int PT>
 __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t *plan, uint8_t *ws, int bucket,
                                                                   int run_len) {
-  __shared__ __align__(16) float2 Bs[(MP + 1) * MP];
+  // factor: (bx, bx, by, by) per element for the paired contraction (PT even), else (bx, by)
+  constexpr bool kPair = PT % 2 == 0;
+  __shared__ __align__(16) float Fsm[(kPair ? 4 : 2) * (MP + 1) * MP];
+  float2 *Bs = reinterpret_cast<float2 *>(Fsm);
+  float4 *Bd = reinterpret_cast<float4 *>(Fsm);
   __shared__ ScanShared sh;
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
   const int nunits = h->scan_jobs[bucket];
@@ -136,15 +140,18 @@ __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t 
         g = &grids[pp->grid_id];
         j = ula_job(*pp, *g, ws);
         __syncthreads();
-        load_job<MP>(j, Bs, sh);
+        if constexpr (kPair) load_job2<MP>(j, Bd, sh); else load_job<MP>(j, Bs, sh);
         __syncthreads();
-        set_threshold<MP>(Bs, j, sh);
+        if constexpr (kPair) set_threshold2<MP>(Bd, j, sh); else set_threshold<MP>(Bs, j, sh);
         __syncthreads();
         cur = u;
       }
       const uint32_t *S = reinterpret_cast<const uint32_t *>(ws + g->S_off);
       const int k0 = (int)(t - pp->tile_start) * TP + threadIdx.x * PT;
-      scan_points<MP, PT>(Bs, j, S, g->L, k0, sh);
+      if constexpr (kPair)
+        scan_points2<MP, PT>(Bd, j, S, g->L, k0, sh);
+      else
+        scan_points<MP, PT>(Bs, j, S, g->L, k0, sh);
     }
     drain_refinements(j, sh);   // once per run: the warps share the FP64 work of its tiles
   }
@@ -160,7 +167,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t 
 // scan. Flagged points of all the group's problems queue up with their problem's position in the
 // group and are re-evaluated in FP64 when the unit ends.
 
-// FP32 copy of each grouped problem's factor (one warp per problem): F32, w32, thresholds.
+// FP32 copy of each grouped problem's factor (one warp per problem): F32 as (bx, bx, by, by) per
+// element, w32, thresholds.
 template <int MP>
 __global__ void __launch_bounds__(kScanThreads) scan_prep_kernel(const uint8_t *plan, uint8_t *ws, int bucket) {
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
@@ -172,27 +180,31 @@ __global__ void __launch_bounds__(kScanThreads) scan_prep_kernel(const uint8_t *
   const int M = pp.p.M, Kf = pp.Kf, Kn = pp.Kn;
   const double2 *F = reinterpret_cast<const double2 *>(ws + pp.fac_off);
   const double *w = pp.Kn > 0 && pp.slot[DOA_EV] >= 0 ? reinterpret_cast<const double *>(F + M * (M + 1)) : nullptr;
-  float2 *F32 = reinterpret_cast<float2 *>(ws + pp.fac_off + fac32_off(M));
+  float4 *F32 = reinterpret_cast<float4 *>(ws + pp.fac_off + fac32_off(M));
   float *w32 = reinterpret_cast<float *>(F32 + (M + 1) * MP);
   for (int e = lane; e < Kf * MP; e += 32) {
     const int k = e / MP, m = e % MP;
-    float2 v = make_float2(0.f, 0.f);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (m < M) {
       const double2 b = F[(size_t)k * M + m];
-      v = make_float2((float)b.x, (float)b.y);
+      const float bx = (float)b.x, by = (float)b.y;
+      v = make_float4(bx, bx, by, by);
     }
     F32[e] = v;
   }
   for (int k = lane; k < Kn; k += 32) w32[k] = w ? (float)w[k] : 1.f;
   __syncwarp();
   float thr[4] = {0.f, 0.f, 0.f, 0.f};
-  job_thresholds<MP>(F32, w32, Kf, Kn, pp.kphd, pp.kmn, thr);
+  job_thresholds2<MP>(F32, w32, Kf, Kn, pp.kphd, pp.kmn, thr);
   if (lane < 4) w32[MP + lane] = thr[lane];
 }
 
 template <int MP, int PT>
-__global__ void __launch_bounds__(kScanThreads) scan_shared_kernel(const uint8_t *plan, uint8_t *ws, int bucket) {
-  __shared__ __align__(16) float2 Bs[(MP + 1) * MP];
+__global__ void __launch_bounds__(kScanThreads, 3) scan_shared_kernel(const uint8_t *plan, uint8_t *ws, int bucket) {
+  constexpr bool kPair = PT % 2 == 0;
+  __shared__ __align__(16) float Fsm[(kPair ? 4 : 2) * (MP + 1) * MP];
+  float2 *Bs = reinterpret_cast<float2 *>(Fsm);
+  float4 *Bd = reinterpret_cast<float4 *>(Fsm);
   __shared__ float w32s[MP], thrs[4];
   __shared__ uint8_t tags[kFlagCap];
   __shared__ ScanShared sh;
@@ -215,21 +227,35 @@ __global__ void __launch_bounds__(kScanThreads) scan_shared_kernel(const uint8_t
     const PlanScanGroup gr = groups[gi];
     const PlanGrid &g = grids[gr.grid_id];
     const int L = g.L, k0 = (int)(u - gr.unit_start) * TP + tid * PT;
-    float2 a[PT][MP];
-    ula_phasors<MP, PT>(reinterpret_cast<const uint32_t *>(ws + g.S_off), L, k0, a);
+    const uint32_t *S = reinterpret_cast<const uint32_t *>(ws + g.S_off);
+    float2 a[kPair ? 1 : PT][MP];
+    uint64_t ax[kPair ? PT / 2 : 1][MP], ay[kPair ? PT / 2 : 1][MP];
+    if constexpr (kPair)
+      ula_phasors2<MP, PT>(S, L, k0, ax, ay);
+    else
+      ula_phasors<MP, PT>(S, L, k0, a);
     for (int i = 0; i < gr.count; ++i) {
       const PlanProblem &pp = probs[list[gr.first + i]];
       const ScanJob j = ula_job(pp, g, ws);
       const uint8_t *f32 = ws + pp.fac_off + fac32_off(j.M);
       __syncthreads();   // the previous problem's contraction has finished reading Bs
       const float4 *src4 = reinterpret_cast<const float4 *>(f32);
-      float4 *dst4 = reinterpret_cast<float4 *>(Bs);
-      for (int e = tid; e < j.Kf * MP / 2; e += kScanThreads) dst4[e] = src4[e];
-      const float *wg = reinterpret_cast<const float *>(f32 + (size_t)(j.M + 1) * MP * 8);
+      if constexpr (kPair) {
+        for (int e = tid; e < j.Kf * MP; e += kScanThreads) Bd[e] = src4[e];
+      } else {
+        for (int e = tid; e < j.Kf * MP; e += kScanThreads) {
+          const float4 v = src4[e];
+          Bs[e] = make_float2(v.x, v.z);
+        }
+      }
+      const float *wg = reinterpret_cast<const float *>(f32 + (size_t)(j.M + 1) * MP * 16);
       for (int k = tid; k < j.Kn; k += kScanThreads) w32s[k] = wg[k];
       if (tid < 4) thrs[tid] = wg[MP + tid];
       __syncthreads();
-      contract_points<MP, PT, UlaSource, true>(Bs, j, a, L, k0, sh, UlaSource{&j}, w32s, thrs, tags, i);
+      if constexpr (kPair)
+        contract_points2<MP, PT, UlaSource, true>(Bd, j, ax, ay, L, k0, sh, UlaSource{&j}, w32s, thrs, tags, i);
+      else
+        contract_points<MP, PT, UlaSource, true>(Bs, j, a, L, k0, sh, UlaSource{&j}, w32s, thrs, tags, i);
     }
     // FP64 re-evaluation of the unit's flagged points, several per warp for small factors; the
     // queue holds the points of each problem together (problems run one after the other)
@@ -243,7 +269,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_shared_kernel(const uint8_t
         while (c1 < end && tags[c1] == tag) ++c1;
         const PlanProblem &pp = probs[list[gr.first + tag]];
         const ScanJob j = ula_job(pp, g, ws);
-        const float *wg = reinterpret_cast<const float *>(ws + pp.fac_off + fac32_off(j.M) + (size_t)(j.M + 1) * MP * 8);
+        const float *wg = reinterpret_cast<const float *>(ws + pp.fac_off + fac32_off(j.M) + (size_t)(j.M + 1) * MP * 16);
         const UlaSource src{&j};
         if (j.M <= 8 && j.Kf <= 8) {
           refine_points_subwarp<8>(j, sh.flags + c0, c1 - c0, src, wg, sh.ph[warp]);

@@ -111,6 +111,70 @@ __device__ __forceinline__ void set_threshold(const float2 *Bs, const ScanJob &j
   }
 }
 
+// Paired-FMA form of the FP32 scan (fma.rn.f32x2: two FP32 FMAs per instruction, one for each of
+// two grid points): the factor is held in shared memory as Bd[k][m] = (bx, bx, by, by), so one
+// 16-byte load gives both operand pairs of an element.
+template <int MP>
+__device__ __forceinline__ void load_job2(const ScanJob &j, float4 *Bd, ScanShared &sh) {
+  for (int e = threadIdx.x; e < j.Kf * MP; e += blockDim.x) {
+    const int k = e / MP, m = e % MP;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (m < j.M) {
+      const double2 b = j.F[(size_t)k * j.M + m];
+      const float bx = (float)b.x, by = (float)b.y;
+      v = make_float4(bx, bx, by, by);
+    }
+    Bd[e] = v;
+  }
+  for (int k = threadIdx.x; k < j.Kn; k += blockDim.x) sh.w32[k] = j.w ? (float)j.w[k] : 1.f;
+}
+
+// job_thresholds on the duplicated layout (the same FP32 values, the same arithmetic).
+template <int MP>
+__device__ __forceinline__ void job_thresholds2(const float4 *Bd, const float *w32, int Kf, int Kn, int kphd, int kmn,
+                                                float (&thr)[4]) {
+  const int lane = threadIdx.x & 31;
+  float em = 0.f, ee = 0.f, ep = -1.f, en = -1.f;
+  for (int k = lane; k < Kf; k += 32) {
+    float n1 = 0.f;
+    for (int m = 0; m < MP; ++m) {
+      const float4 b = Bd[k * MP + m];
+      n1 = __fadd_rn(n1, __fsqrt_rn(__fmaf_rn(b.x, b.x, __fmul_rn(b.z, b.z))));
+    }
+    const float e = __fmul_rn(n1, n1);
+    if (k < Kn) {
+      em = __fadd_rn(em, e);
+      ee = __fmaf_rn(w32[k], e, ee);
+    }
+    if (k == kphd) ep = e;
+    if (k == kmn) en = e;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    em = __fadd_rn(em, __shfl_xor_sync(0xffffffffu, em, off));
+    ee = __fadd_rn(ee, __shfl_xor_sync(0xffffffffu, ee, off));
+    ep = fmaxf(ep, __shfl_xor_sync(0xffffffffu, ep, off));
+    en = fmaxf(en, __shfl_xor_sync(0xffffffffu, en, off));
+  }
+  thr[kRoMusic] = __fmul_rn(kRefineC, em);
+  thr[kRoEv] = __fmul_rn(kRefineC, ee);
+  if (kphd >= 0) thr[kRoPhd] = __fmul_rn(kRefineC, ep);
+  if (kmn >= 0) thr[kRoMn] = __fmul_rn(kRefineC, en);
+}
+
+template <int MP>
+__device__ __forceinline__ void set_threshold2(const float4 *Bd, const ScanJob &j, ScanShared &sh) {
+  if (threadIdx.x < 32) {
+    float thr[4] = {0.f, 0.f, 0.f, 0.f};
+    job_thresholds2<MP>(Bd, sh.w32, j.Kf, j.Kn, j.kphd, j.kmn, thr);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) sh.thr[r] = thr[r];
+      sh.nflag = 0;
+    }
+  }
+}
+
 __device__ __forceinline__ uint64_t phase64_of_point(const ScanJob &j, int k) {
   if (j.S64) return j.S64[k];
   const double theta = __dadd_rn(j.lo, __dmul_rn((double)(k + j.kofs), j.step));
@@ -322,11 +386,14 @@ __device__ __forceinline__ void contract_points(const float2 *Bs, const ScanJob 
   float dm[PT], de[PT], dp[PT], dn[PT], n[PT];
 #pragma unroll
   for (int q = 0; q < PT; ++q) dm[q] = de[q] = dp[q] = dn[q] = n[q] = 0.f;
-  // n = |f_k^H a|^2 for the PT points; factor rows read two elements (16 bytes) at a time
+  // n = |f_k^H a|^2 for the PT points; factor rows read two elements (16 bytes) at a time.
+  // conj(b) * a = (br ar + bi ai) + j (br ai - bi ar): the imaginary part as two sums subtracted at
+  // the end of the column, the operations (and their order) of contract_points2, so every launch
+  // shape gives the same bits.
   auto column = [&](int k) {
-    float yr[PT], yi[PT];
+    float yr[PT], ya[PT], yb[PT];
 #pragma unroll
-    for (int q = 0; q < PT; ++q) yr[q] = yi[q] = 0.f;
+    for (int q = 0; q < PT; ++q) yr[q] = ya[q] = yb[q] = 0.f;
     const float4 *b2 = reinterpret_cast<const float4 *>(Bs + k * MP);
 #pragma unroll
     for (int m2 = 0; m2 < MP / 2; ++m2) {
@@ -337,14 +404,17 @@ __device__ __forceinline__ void contract_points(const float2 *Bs, const ScanJob 
         const int m = 2 * m2 + h;
 #pragma unroll
         for (int q = 0; q < PT; ++q) {
-          // conj(b) * a = (br ar + bi ai) + j (br ai - bi ar)
-          yr[q] = fmaf(bx, a[q][m].x, fmaf(by, a[q][m].y, yr[q]));
-          yi[q] = fmaf(bx, a[q][m].y, fmaf(-by, a[q][m].x, yi[q]));
+          yr[q] = __fmaf_rn(bx, a[q][m].x, __fmaf_rn(by, a[q][m].y, yr[q]));
+          ya[q] = __fmaf_rn(bx, a[q][m].y, ya[q]);
+          yb[q] = __fmaf_rn(by, a[q][m].x, yb[q]);
         }
       }
     }
 #pragma unroll
-    for (int q = 0; q < PT; ++q) n[q] = fmaf(yr[q], yr[q], yi[q] * yi[q]);
+    for (int q = 0; q < PT; ++q) {
+      const float yi = __fsub_rn(ya[q], yb[q]);
+      n[q] = __fmaf_rn(yr[q], yr[q], __fmul_rn(yi, yi));
+    }
   };
   const int Kf = j.Kf, Kn = j.Kn, kphd = j.kphd, kmn = j.kmn;
   // E_n columns: MUSIC and EV sums (PHD, when present, reads the last of them)
@@ -353,8 +423,8 @@ __device__ __forceinline__ void contract_points(const float2 *Bs, const ScanJob 
     const float w = w32[k];
 #pragma unroll
     for (int q = 0; q < PT; ++q) {
-      dm[q] += n[q];
-      de[q] = fmaf(w, n[q], de[q]);
+      dm[q] = __fadd_rn(dm[q], n[q]);
+      de[q] = __fmaf_rn(w, n[q], de[q]);
     }
   }
   if (Kn > 0 && kphd == Kn - 1) {
@@ -409,6 +479,136 @@ __device__ __forceinline__ void contract_points(const float2 *Bs, const ScanJob 
     if (pos[q] >= kFlagCap) refine_point_thread_src(j, k0 + q, src, w32);
 }
 
+// Paired FP32 arithmetic on two values in one 64-bit register pair (lo, hi).
+__device__ __forceinline__ uint64_t f2pack(float lo, float hi) {
+  return (uint64_t)__float_as_uint(lo) | ((uint64_t)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float f2lo(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float f2hi(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2sub(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// contract_points in the paired form: the PT points (PT even) are taken two at a time, ax[p][m] /
+// ay[p][m] holding Re / Im of a_m at points k0 + 2p and k0 + 2p + 1. Per element and pair, four
+// paired FMAs: yr += bx ax + by ay, yi_a += bx ay, yi_b += by ax (yi = yi_a - yi_b at the end of the
+// column), so every FMA of the contraction is half an instruction. Readouts, thresholds and the
+// refinement queue are those of contract_points.
+template <int MP, int PT, class Src, bool kExt = false>
+__device__ __forceinline__ void contract_points2(const float4 *Bd, const ScanJob &j, const uint64_t (&ax)[PT / 2][MP],
+                                                 const uint64_t (&ay)[PT / 2][MP], int L, int k0, ScanShared &sh,
+                                                 const Src &src, const float *w32x = nullptr,
+                                                 const float *thrx = nullptr, uint8_t *tags = nullptr, int tag = 0) {
+  static_assert(PT % 2 == 0, "points are paired");
+  constexpr int HP = PT / 2;
+  const float *w32 = kExt ? w32x : sh.w32;
+  const float *thr_ = kExt ? thrx : sh.thr;
+  uint64_t dm[HP], de[HP], dp[HP], dn[HP], n[HP];
+#pragma unroll
+  for (int q = 0; q < HP; ++q) dm[q] = de[q] = dp[q] = dn[q] = n[q] = 0ull;
+  auto column = [&](int k) {
+    uint64_t yr[HP], ya[HP], yb[HP];
+#pragma unroll
+    for (int q = 0; q < HP; ++q) yr[q] = ya[q] = yb[q] = 0ull;
+    const float4 *b4 = Bd + k * MP;
+#pragma unroll
+    for (int m = 0; m < MP; ++m) {
+      const float4 bb = b4[m];
+      const uint64_t bxx = f2pack(bb.x, bb.y), byy = f2pack(bb.z, bb.w);
+#pragma unroll
+      for (int q = 0; q < HP; ++q) {
+        yr[q] = f2fma(bxx, ax[q][m], f2fma(byy, ay[q][m], yr[q]));
+        ya[q] = f2fma(bxx, ay[q][m], ya[q]);
+        yb[q] = f2fma(byy, ax[q][m], yb[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < HP; ++q) {
+      const uint64_t yi = f2sub(ya[q], yb[q]);
+      n[q] = f2fma(yr[q], yr[q], f2mul(yi, yi));
+    }
+  };
+  const int Kf = j.Kf, Kn = j.Kn, kphd = j.kphd, kmn = j.kmn;
+  for (int k = 0; k < Kn; ++k) {
+    column(k);
+    const float w = w32[k];
+    const uint64_t ww = f2pack(w, w);
+#pragma unroll
+    for (int q = 0; q < HP; ++q) {
+      dm[q] = f2add(dm[q], n[q]);
+      de[q] = f2fma(ww, n[q], de[q]);
+    }
+  }
+  if (Kn > 0 && kphd == Kn - 1) {
+#pragma unroll
+    for (int q = 0; q < HP; ++q) dp[q] = n[q];
+  }
+  for (int k = Kn; k < Kf; ++k) {
+    column(k);
+    if (k == kphd) {
+#pragma unroll
+      for (int q = 0; q < HP; ++q) dp[q] = n[q];
+    }
+    if (k == kmn) {
+#pragma unroll
+      for (int q = 0; q < HP; ++q) dn[q] = n[q];
+    }
+  }
+  bool flag[PT];
+#pragma unroll
+  for (int q = 0; q < PT; ++q) flag[q] = false;
+  float out[PT];
+#define DOA_READOUT2(R, DEN)                                                  \
+  if (j.P[R]) {                                                               \
+    const float thr = thr_[R];                                                \
+    _Pragma("unroll") for (int q = 0; q < HP; ++q) {                          \
+      const float d0 = f2lo(DEN[q]), d1 = f2hi(DEN[q]);                       \
+      out[2 * q] = __frcp_rn(fmaxf(d0, FLT_MIN));                              \
+      out[2 * q + 1] = __frcp_rn(fmaxf(d1, FLT_MIN));                          \
+      flag[2 * q] = flag[2 * q] || d0 < thr;                                  \
+      flag[2 * q + 1] = flag[2 * q + 1] || d1 < thr;                          \
+    }                                                                         \
+    store_row<PT>(j.P[R], L, k0, out);                                        \
+  }
+  DOA_READOUT2(kRoPhd, dp)
+  DOA_READOUT2(kRoMusic, dm)
+  DOA_READOUT2(kRoEv, de)
+  DOA_READOUT2(kRoMn, dn)
+#undef DOA_READOUT2
+  int pos[PT];
+#pragma unroll
+  for (int q = 0; q < PT; ++q) {
+    pos[q] = -1;
+    if (k0 + q < L && flag[q]) {
+      pos[q] = atomicAdd(&sh.nflag, 1);
+      if (pos[q] < kFlagCap) {
+        sh.flags[pos[q]] = k0 + q;
+        if (kExt) tags[pos[q]] = (uint8_t)tag;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < PT; ++q)
+    if (pos[q] >= kFlagCap) refine_point_thread_src(j, k0 + q, src, w32);
+}
+
 // Steering phasors of the points k0 .. k0+PT-1 (those < L; the others get phase 0) from their
 // 32-bit phase steps: a_m, m = 4i + r: a_{4i} and a_r (r = 1..3) from their exact integer phases,
 // the rest as the product a_{4i} a_r (one FP32 complex multiply of two polynomial phasors).
@@ -443,6 +643,29 @@ __device__ __forceinline__ void scan_points(const float2 *Bs, const ScanJob &j, 
   float2 a[PT][MP];
   ula_phasors<MP, PT>(S, L, k0, a);
   contract_points<MP, PT>(Bs, j, a, L, k0, sh, UlaSource{&j});
+}
+
+// ula_phasors packed for contract_points2 (PT even).
+template <int MP, int PT>
+__device__ __forceinline__ void ula_phasors2(const uint32_t *S, int L, int k0, uint64_t (&ax)[PT / 2][MP],
+                                             uint64_t (&ay)[PT / 2][MP]) {
+  float2 a[PT][MP];
+  ula_phasors<MP, PT>(S, L, k0, a);
+#pragma unroll
+  for (int q = 0; q < PT / 2; ++q)
+#pragma unroll
+    for (int m = 0; m < MP; ++m) {
+      ax[q][m] = f2pack(a[2 * q][m].x, a[2 * q + 1][m].x);
+      ay[q][m] = f2pack(a[2 * q][m].y, a[2 * q + 1][m].y);
+    }
+}
+
+template <int MP, int PT>
+__device__ __forceinline__ void scan_points2(const float4 *Bd, const ScanJob &j, const uint32_t *S, int L, int k0,
+                                             ScanShared &sh) {
+  uint64_t ax[PT / 2][MP], ay[PT / 2][MP];
+  ula_phasors2<MP, PT>(S, L, k0, ax, ay);
+  contract_points2<MP, PT>(Bd, j, ax, ay, L, k0, sh, UlaSource{&j});
 }
 
 }  // namespace scanc

@@ -32,7 +32,8 @@ EXPORTS = ("doa_status_str", "doa_covariance", "doa_covariance_noalloc", "doa_no
            "doa_mlp_refresh", "doa_mlp_forward", "doa_mlp_backward", "doa_mlp_adam", "doa_synth_ula",
            "doa_proposal_windows", "doa_scan_windows", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices", "doa_probe_fma",
            "doa_scan_geometry", "doa_scan_geometry_ws_bytes", "doa_peaks2d", "doa_refine_peaks",
-           "doa_refine_peaks2d", "doa_model_order", "doa_root_music")
+           "doa_refine_peaks2d", "doa_model_order", "doa_root_music", "doa_proposal_judge", "doa_svd_data",
+           "doa_svd_data_ws_bytes")
 SLICE_MAXD = 64
 
 
@@ -101,10 +102,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.doa_model_order.argtypes = [vp, i, i, vp, vp, vp]
     lib.doa_root_music.argtypes = [vp, i, i, i, vp, vp, vp]
     lib.doa_refine_peaks2d.argtypes = [vp, i, i, Grid, Geometry, vp, vp, i, vp, vp]
+    lib.doa_svd_data_ws_bytes.argtypes = [i, i]
+    lib.doa_svd_data_ws_bytes.restype = sz
+    lib.doa_svd_data.argtypes = [vp, i, i, i, i, ctypes.c_double, i, vp, vp, vp, vp, sz, vp]
     for name in ("doa_covariance", "doa_covariance_noalloc", "doa_noise_subspace", "doa_scan", "doa_peaks",
                  "doa_batch_plan", "doa_solve_batch", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices", "doa_probe_fma",
-                 "doa_scan_geometry", "doa_scan_geometry_ws_bytes", "doa_peaks2d", "doa_refine_peaks",
-           "doa_refine_peaks2d", "doa_model_order", "doa_root_music"):
+                 "doa_scan_geometry", "doa_peaks2d", "doa_refine_peaks", "doa_refine_peaks2d", "doa_model_order",
+                 "doa_root_music", "doa_proposal_judge", "doa_svd_data"):
         getattr(lib, name).restype = i
     return lib
 
@@ -220,17 +224,19 @@ def doa_merge_slices(sums: Sequence[SliceSummary], d: int):
     return np.array(idx[:n], dtype=np.int32), np.array(val[:n], dtype=np.float32)
 
 
-def probe_fma_tflops(fp64: bool, device: str = "cuda", iters: int = 1 << 14, reps: int = 5) -> float:
-    """Measured FMA issue rate (TFLOP/s, best of `reps`) of FP32 or FP64 chains on every SM."""
+def probe_fma_tflops(fp64, device: str = "cuda", iters: int = 1 << 14, reps: int = 5) -> float:
+    """Measured FMA rate (TFLOP/s, best of `reps`) of FP32 (False / 0), FP64 (True / 1) or paired
+    FP32 (2: fma.rn.f32x2) chains on every SM."""
+    mode = int(fp64)
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     blocks = sms * 8
-    out = torch.empty(blocks * 256, dtype=torch.float64 if fp64 else torch.float32, device=device)
+    out = torch.empty(blocks * 256, dtype=torch.float64 if mode == 1 else torch.float32, device=device)
     flops = ctypes.c_double(0.0)
     best = 0.0
     for _ in range(reps + 1):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        _check(lib().doa_probe_fma(1 if fp64 else 0, blocks, iters, _dev(out), ctypes.byref(flops), _stream(None)),
+        _check(lib().doa_probe_fma(mode, blocks, iters, _dev(out), ctypes.byref(flops), _stream(None)),
                "doa_probe_fma")
         e1.record()
         torch.cuda.synchronize()
@@ -266,6 +272,28 @@ def doa_model_order(evals: torch.Tensor, N: int, out: torch.Tensor, stream=None)
     """MDL and AIC source-count estimates (out: 2 int32 on the device) from descending eigenvalues."""
     _check(lib().doa_model_order(_dev(evals), evals.numel(), N, _dev(out), out.data_ptr() + 4, _stream(stream)),
            "doa_model_order")
+
+
+def svd_data_ws_bytes(M: int, N: int) -> int:
+    return int(lib().doa_svd_data_ws_bytes(M, N))
+
+
+def doa_svd_data(X: torch.Tensor, evals: torch.Tensor, U: torch.Tensor, info: torch.Tensor, ws: torch.Tensor = None,
+                 tol: float = 1e-15, max_sweeps: int = 60, stream=None) -> torch.Tensor:
+    """Step-2 as a one-sided Jacobi SVD of X (M x N complex64 or complex128 on the device, unit
+    inner stride): evals (M float64, descending), U (M x M complex128; its transpose is the
+    column-major array the call writes, so U[k] is singular vector k), info (1 int32: sweeps or
+    -ENOCONV). ws: None (allocated here) or a uint8 device buffer. Returns ws."""
+    assert X.dim() == 2 and X.stride(1) == 1 and X.dtype in (torch.complex64, torch.complex128)
+    M, N = X.shape
+    assert evals.dtype == torch.float64 and U.dtype == torch.complex128 and info.dtype == torch.int32
+    need = svd_data_ws_bytes(M, N)
+    if ws is None:
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=X.device)
+    _check(lib().doa_svd_data(_dev(X), 1 if X.dtype == torch.complex128 else 0, M, N, X.stride(0), tol, max_sweeps,
+                              _dev(evals), _dev(U), _dev(info), _dev(ws), ws.numel(), _stream(stream)),
+           "doa_svd_data")
+    return ws
 
 
 def doa_refine_peaks(B: torch.Tensor, M: int, K: int, g: Grid, idx: torch.Tensor, count: torch.Tensor,
@@ -369,7 +397,9 @@ class BatchPlan:
         peaks = int(ngeo < int(h[1])) + int(ngeo > 0) + (2 if int(h[74]) > 0 else 0)
         covtc = int(h[108] > 0) + int(h[109] > 0)
         covtc += int(covtc > 0)                                # the fixup kernel after them
-        return (int(h[3] > 0) + int(h[96] > 0) + int(h[104] > 0) + cov + covtc + eig_b + scan_b + peaks
+        # grid-shared scan: a prep kernel and the scan kernel per M bucket that has groups
+        shared = 2 * sum(int(u) > 0 for u in self.host[496:528].view(np.int64))
+        return (int(h[3] > 0) + int(h[96] > 0) + int(h[104] > 0) + cov + covtc + eig_b + scan_b + shared + peaks
                 + int(h[100] > 0) + int(h[101] > 0))
 
     def covariance(self, ws: torch.Tensor, i: int) -> torch.Tensor:
@@ -524,7 +554,8 @@ def _bind_proposal(lib_):
     lib_.doa_synth_ula.argtypes = [i, i, i, vp, vp, i, vp, u64, u64, vp, vp]
     lib_.doa_proposal_windows.argtypes = [vp, vp, i, i, i, Grid, i, vp, vp]
     lib_.doa_scan_windows.argtypes = [vp, i, vp, vp, vp, i, i, Grid, vp, i, i, vp, vp, vp, vp, vp, vp, vp]
-    for n in ("doa_synth_ula", "doa_proposal_windows", "doa_scan_windows"):
+    lib_.doa_proposal_judge.argtypes = [vp, i, vp, vp, i, vp, Grid, Grid, vp, i, i, vp, vp, i, vp, vp, vp, vp, vp]
+    for n in ("doa_synth_ula", "doa_proposal_windows", "doa_scan_windows", "doa_proposal_judge"):
         getattr(lib_, n).restype = i
 
 
@@ -556,3 +587,21 @@ def doa_scan_windows(B: torch.Tensor, M: int, K: torch.Tensor, d: torch.Tensor, 
     _check(lib().doa_scan_windows(_dev(B), M, _dev(K), _dev(d), _dev(rows), n, dmax, fine, _dev(win_first), width,
                                   1 if full else 0, _dev(S), _dev(Pwin), _dev(idx), _dev(val), _dev(count),
                                   _dev(fallback), _stream(stream)), "doa_scan_windows")
+
+
+JUDGE_MAX = 16
+
+
+def doa_proposal_judge(B: torch.Tensor, M: int, K: torch.Tensor, d: torch.Tensor, Pc: torch.Tensor, coarse: Grid,
+                       fine: Grid, win_first: torch.Tensor, width: int, val: torch.Tensor, count: torch.Tensor,
+                       jwidth: int, judge_first: torch.Tensor, S: torch.Tensor, Pjudge: torch.Tensor,
+                       fallback: torch.Tensor, stream=None) -> None:
+    """Marks in `fallback` the rows whose windowed peaks may differ from the full-grid method's
+    (see include/doa.h). Pc: (batch, coarse.L) coarse spectra; judge_first: (batch, 16) int32;
+    Pjudge: (batch, 16, jwidth) float32 scratch."""
+    _bind_proposal(lib())
+    batch, dmax = win_first.shape
+    _check(lib().doa_proposal_judge(_dev(B), M, _dev(K), _dev(d), batch, _dev(Pc), coarse, fine, _dev(win_first), dmax,
+                                    width, _dev(val), _dev(count), jwidth, _dev(judge_first), _dev(S), _dev(Pjudge),
+                                    _dev(fallback), _stream(stream)), "doa_proposal_judge")
+

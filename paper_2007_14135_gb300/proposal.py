@@ -7,10 +7,13 @@ which also writes the network input (trace-normalised upper triangle of R). The 
 instance is the set of 1-degree bins that contain the plain method's d peaks, so the network
 imitates the method and the method remains the arbiter.
 
-Inference: covariance + Jacobi + features + MUSIC factor for the batch, network forward,
-doa_proposal_windows (the d best bins with 1-bin suppression -> +-2 deg windows on the 0.001 deg
-grid), doa_scan_windows over the windows, and for the rows it flags (fewer than d interior
-window maxima, or a window maximum on a window edge) the plain full-grid scan as fallback.
+Inference: covariance + Jacobi + features + MUSIC factor for the batch, with the plain MUSIC scan
+on the coarse 0.1 deg full grid, network forward, doa_proposal_windows (the d best bins with
+1-bin suppression -> +-2 deg windows on the 0.001 deg grid), doa_scan_windows over the windows,
+then the judge (doa_proposal_judge): every coarse local maximum that no window covers gets a
++-0.2 deg judge window on the fine grid, and a row falls back to the plain full-grid scan when a
+judge window reaches its weakest selected peak, when it has fewer than d window peaks, or when a
+window maximum lies on a window edge above that peak.
 This module only marshals arguments and loops over chunks; all arithmetic runs in libdoa.so.
 """
 from __future__ import annotations
@@ -30,6 +33,7 @@ EXTRA = 2
 COARSE_STEP = 0.1                       # label grid
 FINE_STEP = 0.001                       # fine grid of the windows and of the full-grid arbiter
 WIDTH = 4001                            # +-2 deg at 0.001 deg
+JUDGE_WIDTH = 401                       # +-0.2 deg judge windows around uncovered coarse maxima
 TRAIN_SEED, TEST_SEED = 20071417, 20071418
 
 
@@ -46,6 +50,7 @@ class Solved:
     d: torch.Tensor          # (n,) int32
     idx: torch.Tensor        # (n, DMAX) int32 peak indices on the solve grid
     count: torch.Tensor      # (n,) int32
+    coarse: Optional[torch.Tensor] = None   # (n, 1801) coarse full-grid MUSIC spectra (the judge's input)
 
 
 def solve_chunk(d: np.ndarray, ang: np.ndarray, snr: np.ndarray, seed: int, first: int, step: float,
@@ -71,8 +76,9 @@ def solve_chunk(d: np.ndarray, ang: np.ndarray, snr: np.ndarray, seed: int, firs
     status = torch.empty(n, dtype=torch.int32, device=device)
     doa.doa_solve_batch(plan, ws, status)
     K = torch.from_numpy((M - d).astype(np.int32)).to(device)
-    del X, P, ws
-    return Solved(feats, B, K, dt, idx, cnt)
+    del X, ws
+    # on the coarse grid the spectra are the judge's input
+    return Solved(feats, B, K, dt, idx, cnt, P if step == COARSE_STEP else None)
 
 
 def labels_from_peaks(idx: np.ndarray, count: np.ndarray, step: float) -> np.ndarray:
@@ -128,13 +134,14 @@ class Inference:
     idx: np.ndarray          # (n, DMAX) fine-grid peak indices, ascending (first count valid)
     count: np.ndarray
     fallback: np.ndarray     # rows rescanned on the full grid
+    judged: np.ndarray       # rows the judge sent to the full grid (a subset of fallback)
     windows: np.ndarray      # (n, DMAX) window starts (-1 unused)
     points: int              # fine-grid points evaluated (windows + fallback rows)
     seconds: float
 
 
-def infer(net: doa.Mlp, sol: Solved, extra: int = EXTRA, device: str = "cuda") -> Inference:
-    """Network forward, windows, windowed scan, fallback for the flagged rows."""
+def infer(net: doa.Mlp, sol: Solved, extra: int = EXTRA, device: str = "cuda", judge: bool = True) -> Inference:
+    """Network forward, windows, windowed scan, judge (needs sol.coarse), fallback for the flagged rows."""
     n = sol.features.shape[0]
     nb = (n + 7) // 8 * 8
     fg = fine_grid()
@@ -148,12 +155,21 @@ def infer(net: doa.Mlp, sol: Solved, extra: int = EXTRA, device: str = "cuda") -
     val = torch.zeros((n, WMAX), dtype=torch.float32, device=device)
     cnt = torch.zeros(n, dtype=torch.int32, device=device)
     fb = torch.zeros(n, dtype=torch.int32, device=device)
+    use_judge = judge and sol.coarse is not None
+    if use_judge:
+        jfirst = torch.full((n, doa.JUDGE_MAX), -1, dtype=torch.int32, device=device)
+        Pj = torch.empty((n, doa.JUDGE_MAX, JUDGE_WIDTH), dtype=torch.float32, device=device)
+        cg = doa.grid(-90.0, COARSE_STEP, synth.grid_size(COARSE_STEP))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     net.forward(feats, ws, probs=probs)
     doa.doa_proposal_windows(probs, sol.d, fg, WIDTH, win, extra=extra)
     doa.doa_scan_windows(sol.B, M, sol.K, sol.d, fg, S, Pwin, idx, val, cnt, win_first=win, width=WIDTH,
                          fallback=fb)
+    fb_windows = fb.clone() if use_judge else fb
+    if use_judge:
+        doa.doa_proposal_judge(sol.B, M, sol.K, sol.d, sol.coarse, cg, fg, win, WIDTH, val, cnt, JUDGE_WIDTH, jfirst,
+                               S, Pj, fb)
     fbh = fb.cpu().numpy()
     rows = np.nonzero(fbh)[0].astype(np.int32)
     if len(rows):
@@ -164,7 +180,11 @@ def infer(net: doa.Mlp, sol: Solved, extra: int = EXTRA, device: str = "cuda") -
     dt = time.perf_counter() - t0
     wins = win.cpu().numpy()
     pts = int((wins >= 0).sum()) * WIDTH + len(rows) * fg.L
-    return Inference(idx.cpu().numpy()[:, :DMAX], cnt.cpu().numpy(), fbh, wins, pts, dt)
+    judged = np.zeros(n, dtype=bool)
+    if use_judge:
+        pts += int((jfirst.cpu().numpy() >= 0).sum()) * JUDGE_WIDTH
+        judged = (fbh != 0) & (fb_windows.cpu().numpy() == 0)
+    return Inference(idx.cpu().numpy()[:, :DMAX], cnt.cpu().numpy(), fbh, judged, wins, pts, dt)
 
 
 def full_grid(sol: Solved, rows_chunk: int = 8192, device: str = "cuda"):
@@ -189,8 +209,9 @@ def full_grid(sol: Solved, rows_chunk: int = 8192, device: str = "cuda"):
 
 class TestSet:
     """A resident batch of proposal-workload instances with a reusable plan: solve() runs the
-    covariance, Jacobi, features and MUSIC factor for every instance (3-point dummy grid: the
-    spectrum is produced later, by the windows or by the full-grid scan)."""
+    covariance, Jacobi, features and MUSIC factor for every instance and the plain MUSIC scan on
+    the coarse 0.1 deg full grid (the judge's input; the fine spectrum is produced later, by the
+    windows or by the full-grid scan)."""
 
     def __init__(self, count: int, seed: int = TEST_SEED, device: str = "cuda"):
         self.d_np, self.ang, self.snr = synth.proposal_params(count, seed)
@@ -201,8 +222,8 @@ class TestSet:
         self.X = torch.empty((n, M, N_SNAP), dtype=torch.complex64, device=device)
         doa.doa_synth_ula(self.d, torch.from_numpy(self.ang).to(device), torch.from_numpy(self.snr).to(device), M,
                           N_SNAP, seed, 0, self.X)
-        g = doa.grid(-90.0, 90.0, 3)
-        self.P = torch.empty((n, 3), dtype=torch.float32, device=device)
+        g = doa.grid(-90.0, COARSE_STEP, synth.grid_size(COARSE_STEP))
+        self.P = torch.empty((n, g.L), dtype=torch.float32, device=device)
         self.idx = torch.empty((n, DMAX), dtype=torch.int32, device=device)
         self.val = torch.empty((n, DMAX), dtype=torch.float32, device=device)
         self.cnt = torch.empty(n, dtype=torch.int32, device=device)
@@ -219,4 +240,4 @@ class TestSet:
         doa.doa_solve_batch(self.plan, self.ws, self.status)
 
     def solved(self) -> Solved:
-        return Solved(self.features, self.B, self.K, self.d, self.idx, self.cnt)
+        return Solved(self.features, self.B, self.K, self.d, self.idx, self.cnt, self.P)

@@ -95,7 +95,7 @@ def test_batch_plan_layout(libdoa):
     # scan factor (M x (M+1) complex128 + M EV weights), each allocation rounded up to 256 bytes
     def factor(M):   # FP64 factor and EV weights, then the FP32 copy (padded rows), w32, thresholds
         mp = 8 if M <= 8 else 16 if M <= 16 else 32 if M <= 32 else 64
-        return (M * (M + 1) * 16 + M * 8 + 15) // 16 * 16 + (M + 1) * mp * 8 + mp * 4 + 16
+        return (M * (M + 1) * 16 + M * 8 + 15) // 16 * 16 + (M + 1) * mp * 16 + mp * 4 + 16
     need = (18001 + 1801) * 12 + 8 + (16 * 16 * 16) + factor(16) + (8 * 8 * 16) + factor(8) \
         + (33 * 33 * 16) * (1 + 3) + factor(33)
     assert ws.value >= need and ws.value < need + 256 * 12
@@ -394,3 +394,29 @@ def test_binding_has_no_host_fallback(libdoa):
         libdoa.doa_covariance(X, R64=R)
     with pytest.raises(ValueError):
         libdoa.doa_peaks(P, 2, idx, val, cnt)
+
+
+def test_svd_data_argument_checks(libdoa):
+    """doa_svd_data: size, pointer, alignment and parameter checks run before anything is enqueued;
+    the workspace covers the FP64 rows (16 M N bytes) and grows with N."""
+    L = libdoa.lib()
+    fake = ctypes.c_void_p(0x10000)
+    big = 1 << 40
+    assert L.doa_svd_data_ws_bytes(1, 100) == 0 and L.doa_svd_data_ws_bytes(65, 100) == 0
+    assert L.doa_svd_data_ws_bytes(16, 0) == 0
+    n1, n2 = L.doa_svd_data_ws_bytes(16, 1000), L.doa_svd_data_ws_bytes(16, 2000)
+    assert n1 >= 16 * 16 * 1000 and n2 - n1 == 16 * 16 * 1000
+    ok = (fake, 0, 16, 1000, 1000, 1e-15, 60, fake, fake, fake, fake, big, None)
+    for k, bad in ((0, None), (2, 1), (2, 65), (3, 0), (4, 999), (5, 0.0), (5, float("nan")), (6, 0), (6, 1001),
+                   (7, None), (8, None), (9, None), (10, None), (1, 2),
+                   (0, ctypes.c_void_p(0x10004)),              # complex64 X: 8-byte aligned
+                   (8, ctypes.c_void_p(0x10008))):             # U: 16-byte aligned
+        args = list(ok)
+        args[k] = bad
+        assert L.doa_svd_data(*args) == libdoa.EINVAL, (k, bad)
+    args = list(ok)
+    args[1], args[0] = 1, ctypes.c_void_p(0x10008)             # complex128 X: 16-byte aligned
+    assert L.doa_svd_data(*args) == libdoa.EINVAL
+    args = list(ok)
+    args[11] = n1 - 1
+    assert L.doa_svd_data(*args) == libdoa.ENOMEM

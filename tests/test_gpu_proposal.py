@@ -124,8 +124,9 @@ def test_windowed_scan_is_the_full_grid_scan_restricted(env):
 
 def test_learned_proposal_gains_over_full_grid(env):
     """Train on 1M method-generated instances, then on 16384 held-out instances the windowed
-    pipeline (one extra window, fallback to the full grid) reproduces the full-grid method's peak
-    indices on >= 99% of them while evaluating >= 3x fewer grid points."""
+    pipeline (one extra window, the judge on the coarse full-grid spectrum, fallback to the full
+    grid) reproduces the full-grid method's peak indices on every one of them while evaluating
+    >= 3x fewer grid points; without the judge some rows differ."""
     torch, doa = env
     from paper_2007_14135_gb300 import proposal
     feats, labels = proposal.make_training_set(1 << 20, seed=proposal.TRAIN_SEED)
@@ -133,10 +134,19 @@ def test_learned_proposal_gains_over_full_grid(env):
     hist = proposal.train(net, feats, labels, epochs=12, batch=4096, lr=2e-3, decay=0.85)
     assert hist[-1] < 0.7 * hist[0]
     d, ang, snr = synth.proposal_params(16384, proposal.TEST_SEED)
-    sol = proposal.solve_chunk(d, ang, snr, proposal.TEST_SEED, 0, 1.0)
-    inf = proposal.infer(net, sol, extra=1)
+    sol = proposal.solve_chunk(d, ang, snr, proposal.TEST_SEED, 0, proposal.COARSE_STEP)
+    assert sol.coarse is not None
     ji, jc, _ = proposal.full_grid(sol)
-    same = np.array([list(inf.idx[i, :inf.count[i]]) == list(ji[i, :jc[i]]) for i in range(len(d))])
     full_pts = len(d) * proposal.fine_grid().L
-    assert same.mean() >= 0.99, (same.mean(), inf.fallback.mean())
-    assert full_pts / inf.points >= 3.0, (full_pts / inf.points, inf.fallback.mean())
+
+    def agreement(inf):
+        return np.array([list(inf.idx[i, :inf.count[i]]) == list(ji[i, :jc[i]]) for i in range(len(d))])
+
+    bare = proposal.infer(net, sol, extra=1, judge=False)
+    judged = proposal.infer(net, sol, extra=1)
+    same = agreement(judged)
+    print("agreement without / with the judge", agreement(bare).mean(), same.mean(),
+          "fallback", bare.fallback.mean(), judged.fallback.mean(), "points ratio", full_pts / judged.points)
+    assert same.all(), (np.nonzero(~same)[0][:10], judged.fallback.mean())
+    assert set(np.nonzero(~agreement(bare))[0]) <= set(np.nonzero(judged.judged)[0])
+    assert full_pts / judged.points >= 3.0, (full_pts / judged.points, judged.fallback.mean())

@@ -1,19 +1,27 @@
 """doa_covariance_noalloc: the covariance for callers that cannot allocate device memory while
 they run (fixed-memory real-time loops, frameworks that forbid allocation after start-up). It
 keeps its scratch in a library-owned device array instead of memory the caller provides, and
-must give the same R as the existing entry point doa_covariance, call after call.
+must agree with the existing entry point doa_covariance and with the FP64 oracle to the accuracy
+of their compensated accumulation, call after call.
 
 This file is collected last so that a stop at the first failure has already run everything else.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_2007_14135_gb300 import synth
 from tests.gpu_common import require_gpu
 
 pytestmark = pytest.mark.gpu
 
-REL_TOL = 2e-6   # the covariance tolerance of the parity tests (relative to max |R|)
+# Both entry points accumulate exact FP32 products in compensated double-float and add their chunk
+# sums in FP64 (about 2^-44 relative); they split the snapshots differently (up to 8 cluster CTAs
+# against 1024-snapshot chunks), so the results agree to that accuracy, not bit for bit. The FP64
+# outputs are held to 1e-12 of max |R| against each other and against the FP64 oracle; the
+# complex64 output to the FP32 rounding of R.
+REL_TOL64 = 1e-12
+REL_TOL32 = 2e-6
 
 
 def _both(torch, doa, inst):
@@ -38,9 +46,11 @@ def test_noalloc_matches_covariance_on_consecutive_calls():
              synth.custom(16, 4, 4097, None, 10.0, 0.1, seed=501)]
     for inst in cases:
         R_ref, R_na, R32 = _both(torch, doa, inst)
-        scale = np.max(np.abs(R_ref))
-        assert np.max(np.abs(R_na - R_ref)) <= REL_TOL * scale
-        assert np.max(np.abs(R32 - R_ref)) <= REL_TOL * scale
+        R_or = oracle.covariance(inst.X)
+        scale = np.max(np.abs(R_or))
+        assert np.max(np.abs(R_na - R_ref)) <= REL_TOL64 * scale
+        assert np.max(np.abs(R_na - R_or)) <= REL_TOL64 * scale
+        assert np.max(np.abs(R32 - R_or)) <= REL_TOL32 * scale
         assert np.array_equal(R_na, R_na.conj().T)
 
 
