@@ -419,10 +419,42 @@ def run_gpu(args):
                                                points, solves)
         result["root_and_order"] = root_order_form(args, doa, torch, X, P, idx, val, cnt, status, g, meta, stream,
                                                    dev, points, solves)
+        if not args.no_workload_forms:
+            result["workloads"] = workload_forms(args)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def workload_forms(args):
+    """The other configurations as compact forms of the default line, each with its own parity
+    against the oracle and its roofline: the uneven batch (1024 problems, CUDA graph, autotuned),
+    the large array (32 replicas, FP32 / FP16x3 contractions, double-float and FP64 Jacobi), the
+    learned proposal (a smaller training set, 65536 test instances, judged) and the paper's UCA
+    scenario. Each runs with 3 timed steps after 3 warm-up steps."""
+    import copy
+    base = {"steps": 3, "warmup": 3, "cpu_sample": 256, "parity_full": 16, "no_cpu_baseline": False}
+    specs = (("uneven_batch", run_uneven, {"batch": 1024}),
+             ("large_array", run_large_array, {"batch": 32, "la_forms": "fp32,fp16x3,fp16x3_fp64_jacobi"}),
+             ("learned_proposal", run_learned, {"batch": 65536, "train": 1 << 18, "epochs": 16, "lr_decay": 0.85}),
+             ("paper_uca", run_uca, {"batch": 4096, "uca_rows": 90}))
+    drop = ("autotune", "clocks", "table10", "single")
+    out = {}
+    for name, fn, kw in specs:
+        a = copy.copy(args)
+        a.__dict__.update(base)
+        a.__dict__.update(kw)
+        t0 = time.perf_counter()
+        try:
+            r = fn(a, emit=False)
+        except Exception as e:   # a failed form is reported, not hidden
+            out[name] = {"error": repr(e)[:400]}
+            continue
+        r = {k: v for k, v in r.items() if k not in drop}
+        r["wall_s"] = round(time.perf_counter() - t0, 1)
+        out[name] = r
+    return out
 
 
 def refinement_form(args, doa, torch, X, P, idx, val, cnt, status, g, meta, stream, dev, points, solves):
@@ -512,7 +544,7 @@ def root_order_form(args, doa, torch, X, P, idx, val, cnt, status, g, meta, stre
                    "eigenvalues after the Jacobi sweeps"}
 
 
-def run_uneven(args):
+def run_uneven(args, emit=True):
     """Uneven batch: 4096 problems, M in {8,12,16,32}, d in U{1..M/2}, N in U{256..8192}, grid step in
     {0.1, 0.01, 0.001} deg, one algorithm each, solved by one doa_solve_batch replayed from a CUDA
     graph, with scan tiles from the autotuner."""
@@ -618,6 +650,13 @@ def run_uneven(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1) / args.steps
+    # FP32 ALU roofline of the scan stage: per problem L K (8M + 4) flops for its K factor columns
+    # (one algorithm each: K = 1 for PHD and MN, M - d for MUSIC and EV)
+    scan_flops = sum(s.L * (1 if s.alg in (0, 3) else s.M - s.d) * (8 * s.M + 4) for s in specs)
+    a_tf = scan_flops / (stage_ms[3] / 1e3) / 1e12
+    scan_roof = {"bound": "alu", "achieved": round(a_tf, 3), "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
+                 "frac": round(a_tf / FP32_PEAK_TFLOPS, 4), "traffic": None, "kernel": "scan stage (all buckets)",
+                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
     result = {
         "metric": METRIC, "value": points / (ms / 1e3), "unit": "points/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -632,6 +671,7 @@ def run_uneven(args):
         "solves_per_s": len(specs) * world / (ms / 1e3),
         "gpu_launches": plan.launches() * args.steps,
         "stages": {n: {"ms": round(v, 4)} for n, v in zip(doa.STAGE_NAMES, stage_ms)},
+        "roofline": scan_roof,
         "autotune": tune_log,
         "e2e": {"value": points / (e2e_ms / 1e3), "unit": "points/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
@@ -660,13 +700,14 @@ def run_uneven(args):
             worst = max(worst, float(np.max(np.abs(10 * np.log10(Pg / Po)))))
             agree += list(ih[i, :ch[i]]) == list(io)
         result["parity"] = {"sampled_solves": len(pick), "peak_index_agreement": agree, "max_db_err": worst}
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    return result
 
 
-def run_large_array(args):
+def run_large_array(args, emit=True):
     """Large array: M=64, d=8 (1 deg separation), N=16384, 360001-point grid (0.0005 deg), MUSIC.
     Each form (FP32 plain, one BF16 product, BF16x3 and FP16x3 split) runs covariance, FP64
     Jacobi, scan and peaks for `batch` replicas (spread over streams); the scan stage is also
@@ -693,16 +734,22 @@ def run_large_array(args):
     nstreams = min(reps, 32)
     streams = [torch.cuda.Stream(dev) for _ in range(nstreams)]
     main = torch.cuda.current_stream(dev)
-    forms = {"fp32": doa.FP32, "bf16": doa.BF16, "bf16x3": doa.BF16X3, "fp16x3": doa.FP16X3}
+    # (contraction precision, Jacobi arithmetic); the double-float Jacobi spreads each M=64 matrix
+    # over a whole CTA on the FP32 pipe, the FP64 form is kept beside it
+    forms = {"fp32": (doa.FP32, doa.EIG_DOUBLE_FLOAT), "bf16": (doa.BF16, doa.EIG_DOUBLE_FLOAT),
+             "bf16x3": (doa.BF16X3, doa.EIG_DOUBLE_FLOAT), "fp16x3": (doa.FP16X3, doa.EIG_DOUBLE_FLOAT),
+             "fp16x3_fp64_jacobi": (doa.FP16X3, doa.EIG_FP64)}
     if args.la_forms:
         forms = {k: v for k, v in forms.items() if k in args.la_forms.split(",")}
     stage_names = ("covariance", "eig_noise_subspace", "scan", "peaks")
 
-    def solve(prec, events=None):
+    def solve(form, events=None):
         # one stage at a time over all replicas, the replicas of a stage spread over the streams
-        # (the single-CTA FP64 Jacobi of one replica per SM; the tensor kernels fill the GPU)
+        # (the single-CTA Jacobi of one replica per SM; the tensor kernels fill the GPU)
+        prec, eprec = form
         calls = (lambda r, st: doa.doa_covariance(X[r], R64=R[r], prec=prec, stream=st),
-                 lambda r, st: doa.doa_noise_subspace(R[r], d, doa.MUSIC, B[r], info[r:r + 1], stream=st),
+                 lambda r, st: doa.doa_noise_subspace_prec(R[r], d, doa.MUSIC, eprec, B[r], info[r:r + 1],
+                                                           stream=st),
                  lambda r, st: doa.doa_scan(B[r], M, K, g, P[r], prec=prec, stream=st),
                  lambda r, st: doa.doa_peaks(P[r], d, idx[r], val[r], cnt[r:r + 1], stream=st))
         for si, call in enumerate(calls):
@@ -739,20 +786,21 @@ def run_large_array(args):
     out = {}
     clocks = ClockSampler(0)
     clocks.start()
-    for name, prec in forms.items():
-        ms_solve = timed(lambda: solve(prec), args.steps)
+    for name, form in forms.items():
+        prec = form[0]
+        ms_solve = timed(lambda: solve(form), args.steps)
         st_info = info.cpu().numpy()
         sev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-        solve(prec, sev)
+        solve(form, sev)
         torch.cuda.synchronize(dev)
         stage_ms = {n: round(sev[i].elapsed_time(sev[i + 1]), 3) for i, n in enumerate(stage_names)}
         ms_scan = timed(lambda: scans(prec), args.steps)
-        solve(prec)
+        solve(form)
         torch.cuda.synchronize(dev)
         res = {"ms_per_step": ms_solve, "solves_per_s": reps / (ms_solve / 1e3), "stages_ms": stage_ms,
                "scan_ms": ms_scan, "scan_points_per_s": reps * L / (ms_scan / 1e3),
                "scan_tflops_algorithmic": reps * L * K * (8 * M + 4) / (ms_scan / 1e3) / 1e12,
-               "eig_status_ok": bool(np.all(st_info > 0))}
+               "eig": "fp64" if form[1] == doa.EIG_FP64 else "double-float", "eig_status_ok": bool(np.all(st_info > 0))}
         if ref is not None:
             Pg = P[:nchk].cpu().numpy().astype(np.float64)
             ig, cg = idx[:nchk].cpu().numpy(), cnt[:nchk].cpu().numpy()
@@ -762,6 +810,15 @@ def run_large_array(args):
     clk = clocks.stop()
     head = "fp16x3" if "fp16x3" in out else next(iter(out))
     fp = out[head]
+    # tensor roofline of the split-operand scan: three real GEMMs of the steering block (L x 2M)
+    # against the real embedding of B (2M x 2K), 8 L M K flops each
+    peaks_json = load_peaks()
+    bf16_peak = peaks_json.get("bf16_tflops", 1899.9)
+    tc_tf = 3 * 8 * reps * L * M * K / (fp["scan_ms"] / 1e3) / 1e12
+    roof = ({"bound": "tensor", "achieved": round(tc_tf, 2), "peak": bf16_peak, "unit": "TFLOP/s",
+             "frac": round(tc_tf / bf16_peak, 4), "traffic": None, "kernel": "scan_tc_kernel (FP16x3)",
+             "peak_source": "measured bf16 burst (MEASURED_PEAKS.json); FP16 runs at the BF16 rate"}
+            if head == "fp16x3" else None)
     result = {
         "metric": METRIC, "value": fp["scan_points_per_s"], "unit": "points/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": fp["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -769,12 +826,14 @@ def run_large_array(args):
         "config": {"workload": f"large array: {reps} replicas of M=64, d=8 (1 deg separation), N=16384, "
                                f"grid -90:0.0005:90 (L=360001), MUSIC", "replicas": reps,
                    "value_is": f"{head} scan points/s (scan stage alone)"},
-        "forms": out, "clocks": clk,
+        "forms": out, "roofline": roof, "clocks": clk,
     }
-    print(json.dumps(result), flush=True)
+    if emit:
+        print(json.dumps(result), flush=True)
+    return result
 
 
-def run_learned(args):
+def run_learned(args, emit=True):
     """Learned proposal: train the network on 1M method-generated instances (M=16, d in U{1..6},
     SNR U[-5,20] dB, angles U[-80,80] with 3 deg separation, N=2048), then solve a batch of
     test instances two ways at the 0.001 deg resolution: covariance + Jacobi + network + windowed
@@ -847,10 +906,12 @@ def run_learned(args):
                      "loss_first_last": [hist[0], hist[-1]]},
         "clocks": clk,
     }
-    print(json.dumps(result), flush=True)
+    if emit:
+        print(json.dumps(result), flush=True)
+    return result
 
 
-def run_uca(args):
+def run_uca(args, emit=True):
     """The paper's own scenario (Sec. 4.2, Tables 8 and 10): a batch of 8-element uniform circular
     arrays (radius 10 m at 15 MHz), two uncorrelated sources at 15 dB SNR, N=1024 snapshots, MUSIC
     over azimuth 0:1:359 x elevation angle 1:1:90 (32 400 points) with the steering vector of Eq. 2
@@ -1133,10 +1194,11 @@ def run_uca(args):
                 worst = max(worst, float(np.max(np.abs(10 * np.log10(Pg[i].astype(np.float64) / Po)))))
         result["parity"] = {"sampled_solves": S, "peak_index_agreement": agree, "max_db_err": worst,
                             "spectra_compared": len(Pg)}
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    return result
 
 
 def _oracle_task_uca(args):
@@ -1214,6 +1276,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-chunk", type=int, default=1024, help="problems per streamed chunk in the e2e leg")
     ap.add_argument("--no-forms", action="store_true", help="skip the tensor-core scan and FP64-Jacobi forms")
+    ap.add_argument("--no-workload-forms", action="store_true",
+                    help="skip the compact uneven / large-array / learned / UCA forms of the default line")
     ap.add_argument("--workload", choices=["paper-density", "uneven", "large-array", "learned", "paper-uca"],
                     default="paper-density")
     ap.add_argument("--uca-rows", type=int, default=90, help="paper-uca workload: elevation rows (360 x rows grid)")

@@ -52,6 +52,14 @@ typedef enum {
 
 typedef enum { DOA_PHD = 0, DOA_MUSIC = 1, DOA_EV = 2, DOA_MN = 3 } doa_alg;
 
+/* Arithmetic of the Jacobi eigensolver (the batch's eig_prec; doa_noise_subspace_prec). GB300
+ * issues FP64 at about 1/64 of its FP32 rate, so DOA_EIG_DOUBLE_FLOAT runs the same rotations in
+ * double-float arithmetic (pairs of FP32 numbers, ~48 significant bits) on the FP32 pipe;
+ * DOA_EIG_FP64 runs them in FP64. In the batch the noise eigenvectors are then checked for
+ * orthonormality in FP64 (max |E_n^H E_n - I| <= 1e-10, else the problem's status is
+ * DOA_ENOCONV). */
+typedef enum { DOA_EIG_DOUBLE_FLOAT = 0, DOA_EIG_FP64 = 1 } doa_eig_prec;
+
 /* Arithmetic of the covariance and scan contractions. */
 typedef enum {
   DOA_FP32 = 0,    /* FP32 operands, FP32 FMA on CUDA cores                                   */
@@ -153,6 +161,15 @@ doa_status doa_covariance_noalloc(const float *X, int M, int N, int ldx, float *
 doa_status doa_noise_subspace(const double *R64, int M, int d, int alg, double *evals, double *B,
                               int *K_out, int *info, void *stream);
 
+/* doa_noise_subspace with the Jacobi's arithmetic chosen (doa_eig_prec): doa_noise_subspace is
+ * this call with DOA_EIG_FP64. With DOA_EIG_DOUBLE_FLOAT the rotations run until no pair has
+ * |a_pq| > 1e-12 sqrt(|a_pp a_qq|), the converged A and V are rounded to FP64 and sorted, and the
+ * factor is formed in FP64 as for the FP64 form. For M > 32 one 512-thread CTA works on the
+ * matrix (the element updates of every round spread over all its threads). DOA_EINVAL also for
+ * an unknown eig_prec. */
+doa_status doa_noise_subspace_prec(const double *R64, int M, int d, int alg, int eig_prec, double *evals,
+                                   double *B, int *K_out, int *info, void *stream);
+
 /*
  * Step-5: P_k = 1 / ||B^H a(theta_k)||^2 for k = 0..L-1 (equal to 1/(a^H C a) with C = B B^H).
  *   B    : M x K complex128 column-major, leading dimension M (as written by
@@ -221,8 +238,9 @@ doa_status doa_model_order(const double *evals, int M, int N, int *mdl, int *aic
  * Sec. 4.2), R = X X^H / N never formed: one-sided Jacobi (Hestenes) on the M rows of X. Rows
  * y_p, y_q are rotated, Y <- J^H Y and U <- U J, by the Hermitian Jacobi rotation of
  * doa_noise_subspace built from alpha = ||y_p||^2, beta = ||y_q||^2, gamma = y_p y_q^H; pairs in
- * row-cyclic order; a pair is rotated when |gamma| > tol sqrt(alpha beta); the iteration stops
- * after the first sweep that rotates nothing. Then X = U S V^H, and the eigenvalues of R are
+ * row-cyclic order; a pair is rotated when |gamma| > tol sqrt(alpha beta) and neither row is
+ * numerically zero (squared norm above 1e-30 of the largest: rank-deficient X, N < M); the
+ * iteration stops after the first sweep that rotates nothing. Then X = U S V^H, and the eigenvalues of R are
  * S_k^2 / N with eigenvectors the columns of U. Small singular values keep their relative
  * accuracy (R's eigenvalues below ~1e-16 of the largest do not).
  * GPU form: the rows live in an FP64 copy Y of X in ws; each sweep is one pass over Y on all SMs
@@ -353,13 +371,6 @@ doa_status doa_merge_slices(const doa_slice_summary *sums, int nslices, int d, i
 /* caller may capture into a CUDA graph.                                                      */
 /* ----------------------------------------------------------------------------------------- */
 
-/* Arithmetic of the batch's Jacobi eigensolver (single calls always use FP64). GB300 issues FP64
- * at about 1/64 of its FP32 rate, so the default runs the same rotations in double-float
- * arithmetic (pairs of FP32 numbers, ~48 significant bits) on the FP32 pipe; DOA_EIG_FP64 runs
- * them in FP64. Either way the noise eigenvectors are then checked for orthonormality in FP64
- * (max |E_n^H E_n - I| <= 1e-10, else the problem's status is DOA_ENOCONV). */
-typedef enum { DOA_EIG_DOUBLE_FLOAT = 0, DOA_EIG_FP64 = 1 } doa_eig_prec;
-
 /* One problem of a batch. All pointers are device pointers owned by the caller. */
 typedef struct {
   const float *X;        /* M x N complex64 row-major, row stride ldx                        */
@@ -422,7 +433,7 @@ typedef struct {
   int32_t scan_group[4]; /* FP32 ULA problems that share a grid are scanned together in groups  */
                          /* of this many (one steering generation per tile of the grid for the   */
                          /* whole group, each problem's factor contracted in turn); 1 scans every */
-                         /* problem alone. Allowed powers of two 1..64; default 32.              */
+                         /* problem alone. Allowed powers of two 1..32; default 32.              */
 } doa_tuning;
 
 /*

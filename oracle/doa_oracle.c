@@ -714,8 +714,10 @@ void oracle_model_order(const double *evals, int M, int N, int *mdl, int *aic, d
  * are rotated, Y <- J^H Y and U <- U J, with the Hermitian Jacobi rotation of oracle_eigh built
  * from the Gram entries alpha = ||y_p||^2, beta = ||y_q||^2, gamma = y_p y_q^H, each recomputed
  * from the rows in FP64 (R is never formed). Pairs row by row; a pair is rotated when
- * |gamma| > tol * sqrt(alpha beta) (and gamma != 0); the iteration stops after the first sweep
- * that rotates nothing. Then X = U S V^H with S_k = ||y_k||, and the eigenvalues of R = X X^H / N
+ * |gamma| > tol * sqrt(alpha beta) (and gamma != 0) and neither row is numerically zero (squared
+ * norm above 1e-30 of the largest at the sweep's start: the threshold relative to the largest
+ * entry that the Jacobi SVD of Sec. 4.2 uses to stop on rank-deficient data); the iteration stops
+ * after the first sweep that rotates nothing. Then X = U S V^H with S_k = ||y_k||, and the eigenvalues of R = X X^H / N
  * (Eq. 3) are S_k^2 / N with eigenvectors the columns of U.
  *
  * X: M x N complex128, row-major, interleaved, row stride ldx complex elements (callers with
@@ -734,6 +736,16 @@ int oracle_svd_data(const double *X, int M, int N, int ldx, double tol, int max_
   while (sweeps < max_sweeps) {
     ++sweeps;
     int rotations = 0;
+    /* rows whose squared norm is below 1e-30 of the largest (at the sweep's start) are numerically
+       zero: a rank-deficient X (N < M) leaves such rows at the rounding level, where |gamma| is
+       comparable to sqrt(alpha beta) whatever is done, so pairs with one are not rotated */
+    double maxd = 0.0;
+    for (int i = 0; i < M; ++i) {
+      double a = 0.0;
+      for (int t = 0; t < N; ++t) a += creal(Y[(size_t)i * N + t] * conj(Y[(size_t)i * N + t]));
+      if (a > maxd) maxd = a;
+    }
+    const double floor_d = 1e-30 * maxd;
     for (int p = 0; p < M - 1; ++p) {
       for (int q = p + 1; q < M; ++q) {
         const double complex *yp = Y + (size_t)p * N, *yq = Y + (size_t)q * N;
@@ -745,7 +757,7 @@ int oracle_svd_data(const double *X, int M, int N, int ldx, double tol, int max_
           gamma += yp[t] * conj(yq[t]);
         }
         double mag = cabs(gamma);
-        if (mag == 0.0 || mag <= tol * sqrt(alpha * beta)) continue;
+        if (mag == 0.0 || mag <= tol * sqrt(alpha * beta) || alpha <= floor_d || beta <= floor_d) continue;
         ++rotations;
         double complex ph = gamma / mag;
         double tau = (beta - alpha) / (2.0 * mag);

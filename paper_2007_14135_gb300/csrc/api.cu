@@ -330,10 +330,16 @@ doa_status doa_covariance(const float *X, int M, int N, int ldx, float *R, doubl
 
 doa_status doa_noise_subspace(const double *R64, int M, int d, int alg, double *evals, double *B, int *K_out,
                               int *info, void *stream) {
-  if (!R64 || !B || !info || M < 2 || M > kMaxM || d < 0 || d >= M || alg < DOA_PHD || alg > DOA_MN)
+  return doa_noise_subspace_prec(R64, M, d, alg, DOA_EIG_FP64, evals, B, K_out, info, stream);
+}
+
+doa_status doa_noise_subspace_prec(const double *R64, int M, int d, int alg, int eig_prec, double *evals, double *B,
+                                   int *K_out, int *info, void *stream) {
+  if (!R64 || !B || !info || M < 2 || M > kMaxM || d < 0 || d >= M || alg < DOA_PHD || alg > DOA_MN ||
+      (eig_prec != DOA_EIG_DOUBLE_FLOAT && eig_prec != DOA_EIG_FP64))
     return DOA_EINVAL;
   if (!aligned(R64, 16) || !aligned(B, 16) || (evals && !aligned(evals, 8))) return DOA_EINVAL;
-  return cuda_status(launch_eig_single(reinterpret_cast<const double2 *>(R64), M, d, alg, evals,
+  return cuda_status(launch_eig_single(reinterpret_cast<const double2 *>(R64), M, d, alg, eig_prec, evals,
                                        reinterpret_cast<double2 *>(B), K_out, info, as_stream(stream)));
 }
 

@@ -1,8 +1,9 @@
 // Per-device host state of the launchers: the dynamic shared-memory limit of each kernel (a
-// function attribute applies to one device's context) and the SM count. Both are looked up once
-// per (device, kernel) under a mutex, so several host threads and several GPUs may launch.
+// function attribute applies to one device's context; it is raised when a launch needs more than
+// the limit set so far) and the SM count, both kept per device under a mutex, so several host
+// threads and several GPUs may launch.
+#include <map>
 #include <mutex>
-#include <set>
 #include <utility>
 
 #include "doa_internal.cuh"
@@ -12,7 +13,7 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
-std::set<std::pair<int, const void *>> g_attr_done;   // (device, kernel) with its limit raised
+std::map<std::pair<int, const void *>, int> g_attr_bytes;   // (device, kernel) -> the limit set
 int g_sms[kMaxDevices] = {};
 
 }  // namespace
@@ -22,9 +23,10 @@ cudaError_t ensure_smem_attr(const void *func, int bytes) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (g_attr_done.count({dev, func})) return cudaSuccess;
+  auto it = g_attr_bytes.find({dev, func});
+  if (it != g_attr_bytes.end() && it->second >= bytes) return cudaSuccess;   // raised only, never lowered
   e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) g_attr_done.insert({dev, func});
+  if (e == cudaSuccess) g_attr_bytes[{dev, func}] = bytes;
   return e;
 }
 

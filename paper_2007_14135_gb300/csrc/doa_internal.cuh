@@ -241,7 +241,7 @@ struct PlanScanGroup {
   int32_t tiles;          // tiles of kScanThreads x scan_pt points covering the grid
   int64_t unit_start;
 };
-constexpr int kScanGroupMax = 64;       // problems per group (a queued point's problem fits a byte)
+constexpr int kScanGroupMax = 32;       // problems per group (their jobs are staged in shared memory)
 constexpr int kScanGroupDefault = 32;
 __host__ __device__ inline bool scan_group_allowed(int g) { return g >= 1 && g <= kScanGroupMax && (g & (g - 1)) == 0; }
 
@@ -376,7 +376,7 @@ cudaError_t launch_covariance_fixup(const uint8_t *plan_dev, const PlanHeader &h
 cudaError_t launch_covariance_tc_single(const float2 *X, int M, int N, int ldx, int prec, float2 *R, double2 *R64,
                                         cudaStream_t s);
 
-cudaError_t launch_eig_single(const double2 *R64, int M, int d, int alg, double *evals, double2 *B,
+cudaError_t launch_eig_single(const double2 *R64, int M, int d, int alg, int prec, double *evals, double2 *B,
                               int *K_out, int *info, cudaStream_t s);
 cudaError_t launch_model_order_single(const double *evals, int M, int N, int *mdl, int *aic, cudaStream_t s);
 cudaError_t launch_eig_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, int *status,

@@ -41,14 +41,14 @@ struct EigSmem {
 };
 
 // A group of T threads works on G matrices: one warp on 8, 4 or 2 matrices of M <= 8, 16, 32
-// (every lane owns one pair), or a whole 8-warp CTA on one matrix of M <= 64 (the 32 pairs
-// are owned by warp 0's lanes; the element updates are spread over all 256 threads).
+// (every lane owns one pair), or a whole 16-warp CTA on one matrix of M <= 64 (the 32 pairs
+// are owned by warp 0's lanes; the element updates are spread over all 512 threads).
 template <int NP>
-__host__ __device__ constexpr int grp_threads() { return NP <= 32 ? 32 : 256; }
+__host__ __device__ constexpr int grp_threads() { return NP <= 32 ? 32 : 512; }
 template <int NP>
 __host__ __device__ constexpr int mats_per_warp() { return NP <= 32 ? 64 / NP : 1; }
 template <int NP>
-__host__ __device__ constexpr int eig_warps() { return NP <= 8 ? 4 : (NP <= 16 ? 2 : (NP <= 32 ? 1 : 8)); }
+__host__ __device__ constexpr int eig_warps() { return NP <= 8 ? 4 : (NP <= 16 ? 2 : (NP <= 32 ? 1 : 16)); }
 template <int NP>
 __host__ __device__ constexpr int groups_per_cta() { return NP <= 32 ? eig_warps<NP>() : 1; }
 
@@ -650,7 +650,7 @@ __device__ int build_scan_factor(const PlanProblem &pp, EigSmem<NP> &s, double2 
   return st;
 }
 
-template <int NP>
+template <int NP, bool kDF>
 __global__ void __launch_bounds__(grp_threads<NP>()) eig_single_kernel(const double2 *R64, int M, int d, int alg, double *evals,
                                                        double2 *B, int *K_out, int *info) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -665,7 +665,10 @@ __global__ void __launch_bounds__(grp_threads<NP>()) eig_single_kernel(const dou
     Ms[j] = j == 0 ? M : 0;
     Rs[j] = R64;
   }
-  jacobi_group<NP, G>(mats, Ms, Rs, res);
+  if (kDF)
+    jacobi_group_df<NP, G>(mats, Ms, Rs, res);
+  else
+    jacobi_group<NP, G>(mats, Ms, Rs, res);
   EigSmem<NP> &s = mats[0];
   int st = 0;
   if (res[0] > 0) {
@@ -753,14 +756,21 @@ __global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_batch_kernel(const u
   }
 }
 
-template <int NP>
-cudaError_t run_single(const double2 *R64, int M, int d, int alg, double *evals, double2 *B, int *K_out,
-                       int *info, cudaStream_t st) {
+template <int NP, bool kDF>
+cudaError_t run_single_p(const double2 *R64, int M, int d, int alg, double *evals, double2 *B, int *K_out,
+                         int *info, cudaStream_t st) {
   const int smem = (int)sizeof(EigSmem<NP>) * mats_per_warp<NP>();
-  cudaError_t e = cudaFuncSetAttribute(eig_single_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = ensure_smem_attr((const void *)eig_single_kernel<NP, kDF>, smem);
   if (e != cudaSuccess) return e;
-  eig_single_kernel<NP><<<1, grp_threads<NP>(), smem, st>>>(R64, M, d, alg, evals, B, K_out, info);
+  eig_single_kernel<NP, kDF><<<1, grp_threads<NP>(), smem, st>>>(R64, M, d, alg, evals, B, K_out, info);
   return cudaGetLastError();
+}
+
+template <int NP>
+cudaError_t run_single(const double2 *R64, int M, int d, int alg, int prec, double *evals, double2 *B, int *K_out,
+                       int *info, cudaStream_t st) {
+  return prec == DOA_EIG_FP64 ? run_single_p<NP, false>(R64, M, d, alg, evals, B, K_out, info, st)
+                              : run_single_p<NP, true>(R64, M, d, alg, evals, B, K_out, info, st);
 }
 
 template <int NP, int G>
@@ -832,13 +842,13 @@ cudaError_t launch_model_order_single(const double *evals, int M, int N, int *md
   return cudaGetLastError();
 }
 
-cudaError_t launch_eig_single(const double2 *R64, int M, int d, int alg, double *evals, double2 *B, int *K_out,
-                              int *info, cudaStream_t s) {
+cudaError_t launch_eig_single(const double2 *R64, int M, int d, int alg, int prec, double *evals, double2 *B,
+                              int *K_out, int *info, cudaStream_t s) {
   switch (m_bucket(M)) {
-    case 0: return run_single<8>(R64, M, d, alg, evals, B, K_out, info, s);
-    case 1: return run_single<16>(R64, M, d, alg, evals, B, K_out, info, s);
-    case 2: return run_single<32>(R64, M, d, alg, evals, B, K_out, info, s);
-    default: return run_single<64>(R64, M, d, alg, evals, B, K_out, info, s);
+    case 0: return run_single<8>(R64, M, d, alg, prec, evals, B, K_out, info, s);
+    case 1: return run_single<16>(R64, M, d, alg, prec, evals, B, K_out, info, s);
+    case 2: return run_single<32>(R64, M, d, alg, prec, evals, B, K_out, info, s);
+    default: return run_single<64>(R64, M, d, alg, prec, evals, B, K_out, info, s);
   }
 }
 

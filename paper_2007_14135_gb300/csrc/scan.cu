@@ -199,15 +199,34 @@ __global__ void __launch_bounds__(kScanThreads) scan_prep_kernel(const uint8_t *
   if (lane < 4) w32[MP + lane] = thr[lane];
 }
 
+// 16-byte global -> shared copies that complete asynchronously (one group per problem).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// CTAs per SM the register budget of the grid-shared scan is set for: 4 where the phasors of a
+// thread's points fit in 128 registers without spilling, else 3.
 template <int MP, int PT>
-__global__ void __launch_bounds__(kScanThreads, 3) scan_shared_kernel(const uint8_t *plan, uint8_t *ws, int bucket) {
+__host__ __device__ constexpr int shared_min_blocks() {
+  return (MP == 8 && PT != 2) || (MP == 16 && PT <= 2) || (MP == 32 && PT == 1) ? 4 : 3;
+}
+
+template <int MP, int PT>
+__global__ void __launch_bounds__(kScanThreads, shared_min_blocks<MP, PT>())
+    scan_shared_kernel(const uint8_t *plan, uint8_t *ws, int bucket) {
   constexpr bool kPair = PT % 2 == 0;
-  __shared__ __align__(16) float Fsm[(kPair ? 4 : 2) * (MP + 1) * MP];
-  float2 *Bs = reinterpret_cast<float2 *>(Fsm);
-  float4 *Bd = reinterpret_cast<float4 *>(Fsm);
-  __shared__ float w32s[MP], thrs[4];
+  // paired form: two factor buffers; the next problem's factor, EV weights and thresholds are
+  // copied asynchronously while the current one is contracted
+  constexpr int kBufs = kPair ? 2 : 1;
+  __shared__ __align__(16) float Fsm[kBufs][(kPair ? 4 : 2) * (MP + 1) * MP];
+  __shared__ __align__(16) float Wsm[kBufs][MP + 4];   // EV weights, then the 4 thresholds
   __shared__ uint8_t tags[kFlagCap];
   __shared__ ScanShared sh;
+  __shared__ ScanJob jobs[kScanGroupMax];   // the current group's jobs (read once per group)
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
   const PlanScanGroup *groups = reinterpret_cast<const PlanScanGroup *>(plan + h->off_sg[bucket]);
   const int ngroups = h->sg_groups[bucket];
@@ -218,6 +237,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) scan_shared_kernel(const uint
   const int tid = threadIdx.x, warp = tid >> 5;
   constexpr int TP = kScanThreads * PT;
   if (tid == 0) sh.nflag = 0;
+  int cached = -1;   // group whose jobs are in shared memory (every thread holds the same value)
   for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
     int gi = 0, hi = ngroups - 1;
     while (gi < hi) {  // last group with unit_start <= u
@@ -228,6 +248,24 @@ __global__ void __launch_bounds__(kScanThreads, 3) scan_shared_kernel(const uint
     const PlanGrid &g = grids[gr.grid_id];
     const int L = g.L, k0 = (int)(u - gr.unit_start) * TP + tid * PT;
     const uint32_t *S = reinterpret_cast<const uint32_t *>(ws + g.S_off);
+    if (gi != cached) {   // the previous unit's drain has ended (barrier at its end)
+      for (int i = tid; i < gr.count; i += kScanThreads) jobs[i] = ula_job(probs[list[gr.first + i]], g, ws);
+      __syncthreads();
+      cached = gi;
+    }
+    // the copies of problem i of the group into buffer b (Kf columns of the factor, then the
+    // MP EV weights and 4 thresholds, all 16-byte multiples)
+    auto issue = [&](int i, int b) {
+      const ScanJob &ji = jobs[i];
+      const uint8_t *f32 = reinterpret_cast<const uint8_t *>(ji.F) + fac32_off(ji.M);
+      const float4 *src = reinterpret_cast<const float4 *>(f32);
+      float4 *dst = reinterpret_cast<float4 *>(Fsm[b]);
+      for (int e = tid; e < ji.Kf * MP; e += kScanThreads) cp_async16(dst + e, src + e);
+      const float4 *wsrc = reinterpret_cast<const float4 *>(f32 + (size_t)(ji.M + 1) * MP * 16);
+      for (int e = tid; e < (MP + 4) / 4; e += kScanThreads) cp_async16(reinterpret_cast<float4 *>(Wsm[b]) + e, wsrc + e);
+      cp_async_commit();
+    };
+    if constexpr (kPair) issue(0, 0);
     float2 a[kPair ? 1 : PT][MP];
     uint64_t ax[kPair ? PT / 2 : 1][MP], ay[kPair ? PT / 2 : 1][MP];
     if constexpr (kPair)
@@ -235,27 +273,28 @@ __global__ void __launch_bounds__(kScanThreads, 3) scan_shared_kernel(const uint
     else
       ula_phasors<MP, PT>(S, L, k0, a);
     for (int i = 0; i < gr.count; ++i) {
-      const PlanProblem &pp = probs[list[gr.first + i]];
-      const ScanJob j = ula_job(pp, g, ws);
-      const uint8_t *f32 = ws + pp.fac_off + fac32_off(j.M);
-      __syncthreads();   // the previous problem's contraction has finished reading Bs
-      const float4 *src4 = reinterpret_cast<const float4 *>(f32);
+      const ScanJob &j = jobs[i];
       if constexpr (kPair) {
-        for (int e = tid; e < j.Kf * MP; e += kScanThreads) Bd[e] = src4[e];
+        const int b = i & 1;
+        cp_async_wait_all();   // this thread's copies of problem i have landed
+        __syncthreads();       // everyone's have; and problem i - 1 is no longer read from buffer b ^ 1
+        if (i + 1 < gr.count) issue(i + 1, b ^ 1);
+        contract_points2<MP, PT, UlaSource, true>(reinterpret_cast<const float4 *>(Fsm[b]), j, ax, ay, L, k0, sh,
+                                                  UlaSource{&j}, Wsm[b], Wsm[b] + MP, tags, i);
       } else {
+        const uint8_t *f32 = reinterpret_cast<const uint8_t *>(j.F) + fac32_off(j.M);
+        float2 *Bs = reinterpret_cast<float2 *>(Fsm[0]);
+        __syncthreads();   // the previous problem's contraction has finished reading Bs
+        const float4 *src4 = reinterpret_cast<const float4 *>(f32);
         for (int e = tid; e < j.Kf * MP; e += kScanThreads) {
           const float4 v = src4[e];
           Bs[e] = make_float2(v.x, v.z);
         }
+        const float *wg = reinterpret_cast<const float *>(f32 + (size_t)(j.M + 1) * MP * 16);
+        for (int k = tid; k < MP + 4; k += kScanThreads) Wsm[0][k] = wg[k];
+        __syncthreads();
+        contract_points<MP, PT, UlaSource, true>(Bs, j, a, L, k0, sh, UlaSource{&j}, Wsm[0], Wsm[0] + MP, tags, i);
       }
-      const float *wg = reinterpret_cast<const float *>(f32 + (size_t)(j.M + 1) * MP * 16);
-      for (int k = tid; k < j.Kn; k += kScanThreads) w32s[k] = wg[k];
-      if (tid < 4) thrs[tid] = wg[MP + tid];
-      __syncthreads();
-      if constexpr (kPair)
-        contract_points2<MP, PT, UlaSource, true>(Bd, j, ax, ay, L, k0, sh, UlaSource{&j}, w32s, thrs, tags, i);
-      else
-        contract_points<MP, PT, UlaSource, true>(Bs, j, a, L, k0, sh, UlaSource{&j}, w32s, thrs, tags, i);
     }
     // FP64 re-evaluation of the unit's flagged points, several per warp for small factors; the
     // queue holds the points of each problem together (problems run one after the other)
@@ -267,9 +306,9 @@ __global__ void __launch_bounds__(kScanThreads, 3) scan_shared_kernel(const uint
         const int tag = tags[c0];
         int c1 = c0 + 1;
         while (c1 < end && tags[c1] == tag) ++c1;
-        const PlanProblem &pp = probs[list[gr.first + tag]];
-        const ScanJob j = ula_job(pp, g, ws);
-        const float *wg = reinterpret_cast<const float *>(ws + pp.fac_off + fac32_off(j.M) + (size_t)(j.M + 1) * MP * 16);
+        const ScanJob &j = jobs[tag];
+        const float *wg = reinterpret_cast<const float *>(reinterpret_cast<const uint8_t *>(j.F) + fac32_off(j.M) +
+                                                          (size_t)(j.M + 1) * MP * 16);
         const UlaSource src{&j};
         if (j.M <= 8 && j.Kf <= 8) {
           refine_points_subwarp<8>(j, sh.flags + c0, c1 - c0, src, wg, sh.ph[warp]);

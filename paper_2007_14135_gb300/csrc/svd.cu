@@ -196,6 +196,12 @@ __global__ void __launch_bounds__(kSvdThreads) svd_sweep_kernel(int M, int N, in
   }
   if (tid == 0) rotated = 0;
   __syncthreads();
+  // rows whose squared norm is below 1e-30 of the largest (fresh Gram diagonal) are numerically
+  // zero (a rank-deficient X leaves them at the rounding level, where |gamma| stays comparable to
+  // sqrt(alpha beta)): pairs with one are not rotated
+  double maxd = 0.0;
+  for (int i = 0; i < M; ++i) maxd = fmax(maxd, G[i * M + i].x);
+  const double floor_d = 1e-30 * maxd;
   const bool last = sweeps + 1 >= max_sweeps;
   for (int p = 0; p < M - 1; ++p) {
     for (int q = p + 1; q < M; ++q) {
@@ -203,7 +209,7 @@ __global__ void __launch_bounds__(kSvdThreads) svd_sweep_kernel(int M, int N, in
       const double alpha = G[p * M + p].x, beta = G[q * M + q].x;
       const double2 gamma = G[p * M + q];
       const double mag = hypot(gamma.x, gamma.y);
-      if (mag == 0.0 || mag <= tol * sqrt(alpha * beta)) continue;
+      if (mag == 0.0 || mag <= tol * sqrt(alpha * beta) || alpha <= floor_d || beta <= floor_d) continue;
       if (tid == 0) rotated = 1;
       if (last) continue;   // the cap is reached: report, do not rotate
       const double2 ph = make_double2(gamma.x / mag, gamma.y / mag);

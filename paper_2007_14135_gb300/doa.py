@@ -33,7 +33,7 @@ EXPORTS = ("doa_status_str", "doa_covariance", "doa_covariance_noalloc", "doa_no
            "doa_proposal_windows", "doa_scan_windows", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices", "doa_probe_fma",
            "doa_scan_geometry", "doa_scan_geometry_ws_bytes", "doa_peaks2d", "doa_refine_peaks",
            "doa_refine_peaks2d", "doa_model_order", "doa_root_music", "doa_proposal_judge", "doa_svd_data",
-           "doa_svd_data_ws_bytes")
+           "doa_svd_data_ws_bytes", "doa_noise_subspace_prec")
 SLICE_MAXD = 64
 
 
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.doa_covariance.argtypes = [vp, i, i, i, vp, vp, i, vp]
     lib.doa_covariance_noalloc.argtypes = [vp, i, i, i, vp, vp, vp]
     lib.doa_noise_subspace.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp]
+    lib.doa_noise_subspace_prec.argtypes = [vp, i, i, i, i, vp, vp, vp, vp, vp]
     lib.doa_scan.argtypes = [vp, i, i, Grid, i, vp, vp]
     lib.doa_peaks.argtypes = [vp, i, i, vp, vp, vp, vp]
     lib.doa_batch_plan_bytes.argtypes = [ctypes.POINTER(Problem), i]
@@ -108,7 +109,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     for name in ("doa_covariance", "doa_covariance_noalloc", "doa_noise_subspace", "doa_scan", "doa_peaks",
                  "doa_batch_plan", "doa_solve_batch", "doa_scan_slice", "doa_slice_peaks", "doa_merge_slices", "doa_probe_fma",
                  "doa_scan_geometry", "doa_peaks2d", "doa_refine_peaks", "doa_refine_peaks2d", "doa_model_order",
-                 "doa_root_music", "doa_proposal_judge", "doa_svd_data"):
+                 "doa_root_music", "doa_proposal_judge", "doa_svd_data", "doa_noise_subspace_prec"):
         getattr(lib, name).restype = i
     return lib
 
@@ -185,6 +186,16 @@ def doa_noise_subspace(R64: torch.Tensor, d: int, alg: int, B: torch.Tensor, inf
     assert R64.dtype == torch.complex128 and B.dtype == torch.complex128 and B.numel() >= M * M
     _check(lib().doa_noise_subspace(_dev(R64), M, d, alg, _dev(evals), _dev(B), _dev(K_out), _dev(info),
                                     _stream(stream)), "doa_noise_subspace")
+
+
+def doa_noise_subspace_prec(R64: torch.Tensor, d: int, alg: int, eig_prec: int, B: torch.Tensor, info: torch.Tensor,
+                            evals: Optional[torch.Tensor] = None, K_out: Optional[torch.Tensor] = None,
+                            stream=None) -> None:
+    """doa_noise_subspace with the Jacobi's arithmetic chosen (EIG_DOUBLE_FLOAT or EIG_FP64)."""
+    M = R64.shape[0]
+    assert R64.dtype == torch.complex128 and B.dtype == torch.complex128 and B.numel() >= M * M
+    _check(lib().doa_noise_subspace_prec(_dev(R64), M, d, alg, eig_prec, _dev(evals), _dev(B), _dev(K_out),
+                                         _dev(info), _stream(stream)), "doa_noise_subspace_prec")
 
 
 def doa_scan(B: torch.Tensor, M: int, K: int, g: Grid, P: torch.Tensor, prec: int = FP32, stream=None) -> None:

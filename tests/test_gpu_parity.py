@@ -66,6 +66,51 @@ def test_noise_subspace(env, M, d):
         assert np.max(np.abs(Cg - Co)) < 1e-10 * np.max(np.abs(Co)), (alg, np.max(np.abs(Cg - Co)))
 
 
+@pytest.mark.parametrize("M,d", [(5, 2), (16, 4), (32, 16), (64, 8)])
+def test_noise_subspace_double_float(env, M, d):
+    """doa_noise_subspace_prec with the double-float Jacobi (~48-bit rotations, FP64 output): the
+    same eigenvalues (1e-12 of the largest) and weighting matrices C = B B^H (1e-10) as the FP64
+    oracle for all four algorithms, on sample covariances and, at M = 64, on an exact covariance
+    A P A^H + sigma^2 I (noise eigenvalues sigma^2 to 1e-13 of the largest, E_n^H a(theta_i) = 0)."""
+    torch, doa = env
+    ang = None if d <= 8 else np.linspace(-70.0, 70.0, d) + 0.37
+    inst = synth.custom(M, d, max(4 * M, 256), ang, 12.0, 0.1, seed=2100 + M * 13 + d)
+    Ro = oracle.covariance(inst.X)
+    ev_o, V_o, _ = oracle.eigh(Ro)
+    R = torch.from_numpy(Ro).cuda()
+    for alg in (PHD, MUSIC, EV, MN):
+        B = torch.zeros(M * M, dtype=torch.complex128, device="cuda")
+        ev = torch.empty(M, dtype=torch.float64, device="cuda")
+        info = torch.zeros(1, dtype=torch.int32, device="cuda")
+        doa.doa_noise_subspace_prec(R, d, alg, doa.EIG_DOUBLE_FLOAT, B, info, evals=ev)
+        torch.cuda.synchronize()
+        assert info.item() > 0, info.item()
+        np.testing.assert_allclose(ev.cpu().numpy(), ev_o, rtol=0, atol=1e-12 * ev_o[0])
+        Kx = 1 if alg in (PHD, MN) else M - d
+        Bg = B.cpu().numpy()[:M * Kx].reshape(Kx, M).T
+        Co, st = oracle.weighting(ev_o, V_o, d, alg)
+        assert st == 0
+        assert np.max(np.abs(Bg @ Bg.conj().T - Co)) < 1e-10 * np.max(np.abs(Co)), alg
+    if M == 64:
+        m = np.arange(M)[:, None]
+        angs = np.linspace(-60.0, 60.0, d) + 0.21
+        A = np.exp(1j * np.pi * m * np.sin(np.radians(angs))[None, :])
+        s2 = 0.1
+        R = torch.from_numpy(A @ A.conj().T + s2 * np.eye(M)).cuda()
+        B = torch.zeros(M * M, dtype=torch.complex128, device="cuda")
+        ev = torch.empty(M, dtype=torch.float64, device="cuda")
+        info = torch.zeros(1, dtype=torch.int32, device="cuda")
+        doa.doa_noise_subspace_prec(R, d, MUSIC, doa.EIG_DOUBLE_FLOAT, B, info, evals=ev)
+        torch.cuda.synchronize()
+        assert info.item() > 0
+        # double-float rotations (~2^-48) leave errors relative to the largest eigenvalue (~M)
+        evg = ev.cpu().numpy()
+        np.testing.assert_allclose(evg[d:], s2, rtol=0, atol=1e-13 * evg[0])
+        En = B.cpu().numpy()[:M * (M - d)].reshape(M - d, M).T
+        assert np.linalg.norm(En.conj().T @ A) < 1e-11 * np.linalg.norm(A)
+        assert np.max(np.abs(En.conj().T @ En - np.eye(M - d))) < 1e-13
+
+
 def test_noise_subspace_exact_covariance(env):
     """R = A A^H + sigma^2 I: noise eigenvalues sigma^2 and E_n^H a(theta_i) = 0 on the GPU too."""
     torch, doa = env

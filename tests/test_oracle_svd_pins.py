@@ -87,3 +87,18 @@ def test_matches_covariance_eig_path():
         assert np.abs(ev - e2).max() <= 1e-13 * e2[0]
         En, Fn = U[:, inst.d:], V[:, inst.d:]
         assert np.abs(En @ En.conj().T - Fn @ Fn.conj().T).max() <= 1e-10
+
+
+def test_rank_deficient_rows_converge():
+    """N < M: X has rank N, so M - N rows end at the rounding level; the zero-row floor (squared
+    norm below 1e-30 of the largest) stops the iteration, the N nonzero eigenvalues match LAPACK's
+    singular values and the rest are zero to rounding, U stays unitary."""
+    rng = np.random.default_rng(23)
+    for M, N in ((2, 1), (5, 3), (8, 4), (16, 7)):
+        X = (rng.standard_normal((M, N)) + 1j * rng.standard_normal((M, N))).astype(np.complex64)
+        ev, U, sweeps = oracle.svd_data(X)
+        assert sweeps > 0, (M, N, sweeps)
+        s2 = np.linalg.svd(X.astype(np.complex128), compute_uv=False) ** 2 / N
+        np.testing.assert_allclose(ev[:N], s2, rtol=1e-12)
+        assert np.all(np.abs(ev[N:]) <= 1e-28 * ev[0])
+        assert np.abs(U.conj().T @ U - np.eye(M)).max() <= 1e-13
