@@ -50,7 +50,7 @@ def workload_name(batch):
 # array from 2048 problems x 2 (profiles/paper_uca_geometry_scan_ncu.md). Reset an entry to None
 # when its kernel changes.
 TRAFFIC_BYTES = {
-    "scan_batch_kernel<16,2>": 4 * (4.274432e6 + 234.934528e6),
+    "scan_shared_kernel<16,2>": None,          # DRAM bytes per 4096-problem launch (ncu), once captured
     "scan_geometry_batch_kernel<8,4>": None,   # changed since its capture: reads shared steering tables
     "scan_geometry_batch_kernel<8,2>": None,
 }
@@ -331,7 +331,7 @@ def run_gpu(args):
     if dname == "scan":
         roof = {"bound": "alu", "achieved": round(stage_info["scan"]["achieved"], 3), "peak": round(FP32_PEAK_TFLOPS, 2),
                 "unit": "TFLOP/s", "frac": round(stage_info["scan"]["achieved"] / FP32_PEAK_TFLOPS, 4),
-                "traffic": TRAFFIC_BYTES.get("scan_batch_kernel<16,2>"), "kernel": "scan_batch_kernel<16,2>",
+                "traffic": TRAFFIC_BYTES.get("scan_shared_kernel<16,2>"), "kernel": "scan_shared_kernel<16,2>",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
     elif dname == "covariance":
         a = stage_info["covariance"]["achieved"]
@@ -351,7 +351,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Eq. 1 ULA snapshots, Philox)",
         "config": {"workload": workload_name(B), "batch_per_gpu": B, "M": M, "d": D, "N": N_SNAP, "L": L,
-                   "algorithms": ["PHD", "MUSIC", "EV", "MN"], "eig": "double-float Jacobi (FP32 pipe)", "scan": "FP32 FFMA", "peaks": "polished (FP64 at peaks +-2)",
+                   "algorithms": ["PHD", "MUSIC", "EV", "MN"], "eig": "double-float Jacobi (FP32 pipe)", "scan": "FP32 FFMA, grid-shared (one steering block per tile for 32 problems)", "peaks": "polished (FP64 at peaks +-2)",
                    "l2": f"inputs {Xh.nbytes / 1e9:.2f} GB per step > 129 MB L2 (no flush needed)",
                    "parallelism": f"replicas x{world}"},
         "solves_per_s": solves / (ms / 1e3),

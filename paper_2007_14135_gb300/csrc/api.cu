@@ -246,7 +246,7 @@ bool count_plan(const doa_problem *probs, int nprob, PlanSizes &sz, std::vector<
 
 struct PlanOffsets {
   int64_t prob, job, grid, cov, reduce, eig[kNumBuckets], scan[kNumBuckets], tc, geo[kNumBuckets], geo_grid,
-      geo_steer, covtc[2], sg[kNumBuckets], sgl[kNumBuckets], total;
+      geo_steer, covtc[2], sg[kNumBuckets], sgl[kNumBuckets], tcg, tcc, tcgl, total;
 };
 
 PlanOffsets plan_offsets(const PlanSizes &sz) {
@@ -292,6 +292,13 @@ PlanOffsets plan_offsets(const PlanSizes &sz) {
     o.sgl[b] = at;
     at = round_up(at + (int64_t)sz.scan[b] * 4, 16);
   }
+  // grid-shared tensor-core scan: room for every split-precision ULA problem
+  o.tcg = at;
+  at = round_up(at + (int64_t)sz.tc * sizeof(PlanTcGroup), 16);
+  o.tcc = at;
+  at = round_up(at + (int64_t)sz.tc * sizeof(PlanTcChunk), 16);
+  o.tcgl = at;
+  at = round_up(at + (int64_t)sz.tc * 4, 16);
   o.total = at;
   return o;
 }
@@ -623,6 +630,15 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     const int b = m_bucket(probs[i].M);
     return ula_fp32(probs[i]) && sgsize[b] > 1 && sharers[(size_t)grid_of[i] * kNumBuckets + b].size() >= 2;
   };
+  // grid-shared tensor-core scan: split-precision ULA problems sharing (grid, M bucket, precision)
+  auto ula_tc = [](const doa_problem &p) { return !p.geom.pos && p.prec != DOA_FP32; };
+  auto tc_key = [&](int i) { return ((size_t)grid_of[i] * kNumBuckets + m_bucket(probs[i].M)) * 4 + probs[i].prec; };
+  std::vector<std::vector<int32_t>> tc_sharers((size_t)sz.ngrids * kNumBuckets * 4);
+  for (int i = 0; i < nprob; ++i)
+    if (ula_tc(probs[i])) tc_sharers[tc_key(i)].push_back(i);
+  auto tc_grouped = [&](int i) {
+    return ula_tc(probs[i]) && sgsize[m_bucket(probs[i].M)] > 1 && tc_sharers[tc_key(i)].size() >= 2;
+  };
   for (int i = 0; i < nprob; ++i) {
     const doa_problem &p = probs[i];
     PlanProblem &q = pp[i];
@@ -670,7 +686,7 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
       q.tile_start = h.geo_tiles[b];
       h.geo_tiles[b] += (q.npts + tp - 1) / tp;
       geo[b][h.geo_jobs[b]++] = i;
-    } else if (grouped(i)) {
+    } else if (grouped(i) || tc_grouped(i)) {
       q.tile_start = 0;   // scanned by its group (grid-shared scan)
     } else if (p.prec == DOA_FP32) {
       const int tp = kScanThreads * pt[b];
@@ -715,6 +731,59 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
       }
     }
   }
+  // tensor-core groups: each key's problems in order, packed while their columns (2 Kf rounded
+  // up to 16) fit kTcgMaxCols and their count the bucket's group size; runs of up to kTcgChunk
+  // groups of one key form the chunks; one record per group in the workspace
+  {
+    PlanTcGroup *tg = reinterpret_cast<PlanTcGroup *>(base + o.tcg);
+    PlanTcChunk *tcc = reinterpret_cast<PlanTcChunk *>(base + o.tcc);
+    int32_t *tgl = reinterpret_cast<int32_t *>(base + o.tcgl);
+    h.off_tcg = o.tcg;
+    h.off_tcc = o.tcc;
+    h.off_tcgl = o.tcgl;
+    for (size_t key = 0; key < tc_sharers.size(); ++key) {
+      const std::vector<int32_t> &v = tc_sharers[key];
+      if (v.size() < 2) continue;
+      const int b = (int)((key / 4) % kNumBuckets), g = (int)(key / 4 / kNumBuckets);
+      if (sgsize[b] <= 1) continue;
+      const int maxp = std::min(kTcgMaxProbs, sgsize[b]);
+      int chunk = -1;
+      size_t f = 0;
+      while (f < v.size()) {
+        PlanTcGroup &e = tg[h.tcg_groups];
+        e.first = h.tcg_probs;
+        e.count = 0;
+        e.prec = probs[v[f]].prec;
+        int cols = 0, Mmax = 0;
+        while (f < v.size() && e.count < maxp) {
+          const int c = (2 * pp[v[f]].Kf + 15) / 16 * 16;
+          if (cols + c > kTcgMaxCols) break;
+          cols += c;
+          Mmax = std::max(Mmax, probs[v[f]].M);
+          tgl[h.tcg_probs++] = v[f++];
+          ++e.count;
+        }
+        e.NG = std::max(16, (cols + 15) / 16 * 16);
+        ws = round_up(ws, 1024);
+        e.rec_off = ws;
+        ws = round_up(ws + kTcgRecBytes, 1024);
+        if (chunk < 0 || tcc[chunk].ngroups == kTcgChunk) {
+          chunk = h.tcg_chunks++;
+          PlanTcChunk &c = tcc[chunk];
+          c.grid_id = g;
+          c.first_group = h.tcg_groups;
+          c.ngroups = 0;
+          c.Mg = 8;
+          c.tiles = (grids[g].L + kTcgTile - 1) / kTcgTile;
+          c.unit_start = h.tcg_units;
+          h.tcg_units += c.tiles;
+        }
+        tcc[chunk].ngroups += 1;
+        tcc[chunk].Mg = std::max(tcc[chunk].Mg, (Mmax + 7) / 8 * 8);
+        ++h.tcg_groups;
+      }
+    }
+  }
   h.next_val_off = -1;
   if (h.npolish > 0) {   // the polish reads, per job, the best peak value below the selection
     h.next_val_off = ws;
@@ -744,6 +813,7 @@ doa_status doa_solve_batch(const void *plan_host, const void *plan_dev, void *ws
   if (!mark(2) || launch_eig_batch(pd, h, w, status, s) != cudaSuccess) return DOA_ECUDA;
   if (!mark(3) || launch_scan_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
   if (h.tc_jobs > 0 && launch_scan_tc_batch(pd, h, w, status, s) != cudaSuccess) return DOA_ECUDA;
+  if (h.tcg_groups > 0 && launch_scan_tc_shared(pd, h, w, status, s) != cudaSuccess) return DOA_ECUDA;
   if (launch_scan_geometry_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
   if (!mark(4) || launch_peaks_batch(pd, h, w, true, true, s) != cudaSuccess) return DOA_ECUDA;
   // peak polish applies to ULA problems only (geometry problems reject the flag)

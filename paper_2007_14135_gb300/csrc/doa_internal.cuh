@@ -241,6 +241,44 @@ struct PlanScanGroup {
   int32_t tiles;          // tiles of kScanThreads x scan_pt points covering the grid
   int64_t unit_start;
 };
+// Grid-shared tensor-core scan: a group's stacked factor columns (each problem's 2 Kf real
+// columns rounded up to 16) form one UMMA N <= kTcgMaxCols; its record in the workspace holds the
+// split operand W (hi, lo: kTcgMaxCols rows of 128 bytes, 128B-swizzled K-major) and a TcgProb per
+// problem.
+constexpr int kTcgMaxCols = 128;
+constexpr int kTcgTile = 128;          // grid points per tile (UMMA M)
+constexpr int kTcgMaxProbs = 16;
+constexpr int kTcgChunk = 8;           // groups per unit (one steering block serves all of them)
+struct PlanTcGroup {
+  int32_t first;          // first entry of the group in the tcg problem list
+  int32_t count;
+  int32_t NG;             // stacked columns (multiple of 16, <= kTcgMaxCols)
+  int32_t prec;           // DOA_BF16X3 or DOA_FP16X3
+  int64_t rec_off;        // workspace byte offset of the group record (1024-aligned)
+};
+struct PlanTcChunk {
+  int32_t grid_id;
+  int32_t first_group;
+  int32_t ngroups;
+  int32_t Mg;             // phasors per point the steering block holds (max M of its groups, to 8)
+  int32_t tiles;          // 128-point tiles of the grid
+  int32_t pad;
+  int64_t unit_start;
+};
+struct TcgProb {
+  float *P[4];            // output row per readout (null: absent)
+  const float2 *B32;      // FP32 factor [Kf][MPs] (re-evaluation)
+  const float *w32;       // FP32 EV weights
+  int32_t prob, col, Kf, Kn, kphd, kmn, M, MPs;
+  float scale2;           // the W scale's square inverse (den = accumulator sum * scale2)
+  float thr32[4];         // FP32 re-evaluation threshold per readout
+  float thrtc[4];         // tensor-product threshold per readout
+  int32_t pad[3];
+};
+static_assert(sizeof(TcgProb) == 128, "TcgProb layout");
+constexpr int64_t kTcgWBytes = (int64_t)kTcgMaxCols * 128;
+constexpr int64_t kTcgRecBytes = 2 * kTcgWBytes + kTcgMaxProbs * (int64_t)sizeof(TcgProb);
+
 constexpr int kScanGroupMax = 32;       // problems per group (their jobs are staged in shared memory)
 constexpr int kScanGroupDefault = 32;
 __host__ __device__ inline bool scan_group_allowed(int g) { return g >= 1 && g <= kScanGroupMax && (g & (g - 1)) == 0; }
@@ -301,12 +339,20 @@ struct PlanHeader {
   int64_t off_sg[kNumBuckets];           // PlanScanGroup arrays
   int64_t off_sgl[kNumBuckets];          // their problem lists
   int32_t sg_probs[kNumBuckets];         // problems in the groups
+  // grid-shared tensor-core scan: split-operand ULA problems that share a grid, M bucket and
+  // precision, stacked into groups of at most kTcgMaxCols factor columns (not in the tc list)
+  int32_t tcg_groups;
+  int32_t tcg_chunks;                    // runs of up to kTcgChunk groups of one grid and key
+  int32_t tcg_probs;
+  int32_t tcg_pad;
+  int64_t tcg_units;                     // (tile, chunk) units
+  int64_t off_tcg, off_tcc, off_tcgl;    // PlanTcGroup, PlanTcChunk arrays and the problem list
 };
 
 // The Python binding reads these header fields by position (int32 index 22 = scan_pt, 58 = eig_mats,
 // 62 = cov_first, 67 = tc_jobs, 74 = npolish, 76 = geo_jobs, 96 = ngeo_grids, 100 = nrefine,
 // 101 = nroots, 104 = ngeo_steer, 108 = ncovtc, 114 = covtc_flag_off (int64), 116 = sg_size,
-// 120 = sg_groups, 124 = sg_units (int64), 148 = sg_probs).
+// 120 = sg_groups, 124 = sg_units (int64), 148 = sg_probs, 152 = tcg_groups, 156 = tcg_units (int64)).
 static_assert(offsetof(PlanHeader, scan_pt) == 88, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, scan_tiles) == 56, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, eig_mats) == 232, "PlanHeader layout changed");
@@ -323,6 +369,9 @@ static_assert(offsetof(PlanHeader, ncovtc) == 432, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, covtc_flag_off) == 456, "PlanHeader layout changed");
 static_assert(offsetof(PlanHeader, sg_size) == 464 && offsetof(PlanHeader, sg_units) == 496 &&
                   offsetof(PlanHeader, sg_probs) == 592,
+              "PlanHeader layout changed");
+static_assert(offsetof(PlanHeader, tcg_groups) == 608 && offsetof(PlanHeader, tcg_units) == 624 &&
+                  sizeof(PlanHeader) == 656,
               "PlanHeader layout changed");
 
 // Scan tiles: kScanThreads threads, each evaluating PT consecutive grid points (tile shape
@@ -387,6 +436,8 @@ cudaError_t launch_scan_single(const double2 *B, int M, int K, int L, double lo,
 cudaError_t launch_scan_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, cudaStream_t s);
 cudaError_t launch_scan_tc_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, int *status,
                                  cudaStream_t s);
+cudaError_t launch_scan_tc_shared(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, int *status,
+                                  cudaStream_t s);
 // Tensor-core batch scan: tiles of 128 points; problems with M <= 32 only.
 constexpr int kTcBatchMaxM = 32;
 __host__ __device__ inline int tc_batch_cols(int Kf) {   // TMEM columns: 2 buffers x 2 accumulators of N

@@ -399,7 +399,7 @@ class BatchPlan:
 
     def launches(self) -> int:
         """Kernels one doa_solve_batch of this plan launches."""
-        h = self.host[:512].view(np.int32)
+        h = self.host[:1024].view(np.int32)
         cf = [int(v) for v in h[62:67]]                       # cov_first: classes MB = 2, 3, 4, other
         cov = sum(2 for c in range(3) if cf[c + 1] > cf[c]) + int(cf[4] > cf[3]) + int(h[5] > 0)
         eig_b = sum(int(c) > 0 for c in h[6:10])
@@ -410,6 +410,7 @@ class BatchPlan:
         covtc += int(covtc > 0)                                # the fixup kernel after them
         # grid-shared scan: a prep kernel and the scan kernel per M bucket that has groups
         shared = 2 * sum(int(u) > 0 for u in self.host[496:528].view(np.int64))
+        shared += 2 * int(h[152] > 0)                          # tensor-core groups: prep + scan
         return (int(h[3] > 0) + int(h[96] > 0) + int(h[104] > 0) + cov + covtc + eig_b + scan_b + shared + peaks
                 + int(h[100] > 0) + int(h[101] > 0))
 

@@ -178,3 +178,53 @@ def test_streamed_batch_matches_resident_solve(env):
     assert np.array_equal(oc.numpy(), cnt.cpu().numpy())
     assert np.array_equal(oi.numpy(), idx.cpu().numpy()) and np.array_equal(ov.numpy(), val.cpu().numpy())
     assert np.array_equal(sb.spectra(2).cpu().numpy(), P[32:48].cpu().numpy())
+
+
+def test_launch_count_matches_captured_graph(env):
+    """BatchPlan.launches() (the bench's gpu_launches figure) equals the number of kernel nodes that
+    a CUDA graph capture of one doa_solve_batch records (driver API through ctypes), for a plan
+    with grid-shared FP32 groups, per-problem FP32, grid-shared and per-problem tensor-core scans,
+    peak polish, tensor-core and CUDA-core covariances."""
+    import ctypes
+    torch, doa = env
+    cu = ctypes.CDLL("libcuda.so.1")
+    probs, keep = [], []
+
+    def add(inst, prec=0, polish=False):
+        X = torch.from_numpy(inst.X).cuda()
+        P = torch.empty(inst.L, dtype=torch.float32, device="cuda")
+        idx = torch.full((max(inst.d, 1),), -1, dtype=torch.int32, device="cuda")
+        val = torch.zeros(max(inst.d, 1), dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        keep.append((X, P, idx, val, cnt))
+        probs.append(doa.make_problem(X, inst.d, 1 << doa.MUSIC, doa.grid(inst.lo, inst.step, inst.L), P, idx, val,
+                                      cnt, prec=prec, polish=polish))
+
+    for i in range(6):
+        add(synth.custom(16, 3, 700 + i, None, 10.0, 0.1, seed=2200 + i), polish=(i % 2 == 0))
+    for i in range(3):
+        add(synth.custom(16, 3, 800 + i, None, 10.0, 0.1, seed=2210 + i), prec=doa.FP16X3)
+    add(synth.custom(8, 2, 900, None, 10.0, 1.0, seed=2220), prec=doa.BF16X3)      # its own grid: alone
+    add(synth.custom(64, 6, 2000, None, 10.0, 0.5, seed=2221))                       # CUDA-core covariance
+    status = torch.zeros(len(probs), dtype=torch.int32, device="cuda")
+    plan = doa.BatchPlan(probs)
+    ws = doa.workspace(plan)
+    s = torch.cuda.Stream()
+    doa.doa_solve_batch(plan, ws, status, stream=s)     # first call outside the capture
+    torch.cuda.synchronize()
+    graph = ctypes.c_void_p()
+    assert cu.cuStreamBeginCapture_v2(ctypes.c_void_p(s.cuda_stream), 0) == 0
+    doa.doa_solve_batch(plan, ws, status, stream=s)
+    assert cu.cuStreamEndCapture(ctypes.c_void_p(s.cuda_stream), ctypes.byref(graph)) == 0
+    n = ctypes.c_size_t(0)
+    assert cu.cuGraphGetNodes(graph, None, ctypes.byref(n)) == 0
+    nodes = (ctypes.c_void_p * n.value)()
+    assert cu.cuGraphGetNodes(graph, nodes, ctypes.byref(n)) == 0
+    kinds = []
+    for k in range(n.value):
+        t = ctypes.c_int(-1)
+        assert cu.cuGraphNodeGetType(ctypes.c_void_p(nodes[k]), ctypes.byref(t)) == 0
+        kinds.append(t.value)
+    cu.cuGraphDestroy(graph)
+    torch.cuda.synchronize()
+    assert kinds.count(0) == plan.launches(), (kinds, plan.launches())   # CU_GRAPH_NODE_TYPE_KERNEL = 0

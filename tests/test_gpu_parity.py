@@ -239,7 +239,7 @@ def test_single_calls_c1(env):
         assert idx.tolist() == ref["idx"].tolist()
 
 
-def _batch_solve(torch, doa, insts, masks, prec=0, eig_prec=0, polish=False):
+def _batch_solve(torch, doa, insts, masks, prec=0, eig_prec=0, polish=False, scan_group=None):
     tensors, probs = [], []
     for inst, mask in zip(insts, masks):
         nalg = bin(mask).count("1")
@@ -252,7 +252,7 @@ def _batch_solve(torch, doa, insts, masks, prec=0, eig_prec=0, polish=False):
         tensors.append((X, P, idx, val, cnt, ev))
         probs.append(doa.make_problem(X, inst.d, mask, doa.grid(inst.lo, inst.step, inst.L), P, idx, val, cnt, ev,
                                       prec=prec, eig_prec=eig_prec, polish=polish))
-    plan = doa.BatchPlan(probs)
+    plan = doa.BatchPlan(probs, scan_group=scan_group)
     ws = doa.workspace(plan)
     status = torch.full((len(insts),), -1, dtype=torch.int32, device="cuda")
     doa.doa_solve_batch(plan, ws, status)
@@ -260,8 +260,10 @@ def _batch_solve(torch, doa, insts, masks, prec=0, eig_prec=0, polish=False):
     return tensors, status.cpu().numpy()
 
 
-def _check_batch(torch, doa, insts, masks, prec=0, eig_prec=0):
-    tensors, status = _batch_solve(torch, doa, insts, masks, prec, eig_prec)
+def _check_batch(torch, doa, insts, masks, prec=0, eig_prec=0, polish=False, tie=1e-4):
+    """Every requested spectrum within DB_TOL of the oracle at every point, the peak indices equal
+    up to ties whose oracle values differ by less than `tie` (relative), the eigenvalues close."""
+    tensors, status = _batch_solve(torch, doa, insts, masks, prec, eig_prec, polish=polish)
     assert np.all(status == 0), status
     worst = 0.0
     for inst, mask, t in zip(insts, masks, tensors):
@@ -277,7 +279,7 @@ def _check_batch(torch, doa, insts, masks, prec=0, eig_prec=0):
             err = db_error(P[slot], ref["P"])
             worst = max(worst, err)
             assert err < DB_TOL, (inst.seed, alg, err)
-            ok, ties = compare_peaks(idx[slot][:cnt[slot]], ref["idx"], ref["P"], 1e-4)
+            ok, ties = compare_peaks(idx[slot][:cnt[slot]], ref["idx"], ref["P"], tie)
             assert ok, (inst.seed, alg, idx[slot][:cnt[slot]], ref["idx"], ties)
             slot += 1
         np.testing.assert_allclose(ev.cpu().numpy(), ref["evals"], rtol=0, atol=1e-5 * ref["evals"][0])
@@ -293,6 +295,14 @@ def test_batch_paper_density_sample(env):
     torch, doa = env
     insts = [synth.paper_density(i) for i in range(8)]
     _check_batch(torch, doa, insts, [0xF] * len(insts))
+
+
+def test_batch_paper_density_sample_polished(env):
+    """The headline configuration (peak polish on): peak indices equal to the oracle's up to ties
+    below float resolution (1e-6 relative), on a sample of the paper-density batch."""
+    torch, doa = env
+    insts = [synth.paper_density(i) for i in range(8, 24)]
+    _check_batch(torch, doa, insts, [0xF] * len(insts), polish=True, tie=1e-6)
 
 
 def test_batch_uneven_sample(env):
@@ -382,6 +392,31 @@ def test_batch_tensor_core_scan(env, prec):
     insts.append(synth.custom(5, 0, 64, [], 0.0, 0.5, seed=731))     # d = 0: Kf = M + 1
     masks.append(0xF)
     _check_batch(torch, doa, insts, masks, prec)
+
+
+@pytest.mark.parametrize("prec", [2, 3])   # DOA_BF16X3, DOA_FP16X3
+def test_batch_tensor_core_scan_grid_groups(env, prec):
+    """The grid-shared tensor-core scan: 40 problems of every M bucket (M = 6 .. 32) and mixed
+    algorithm subsets on one grid (groups of stacked factors, chunks of groups sharing a steering
+    block, a ragged last tile), against the oracle on every fifth problem (0.01 dB, same peaks),
+    and against the per-problem tensor-core scan (scan_group 1) on all of them."""
+    torch, doa = env
+    Ms = [6, 8, 12, 16, 16, 24, 32]
+    insts, masks = [], []
+    for i in range(40):
+        M = Ms[i % len(Ms)]
+        d = 1 + i % min(4, M - 2)
+        inst = synth.custom(M, d, 600 + 13 * i, None, 6.0 + (i % 9), 0.1, seed=1300 + i)
+        insts.append(inst)
+        masks.append([0xF, 0x2, 0x5, 0xA, 0x7][i % 5])
+    assert len({(x.lo, x.step, x.L) for x in insts}) == 1      # one grid for all
+    grouped, st = _batch_solve(torch, doa, insts, masks, prec)
+    assert np.all(st == 0), st
+    alone, st1 = _batch_solve(torch, doa, insts, masks, prec, scan_group=[1, 1, 1, 1])
+    assert np.all(st1 == 0), st1
+    for inst, mask, a, b in zip(insts, masks, grouped, alone):
+        assert db_error(a[1].cpu().numpy(), b[1].cpu().numpy().astype(np.float64)) < 2e-3, inst.seed
+    _check_batch(torch, doa, insts[::5], masks[::5], prec)
 
 
 def test_batch_fp64_jacobi(env):
