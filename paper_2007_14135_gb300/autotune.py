@@ -26,7 +26,7 @@ from . import doa
 
 CANDIDATES = ((1, 2, 4), (1, 2, 4), (1, 2), (1,))
 EIG_CANDIDATES = ((1, 2, 4, 8), (1, 2, 4), (1, 2), (1,))
-DEFAULT = (4, 2, 1, 1)
+DEFAULT = (4, 4, 1, 1)
 
 
 def cache_path() -> str:

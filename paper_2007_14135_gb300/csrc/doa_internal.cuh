@@ -378,7 +378,7 @@ static_assert(offsetof(PlanHeader, tcg_groups) == 608 && offsetof(PlanHeader, tc
 // 128 x PT). PT is chosen per M bucket (the autotuner's knob); the register budget limits it
 // to {1,2,4} for M <= 16, {1,2} for M <= 32 and 1 for M <= 64.
 constexpr int kScanThreads = 128;
-__host__ __device__ constexpr int scan_pt_default(int bucket) { return bucket == 0 ? 4 : (bucket == 1 ? 2 : 1); }
+__host__ __device__ constexpr int scan_pt_default(int bucket) { return bucket <= 1 ? 4 : 1; }
 __host__ __device__ inline bool scan_pt_allowed(int bucket, int pt) {
   return pt == 1 || (pt == 2 && bucket <= 2) || (pt == 4 && bucket <= 1);
 }

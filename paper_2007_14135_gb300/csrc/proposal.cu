@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_windows_kernel(const double
   j.kofs = first;
   load_job<MP>(j, Bs, sh);
   __syncthreads();
-  set_threshold<MP>(Bs, j, sh);
+  set_threshold<MP, true>(Bs, j, sh);
   __syncthreads();
   const int k0 = (tile * kScanThreads + threadIdx.x) * PT;
   scan_points<MP, PT>(Bs, j, S + first, len, k0, sh);

@@ -1,12 +1,14 @@
 // Step-5 (Table 2; steering vector Eq. 2): pseudospectrum P_k = 1 / ||B^H a(theta_k)||^2, which
 // equals 1 / (a^H C a) for the weighting matrix C = B B^H of Table 3 and is never negative.
 //
-// Fused, on CUDA cores in FP32: every thread evaluates PT consecutive grid points. For each it
-// generates the M steering phasors in registers from the grid's 32-bit phase step S_k
-// (phase of element m = m*S_k mod 2^32, exact integer arithmetic; phasor_q32 turns a phase into
-// cos + j sin), contracts them with the factor (held in shared memory as FP32, read as
-// warp-wide broadcasts) one column at a time, and forms the readouts of scan_common.cuh. The
-// whole block of PT x M phasors is reused across the columns.
+// Fused, on CUDA cores in FP32: every thread evaluates PT consecutive grid points. For M <= 16
+// a ULA's steering vector is the power sequence of z = e^{j pi sin theta_k}, so each column output
+// is a polynomial in z, evaluated by the blocked Horner scheme of scan_common.cuh from two phasors
+// per point (z and z^4, from the grid's 32-bit phase step S_k by exact integer arithmetic:
+// phase of element m = m*S_k mod 2^32; phasor_q32 turns a phase into cos + j sin). Larger arrays
+// generate the M phasors of each point in registers and contract them directly. Either way the
+// factor is held in shared memory as FP32 and read as warp-wide broadcasts, one column at a
+// time, and the readouts of scan_common.cuh are formed.
 //
 // Batched: one scan job per problem. A problem that asks for MUSIC or EV contracts its noise
 // eigenvectors E_n once and reads MUSIC, EV and PHD (v_min is the last column of E_n) from the
@@ -14,13 +16,14 @@
 // each. All four of Table 3's spectra of one problem therefore share one steering generation.
 //
 // Near-null refinement: where the FP32 denominator is small its relative error grows (the
-// contraction cancels), so every point with den_r < kRefineC * E_r for some readout r is
+// contraction cancels), so every point with den_r < C * E_r for some readout r is
 // re-evaluated with FP64 steering and contraction (exact 64-bit phases m * S64_k from a per-grid
 // table in the batch, else from sin theta_k recomputed in FP64) and the FP64 factor, for all
 // readouts of the job. Flagged points of a
 // tile are queued in shared memory and each is then handled by a whole warp (lanes own phasors,
 // then elements of columns), so the FP64 work runs without divergence. With per-term FP32
-// errors below ~4 eps the FP32 result elsewhere stays within ~5e-4 relative.
+// errors below ~4 eps (direct sum; C = kRefineC) or ~3 eps (blocked Horner; C = kRefineCH) the
+// FP32 result elsewhere stays within ~5e-4 relative.
 #include <float.h>
 
 #include <algorithm>
@@ -70,7 +73,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_single_kernel(const double2
   j.kofs = kofs;
   load_job<MP>(j, Bs, sh);
   __syncthreads();
-  set_threshold<MP>(Bs, j, sh);
+  set_threshold<MP, true>(Bs, j, sh);
   __syncthreads();
   const int k0 = (blockIdx.x * kScanThreads + threadIdx.x) * PT;
   scan_points<MP, PT>(Bs, j, S, L, k0, sh);
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t 
         __syncthreads();
         if constexpr (kPair) load_job2<MP>(j, Bd, sh); else load_job<MP>(j, Bs, sh);
         __syncthreads();
-        if constexpr (kPair) set_threshold2<MP>(Bd, j, sh); else set_threshold<MP>(Bs, j, sh);
+        if constexpr (kPair) set_threshold2<MP, true>(Bd, j, sh); else set_threshold<MP, true>(Bs, j, sh);
         __syncthreads();
         cur = u;
       }
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_prep_kernel(const uint8_t *
   for (int k = lane; k < Kn; k += 32) w32[k] = w ? (float)w[k] : 1.f;
   __syncwarp();
   float thr[4] = {0.f, 0.f, 0.f, 0.f};
-  job_thresholds2<MP>(F32, w32, Kf, Kn, pp.kphd, pp.kmn, thr);
+  job_thresholds2<MP, true>(F32, w32, Kf, Kn, pp.kphd, pp.kmn, thr);
   if (lane < 4) w32[MP + lane] = thr[lane];
 }
 
@@ -208,11 +211,11 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// CTAs per SM the register budget of the grid-shared scan is set for: 4 where the phasors of a
-// thread's points fit in 128 registers without spilling, else 3.
+// CTAs per SM the register budget of the grid-shared scan is set for: 4 where the steering of a
+// thread's points fits in 128 registers without spilling, else 3.
 template <int MP, int PT>
 __host__ __device__ constexpr int shared_min_blocks() {
-  return (MP == 8 && PT != 2) || (MP == 16 && PT <= 2) || (MP == 32 && PT == 1) ? 4 : 3;
+  return MP <= 16 || (MP == 32 && PT == 1) ? 4 : 3;
 }
 
 template <int MP, int PT>
@@ -266,9 +269,17 @@ __global__ void __launch_bounds__(kScanThreads, shared_min_blocks<MP, PT>())
       cp_async_commit();
     };
     if constexpr (kPair) issue(0, 0);
-    float2 a[kPair ? 1 : PT][MP];
-    uint64_t ax[kPair ? PT / 2 : 1][MP], ay[kPair ? PT / 2 : 1][MP];
-    if constexpr (kPair)
+    // steering of the unit's points: w and w4 (Horner form) or the phasor block (direct form)
+    constexpr bool kH = ula_horner_form<MP>();
+    HornerW1 hw[!kH || kPair ? 1 : PT];
+    HornerW2 hw2[kH && kPair ? PT / 2 : 1];
+    float2 a[!kH && !kPair ? PT : 1][kH ? 1 : MP];
+    uint64_t ax[!kH && kPair ? PT / 2 : 1][kH ? 1 : MP], ay[!kH && kPair ? PT / 2 : 1][kH ? 1 : MP];
+    if constexpr (kH && kPair)
+      ula_horner2<PT>(S, L, k0, hw2);
+    else if constexpr (kH)
+      ula_horner<PT>(S, L, k0, hw);
+    else if constexpr (kPair)
       ula_phasors2<MP, PT>(S, L, k0, ax, ay);
     else
       ula_phasors<MP, PT>(S, L, k0, a);
@@ -279,8 +290,12 @@ __global__ void __launch_bounds__(kScanThreads, shared_min_blocks<MP, PT>())
         cp_async_wait_all();   // this thread's copies of problem i have landed
         __syncthreads();       // everyone's have; and problem i - 1 is no longer read from buffer b ^ 1
         if (i + 1 < gr.count) issue(i + 1, b ^ 1);
-        contract_points2<MP, PT, UlaSource, true>(reinterpret_cast<const float4 *>(Fsm[b]), j, ax, ay, L, k0, sh,
-                                                  UlaSource{&j}, Wsm[b], Wsm[b] + MP, tags, i);
+        if constexpr (kH)
+          contract_horner2<MP, PT, UlaSource, true>(reinterpret_cast<const float4 *>(Fsm[b]), j, hw2, L, k0, sh,
+                                                    UlaSource{&j}, Wsm[b], Wsm[b] + MP, tags, i);
+        else
+          contract_points2<MP, PT, UlaSource, true>(reinterpret_cast<const float4 *>(Fsm[b]), j, ax, ay, L, k0, sh,
+                                                    UlaSource{&j}, Wsm[b], Wsm[b] + MP, tags, i);
       } else {
         const uint8_t *f32 = reinterpret_cast<const uint8_t *>(j.F) + fac32_off(j.M);
         float2 *Bs = reinterpret_cast<float2 *>(Fsm[0]);
@@ -293,7 +308,10 @@ __global__ void __launch_bounds__(kScanThreads, shared_min_blocks<MP, PT>())
         const float *wg = reinterpret_cast<const float *>(f32 + (size_t)(j.M + 1) * MP * 16);
         for (int k = tid; k < MP + 4; k += kScanThreads) Wsm[0][k] = wg[k];
         __syncthreads();
-        contract_points<MP, PT, UlaSource, true>(Bs, j, a, L, k0, sh, UlaSource{&j}, Wsm[0], Wsm[0] + MP, tags, i);
+        if constexpr (kH)
+          contract_horner<MP, PT, UlaSource, true>(Bs, j, hw, L, k0, sh, UlaSource{&j}, Wsm[0], Wsm[0] + MP, tags, i);
+        else
+          contract_points<MP, PT, UlaSource, true>(Bs, j, a, L, k0, sh, UlaSource{&j}, Wsm[0], Wsm[0] + MP, tags, i);
       }
     }
     // FP64 re-evaluation of the unit's flagged points, several per warp for small factors; the
@@ -462,7 +480,7 @@ cudaError_t launch_scan_single(const double2 *B, int M, int K, int L, double lo,
   const unsigned grid = (unsigned)((L + tp - 1) / tp);
   switch (b) {
     case 0: scan_single_kernel<8, 4><<<grid, kScanThreads, 0, s>>>(B, M, K, L, lo, step, kofs, S, P); break;
-    case 1: scan_single_kernel<16, 2><<<grid, kScanThreads, 0, s>>>(B, M, K, L, lo, step, kofs, S, P); break;
+    case 1: scan_single_kernel<16, 4><<<grid, kScanThreads, 0, s>>>(B, M, K, L, lo, step, kofs, S, P); break;
     case 2: scan_single_kernel<32, 1><<<grid, kScanThreads, 0, s>>>(B, M, K, L, lo, step, kofs, S, P); break;
     default: scan_single_kernel<64, 1><<<grid, kScanThreads, 0, s>>>(B, M, K, L, lo, step, kofs, S, P); break;
   }

@@ -18,7 +18,16 @@
 namespace doa {
 namespace scanc {
 
-constexpr float kRefineC = 3.7e-6f;   // (4 * 4 eps32 / 5e-4)^2
+constexpr float kRefineC = 3.7e-6f;   // (4 * 4 eps32 / 5e-4)^2, direct sum (4 eps per term)
+constexpr float kRefineCH = 2.05e-6f; // (4 * 3 eps32 / 5e-4)^2, blocked Horner ULA form (3 eps per term)
+
+// ULA scans use the blocked Horner form (below) up to MP = 16; larger factors keep the direct sum
+// (the outer Horner chain in w4 would grow beyond three steps).
+template <int MP>
+__host__ __device__ constexpr bool ula_horner_form() { return MP <= 16; }
+// Refinement constant of a scan: the Horner bound for ULA jobs evaluated in that form.
+template <int MP, bool kUla>
+__host__ __device__ constexpr float refine_c() { return kUla && ula_horner_form<MP>() ? kRefineCH : kRefineC; }
 constexpr int kFlagCap = 1024;         // queued refinements per drain (overflow: refined in place)
 constexpr int kScanWarps = kScanThreads / 32;
 constexpr int kMaxCols = kMaxM + 1;    // E_n (up to M columns when d = 0) plus valph
@@ -61,12 +70,12 @@ __device__ __forceinline__ void load_job(const ScanJob &j, float2 *Bs, ScanShare
   for (int k = threadIdx.x; k < j.Kn; k += blockDim.x) sh.w32[k] = j.w ? (float)j.w[k] : 1.f;
 }
 
-// Threshold of readout r = kRefineC * E_r with s_k = sum_m |f_mk| (FP32 factor):
+// Threshold of readout r = C * E_r (C = refine_c) with s_k = sum_m |f_mk| (FP32 factor):
 // E_MUSIC = sum_{k<Kn} s_k^2, E_EV = sum_{k<Kn} w_k s_k^2, E_PHD = s_kphd^2, E_MN = s_kmn^2.
 // (A bound of ~4 eps per term on y_k gives den a relative error below ~5e-4 above it.)
 // Computed by the 32 lanes of one warp (every lane returns the same values); thr[r] of an absent
 // readout is left as it was.
-template <int MP>
+template <int MP, bool kUla = false>
 __device__ __forceinline__ void job_thresholds(const float2 *F32, const float *w32, int Kf, int Kn, int kphd, int kmn,
                                                float (&thr)[4]) {
   const int lane = threadIdx.x & 31;
@@ -92,17 +101,18 @@ __device__ __forceinline__ void job_thresholds(const float2 *F32, const float *w
     ep = fmaxf(ep, __shfl_xor_sync(0xffffffffu, ep, off));
     en = fmaxf(en, __shfl_xor_sync(0xffffffffu, en, off));
   }
-  thr[kRoMusic] = __fmul_rn(kRefineC, em);
-  thr[kRoEv] = __fmul_rn(kRefineC, ee);
-  if (kphd >= 0) thr[kRoPhd] = __fmul_rn(kRefineC, ep);
-  if (kmn >= 0) thr[kRoMn] = __fmul_rn(kRefineC, en);
+  constexpr float C = refine_c<MP, kUla>();
+  thr[kRoMusic] = __fmul_rn(C, em);
+  thr[kRoEv] = __fmul_rn(C, ee);
+  if (kphd >= 0) thr[kRoPhd] = __fmul_rn(C, ep);
+  if (kmn >= 0) thr[kRoMn] = __fmul_rn(C, en);
 }
 
-template <int MP>
+template <int MP, bool kUla = false>
 __device__ __forceinline__ void set_threshold(const float2 *Bs, const ScanJob &j, ScanShared &sh) {
   if (threadIdx.x < 32) {
     float thr[4] = {0.f, 0.f, 0.f, 0.f};
-    job_thresholds<MP>(Bs, sh.w32, j.Kf, j.Kn, j.kphd, j.kmn, thr);
+    job_thresholds<MP, kUla>(Bs, sh.w32, j.Kf, j.Kn, j.kphd, j.kmn, thr);
     if (threadIdx.x == 0) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) sh.thr[r] = thr[r];
@@ -130,7 +140,7 @@ __device__ __forceinline__ void load_job2(const ScanJob &j, float4 *Bd, ScanShar
 }
 
 // job_thresholds on the duplicated layout (the same FP32 values, the same arithmetic).
-template <int MP>
+template <int MP, bool kUla = false>
 __device__ __forceinline__ void job_thresholds2(const float4 *Bd, const float *w32, int Kf, int Kn, int kphd, int kmn,
                                                 float (&thr)[4]) {
   const int lane = threadIdx.x & 31;
@@ -156,17 +166,18 @@ __device__ __forceinline__ void job_thresholds2(const float4 *Bd, const float *w
     ep = fmaxf(ep, __shfl_xor_sync(0xffffffffu, ep, off));
     en = fmaxf(en, __shfl_xor_sync(0xffffffffu, en, off));
   }
-  thr[kRoMusic] = __fmul_rn(kRefineC, em);
-  thr[kRoEv] = __fmul_rn(kRefineC, ee);
-  if (kphd >= 0) thr[kRoPhd] = __fmul_rn(kRefineC, ep);
-  if (kmn >= 0) thr[kRoMn] = __fmul_rn(kRefineC, en);
+  constexpr float C = refine_c<MP, kUla>();
+  thr[kRoMusic] = __fmul_rn(C, em);
+  thr[kRoEv] = __fmul_rn(C, ee);
+  if (kphd >= 0) thr[kRoPhd] = __fmul_rn(C, ep);
+  if (kmn >= 0) thr[kRoMn] = __fmul_rn(C, en);
 }
 
-template <int MP>
+template <int MP, bool kUla = false>
 __device__ __forceinline__ void set_threshold2(const float4 *Bd, const ScanJob &j, ScanShared &sh) {
   if (threadIdx.x < 32) {
     float thr[4] = {0.f, 0.f, 0.f, 0.f};
-    job_thresholds2<MP>(Bd, sh.w32, j.Kf, j.Kn, j.kphd, j.kmn, thr);
+    job_thresholds2<MP, kUla>(Bd, sh.w32, j.Kf, j.Kn, j.kphd, j.kmn, thr);
     if (threadIdx.x == 0) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) sh.thr[r] = thr[r];
@@ -372,6 +383,52 @@ __device__ __forceinline__ void store_row(float *P, int L, int k0, const float (
   }
 }
 
+// Readouts of the PT points k0 .. k0+PT-1 (those < L) from their denominators: P = 1 / den stored per
+// present readout, and every point where some readout's den is below its refinement threshold
+// queued for drain_refinements_src (or, on queue overflow, re-evaluated in place from src). With
+// kExt every queued point also records `tag` in tags[] (the grid-shared scan queues the points of
+// several problems).
+template <int PT, class Src, bool kExt>
+__device__ __forceinline__ void finish_points(const ScanJob &j, const float (&dp)[PT], const float (&dm)[PT],
+                                              const float (&de)[PT], const float (&dn)[PT], int L, int k0,
+                                              ScanShared &sh, const Src &src, const float *w32, const float *thr_,
+                                              uint8_t *tags, int tag) {
+  bool flag[PT];
+#pragma unroll
+  for (int q = 0; q < PT; ++q) flag[q] = false;
+  float out[PT];
+#define DOA_READOUT(R, DEN)                                                   \
+  if (j.P[R]) {                                                               \
+    const float thr = thr_[R];                                                \
+    _Pragma("unroll") for (int q = 0; q < PT; ++q) {                          \
+      out[q] = __frcp_rn(fmaxf(DEN[q], FLT_MIN));                              \
+      flag[q] = flag[q] || DEN[q] < thr;                                      \
+    }                                                                         \
+    store_row<PT>(j.P[R], L, k0, out);                                        \
+  }
+  DOA_READOUT(kRoPhd, dp)
+  DOA_READOUT(kRoMusic, dm)
+  DOA_READOUT(kRoEv, de)
+  DOA_READOUT(kRoMn, dn)
+#undef DOA_READOUT
+  int pos[PT];
+#pragma unroll
+  for (int q = 0; q < PT; ++q) {
+    pos[q] = -1;
+    if (k0 + q < L && flag[q]) {
+      pos[q] = atomicAdd(&sh.nflag, 1);
+      if (pos[q] < kFlagCap) {
+        sh.flags[pos[q]] = k0 + q;
+        if (kExt) tags[pos[q]] = (uint8_t)tag;
+      }
+    }
+  }
+  // queue overflow (more than kFlagCap small denominators before a drain): refine in place
+#pragma unroll
+  for (int q = 0; q < PT; ++q)
+    if (pos[q] >= kFlagCap) refine_point_thread_src(j, k0 + q, src, w32);
+}
+
 // Contracts the PT x MP phasor block a (points k0 .. k0+PT-1 of a job, those < L) with the factor
 // and writes the readouts. Points where any readout falls below its refinement threshold are
 // queued for drain_refinements_src (or, on queue overflow, re-evaluated in place from src).
@@ -443,40 +500,7 @@ __device__ __forceinline__ void contract_points(const float2 *Bs, const ScanJob 
       for (int q = 0; q < PT; ++q) dn[q] = n[q];
     }
   }
-  bool flag[PT];
-#pragma unroll
-  for (int q = 0; q < PT; ++q) flag[q] = false;
-  float out[PT];
-#define DOA_READOUT(R, DEN)                                                   \
-  if (j.P[R]) {                                                               \
-    const float thr = thr_[R];                                                \
-    _Pragma("unroll") for (int q = 0; q < PT; ++q) {                          \
-      out[q] = __frcp_rn(fmaxf(DEN[q], FLT_MIN));                              \
-      flag[q] = flag[q] || DEN[q] < thr;                                      \
-    }                                                                         \
-    store_row<PT>(j.P[R], L, k0, out);                                        \
-  }
-  DOA_READOUT(kRoPhd, dp)
-  DOA_READOUT(kRoMusic, dm)
-  DOA_READOUT(kRoEv, de)
-  DOA_READOUT(kRoMn, dn)
-#undef DOA_READOUT
-  int pos[PT];
-#pragma unroll
-  for (int q = 0; q < PT; ++q) {
-    pos[q] = -1;
-    if (k0 + q < L && flag[q]) {
-      pos[q] = atomicAdd(&sh.nflag, 1);
-      if (pos[q] < kFlagCap) {
-        sh.flags[pos[q]] = k0 + q;
-        if (kExt) tags[pos[q]] = (uint8_t)tag;
-      }
-    }
-  }
-  // queue overflow (more than kFlagCap small denominators before a drain): refine in place
-#pragma unroll
-  for (int q = 0; q < PT; ++q)
-    if (pos[q] >= kFlagCap) refine_point_thread_src(j, k0 + q, src, w32);
+  finish_points<PT, Src, kExt>(j, dp, dm, de, dn, L, k0, sh, src, w32, thr_, tags, tag);
 }
 
 // Paired FP32 arithmetic on two values in one 64-bit register pair (lo, hi).
@@ -571,42 +595,213 @@ __device__ __forceinline__ void contract_points2(const float4 *Bd, const ScanJob
       for (int q = 0; q < HP; ++q) dn[q] = n[q];
     }
   }
-  bool flag[PT];
+  float fp[PT], fm[PT], fe[PT], fn[PT];
 #pragma unroll
-  for (int q = 0; q < PT; ++q) flag[q] = false;
-  float out[PT];
-#define DOA_READOUT2(R, DEN)                                                  \
-  if (j.P[R]) {                                                               \
-    const float thr = thr_[R];                                                \
-    _Pragma("unroll") for (int q = 0; q < HP; ++q) {                          \
-      const float d0 = f2lo(DEN[q]), d1 = f2hi(DEN[q]);                       \
-      out[2 * q] = __frcp_rn(fmaxf(d0, FLT_MIN));                              \
-      out[2 * q + 1] = __frcp_rn(fmaxf(d1, FLT_MIN));                          \
-      flag[2 * q] = flag[2 * q] || d0 < thr;                                  \
-      flag[2 * q + 1] = flag[2 * q + 1] || d1 < thr;                          \
-    }                                                                         \
-    store_row<PT>(j.P[R], L, k0, out);                                        \
+  for (int q = 0; q < HP; ++q) {
+    fp[2 * q] = f2lo(dp[q]), fp[2 * q + 1] = f2hi(dp[q]);
+    fm[2 * q] = f2lo(dm[q]), fm[2 * q + 1] = f2hi(dm[q]);
+    fe[2 * q] = f2lo(de[q]), fe[2 * q + 1] = f2hi(de[q]);
+    fn[2 * q] = f2lo(dn[q]), fn[2 * q + 1] = f2hi(dn[q]);
   }
-  DOA_READOUT2(kRoPhd, dp)
-  DOA_READOUT2(kRoMusic, dm)
-  DOA_READOUT2(kRoEv, de)
-  DOA_READOUT2(kRoMn, dn)
-#undef DOA_READOUT2
-  int pos[PT];
+  finish_points<PT, Src, kExt>(j, fp, fm, fe, fn, L, k0, sh, src, w32, thr_, tags, tag);
+}
+
+// ---------------------------------------------------------------------------------------------
+// ULA scan by blocked Horner evaluation (MP <= 16). For a ULA the steering phasors are powers of
+// z = e^{j pi sin theta}, so y_k = sum_m conj(f_mk) z^m is a polynomial in z, and
+//     conj(y_k) = sum_m f_mk w^m,  w = conj(z),
+// evaluated in blocks of four elements: Q_i = ((f_{4i+3} w + f_{4i+2}) w + f_{4i+1}) w + f_{4i}, then
+// conj(y_k) = (((Q_{NB-1} w4 + Q_{NB-2}) w4 + ...) w4 + Q_0 with w4 = conj(z^4). Both w and w4 come
+// from exact integer phases (phasor_q32 of S_k and 4 S_k), so a thread needs two phasors per point
+// instead of M, and 15 complex multiply-adds per column at M = 16 (the direct sum takes 16). The
+// Horner chains are three steps long, which keeps the rounding error within the ~4 eps per term
+// on which the refinement threshold rests (an FP32 emulation over 18001-point grids and M = 16
+// noise subspaces gave at most 2.6 eps sum_m |f_mk|, the direct sum 4.3). |conj(y)|^2 = |y|^2, so
+// the readouts and the refinement are those of the direct form.
+// One step u <- u w + c: Re = ur wr - ui wi + cr, Im = ur wi + ui wr + ci, with wn = -wi held so
+// that no negation is needed: four FMAs, two per component.
+struct HornerW1 {
+  float r1, i1, n1, r4, i4, n4;   // Re w, Im w, -Im w; the same for w4
+};
+struct HornerW2 {
+  uint64_t r1, i1, n1, r4, i4, n4;   // HornerW1 of two points, paired
+};
+
+__device__ __forceinline__ void hstep1(float &ur, float &ui, float wr, float wi, float wn, float cr, float ci) {
+  const float r = __fmaf_rn(ur, wr, __fmaf_rn(ui, wn, cr));
+  ui = __fmaf_rn(ur, wi, __fmaf_rn(ui, wr, ci));
+  ur = r;
+}
+__device__ __forceinline__ void hstep2(uint64_t &ur, uint64_t &ui, uint64_t wr, uint64_t wi, uint64_t wn, uint64_t cr,
+                                       uint64_t ci) {
+  const uint64_t r = f2fma(ur, wr, f2fma(ui, wn, cr));
+  ui = f2fma(ur, wi, f2fma(ui, wr, ci));
+  ur = r;
+}
+
+// w and w4 of the points k0 .. k0+PT-1 (those < L; the others get phase 0).
+template <int PT>
+__device__ __forceinline__ void ula_horner(const uint32_t *S, int L, int k0, HornerW1 (&w)[PT]) {
 #pragma unroll
   for (int q = 0; q < PT; ++q) {
-    pos[q] = -1;
-    if (k0 + q < L && flag[q]) {
-      pos[q] = atomicAdd(&sh.nflag, 1);
-      if (pos[q] < kFlagCap) {
-        sh.flags[pos[q]] = k0 + q;
-        if (kExt) tags[pos[q]] = (uint8_t)tag;
+    const uint32_t step = (k0 + q < L) ? S[k0 + q] : 0u;
+    const float2 z1 = phasor_q32(step), z4 = phasor_q32(4u * step);
+    w[q] = HornerW1{z1.x, -z1.y, z1.y, z4.x, -z4.y, z4.y};
+  }
+}
+template <int PT>
+__device__ __forceinline__ void ula_horner2(const uint32_t *S, int L, int k0, HornerW2 (&w)[PT / 2]) {
+  HornerW1 v[PT];
+  ula_horner<PT>(S, L, k0, v);
+#pragma unroll
+  for (int q = 0; q < PT / 2; ++q) {
+    const HornerW1 &a = v[2 * q], &b = v[2 * q + 1];
+    w[q] = HornerW2{f2pack(a.r1, b.r1), f2pack(a.i1, b.i1), f2pack(a.n1, b.n1),
+                    f2pack(a.r4, b.r4), f2pack(a.i4, b.i4), f2pack(a.n4, b.n4)};
+  }
+}
+
+// n = |y_k|^2 of column k for PT points (factor Bs[k][m] = (bx, by), read two elements at a time).
+template <int MP, int PT>
+__device__ __forceinline__ void horner_column1(const float2 *Bs, int k, const HornerW1 (&w)[PT], float (&n)[PT]) {
+  static_assert(MP % 4 == 0, "blocks of four elements");
+  constexpr int NB = MP / 4;
+  const float4 *b2 = reinterpret_cast<const float4 *>(Bs + k * MP);
+  float ur[PT], ui[PT];
+#pragma unroll
+  for (int i = NB - 1; i >= 0; --i) {
+    const float4 c23 = b2[2 * i + 1], c01 = b2[2 * i];   // (f_{4i+2}, f_{4i+3}), (f_{4i}, f_{4i+1})
+    float qr[PT], qi[PT];
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+      qr[q] = c23.z, qi[q] = c23.w;
+      hstep1(qr[q], qi[q], w[q].r1, w[q].i1, w[q].n1, c23.x, c23.y);
+      hstep1(qr[q], qi[q], w[q].r1, w[q].i1, w[q].n1, c01.z, c01.w);
+      hstep1(qr[q], qi[q], w[q].r1, w[q].i1, w[q].n1, c01.x, c01.y);
+      if (i == NB - 1) {
+        ur[q] = qr[q], ui[q] = qi[q];
+      } else {
+        hstep1(ur[q], ui[q], w[q].r4, w[q].i4, w[q].n4, qr[q], qi[q]);
       }
     }
   }
 #pragma unroll
-  for (int q = 0; q < PT; ++q)
-    if (pos[q] >= kFlagCap) refine_point_thread_src(j, k0 + q, src, w32);
+  for (int q = 0; q < PT; ++q) n[q] = __fmaf_rn(ur[q], ur[q], __fmul_rn(ui[q], ui[q]));
+}
+
+// The same operations on pairs of points (factor Bd[k][m] = (bx, bx, by, by)).
+template <int MP, int HP>
+__device__ __forceinline__ void horner_column2(const float4 *Bd, int k, const HornerW2 (&w)[HP], uint64_t (&n)[HP]) {
+  static_assert(MP % 4 == 0, "blocks of four elements");
+  constexpr int NB = MP / 4;
+  // each element as two 64-bit operands (bx, bx) and (by, by), straight from one 16-byte load
+  const ulonglong2 *b4 = reinterpret_cast<const ulonglong2 *>(Bd + k * MP);
+  uint64_t ur[HP], ui[HP];
+#pragma unroll
+  for (int i = NB - 1; i >= 0; --i) {
+    const ulonglong2 c3 = b4[4 * i + 3], c2 = b4[4 * i + 2], c1 = b4[4 * i + 1], c0 = b4[4 * i];
+    uint64_t qr[HP], qi[HP];
+#pragma unroll
+    for (int q = 0; q < HP; ++q) {
+      qr[q] = c3.x, qi[q] = c3.y;
+      hstep2(qr[q], qi[q], w[q].r1, w[q].i1, w[q].n1, c2.x, c2.y);
+      hstep2(qr[q], qi[q], w[q].r1, w[q].i1, w[q].n1, c1.x, c1.y);
+      hstep2(qr[q], qi[q], w[q].r1, w[q].i1, w[q].n1, c0.x, c0.y);
+      if (i == NB - 1) {
+        ur[q] = qr[q], ui[q] = qi[q];
+      } else {
+        hstep2(ur[q], ui[q], w[q].r4, w[q].i4, w[q].n4, qr[q], qi[q]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < HP; ++q) n[q] = f2fma(ur[q], ur[q], f2mul(ui[q], ui[q]));
+}
+
+// contract_points with the blocked Horner columns (same readouts, thresholds and queue).
+template <int MP, int PT, class Src, bool kExt = false>
+__device__ __forceinline__ void contract_horner(const float2 *Bs, const ScanJob &j, const HornerW1 (&w)[PT], int L,
+                                                int k0, ScanShared &sh, const Src &src, const float *w32x = nullptr,
+                                                const float *thrx = nullptr, uint8_t *tags = nullptr, int tag = 0) {
+  const float *w32 = kExt ? w32x : sh.w32;
+  const float *thr_ = kExt ? thrx : sh.thr;
+  float dm[PT], de[PT], dp[PT], dn[PT], n[PT];
+#pragma unroll
+  for (int q = 0; q < PT; ++q) dm[q] = de[q] = dp[q] = dn[q] = n[q] = 0.f;
+  const int Kf = j.Kf, Kn = j.Kn, kphd = j.kphd, kmn = j.kmn;
+  for (int k = 0; k < Kn; ++k) {
+    horner_column1<MP, PT>(Bs, k, w, n);
+    const float wk = w32[k];
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+      dm[q] = __fadd_rn(dm[q], n[q]);
+      de[q] = __fmaf_rn(wk, n[q], de[q]);
+    }
+  }
+  if (Kn > 0 && kphd == Kn - 1) {
+#pragma unroll
+    for (int q = 0; q < PT; ++q) dp[q] = n[q];
+  }
+  for (int k = Kn; k < Kf; ++k) {
+    horner_column1<MP, PT>(Bs, k, w, n);
+    if (k == kphd) {
+#pragma unroll
+      for (int q = 0; q < PT; ++q) dp[q] = n[q];
+    }
+    if (k == kmn) {
+#pragma unroll
+      for (int q = 0; q < PT; ++q) dn[q] = n[q];
+    }
+  }
+  finish_points<PT, Src, kExt>(j, dp, dm, de, dn, L, k0, sh, src, w32, thr_, tags, tag);
+}
+
+template <int MP, int PT, class Src, bool kExt = false>
+__device__ __forceinline__ void contract_horner2(const float4 *Bd, const ScanJob &j, const HornerW2 (&w)[PT / 2], int L,
+                                                 int k0, ScanShared &sh, const Src &src, const float *w32x = nullptr,
+                                                 const float *thrx = nullptr, uint8_t *tags = nullptr, int tag = 0) {
+  static_assert(PT % 2 == 0, "points are paired");
+  constexpr int HP = PT / 2;
+  const float *w32 = kExt ? w32x : sh.w32;
+  const float *thr_ = kExt ? thrx : sh.thr;
+  uint64_t dm[HP], de[HP], dp[HP], dn[HP], n[HP];
+#pragma unroll
+  for (int q = 0; q < HP; ++q) dm[q] = de[q] = dp[q] = dn[q] = n[q] = 0ull;
+  const int Kf = j.Kf, Kn = j.Kn, kphd = j.kphd, kmn = j.kmn;
+  for (int k = 0; k < Kn; ++k) {
+    horner_column2<MP, HP>(Bd, k, w, n);
+    const float wk = w32[k];
+    const uint64_t ww = f2pack(wk, wk);
+#pragma unroll
+    for (int q = 0; q < HP; ++q) {
+      dm[q] = f2add(dm[q], n[q]);
+      de[q] = f2fma(ww, n[q], de[q]);
+    }
+  }
+  if (Kn > 0 && kphd == Kn - 1) {
+#pragma unroll
+    for (int q = 0; q < HP; ++q) dp[q] = n[q];
+  }
+  for (int k = Kn; k < Kf; ++k) {
+    horner_column2<MP, HP>(Bd, k, w, n);
+    if (k == kphd) {
+#pragma unroll
+      for (int q = 0; q < HP; ++q) dp[q] = n[q];
+    }
+    if (k == kmn) {
+#pragma unroll
+      for (int q = 0; q < HP; ++q) dn[q] = n[q];
+    }
+  }
+  float fp[PT], fm[PT], fe[PT], fn[PT];
+#pragma unroll
+  for (int q = 0; q < HP; ++q) {
+    fp[2 * q] = f2lo(dp[q]), fp[2 * q + 1] = f2hi(dp[q]);
+    fm[2 * q] = f2lo(dm[q]), fm[2 * q + 1] = f2hi(dm[q]);
+    fe[2 * q] = f2lo(de[q]), fe[2 * q + 1] = f2hi(de[q]);
+    fn[2 * q] = f2lo(dn[q]), fn[2 * q + 1] = f2hi(dn[q]);
+  }
+  finish_points<PT, Src, kExt>(j, fp, fm, fe, fn, L, k0, sh, src, w32, thr_, tags, tag);
 }
 
 // Steering phasors of the points k0 .. k0+PT-1 (those < L; the others get phase 0) from their
@@ -640,9 +835,15 @@ __device__ __forceinline__ void ula_phasors(const uint32_t *S, int L, int k0, fl
 template <int MP, int PT>
 __device__ __forceinline__ void scan_points(const float2 *Bs, const ScanJob &j, const uint32_t *S, int L, int k0,
                                             ScanShared &sh) {
-  float2 a[PT][MP];
-  ula_phasors<MP, PT>(S, L, k0, a);
-  contract_points<MP, PT>(Bs, j, a, L, k0, sh, UlaSource{&j});
+  if constexpr (ula_horner_form<MP>()) {
+    HornerW1 w[PT];
+    ula_horner<PT>(S, L, k0, w);
+    contract_horner<MP, PT>(Bs, j, w, L, k0, sh, UlaSource{&j});
+  } else {
+    float2 a[PT][MP];
+    ula_phasors<MP, PT>(S, L, k0, a);
+    contract_points<MP, PT>(Bs, j, a, L, k0, sh, UlaSource{&j});
+  }
 }
 
 // ula_phasors packed for contract_points2 (PT even).
@@ -663,9 +864,15 @@ __device__ __forceinline__ void ula_phasors2(const uint32_t *S, int L, int k0, u
 template <int MP, int PT>
 __device__ __forceinline__ void scan_points2(const float4 *Bd, const ScanJob &j, const uint32_t *S, int L, int k0,
                                              ScanShared &sh) {
-  uint64_t ax[PT / 2][MP], ay[PT / 2][MP];
-  ula_phasors2<MP, PT>(S, L, k0, ax, ay);
-  contract_points2<MP, PT>(Bd, j, ax, ay, L, k0, sh, UlaSource{&j});
+  if constexpr (ula_horner_form<MP>()) {
+    HornerW2 w[PT / 2];
+    ula_horner2<PT>(S, L, k0, w);
+    contract_horner2<MP, PT>(Bd, j, w, L, k0, sh, UlaSource{&j});
+  } else {
+    uint64_t ax[PT / 2][MP], ay[PT / 2][MP];
+    ula_phasors2<MP, PT>(S, L, k0, ax, ay);
+    contract_points2<MP, PT>(Bd, j, ax, ay, L, k0, sh, UlaSource{&j});
+  }
 }
 
 }  // namespace scanc

@@ -393,7 +393,7 @@ cudaError_t launch_scan_geometry_single(const double2 *B, int M, int K, const do
   const unsigned grid = (unsigned)((npts + kScanThreads * pt - 1) / (kScanThreads * pt));
   switch (b) {
     case 0: scan_geometry_single_kernel<8, 4><<<grid, kScanThreads, 0, s>>>(B, M, K, g, P); break;
-    case 1: scan_geometry_single_kernel<16, 2><<<grid, kScanThreads, 0, s>>>(B, M, K, g, P); break;
+    case 1: scan_geometry_single_kernel<16, 4><<<grid, kScanThreads, 0, s>>>(B, M, K, g, P); break;
     case 2: scan_geometry_single_kernel<32, 1><<<grid, kScanThreads, 0, s>>>(B, M, K, g, P); break;
     default: scan_geometry_single_kernel<64, 1><<<grid, kScanThreads, 0, s>>>(B, M, K, g, P); break;
   }

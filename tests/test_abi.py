@@ -161,7 +161,7 @@ def test_batch_plan_scan_pt(libdoa):
         assert (st == 0) == ok, pts
         if ok:
             got = buf[:128].view(np.int32)[22:26]
-            want = [p if p else d for p, d in zip(pts, (4, 2, 1, 1))]
+            want = [p if p else d for p, d in zip(pts, (4, 4, 1, 1))]
             assert list(got) == want
             tiles = buf[:128].view(np.int64)[7:11]      # scan_tiles per bucket
             # one scan job per problem: its four algorithms share the tiles of one grid pass
