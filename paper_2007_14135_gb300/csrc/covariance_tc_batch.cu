@@ -27,8 +27,10 @@
 // written to the workspace as FP64 (full Hermitian matrix, zero imaginary diagonal).
 //
 // Roles (one persistent CTA per SM, static round-robin over the problems, longest first):
-//   warps 0-7  producers: slice one stage (64 snapshots) into the operand ring (128B-swizzled,
-//              K-major); the first stage of a problem also fixes its scaling unit;
+//   warps 0-7  producers, four groups of two warps: group q slices the operand stages g = q (mod 4)
+//              (64 snapshots each) into a five-deep operand ring (128B-swizzled, K-major), so four
+//              stages are sliced at once; the group that slices a problem's first stage also fixes
+//              its scaling unit and hands it to the others;
 //   warps 8-11 TMEM readout (warp w reads lanes 32 (w % 4) ..), int64 sums, per-problem finalize;
 //   warp 13    one thread: TMA bulk copies (cp.async.bulk) of 256 snapshots of each of the M rows
 //              per staging stage (one copy per row: the copy engine's cost is per request, so few
@@ -54,13 +56,16 @@ constexpr int kCbSnap = 64;          // snapshots per operand stage (64 BF16 = o
 constexpr int kCbStgSnap = 256;      // snapshots per staging stage (one bulk copy of 2 KB per row)
 constexpr int kCbSub = kCbStgSnap / kCbSnap;
 constexpr int kCbStg = 3;            // staging ring depth (99 KB of reads in flight per SM at M = 16)
-constexpr int kCbOps = 4;            // operand ring depth
+constexpr int kCbOps = 5;            // operand ring depth (four stages being sliced, one waiting)
 constexpr int kCbWin = 15;           // operand stages per exact accumulation window (960 snapshots)
 constexpr int kCbRowPitch = 2064;    // staging bytes per element row (2048 + 16)
 // Warp w issues from SM sub-partition w % 4. The readout warps take one per sub-partition (warp
 // w reads TMEM lanes 32 (w % 4) ..); the MMA issuer shares sub-partition 0 with the readout of
 // slice 4 (two blocks), away from the readout of slice 0 (five blocks, sub-partition 1).
 constexpr int kCbProdWarps = 8;     // producer warps 0-7
+constexpr int kCbGroups = 4;        // producer groups of two warps; group q slices the stages g = q (mod 4)
+constexpr int kCbGroupWarps = kCbProdWarps / kCbGroups;
+constexpr int kCbTasks = 256 / (32 * kCbGroupWarps);   // tasks per producer thread and stage
 constexpr int kCbReadWarp0 = 8;     // readout warps 8-11
 constexpr int kCbMmaWarp = 12, kCbTmaWarp = 13;
 constexpr int kCbThreads = 32 * 14;
@@ -145,12 +150,14 @@ struct CbLayout {
 struct CbShared {
   uint64_t full[kCbStg], empty[kCbStg], opfull[kCbOps], opempty[kCbOps], accfull[2], accempty[2];
   uint64_t efull[kCbRing], eempty[kCbRing], fin;
-  uint64_t pred[2];           // producers' first-stage maximum exchange (count 4 warps)
+  uint64_t pred[kCbGroups][2];  // a group's first-stage maximum exchange (count 2 warps)
+  uint64_t sfull[kCbRing];     // scaling unit of ring slot fixed (producers -> the other groups)
   uint64_t rb[2];             // readout warps' finalize steps (count 4 warps)
   uint32_t tmem;
   int abort;
   int eexp[kCbRing];          // scaling exponent k of the problem in ring slot (or INT_MIN: marked)
-  float red[2][kCbProdWarps];  // producers' first-stage maxima (double-buffered by problem parity)
+  float escale[kCbRing];      // scaling factor 2^(5 - k) of the problem in ring slot (0: marked)
+  float red[kCbGroups][2][kCbGroupWarps];   // a group's first-stage maxima (double-buffered)
 };
 
 __device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
@@ -163,6 +170,9 @@ __device__ __forceinline__ void arrive_tx(uint32_t mbar, uint32_t bytes) {
 }
 __device__ __forceinline__ void arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void arrive_cnt(uint32_t mbar, uint32_t cnt) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(cnt) : "memory");
 }
 __device__ __forceinline__ void commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
@@ -301,14 +311,15 @@ __global__ void __launch_bounds__(kCbThreads, 1) covariance_tc_batch_kernel(cons
     };
     init(sh.full, kCbStg, 1);
     init(sh.empty, kCbStg, kCbProdWarps);
-    init(sh.opfull, kCbOps, kCbProdWarps);
+    init(sh.opfull, kCbOps, kCbGroupWarps);
     init(sh.opempty, kCbOps, 1);
     init(sh.accfull, 2, 1);
     init(sh.accempty, 2, 4);
     init(sh.efull, kCbRing, 1);
     init(sh.eempty, kCbRing, 4);
     init(&sh.fin, 1, 1);
-    init(sh.pred, 2, kCbProdWarps);
+    for (int q = 0; q < kCbGroups; ++q) init(sh.pred[q], 2, kCbGroupWarps);
+    init(sh.sfull, kCbRing, 1);
     init(sh.rb, 2, 4);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sh.abort = 0;
@@ -325,80 +336,121 @@ __global__ void __launch_bounds__(kCbThreads, 1) covariance_tc_batch_kernel(cons
 
   if (warp < kCbProdWarps) {
     // ---------------------------------------------------------------- producers
-    // tasks: MP rows x (64 / SN) chunks of SN snapshots, one per thread. A quarter-warp takes 8
-    // consecutive rows of one chunk (its 16-byte staging loads then fall on distinct banks, the
-    // rows being 528 bytes apart), and the two quarter-warps of a half-warp take two neighbouring
-    // chunks (its 8-byte operand stores fill both halves of each swizzled 16-byte slot).
+    // Four groups of two warps: group q slices the operand stages g = q (mod 4) of the CTA's stage
+    // sequence, so four stages are sliced at once and a group has four stages' time for one. A
+    // thread takes kCbTasks of the stage's 256 tasks (MP rows x (64 / SN) chunks of SN
+    // snapshots); its task j is virtual thread vt = lt + 64 j of a 256-thread layout in which a
+    // quarter-warp takes 8 consecutive rows of one chunk (its 16-byte staging loads then fall on
+    // distinct banks, the rows being 2064 bytes apart) and the two quarter-warps of a half-warp
+    // take two neighbouring chunks (its 8-byte operand stores fill both halves of each swizzled
+    // 16-byte slot); every warp instruction covers one such virtual warp.
     constexpr int SN = S::kSN;
-    const int qw = tid >> 3, r8 = tid & 7;
-    const int m = MP == 16 ? r8 + 8 * ((qw >> 1) & 1) : r8;
-    const int c = MP == 16 ? (qw & 1) + 2 * (qw >> 2) : qw;
-    uint32_t g = 0, gs = 0;                      // operand and staging stage counters
-    int kth = 0;                                 // problem counter of this CTA
-    for (int pi = blockIdx.x; pi < count && !*abort; pi += gridDim.x, ++kth) {
+    const int grp = warp / kCbGroupWarps, lt = tid % (32 * kCbGroupWarps);
+    int mt[kCbTasks], ct[kCbTasks];   // the tasks' row and chunk
+    uint32_t so[kCbTasks];            // swizzled byte offset of the task's Re row in slice block 0
+#pragma unroll
+    for (int j = 0; j < kCbTasks; ++j) {
+      const int vt = lt + 32 * kCbGroupWarps * j, qw = vt >> 3, r8 = vt & 7;
+      mt[j] = MP == 16 ? r8 + 8 * ((qw >> 1) & 1) : r8;
+      ct[j] = MP == 16 ? (qw & 1) + 2 * (qw >> 2) : qw;
+      so[j] = sw128(mt[j], SN * ct[j]);
+    }
+    // rows block * kBlock + m and that + MP (Im plane): multiples of 8 rows apart, so the swizzle
+    // pattern of row m carries over and the offsets differ by whole 1024-byte row groups
+    constexpr uint32_t kImOff = (uint32_t)(MP / 8) * 1024u;
+    uint32_t g0 = 0, gs0 = 0;   // CTA operand / staging stage of the current problem's first stage
+    uint32_t own = 0;           // problems whose scaling unit this group has fixed
+    int kth = 0;                // problem counter of this CTA
+    bool live = true;
+    for (int pi = blockIdx.x; pi < count && live && !*abort; pi += gridDim.x, ++kth) {
       const PlanProblem &pp = probs[list[pi]];
       const int M = pp.p.M, N = pp.p.N, ldx = pp.p.ldx;
       const float2 *X = reinterpret_cast<const float2 *>(pp.p.X);
-      const int nst = (N + kCbSnap - 1) / kCbSnap;
+      const int nst = (N + kCbSnap - 1) / kCbSnap, nstg = (N + kCbStgSnap - 1) / kCbStgSnap;
+      const int r = kth % kCbRing;
       float scale = 0.f;
-      bool bad = false, live = true;
-      for (int s = 0; s < nst && live; ++s, ++g) {
+      bool bad = false, have = false;
+      for (int s = (grp - (int)(g0 % kCbGroups) + kCbGroups) % kCbGroups; s < nst; s += kCbGroups) {
+        const uint32_t g = g0 + (uint32_t)s, gs = gs0 + (uint32_t)(s / kCbSub);
         const int sub = s % kCbSub, ss = gs % kCbStg, os = g % kCbOps;
-        if (sub == 0 && !warp_wait(smem_u32(&sh.full[ss]), (gs / kCbStg) & 1u, abort)) break;
-        // this task's SN snapshots of row m (zeros past N and for rows >= M); t counts snapshots
+        if (!warp_wait(smem_u32(&sh.full[ss]), (gs / kCbStg) & 1u, abort)) {
+          live = false;
+          break;
+        }
+        // the tasks' SN snapshots of row m (zeros past N and for rows >= M); t counts snapshots
         // from the start of the staging stage, whose first cb arrived by bulk copy
-        float re[SN], im[SN];
+        float re[kCbTasks][SN], im[kCbTasks][SN];
         const int t0 = (s - sub) * kCbSnap, cnt = min(kCbStgSnap, N - t0), cb = cnt & ~1;
-        const float *stg = reinterpret_cast<const float *>(sm + Lay::kOffStg + ss * Lay::kStgBytes +
-                                                           m * kCbRowPitch) + 2 * (sub * kCbSnap + c * SN);
+        const uint8_t *stg = sm + Lay::kOffStg + ss * Lay::kStgBytes;
 #pragma unroll
-        for (int q = 0; q < SN / 2; ++q) {
-          const int t = sub * kCbSnap + c * SN + 2 * q;
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (m < M) {
-            if (t + 1 < cb) {
-              v = *reinterpret_cast<const float4 *>(stg + 4 * q);
-            } else {
-              if (t < cnt) {   // t >= cb: the odd last snapshot, outside the bulk copy
+        for (int j = 0; j < kCbTasks; ++j) {
+          const int m = mt[j], c = ct[j];
+#pragma unroll
+          for (int q = 0; q < SN / 2; ++q) {
+            const int t = sub * kCbSnap + c * SN + 2 * q;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (m < M) {
+              if (t + 1 < cb) {
+                v = *reinterpret_cast<const float4 *>(stg + m * kCbRowPitch + 8 * t);
+              } else if (t < cnt) {   // t >= cb: the odd last snapshot, outside the bulk copy
                 const float2 a = X[(size_t)m * ldx + t0 + t];
                 v.x = a.x;
                 v.y = a.y;
               }
             }
+            re[j][2 * q] = v.x;
+            im[j][2 * q] = v.y;
+            re[j][2 * q + 1] = v.z;
+            im[j][2 * q + 1] = v.w;
           }
-          re[2 * q] = v.x;
-          im[2 * q] = v.y;
-          re[2 * q + 1] = v.z;
-          im[2 * q + 1] = v.w;
         }
-        if (sub == kCbSub - 1 || s == nst - 1) {   // the staging stage has been read: release it
+        // this sub-stage of the staging stage has been read. A staging stage takes 8 arrivals (four
+        // sub-stages x two warps); the last sub-stage of a short one stands in for the missing ones.
+        {
+          const int nsub = min(kCbSub, nst - (s - sub));
           __syncwarp();
-          if (lane == 0) arrive(smem_u32(&sh.empty[ss]));
-          ++gs;
+          if (lane == 0) arrive_cnt(smem_u32(&sh.empty[ss]), sub == nsub - 1 ? (uint32_t)(1 + kCbSub - nsub) : 1u);
         }
         if (s == 0) {
-          // scaling unit from the first stage's largest |component|: 2^(k-1) <= mx < 2^k,
+          // this group fixes the scaling unit from the problem's first stage: 2^(k-1) <= mx < 2^k,
           // u0 = 2^(k-5), so |w| = |x| / u0 <= 64 for |x| <= 2^(k+1) (one bit of headroom)
           float mx = 0.f;
 #pragma unroll
-          for (int q = 0; q < SN; ++q) mx = fmaxf(mx, fmaxf(fabsf(re[q]), fabsf(im[q])));
+          for (int j = 0; j < kCbTasks; ++j)
+#pragma unroll
+            for (int q = 0; q < SN; ++q) mx = fmaxf(mx, fmaxf(fabsf(re[j][q]), fabsf(im[j][q])));
 #pragma unroll
           for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-          if (lane == 0) sh.red[kth & 1][warp] = mx;
-          if (!warp_bar(&sh.pred[kth & 1], (uint32_t)((kth >> 1) & 1), abort)) break;
+          const int slot = own & 1;
+          if (lane == 0) sh.red[grp][slot][warp % kCbGroupWarps] = mx;
+          if (!warp_bar(&sh.pred[grp][slot], (own >> 1) & 1u, abort)) {
+            live = false;
+            break;
+          }
           mx = 0.f;
 #pragma unroll
-          for (int w = 0; w < kCbProdWarps; ++w) mx = fmaxf(mx, sh.red[kth & 1][w]);
+          for (int w = 0; w < kCbGroupWarps; ++w) mx = fmaxf(mx, sh.red[grp][slot][w]);
+          ++own;
           const int eb = (int)((__float_as_uint(mx) >> 23) & 0xffu);
           bad = eb < 4 || eb > 254;                       // zero, subnormal, tiny or non-finite
           const int k = eb - 126;
           scale = bad ? 0.f : __uint_as_float((uint32_t)(258 - eb) << 23);   // 2^(5 - k)
-          if (tid == 0) {
-            const int r = kth % kCbRing;
+          if (lt == 0) {
             if (kth >= kCbRing) cb_wait(smem_u32(&sh.eempty[r]), (uint32_t)((kth / kCbRing - 1) & 1), abort);
             sh.eexp[r] = bad ? INT_MIN : k;
+            sh.escale[r] = scale;
             arrive(smem_u32(&sh.efull[r]));
+            arrive(smem_u32(&sh.sfull[r]));
           }
+          have = true;
+        } else if (!have) {
+          // the scaling unit fixed by the group that sliced the problem's first stage
+          if (!warp_wait(smem_u32(&sh.sfull[r]), (uint32_t)((kth / kCbRing) & 1), abort)) {
+            live = false;
+            break;
+          }
+          scale = sh.escale[r];
+          have = true;
         }
         // operand slot free (the MMAs of its previous stage are done)
         if (g >= (uint32_t)kCbOps && !warp_wait(smem_u32(&sh.opempty[os]), (g / kCbOps - 1) & 1u, abort)) {
@@ -408,37 +460,43 @@ __global__ void __launch_bounds__(kCbThreads, 1) covariance_tc_batch_kernel(cons
         uint8_t *op = sm + Lay::kOffOp + os * Lay::kOpBytes;
         // w = x * scale, pairs of consecutive snapshots in 64-bit registers
         const uint64_t sc2 = pack2(scale, scale);
-        uint64_t wr[SN / 2], wi[SN / 2];
+        uint64_t wr[kCbTasks][SN / 2], wi[kCbTasks][SN / 2];
 #pragma unroll
-        for (int q = 0; q < SN / 2; ++q) {
-          wr[q] = mul2(pack2(re[2 * q], re[2 * q + 1]), sc2);
-          wi[q] = mul2(pack2(im[2 * q], im[2 * q + 1]), sc2);
-          bad |= !(fabsf(lo2(wr[q])) <= 64.f) || !(fabsf(hi2(wr[q])) <= 64.f) || !(fabsf(lo2(wi[q])) <= 64.f) ||
-                 !(fabsf(hi2(wi[q])) <= 64.f);
-        }
+        for (int j = 0; j < kCbTasks; ++j)
+#pragma unroll
+          for (int q = 0; q < SN / 2; ++q) {
+            wr[j][q] = mul2(pack2(re[j][2 * q], re[j][2 * q + 1]), sc2);
+            wi[j][q] = mul2(pack2(im[j][2 * q], im[j][2 * q + 1]), sc2);
+            bad |= !(fabsf(lo2(wr[j][q])) <= 64.f) | !(fabsf(hi2(wr[j][q])) <= 64.f) |
+                   !(fabsf(lo2(wi[j][q])) <= 64.f) | !(fabsf(hi2(wi[j][q])) <= 64.f);
+          }
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
           const float Cf = slice_magic(k);
           const uint64_t C = pack2(Cf, Cf);
-          uint32_t pr[SN / 2], pim[SN / 2];
+          const uint32_t blk = (uint32_t)(S::block_of(k) * S::kBlock / 8) * 1024u;
 #pragma unroll
-          for (int q = 0; q < SN / 2; ++q) {
-            const uint64_t sr = sub2(add2(wr[q], C), C), si = sub2(add2(wi[q], C), C);
-            if (k < 5) {
-              wr[q] = sub2(wr[q], sr);
-              wi[q] = sub2(wi[q], si);
+          for (int j = 0; j < kCbTasks; ++j) {
+            uint32_t pr[SN / 2], pim[SN / 2];
+#pragma unroll
+            for (int q = 0; q < SN / 2; ++q) {
+              const uint64_t sr = sub2(add2(wr[j][q], C), C), si = sub2(add2(wi[j][q], C), C);
+              if (k < 5) {
+                wr[j][q] = sub2(wr[j][q], sr);
+                wi[j][q] = sub2(wi[j][q], si);
+              }
+              const __nv_bfloat162 a = __floats2bfloat162_rn(lo2(sr), hi2(sr)),
+                                   b = __floats2bfloat162_rn(lo2(si), hi2(si));
+              pr[q] = *reinterpret_cast<const uint32_t *>(&a);
+              pim[q] = *reinterpret_cast<const uint32_t *>(&b);
             }
-            const __nv_bfloat162 a = __floats2bfloat162_rn(lo2(sr), hi2(sr)), b = __floats2bfloat162_rn(lo2(si), hi2(si));
-            pr[q] = *reinterpret_cast<const uint32_t *>(&a);
-            pim[q] = *reinterpret_cast<const uint32_t *>(&b);
-          }
-          const int rre = S::block_of(k) * S::kBlock + m, rim = rre + MP;
-          if constexpr (SN == 4) {
-            *reinterpret_cast<uint2 *>(op + sw128(rre, 4 * c)) = make_uint2(pr[0], pr[1]);
-            *reinterpret_cast<uint2 *>(op + sw128(rim, 4 * c)) = make_uint2(pim[0], pim[1]);
-          } else {
-            *reinterpret_cast<uint32_t *>(op + sw128(rre, 2 * c)) = pr[0];
-            *reinterpret_cast<uint32_t *>(op + sw128(rim, 2 * c)) = pim[0];
+            if constexpr (SN == 4) {
+              *reinterpret_cast<uint2 *>(op + so[j] + blk) = make_uint2(pr[0], pr[1]);
+              *reinterpret_cast<uint2 *>(op + so[j] + blk + kImOff) = make_uint2(pim[0], pim[1]);
+            } else {
+              *reinterpret_cast<uint32_t *>(op + so[j] + blk) = pr[0];
+              *reinterpret_cast<uint32_t *>(op + so[j] + blk + kImOff) = pim[0];
+            }
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -446,7 +504,9 @@ __global__ void __launch_bounds__(kCbThreads, 1) covariance_tc_batch_kernel(cons
         if (lane == 0) arrive(smem_u32(&sh.opfull[os]));
       }
       // a sample outside the unit's range (or a non-finite one): recompute the problem elsewhere
-      if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&flags[pi], 1);
+      if (live && __any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&flags[pi], 1);
+      g0 += (uint32_t)nst;
+      gs0 += (uint32_t)nstg;
     }
   } else if (warp == kCbTmaWarp) {
     // ---------------------------------------------------------------- TMA: staging copies
