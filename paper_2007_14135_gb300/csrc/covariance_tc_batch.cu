@@ -79,6 +79,13 @@ __device__ __forceinline__ float slice_magic(int k) {
 
 // Paired FP32 arithmetic (two IEEE round-to-nearest operations per instruction), on the values of
 // two consecutive snapshots held as one 64-bit register pair.
+// max(|a|, |b|), NaN when either is NaN (so a NaN sample cannot hide behind a finite maximum).
+__device__ __forceinline__ float max_abs_nan(float a, float b) {
+  float d;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(fabsf(a)), "f"(fabsf(b)));
+  return d;
+}
+
 __device__ __forceinline__ uint64_t pack2(float lo, float hi) {
   return (uint64_t)__float_as_uint(lo) | ((uint64_t)__float_as_uint(hi) << 32);
 }
@@ -178,16 +185,21 @@ __device__ __forceinline__ void commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
-// Bounded wait that also gives up as soon as another role has given up.
+// Bounded wait that also gives up as soon as another role has given up. The waiting thread is
+// suspended for up to kCbSuspendNs per try (it resumes as soon as the phase completes), so a
+// role that waits most of the time (the MMA issuer, the readout, the copies) takes few issue
+// slots from the producers; at most kCbWaitTries tries (about a second).
+constexpr uint32_t kCbSuspendNs = 10000;
+constexpr int kCbWaitTries = 1 << 17;
 __device__ __forceinline__ bool cb_wait(uint32_t mbar, uint32_t parity, volatile int *abort) {
   uint32_t done = 0;
-  for (int it = 0; it < kWaitIters && !done; ++it) {
+  for (int it = 0; it < kCbWaitTries && !done; ++it) {
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.b32 %0, 1, 0, p;\n}\n"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.b32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(mbar), "r"(parity)
+        : "r"(mbar), "r"(parity), "r"(kCbSuspendNs)
         : "memory");
-    if (!done && (it & 255) == 255 && *abort) break;
+    if (!done && (it & 15) == 15 && *abort) break;
   }
   if (!done) *abort = 1;
   return done != 0;
@@ -461,15 +473,17 @@ __global__ void __launch_bounds__(kCbThreads, 1) covariance_tc_batch_kernel(cons
         // w = x * scale, pairs of consecutive snapshots in 64-bit registers
         const uint64_t sc2 = pack2(scale, scale);
         uint64_t wr[kCbTasks][SN / 2], wi[kCbTasks][SN / 2];
+        float amax = 0.f;   // largest |w| of the thread's samples, NaN if any is NaN
 #pragma unroll
         for (int j = 0; j < kCbTasks; ++j)
 #pragma unroll
           for (int q = 0; q < SN / 2; ++q) {
             wr[j][q] = mul2(pack2(re[j][2 * q], re[j][2 * q + 1]), sc2);
             wi[j][q] = mul2(pack2(im[j][2 * q], im[j][2 * q + 1]), sc2);
-            bad |= !(fabsf(lo2(wr[j][q])) <= 64.f) | !(fabsf(hi2(wr[j][q])) <= 64.f) |
-                   !(fabsf(lo2(wi[j][q])) <= 64.f) | !(fabsf(hi2(wi[j][q])) <= 64.f);
+            amax = max_abs_nan(amax, max_abs_nan(max_abs_nan(lo2(wr[j][q]), hi2(wr[j][q])),
+                                                 max_abs_nan(lo2(wi[j][q]), hi2(wi[j][q]))));
           }
+        bad |= !(amax <= 64.f);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
           const float Cf = slice_magic(k);

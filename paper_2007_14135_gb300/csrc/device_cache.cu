@@ -1,7 +1,7 @@
 // Per-device host state of the launchers: the dynamic shared-memory limit of each kernel (a
 // function attribute applies to one device's context; it is raised when a launch needs more than
-// the limit set so far) and the SM count, both kept per device under a mutex, so several host
-// threads and several GPUs may launch.
+// the limit set so far), the SM count and the shared-memory budgets, all kept per device under a
+// mutex, so several host threads and several GPUs may launch.
 #include <map>
 #include <mutex>
 #include <utility>
@@ -15,6 +15,7 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 std::map<std::pair<int, const void *>, int> g_attr_bytes;   // (device, kernel) -> the limit set
 int g_sms[kMaxDevices] = {};
+SmemLimits g_smem[kMaxDevices] = {};
 
 }  // namespace
 
@@ -40,6 +41,21 @@ int device_sm_count() {
     g_sms[dev] = n > 0 ? n : 1;
   }
   return g_sms[dev];
+}
+
+SmemLimits device_smem_limits() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SmemLimits{49152, 49152, 0};
+  std::lock_guard<std::mutex> lock(g_mutex);
+  SmemLimits &l = g_smem[dev];
+  if (l.per_sm <= 0) {
+    int sm = 0, blk = 0, res = 0;
+    cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&res, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    l = SmemLimits{sm > 0 ? sm : 49152, blk > 0 ? blk : 49152, res > 0 ? res : 0};
+  }
+  return l;
 }
 
 }  // namespace doa

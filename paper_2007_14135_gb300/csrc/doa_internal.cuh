@@ -407,6 +407,11 @@ constexpr int kCovTcMaxN = 1 << 21;
 // ------------------------------------------------------------------------------------------
 cudaError_t ensure_smem_attr(const void *func, int bytes);
 int device_sm_count();
+// Shared memory of the current device: per SM, per block (opt-in maximum), reserved per block.
+struct SmemLimits {
+  int per_sm, per_block, reserve;
+};
+SmemLimits device_smem_limits();
 
 // ------------------------------------------------------------------------------------------
 // Host launchers (one translation unit each). They return cudaError_t of the launch.

@@ -31,13 +31,18 @@ struct Rot {
 
 template <int NP>
 struct EigSmem {
-  double2 A[NP][NP + 1];
-  double2 V[NP][NP + 1];
-  Rot rot[NP / 2];
+  // A and V row-major without padding; element (i, k) sits in column slot k ^ (i & 7), so that
+  // both row walks (fixed i) and column walks (fixed k, consecutive rows) touch distinct banks
+  double2 A[NP][NP];
+  double2 V[NP][NP];
+  Rot rot[NP / 2];      // the sweeps' rotations; after the sweeps the same bytes hold lam, order
   int2 pq[NP / 2];
-  double lam[NP];
-  int order[NP];
-  unsigned mask;   // rotation mask broadcast when a group spans several warps
+  unsigned mask;        // rotation mask broadcast when a group spans several warps
+  __device__ __forceinline__ double2 &a(int i, int k) { return A[i][k ^ (i & 7)]; }
+  __device__ __forceinline__ double2 &v(int i, int k) { return V[i][k ^ (i & 7)]; }
+  __device__ __forceinline__ double *lam() { return reinterpret_cast<double *>(rot); }
+  __device__ __forceinline__ int *order() { return reinterpret_cast<int *>(reinterpret_cast<double *>(rot) + NP); }
+  static_assert(sizeof(Rot) * (NP / 2) >= NP * (sizeof(double) + sizeof(int)), "lam and order fit in rot");
 };
 
 // A group of T threads works on G matrices: one warp on 8, 4 or 2 matrices of M <= 8, 16, 32
@@ -47,10 +52,13 @@ template <int NP>
 __host__ __device__ constexpr int grp_threads() { return NP <= 32 ? 32 : 512; }
 template <int NP>
 __host__ __device__ constexpr int mats_per_warp() { return NP <= 32 ? 64 / NP : 1; }
+// Warps per CTA of the batch kernel, at most (the launch picks the count for the resident total).
 template <int NP>
-__host__ __device__ constexpr int eig_warps() { return NP <= 8 ? 4 : (NP <= 16 ? 2 : (NP <= 32 ? 1 : 16)); }
+__host__ __device__ constexpr int eig_warps() { return NP <= 8 ? 4 : (NP <= 16 ? 9 : (NP <= 32 ? 1 : 16)); }
+// CTAs per SM the batch kernel's register budget is set for: three nine-warp CTAs at M <= 16,
+// elsewhere 64 registers a thread.
 template <int NP>
-__host__ __device__ constexpr int groups_per_cta() { return NP <= 32 ? eig_warps<NP>() : 1; }
+__host__ __device__ constexpr int eig_min_ctas() { return NP > 8 && NP <= 16 ? 3 : 1024 / (32 * eig_warps<NP>()); }
 
 template <int T>
 struct Grp {
@@ -69,8 +77,8 @@ __device__ __forceinline__ int rr_player(int pos, int r, int n) {
 // Rotation of pair (p, q) of A; returns false if the pair is below threshold.
 template <int NP>
 __device__ __forceinline__ bool rotation(EigSmem<NP> &s, int p, int q, Rot &ro) {
-  const double app = s.A[p][p].x, aqq = s.A[q][q].x;
-  const double2 apq = s.A[p][q];
+  const double app = s.a(p, p).x, aqq = s.a(q, q).x;
+  const double2 apq = s.a(p, q);
   const double n2 = apq.x * apq.x + apq.y * apq.y;
   if (!(n2 > 0.0) || !(n2 > kJacobiTol * kJacobiTol * fabs(app * aqq))) return false;
   const double r = rsqrt(n2);                         // 1 / |a_pq|
@@ -116,8 +124,8 @@ __device__ void jacobi_group(EigSmem<NP> *mats, const int *Ms, const double2 *co
       }
       if (i == k) v.y = 0.0;
       finite = finite && isfinite(v.x) && isfinite(v.y);
-      s.A[i][k] = v;
-      s.V[i][k] = make_double2(i == k ? 1.0 : 0.0, 0.0);
+      s.a(i, k) = v;
+      s.v(i, k) = make_double2(i == k ? 1.0 : 0.0, 0.0);
     }
     if (g::all(finite))
       live |= 1u << j;
@@ -173,10 +181,10 @@ __device__ void jacobi_group(EigSmem<NP> *mats, const int *Ms, const double2 *co
           if (!((seg >> i) & 1u)) continue;
           const Rot ro = s.rot[i];
           const int2 pq = s.pq[i];
-          const double2 xp = s.A[pq.x][k], xq = s.A[pq.y][k];
-          s.A[pq.x][k] = make_double2(ro.c * xp.x - (ro.sr * xq.x - ro.si * xq.y),
+          const double2 xp = s.a(pq.x, k), xq = s.a(pq.y, k);
+          s.a(pq.x, k) = make_double2(ro.c * xp.x - (ro.sr * xq.x - ro.si * xq.y),
                                       ro.c * xp.y - (ro.sr * xq.y + ro.si * xq.x));
-          s.A[pq.y][k] = make_double2(ro.c * xq.x + (ro.sr * xp.x + ro.si * xp.y),
+          s.a(pq.y, k) = make_double2(ro.c * xq.x + (ro.sr * xp.x + ro.si * xp.y),
                                       ro.c * xq.y + (ro.sr * xp.y - ro.si * xp.x));
         }
       }
@@ -192,15 +200,15 @@ __device__ void jacobi_group(EigSmem<NP> *mats, const int *Ms, const double2 *co
           if (!((seg >> i) & 1u)) continue;
           const Rot ro = s.rot[i];
           const int2 pq = s.pq[i];
-          const double2 xp = s.A[k][pq.x], xq = s.A[k][pq.y];
-          s.A[k][pq.x] = make_double2(ro.c * xp.x - (ro.sr * xq.x + ro.si * xq.y),
+          const double2 xp = s.a(k, pq.x), xq = s.a(k, pq.y);
+          s.a(k, pq.x) = make_double2(ro.c * xp.x - (ro.sr * xq.x + ro.si * xq.y),
                                       ro.c * xp.y - (ro.sr * xq.y - ro.si * xq.x));
-          s.A[k][pq.y] = make_double2(ro.c * xq.x + (ro.sr * xp.x - ro.si * xp.y),
+          s.a(k, pq.y) = make_double2(ro.c * xq.x + (ro.sr * xp.x - ro.si * xp.y),
                                       ro.c * xq.y + (ro.sr * xp.y + ro.si * xp.x));
-          const double2 vp = s.V[k][pq.x], vq = s.V[k][pq.y];
-          s.V[k][pq.x] = make_double2(ro.c * vp.x - (ro.sr * vq.x + ro.si * vq.y),
+          const double2 vp = s.v(k, pq.x), vq = s.v(k, pq.y);
+          s.v(k, pq.x) = make_double2(ro.c * vp.x - (ro.sr * vq.x + ro.si * vq.y),
                                       ro.c * vp.y - (ro.sr * vq.y - ro.si * vq.x));
-          s.V[k][pq.y] = make_double2(ro.c * vq.x + (ro.sr * vp.x - ro.si * vp.y),
+          s.v(k, pq.y) = make_double2(ro.c * vq.x + (ro.sr * vp.x - ro.si * vp.y),
                                       ro.c * vq.y + (ro.sr * vp.y + ro.si * vp.x));
         }
       }
@@ -208,10 +216,10 @@ __device__ void jacobi_group(EigSmem<NP> *mats, const int *Ms, const double2 *co
       if (act) {
         EigSmem<NP> &s = mats[lj];
         const int2 pq = s.pq[li];
-        s.A[pq.x][pq.y] = make_double2(0.0, 0.0);
-        s.A[pq.y][pq.x] = make_double2(0.0, 0.0);
-        s.A[pq.x][pq.x].y = 0.0;
-        s.A[pq.y][pq.y].y = 0.0;
+        s.a(pq.x, pq.y) = make_double2(0.0, 0.0);
+        s.a(pq.y, pq.x) = make_double2(0.0, 0.0);
+        s.a(pq.x, pq.x).y = 0.0;
+        s.a(pq.y, pq.y).y = 0.0;
       }
       g::sync();
     }
@@ -284,15 +292,17 @@ struct RotDF {
 
 template <int NP>
 struct EigSmemDF {   // the same bytes as EigSmem<NP>, viewed as double-float
-  float4 A[NP][NP + 1];
-  float4 V[NP][NP + 1];
+  float4 A[NP][NP];
+  float4 V[NP][NP];
   RotDF rot[NP / 2];
+  __device__ __forceinline__ float4 &a(int i, int k) { return A[i][k ^ (i & 7)]; }
+  __device__ __forceinline__ float4 &v(int i, int k) { return V[i][k ^ (i & 7)]; }
 };
 static_assert(sizeof(RotDF) == sizeof(Rot), "rotation records share storage");
 
 template <int NP>
 __device__ __forceinline__ bool rotation_df(EigSmemDF<NP> &s, int p, int q, RotDF &ro) {
-  const float4 app = s.A[p][p], aqq = s.A[q][q], apq = s.A[p][q];
+  const float4 app = s.a(p, p), aqq = s.a(q, q), apq = s.a(p, q);
   const float n2 = apq.x * apq.x + apq.z * apq.z;
   if (!(n2 > 0.f) || !(n2 > kJacobiTolDF * kJacobiTolDF * fabsf(app.x * aqq.x))) return false;
   const float r = rsqrtf(n2);                                   // 1 / |a_pq|
@@ -349,8 +359,8 @@ __device__ void jacobi_group_df(EigSmem<NP> *mats64, const int *Ms, const double
       }
       if (i == k) v.y = 0.0;
       finite = finite && isfinite(v.x) && isfinite(v.y);
-      s.A[i][k] = df_of(v);
-      s.V[i][k] = make_float4(i == k ? 1.f : 0.f, 0.f, 0.f, 0.f);
+      s.a(i, k) = df_of(v);
+      s.v(i, k) = make_float4(i == k ? 1.f : 0.f, 0.f, 0.f, 0.f);
     }
     if (g::all(finite))
       live |= 1u << j;
@@ -405,10 +415,10 @@ __device__ void jacobi_group_df(EigSmem<NP> *mats64, const int *Ms, const double
           if (!((seg >> i) & 1u)) continue;
           const RotDF ro = s.rot[i];
           const int2 pq = mats64[j].pq[i];
-          const float4 xp = s.A[pq.x][k], xq = s.A[pq.y][k];
-          s.A[pq.x][k] = cplx(dot3(ro.c, re_of(xp), neg(ro.sr), re_of(xq), ro.si, im_of(xq)),
+          const float4 xp = s.a(pq.x, k), xq = s.a(pq.y, k);
+          s.a(pq.x, k) = cplx(dot3(ro.c, re_of(xp), neg(ro.sr), re_of(xq), ro.si, im_of(xq)),
                               dot3(ro.c, im_of(xp), neg(ro.sr), im_of(xq), neg(ro.si), re_of(xq)));
-          s.A[pq.y][k] = cplx(dot3(ro.c, re_of(xq), ro.sr, re_of(xp), ro.si, im_of(xp)),
+          s.a(pq.y, k) = cplx(dot3(ro.c, re_of(xq), ro.sr, re_of(xp), ro.si, im_of(xp)),
                               dot3(ro.c, im_of(xq), ro.sr, im_of(xp), neg(ro.si), re_of(xp)));
         }
       }
@@ -424,15 +434,15 @@ __device__ void jacobi_group_df(EigSmem<NP> *mats64, const int *Ms, const double
           if (!((seg >> i) & 1u)) continue;
           const RotDF ro = s.rot[i];
           const int2 pq = mats64[j].pq[i];
-          const float4 xp = s.A[k][pq.x], xq = s.A[k][pq.y];
-          s.A[k][pq.x] = cplx(dot3(ro.c, re_of(xp), neg(ro.sr), re_of(xq), neg(ro.si), im_of(xq)),
+          const float4 xp = s.a(k, pq.x), xq = s.a(k, pq.y);
+          s.a(k, pq.x) = cplx(dot3(ro.c, re_of(xp), neg(ro.sr), re_of(xq), neg(ro.si), im_of(xq)),
                               dot3(ro.c, im_of(xp), neg(ro.sr), im_of(xq), ro.si, re_of(xq)));
-          s.A[k][pq.y] = cplx(dot3(ro.c, re_of(xq), ro.sr, re_of(xp), neg(ro.si), im_of(xp)),
+          s.a(k, pq.y) = cplx(dot3(ro.c, re_of(xq), ro.sr, re_of(xp), neg(ro.si), im_of(xp)),
                               dot3(ro.c, im_of(xq), ro.sr, im_of(xp), ro.si, re_of(xp)));
-          const float4 vp = s.V[k][pq.x], vq = s.V[k][pq.y];
-          s.V[k][pq.x] = cplx(dot3(ro.c, re_of(vp), neg(ro.sr), re_of(vq), neg(ro.si), im_of(vq)),
+          const float4 vp = s.v(k, pq.x), vq = s.v(k, pq.y);
+          s.v(k, pq.x) = cplx(dot3(ro.c, re_of(vp), neg(ro.sr), re_of(vq), neg(ro.si), im_of(vq)),
                               dot3(ro.c, im_of(vp), neg(ro.sr), im_of(vq), ro.si, re_of(vq)));
-          s.V[k][pq.y] = cplx(dot3(ro.c, re_of(vq), ro.sr, re_of(vp), neg(ro.si), im_of(vp)),
+          s.v(k, pq.y) = cplx(dot3(ro.c, re_of(vq), ro.sr, re_of(vp), neg(ro.si), im_of(vp)),
                               dot3(ro.c, im_of(vq), ro.sr, im_of(vp), ro.si, re_of(vp)));
         }
       }
@@ -440,8 +450,8 @@ __device__ void jacobi_group_df(EigSmem<NP> *mats64, const int *Ms, const double
       if (act) {   // the diagonal of a Hermitian matrix is real
         EigSmemDF<NP> &s = df(lj);
         const int2 pq = mats64[lj].pq[li];
-        s.A[pq.x][pq.x].z = s.A[pq.x][pq.x].w = 0.f;
-        s.A[pq.y][pq.y].z = s.A[pq.y][pq.y].w = 0.f;
+        s.a(pq.x, pq.x).z = s.a(pq.x, pq.x).w = 0.f;
+        s.a(pq.y, pq.y).z = s.a(pq.y, pq.y).w = 0.f;
       }
       g::sync();
     }
@@ -460,9 +470,9 @@ __device__ void jacobi_group_df(EigSmem<NP> *mats64, const int *Ms, const double
     EigSmemDF<NP> &s = df(j);
     for (int e = lane; e < M * M; e += T) {
       const int i = e / M, k = e % M;
-      const float4 a = s.A[i][k], v = s.V[i][k];
-      mats64[j].A[i][k] = make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
-      mats64[j].V[i][k] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+      const float4 a = s.a(i, k), v = s.v(i, k);
+      mats64[j].a(i, k) = make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
+      mats64[j].v(i, k) = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
     }
   }
   g::sync();
@@ -474,17 +484,17 @@ __device__ void sort_desc(int M, EigSmem<NP> &s) {
   constexpr int T = grp_threads<NP>();
   using g = Grp<T>;
   const int lane = g::id();
-  for (int i = lane; i < M; i += T) s.lam[i] = s.A[i][i].x;
+  for (int i = lane; i < M; i += T) s.lam()[i] = s.a(i, i).x;
   g::sync();
   // ranks form a permutation even for non-finite values (NaN ranks below every number)
   for (int i = lane; i < M; i += T) {
-    const double li = isnan(s.lam[i]) ? -INFINITY : s.lam[i];
+    const double li = isnan(s.lam()[i]) ? -INFINITY : s.lam()[i];
     int rank = 0;
     for (int j = 0; j < M; ++j) {
-      const double lj = isnan(s.lam[j]) ? -INFINITY : s.lam[j];
+      const double lj = isnan(s.lam()[j]) ? -INFINITY : s.lam()[j];
       rank += (lj > li) || (lj == li && j < i);
     }
-    s.order[rank] = i;
+    s.order()[rank] = i;
   }
   g::sync();
 }
@@ -497,18 +507,18 @@ __device__ int build_factor(int M, int d, int alg, EigSmem<NP> &s, double2 *__re
   const int lane = g::id();
   const int Kn = M - d;  // noise subspace dimension
   if (alg == DOA_PHD) {
-    int col = s.order[M - 1];
-    for (int r = lane; r < M; r += T) B[r] = s.V[r][col];
+    int col = s.order()[M - 1];
+    for (int r = lane; r < M; r += T) B[r] = s.v(r, col);
     return 0;
   }
   if (alg == DOA_MUSIC || alg == DOA_EV) {
     bool bad = false;
     for (int e = lane; e < M * Kn; e += T) {
       int c = e / M, r = e % M;
-      int col = s.order[d + c];
-      double2 v = s.V[r][col];
+      int col = s.order()[d + c];
+      double2 v = s.v(r, col);
       if (alg == DOA_EV) {
-        double l = s.lam[col];
+        double l = s.lam()[col];
         if (!(l > 0.0)) {
           bad = true;
           v = make_double2(0.0, 0.0);
@@ -526,7 +536,7 @@ __device__ int build_factor(int M, int d, int alg, EigSmem<NP> &s, double2 *__re
   // MN: valph = P_n e1 / (e1^H P_n e1); (P_n e1)_r = sum_c V[r][c] conj(V[0][c]) over noise c
   double nrm = 0.0;
   for (int c = 0; c < Kn; ++c) {
-    double2 g = s.V[0][s.order[d + c]];
+    double2 g = s.v(0, s.order()[d + c]);
     nrm += g.x * g.x + g.y * g.y;
   }
   if (!(nrm > 0.0)) {
@@ -537,8 +547,8 @@ __device__ int build_factor(int M, int d, int alg, EigSmem<NP> &s, double2 *__re
   for (int r = lane; r < M; r += T) {
     double2 acc = make_double2(0.0, 0.0);
     for (int c = 0; c < Kn; ++c) {
-      int col = s.order[d + c];
-      double2 v = s.V[r][col], g = s.V[0][col];
+      int col = s.order()[d + c];
+      double2 v = s.v(r, col), g = s.v(0, col);
       // v * conj(g)
       acc.x += v.x * g.x + v.y * g.y;
       acc.y += v.y * g.x - v.x * g.y;
@@ -561,10 +571,10 @@ __device__ bool noise_orthonormal(int M, int d, EigSmem<NP> &s) {
   for (int e = lane; e < Kn * Kn; e += T) {
     const int a = e / Kn, b = e % Kn;
     if (a > b) continue;
-    const int ca = s.order[d + a], cb = s.order[d + b];
+    const int ca = s.order()[d + a], cb = s.order()[d + b];
     double gr = 0.0, gi = 0.0;
     for (int r = 0; r < M; ++r) {   // conj(V[r][ca]) * V[r][cb]
-      const double2 x = s.V[r][ca], y = s.V[r][cb];
+      const double2 x = s.v(r, ca), y = s.v(r, cb);
       gr = fma(x.x, y.x, fma(x.y, y.y, gr));
       gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
     }
@@ -590,20 +600,20 @@ __device__ void model_order(int M, int N, EigSmem<NP> &s, int32_t *out) {
     double sum = 0.0, ls = 0.0;
     bool bad = false;
     for (int i = k; i < M; ++i) {
-      const double l = s.lam[s.order[i]];
+      const double l = s.lam()[s.order()[i]];
       sum += l;
       if (l > 0.0) ls += log(l); else bad = true;
     }
     const double L = bad ? CUDART_INF : (double)N * (double)n * (log(sum / (double)n) - ls / (double)n);
     const double pen = (double)k * (double)(2 * M - k);
-    s.A[0][k] = make_double2(L + 0.5 * pen * logN, 2.0 * L + 2.0 * pen);
+    s.a(0, k) = make_double2(L + 0.5 * pen * logN, 2.0 * L + 2.0 * pen);
   }
   g::sync();
   if (lane == 0) {
     int bm = 0, ba = 0;
     double vm = CUDART_INF, va = CUDART_INF;
     for (int k = 0; k < M; ++k) {
-      const double2 v = s.A[0][k];
+      const double2 v = s.a(0, k);
       if (v.x < vm) {
         vm = v.x;
         bm = k;
@@ -634,7 +644,7 @@ __device__ int build_scan_factor(const PlanProblem &pp, EigSmem<NP> &s, double2 
     if (pp.slot[DOA_EV] >= 0) {
       bool bad = false;
       for (int c = lane; c < pp.Kn; c += T) {
-        const double l = s.lam[s.order[d + c]];
+        const double l = s.lam()[s.order()[d + c]];
         bad = bad || !(l > 0.0);
         w[c] = l > 0.0 ? 1.0 / l : 0.0;
       }
@@ -674,7 +684,7 @@ __global__ void __launch_bounds__(grp_threads<NP>()) eig_single_kernel(const dou
   if (res[0] > 0) {
     sort_desc<NP>(M, s);
     if (evals)
-      for (int i = lane; i < M; i += T) evals[i] = s.lam[s.order[i]];
+      for (int i = lane; i < M; i += T) evals[i] = s.lam()[s.order()[i]];
     st = build_factor<NP>(M, d, alg, s, B);
   } else {
     st = -res[0];
@@ -686,14 +696,14 @@ __global__ void __launch_bounds__(grp_threads<NP>()) eig_single_kernel(const dou
 }
 
 template <int NP, int G>
-__global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_batch_kernel(const uint8_t *plan, uint8_t *ws, int bucket,
+__global__ void __launch_bounds__(32 * eig_warps<NP>(), eig_min_ctas<NP>()) eig_batch_kernel(const uint8_t *plan, uint8_t *ws, int bucket,
                                                                          int *status) {
   extern __shared__ __align__(16) uint8_t smem[];
   constexpr int T = grp_threads<NP>();
   const int grp = threadIdx.x / T, lane = Grp<T>::id();
   EigSmem<NP> *mats = reinterpret_cast<EigSmem<NP> *>(smem) + grp * G;
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
-  const int base = (blockIdx.x * groups_per_cta<NP>() + grp) * G;
+  const int base = (blockIdx.x * (int)(blockDim.x / T) + grp) * G;
   const int count = h->eig_count[bucket];
   if (base >= count) return;
   const int32_t *list = reinterpret_cast<const int32_t *>(plan + h->off_eig[bucket]);
@@ -737,7 +747,7 @@ __global__ void __launch_bounds__(32 * eig_warps<NP>()) eig_batch_kernel(const u
     if (res[j] > 0) {
       sort_desc<NP>(M, s);
       if (pp.p.evals)
-        for (int i = lane; i < M; i += T) pp.p.evals[i] = s.lam[s.order[i]];
+        for (int i = lane; i < M; i += T) pp.p.evals[i] = s.lam()[s.order()[i]];
       st = build_scan_factor<NP>(pp, s, F, w);
       if (!noise_orthonormal<NP>(M, d, s) && !st) st = DOA_ENOCONV;
       if (pp.p.B_out) build_factor<NP>(M, d, jobs[pp.first_job].alg, s, reinterpret_cast<double2 *>(pp.p.B_out));
@@ -773,12 +783,34 @@ cudaError_t run_single(const double2 *R64, int M, int d, int alg, int prec, doub
                               : run_single_p<NP, true>(R64, M, d, alg, evals, B, K_out, info, st);
 }
 
+// Warps per CTA: the count (up to eig_warps) that keeps the most matrices resident per SM, the
+// larger count on a tie. Shared memory is the limit (each CTA also costs the driver's reserve),
+// so for M <= 16, nine one-matrix warps per CTA hold 27 matrices per SM where two held 24: a
+// 4096-matrix batch then runs in one wave instead of 1.12.
+template <int NP, int G>
+int eig_cta_warps() {
+  if (NP > 32) return 1;
+  const SmemLimits lim = device_smem_limits();
+  const int per_mat = (int)sizeof(EigSmem<NP>);
+  int best = 1, best_res = -1;
+  for (int w = 1; w <= eig_warps<NP>(); ++w) {
+    const int bytes = w * G * per_mat;
+    if (bytes > lim.per_block) break;
+    const int ctas = lim.per_sm / (bytes + lim.reserve);
+    if (ctas * w * G >= best_res) {
+      best_res = ctas * w * G;
+      best = w;
+    }
+  }
+  return best;
+}
+
 template <int NP, int G>
 cudaError_t run_batch_g(const uint8_t *plan, int count, uint8_t *ws, int *status, int bucket, cudaStream_t st) {
-  constexpr int W = eig_warps<NP>();
-  constexpr int per_cta = groups_per_cta<NP>() * G;
+  const int W = NP <= 32 ? eig_cta_warps<NP, G>() : eig_warps<NP>();
+  const int per_cta = (NP <= 32 ? W : 1) * G;
   const int smem = (int)sizeof(EigSmem<NP>) * per_cta;
-  cudaError_t e = cudaFuncSetAttribute(eig_batch_kernel<NP, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void *>(eig_batch_kernel<NP, G>), smem);
   if (e != cudaSuccess) return e;
   eig_batch_kernel<NP, G><<<(count + per_cta - 1) / per_cta, 32 * W, smem, st>>>(plan, ws, bucket, status);
   return cudaGetLastError();
