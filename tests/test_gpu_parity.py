@@ -1,5 +1,7 @@
 """GPU parity: every stage of the CUDA path, called through the C ABI, against the FP64 oracle on
 the same seeded complex64 inputs."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -292,9 +294,43 @@ def test_batch_c1_all_algorithms(env):
 
 
 def test_batch_paper_density_sample(env):
+    """Peak polish on, as in the headline: peak indices equal to the oracle's up to ties below
+    float resolution (1e-6 relative)."""
+    torch, doa = env
+    insts = [synth.paper_density(i) for i in range(8)]
+    _check_batch(torch, doa, insts, [0xF] * len(insts), polish=True, tie=1e-6)
+
+
+def test_batch_paper_density_sample_unpolished(env):
+    """Without the polish two neighbouring grid points whose oracle values differ by less than the
+    FP32 path's error bound may swap: ties up to 1e-4 relative are accepted there."""
     torch, doa = env
     insts = [synth.paper_density(i) for i in range(8)]
     _check_batch(torch, doa, insts, [0xF] * len(insts))
+
+
+def test_scan_refinement_queue_overflow(env):
+    """More near-null points than the refinement queue holds (1024) before a drain: a 2-element
+    array with a strong source at broadside, scanned from -0.1 to 0.1 deg in steps of 1e-5 deg,
+    puts about half of the 20001 points below the refinement threshold (den = 1 - cos(pi u) near
+    the MUSIC null), so the queue overflows and the overflowing points are re-evaluated in place,
+    one thread each. Alone (per-problem scan, runs of several tiles per drain) and as 32 problems
+    sharing the grid (grid-shared scan, one tile of all 32 per drain), every point of all four
+    spectra stays within DB_TOL of the oracle."""
+    torch, doa = env
+    base = synth.custom(2, 1, 2048, [0.0], 20.0, 0.01, seed=777)
+    inst = dataclasses.replace(base, lo=-0.1, step=1e-5, L=20001)
+    refs = [oracle.solve(inst.X, inst.d, alg, inst.lo, inst.step, inst.L)["P"] for alg in range(4)]
+    # the MUSIC denominator near the null: far more than 1024 points below 2.05e-6 (sum |f_m|)^2 = 4.1e-6
+    assert np.sum(1.0 / refs[MUSIC] < 4.1e-6) > 4 * 1024
+    for group in ([inst], [inst] * 32):
+        tensors, status = _batch_solve(torch, doa, group, [0xF] * len(group))
+        assert np.all(status == 0), status
+        for t in tensors:
+            P = t[1].cpu().numpy().reshape(4, inst.L)
+            for alg in range(4):
+                err = db_error(P[alg], refs[alg])
+                assert err < DB_TOL, (len(group), alg, err)
 
 
 def test_batch_paper_density_sample_polished(env):
