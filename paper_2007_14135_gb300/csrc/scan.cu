@@ -364,6 +364,7 @@ __global__ void __launch_bounds__(32 * kPolishWarps) polish_batch_kernel(const u
   __shared__ float2 yb[kPolishWarps][kMaxCols];
   __shared__ float w32[kPolishWarps][kMaxM];
   __shared__ int pk[kPolishWarps][kPolishMax];
+  __shared__ int cand[kPolishWarps][kPolishMax];
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int prob = blockIdx.x * kPolishWarps + warp;
@@ -389,30 +390,54 @@ __global__ void __launch_bounds__(32 * kPolishWarps) polish_batch_kernel(const u
   for (int c = lane; c < j.Kn; c += 32) w32[warp][c] = j.w ? (float)j.w[c] : 1.f;
   const int d = pp.p.d, L = g.L;
   const float *next = h->next_val_off >= 0 ? reinterpret_cast<const float *>(ws + h->next_val_off) : nullptr;
+  // lane s < njobs: is job s's selection decided by its FP32 values (its weakest selected peak
+  // above its best unselected value by more than the FP32 error)?
+  bool bnd = true;
+  if (lane < pp.njobs) {
+    const int cnt = min(pp.p.peak_count[lane], d);
+    if (cnt == d && next) {
+      float vmin = INFINITY;
+      for (int q = 0; q < cnt; ++q) vmin = fminf(vmin, pp.p.peak_val[(size_t)lane * d + q]);
+      const float nv = next[pp.first_job + lane];
+      bnd = !(nv > -INFINITY) || (vmin > nv && order_certain(vmin, nv));
+    }
+  }
+  const unsigned bmask = __ballot_sync(0xffffffffu, bnd);
+  // lane e takes peak e % d of job e / d: undecided peaks go to cand[] (one round of loads for all)
+  int ncand = 0;
+  for (int e0 = 0; e0 < pp.njobs * d; e0 += 32) {
+    const int e = e0 + lane;
+    int k = -1;
+    if (e < pp.njobs * d) {
+      const int sj = e / d, q = e % d;
+      if (q < min(pp.p.peak_count[sj], d)) {
+        k = pp.p.peak_idx[(size_t)sj * d + q];
+        const float *Ps = pp.p.P + (size_t)sj * L;
+        const int i0 = max(k - 3, 0), i1 = min(k + 3, L - 1);
+        float v[7];
+#pragma unroll
+        for (int t = 0; t < 7; ++t) v[t] = i0 + t <= i1 ? Ps[i0 + t] : 0.f;
+        bool decided = ((bmask >> sj) & 1u) && next;
+#pragma unroll
+        for (int t = 0; t < 6; ++t) decided = decided && (i0 + t >= i1 || order_certain(v[t], v[t + 1]));
+        if (decided) k = -1;
+      }
+    }
+    const unsigned um = __ballot_sync(0xffffffffu, k >= 0);
+    if (k >= 0) cand[warp][ncand + __popc(um & ((1u << lane) - 1u))] = k;
+    ncand += __popc(um);
+  }
+  __syncwarp();
   int n = 0;
-  if (lane == 0) {   // the algorithms' undecided peaks, sorted, each once
-    for (int s = 0; s < pp.njobs; ++s) {
-      const int cnt = min(pp.p.peak_count[s], d);
-      const float *Ps = pp.p.P + (size_t)s * L;
-      bool boundary = true;             // the selection is decided by the FP32 values
-      if (cnt == d && next) {
-        float vmin = INFINITY;
-        for (int q = 0; q < cnt; ++q) vmin = fminf(vmin, pp.p.peak_val[(size_t)s * d + q]);
-        const float nv = next[pp.first_job + s];
-        boundary = !(nv > -INFINITY) || (vmin > nv && order_certain(vmin, nv));
-      }
-      for (int q = 0; q < cnt; ++q) {
-        const int k = pp.p.peak_idx[(size_t)s * d + q];
-        bool decided = boundary && next;
-        for (int i = max(k - 3, 0); decided && i < min(k + 3, L - 1); ++i) decided = order_certain(Ps[i], Ps[i + 1]);
-        if (decided) continue;
-        int a = n;
-        while (a > 0 && pk[warp][a - 1] > k) --a;
-        if (a > 0 && pk[warp][a - 1] == k) continue;
-        for (int b = n; b > a; --b) pk[warp][b] = pk[warp][b - 1];
-        pk[warp][a] = k;
-        ++n;
-      }
+  if (lane == 0) {   // the undecided peaks, sorted, each once
+    for (int c = 0; c < ncand; ++c) {
+      const int k = cand[warp][c];
+      int a = n;
+      while (a > 0 && pk[warp][a - 1] > k) --a;
+      if (a > 0 && pk[warp][a - 1] == k) continue;
+      for (int b = n; b > a; --b) pk[warp][b] = pk[warp][b - 1];
+      pk[warp][a] = k;
+      ++n;
     }
   }
   n = __shfl_sync(0xffffffffu, n, 0);
@@ -430,17 +455,6 @@ __global__ void __launch_bounds__(32 * kPolishWarps) polish_batch_kernel(const u
   }
 }
 
-int g_num_sms = 0;
-
-int num_sms() {
-  if (g_num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 1;
-  }
-  return g_num_sms;
-}
 
 template <int MP, int PT>
 cudaError_t run_batch(const uint8_t *plan, const PlanHeader &h, uint8_t *ws, int bucket, cudaStream_t s) {
@@ -449,7 +463,7 @@ cudaError_t run_batch(const uint8_t *plan, const PlanHeader &h, uint8_t *ws, int
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_batch_kernel<MP, PT>, kScanThreads, 0);
   if (per_sm < 1) per_sm = 1;
-  const int64_t cap = (int64_t)num_sms() * per_sm;
+  const int64_t cap = (int64_t)device_sm_count() * per_sm;
   const int run_len = (int)std::min<int64_t>(kRun, std::max<int64_t>(1, (tiles + cap - 1) / cap));
   const int64_t grid = std::min<int64_t>(cap, (tiles + run_len - 1) / run_len);
   scan_batch_kernel<MP, PT><<<(unsigned)grid, kScanThreads, 0, s>>>(plan, ws, bucket, run_len);
@@ -500,7 +514,7 @@ cudaError_t run_shared(const uint8_t *plan, const PlanHeader &h, uint8_t *ws, in
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_shared_kernel<MP, PT>, kScanThreads, 0);
   if (per_sm < 1) per_sm = 1;
-  const int64_t grid = std::min<int64_t>((int64_t)num_sms() * per_sm, h.sg_units[bucket]);
+  const int64_t grid = std::min<int64_t>((int64_t)device_sm_count() * per_sm, h.sg_units[bucket]);
   scan_shared_kernel<MP, PT><<<(unsigned)grid, kScanThreads, 0, s>>>(plan, ws, bucket);
   return cudaGetLastError();
 }

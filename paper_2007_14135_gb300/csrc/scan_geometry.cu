@@ -352,17 +352,6 @@ __global__ void __launch_bounds__(kScanThreads) scan_geometry_batch_kernel(const
   }
 }
 
-int g_num_sms = 0;
-
-int num_sms() {
-  if (g_num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 1;
-  }
-  return g_num_sms;
-}
 
 template <int MP, int PT>
 cudaError_t run_geo_batch(const uint8_t *plan, const PlanHeader &h, uint8_t *ws, int bucket, cudaStream_t s) {
@@ -371,7 +360,7 @@ cudaError_t run_geo_batch(const uint8_t *plan, const PlanHeader &h, uint8_t *ws,
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_geometry_batch_kernel<MP, PT>, kScanThreads, 0);
   if (per_sm < 1) per_sm = 1;
-  const int64_t cap = (int64_t)num_sms() * per_sm;
+  const int64_t cap = (int64_t)device_sm_count() * per_sm;
   const int run_len = (int)std::min<int64_t>(kRun, std::max<int64_t>(1, (tiles + cap - 1) / cap));
   const int64_t grid = std::min<int64_t>(cap, (tiles + run_len - 1) / run_len);
   scan_geometry_batch_kernel<MP, PT><<<(unsigned)grid, kScanThreads, 0, s>>>(plan, ws, bucket, run_len);
@@ -405,7 +394,7 @@ cudaError_t launch_geo_tables(const uint8_t *plan_dev, const PlanHeader &h, uint
   const int bx = (h.geo_grid_points + 255) / 256;
   geo_table_batch_kernel<<<dim3(bx, h.ngeo_grids), 256, 0, s>>>(plan_dev, ws);
   if (h.ngeo_steer > 0) {   // the shared steering tables read the FP64 sin / cos tables just written
-    const int sx = std::min(2 * num_sms(), (h.steer_max_ldt + 255) / 256);
+    const int sx = std::min(2 * device_sm_count(), (h.steer_max_ldt + 255) / 256);
     geo_steer_kernel<<<dim3(sx, h.ngeo_steer), 256, 0, s>>>(plan_dev, ws);
   }
   return cudaGetLastError();
