@@ -44,13 +44,14 @@ def workload_name(batch):
             f"grid -90:{STEP}:90 deg (L={grid_L()}), PHD+MUSIC+EV+MN on each")
 
 
-# DRAM bytes (read + write) per launch of the dominant kernels: ncu captures of a smaller case scaled
-# to the bench's batch by the problem count (every problem is an independent, equal unit):
-# paper density from 1024 problems x 4 (profiles/paper_density_batch_kernels_ncu.md), the circular
-# array from 2048 problems x 2 (profiles/paper_uca_geometry_scan_ncu.md). Reset an entry to None
+# DRAM bytes (read + write) per launch of the dominant kernels, from ncu: the paper-density kernels
+# captured at the bench's 4096 problems (one pass, profiles/paper_density_batch_launches.md), the
+# circular array from a smaller case scaled to the bench's batch by the problem count (every problem
+# is an independent, equal unit; profiles/paper_uca_geometry_scan_ncu.md). Reset an entry to None
 # when its kernel changes.
 TRAFFIC_BYTES = {
-    "scan_shared_kernel<16,2>": None,          # DRAM bytes per 4096-problem launch (ncu), once captured
+    "scan_shared_kernel<16,4>": 38949632 + 1117904128,        # read + written, 4096-problem launch
+    "covariance_tc_batch_kernel<16>": 2148942336 + 15538176,
     "scan_geometry_batch_kernel<8,4>": None,   # changed since its capture: reads shared steering tables
     "scan_geometry_batch_kernel<8,2>": None,
 }
@@ -331,12 +332,14 @@ def run_gpu(args):
     if dname == "scan":
         roof = {"bound": "alu", "achieved": round(stage_info["scan"]["achieved"], 3), "peak": round(FP32_PEAK_TFLOPS, 2),
                 "unit": "TFLOP/s", "frac": round(stage_info["scan"]["achieved"] / FP32_PEAK_TFLOPS, 4),
-                "traffic": TRAFFIC_BYTES.get("scan_shared_kernel<16,2>"), "kernel": "scan_shared_kernel<16,2>",
+                "traffic": TRAFFIC_BYTES.get(f"scan_shared_kernel<16,{plan.scan_pt[1]}>"),
+                "kernel": f"scan_shared_kernel<16,{plan.scan_pt[1]}>",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
     elif dname == "covariance":
         a = stage_info["covariance"]["achieved"]
         roof = {"bound": "hbm", "achieved": round(a, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(a / hbm_peak, 4), "traffic": None, "kernel": "covariance_batch_kernel",
+                "frac": round(a / hbm_peak, 4), "traffic": TRAFFIC_BYTES.get("covariance_tc_batch_kernel<16>"),
+                "kernel": "covariance_tc_batch_kernel<16>",
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
@@ -1290,7 +1293,13 @@ def main():
     ap.add_argument("--la-forms", default="", help="large-array workload: comma list of forms (default all)")
     ap.add_argument("--tc-min-m", type=int, default=0,
                     help="uneven workload: problems with M >= this (<= 32) scan on the tensor cores (FP16x3)")
+    ap.add_argument("--grid-step", type=float, default=None,
+                    help="paper-density workload: scan grid step in degrees (default 0.01; a coarser grid keeps "
+                         "profiles of the stages before the scan small at the full batch)")
     args = ap.parse_args()
+    if args.grid_step is not None:
+        global STEP
+        STEP = float(args.grid_step)
     if args.batch is None:
         args.batch = {"large-array": 32, "learned": 65536}.get(args.workload, 4096)
     if args.warmup < 3 and args.impl == "gpu":

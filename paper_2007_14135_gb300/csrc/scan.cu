@@ -344,8 +344,9 @@ __global__ void __launch_bounds__(kScanThreads, shared_min_blocks<MP, PT>())
 }
 
 // Peak polish (DOA_FLAG_POLISH_PEAKS): one warp per problem re-evaluates, with the FP64
-// steering and contraction of refine_point_warp, every readout of the problem at the union of
-// its algorithms' picked peaks and their two neighbours on each side (each point once); the
+// steering and contraction of the scan's refinement (two or four points per pass in sub-warps
+// for small factors), every readout of the problem at the union of its algorithms' picked peaks
+// and their two neighbours on each side (each point once); the
 // peaks are then picked again. A peak whose outcome the FP32 values already decide is skipped:
 // the FP32 spectrum is within kPolishCertain / 2 (relative) of the FP64 one, so when every pair of
 // consecutive points from k-3 to k+3 differs by more than kPolishCertain, and the algorithm's
@@ -365,6 +366,7 @@ __global__ void __launch_bounds__(32 * kPolishWarps) polish_batch_kernel(const u
   __shared__ float w32[kPolishWarps][kMaxM];
   __shared__ int pk[kPolishWarps][kPolishMax];
   __shared__ int cand[kPolishWarps][kPolishMax];
+  __shared__ int pts[kPolishWarps][4];
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int prob = blockIdx.x * kPolishWarps + warp;
@@ -445,14 +447,32 @@ __global__ void __launch_bounds__(32 * kPolishWarps) polish_batch_kernel(const u
   // mark the problem's jobs for the second pick (a NaN in their next-value slots); the jobs of a
   // problem with nothing to polish keep their first pick
   if (n > 0 && next && lane < pp.njobs) const_cast<float *>(next)[pp.first_job + lane] = CUDART_NAN_F;
-  int last = -1;
+  // the points, each once and in increasing order, several per pass for small factors (sub-warps
+  // of 8 or 16 lanes per point, as in the scan's refinement), else one per pass
+  const bool sub8 = j.M <= 8 && j.Kf <= 8, sub16 = !sub8 && j.M <= 16 && j.Kf <= 16;
+  const int per = sub8 ? 4 : (sub16 ? 2 : 1);
+  int last = -1, nb = 0;
+  auto flush = [&]() {
+    __syncwarp();
+    if (sub8)
+      refine_points_subwarp<8>(j, pts[warp], nb, UlaSource{&j}, w32[warp], ph[warp]);
+    else if (sub16)
+      refine_points_subwarp<16>(j, pts[warp], nb, UlaSource{&j}, w32[warp], ph[warp]);
+    else
+      refine_point_warp(j, pts[warp][0], w32[warp], ph[warp], yb[warp]);
+    __syncwarp();
+    nb = 0;
+  };
   for (int i = 0; i < n; ++i) {
     const int k0 = pk[warp][i];
     for (int k = max(max(k0 - 2, last + 1), 0); k <= min(k0 + 2, L - 1); ++k) {
-      refine_point_warp(j, k, w32[warp], ph[warp], yb[warp]);
+      if (lane == 0) pts[warp][nb] = k;
+      ++nb;
       last = k;
+      if (nb == per) flush();
     }
   }
+  if (nb > 0) flush();
 }
 
 
