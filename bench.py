@@ -52,7 +52,7 @@ def workload_name(batch):
 TRAFFIC_BYTES = {
     "scan_shared_kernel<16,4>": 38949632 + 1117904128,        # read + written, 4096-problem launch
     "covariance_tc_batch_kernel<16>": 2148942336 + 15538176,
-    "scan_geometry_batch_kernel<8,4>": None,   # changed since its capture: reads shared steering tables
+    "scan_geometry_batch_kernel<8,4>": 2 * (4493312 + 206536704),   # 2048-problem capture x 2
     "scan_geometry_batch_kernel<8,2>": None,
 }
 
