@@ -354,7 +354,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Eq. 1 ULA snapshots, Philox)",
         "config": {"workload": workload_name(B), "batch_per_gpu": B, "M": M, "d": D, "N": N_SNAP, "L": L,
-                   "algorithms": ["PHD", "MUSIC", "EV", "MN"], "eig": "double-float Jacobi (FP32 pipe)", "scan": "FP32 FFMA, grid-shared (one steering block per tile for 32 problems)", "peaks": "polished (FP64 at peaks +-2)",
+                   "algorithms": ["PHD", "MUSIC", "EV", "MN"], "eig": "double-float Jacobi (FP32 pipe)", "scan": "FP32 FFMA, blocked Horner in z and z^4, grid-shared (32 problems per tile), 4 points per thread", "peaks": "polished (FP64 at peaks +-2)",
                    "l2": f"inputs {Xh.nbytes / 1e9:.2f} GB per step > 129 MB L2 (no flush needed)",
                    "parallelism": f"replicas x{world}"},
         "solves_per_s": solves / (ms / 1e3),
