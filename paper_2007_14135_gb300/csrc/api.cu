@@ -549,8 +549,9 @@ doa_status doa_batch_plan(const doa_problem *probs, int nprob, const doa_tuning 
     h.off_eig[b] = o.eig[b];
     h.off_scan[b] = o.scan[b];
   }
-  // workspace: per-grid 32- and 64-bit phase tables, then per problem R, partials and scan factor
-  int64_t ws = 0;
+  // workspace: per-solve counters, per-grid 32- and 64-bit phase tables, then per problem R,
+  // partials and scan factor
+  int64_t ws = kWsCounterBytes;
   for (int g = 0; g < sz.ngrids; ++g) {
     pg[g].lo = grids[g].lo_deg;
     pg[g].step = grids[g].step_deg;

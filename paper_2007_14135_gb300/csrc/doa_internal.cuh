@@ -407,6 +407,9 @@ constexpr int kCovTcMaxN = 1 << 21;
 // ------------------------------------------------------------------------------------------
 cudaError_t ensure_smem_attr(const void *func, int bytes);
 int device_sm_count();
+// The first bytes of a batch workspace hold per-solve counters: the grid-shared FP32 scan's next
+// unit, one uint32 per M bucket (reset by the scan's prep kernel before each scan launch).
+constexpr int64_t kWsCounterBytes = 256;
 // Shared memory of the current device: per SM, per block (opt-in maximum), reserved per block.
 struct SmemLimits {
   int per_sm, per_block, reserve;

@@ -162,9 +162,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t 
 
 // Grid-shared scan (problems of one M bucket that share a grid, in groups of up to
 // kScanGroupMax). A unit is one tile of the grid for every problem of a group: the CTA generates
-// the tile's steering phasors once, keeps them in registers and contracts them with the factor of
-// each problem of the group in turn, so the phasor polynomials cost 1 / count of the per-problem
-// scan and nearly every instruction left is a contraction FMA. Each problem's FP32 factor, EV
+// the tile's steering once (w and w^4 per point in the Horner form, the M phasors otherwise), keeps
+// it in registers and contracts it with the factor of each problem of the group in turn, so the
+// phasor polynomials cost 1 / count of the per-problem scan and nearly every instruction left is
+// a contraction FMA. Each problem's FP32 factor, EV
 // weights and thresholds were written once per solve by scan_prep_kernel (the same values the
 // per-problem scan computes), so every point gets bit for bit the spectrum of the per-problem
 // scan. Flagged points of all the group's problems queue up with their problem's position in the
@@ -178,6 +179,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_prep_kernel(const uint8_t *
   const int32_t *list = reinterpret_cast<const int32_t *>(plan + h->off_sgl[bucket]);
   const PlanProblem *probs = reinterpret_cast<const PlanProblem *>(plan + h->off_prob);
   const int i = blockIdx.x * kScanWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (blockIdx.x == 0 && threadIdx.x == 0) reinterpret_cast<unsigned *>(ws)[bucket] = 0u;   // next unit
   if (i >= h->sg_probs[bucket]) return;
   const PlanProblem &pp = probs[list[i]];
   const int M = pp.p.M, Kf = pp.Kf, Kn = pp.Kn;
@@ -241,7 +243,15 @@ __global__ void __launch_bounds__(kScanThreads, shared_min_blocks<MP, PT>())
   constexpr int TP = kScanThreads * PT;
   if (tid == 0) sh.nflag = 0;
   int cached = -1;   // group whose jobs are in shared memory (every thread holds the same value)
-  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+  // units are taken from a counter in the workspace (reset by scan_prep_kernel), so the CTAs
+  // that meet cheap units (a grid's short last tile) take more of them and all end together
+  __shared__ unsigned s_unit;
+  unsigned *next_unit = reinterpret_cast<unsigned *>(ws) + bucket;
+  for (;;) {
+    if (tid == 0) s_unit = atomicAdd(next_unit, 1u);
+    __syncthreads();   // the previous unit ended with a barrier, so s_unit is not read while rewritten
+    const int64_t u = s_unit;
+    if (u >= nunits) break;
     int gi = 0, hi = ngroups - 1;
     while (gi < hi) {  // last group with unit_start <= u
       const int mid = (gi + hi + 1) >> 1;
@@ -317,7 +327,7 @@ __global__ void __launch_bounds__(kScanThreads, shared_min_blocks<MP, PT>())
     // FP64 re-evaluation of the unit's flagged points, several per warp for small factors; the
     // queue holds the points of each problem together (problems run one after the other)
     __syncthreads();
-    const int n = min(sh.nflag, kFlagCap);
+    const int n = queue_front(sh.nflag), nb = queue_back(sh.nflag);
     for (int i0 = warp * 4; i0 < n; i0 += kScanWarps * 4) {
       const int end = min(i0 + 4, n);
       for (int c0 = i0; c0 < end;) {
@@ -335,6 +345,18 @@ __global__ void __launch_bounds__(kScanThreads, shared_min_blocks<MP, PT>())
         } else {
           for (int c = c0; c < c1; ++c) refine_point_warp_src(j, sh.flags[c], src, wg, sh.ph[warp], sh.yb[warp]);
         }
+        c0 = c1;
+      }
+    }
+    // points flagged for PHD / MN alone (the back of the queue): those columns only
+    for (int i0 = kFlagCap - nb + warp * 4; i0 < kFlagCap; i0 += kScanWarps * 4) {
+      const int end = min(i0 + 4, kFlagCap);
+      for (int c0 = i0; c0 < end;) {
+        const int tag = tags[c0];
+        int c1 = c0 + 1;
+        while (c1 < end && tags[c1] == tag) ++c1;
+        const ScanJob &j = jobs[tag];
+        refine_single_run(j, sh.flags + c0, sh.fmask + c0, c1 - c0, UlaSource{&j});
         c0 = c1;
       }
     }

@@ -49,10 +49,18 @@ struct ScanShared {
   double2 ph[kScanWarps][kMaxM];      // per-warp FP64 phasors for refinement
   float2 yb[kScanWarps][kMaxCols];    // per-warp column outputs of refinement (rounded once)
   float w32[kMaxM];                   // FP32 EV weights
+  // Refinement queue: points whose FP32 value of MUSIC or EV (or any readout, for M > 32) is
+  // below its threshold fill flags[] from the front and are re-evaluated for every readout;
+  // points flagged only for PHD and / or MN fill it from the back, with fmask[] naming the
+  // readouts (bit r = readout r), and are re-evaluated for those columns alone. nflag counts both:
+  // front entries in its low 16 bits, back entries in its high 16 bits.
   int flags[kFlagCap];
-  int nflag;
+  uint8_t fmask[kFlagCap];
+  unsigned nflag;
   float thr[4];                       // per-readout refinement thresholds (-1: readout absent)
 };
+__device__ __forceinline__ int queue_front(unsigned n) { return (int)(n & 0xffffu); }
+__device__ __forceinline__ int queue_back(unsigned n) { return (int)(n >> 16); }
 
 // F (M x Kf complex128, column-major, ld M) -> Bs[k][m] (FP32, rows m >= M zero-padded to MP);
 // EV weights -> sh.w32.
@@ -344,12 +352,62 @@ inline __device__ void refine_points_subwarp(const ScanJob &j, const int *ks, in
   __syncwarp();
 }
 
+// Re-evaluation of the PHD and / or MN readouts alone (the others were above their thresholds):
+// a sub-warp of W lanes per point (W = 8, 16 or 32; M <= W), lane m the product conj(f_mc) a_m in
+// FP64 for the flagged column c (v_min, valph), the sum over the sub-warp by shuffles, y rounded
+// once to FP32 and P = 1 / |y|^2 as in refine_point_warp_src. Every lane runs the same steps (a
+// sub-warp without a point or without the readout sums zeros and does not store).
+template <int W, class Src>
+inline __device__ void refine_points_single(const ScanJob &j, const int *ks, const uint8_t *masks, int cnt,
+                                            const Src &src) {
+  const int lane = threadIdx.x & 31, sub = lane % W, grp = lane / W;
+  const bool live = grp < cnt;
+  const int k = ks[live ? grp : 0];
+  const unsigned mk = live ? masks[grp] : 0u;
+  const auto st = src.prep(k);
+  double2 a = make_double2(0.0, 0.0);
+  if (sub < j.M) a = src.phasor(st, sub);
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int R = r == 0 ? kRoPhd : kRoMn, col = r == 0 ? j.kphd : j.kmn;
+    const bool want = ((mk >> R) & 1u) && col >= 0;
+    double yr = 0.0, yi = 0.0;
+    if (want && sub < j.M) {
+      const double2 b = j.F[(size_t)col * j.M + sub];   // conj(b) * a
+      yr = fma(b.x, a.x, b.y * a.y);
+      yi = fma(b.x, a.y, -b.y * a.x);
+    }
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1) {
+      yr += __shfl_xor_sync(0xffffffffu, yr, off);
+      yi += __shfl_xor_sync(0xffffffffu, yi, off);
+    }
+    if (want && sub == 0) {
+      const float fr = (float)yr, fi = (float)yi;
+      j.P[R][k] = recip_out(fmaf(fr, fr, fi * fi));
+    }
+  }
+}
+
+// The back of the queue (points flagged for PHD / MN alone): 4, 2 or 1 points per warp pass.
+template <class Src>
+__device__ __forceinline__ void refine_single_run(const ScanJob &j, const int *ks, const uint8_t *masks, int n,
+                                                  const Src &src) {
+  if (j.M <= 8) {
+    for (int c = 0; c < n; c += 4) refine_points_single<8>(j, ks + c, masks + c, min(4, n - c), src);
+  } else if (j.M <= 16) {
+    for (int c = 0; c < n; c += 2) refine_points_single<16>(j, ks + c, masks + c, min(2, n - c), src);
+  } else {
+    for (int c = 0; c < n; ++c) refine_points_single<32>(j, ks + c, masks + c, 1, src);
+  }
+}
+
 // Drains the tile's refinement queue (all threads of the CTA call this): several points per warp
 // when the factor is small enough, else one point per warp.
 template <class Src>
 __device__ __forceinline__ void drain_refinements_src(const ScanJob &j, const Src &src, ScanShared &sh) {
   __syncthreads();
-  const int n = min(sh.nflag, kFlagCap);
+  const int n = queue_front(sh.nflag), nb = queue_back(sh.nflag);
   const int warp = threadIdx.x >> 5;
   if (j.M <= 8 && j.Kf <= 8) {
     for (int i = warp * 4; i < n; i += kScanWarps * 4)
@@ -361,6 +419,9 @@ __device__ __forceinline__ void drain_refinements_src(const ScanJob &j, const Sr
     for (int i = warp; i < n; i += kScanWarps)
       refine_point_warp_src(j, sh.flags[i], src, sh.w32, sh.ph[warp], sh.yb[warp]);
   }
+  // back entries, kFlagCap - nb .. kFlagCap - 1, in chunks of 4 per warp
+  for (int i = kFlagCap - nb + warp * 4; i < kFlagCap; i += kScanWarps * 4)
+    refine_single_run(j, sh.flags + i, sh.fmask + i, min(4, kFlagCap - i), src);
   __syncthreads();
   if (threadIdx.x == 0) sh.nflag = 0;
   __syncthreads();
@@ -393,16 +454,16 @@ __device__ __forceinline__ void finish_points(const ScanJob &j, const float (&dp
                                               const float (&de)[PT], const float (&dn)[PT], int L, int k0,
                                               ScanShared &sh, const Src &src, const float *w32, const float *thr_,
                                               uint8_t *tags, int tag) {
-  bool flag[PT];
+  unsigned mk[PT];   // bit r: readout r below its threshold
 #pragma unroll
-  for (int q = 0; q < PT; ++q) flag[q] = false;
+  for (int q = 0; q < PT; ++q) mk[q] = 0u;
   float out[PT];
 #define DOA_READOUT(R, DEN)                                                   \
   if (j.P[R]) {                                                               \
     const float thr = thr_[R];                                                \
     _Pragma("unroll") for (int q = 0; q < PT; ++q) {                          \
       out[q] = __frcp_rn(fmaxf(DEN[q], FLT_MIN));                              \
-      flag[q] = flag[q] || DEN[q] < thr;                                      \
+      mk[q] |= (DEN[q] < thr ? 1u : 0u) << R;                                 \
     }                                                                         \
     store_row<PT>(j.P[R], L, k0, out);                                        \
   }
@@ -411,22 +472,32 @@ __device__ __forceinline__ void finish_points(const ScanJob &j, const float (&dp
   DOA_READOUT(kRoEv, de)
   DOA_READOUT(kRoMn, dn)
 #undef DOA_READOUT
-  int pos[PT];
+  bool over[PT];
 #pragma unroll
   for (int q = 0; q < PT; ++q) {
-    pos[q] = -1;
-    if (k0 + q < L && flag[q]) {
-      pos[q] = atomicAdd(&sh.nflag, 1);
-      if (pos[q] < kFlagCap) {
-        sh.flags[pos[q]] = k0 + q;
-        if (kExt) tags[pos[q]] = (uint8_t)tag;
+    over[q] = false;
+    if (k0 + q < L && mk[q]) {
+      // whole re-evaluation for MUSIC / EV (every E_n column) and for M > 32; PHD / MN alone
+      // need their own column only
+      const bool whole = (mk[q] & ((1u << kRoMusic) | (1u << kRoEv))) || j.M > 32;
+      const unsigned inc = whole ? 1u : 0x10000u;
+      const unsigned old = atomicAdd(&sh.nflag, inc);
+      const int f = queue_front(old), b = queue_back(old);
+      if (f + b < kFlagCap) {
+        const int slot = whole ? f : kFlagCap - 1 - b;
+        sh.flags[slot] = k0 + q;
+        sh.fmask[slot] = (uint8_t)mk[q];
+        if (kExt) tags[slot] = (uint8_t)tag;
+      } else {
+        atomicSub(&sh.nflag, inc);   // not queued (the queue is full): the count stays that of the entries
+        over[q] = true;
       }
     }
   }
   // queue overflow (more than kFlagCap small denominators before a drain): refine in place
 #pragma unroll
   for (int q = 0; q < PT; ++q)
-    if (pos[q] >= kFlagCap) refine_point_thread_src(j, k0 + q, src, w32);
+    if (over[q]) refine_point_thread_src(j, k0 + q, src, w32);
 }
 
 // Contracts the PT x MP phasor block a (points k0 .. k0+PT-1 of a job, those < L) with the factor

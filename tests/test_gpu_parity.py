@@ -315,22 +315,27 @@ def test_scan_refinement_queue_overflow(env):
     puts about half of the 20001 points below the refinement threshold (den = 1 - cos(pi u) near
     the MUSIC null), so the queue overflows and the overflowing points are re-evaluated in place,
     one thread each. Alone (per-problem scan, runs of several tiles per drain) and as 32 problems
-    sharing the grid (grid-shared scan, one tile of all 32 per drain), every point of all four
-    spectra stays within DB_TOL of the oracle."""
+    sharing the grid (grid-shared scan, one tile of all 32 per drain), with all four algorithms and
+    with PHD and MN alone (points flagged for those readouts only fill the queue from its back),
+    every point stays within DB_TOL of the oracle."""
     torch, doa = env
     base = synth.custom(2, 1, 2048, [0.0], 20.0, 0.01, seed=777)
     inst = dataclasses.replace(base, lo=-0.1, step=1e-5, L=20001)
     refs = [oracle.solve(inst.X, inst.d, alg, inst.lo, inst.step, inst.L)["P"] for alg in range(4)]
     # the MUSIC denominator near the null: far more than 1024 points below 2.05e-6 (sum |f_m|)^2 = 4.1e-6
     assert np.sum(1.0 / refs[MUSIC] < 4.1e-6) > 4 * 1024
-    for group in ([inst], [inst] * 32):
-        tensors, status = _batch_solve(torch, doa, group, [0xF] * len(group))
-        assert np.all(status == 0), status
-        for t in tensors:
-            P = t[1].cpu().numpy().reshape(4, inst.L)
-            for alg in range(4):
-                err = db_error(P[alg], refs[alg])
-                assert err < DB_TOL, (len(group), alg, err)
+    # all four spectra (MUSIC / EV flagged: the whole re-evaluation, front of the queue), and PHD + MN
+    # alone (their columns only, back of the queue)
+    for mask in (0xF, (1 << PHD) | (1 << MN)):
+        algs = [a for a in range(4) if (mask >> a) & 1]
+        for group in ([inst], [inst] * 32):
+            tensors, status = _batch_solve(torch, doa, group, [mask] * len(group))
+            assert np.all(status == 0), status
+            for t in tensors:
+                P = t[1].cpu().numpy().reshape(len(algs), inst.L)
+                for slot, alg in enumerate(algs):
+                    err = db_error(P[slot], refs[alg])
+                    assert err < DB_TOL, (mask, len(group), alg, err)
 
 
 def test_batch_paper_density_sample_polished(env):
