@@ -808,7 +808,9 @@ doa_status doa_solve_batch(const void *plan_host, const void *plan_dev, void *ws
   auto mark = [&](int i) -> bool {
     return !stage_events || cudaEventRecord(static_cast<cudaEvent_t>(stage_events[i]), s) == cudaSuccess;
   };
-  if (!mark(0) || launch_grid_tables(pd, h, w, s) != cudaSuccess || launch_geo_tables(pd, h, w, s) != cudaSuccess)
+  // the per-solve counters at the start of the workspace (the persistent scans' next unit / run)
+  if (!mark(0) || cudaMemsetAsync(w, 0, (size_t)kWsCounterBytes, s) != cudaSuccess ||
+      launch_grid_tables(pd, h, w, s) != cudaSuccess || launch_geo_tables(pd, h, w, s) != cudaSuccess)
     return DOA_ECUDA;
   if (!mark(1) || launch_covariance_batch(pd, h, w, s) != cudaSuccess) return DOA_ECUDA;
   if (!mark(2) || launch_eig_batch(pd, h, w, status, s) != cudaSuccess) return DOA_ECUDA;

@@ -128,7 +128,14 @@ __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const uint8_t 
   ScanJob j{};
   const PlanProblem *pp = nullptr;
   const PlanGrid *g = nullptr;
-  for (int64_t run = blockIdx.x; run * run_len < ntiles; run += gridDim.x) {
+  // runs are taken from a counter in the workspace (zeroed at the start of the solve)
+  __shared__ unsigned s_run;
+  unsigned *next_run = reinterpret_cast<unsigned *>(ws) + kCtrBatch + bucket;
+  for (;;) {
+    if (threadIdx.x == 0) s_run = atomicAdd(next_run, 1u);
+    __syncthreads();   // the previous run ended with a barrier, so s_run is not read while rewritten
+    const int64_t run = s_run;
+    if (run * run_len >= ntiles) break;
     const int64_t t_begin = run * run_len, t_end = min(ntiles, t_begin + run_len);
     int u = 0, hi = nunits - 1;
     while (u < hi) {  // last problem with tile_start <= t_begin
@@ -179,7 +186,6 @@ __global__ void __launch_bounds__(kScanThreads) scan_prep_kernel(const uint8_t *
   const int32_t *list = reinterpret_cast<const int32_t *>(plan + h->off_sgl[bucket]);
   const PlanProblem *probs = reinterpret_cast<const PlanProblem *>(plan + h->off_prob);
   const int i = blockIdx.x * kScanWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (blockIdx.x == 0 && threadIdx.x == 0) reinterpret_cast<unsigned *>(ws)[bucket] = 0u;   // next unit
   if (i >= h->sg_probs[bucket]) return;
   const PlanProblem &pp = probs[list[i]];
   const int M = pp.p.M, Kf = pp.Kf, Kn = pp.Kn;
@@ -243,10 +249,11 @@ __global__ void __launch_bounds__(kScanThreads, shared_min_blocks<MP, PT>())
   constexpr int TP = kScanThreads * PT;
   if (tid == 0) sh.nflag = 0;
   int cached = -1;   // group whose jobs are in shared memory (every thread holds the same value)
-  // units are taken from a counter in the workspace (reset by scan_prep_kernel), so the CTAs
-  // that meet cheap units (a grid's short last tile) take more of them and all end together
+  // units are taken from a counter in the workspace (zeroed at the start of the solve), so the
+  // CTAs that meet cheap units (a grid's short last tile, few near-null points) take more of them
+  // and all end together
   __shared__ unsigned s_unit;
-  unsigned *next_unit = reinterpret_cast<unsigned *>(ws) + bucket;
+  unsigned *next_unit = reinterpret_cast<unsigned *>(ws) + kCtrShared + bucket;
   for (;;) {
     if (tid == 0) s_unit = atomicAdd(next_unit, 1u);
     __syncthreads();   // the previous unit ended with a barrier, so s_unit is not read while rewritten

@@ -300,6 +300,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_geometry_batch_kernel(const
   const PlanProblem *pp = nullptr;
   const float2 *tab = nullptr;
   int ldt = 0;
+  // (runs dealt round-robin: taking them from a counter, as the ULA scans do, measured slower here)
   for (int64_t run = blockIdx.x; run * run_len < ntiles; run += gridDim.x) {
     const int64_t t_begin = run * run_len, t_end = min(ntiles, t_begin + run_len);
     int u = 0, hi = nunits - 1;
