@@ -408,10 +408,11 @@ constexpr int kCovTcMaxN = 1 << 21;
 cudaError_t ensure_smem_attr(const void *func, int bytes);
 int device_sm_count();
 // The first bytes of a batch workspace hold per-solve counters (uint32, zeroed at the start of
-// every doa_solve_batch): the next unit of the grid-shared FP32 scan (slot bucket) and the next
-// run of the per-problem FP32 scan (slot 4 + bucket).
+// every doa_solve_batch): the next unit of the grid-shared FP32 scan (slot bucket), the next run
+// of the per-problem FP32 scan (slot 4 + bucket) and the next unit of the grid-shared
+// tensor-core scan (slot 8).
 constexpr int64_t kWsCounterBytes = 256;
-constexpr int kCtrShared = 0, kCtrBatch = 4;
+constexpr int kCtrShared = 0, kCtrBatch = 4, kCtrTcg = 8;
 // Shared memory of the current device: per SM, per block (opt-in maximum), reserved per block.
 struct SmemLimits {
   int per_sm, per_block, reserve;

@@ -303,7 +303,15 @@ __global__ void __launch_bounds__(kTgThreads, 1) tcg_scan_kernel(const uint8_t *
   uint32_t tph[2] = {0u, 0u}, mph[2] = {0u, 0u};
   bool tpend[2] = {false, false}, mpend[2] = {false, false};
 
-  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+  // units are taken from a counter in the workspace (zeroed at the start of the solve), so the
+  // CTAs whose units re-evaluate many points take fewer of them
+  __shared__ unsigned s_unit;
+  unsigned *next_unit = reinterpret_cast<unsigned *>(ws) + kCtrTcg;
+  for (;;) {
+    if (tid == 0) s_unit = atomicAdd(next_unit, 1u);
+    __syncthreads();   // the previous unit ended with a barrier, so s_unit is not read while rewritten
+    const int64_t u = s_unit;
+    if (u >= nunits) break;
     int ci = 0, hi = nchunks - 1;
     while (ci < hi) {   // last chunk with unit_start <= u
       const int mid = (ci + hi + 1) >> 1;
