@@ -50,7 +50,7 @@ def workload_name(batch):
 # is an independent, equal unit; profiles/paper_uca_geometry_scan_ncu.md). Reset an entry to None
 # when its kernel changes.
 TRAFFIC_BYTES = {
-    "scan_shared_kernel<16,4>": 38949632 + 1117904128,        # read + written, 4096-problem launch
+    "scan_shared_kernel<16,4>": 35197696 + 1122881024,        # read + written, 4096-problem launch
     "covariance_tc_batch_kernel<16>": 2148942336 + 15538176,
     "scan_geometry_batch_kernel<8,4>": 2 * (4493312 + 206536704),   # 2048-problem capture x 2
     "scan_geometry_batch_kernel<8,2>": None,
