@@ -738,7 +738,7 @@ def run_large_array(args, emit=True):
     streams = [torch.cuda.Stream(dev) for _ in range(nstreams)]
     main = torch.cuda.current_stream(dev)
     # (contraction precision, Jacobi arithmetic); the double-float Jacobi spreads each M=64 matrix
-    # over a whole CTA on the FP32 pipe, the FP64 form is kept beside it
+    # over a four-CTA cluster on the FP32 pipe, the FP64 form (one CTA) is kept beside it
     forms = {"fp32": (doa.FP32, doa.EIG_DOUBLE_FLOAT), "bf16": (doa.BF16, doa.EIG_DOUBLE_FLOAT),
              "bf16x3": (doa.BF16X3, doa.EIG_DOUBLE_FLOAT), "fp16x3": (doa.FP16X3, doa.EIG_DOUBLE_FLOAT),
              "fp16x3_fp64_jacobi": (doa.FP16X3, doa.EIG_FP64)}
@@ -748,7 +748,7 @@ def run_large_array(args, emit=True):
 
     def solve(form, events=None):
         # one stage at a time over all replicas, the replicas of a stage spread over the streams
-        # (the single-CTA Jacobi of one replica per SM; the tensor kernels fill the GPU)
+        # (the Jacobi of one replica per four-SM cluster; the tensor kernels fill the GPU)
         prec, eprec = form
         calls = (lambda r, st: doa.doa_covariance(X[r], R64=R[r], prec=prec, stream=st),
                  lambda r, st: doa.doa_noise_subspace_prec(R[r], d, doa.MUSIC, eprec, B[r], info[r:r + 1],

@@ -15,15 +15,19 @@
 // A <- J^H A for all rotated pairs, then the column updates A <- A J and V <- V J. A pair is
 // rotated when |a_pq|^2 > tol^2 |a_pp a_qq|; a matrix has converged after a sweep that rotates
 // nothing. A warp holds 32 / (NP/2) matrices so that every lane owns one pair's rotation
-// (8 matrices of M <= 8, 4 of M <= 16, 2 of M <= 32); a matrix of M <= 64 gets a whole CTA.
+// (8 matrices of M <= 8, 4 of M <= 16, 2 of M <= 32); a matrix of M <= 64 gets a whole CTA in
+// FP64, or in double-float a cluster of four CTAs that split its rows (jacobi_cluster_df).
 // The element updates of each matrix are spread over all threads of its group. A and V live in shared memory with a padded row stride
 // (NP + 1 complex128) so that column accesses by consecutive lanes hit distinct banks.
+#include <cooperative_groups.h>
 #include <math_constants.h>
 
 #include "doa_internal.cuh"
 
 namespace doa {
 namespace {
+
+namespace cg = cooperative_groups;
 
 struct Rot {
   double c, sr, si;  // cosine and sigma = s e^{j phi}
@@ -300,9 +304,8 @@ struct EigSmemDF {   // the same bytes as EigSmem<NP>, viewed as double-float
 };
 static_assert(sizeof(RotDF) == sizeof(Rot), "rotation records share storage");
 
-template <int NP>
-__device__ __forceinline__ bool rotation_df(EigSmemDF<NP> &s, int p, int q, RotDF &ro) {
-  const float4 app = s.a(p, p), aqq = s.a(q, q), apq = s.a(p, q);
+// Rotation of a pair from its entries a_pp, a_qq, a_pq; returns false below threshold.
+__device__ __forceinline__ bool rotation_df_of(const float4 app, const float4 aqq, const float4 apq, RotDF &ro) {
   const float n2 = apq.x * apq.x + apq.z * apq.z;
   if (!(n2 > 0.f) || !(n2 > kJacobiTolDF * kJacobiTolDF * fabsf(app.x * aqq.x))) return false;
   const float r = rsqrtf(n2);                                   // 1 / |a_pq|
@@ -327,6 +330,11 @@ __device__ __forceinline__ bool rotation_df(EigSmemDF<NP> &s, int p, int q, RotD
   const float eps = delta * fmaf(0.375f, delta, -0.5f);        // (1 + delta)^(-1/2) - 1 to O(delta^3)
   ro = RotDF{F2{c0, c0 * eps}, F2{sr0, sr0 * eps}, F2{si0, si0 * eps}};
   return true;
+}
+
+template <int NP>
+__device__ __forceinline__ bool rotation_df(EigSmemDF<NP> &s, int p, int q, RotDF &ro) {
+  return rotation_df_of(s.a(p, p), s.a(q, q), s.a(p, q), ro);
 }
 
 // Same contract as jacobi_group, in double-float arithmetic; on return A and V hold FP64.
@@ -476,6 +484,179 @@ __device__ void jacobi_group_df(EigSmem<NP> *mats64, const int *Ms, const double
     }
   }
   g::sync();
+}
+
+// ---- One matrix of 33 <= M <= 64 on a cluster of four CTAs (double-float) ----
+// The same rounds as jacobi_group_df with the rows of A and V spread over the cluster: CTA c owns
+// rows 16c .. 16c+15 (one per warp). For a round's rotation J (n/2 disjoint pairs) the element
+// (i, col) of J^H A J needs only rows i and partner(i) at the columns of col's pair, so warp w
+// forms row i's new values pair by pair (lane j: columns p_j, q_j): first the row mix with the
+// partner row (read through distributed shared memory when another CTA owns it), then the column
+// mix, in the same double-float operations and order as the row and column passes of
+// jacobi_group_df; V's rows take the column mix in place. A is double-buffered, so one cluster
+// barrier per round orders every CTA's reads of the current buffer before the writes that reuse
+// it. Warp 0 of every CTA forms the round's rotations from the same bytes with the same code, so
+// every CTA takes the same decisions (rounds to skip, sweeps, convergence) and meets the same
+// barriers.
+constexpr int kClRanks = 4;                 // CTAs per matrix
+constexpr int kClRows = 64 / kClRanks;      // rows of A and V owned by a CTA (one per warp)
+constexpr int kClThreads = 32 * kClRows;
+static_assert(kClThreads == grp_threads<64>(), "the cluster's rank 0 runs the M <= 64 finishing code");
+
+struct ClusterDF {
+  float4 A[2][kClRows][64];    // double-float (hi, lo) re, (hi, lo) im
+  float4 V[kClRows][64];
+  RotDF rot[2][32];            // the round's rotations, by round parity
+  int2 pq[2][32];
+  unsigned mask[2];
+};
+
+// Shared memory of a cluster kernel: the FP64 record that rank 0 finishes in, then the rows.
+constexpr int kClFinBytes = (int)((sizeof(EigSmem<64>) + 15) / 16 * 16);
+constexpr int kClSmemBytes = kClFinBytes + (int)sizeof(ClusterDF);
+
+// Row mixes of A <- J^H A: row p of the pair becomes c x_p - sigma x_q, row q conj(sigma) x_p + c x_q.
+__device__ __forceinline__ float4 mix_row_p(const RotDF &ro, float4 xp, float4 xq) {
+  return cplx(dot3(ro.c, re_of(xp), neg(ro.sr), re_of(xq), ro.si, im_of(xq)),
+              dot3(ro.c, im_of(xp), neg(ro.sr), im_of(xq), neg(ro.si), re_of(xq)));
+}
+__device__ __forceinline__ float4 mix_row_q(const RotDF &ro, float4 xp, float4 xq) {
+  return cplx(dot3(ro.c, re_of(xq), ro.sr, re_of(xp), ro.si, im_of(xp)),
+              dot3(ro.c, im_of(xq), ro.sr, im_of(xp), neg(ro.si), re_of(xp)));
+}
+// Column mix of A <- A J (and V <- V J): column p becomes c x_p - conj(sigma) x_q, column q
+// sigma x_p + c x_q.
+__device__ __forceinline__ void mix_cols(const RotDF &ro, float4 &xp, float4 &xq) {
+  const float4 np = cplx(dot3(ro.c, re_of(xp), neg(ro.sr), re_of(xq), neg(ro.si), im_of(xq)),
+                         dot3(ro.c, im_of(xp), neg(ro.sr), im_of(xq), ro.si, re_of(xq)));
+  const float4 nq = cplx(dot3(ro.c, re_of(xq), ro.sr, re_of(xp), neg(ro.si), im_of(xp)),
+                         dot3(ro.c, im_of(xq), ro.sr, im_of(xp), ro.si, re_of(xp)));
+  xp = np;
+  xq = nq;
+}
+
+// Cyclic Jacobi of the Hermitian M x M matrix R (FP64, row-major; the upper triangle is read) in
+// double-float over the calling cluster. Returns the sweep count (> 0), -DOA_ENONFINITE or
+// -DOA_ENOCONV, the same in every CTA; on a positive return rank 0's fin holds V and the diagonal
+// of A in FP64 (the finishing code reads nothing else of A).
+__device__ int jacobi_cluster_df(ClusterDF &w, EigSmem<64> &fin, int M, const double2 *__restrict__ R) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31;
+  const int row = rank * kClRows + wp;
+  // every CTA checks the whole upper triangle, so all reach the same verdict
+  bool finite = true;
+  for (int e = tid; e < M * M; e += kClThreads) {
+    const int i = e / M, k = e % M;
+    if (i > k) continue;
+    const double2 v = R[e];
+    finite = finite && isfinite(v.x) && (i == k || isfinite(v.y));
+  }
+  for (int e = tid; e < kClRows * 64; e += kClThreads) {
+    const int li = e / 64, k = e % 64, i = rank * kClRows + li;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), v = a;
+    if (i < M && k < M) {
+      double2 x;
+      if (i <= k) {
+        x = R[i * M + k];
+      } else {
+        x = R[k * M + i];
+        x.y = -x.y;
+      }
+      if (i == k) x.y = 0.0;
+      a = df_of(x);
+      v.x = i == k ? 1.f : 0.f;
+    }
+    w.A[0][li][k] = a;
+    w.A[1][li][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    w.V[li][k] = v;
+  }
+  const bool ok = __syncthreads_and(finite) != 0;
+  cl.sync();   // every CTA's rows are in place before the first remote read
+  if (!ok) return -DOA_ENONFINITE;
+  const int n = (M + 1) & ~1;
+  int cur = 0, res = -DOA_ENOCONV;
+  unsigned t = 0;   // rounds so far: the parity selects the rotation record
+  for (int sweep = 1; sweep <= kMaxSweeps; ++sweep) {
+    bool rotated = false;
+    for (int r = 0; r < n - 1; ++r, ++t) {
+      const int sl = (int)(t & 1u);
+      if (wp == 0) {
+        bool act = false;
+        if (lane < n / 2) {
+          const int a = rr_player(lane, r, n), b = rr_player(n - 1 - lane, r, n);
+          const int p = min(a, b), q = max(a, b);
+          w.pq[sl][lane] = make_int2(p, q);
+          if (q < M) {
+            const float4 *Ap = cl.map_shared_rank(&w.A[cur][p % kClRows][0], p / kClRows);
+            const float4 *Aq = cl.map_shared_rank(&w.A[cur][q % kClRows][0], q / kClRows);
+            RotDF ro;
+            act = rotation_df_of(Ap[p], Aq[q], Ap[q], ro);
+            if (act) w.rot[sl][lane] = ro;
+          }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, act);
+        if (lane == 0) w.mask[sl] = m;
+      }
+      __syncthreads();
+      const unsigned mask = w.mask[sl];
+      if (mask == 0u) continue;   // nothing written: the buffers stay as they are
+      rotated = true;
+      const int nxt = cur ^ 1;
+      if (row < M && lane < n / 2) {
+        const int2 pj = w.pq[sl][lane];
+        float4 xp = w.A[cur][wp][pj.x], xq = w.A[cur][wp][pj.y];
+        // the pair that holds this row: its position in the round-robin order, folded
+        const int pos = row == 0 ? 0 : ((row - 1 - r) % (n - 1) + (n - 1)) % (n - 1) + 1;
+        const int k = min(pos, n - 1 - pos);
+        if ((mask >> k) & 1u) {
+          const RotDF rk = w.rot[sl][k];
+          const int2 pk = w.pq[sl][k];
+          const int other = pk.x + pk.y - row;
+          const float4 *Ao = cl.map_shared_rank(&w.A[cur][other % kClRows][0], other / kClRows);
+          const float4 yp = Ao[pj.x], yq = Ao[pj.y];
+          if (row == pk.x) {
+            xp = mix_row_p(rk, xp, yp);
+            xq = mix_row_p(rk, xq, yq);
+          } else {
+            xp = mix_row_q(rk, yp, xp);
+            xq = mix_row_q(rk, yq, xq);
+          }
+        }
+        if ((mask >> lane) & 1u) {
+          const RotDF rj = w.rot[sl][lane];
+          mix_cols(rj, xp, xq);
+          float4 vp = w.V[wp][pj.x], vq = w.V[wp][pj.y];
+          mix_cols(rj, vp, vq);
+          w.V[wp][pj.x] = vp;
+          w.V[wp][pj.y] = vq;
+        }
+        if (row == pj.x) xp.z = xp.w = 0.f;   // the diagonal of a Hermitian matrix is real
+        if (row == pj.y) xq.z = xq.w = 0.f;
+        w.A[nxt][wp][pj.x] = xp;
+        w.A[nxt][wp][pj.y] = xq;
+      }
+      cl.sync();   // this round's writes are visible, and nobody still reads the old buffer
+      cur = nxt;
+    }
+    if (!rotated) {
+      res = sweep;
+      break;
+    }
+  }
+  if (res > 0 && rank == 0) {
+    for (int e = tid; e < M * M; e += kClThreads) {
+      const int i = e / M, k = e % M;
+      const float4 v = cl.map_shared_rank(&w.V[i % kClRows][0], i / kClRows)[k];
+      fin.v(i, k) = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+      if (i == k) {
+        const float4 a = cl.map_shared_rank(&w.A[cur][i % kClRows][0], i / kClRows)[i];
+        fin.a(i, i) = make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
+      }
+    }
+  }
+  cl.sync();   // the other CTAs' rows stay in place until rank 0 has read them
+  return res;
 }
 
 // Stable descending order of the eigenvalues (equal values keep index order).
@@ -660,14 +841,34 @@ __device__ int build_scan_factor(const PlanProblem &pp, EigSmem<NP> &s, double2 
   return st;
 }
 
+// The eigenvalues, B and the status of a single call from a finished decomposition (res: the
+// sweep count, or minus a doa_status).
+template <int NP>
+__device__ void finish_single(int M, int d, int alg, EigSmem<NP> &s, int res, double *evals, double2 *B, int *K_out,
+                              int *info) {
+  constexpr int T = grp_threads<NP>();
+  const int lane = Grp<T>::id();
+  int st = 0;
+  if (res > 0) {
+    sort_desc<NP>(M, s);
+    if (evals)
+      for (int i = lane; i < M; i += T) evals[i] = s.lam()[s.order()[i]];
+    st = build_factor<NP>(M, d, alg, s, B);
+  } else {
+    st = -res;
+  }
+  if (lane == 0) {
+    *info = st ? -st : res;
+    if (K_out) *K_out = (alg == DOA_PHD || alg == DOA_MN) ? 1 : M - d;
+  }
+}
+
 template <int NP, bool kDF>
 __global__ void __launch_bounds__(grp_threads<NP>()) eig_single_kernel(const double2 *R64, int M, int d, int alg, double *evals,
                                                        double2 *B, int *K_out, int *info) {
   extern __shared__ __align__(16) uint8_t smem[];
   constexpr int G = mats_per_warp<NP>();
   EigSmem<NP> *mats = reinterpret_cast<EigSmem<NP> *>(smem);
-  constexpr int T = grp_threads<NP>();
-  const int lane = Grp<T>::id();
   int Ms[G];
   const double2 *Rs[G];
   int res[G];
@@ -679,20 +880,66 @@ __global__ void __launch_bounds__(grp_threads<NP>()) eig_single_kernel(const dou
     jacobi_group_df<NP, G>(mats, Ms, Rs, res);
   else
     jacobi_group<NP, G>(mats, Ms, Rs, res);
-  EigSmem<NP> &s = mats[0];
+  finish_single<NP>(M, d, alg, mats[0], res[0], evals, B, K_out, info);
+}
+
+// Single call, 33 <= M <= 64, double-float: one four-CTA cluster; rank 0 finishes.
+__global__ void __cluster_dims__(kClRanks, 1, 1) __launch_bounds__(kClThreads, 1)
+    eig_cluster_single_kernel(const double2 *R64, int M, int d, int alg, double *evals, double2 *B, int *K_out,
+                              int *info) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  EigSmem<64> &s = *reinterpret_cast<EigSmem<64> *>(smem);
+  ClusterDF &w = *reinterpret_cast<ClusterDF *>(smem + kClFinBytes);
+  const int res = jacobi_cluster_df(w, s, M, R64);
+  if (cg::this_cluster().block_rank() != 0) return;
+  finish_single<64>(M, d, alg, s, res, evals, B, K_out, info);
+}
+
+// A batch problem's outputs from its finished decomposition (res: the sweep count, or minus a
+// doa_status): evals, the scan factor and EV weights, the optional B, order estimates and
+// proposal features, and the status.
+template <int NP>
+__device__ void finish_batch(const PlanProblem &pp, const PlanJob *jobs, EigSmem<NP> &s, int res, uint8_t *ws,
+                             int *status) {
+  constexpr int T = grp_threads<NP>();
+  const int lane = Grp<T>::id();
+  const int M = pp.p.M, d = pp.p.d;
   int st = 0;
-  if (res[0] > 0) {
+  if (pp.p.features) {
+    // proposal-network input: upper triangle of R / tr(R), (re, im) pairs row by row
+    const double2 *R = reinterpret_cast<const double2 *>(ws + pp.r64_off);
+    double tr = 0.0;
+    for (int i = 0; i < M; ++i) tr += R[i * M + i].x;
+    const double inv = tr > 0.0 ? 1.0 / tr : 0.0;
+    for (int e = lane; e < M * (M + 1) / 2; e += T) {
+      int i = 0, rem = e;
+      while (rem >= M - i) { rem -= M - i; ++i; }
+      const double2 v = R[i * M + i + rem];
+      pp.p.features[2 * e] = (float)(v.x * inv);
+      pp.p.features[2 * e + 1] = (float)(v.y * inv);
+    }
+  }
+  double2 *F = reinterpret_cast<double2 *>(ws + pp.fac_off);
+  double *w = reinterpret_cast<double *>(F + (size_t)M * (M + 1));
+  if (res > 0) {
     sort_desc<NP>(M, s);
-    if (evals)
-      for (int i = lane; i < M; i += T) evals[i] = s.lam()[s.order()[i]];
-    st = build_factor<NP>(M, d, alg, s, B);
+    if (pp.p.evals)
+      for (int i = lane; i < M; i += T) pp.p.evals[i] = s.lam()[s.order()[i]];
+    st = build_scan_factor<NP>(pp, s, F, w);
+    if (!noise_orthonormal<NP>(M, d, s) && !st) st = DOA_ENOCONV;
+    if (pp.p.B_out) build_factor<NP>(M, d, jobs[pp.first_job].alg, s, reinterpret_cast<double2 *>(pp.p.B_out));
+    if (pp.p.order_est) {
+      Grp<T>::sync();
+      model_order<NP>(M, pp.p.N, s, pp.p.order_est);
+    }
   } else {
-    st = -res[0];
+    st = -res;
+    // a failed decomposition leaves a zero factor, so the scan writes the 1/FLT_MIN sentinel
+    for (int e = lane; e < M * pp.Kf; e += T) F[e] = make_double2(0.0, 0.0);
+    for (int e = lane; e < pp.Kn; e += T) w[e] = 0.0;
   }
-  if (lane == 0) {
-    *info = st ? -st : res[0];
-    if (K_out) *K_out = (alg == DOA_PHD || alg == DOA_MN) ? 1 : M - d;
-  }
+  if (lane == 0) *status = st;
+  Grp<T>::sync();
 }
 
 template <int NP, int G>
@@ -724,47 +971,41 @@ __global__ void __launch_bounds__(32 * eig_warps<NP>(), eig_min_ctas<NP>()) eig_
     jacobi_group_df<NP, G>(mats, Ms, Rs, res);
   for (int j = 0; j < G; ++j) {
     if (prob[j] < 0) continue;
-    const PlanProblem &pp = probs[prob[j]];
-    EigSmem<NP> &s = mats[j];
-    const int M = pp.p.M, d = pp.p.d;
-    int st = 0;
-    if (pp.p.features) {
-      // proposal-network input: upper triangle of R / tr(R), (re, im) pairs row by row
-      const double2 *R = reinterpret_cast<const double2 *>(ws + pp.r64_off);
-      double tr = 0.0;
-      for (int i = 0; i < M; ++i) tr += R[i * M + i].x;
-      const double inv = tr > 0.0 ? 1.0 / tr : 0.0;
-      for (int e = lane; e < M * (M + 1) / 2; e += T) {
-        int i = 0, rem = e;
-        while (rem >= M - i) { rem -= M - i; ++i; }
-        const double2 v = R[i * M + i + rem];
-        pp.p.features[2 * e] = (float)(v.x * inv);
-        pp.p.features[2 * e + 1] = (float)(v.y * inv);
-      }
-    }
-    double2 *F = reinterpret_cast<double2 *>(ws + pp.fac_off);
-    double *w = reinterpret_cast<double *>(F + (size_t)M * (M + 1));
-    if (res[j] > 0) {
-      sort_desc<NP>(M, s);
-      if (pp.p.evals)
-        for (int i = lane; i < M; i += T) pp.p.evals[i] = s.lam()[s.order()[i]];
-      st = build_scan_factor<NP>(pp, s, F, w);
-      if (!noise_orthonormal<NP>(M, d, s) && !st) st = DOA_ENOCONV;
-      if (pp.p.B_out) build_factor<NP>(M, d, jobs[pp.first_job].alg, s, reinterpret_cast<double2 *>(pp.p.B_out));
-      if (pp.p.order_est) {
-        Grp<T>::sync();
-        model_order<NP>(M, pp.p.N, s, pp.p.order_est);
-      }
-    } else {
-      st = -res[j];
-      // a failed decomposition leaves a zero factor, so the scan writes the 1/FLT_MIN sentinel
-      for (int e = lane; e < M * pp.Kf; e += T) F[e] = make_double2(0.0, 0.0);
-      for (int e = lane; e < pp.Kn; e += T) w[e] = 0.0;
-    }
-    if (lane == 0) status[prob[j]] = st;
-    Grp<T>::sync();
+    finish_batch<NP>(probs[prob[j]], jobs, mats[j], res[j], ws, status + prob[j]);
   }
 }
+
+// Bucket M <= 64 of the batch in double-float: one four-CTA cluster per problem; rank 0 finishes.
+// A problem that asks for the FP64 Jacobi runs it in rank 0 alone (the other CTAs leave at once).
+__global__ void __cluster_dims__(kClRanks, 1, 1) __launch_bounds__(kClThreads, 1)
+    eig_cluster_batch_kernel(const uint8_t *plan, uint8_t *ws, int bucket, int *status) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  EigSmem<64> &s = *reinterpret_cast<EigSmem<64> *>(smem);
+  ClusterDF &w = *reinterpret_cast<ClusterDF *>(smem + kClFinBytes);
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(plan);
+  const int idx = (int)(blockIdx.x / kClRanks);   // the same for every CTA of the cluster
+  if (idx >= h->eig_count[bucket]) return;
+  const int32_t *list = reinterpret_cast<const int32_t *>(plan + h->off_eig[bucket]);
+  const PlanProblem *probs = reinterpret_cast<const PlanProblem *>(plan + h->off_prob);
+  const PlanJob *jobs = reinterpret_cast<const PlanJob *>(plan + h->off_job);
+  const int prob = list[idx];
+  const PlanProblem &pp = probs[prob];
+  const double2 *R = reinterpret_cast<const double2 *>(ws + pp.r64_off);
+  const bool rank0 = cg::this_cluster().block_rank() == 0;
+  int res;
+  if (pp.p.eig_prec == DOA_EIG_FP64) {
+    if (!rank0) return;
+    int Ms[1] = {pp.p.M}, r1[1];
+    const double2 *Rs[1] = {R};
+    jacobi_group<64, 1>(&s, Ms, Rs, r1);
+    res = r1[0];
+  } else {
+    res = jacobi_cluster_df(w, s, pp.p.M, R);
+    if (!rank0) return;
+  }
+  finish_batch<64>(pp, jobs, s, res, ws, status + prob);
+}
+
 
 template <int NP, bool kDF>
 cudaError_t run_single_p(const double2 *R64, int M, int d, int alg, double *evals, double2 *B, int *K_out,
@@ -776,11 +1017,22 @@ cudaError_t run_single_p(const double2 *R64, int M, int d, int alg, double *eval
   return cudaGetLastError();
 }
 
+cudaError_t run_single_cluster(const double2 *R64, int M, int d, int alg, double *evals, double2 *B, int *K_out,
+                               int *info, cudaStream_t st) {
+  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void *>(eig_cluster_single_kernel), kClSmemBytes);
+  if (e != cudaSuccess) return e;
+  eig_cluster_single_kernel<<<kClRanks, kClThreads, kClSmemBytes, st>>>(R64, M, d, alg, evals, B, K_out, info);
+  return cudaGetLastError();
+}
+
 template <int NP>
 cudaError_t run_single(const double2 *R64, int M, int d, int alg, int prec, double *evals, double2 *B, int *K_out,
                        int *info, cudaStream_t st) {
-  return prec == DOA_EIG_FP64 ? run_single_p<NP, false>(R64, M, d, alg, evals, B, K_out, info, st)
-                              : run_single_p<NP, true>(R64, M, d, alg, evals, B, K_out, info, st);
+  if (prec == DOA_EIG_FP64) return run_single_p<NP, false>(R64, M, d, alg, evals, B, K_out, info, st);
+  if constexpr (NP == 64)
+    return run_single_cluster(R64, M, d, alg, evals, B, K_out, info, st);
+  else
+    return run_single_p<NP, true>(R64, M, d, alg, evals, B, K_out, info, st);
 }
 
 // Warps per CTA: the count (up to eig_warps) that keeps the most matrices resident per SM, the
@@ -827,6 +1079,17 @@ cudaError_t run_batch(const uint8_t *plan, const PlanHeader &h, uint8_t *ws, int
   if (g >= 4 && mats_per_warp<NP>() >= 4) return run_batch_g<NP, (mats_per_warp<NP>() >= 4 ? 4 : 1)>(plan, count, ws, status, bucket, st);
   if (g >= 2 && mats_per_warp<NP>() >= 2) return run_batch_g<NP, (mats_per_warp<NP>() >= 2 ? 2 : 1)>(plan, count, ws, status, bucket, st);
   return run_batch_g<NP, 1>(plan, count, ws, status, bucket, st);
+}
+
+// Bucket M <= 64: one four-CTA cluster per problem.
+cudaError_t run_batch_cluster(const uint8_t *plan, const PlanHeader &h, uint8_t *ws, int *status, int bucket,
+                              cudaStream_t st) {
+  const int count = h.eig_count[bucket];
+  if (count == 0) return cudaSuccess;
+  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void *>(eig_cluster_batch_kernel), kClSmemBytes);
+  if (e != cudaSuccess) return e;
+  eig_cluster_batch_kernel<<<(unsigned)count * kClRanks, kClThreads, kClSmemBytes, st>>>(plan, ws, bucket, status);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -890,7 +1153,7 @@ cudaError_t launch_eig_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8
   if ((e = run_batch<8>(plan_dev, h, ws, status, 0, s)) != cudaSuccess) return e;
   if ((e = run_batch<16>(plan_dev, h, ws, status, 1, s)) != cudaSuccess) return e;
   if ((e = run_batch<32>(plan_dev, h, ws, status, 2, s)) != cudaSuccess) return e;
-  return run_batch<64>(plan_dev, h, ws, status, 3, s);
+  return run_batch_cluster(plan_dev, h, ws, status, 3, s);
 }
 
 }  // namespace doa

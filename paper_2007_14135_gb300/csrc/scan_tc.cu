@@ -369,8 +369,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) scan_tc_kernel(TcArgs a, int nt
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(lay.tmem_cols));
 }
 
-int g_tc_sms = 0;
-
 }  // namespace
 
 cudaError_t launch_scan_tc_single(const double2 *B, int M, int K, int L, double lo, double step, int prec,
@@ -378,14 +376,9 @@ cudaError_t launch_scan_tc_single(const double2 *B, int M, int K, int L, double 
   const TcLayout lay = tc_layout(M, K, prec);
   cudaError_t e = cudaFuncSetAttribute(scan_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);
   if (e != cudaSuccess) return e;
-  if (g_tc_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_tc_sms <= 0) g_tc_sms = 1;
-  }
+  const int sms = device_sm_count();
   const int ntiles = (L + kTcRows - 1) / kTcRows;
-  const int grid = ntiles < g_tc_sms ? ntiles : g_tc_sms;
+  const int grid = ntiles < sms ? ntiles : sms;
   TcArgs a{B, M, K, L, prec, lo, step, S, P};
   scan_tc_kernel<<<grid, kTcThreads, lay.total, s>>>(a, ntiles);
   return cudaGetLastError();

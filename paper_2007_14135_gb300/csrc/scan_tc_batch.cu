@@ -449,27 +449,16 @@ __global__ void __launch_bounds__(kTbThreads, 2) scan_tc_batch_kernel(const uint
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
 }
 
-int g_tb_sms = 0;
-
 }  // namespace
 
 cudaError_t launch_scan_tc_batch(const uint8_t *plan_dev, const PlanHeader &h, uint8_t *ws, int *status,
                                  cudaStream_t s) {
   if (h.tc_jobs == 0 || h.tc_tiles == 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(scan_tc_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTbSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  if (g_tb_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_tb_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_tb_sms <= 0) g_tb_sms = 1;
-  }
+  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void *>(scan_tc_batch_kernel), kTbSmem);
+  if (e != cudaSuccess) return e;
+  const int sms = device_sm_count();
   const int64_t runs = (h.tc_tiles + kTbRun - 1) / kTbRun;
-  int64_t grid = (int64_t)g_tb_sms * (h.tc_cols <= 256 ? 2 : 1);   // TMEM: 512 columns per SM
+  int64_t grid = (int64_t)sms * (h.tc_cols <= 256 ? 2 : 1);   // TMEM: 512 columns per SM
   if (grid > runs) grid = runs;
   scan_tc_batch_kernel<<<(unsigned)grid, kTbThreads, kTbSmem, s>>>(plan_dev, ws, status);
   return cudaGetLastError();
