@@ -68,7 +68,7 @@ def test_noise_subspace(env, M, d):
         assert np.max(np.abs(Cg - Co)) < 1e-10 * np.max(np.abs(Co)), (alg, np.max(np.abs(Cg - Co)))
 
 
-@pytest.mark.parametrize("M,d", [(5, 2), (16, 4), (32, 16), (64, 8)])
+@pytest.mark.parametrize("M,d", [(5, 2), (16, 4), (32, 16), (33, 3), (47, 6), (64, 8)])
 def test_noise_subspace_double_float(env, M, d):
     """doa_noise_subspace_prec with the double-float Jacobi (~48-bit rotations, FP64 output): the
     same eigenvalues (1e-12 of the largest) and weighting matrices C = B B^H (1e-10) as the FP64
@@ -467,6 +467,23 @@ def test_batch_fp64_jacobi(env):
     insts = [synth.paper_density(i) for i in range(3)] + [synth.custom(32, 6, 3000, None, 12.0, 0.1, seed=41),
                                                           synth.custom(8, 2, 900, None, 8.0, 0.1, seed=42)]
     masks = [0xF] * len(insts)
+    _check_batch(torch, doa, insts, masks, eig_prec=1)
+    a, _ = _batch_solve(torch, doa, insts, masks, eig_prec=1)
+    b, _ = _batch_solve(torch, doa, insts, masks, eig_prec=0)
+    for ta, tb in zip(a, b):
+        assert db_error(ta[1].cpu().numpy(), tb[1].cpu().numpy().astype(np.float64)) < 1e-3
+
+
+def test_batch_cluster_jacobi_bucket(env):
+    """The batch's M <= 64 bucket: double-float Jacobi on four-CTA clusters (odd M pads the round-
+    robin order with a skipped index; M = 33 leaves the fourth CTA without rows) and the FP64
+    Jacobi in one CTA of the same kernel; both meet the oracle bar and agree with each other."""
+    torch, doa = env
+    insts = [synth.custom(33, 3, 2000, None, 12.0, 0.1, seed=51),
+             synth.custom(48, 5, 2500, None, 10.0, 0.1, seed=52),
+             synth.custom(64, 8, 4000, None, 12.0, 0.1, seed=53)]
+    masks = [0xF, 0b0110, 0xF]
+    _check_batch(torch, doa, insts, masks, eig_prec=0)
     _check_batch(torch, doa, insts, masks, eig_prec=1)
     a, _ = _batch_solve(torch, doa, insts, masks, eig_prec=1)
     b, _ = _batch_solve(torch, doa, insts, masks, eig_prec=0)
