@@ -164,8 +164,10 @@ doa_status doa_noise_subspace(const double *R64, int M, int d, int alg, double *
 /* doa_noise_subspace with the Jacobi's arithmetic chosen (doa_eig_prec): doa_noise_subspace is
  * this call with DOA_EIG_FP64. With DOA_EIG_DOUBLE_FLOAT the rotations run until no pair has
  * |a_pq| > 1e-12 sqrt(|a_pp a_qq|), the converged A and V are rounded to FP64 and sorted, and the
- * factor is formed in FP64 as for the FP64 form. For M > 32 one 512-thread CTA works on the
- * matrix (the element updates of every round spread over all its threads). DOA_EINVAL also for
+ * factor is formed in FP64 as for the FP64 form. For M > 32 the FP64 form runs one 512-thread CTA
+ * per matrix (the element updates of every round spread over all its threads); the double-float
+ * form runs a cluster of four 512-thread CTAs (about 200 KB of shared memory each, one per SM),
+ * each owning 16 rows of A and V, with results identical to the one-CTA form. DOA_EINVAL also for
  * an unknown eig_prec. */
 doa_status doa_noise_subspace_prec(const double *R64, int M, int d, int alg, int eig_prec, double *evals,
                                    double *B, int *K_out, int *info, void *stream);
